@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the pointwise thermochemistry hot path on GB300.
+
+Workload: the 53-species / 325-reaction synthetic mechanism (20 third-body, 25 Troe) on a
+flame-like field of 4,096 hexahedral elements x 8^3 GLL points = 2,097,152 points
+(polynomial order 7, Sec. 3.3 of the paper), FP64 state in HBM (inputs 0.92 GB, larger
+than L2, so no flush between iterations is needed).
+
+One step = one pass of every row of the hot path over all points, each through the C ABI:
+  thermo_eval (FP64), rates_eval (FP64), transport_eval (FP64), rates_eval (mixed),
+  transport_eval (mixed), rates_jvp, rates_vjp (with the ln A reduction).
+Each launch is bracketed by CUDA events on the launching stream.  The headline value is
+Mpoints/s of rates + transport in FP64 (points / (t_rates + t_transport) summed over the
+timed steps); the mixed form, JVP/forward and VJP/forward ratios come from the same steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the same workload on its own GPU (weak scaling, no
+collective in the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s rates+transport (FP64 vs mixed), % roofline; VJP/forward time ratio"
+UNIT = "Mpoints/s"
+MECH = "ch4_53sp_325rx"
+WORKLOAD = "flame_4096el"
+# FP64 peak of GB300: 1.25 TFLOP/s nominal dense FP64 (vendor figure at the maximum SM clock)
+FP64_PEAK_TFLOPS = 1.25
+# flops charged per exp/log/pow: table-driven exponential after Tang (1989): argument
+# reduction (2 FMA), degree-5 polynomial (5 FMA), table scaling (1 multiply) = 15 flops
+TRANSC_FLOPS = 15.0
+
+
+# ---------------------------------------------------------------------------------- flop model
+def _entries(mech, r):
+    reac = [(int(mech.reac_sp[i]), int(mech.reac_nu[i])) for i in range(mech.reac_ptr[r], mech.reac_ptr[r + 1])]
+    prod = [(int(mech.prod_sp[i]), int(mech.prod_nu[i])) for i in range(mech.prod_ptr[r], mech.prod_ptr[r + 1])]
+    return reac, prod
+
+
+def algorithmic_flops(mech) -> dict:
+    """FP64 flops per point of each row (FMA = 2, exp/log = TRANSC_FLOPS).  Minimal arithmetic
+    of the evaluated definitions, independent of how a kernel organises it."""
+    import numpy as np
+    t = TRANSC_FLOPS
+    K, R = mech.K, mech.R
+    P = K * (K - 1) // 2
+    n_eff = [int(np.sum(mech.eff[r] != 1.0)) if mech.rtype[r] else 0 for r in range(R)]
+    pre = 2 * t + 4 + K * (3 + 14)                 # ln T, 1/T, rho; y_k, sum, C_k, g_k/RT
+    per_rxn, per_rxn_d = 0.0, 0.0
+    for r in range(R):
+        reac, prod = _entries(mech, r)
+        ne = len(reac) + len(prod)
+        nu_r = sum(nu for _, nu in reac)
+        nu_p = sum(nu for _, nu in prod)
+        f = 4 + 2 * ne + 2 + (nu_r - 1) + (nu_p - 1) + 2 * t + 3 + 2 * ne
+        if mech.rtype[r] == 1:
+            f += 1 + 2 * n_eff[r]
+        if mech.rtype[r] == 2:
+            f += 2 * n_eff[r] + 4 + 2 + t + (3 if mech.troe[r, 3] > 0 else 2) * t + 4 + t + 12 + 3 + t + 2 + t + 2
+        per_rxn += f
+        # tangent (JVP) or adjoint (VJP) of the same operations: the product rule doubles every
+        # multiply, plus the chain factors of each exponential
+        per_rxn_d += f + (4 + 2 * ne + 2 + 2 * (nu_r + nu_p) + 8 + 2 * ne) + (40 if mech.rtype[r] == 2 else 0)
+    hrr = K * 14 + 2
+    rates = pre + per_rxn + hrr
+    transport = (t + 4 + 3 * K                      # ln T, Wbar, X_k
+                 + P * (6 + t + 1 + 4)              # ln D_jk cubic, exp, pressure scale, two FMA
+                 + K * 4                            # numerators (prefix/suffix) and division
+                 + K * (6 + 2 * t + 4)              # lambda_k, 1/lambda_k, two FMA
+                 + K * (6 + t + 2)                  # mu_k^1/2, sigma_k, tau_k
+                 + K * 4 + K * K * 6                # X tau, X tau^2; three FMA per pair
+                 + K * 8)                           # Wilke denominators and the mixture sum
+    thermo = 2 * t + 4 + K * (3 + 10 + 12 + 14 + 4)
+    jvp = pre + K * 16 + per_rxn_d + hrr * 2 + K * 10
+    vjp = pre + K * 24 + per_rxn_d + 10 * R + K * 8
+    return {"thermo": thermo, "rates_fp64": rates, "transport_fp64": transport, "rates_mixed": rates,
+            "transport_mixed": transport, "jvp": jvp, "vjp": vjp}
+
+
+# ---------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------- helpers
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def _traffic(kernel_row):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if the
+    kernel source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel_row)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if h == rec.get("source_sha256") else None
+
+
+def _oracle_sample(n_points):
+    """The oracle as it stands on a bounded sample of the workload (first n_points points)."""
+    import oracle
+    from paper_2409_06404_gb300 import synth
+    mech = synth.mechanism(MECH)
+    st = synth.workload_states(WORKLOAD, mech.K, n_points=n_points)
+    return oracle, mech, st
+
+
+def cpu_baseline(st_full, n_points=524288):
+    """Oracle rates + transport (FP64) on the first n_points points, all host cores."""
+    import numpy as np
+    import oracle
+    from paper_2409_06404_gb300 import synth
+    mech = synth.mechanism(MECH)
+    n_points = min(n_points, st_full.n)
+    T, p, Y = st_full.T[:n_points], st_full.p[:n_points], np.ascontiguousarray(st_full.Y[:, :n_points])
+    t0 = time.perf_counter()
+    oracle.rates(mech, T, p, Y)
+    oracle.transport(mech, T, p, Y)
+    dt = time.perf_counter() - t0
+    return {"value": n_points / dt / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {n_points} points ({n_points // 512} elements) of the {WORKLOAD} workload, "
+                      f"rates + transport FP64, OpenMP over points, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    n_points = 32768
+    oracle, mech, st = _oracle_sample(n_points)
+
+    def step():
+        oracle.rates(mech, st.T, st.p, st.Y)
+        oracle.transport(mech, st.T, st.p, st.Y)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = n_points * args.steps / dt / 1e6
+    cores = oracle.max_threads()
+    _emit({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{MECH} on {WORKLOAD} (2,097,152 points); each step a "
+                                  f"{n_points}-point sample", "mechanism": MECH, "points": n_points},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"first {n_points} points of {WORKLOAD} per step, rates + transport FP64"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# ---------------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2409_06404_gb300 as nk
+    from paper_2409_06404_gb300 import synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    mech = synth.mechanism(MECH)
+    st = synth.workload_states(WORKLOAD, mech.K, n_elements=args.elements)
+    n, K, R = st.n, mech.K, mech.R
+    m = nk.mechanism_load(mech)
+    T = torch.from_numpy(st.T).to(dev)
+    p = torch.from_numpy(st.p).to(dev)
+    Y = torch.from_numpy(st.Y).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(5000 + rank)
+    vT = torch.randn(n, generator=gen, dtype=torch.float64, device=dev)
+    vY = torch.randn((K, n), generator=gen, dtype=torch.float64, device=dev)
+    wbar = torch.randn((K, n), generator=gen, dtype=torch.float64, device=dev)
+    f64 = dict(dtype=torch.float64, device=dev)
+    out = {k: torch.empty(n, **f64) for k in ("cp", "h", "wb", "rho", "hrr", "mu", "lam", "hrr_m", "mu_m", "lam_m",
+                                               "dh", "gT")}
+    out.update({k: torch.empty((K, n), **f64) for k in ("w", "D", "w_m", "D_m", "dw", "gY")})
+    g_lnA = torch.empty(R, **f64)
+    wsb = torch.empty(max(nk.rates_vjp_workspace(m, n), 8), dtype=torch.uint8, device=dev)
+    L = nk.lib()
+    s = torch.cuda.current_stream()
+    sp = nk._vp(s.cuda_stream)
+    P = lambda t: nk._vp(t.data_ptr())
+    h = m.handle
+
+    def chk(st_):
+        if st_ != 0:
+            raise nk.NkError(st_, L.nk_last_error().decode())
+
+    rows = {
+        "thermo": lambda: chk(L.nk_thermo_eval(h, n, n, P(T), P(p), P(Y), P(out["cp"]), P(out["h"]), P(out["wb"]),
+                                               P(out["rho"]), None, None, None, sp)),
+        "rates_fp64": lambda: chk(L.nk_rates_eval(h, n, n, P(T), P(p), P(Y), None, P(out["w"]), P(out["hrr"]), 0, sp)),
+        "transport_fp64": lambda: chk(L.nk_transport_eval(h, n, n, P(T), P(p), P(Y), P(out["mu"]), P(out["lam"]),
+                                                          P(out["D"]), 0, sp)),
+        "rates_mixed": lambda: chk(L.nk_rates_eval(h, n, n, P(T), P(p), P(Y), None, P(out["w_m"]), P(out["hrr_m"]),
+                                                   1, sp)),
+        "transport_mixed": lambda: chk(L.nk_transport_eval(h, n, n, P(T), P(p), P(Y), P(out["mu_m"]),
+                                                           P(out["lam_m"]), P(out["D_m"]), 1, sp)),
+        "jvp": lambda: chk(L.nk_rates_jvp(h, n, n, P(T), P(p), P(Y), None, P(vT), P(vY), None, None, P(out["dw"]),
+                                          P(out["dh"]), sp)),
+        "vjp": lambda: chk(L.nk_rates_vjp(h, n, n, P(T), P(p), P(Y), None, P(wbar), None, P(out["gT"]), P(out["gY"]),
+                                          P(g_lnA), P(wsb), wsb.numel(), sp)),
+    }
+    launches_per_step = {"thermo": 1, "rates_fp64": 1, "transport_fp64": 1, "rates_mixed": 1,
+                         "transport_mixed": 1, "jvp": 1, "vjp": 2}
+    names = list(rows)
+
+    for _ in range(args.warmup):
+        for f in rows.values():
+            f()
+    torch.cuda.synchronize()
+    ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)] for k in names}
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            for k in names:
+                ev[k][i][0].record(s)
+                rows[k]()
+                ev[k][i][1].record(s)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if ws > 1:
+        dist.barrier()
+    ms = {k: [a.elapsed_time(b) for a, b in ev[k]] for k in names}
+    step_ms = [ev[names[0]][i][0].elapsed_time(ev[names[-1]][i][1]) for i in range(args.steps)]
+    fwd_ms = sum(ms["rates_fp64"]) + sum(ms["transport_fp64"])
+    mix_ms = sum(ms["rates_mixed"]) + sum(ms["transport_mixed"])
+    tot_ms = sum(step_ms)
+    vals = torch.tensor([fwd_ms, mix_ms, tot_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    fwd_ms, mix_ms, tot_ms = vals.tolist()
+    value = ws * n * args.steps / (fwd_ms * 1e-3) / 1e6
+    mixed_value = ws * n * args.steps / (mix_ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers (pinned), FP64 forward
+    e2e = None
+    if not args.no_e2e:
+        hT = torch.from_numpy(st.T).pin_memory()
+        hp = torch.from_numpy(st.p).pin_memory()
+        hY = torch.from_numpy(st.Y).pin_memory()
+        ho = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in ("hrr", "mu", "lam")}
+        ho.update({k: torch.empty((K, n), dtype=torch.float64).pin_memory() for k in ("w", "D")})
+        dT, dp_, dY = torch.empty_like(T), torch.empty_like(p), torch.empty_like(Y)
+
+        def e2e_step():
+            dT.copy_(hT, non_blocking=True)
+            dp_.copy_(hp, non_blocking=True)
+            dY.copy_(hY, non_blocking=True)
+            w, hr = nk.rates_eval(m, dT, dp_, dY)
+            mu, lam, D = nk.transport_eval(m, dT, dp_, dY)
+            ho["w"].copy_(w, non_blocking=True)
+            ho["hrr"].copy_(hr, non_blocking=True)
+            ho["mu"].copy_(mu, non_blocking=True)
+            ho["lam"].copy_(lam, non_blocking=True)
+            ho["D"].copy_(D, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(s)
+        torch.cuda.synchronize()
+        e_ms = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * n * args.steps / (e_ms.item() * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": (2 + K) * 8 * n, "d2h_bytes_per_step": (2 * K + 3) * 8 * n}
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel (ALU bound: FP64 pipe)
+    fl = algorithmic_flops(mech)
+    avg = {k: sum(v) / len(v) for k, v in ms.items()}
+    dom = max(avg, key=lambda k: avg[k])
+    achieved = fl[dom] * n / (avg[dom] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic(dom),
+            "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s), no measured FP64 peak in MEASURED_PEAKS.json",
+            "flops_per_point": fl[dom]}
+    rows_out = {k: {"ms": avg[k], "mpts": n / (avg[k] * 1e-3) / 1e6,
+                    "tflops": fl[k] * n / (avg[k] * 1e-3) / 1e12} for k in names}
+    fwd_avg = avg["rates_fp64"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{MECH} (53 species, 325 reactions: 20 third-body, 25 Troe) on {WORKLOAD}: "
+                               f"{args.elements} elements x 512 GLL points = {n} points, FP64 SoA",
+                   "mechanism": MECH, "points": n, "value_basis": "points / (rates_fp64 + transport_fp64 time)",
+                   "step": names, "l2": "inputs (0.92 GB) larger than L2; no flush"},
+        "mixed_value": mixed_value,
+        "vjp_over_fwd": avg["vjp"] / fwd_avg, "jvp_over_fwd": avg["jvp"] / fwd_avg,
+        "rows": rows_out,
+        "roofline": roof,
+        "gpu_launches": sum(launches_per_step.values()) * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(st)
+    _emit(line)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--elements", type=int, default=4096,
+                    help="flame field size in elements (a cube; 4096 = the benchmark workload)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

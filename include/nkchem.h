@@ -1,0 +1,213 @@
+/*
+ * nkchem — pointwise thermochemistry for spectral-element reacting-flow solvers, on GB300.
+ *
+ * C ABI of the library (libnkchem.so).  It evaluates, independently at every grid point,
+ * the right-hand-side quantities that the implicit thermochemistry stage of a low-Mach
+ * reacting-flow solver needs (nekCRF, arXiv 2409.06404, Sec. 2, Eq. 1-4 and the "rates" and
+ * "properties" kernels of Tab. 3-4): NASA-7 thermodynamics, net species production rates
+ * omega_k with heat release, mixture-averaged transport, and exact Jacobian-vector and
+ * vector-Jacobian products of (omega_k, heat release).
+ *
+ * Conventions shared by every entry point
+ *  - Units are SI: K, Pa, kg/mol, J/mol, mol/m^3, s.
+ *  - State arrays are structure-of-arrays in DEVICE memory, owned by the caller:
+ *      T[n], p[n]                  point temperature and pressure
+ *      Y[K*ld]                     mass fractions, species k of point i at Y[k*ld + i]
+ *    Per-species outputs use the same [K][ld] layout; per-point outputs are [n].
+ *    ld >= n is the row stride, so a chunk of a larger field is passed as (ptr + offset, ld).
+ *  - Every double array must be 8-byte aligned (else NK_EALIGN).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *    return after enqueueing.  Only argument errors and launch failures are reported
+ *    synchronously; kernels never trap.  Non-finite or non-physical inputs (T <= 0, all
+ *    Y = 0) propagate NaN/Inf to that point's outputs only.
+ *  - Mass fractions are used as given: no clipping and no renormalisation; negative Y_k
+ *    give negative concentrations and are evaluated as such.
+ *  - On failure a thread-local message is available from nk_last_error().
+ *  - One nk_mech may be used from several streams and host threads concurrently.
+ */
+#ifndef NKCHEM_H
+#define NKCHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NKCHEM_VERSION 1
+
+typedef struct CUstream_st* nk_stream; /* identical to cudaStream_t */
+
+typedef enum {
+    NK_OK = 0,
+    NK_EINVAL = 1,        /* bad argument: null pointer, n < 0, ld < n, bad enum, bad table */
+    NK_EALIGN = 2,        /* an array is not 8-byte aligned */
+    NK_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    NK_ENOMEM = 4,        /* device allocation failed (mechanism load only) */
+    NK_EUNSUPPORTED = 5   /* mechanism beyond the library's limits (see nk_mechanism_load) */
+} nk_status;
+
+typedef enum {
+    NK_FP64 = 0,   /* every operation in double precision */
+    NK_MIXED = 1   /* rates: Arrhenius/Troe arguments and k_f in single precision, equilibrium
+                      constants, forward-minus-reverse difference and omega accumulation in
+                      double; transport: fits, mixture rules and sums in single precision */
+} nk_precision;
+
+/* Reaction kinds of nk_mech_desc.rtype */
+enum { NK_RXN_ELEMENTARY = 0, NK_RXN_THIRD_BODY = 1, NK_RXN_TROE = 2 };
+
+/* Opaque, immutable device copy of a mechanism; owned by the library. */
+typedef struct nk_mech nk_mech;
+
+/*
+ * Host-side description of a mechanism (read during nk_mechanism_load, then no longer
+ * referenced).  This is the data a Cantera-format mechanism carries (Sec. 2: species
+ * thermodynamics, reactions, transport fits), as flat arrays:
+ *   K species, R reactions, n_elem elements.
+ *   W[K]                  molar masses (kg/mol)
+ *   atoms[K*n_elem]       element counts (informational; not used in evaluation)
+ *   nasa_lo[K*7], nasa_hi[K*7]   NASA-7 coefficients a1..a7, low range used for T <= T_mid[k]
+ *   T_mid[K]
+ *   reac_ptr[R+1], reac_sp[], reac_nu[]  reactant entries of reaction r in
+ *                         [reac_ptr[r], reac_ptr[r+1]): species index, stoichiometric
+ *                         coefficient (positive integer); products likewise (prod_*).
+ *                         Every reaction is reversible.
+ *   rtype[R]              NK_RXN_* kind
+ *   lnA[R], beta[R], Ea[R]       Arrhenius k = exp(lnA) T^beta exp(-Ea/(R T)); for Troe rows
+ *                         this is the high-pressure limit k_inf
+ *   lnA0[R], beta0[R], Ea0[R]    Troe low-pressure limit k_0 (read for Troe rows only)
+ *   troe[R*4]             Troe a, T3, T1, T2 (T2 <= 0: the exp(-T2/T) term is absent)
+ *   eff[R*K]              third-body efficiencies (read for third-body and Troe rows)
+ *   mu_fit[K*4], lam_fit[K*4]    ln(mu_k / Pa s), ln(lambda_k / W/m/K) as cubics in ln T,
+ *                         lowest order first
+ *   D_fit[K*(K-1)/2*4]    ln(D_jk / m^2/s) at p_ref as cubics in ln T, for pairs j<k packed
+ *                         row-major: pair (j,k) at j*K - j*(j+1)/2 + (k-j-1)
+ *   p_ref                 reference pressure of D_fit (Pa)
+ */
+typedef struct {
+    int32_t K, R, n_elem;
+    const double* W;
+    const int32_t* atoms;
+    const double* nasa_lo;
+    const double* nasa_hi;
+    const double* T_mid;
+    const int32_t* reac_ptr;
+    const int32_t* reac_sp;
+    const int32_t* reac_nu;
+    const int32_t* prod_ptr;
+    const int32_t* prod_sp;
+    const int32_t* prod_nu;
+    const int32_t* rtype;
+    const double* lnA;
+    const double* beta;
+    const double* Ea;
+    const double* lnA0;
+    const double* beta0;
+    const double* Ea0;
+    const double* troe;
+    const double* eff;
+    const double* mu_fit;
+    const double* lam_fit;
+    const double* D_fit;
+    double p_ref;
+} nk_mech_desc;
+
+/*
+ * Copy a mechanism to the current CUDA device and build the kernels' coefficient tables.
+ * The mechanism input the paper feeds its generated kernels (Sec. 2, "Cantera format").
+ * Limits: 1 <= K <= 256, 1 <= R <= 8192, at most 4 reactant and 4 product entries per
+ * reaction, stoichiometric coefficients 1..8 (else NK_EUNSUPPORTED).  Synchronous.
+ * On success *out owns device memory until nk_mechanism_free.
+ */
+nk_status nk_mechanism_load(const nk_mech_desc* desc, nk_mech** out);
+
+/* Release a mechanism (NULL is accepted).  The caller ensures no call using it is running. */
+nk_status nk_mechanism_free(nk_mech* mech);
+
+/* Number of species and reactions of a loaded mechanism (either pointer may be NULL). */
+nk_status nk_mechanism_info(const nk_mech* mech, int32_t* K, int32_t* R);
+
+/*
+ * Thermodynamic properties (Eq. 1b-1d: c_p, c_p,k, h_k, and p0 = rho R T / Wbar).
+ * Outputs (NULL = not wanted):
+ *   cp_mix[n]  mixture heat capacity, J/(kg K)      h_mix[n]  mixture enthalpy, J/kg
+ *   Wbar[n]    mean molar mass, kg/mol              rho[n]    density, kg/m^3
+ *   cp_k, h_k, g_k [K*ld]  species molar c_p (J/(mol K)), enthalpy and Gibbs energy (J/mol)
+ * Double precision.
+ */
+nk_status nk_thermo_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                         const double* p, const double* Y, double* cp_mix, double* h_mix,
+                         double* Wbar, double* rho, double* cp_k, double* h_k, double* g_k,
+                         nk_stream stream);
+
+/*
+ * Net production rates and heat release (the "rates" kernel, Tab. 3-4; omega_k of Eq. 1a
+ * and the heat release of Eq. 1b / iHRR of Sec. 3.3):
+ *   omega[K*ld]  omega_k = sum_r nu_kr q_r, mol/(m^3 s)
+ *   hrr[n]       -sum_k h_k(T) omega_k, W/m^3 (positive when exothermic)
+ * dlnA: NULL or device [R] shift added to ln A_r (to both limits of a Troe reaction).
+ * precision: NK_FP64 or NK_MIXED.
+ */
+nk_status nk_rates_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                        const double* p, const double* Y, const double* dlnA, double* omega,
+                        double* hrr, nk_precision precision, nk_stream stream);
+
+/*
+ * Mixture-averaged transport properties (the "properties" kernel, Tab. 3; Eq. 2 and 4):
+ *   mu[n]      mixture viscosity (Wilke), Pa s
+ *   lambda[n]  mixture conductivity (Mathur-Saxena average), W/(m K)
+ *   Dmix[K*ld] mixture-averaged diffusion coefficients D_k of Eq. 2, m^2/s
+ *              (D_km = sum_{j!=k} X_j W_j / (Wbar sum_{j!=k} X_j/D_jk); 0 for a pure species)
+ * Any output may be NULL.  precision: NK_FP64 or NK_MIXED.
+ */
+nk_status nk_transport_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                            const double* p, const double* Y, double* mu, double* lambda,
+                            double* Dmix, nk_precision precision, nk_stream stream);
+
+/*
+ * Exact Jacobian-vector product of (omega_k, hrr) with respect to (T, Y_k) at fixed p: the
+ * product the Newton-GMRES stage of the paper forms by difference quotients (Sec. 2 and 4).
+ *   vT[n], vY[K*ld]        direction
+ *   d_omega[K*ld], d_hrr[n]  J v
+ *   omega[K*ld], hrr[n]    NULL, or also return the primal values
+ * Rates of progress are recomputed per point, never stored.  Double precision.
+ */
+nk_status nk_rates_jvp(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                       const double* p, const double* Y, const double* dlnA, const double* vT,
+                       const double* vY, double* omega, double* hrr, double* d_omega,
+                       double* d_hrr, nk_stream stream);
+
+/*
+ * Bytes of device workspace nk_rates_vjp needs for n points when g_lnA is requested
+ * (per-block partial sums of the ln A gradient, reduced in a fixed order).
+ */
+nk_status nk_rates_vjp_workspace(const nk_mech* mech, int64_t n, size_t* bytes);
+
+/*
+ * Vector-Jacobian product of (omega_k, hrr) (gradients for mechanism calibration and for
+ * adjoint solves; the exact transpose of nk_rates_jvp):
+ *   bar_omega[K*ld], bar_hrr[n] (NULL = 0)   cotangents
+ *   gT[n], gY[K*ld]                          J^T (bar_omega, bar_hrr) with respect to T, Y
+ *   g_lnA[R] (NULL = not wanted)  sum over the n points of d/d lnA_r; overwritten.  Needs
+ *            workspace of nk_rates_vjp_workspace bytes; the sum is deterministic for a
+ *            given n (fixed partition and summation order, no atomics).
+ * Double precision.
+ */
+nk_status nk_rates_vjp(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                       const double* p, const double* Y, const double* dlnA,
+                       const double* bar_omega, const double* bar_hrr, double* gT, double* gY,
+                       double* g_lnA, void* workspace, size_t workspace_bytes, nk_stream stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* nk_last_error(void);
+
+/* NKCHEM_VERSION of the built library. */
+int32_t nk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NKCHEM_H */

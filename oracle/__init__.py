@@ -56,29 +56,62 @@ class _Mech(ctypes.Structure):
     ]
 
 
+def build_variant(source_text: str, out_path: str) -> str:
+    """Compile an edited copy of the oracle source to ``out_path`` (used by the mutation tests
+    that check the pins catch planted mistakes)."""
+    src = out_path + ".cpp"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.run(["g++", "-O1", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
+                    "-ffp-contract=off", "-o", out_path, src], check=True)
+    return out_path
+
+
+class use_library:
+    """Context manager: route every oracle call through another compiled variant."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _lib_handle()
+        self.saved = _lib
+        _lib = None
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
 def _lib_handle():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P, I = _p_dbl, _i64
-            M = ctypes.POINTER(_Mech)
-            ci = ctypes.c_int
-            lib.or_max_threads.restype = ci
-            lib.or_thermo.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, P, ci]
-            lib.or_nasa7_cs.argtypes = [M, ci, I, P, P, P, P, P, P]
-            lib.or_rates.argtypes = [M, I, I, P, P, P, P, P, P, P, P, ci]
-            lib.or_rates_of_progress.argtypes = [M, I, I, P, P, P, P, P, P, ci]
-            lib.or_transport.argtypes = [M, I, I, P, P, P, P, P, P, ci]
-            lib.or_rates_jacobian.argtypes = [M, I, I, P, P, P, P, P, ci]
-            lib.or_rates_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, P, ci]
-            lib.or_rates_grad_lnA.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
-            lib.or_count_ops.argtypes = [M, _c_dbl, _c_dbl, P, ci, P]
-            for f in ("or_thermo", "or_nasa7_cs", "or_rates", "or_rates_of_progress", "or_transport",
-                      "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops"):
-                getattr(lib, f).restype = None
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    P, I = _p_dbl, _i64
+    M = ctypes.POINTER(_Mech)
+    ci = ctypes.c_int
+    lib.or_max_threads.restype = ci
+    lib.or_thermo.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, P, ci]
+    lib.or_nasa7_cs.argtypes = [M, ci, I, P, P, P, P, P, P]
+    lib.or_rates.argtypes = [M, I, I, P, P, P, P, P, P, P, P, ci]
+    lib.or_rates_of_progress.argtypes = [M, I, I, P, P, P, P, P, P, ci]
+    lib.or_transport.argtypes = [M, I, I, P, P, P, P, P, P, ci]
+    lib.or_rates_jacobian.argtypes = [M, I, I, P, P, P, P, P, P, ci]
+    lib.or_rates_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, P, ci]
+    lib.or_rates_grad_lnA.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
+    lib.or_count_ops.argtypes = [M, _c_dbl, _c_dbl, P, ci, P]
+    for f in ("or_thermo", "or_nasa7_cs", "or_rates", "or_rates_of_progress", "or_transport",
+              "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops"):
+        getattr(lib, f).restype = None
+    return lib
 
 
 def max_threads() -> int:
@@ -201,14 +234,16 @@ def transport(mech, T, p, Y, threads: int = 0):
     return mu, lam, D
 
 
-def jacobian(mech, T, p, Y, dlnA=None, threads: int = 0):
-    """Dense complex-step Jacobian [n, K+1, K+1]: rows (omega_k, hrr), columns (T, Y_k)."""
+def jacobian(mech, T, p, Y, dlnA=None, threads: int = 0, scales: bool = False):
+    """Dense complex-step Jacobian [n, K+1, K+1]: rows (omega_k, hrr), columns (T, Y_k); with
+    ``scales`` also the per-entry magnitudes sum_r |nu_kr| (|d fwd_r/dx| + |d rev_r/dx|)."""
     pk = _Packed(mech)
     T, p, Y, n = _state(T, p, Y, pk.K)
     d = None if dlnA is None else _f64(dlnA)
     J = np.empty((n, pk.K + 1, pk.K + 1))
-    _lib_handle().or_rates_jacobian(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(d), _dp(J), threads)
-    return J
+    Js = np.empty_like(J) if scales else None
+    _lib_handle().or_rates_jacobian(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(d), _dp(J), _dp(Js), threads)
+    return (J, Js) if scales else J
 
 
 def jvp(mech, T, p, Y, vT, vY, dlnA=None, threads: int = 0, scales: bool = False):

@@ -474,9 +474,11 @@ void or_transport(const or_mech* m, int64_t n, int64_t ld, const double* T, cons
 }
 
 /* Dense Jacobian d(omega_0..omega_{K-1}, hrr)/d(T, Y_0..Y_{K-1}) at fixed p, by complex step.
- * J: [n][(K+1)*(K+1)], row = output, column = input. */
+ * J: [n][(K+1)*(K+1)], row = output, column = input.
+ * Js (nullable), same shape: sum_r |nu_kr| (|d fwd_r/dx| + |d rev_r/dx|) and the heat-release
+ * analogue, the magnitudes behind each entry for cancellation-aware tolerances. */
 void or_rates_jacobian(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
-                       const double* Y, const double* dlnA, double* J, int nthreads) {
+                       const double* Y, const double* dlnA, double* J, double* Js, int nthreads) {
     const int K = m->K, R = m->R, N = K + 1;
     const double hstep = 1e-30;
 #pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
@@ -486,10 +488,17 @@ void or_rates_jacobian(const or_mech* m, int64_t n, int64_t ld, const double* T,
         for (int j = 0; j < N; ++j) {
             for (int k = 0; k < K; ++k) y[k] = cplx(Y[k * ld + i], (j == k + 1) ? hstep : 0.0);
             cplx Tc(T[i], j == 0 ? hstep : 0.0), h;
-            rates_point<cplx>(*m, Tc, p[i], y.data(), sh.data(), w.data(), h, nullptr, nullptr);
+            std::vector<double> sc(K), dsc(K);
+            double sh_, dsh_;
+            rates_point<cplx>(*m, Tc, p[i], y.data(), sh.data(), w.data(), h, sc.data(), &sh_, dsc.data(), &dsh_);
             double* Ji = J + (size_t)i * N * N;
             for (int k = 0; k < K; ++k) Ji[k * N + j] = w[k].imag() / hstep;
             Ji[K * N + j] = h.imag() / hstep;
+            if (Js) {
+                double* Si = Js + (size_t)i * N * N;
+                for (int k = 0; k < K; ++k) Si[k * N + j] = dsc[k] / hstep;
+                Si[K * N + j] = dsh_ / hstep;
+            }
         }
     }
 }

@@ -1,0 +1,470 @@
+// C-ABI layer of nkchem: argument checking, error reporting, mechanism upload and the
+// dispatch to the kernel launchers.  Every entry point declared in include/nkchem.h is
+// defined here.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "nk_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+nk_status fail(nk_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+nk_status ok() {
+    g_err[0] = '\0';
+    return NK_OK;
+}
+
+nk_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(NK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool misaligned(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 7u); }
+
+// Bump allocator over one host staging buffer mirrored by one device allocation.
+struct Layout {
+    size_t bytes = 0;
+    size_t add(size_t n) {
+        size_t off = (bytes + 255) & ~size_t(255);
+        bytes = off + n;
+        return off;
+    }
+};
+
+nk_status check_mech_desc(const nk_mech_desc* d) {
+    if (!d) return fail(NK_EINVAL, "desc is NULL");
+    if (d->K < 1 || d->R < 1) return fail(NK_EINVAL, "K and R must be >= 1 (K=%d, R=%d)", d->K, d->R);
+    if (d->K > nk::kMaxK) return fail(NK_EUNSUPPORTED, "K=%d exceeds %d species", d->K, nk::kMaxK);
+    if (d->R > nk::kMaxR) return fail(NK_EUNSUPPORTED, "R=%d exceeds %d reactions", d->R, nk::kMaxR);
+    const void* req[] = {d->W, d->nasa_lo, d->nasa_hi, d->T_mid, d->reac_ptr, d->reac_sp, d->reac_nu,
+                         d->prod_ptr, d->prod_sp, d->prod_nu, d->rtype, d->lnA, d->beta, d->Ea,
+                         d->lnA0, d->beta0, d->Ea0, d->troe, d->eff, d->mu_fit, d->lam_fit};
+    for (const void* p : req)
+        if (!p) return fail(NK_EINVAL, "a required mechanism array is NULL");
+    if (d->K > 1 && !d->D_fit) return fail(NK_EINVAL, "D_fit is NULL");
+    if (!(d->p_ref > 0.0)) return fail(NK_EINVAL, "p_ref must be > 0");
+    for (int k = 0; k < d->K; ++k) {
+        if (!(d->W[k] > 0.0)) return fail(NK_EINVAL, "W[%d] must be > 0", k);
+        if (!(d->T_mid[k] > 0.0)) return fail(NK_EINVAL, "T_mid[%d] must be > 0", k);
+    }
+    const int32_t* ptrs[2] = {d->reac_ptr, d->prod_ptr};
+    const int32_t* sps[2] = {d->reac_sp, d->prod_sp};
+    const int32_t* nus[2] = {d->reac_nu, d->prod_nu};
+    for (int side = 0; side < 2; ++side) {
+        if (ptrs[side][0] != 0) return fail(NK_EINVAL, "stoichiometry pointer arrays must start at 0");
+        for (int r = 0; r < d->R; ++r) {
+            const int c = ptrs[side][r + 1] - ptrs[side][r];
+            if (c < 1) return fail(NK_EINVAL, "reaction %d has an empty side", r);
+            if (c > nk::kMaxSide)
+                return fail(NK_EUNSUPPORTED, "reaction %d has %d entries on one side (max %d)", r, c, nk::kMaxSide);
+            for (int e = ptrs[side][r]; e < ptrs[side][r + 1]; ++e) {
+                if (sps[side][e] < 0 || sps[side][e] >= d->K)
+                    return fail(NK_EINVAL, "reaction %d: species index %d out of range", r, sps[side][e]);
+                if (nus[side][e] < 1 || nus[side][e] > nk::kMaxNu)
+                    return fail(NK_EUNSUPPORTED, "reaction %d: stoichiometric coefficient %d not in 1..%d", r,
+                                nus[side][e], nk::kMaxNu);
+            }
+        }
+    }
+    for (int r = 0; r < d->R; ++r)
+        if (d->rtype[r] < 0 || d->rtype[r] > 2) return fail(NK_EINVAL, "rtype[%d]=%d", r, d->rtype[r]);
+    return NK_OK;
+}
+
+}  // namespace
+
+namespace nk {
+
+int pick_block(size_t bytes_per_thread, size_t budget) {
+    for (int b : {128, 64, 32})
+        if (bytes_per_thread * (size_t)b <= budget) return b;
+    return 0;
+}
+
+namespace {
+struct SmemEntry {
+    const void* kernel;
+    int device;
+    size_t bytes;
+};
+std::mutex g_smem_mu;
+std::vector<SmemEntry> g_smem;
+}  // namespace
+
+cudaError_t ensure_smem(const void* kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    for (const SmemEntry& s : g_smem)
+        if (s.kernel == kernel && s.device == dev && s.bytes >= bytes) return cudaSuccess;
+    const size_t lim = smem_limit();
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    if (e != cudaSuccess) return e;
+    g_smem.push_back({kernel, dev, lim});
+    return cudaSuccess;
+}
+
+size_t smem_limit() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 48 * 1024;
+    return (size_t)v;
+}
+
+}  // namespace nk
+
+extern "C" {
+
+int32_t nk_version(void) { return NKCHEM_VERSION; }
+
+const char* nk_last_error(void) { return g_err; }
+
+nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
+    if (!out) return fail(NK_EINVAL, "out is NULL");
+    *out = nullptr;
+    nk_status st = check_mech_desc(d);
+    if (st != NK_OK) return st;
+    const int K = d->K, R = d->R, P = K * (K - 1) / 2;
+
+    // ---- build host tables
+    std::vector<double> invW(K), Tmid(K), nasa((size_t)K * 2 * nk::kNasaStride, 0.0);
+    for (int k = 0; k < K; ++k) {
+        invW[k] = 1.0 / d->W[k];
+        Tmid[k] = d->T_mid[k];
+        for (int range = 0; range < 2; ++range) {
+            const double* a = (range == 0 ? d->nasa_lo : d->nasa_hi) + 7 * k;
+            double* c = nasa.data() + ((size_t)k * 2 + range) * nk::kNasaStride;
+            for (int j = 0; j < 7; ++j) c[j] = a[j];
+            c[7] = a[1] / 2.0;
+            c[8] = a[2] / 3.0;
+            c[9] = a[3] / 4.0;
+            c[10] = a[4] / 5.0;
+            c[11] = -a[1] / 2.0;
+            c[12] = -a[2] / 6.0;
+            c[13] = -a[3] / 12.0;
+            c[14] = -a[4] / 20.0;
+        }
+    }
+    std::vector<nk::RxnRec> rxn(R);
+    std::vector<nk::RxnRecF> rxnf(R);
+    std::vector<nk::TroeRec> troe;
+    std::vector<nk::TroeRecF> troef;
+    std::vector<int32_t> eff_ptr(R + 1, 0), eff_sp;
+    std::vector<double> eff_m1;
+    for (int r = 0; r < R; ++r) {
+        nk::RxnRec& x = rxn[r];
+        std::memset(&x, 0, sizeof x);
+        x.lnA = d->lnA[r];
+        x.beta = d->beta[r];
+        x.EaR = d->Ea[r] / nk::kR;
+        x.type = d->rtype[r];
+        x.nr = d->reac_ptr[r + 1] - d->reac_ptr[r];
+        x.np = d->prod_ptr[r + 1] - d->prod_ptr[r];
+        int dnu = 0, e = 0;
+        for (int i = d->reac_ptr[r]; i < d->reac_ptr[r + 1]; ++i, ++e) {
+            x.sp[e] = d->reac_sp[i];
+            x.nu[e] = d->reac_nu[i];
+            dnu -= d->reac_nu[i];
+        }
+        e = nk::kMaxSide;
+        for (int i = d->prod_ptr[r]; i < d->prod_ptr[r + 1]; ++i, ++e) {
+            x.sp[e] = d->prod_sp[i];
+            x.nu[e] = d->prod_nu[i];
+            dnu += d->prod_nu[i];
+        }
+        x.dnu = (double)dnu;
+        x.aux = -1;
+        rxnf[r] = nk::RxnRecF{(float)x.lnA, (float)x.beta, (float)x.EaR, 0.0f};
+        if (x.type == NK_RXN_TROE) {
+            const double* t = d->troe + 4 * r;
+            if (!(t[1] > 0.0) || !(t[2] > 0.0))
+                return fail(NK_EINVAL, "reaction %d: Troe T3 and T1 must be > 0", r);
+            nk::TroeRec tr;
+            tr.lnA0 = d->lnA0[r];
+            tr.beta0 = d->beta0[r];
+            tr.Ea0R = d->Ea0[r] / nk::kR;
+            tr.a = t[0];
+            tr.invT3 = 1.0 / t[1];
+            tr.invT1 = 1.0 / t[2];
+            tr.T2 = t[3] > 0.0 ? t[3] : 0.0;
+            tr.hasT2 = t[3] > 0.0 ? 1.0 : 0.0;
+            x.aux = (int32_t)troe.size();
+            troe.push_back(tr);
+            troef.push_back(nk::TroeRecF{(float)tr.lnA0, (float)tr.beta0, (float)tr.Ea0R, (float)tr.a,
+                                         (float)tr.invT3, (float)tr.invT1, (float)tr.T2, (float)tr.hasT2});
+        }
+        if (x.type != NK_RXN_ELEMENTARY) {
+            for (int k = 0; k < K; ++k) {
+                const double eps = d->eff[(size_t)r * K + k];
+                if (eps != 1.0) {
+                    eff_sp.push_back(k);
+                    eff_m1.push_back(eps - 1.0);
+                }
+            }
+        }
+        eff_ptr[r + 1] = (int32_t)eff_sp.size();
+    }
+    std::vector<double> wilkeA((size_t)K * K), qrtW(K), sqrtW(K);
+    for (int k = 0; k < K; ++k) {
+        qrtW[k] = std::pow(d->W[k], 0.25);
+        sqrtW[k] = std::sqrt(d->W[k]);
+        for (int j = 0; j < K; ++j) wilkeA[(size_t)k * K + j] = 1.0 / std::sqrt(8.0 * (1.0 + d->W[k] / d->W[j]));
+    }
+    auto to_f = [](const double* s, size_t n) {
+        std::vector<float> v(n);
+        for (size_t i = 0; i < n; ++i) v[i] = (float)s[i];
+        return v;
+    };
+    std::vector<float> f_mu = to_f(d->mu_fit, (size_t)K * 4), f_lam = to_f(d->lam_fit, (size_t)K * 4),
+                       f_D = to_f(P ? d->D_fit : nullptr, (size_t)P * 4), f_A = to_f(wilkeA.data(), wilkeA.size()),
+                       f_q = to_f(qrtW.data(), K), f_s = to_f(sqrtW.data(), K), f_iw = to_f(invW.data(), K);
+
+    // ---- one device block for everything
+    Layout L;
+    const size_t o_invW = L.add(K * 8), o_Tmid = L.add(K * 8), o_nasa = L.add(nasa.size() * 8),
+                 o_rxn = L.add(R * sizeof(nk::RxnRec)), o_rxnf = L.add(R * sizeof(nk::RxnRecF)),
+                 o_troe = L.add(troe.size() * sizeof(nk::TroeRec) + 16),
+                 o_troef = L.add(troef.size() * sizeof(nk::TroeRecF) + 16), o_effp = L.add((R + 1) * 4),
+                 o_effs = L.add(eff_sp.size() * 4 + 16), o_effv = L.add(eff_m1.size() * 8 + 16),
+                 o_mu = L.add(K * 32), o_lam = L.add(K * 32), o_D = L.add((size_t)P * 32 + 16),
+                 o_A = L.add((size_t)K * K * 8), o_q = L.add(K * 8), o_s = L.add(K * 8),
+                 o_fmu = L.add(K * 16), o_flam = L.add(K * 16), o_fD = L.add((size_t)P * 16 + 16),
+                 o_fA = L.add((size_t)K * K * 4), o_fq = L.add(K * 4), o_fs = L.add(K * 4), o_fiw = L.add(K * 4);
+    std::vector<unsigned char> host(L.bytes, 0);
+    auto put = [&](size_t off, const void* src, size_t n) {
+        if (n) std::memcpy(host.data() + off, src, n);
+    };
+    put(o_invW, invW.data(), K * 8);
+    put(o_Tmid, Tmid.data(), K * 8);
+    put(o_nasa, nasa.data(), nasa.size() * 8);
+    put(o_rxn, rxn.data(), R * sizeof(nk::RxnRec));
+    put(o_rxnf, rxnf.data(), R * sizeof(nk::RxnRecF));
+    put(o_troe, troe.data(), troe.size() * sizeof(nk::TroeRec));
+    put(o_troef, troef.data(), troef.size() * sizeof(nk::TroeRecF));
+    put(o_effp, eff_ptr.data(), (R + 1) * 4);
+    put(o_effs, eff_sp.data(), eff_sp.size() * 4);
+    put(o_effv, eff_m1.data(), eff_m1.size() * 8);
+    put(o_mu, d->mu_fit, K * 32);
+    put(o_lam, d->lam_fit, K * 32);
+    if (P) put(o_D, d->D_fit, (size_t)P * 32);
+    put(o_A, wilkeA.data(), (size_t)K * K * 8);
+    put(o_q, qrtW.data(), K * 8);
+    put(o_s, sqrtW.data(), K * 8);
+    put(o_fmu, f_mu.data(), K * 16);
+    put(o_flam, f_lam.data(), K * 16);
+    put(o_fD, f_D.data(), (size_t)P * 16);
+    put(o_fA, f_A.data(), (size_t)K * K * 4);
+    put(o_fq, f_q.data(), K * 4);
+    put(o_fs, f_s.data(), K * 4);
+    put(o_fiw, f_iw.data(), K * 4);
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    void* block = nullptr;
+    e = cudaMalloc(&block, L.bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? NK_ENOMEM : NK_ECUDA, "cudaMalloc(%zu): %s", L.bytes,
+                    cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(block, host.data(), L.bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(block);
+        return cuda_fail(e, "cudaMemcpy(mechanism tables)");
+    }
+    nk_mech* m = new nk_mech;
+    m->device = dev;
+    m->block = block;
+    m->bytes = L.bytes;
+    unsigned char* b = static_cast<unsigned char*>(block);
+    nk::DevMech& dm = m->d;
+    dm.K = K;
+    dm.R = R;
+    dm.P = P;
+    dm.n_troe = (int32_t)troe.size();
+    dm.n_eff_rows = R;
+    dm.p_ref = d->p_ref;
+    dm.invW = reinterpret_cast<const double*>(b + o_invW);
+    dm.Tmid = reinterpret_cast<const double*>(b + o_Tmid);
+    dm.nasa = reinterpret_cast<const double*>(b + o_nasa);
+    dm.rxn = reinterpret_cast<const nk::RxnRec*>(b + o_rxn);
+    dm.rxnf = reinterpret_cast<const nk::RxnRecF*>(b + o_rxnf);
+    dm.troe = reinterpret_cast<const nk::TroeRec*>(b + o_troe);
+    dm.troef = reinterpret_cast<const nk::TroeRecF*>(b + o_troef);
+    dm.eff_ptr = reinterpret_cast<const int32_t*>(b + o_effp);
+    dm.eff_sp = reinterpret_cast<const int32_t*>(b + o_effs);
+    dm.eff_m1 = reinterpret_cast<const double*>(b + o_effv);
+    dm.mu_fit = reinterpret_cast<const double*>(b + o_mu);
+    dm.lam_fit = reinterpret_cast<const double*>(b + o_lam);
+    dm.D_fit = reinterpret_cast<const double*>(b + o_D);
+    dm.wilkeA = reinterpret_cast<const double*>(b + o_A);
+    dm.qrtW = reinterpret_cast<const double*>(b + o_q);
+    dm.sqrtW = reinterpret_cast<const double*>(b + o_s);
+    dm.f_mu_fit = reinterpret_cast<const float*>(b + o_fmu);
+    dm.f_lam_fit = reinterpret_cast<const float*>(b + o_flam);
+    dm.f_D_fit = reinterpret_cast<const float*>(b + o_fD);
+    dm.f_wilkeA = reinterpret_cast<const float*>(b + o_fA);
+    dm.f_qrtW = reinterpret_cast<const float*>(b + o_fq);
+    dm.f_sqrtW = reinterpret_cast<const float*>(b + o_fs);
+    dm.f_invW = reinterpret_cast<const float*>(b + o_fiw);
+    *out = m;
+    return ok();
+}
+
+nk_status nk_mechanism_free(nk_mech* m) {
+    if (!m) return ok();
+    cudaError_t e = cudaFree(m->block);
+    delete m;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    return ok();
+}
+
+nk_status nk_mechanism_info(const nk_mech* m, int32_t* K, int32_t* R) {
+    if (!m) return fail(NK_EINVAL, "mech is NULL");
+    if (K) *K = m->d.K;
+    if (R) *R = m->d.R;
+    return ok();
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checks shared by the evaluation entry points.  Returns NK_OK with *skip = true for n == 0.
+nk_status check_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                     const double* Y, bool* skip) {
+    *skip = false;
+    if (!m) return fail(NK_EINVAL, "mech is NULL");
+    if (n < 0) return fail(NK_EINVAL, "n=%lld < 0", (long long)n);
+    if (ld < n) return fail(NK_EINVAL, "ld=%lld < n=%lld", (long long)ld, (long long)n);
+    if (n == 0) {
+        *skip = true;
+        return NK_OK;
+    }
+    if (ld > ((int64_t)1 << 40) || n > ((int64_t)1 << 36))
+        return fail(NK_EINVAL, "n=%lld / ld=%lld too large", (long long)n, (long long)ld);
+    if (!T || !p || !Y) return fail(NK_EINVAL, "T, p and Y must not be NULL");
+    if (misaligned(T) || misaligned(p) || misaligned(Y)) return fail(NK_EALIGN, "T, p, Y must be 8-byte aligned");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != m->device)
+        return fail(NK_EINVAL, "mechanism lives on device %d but device %d is current", m->device, dev);
+    return NK_OK;
+}
+
+nk_status check_out(std::initializer_list<const void*> ptrs) {
+    for (const void* q : ptrs)
+        if (misaligned(q)) return fail(NK_EALIGN, "output arrays must be 8-byte aligned");
+    return NK_OK;
+}
+
+nk_status launched(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return ok();
+}
+
+}  // namespace
+
+extern "C" {
+
+nk_status nk_thermo_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                         const double* Y, double* cp_mix, double* h_mix, double* Wbar, double* rho,
+                         double* cp_k, double* h_k, double* g_k, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if ((st = check_out({cp_mix, h_mix, Wbar, rho, cp_k, h_k, g_k})) != NK_OK) return st;
+    return launched(nk::launch_thermo(m->d, n, ld, T, p, Y, cp_mix, h_mix, Wbar, rho, cp_k, h_k, g_k,
+                                      (cudaStream_t)stream),
+                    "thermo kernel launch");
+}
+
+nk_status nk_rates_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                        const double* Y, const double* dlnA, double* omega, double* hrr,
+                        nk_precision precision, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (precision != NK_FP64 && precision != NK_MIXED) return fail(NK_EINVAL, "bad precision %d", (int)precision);
+    if (!omega || !hrr) return fail(NK_EINVAL, "omega and hrr must not be NULL");
+    if ((st = check_out({omega, hrr, dlnA})) != NK_OK) return st;
+    return launched(nk::launch_rates(m->d, n, ld, T, p, Y, dlnA, omega, hrr, (int)precision, (cudaStream_t)stream),
+                    "rates kernel launch");
+}
+
+nk_status nk_transport_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                            const double* Y, double* mu, double* lambda, double* Dmix,
+                            nk_precision precision, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (precision != NK_FP64 && precision != NK_MIXED) return fail(NK_EINVAL, "bad precision %d", (int)precision);
+    if ((st = check_out({mu, lambda, Dmix})) != NK_OK) return st;
+    if (!mu && !lambda && !Dmix) return ok();
+    return launched(nk::launch_transport(m->d, n, ld, T, p, Y, mu, lambda, Dmix, (int)precision,
+                                         (cudaStream_t)stream),
+                    "transport kernel launch");
+}
+
+nk_status nk_rates_jvp(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                       const double* Y, const double* dlnA, const double* vT, const double* vY,
+                       double* omega, double* hrr, double* d_omega, double* d_hrr, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!vT || !vY || !d_omega || !d_hrr) return fail(NK_EINVAL, "vT, vY, d_omega and d_hrr must not be NULL");
+    if ((st = check_out({vT, vY, d_omega, d_hrr, omega, hrr, dlnA})) != NK_OK) return st;
+    return launched(nk::launch_jvp(m->d, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr,
+                                   (cudaStream_t)stream),
+                    "jvp kernel launch");
+}
+
+nk_status nk_rates_vjp_workspace(const nk_mech* m, int64_t n, size_t* bytes) {
+    if (!m || !bytes) return fail(NK_EINVAL, "mech and bytes must not be NULL");
+    if (n < 0) return fail(NK_EINVAL, "n < 0");
+    *bytes = n == 0 ? 0 : nk::vjp_workspace_bytes(m->d, n);
+    return ok();
+}
+
+nk_status nk_rates_vjp(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                       const double* Y, const double* dlnA, const double* bar_omega, const double* bar_hrr,
+                       double* gT, double* gY, double* g_lnA, void* workspace, size_t workspace_bytes,
+                       nk_stream stream) {
+    if (m && g_lnA && n == 0) {
+        // the gradient of an empty sum is zero
+        cudaError_t e = cudaMemsetAsync(g_lnA, 0, sizeof(double) * m->d.R, (cudaStream_t)stream);
+        return launched(e, "cudaMemsetAsync(g_lnA)");
+    }
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!bar_omega || !gT || !gY) return fail(NK_EINVAL, "bar_omega, gT and gY must not be NULL");
+    if ((st = check_out({bar_omega, bar_hrr, gT, gY, g_lnA, dlnA, workspace})) != NK_OK) return st;
+    if (g_lnA) {
+        const size_t need = nk::vjp_workspace_bytes(m->d, n);
+        if (!workspace || workspace_bytes < need)
+            return fail(NK_EINVAL, "g_lnA needs %zu bytes of workspace, got %zu", need,
+                        workspace ? workspace_bytes : (size_t)0);
+    }
+    return launched(nk::launch_vjp(m->d, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, g_lnA, workspace,
+                                   (cudaStream_t)stream),
+                    "vjp kernel launch");
+}
+
+}  // extern "C"

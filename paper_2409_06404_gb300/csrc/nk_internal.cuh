@@ -1,0 +1,155 @@
+// Internal declarations of the nkchem CUDA library: device-side mechanism tables, the
+// launch interface between the C-ABI layer and the kernels, and device helpers shared by
+// the kernels.  Not part of the public ABI (see include/nkchem.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nkchem.h"
+
+namespace nk {
+
+// Physical constants of the evaluated model (SI).
+constexpr double kR = 8.314462618;          // molar gas constant, J/(mol K)
+constexpr double kInvR = 1.0 / 8.314462618;
+constexpr double kP0 = 101325.0;            // standard-state pressure of K_c (1 atm)
+constexpr double kLn10 = 2.302585092994045684;
+constexpr double kInvLn10 = 0.434294481903251828;
+
+constexpr int kMaxK = 256;
+constexpr int kMaxR = 8192;
+constexpr int kMaxSide = 4;                 // reactant / product entries per reaction
+constexpr int kMaxNu = 8;
+
+// One reaction, read by every thread of a warp at the same address (a broadcast load).
+struct __align__(16) RxnRec {
+    double lnA;        // ln A (high-pressure limit for Troe)
+    double beta;
+    double EaR;        // Ea / R, kelvin
+    double dnu;        // sum of net stoichiometric coefficients (products - reactants)
+    int32_t type;      // NK_RXN_*
+    int32_t nr, np;    // reactant / product entry counts
+    int32_t aux;       // Troe record index (type 2), else -1
+    int32_t sp[2 * kMaxSide];   // species of entries: reactants at [0, nr),
+                                // products at [kMaxSide, kMaxSide + np)
+    int32_t nu[2 * kMaxSide];   // stoichiometric coefficients of the entries
+};
+
+// Single-precision copy of the Arrhenius data for the mixed form.
+struct __align__(16) RxnRecF {
+    float lnA, beta, EaR, pad;
+};
+
+struct __align__(16) TroeRec {
+    double lnA0, beta0, Ea0R;   // low-pressure limit
+    double a, invT3, invT1, T2; // broadening parameters (T2 <= 0: term absent)
+    double hasT2;               // 1.0 or 0.0
+};
+
+struct __align__(16) TroeRecF {
+    float lnA0, beta0, Ea0R, a, invT3, invT1, T2, hasT2;
+};
+
+// NASA-7 coefficients of one temperature range, with the derived forms the kernels use:
+//   c[0..6] = a1..a7; c[7..10] = a2/2, a3/3, a4/4, a5/5 (h/RT);
+//   c[11..14] = -a2/2, -a3/6, -a4/12, -a5/20 (g/RT); c[15] unused.
+constexpr int kNasaStride = 16;   // per range; species k: [k][2][16] (low, high)
+
+// Device view of a loaded mechanism (passed by value to every kernel).
+struct DevMech {
+    int32_t K, R, P;              // species, reactions, species pairs K(K-1)/2
+    int32_t n_troe, n_eff_rows;
+    double p_ref;
+    const double* invW;           // [K] 1/W
+    const double* Tmid;           // [K]
+    const double* nasa;           // [K][2][16]
+    const RxnRec* rxn;            // [R]
+    const RxnRecF* rxnf;          // [R]
+    const TroeRec* troe;          // [n_troe]
+    const TroeRecF* troef;        // [n_troe]
+    const int32_t* eff_ptr;       // [R + 1] third-body efficiencies of reaction r, sparse:
+    const int32_t* eff_sp;        //   species with eps != 1 in [eff_ptr[r], eff_ptr[r+1])
+    const double* eff_m1;         //   eps - 1 (all other species have eps = 1)
+    // transport
+    const double* mu_fit;         // [K][4]
+    const double* lam_fit;        // [K][4]
+    const double* D_fit;          // [P][4]
+    const double* wilkeA;         // [K][K] A_kj = 8^-1/2 (1 + W_k/W_j)^-1/2
+    const double* qrtW;           // [K] W^(1/4)
+    const double* sqrtW;          // [K] W^(1/2)
+    const float* f_mu_fit;        // single-precision copies for the mixed form
+    const float* f_lam_fit;
+    const float* f_D_fit;
+    const float* f_wilkeA;
+    const float* f_qrtW;
+    const float* f_sqrtW;
+    const float* f_invW;
+};
+
+}  // namespace nk
+
+// The opaque handle of the public ABI.
+struct nk_mech {
+    nk::DevMech d;
+    int device;
+    void* block;        // single device allocation holding every table
+    size_t bytes;
+};
+
+namespace nk {
+
+// Launchers (one per kernel family); each returns cudaGetLastError() after the launch.
+cudaError_t launch_thermo(const DevMech& m, int64_t n, int64_t ld, const double* T,
+                          const double* p, const double* Y, double* cp_mix, double* h_mix,
+                          double* Wbar, double* rho, double* cp_k, double* h_k, double* g_k,
+                          cudaStream_t s);
+cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                         const double* Y, const double* dlnA, double* omega, double* hrr,
+                         int precision, cudaStream_t s);
+cudaError_t launch_transport(const DevMech& m, int64_t n, int64_t ld, const double* T,
+                             const double* p, const double* Y, double* mu, double* lam,
+                             double* Dmix, int precision, cudaStream_t s);
+cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                       const double* Y, const double* dlnA, const double* vT, const double* vY,
+                       double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s);
+size_t vjp_workspace_bytes(const DevMech& m, int64_t n);
+cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                       const double* Y, const double* dlnA, const double* bar_omega,
+                       const double* bar_hrr, double* gT, double* gY, double* g_lnA,
+                       void* ws, cudaStream_t s);
+
+// Largest block size in {128, 64, 32} whose per-thread shared-memory scratch
+// (bytes_per_thread * block) stays within the budget; 0 if none fits.
+int pick_block(size_t bytes_per_thread, size_t budget);
+// Opt a kernel into `bytes` of dynamic shared memory on the current device (cached).
+cudaError_t ensure_smem(const void* kernel, size_t bytes);
+// Opt-in shared-memory limit per block of the current device.
+size_t smem_limit();
+
+// ------------------------------------------------------------------ device helpers
+// NASA-7 polynomials of species k at (T, lnT, 1/T); c points at the chosen range.
+__device__ __forceinline__ const double* nasa_range(const DevMech& m, int k, double T) {
+    const double* base = m.nasa + (size_t)k * 2 * kNasaStride;
+    return (T <= __ldg(m.Tmid + k)) ? base : base + kNasaStride;
+}
+__device__ __forceinline__ double nasa_gRT(const double* c, double T, double lnT, double invT) {
+    const double poly = T * fma(T, fma(T, fma(T, __ldg(c + 14), __ldg(c + 13)), __ldg(c + 12)), __ldg(c + 11));
+    return fma(__ldg(c + 0), 1.0 - lnT, fma(__ldg(c + 5), invT, poly - __ldg(c + 6)));
+}
+__device__ __forceinline__ double nasa_hRT(const double* c, double T, double invT) {
+    const double poly = T * fma(T, fma(T, fma(T, __ldg(c + 10), __ldg(c + 9)), __ldg(c + 8)), __ldg(c + 7));
+    return __ldg(c + 0) + fma(__ldg(c + 5), invT, poly);
+}
+__device__ __forceinline__ double nasa_cpR(const double* c, double T) {
+    return fma(T, fma(T, fma(T, fma(T, __ldg(c + 4), __ldg(c + 3)), __ldg(c + 2)), __ldg(c + 1)), __ldg(c + 0));
+}
+
+// x^nu for a small positive integer nu (uniform across the warp)
+__device__ __forceinline__ double ipow(double x, int nu) {
+    double r = x;
+    for (int j = 1; j < nu; ++j) r *= x;
+    return r;
+}
+
+}  // namespace nk

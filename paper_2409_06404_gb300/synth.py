@@ -447,12 +447,13 @@ def mechanism(name) -> Mechanism:
     return _MECH_CACHE[name]
 
 
-def workload_states(name, K, n_points=None):
-    """States of a named workload; ``n_points`` takes the first points (whole elements first)."""
+def workload_states(name, K, n_points=None, n_elements=None):
+    """States of a named workload; ``n_points`` takes the first points (whole elements first).
+    ``n_elements`` (a cube) shrinks the flame field to that many elements, same profile."""
     if name == "uniform_64el":        # 64 elements x 512 = 32,768 points
         st = states_uniform(K, 64 * 512, seed=2009, alpha=0.5)
     elif name == "flame_4096el":      # 16^3 elements x 512 = 2,097,152 points
-        st = states_flame(K, 4096, seed=2053 if K == 53 else 2120)
+        st = states_flame(K, n_elements or 4096, seed=2053 if K == 53 else 2120)
     else:
         raise KeyError(name)
     if n_points is not None:

@@ -1,0 +1,103 @@
+"""Do the oracle's pins catch plausible mistakes?  Each case plants one mistake in a copy of
+the oracle source (a dropped term, a wrong sign, index or constant, a transposed operand),
+builds it on the CPU and requires that at least one pin fails against it."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle
+from paper_2409_06404_gb300 import synth
+from conftest import P_ATM
+import test_oracle_thermo as th
+import test_oracle_rates as rt
+import test_oracle_transport as tr
+import test_oracle_derivs as dv
+
+SRC = open(os.path.join(os.path.dirname(oracle.__file__), "nkoracle.cpp")).read()
+
+MUTATIONS = {
+    "h_coefficient": ("hRT = S(a[0]) + S(a[1]) * T / S(2.0)", "hRT = S(a[0]) + S(a[1]) * T / S(3.0)"),
+    "s_drops_a7": ("S(a[4]) * T4 / S(4.0) + S(a[6]);", "S(a[4]) * T4 / S(4.0);"),
+    "nasa_range_swapped": ("(re(T) <= m.T_mid[k])", "(re(T) > m.T_mid[k])"),
+    "Kc_sign": ("S Kc = exp(-sum_nu_g)", "S Kc = exp(sum_nu_g)"),
+    "standard_pressure": ("const double P0 = 101325.0;", "const double P0 = 100000.0;"),
+    "third_body_not_applied": ("        fwd = fwd * M;\n        rev = rev * M;\n", ""),
+    "troe_0.14": ("S(0.14)", "S(0.15)"),
+    "troe_n_slope": ("S(0.75) - S(1.27) * lFc", "S(0.75) - S(1.17) * lFc"),
+    "troe_T2_sign": ("Fcent += exp(S(-T2) / T);", "Fcent += exp(S(T2) / T);"),
+    "troe_weights_swapped": ("S(1.0 - a) * exp(-T / S(T3)) + S(a) * exp(-T / S(T1))",
+                             "S(a) * exp(-T / S(T3)) + S(1.0 - a) * exp(-T / S(T1))"),
+    "product_scatter_sign": ("omega[m.prod_sp[i]] += S((double)m.prod_nu[i]) * o.q;",
+                             "omega[m.prod_sp[i]] -= S((double)m.prod_nu[i]) * o.q;"),
+    "arrhenius_missing_R": ("exp(S(-Ea) / (S(RU) * T))", "exp(S(-Ea) / T)"),
+    "arrhenius_beta_sign": ("pow(T, beta)", "pow(T, -beta)"),
+    "density": ("mx.rho = S(p) * mx.Wbar / (S(RU) * T);", "mx.rho = S(p) / mx.Wbar / (S(RU) * T);"),
+    "concentration_missing_W": ("mx.C[k] = mx.rho * Y[k] / S(m.W[k]);", "mx.C[k] = mx.rho * Y[k];"),
+    "hrr_sign": ("hrr -= h * omega[k];", "hrr += h * omega[k];"),
+    "wilke_quarter_power": ("pow(S(m.W[j] / m.W[k]), 0.25)", "pow(S(m.W[k] / m.W[j]), 0.25)"),
+    "mathur_harmonic": ("lam = S(0.5) * (s1 + S(1.0) / s2);", "lam = S(0.5) * (s1 + S(1.0) * s2);"),
+    "diffusion_pressure": ("* S(m.p_ref / p)", "* S(p / m.p_ref)"),
+    "diffusion_numerator": ("num += mx.X[j] * S(m.W[j]);", "num += mx.X[j];"),
+}
+
+
+def _pins():
+    m9, m53, m120 = (synth.mechanism(n) for n in ("h2_9sp_21rx", "ch4_53sp_325rx", "big_120sp_700rx"))
+    return [
+        lambda: th.test_cp_is_dh_dT_and_ds_dT_is_cp_over_T(m53),
+        lambda: th.test_continuity_at_T_mid(m53, m9),
+        th.test_constant_cp_ideal_gas,
+        lambda: th.test_pure_species_and_binary_mixture_state(m9),
+        lambda: th.test_mixture_properties_are_mass_weighted(m53),
+        lambda: th.test_heat_capacity_stays_on_the_fitted_curve(m53, m120),
+        lambda: rt.test_mass_and_element_conservation("h2_9sp_21rx"),
+        lambda: rt.test_zero_net_rates_at_equilibrium("h2_9sp_21rx", 2000.0, 5 * P_ATM),
+        lambda: rt.test_zero_net_rates_at_equilibrium("ch4_53sp_325rx", 2500.0, P_ATM),
+        lambda: rt.test_de_donder_relation("h2_9sp_21rx"),
+        rt.test_arrhenius_special_values,
+        rt.test_third_body_concentration,
+        rt.test_troe_lindemann_limit,
+        rt.test_troe_centre_and_limits,
+        lambda: rt.test_enthalpy_shift_invariance("h2_9sp_21rx"),
+        lambda: rt.test_heat_release_is_minus_sum_h_omega(m53),
+        lambda: rt.test_species_relabelling(m53),
+        tr.test_power_law_fits_and_pure_species_limits,
+        tr.test_wilke_binary_hand_values,
+        tr.test_mathur_binary_hand_value,
+        lambda: tr.test_diffusion_pressure_scaling(m53),
+        lambda: tr.test_hirschfelder_curtiss_textbook_form(m9),
+        lambda: tr.test_mixture_values_within_species_bounds(m53),
+        lambda: dv.test_jacobian_matches_central_differences("h2_9sp_21rx"),
+        lambda: dv.test_grad_lnA_closed_form_and_fd("h2_9sp_21rx"),
+    ]
+
+
+@pytest.fixture(scope="module")
+def variants(tmp_path_factory):
+    d = tmp_path_factory.mktemp("oracle_mutants")
+
+    def make(item):
+        name, (old, new) = item
+        assert SRC.count(old) == 1, f"mutation {name}: snippet must occur exactly once"
+        return name, oracle.build_variant(SRC.replace(old, new), str(d / f"lib_{name}.so"))
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return dict(ex.map(make, MUTATIONS.items()))
+
+
+def test_unmutated_oracle_passes_every_pin():
+    for pin in _pins():
+        pin()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(variants, name):
+    caught = 0
+    with oracle.use_library(variants[name]):
+        for pin in _pins():
+            try:
+                pin()
+            except (AssertionError, ValueError, FloatingPointError):
+                caught += 1
+    assert caught >= 1, f"no pin fails for the planted mistake {name}"

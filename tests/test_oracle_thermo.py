@@ -81,3 +81,15 @@ def test_mixture_properties_are_mass_weighted(mech53):
     # g = h - T s consistency with the complex-step s of one species
     o = oracle.nasa7_cs(mech53, 7, st.T)
     assert np.allclose(th["g_k"][7], o["h"] - st.T * o["s"], rtol=1e-12, atol=1e-9 * R_GAS * st.T.max())
+
+
+def test_heat_capacity_stays_on_the_fitted_curve(mech53, mech120):
+    """c_p/R of every species stays within the range of the smooth curve it was fitted to
+    (c0 in [2.5, 4.5], rise up to 1.5 per atom): evaluating the wrong NASA range, or a
+    coefficient in the wrong slot, leaves this band."""
+    T = np.linspace(300.0, 3500.0, 161)
+    for m in (mech53, mech120):
+        for k in range(m.K):
+            cp = oracle.nasa7_cs(m, k, T)["cp"] / R_GAS
+            top = 4.5 + 1.5 * m.atoms[k].sum()
+            assert np.all(cp > 2.3) and np.all(cp < top + 0.3), k
