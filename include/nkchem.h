@@ -200,6 +200,32 @@ nk_status nk_rates_vjp(const nk_mech* mech, int64_t n, int64_t ld, const double*
                        const double* bar_omega, const double* bar_hrr, double* gT, double* gY,
                        double* g_lnA, void* workspace, size_t workspace_bytes, nk_stream stream);
 
+/*
+ * nk_rates_vjp without a workspace argument; it allocates no device memory.  (No counterpart
+ * in the paper: this is a convenience of the library.)
+ *
+ * For callers that cannot allocate device memory or hand one in: for example a right-hand-
+ * side or Jacobian-product callback of an ODE or nonlinear solver whose fixed signature has
+ * no place for a workspace, or code inside a framework whose memory pool owns the whole
+ * device and forbids direct cudaMalloc.  cudaMalloc/cudaFree may also synchronize the device,
+ * which a caller in the middle of asynchronous work on several streams must avoid.
+ *
+ * Same arguments, results and errors as nk_rates_vjp, except that the per-block ln A partial
+ * sums go to a fixed scratch array compiled into the library (8 MiB, held on every GPU that
+ * loads the library until the process exits).  If g_lnA would need more than that (more than
+ * 1024 reactions at full occupancy; see nk_rates_vjp_workspace), the call returns
+ * NK_EUNSUPPORTED and enqueues nothing.  The first call on a device looks up the scratch
+ * address on that device (make that first call before any stream capture); later calls only
+ * read a cached pointer.  All calls share the one scratch array: calls that overlap on the
+ * GPU (on different streams, or from different host threads without ordering) race and
+ * corrupt each other's g_lnA; order them on one stream.  Every call overwrites the partial
+ * sums it reads, so nothing needs clearing between calls.
+ */
+nk_status nk_rates_vjp_noalloc(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                               const double* p, const double* Y, const double* dlnA,
+                               const double* bar_omega, const double* bar_hrr, double* gT,
+                               double* gY, double* g_lnA, nk_stream stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* nk_last_error(void);
 

@@ -67,6 +67,7 @@ _SIGS = {
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_rates_vjp_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_rates_vjp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [ctypes.c_size_t, _vp]),
+    "nk_rates_vjp_noalloc": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 9 + [_vp]),
 }
 
 

@@ -9,6 +9,8 @@
 // qbar_r q_r (a shift of ln A_r scales k_f and k_r alike, and both limits of a Troe reaction);
 // it is summed over the points of a warp by shuffles, over the warps of a block in shared
 // memory, and over blocks by a second kernel in a fixed order: deterministic, no atomics.
+#include <mutex>
+
 #include "nk_internal.cuh"
 
 namespace nk {
@@ -294,6 +296,34 @@ cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, c
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- no-allocation variant
+// Scratch for the per-block ln A partial sums of nk_rates_vjp_noalloc: a fixed device array in
+// this library's module, present on every GPU that loads the library until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};   // device address of the array, per device ordinal
+}  // namespace
+
+cudaError_t noalloc_scratch(void** ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        // host code may not use the array's name as a device address: ask the runtime once
+        // per device, with that device current
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
 
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n) {
     const int blk = vjp_block(m);

@@ -467,4 +467,32 @@ nk_status nk_rates_vjp(const nk_mech* m, int64_t n, int64_t ld, const double* T,
                     "vjp kernel launch");
 }
 
+nk_status nk_rates_vjp_noalloc(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                               const double* Y, const double* dlnA, const double* bar_omega,
+                               const double* bar_hrr, double* gT, double* gY, double* g_lnA, nk_stream stream) {
+    if (m && g_lnA && n == 0) {
+        cudaError_t e = cudaMemsetAsync(g_lnA, 0, sizeof(double) * m->d.R, (cudaStream_t)stream);
+        return launched(e, "cudaMemsetAsync(g_lnA)");
+    }
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!bar_omega || !gT || !gY) return fail(NK_EINVAL, "bar_omega, gT and gY must not be NULL");
+    if ((st = check_out({bar_omega, bar_hrr, gT, gY, g_lnA, dlnA})) != NK_OK) return st;
+    void* scratch = nullptr;
+    if (g_lnA) {
+        const size_t need = nk::vjp_workspace_bytes(m->d, n);
+        const size_t cap = nk::kNoallocScratchDoubles * sizeof(double);
+        if (need > cap)
+            return fail(NK_EUNSUPPORTED,
+                        "nk_rates_vjp_noalloc: the ln A partial sums need %zu bytes, more than its fixed %zu-byte "
+                        "scratch (R=%d reactions); use nk_rates_vjp with a workspace", need, cap, m->d.R);
+        cudaError_t e = nk::noalloc_scratch(&scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    }
+    return launched(nk::launch_vjp(m->d, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, g_lnA, scratch,
+                                   (cudaStream_t)stream),
+                    "vjp kernel launch");
+}
+
 }  // extern "C"

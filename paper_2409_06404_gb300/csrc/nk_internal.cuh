@@ -119,6 +119,11 @@ cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        const double* bar_hrr, double* gT, double* gY, double* g_lnA,
                        void* ws, cudaStream_t s);
 
+// Capacity of the fixed device scratch of nk_rates_vjp_noalloc (8 MiB of doubles).
+constexpr size_t kNoallocScratchDoubles = (size_t)1 << 20;
+// Device address of that scratch on the current device (looked up once per device).
+cudaError_t noalloc_scratch(void** ptr);
+
 // Largest block size in {128, 64, 32} whose per-thread shared-memory scratch
 // (bytes_per_thread * block) stays within the budget; 0 if none fits.
 int pick_block(size_t bytes_per_thread, size_t budget);
