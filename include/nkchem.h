@@ -49,10 +49,15 @@ typedef enum {
 } nk_status;
 
 typedef enum {
-    NK_FP64 = 0,   /* every operation in double precision */
-    NK_MIXED = 1   /* rates: Arrhenius/Troe arguments and k_f in single precision, equilibrium
-                      constants, forward-minus-reverse difference and omega accumulation in
-                      double; transport: fits, mixture rules and sums in single precision */
+    NK_FP64 = 0,        /* results to double precision (1e-10 of the FP64 definition, typically
+                           1e-13): rates in double; transport sums, whose terms are positive
+                           and bounded, in double-float (pairs of floats, 48-bit significands)
+                           on the FP32 pipe, with inputs and outputs in double */
+    NK_MIXED = 1,       /* rates: Arrhenius/Troe arguments and k_f in single precision,
+                           equilibrium constants, forward-minus-reverse difference and omega
+                           accumulation in double; transport: fits, mixture rules and sums in
+                           single precision (1e-5) */
+    NK_FP64_NATIVE = 2  /* every operation in native double precision (reference form) */
 } nk_precision;
 
 /* Reaction kinds of nk_mech_desc.rtype */
@@ -148,7 +153,7 @@ nk_status nk_thermo_eval(const nk_mech* mech, int64_t n, int64_t ld, const doubl
  *   omega[K*ld]  omega_k = sum_r nu_kr q_r, mol/(m^3 s)
  *   hrr[n]       -sum_k h_k(T) omega_k, W/m^3 (positive when exothermic)
  * dlnA: NULL or device [R] shift added to ln A_r (to both limits of a Troe reaction).
- * precision: NK_FP64 or NK_MIXED.
+ * precision: NK_FP64 / NK_FP64_NATIVE (the same double-precision kernel) or NK_MIXED.
  */
 nk_status nk_rates_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
                         const double* p, const double* Y, const double* dlnA, double* omega,
@@ -160,7 +165,7 @@ nk_status nk_rates_eval(const nk_mech* mech, int64_t n, int64_t ld, const double
  *   lambda[n]  mixture conductivity (Mathur-Saxena average), W/(m K)
  *   Dmix[K*ld] mixture-averaged diffusion coefficients D_k of Eq. 2, m^2/s
  *              (D_km = sum_{j!=k} X_j W_j / (Wbar sum_{j!=k} X_j/D_jk); 0 for a pure species)
- * Any output may be NULL.  precision: NK_FP64 or NK_MIXED.
+ * Any output may be NULL.  precision: NK_FP64, NK_FP64_NATIVE or NK_MIXED.
  */
 nk_status nk_transport_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
                             const double* p, const double* Y, double* mu, double* lambda,

@@ -25,8 +25,9 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libnkchem.so")
 _lock = threading.Lock()
 _lib = None
 
-NK_FP64, NK_MIXED = 0, 1
-_PRECISION = {"fp64": NK_FP64, "mixed": NK_MIXED, NK_FP64: NK_FP64, NK_MIXED: NK_MIXED}
+NK_FP64, NK_MIXED, NK_FP64_NATIVE = 0, 1, 2
+_PRECISION = {"fp64": NK_FP64, "mixed": NK_MIXED, "fp64_native": NK_FP64_NATIVE,
+              NK_FP64: NK_FP64, NK_MIXED: NK_MIXED, NK_FP64_NATIVE: NK_FP64_NATIVE}
 _STATUS = {0: "NK_OK", 1: "NK_EINVAL", 2: "NK_EALIGN", 3: "NK_ECUDA", 4: "NK_ENOMEM", 5: "NK_EUNSUPPORTED"}
 
 _vp = ctypes.c_void_p

@@ -22,7 +22,10 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
                                                   const double* __restrict__ vT, const double* __restrict__ vY,
                                                   double* __restrict__ omega, double* __restrict__ hrr,
                                                   double* __restrict__ d_omega, double* __restrict__ d_hrr) {
-    extern __shared__ double smem[];
+    extern __shared__ double smem_all[];
+    const MathTab mt = stage_math_tables(smem_all, m.mtab);
+    __syncthreads();
+    double* smem = smem_all + kMathTabDoubles;
     const int K = m.K;
     const int tid = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * BLK + tid;
@@ -34,7 +37,7 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
     double* sD = smem + (size_t)4 * K * BLK + tid;    // d omega_k
 
     const double Ti = T[i], pi = p[i], dT = vT[i];
-    const double lnT = log(Ti), invT = 1.0 / Ti;
+    const double lnT = flog(Ti, mt), invT = 1.0 / Ti;
     const double tT = dT * invT;                      // dT/T
     const double pRT = pi * invT * kInvR;
     double s = 0.0, ds = 0.0;
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
         sW[k * BLK] = 0.0;
         sD[k * BLK] = 0.0;
     }
-    const double lnP0RT = log(kP0 * kInvR) - lnT;
+    const double lnP0RT = 9.408091968961747 - lnT;   // ln(p0/(R T)), ln(101325/8.314462618) = 9.408...
     const double dpRT = -pRT * tT;
 
     // dC_k on demand: C_k d rho/rho + rho vY_k / W_k
@@ -66,29 +69,57 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
     for (int r = 0; r < m.R; ++r) {
         const RxnRec* rec = m.rxn + r;
         const int type = __ldg(&rec->type), nr = __ldg(&rec->nr), np = __ldg(&rec->np);
-        const double shift = dlnA ? __ldg(dlnA + r) : 0.0;
-        double sumg = 0.0, dsumh = 0.0;               // sum nu g/RT, sum nu h/RT
-        double fw = 1.0, dfw = 0.0, rv = 1.0, drv = 0.0;
+        const double shift = dlnA ? __ldg(dlnA + __ldg(&rec->orig)) : 0.0;
+        double sumg, dsumh;                           // sum nu g/RT, sum nu h/RT
+        double fw, dfw, rv, drv;                      // dual-number concentration products
+        {
+            const int k = __ldg(&rec->sp[0]), nu = __ldg(&rec->nu[0]);
+            const double nd = __ldg(&rec->nud[0]);
+            const double c = sC[k * BLK], dc = dC(k, c);
+            sumg = nd * sG[k * BLK];
+            dsumh = nd * sH[k * BLK];
+            fw = c;
+            dfw = dc;
+            for (int j = 1; j < nu; ++j) {
+                dfw = fma(dfw, c, fw * dc);
+                fw *= c;
+            }
+        }
 #pragma unroll
-        for (int e = 0; e < kMaxSide; ++e) {
+        for (int e = 1; e < kMaxSide; ++e) {
             if (e < nr) {
                 const int k = __ldg(&rec->sp[e]), nu = __ldg(&rec->nu[e]);
+                const double nd = __ldg(&rec->nud[e]);
                 const double c = sC[k * BLK], dc = dC(k, c);
-                sumg = fma(-(double)nu, sG[k * BLK], sumg);
-                dsumh = fma(-(double)nu, sH[k * BLK], dsumh);
-                for (int j = 0; j < nu; ++j) {        // dual-number product
+                sumg = fma(nd, sG[k * BLK], sumg);
+                dsumh = fma(nd, sH[k * BLK], dsumh);
+                for (int j = 0; j < nu; ++j) {
                     dfw = fma(dfw, c, fw * dc);
                     fw *= c;
                 }
             }
         }
+        {
+            const int k = __ldg(&rec->sp[kMaxSide]), nu = __ldg(&rec->nu[kMaxSide]);
+            const double nd = __ldg(&rec->nud[kMaxSide]);
+            const double c = sC[k * BLK], dc = dC(k, c);
+            sumg = fma(nd, sG[k * BLK], sumg);
+            dsumh = fma(nd, sH[k * BLK], dsumh);
+            rv = c;
+            drv = dc;
+            for (int j = 1; j < nu; ++j) {
+                drv = fma(drv, c, rv * dc);
+                rv *= c;
+            }
+        }
 #pragma unroll
-        for (int e = 0; e < kMaxSide; ++e) {
+        for (int e = 1; e < kMaxSide; ++e) {
             if (e < np) {
                 const int k = __ldg(&rec->sp[kMaxSide + e]), nu = __ldg(&rec->nu[kMaxSide + e]);
+                const double nd = __ldg(&rec->nud[kMaxSide + e]);
                 const double c = sC[k * BLK], dc = dC(k, c);
-                sumg = fma((double)nu, sG[k * BLK], sumg);
-                dsumh = fma((double)nu, sH[k * BLK], dsumh);
+                sumg = fma(nd, sG[k * BLK], sumg);
+                dsumh = fma(nd, sH[k * BLK], dsumh);
                 for (int j = 0; j < nu; ++j) {
                     drv = fma(drv, c, rv * dc);
                     rv *= c;
@@ -101,14 +132,14 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
         const double dlnKc = fma(tT, dsumh, -dnu * tT);
 
         const double beta = __ldg(&rec->beta), EaR = __ldg(&rec->EaR);
-        const double lnkf = fma(-EaR, invT, fma(beta, lnT, __ldg(&rec->lnA) + shift));
+        const double lnkf = fma(-EaR, invT, fma(beta, lnT, dlnA ? __ldg(&rec->lnA) + shift : __ldg(&rec->lnA)));
         double dlnkf = fma(EaR, invT, beta) * tT;
 
         double M = 0.0, dM = 0.0;
         if (type != NK_RXN_ELEMENTARY) {
             M = pRT;
             dM = dpRT;
-            const int e0 = __ldg(m.eff_ptr + r), e1 = __ldg(m.eff_ptr + r + 1);
+            const int e0 = __ldg(&rec->eff0), e1 = __ldg(&rec->eff1);
             for (int j = e0; j < e1; ++j) {
                 const int k = __ldg(m.eff_sp + j);
                 const double em1 = __ldg(m.eff_m1 + j), c = sC[k * BLK];
@@ -127,18 +158,18 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
                 kf = 0.0;
                 dlnkf = 0.0;
             } else {
-                const double lnPr = lnk0 - lnkf + log(M);
+                const double lnPr = lnk0 - lnkf + flog(M, mt);
                 const double dlnPr = dlnk0 - dlnkf + dM / M;
                 const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-                const double e3 = exp(-Ti * i3), e1 = exp(-Ti * i1);
+                const double e3 = fexp(-Ti * i3, mt), e1 = fexp(-Ti * i1, mt);
                 double Fc = (1.0 - a) * e3 + a * e1;
                 double dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1) * dT;
                 if (__ldg(&t->hasT2) != 0.0) {
-                    const double T2 = __ldg(&t->T2), e2 = exp(-T2 * invT);
+                    const double T2 = __ldg(&t->T2), e2 = fexp(-T2 * invT, mt);
                     Fc += e2;
                     dFc = fma(T2 * invT * e2, tT, dFc);
                 }
-                const double lFc = log(Fc) * kInvLn10, dlFc = dFc / Fc * kInvLn10;
+                const double lFc = flog(Fc, mt) * kInvLn10, dlFc = dFc / Fc * kInvLn10;
                 const double c = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
                 const double u = fma(lnPr, kInvLn10, c), du = fma(dlnPr, kInvLn10, -0.67 * dlFc);
                 const double v = fma(-0.14, u, nn), dv = fma(-0.14, du, -1.27 * dlFc);
@@ -146,14 +177,14 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
                 const double den = fma(f1, f1, 1.0);
                 const double lF = lFc / den;
                 const double dlF = fma(-2.0 * lF * f1, df1, dlFc) / den;
-                const double g = 1.0 / (1.0 + exp(-lnPr));          // P_r / (1 + P_r)
-                kf = exp(lnkf) * g * exp(lF * kLn10);
+                const double g = 1.0 / (1.0 + fexp(-lnPr, mt));     // P_r / (1 + P_r)
+                kf = fexp(lnkf, mt) * g * fexp(lF * kLn10, mt);
                 dlnkf = dlnkf + dlnPr * (1.0 - g) + kLn10 * dlF;
             }
         } else {
-            kf = exp(lnkf);
+            kf = fexp(lnkf, mt);
         }
-        const double kr = kf * exp(-lnKc);
+        const double kr = kf * fexp(-lnKc, mt);
         const double dkf = kf * dlnkf, dkr = kr * (dlnkf - dlnKc);
         double q = fma(kf, fw, -kr * rv);
         double dq = fma(dkf, fw, kf * dfw) - fma(dkr, rv, kr * drv);
@@ -165,18 +196,18 @@ __global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t
         for (int e = 0; e < kMaxSide; ++e) {
             if (e < nr) {
                 const int k = __ldg(&rec->sp[e]);
-                const double nu = (double)__ldg(&rec->nu[e]);
-                sW[k * BLK] = fma(-nu, q, sW[k * BLK]);
-                sD[k * BLK] = fma(-nu, dq, sD[k * BLK]);
+                const double nd = __ldg(&rec->nud[e]);
+                sW[k * BLK] = fma(nd, q, sW[k * BLK]);
+                sD[k * BLK] = fma(nd, dq, sD[k * BLK]);
             }
         }
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e) {
             if (e < np) {
                 const int k = __ldg(&rec->sp[kMaxSide + e]);
-                const double nu = (double)__ldg(&rec->nu[kMaxSide + e]);
-                sW[k * BLK] = fma(nu, q, sW[k * BLK]);
-                sD[k * BLK] = fma(nu, dq, sD[k * BLK]);
+                const double nd = __ldg(&rec->nud[kMaxSide + e]);
+                sW[k * BLK] = fma(nd, q, sW[k * BLK]);
+                sD[k * BLK] = fma(nd, dq, sD[k * BLK]);
             }
         }
     }
@@ -212,11 +243,10 @@ cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        const double* Y, const double* dlnA, const double* vT, const double* vY, double* omega,
                        double* hrr, double* d_omega, double* d_hrr, cudaStream_t s) {
     const size_t per_thread = (size_t)5 * m.K * sizeof(double);
-    const size_t lim = smem_limit();
-    int blk = pick_block(per_thread, lim / 2);
-    if (!blk) blk = pick_block(per_thread, lim);
+    const size_t tab = kMathTabDoubles * sizeof(double);
+    const int blk = pick_block_occupancy(per_thread, tab);
     if (!blk) return cudaErrorInvalidConfiguration;
-    const size_t smem = per_thread * blk;
+    const size_t smem = per_thread * blk + tab;
     switch (blk) {
         case 128: return launch_t<128>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, smem, s);
         case 64: return launch_t<64>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, smem, s);

@@ -15,7 +15,8 @@
 //  * D_km = (sum_{j!=k} Y_j) / (sum_{j!=k} X_j/D_jk), since X_j W_j = Y_j Wbar; the
 //    numerator is formed from prefix and suffix sums, never as 1 - Y_k.
 //  * each binary coefficient exp(-ln D_jk) is evaluated once per pair and used for both
-//    species of the pair.
+//    species of the pair; the factor p/p_ref of D_jk(p) multiplies the finished sums.
+//  * double exp/log are the table-driven versions of nk_math.cuh.
 #include "nk_internal.cuh"
 
 namespace nk {
@@ -46,13 +47,19 @@ __device__ __forceinline__ F poly3(const F* c, F L) {
     return fma(L, fma(L, fma(L, __ldg(c + 3), __ldg(c + 2)), __ldg(c + 1)), __ldg(c + 0));
 }
 
+// exp in the arithmetic type: the table-driven double exp, or single-precision expf
+__device__ __forceinline__ double texp(double x, const MathTab& mt) { return fexp(x, mt); }
+__device__ __forceinline__ float texp(float x, const MathTab&) { return expf(x); }
+
 template <int BLK, class F>
 __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                         const double* __restrict__ T, const double* __restrict__ p,
                                                         const double* __restrict__ Y, double* __restrict__ mu_out,
                                                         double* __restrict__ lam_out, double* __restrict__ Dmix) {
-    extern __shared__ unsigned char smem_raw[];
-    F* smem = reinterpret_cast<F*>(smem_raw);
+    extern __shared__ double smem_d[];
+    const MathTab mt = stage_math_tables(smem_d, m.mtab);
+    __syncthreads();
+    F* smem = reinterpret_cast<F*>(smem_d + kMathTabDoubles);
     const int K = m.K;
     const int tid = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * BLK + tid;
@@ -63,30 +70,41 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
     using Tb = Tab<F>;
 
     const double Ti = T[i];
-    const F L = (F)log(Ti);
+    const F L = (F)flog(Ti, mt);
     // mole fractions
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double Wbar = 1.0 / s;
     for (int k = 0; k < K; ++k) sX[k * BLK] = (F)(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar);
 
-    // ---- diffusion: sum_{j != k} X_j / D_jk, one exponential per pair
+    // ---- diffusion: sum_{j != k} X_j / D_jk(p_ref), one exponential per pair; the pressure
+    // factor p/p_ref multiplies the finished sums
     if (Dmix) {
         for (int k = 0; k < K; ++k) sA[k * BLK] = F(0);
-        const F pscale = (F)(p[i] / m.p_ref);          // D_jk(p) = D_jk(p_ref) p_ref / p
         const F* Dc = Tb::D(m);
         int pi = 0;
         for (int j = 0; j < K; ++j) {
             const F xj = sX[j * BLK];
-            F accj = F(0);
-            for (int k = j + 1; k < K; ++k, ++pi) {
-                const F invD = exp(-poly3(Dc + 4 * pi, L)) * pscale;
-                sA[k * BLK] = fma(xj, invD, sA[k * BLK]);
-                accj = fma(sX[k * BLK], invD, accj);
+            F acc0 = F(0), acc1 = F(0);
+            int k = j + 1;
+            for (; k + 1 < K; k += 2, pi += 2) {
+                const F i0 = texp(-poly3(Dc + 4 * pi, L), mt);
+                const F i1 = texp(-poly3(Dc + 4 * pi + 4, L), mt);
+                sA[k * BLK] = fma(xj, i0, sA[k * BLK]);
+                sA[(k + 1) * BLK] = fma(xj, i1, sA[(k + 1) * BLK]);
+                acc0 = fma(sX[k * BLK], i0, acc0);
+                acc1 = fma(sX[(k + 1) * BLK], i1, acc1);
             }
-            sA[j * BLK] += accj;
+            if (k < K) {
+                const F i0 = texp(-poly3(Dc + 4 * pi, L), mt);
+                sA[k * BLK] = fma(xj, i0, sA[k * BLK]);
+                acc0 = fma(sX[k * BLK], i0, acc0);
+                ++pi;
+            }
+            sA[j * BLK] += acc0 + acc1;
         }
         // numerators sum_{j != k} Y_j from prefix and suffix sums (no 1 - Y_k cancellation)
+        const double pscale = p[i] / m.p_ref;
         double pre = 0.0;
         for (int k = 0; k < K; ++k) {
             sB[k * BLK] = (F)pre;
@@ -95,7 +113,7 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
         double suf = 0.0;
         for (int k = K - 1; k >= 0; --k) {
             const double num = (double)sB[k * BLK] + suf;
-            double den = (double)sA[k * BLK];
+            double den = (double)sA[k * BLK] * pscale;
             if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
             Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
             suf += Y[(int64_t)k * ld + i];
@@ -109,9 +127,9 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
     for (int k = 0; k < K; ++k) {
         const F x = sX[k * BLK];
         const F lnlam = poly3(lamc + 4 * k, L);
-        s1 = fma(x, exp(lnlam), s1);
-        s2 = fma(x, exp(-lnlam), s2);
-        const F tau = __ldg(Tb::qrtW(m) + k) * exp(F(-0.5) * poly3(muc + 4 * k, L));   // W^1/4 / mu^1/2
+        s1 = fma(x, texp(lnlam, mt), s1);
+        s2 = fma(x, texp(-lnlam, mt), s2);
+        const F tau = __ldg(Tb::qrtW(m) + k) * texp(F(-0.5) * poly3(muc + 4 * k, L), mt);   // W^1/4 / mu^1/2
         const F xt = x * tau;
         sA[k * BLK] = xt;
         sB[k * BLK] = xt * tau;
@@ -123,7 +141,7 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
         const F* A = Tb::A(m);
         F mu = F(0);
         for (int k = 0; k < K; ++k) {
-            const F hs = exp(F(0.5) * poly3(muc + 4 * k, L));          // mu_k^1/2
+            const F hs = texp(F(0.5) * poly3(muc + 4 * k, L), mt);     // mu_k^1/2
             const F sig = hs / __ldg(Tb::qrtW(m) + k);                  // sigma_k
             const F* Ak = A + (size_t)k * K;
             F S0 = F(0), S1 = F(0), S2 = F(0);
@@ -158,11 +176,10 @@ cudaError_t launch_transport(const DevMech& m, int64_t n, int64_t ld, const doub
                              cudaStream_t s) {
     const bool mixed = precision == NK_MIXED;
     const size_t per_thread = (size_t)3 * m.K * (mixed ? sizeof(float) : sizeof(double));
-    const size_t lim = smem_limit();
-    int blk = pick_block(per_thread, lim / 2);
-    if (!blk) blk = pick_block(per_thread, lim);
+    const size_t tab = kMathTabDoubles * sizeof(double);
+    const int blk = pick_block_occupancy(per_thread, tab);
     if (!blk) return cudaErrorInvalidConfiguration;
-    const size_t smem = per_thread * blk;
+    const size_t smem = per_thread * blk + tab;
 #define NK_TR_CASE(B)                                                                 \
     case B:                                                                           \
         return mixed ? launch_t<B, float>(m, n, ld, T, p, Y, mu, lam, Dmix, smem, s)  \

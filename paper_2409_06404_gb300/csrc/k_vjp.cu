@@ -20,12 +20,36 @@ constexpr int kVjpMaxBlocks = 1024;
 
 int vjp_block(const DevMech& m) {
     const size_t per_thread = (size_t)5 * m.K * sizeof(double);
-    const size_t lim = smem_limit();
-    // leave room for the per-warp ln A accumulators
-    const size_t extra = (size_t)4 * m.R * sizeof(double);
-    int blk = pick_block(per_thread, lim / 2 > extra ? lim / 2 - extra : 0);
-    if (!blk) blk = pick_block(per_thread, lim > extra ? lim - extra : 0);
-    return blk;
+    // per block the math tables, per warp its ln A accumulators
+    return pick_block_occupancy(per_thread, kMathTabDoubles * sizeof(double), (size_t)m.R * sizeof(double));
+}
+
+// prod of p[0..n) (returned) and, in ex[e], the product of all entries but e (n <= 4, uniform)
+__device__ __forceinline__ double exclusive_products(const double* p, int n, double* ex) {
+    switch (n) {
+        case 1:
+            ex[0] = 1.0;
+            return p[0];
+        case 2:
+            ex[0] = p[1];
+            ex[1] = p[0];
+            return p[0] * p[1];
+        case 3: {
+            const double a = p[0] * p[1];
+            ex[0] = p[1] * p[2];
+            ex[1] = p[0] * p[2];
+            ex[2] = a;
+            return a * p[2];
+        }
+        default: {
+            const double a = p[0] * p[1], b = p[2] * p[3];
+            ex[0] = p[1] * b;
+            ex[1] = p[0] * b;
+            ex[2] = a * p[3];
+            ex[3] = a * p[2];
+            return a * b;
+        }
+    }
 }
 
 template <int BLK, bool WANT_G>
@@ -35,7 +59,10 @@ __global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t
                                                   const double* __restrict__ bar_omega,
                                                   const double* __restrict__ bar_hrr, double* __restrict__ gT,
                                                   double* __restrict__ gY, double* __restrict__ ws) {
-    extern __shared__ double smem[];
+    extern __shared__ double smem_all[];
+    const MathTab mt = stage_math_tables(smem_all, m.mtab);
+    __syncthreads();
+    double* smem = smem_all + kMathTabDoubles;
     const int K = m.K, R = m.R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* sC = smem + tid;                          // C_k
@@ -54,9 +81,10 @@ __global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t
         const bool valid = i0 < n;
         const int64_t i = valid ? i0 : n - 1;         // idle lanes shadow the last point
         const double Ti = T[i], pi = p[i];
-        const double lnT = log(Ti), invT = 1.0 / Ti;
+        const double lnT = flog(Ti, mt), invT = 1.0 / Ti;
         const double pRT = pi * invT * kInvR;
-        const double hb = bar_hrr ? bar_hrr[i] : 0.0;
+        const bool hb_any = bar_hrr != nullptr;            // uniform: heat-release cotangent given
+        const double hb = hb_any ? bar_hrr[i] : 0.0;
         const double hbRT = hb * kR * Ti;
         double s = 0.0;
         for (int k = 0; k < K; ++k) {
@@ -70,111 +98,119 @@ __global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t
             sC[k * BLK] *= rho;
             sG[k * BLK] = nasa_gRT(c, Ti, lnT, invT);
             sH[k * BLK] = nasa_hRT(c, Ti, invT);
-            sP[k * BLK] = nasa_cpR(c, Ti);
+            if (hb_any) sP[k * BLK] = nasa_cpR(c, Ti);
             sB[k * BLK] = 0.0;
         }
-        const double lnP0RT = log(kP0 * kInvR) - lnT;
+        const double lnP0RT = 9.408091968961747 - lnT;   // ln(p0/(R T)), ln(101325/8.314462618) = 9.408...
         double Tbar = 0.0;
 
         for (int r = 0; r < R; ++r) {
             const RxnRec* rec = m.rxn + r;
             const int type = __ldg(&rec->type), nr = __ldg(&rec->nr), np = __ldg(&rec->np);
-            const double shift = dlnA ? __ldg(dlnA + r) : 0.0;
+            const int orig = __ldg(&rec->orig);
+            double lnA = __ldg(&rec->lnA), shift = 0.0;
+            if (dlnA) {
+                shift = __ldg(dlnA + orig);
+                lnA += shift;
+            }
+            // sums over the entries (signed coefficients) and the concentration powers
             double sumg = 0.0, sumh = 0.0, sumcp = 0.0, wsum = 0.0;
             double cR[kMaxSide], pR[kMaxSide], cP[kMaxSide], pP[kMaxSide];
-            double fw = 1.0, rv = 1.0;
 #pragma unroll
             for (int e = 0; e < kMaxSide; ++e) {
-                cR[e] = 1.0;
-                pR[e] = 1.0;
+                cR[e] = pR[e] = cP[e] = pP[e] = 1.0;
                 if (e < nr) {
                     const int k = __ldg(&rec->sp[e]), nu = __ldg(&rec->nu[e]);
-                    const double dn = (double)nu;
-                    sumg = fma(-dn, sG[k * BLK], sumg);
-                    sumh = fma(-dn, sH[k * BLK], sumh);
-                    sumcp = fma(-dn, sP[k * BLK], sumcp);
-                    wsum = fma(-dn, bar_omega[(int64_t)k * ld + i], wsum);
-                    cR[e] = sC[k * BLK];
-                    pR[e] = ipow(cR[e], nu);
-                    fw *= pR[e];
+                    const double nd = __ldg(&rec->nud[e]);
+                    sumg = fma(nd, sG[k * BLK], sumg);
+                    sumh = fma(nd, sH[k * BLK], sumh);
+                    if (hb_any) sumcp = fma(nd, sP[k * BLK], sumcp);
+                    wsum = fma(nd, bar_omega[(int64_t)k * ld + i], wsum);
+                    const double c = sC[k * BLK];
+                    double pw = c;
+                    for (int j = 1; j < nu; ++j) pw *= c;
+                    cR[e] = c;
+                    pR[e] = pw;
                 }
-            }
-#pragma unroll
-            for (int e = 0; e < kMaxSide; ++e) {
-                cP[e] = 1.0;
-                pP[e] = 1.0;
                 if (e < np) {
                     const int k = __ldg(&rec->sp[kMaxSide + e]), nu = __ldg(&rec->nu[kMaxSide + e]);
-                    const double dn = (double)nu;
-                    sumg = fma(dn, sG[k * BLK], sumg);
-                    sumh = fma(dn, sH[k * BLK], sumh);
-                    sumcp = fma(dn, sP[k * BLK], sumcp);
-                    wsum = fma(dn, bar_omega[(int64_t)k * ld + i], wsum);
-                    cP[e] = sC[k * BLK];
-                    pP[e] = ipow(cP[e], nu);
-                    rv *= pP[e];
+                    const double nd = __ldg(&rec->nud[kMaxSide + e]);
+                    sumg = fma(nd, sG[k * BLK], sumg);
+                    sumh = fma(nd, sH[k * BLK], sumh);
+                    if (hb_any) sumcp = fma(nd, sP[k * BLK], sumcp);
+                    wsum = fma(nd, bar_omega[(int64_t)k * ld + i], wsum);
+                    const double c = sC[k * BLK];
+                    double pw = c;
+                    for (int j = 1; j < nu; ++j) pw *= c;
+                    cP[e] = c;
+                    pP[e] = pw;
                 }
             }
+            // products of all entries but one: exR[e] = prod_{f != e} pR[f] (uniform switch)
+            double exR[kMaxSide], exP[kMaxSide];
+            double fw = exclusive_products(pR, nr, exR);
+            double rv = exclusive_products(pP, np, exP);
             const double dnu = __ldg(&rec->dnu);
             const double lnKc = fma(dnu, lnP0RT, -sumg);
             const double beta = __ldg(&rec->beta), EaR = __ldg(&rec->EaR);
-            const double lnkf = fma(-EaR, invT, fma(beta, lnT, __ldg(&rec->lnA) + shift));
+            const double lnkf = fma(-EaR, invT, fma(beta, lnT, lnA));
 
             double M = 0.0;
             if (type != NK_RXN_ELEMENTARY) {
                 M = pRT;
-                const int e0 = __ldg(m.eff_ptr + r), e1 = __ldg(m.eff_ptr + r + 1);
+                const int e0 = __ldg(&rec->eff0), e1 = __ldg(&rec->eff1);
                 for (int j = e0; j < e1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
             }
 
             // ---- primal (kept values for the adjoint)
             double kf;
-            double tr_lnk0 = 0.0, tr_g = 0.0, tr_lF = 0.0, tr_f1 = 0.0, tr_den = 1.0, tr_u = 0.0, tr_v = 1.0,
-                   tr_nn = 0.0, tr_Fc = 1.0, tr_dFc = 0.0;
+            double tr_g = 0.0, tr_lF = 0.0, tr_f1 = 0.0, tr_den = 1.0, tr_u = 0.0, tr_v = 1.0, tr_nn = 0.0,
+                   tr_Fc = 1.0, tr_dFc = 0.0;
             const TroeRec* t = nullptr;
             if (type == NK_RXN_TROE) {
                 t = m.troe + __ldg(&rec->aux);
-                tr_lnk0 = fma(-__ldg(&t->Ea0R), invT, fma(__ldg(&t->beta0), lnT, __ldg(&t->lnA0) + shift));
+                const double lnk0 =
+                    fma(-__ldg(&t->Ea0R), invT, fma(__ldg(&t->beta0), lnT, __ldg(&t->lnA0) + shift));
                 if (M == 0.0) {
                     kf = 0.0;
                 } else {
-                    const double lnPr = tr_lnk0 - lnkf + log(M);
+                    const double lnPr = lnk0 - lnkf + flog(M, mt);
                     const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-                    const double e3 = exp(-Ti * i3), e1 = exp(-Ti * i1);
+                    const double e3 = fexp(-Ti * i3, mt), e1 = fexp(-Ti * i1, mt);
                     tr_Fc = (1.0 - a) * e3 + a * e1;
                     tr_dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1);
                     if (__ldg(&t->hasT2) != 0.0) {
-                        const double T2 = __ldg(&t->T2), e2 = exp(-T2 * invT);
+                        const double T2 = __ldg(&t->T2), e2 = fexp(-T2 * invT, mt);
                         tr_Fc += e2;
                         tr_dFc = fma(T2 * invT * invT, e2, tr_dFc);
                     }
-                    const double lFc = log(tr_Fc) * kInvLn10;
-                    const double c = -0.4 - 0.67 * lFc;
-                    tr_nn = 0.75 - 1.27 * lFc;
+                    const double lFc = flog(tr_Fc, mt) * kInvLn10;
+                    const double c = fma(-0.67, lFc, -0.4);
+                    tr_nn = fma(-1.27, lFc, 0.75);
                     tr_u = fma(lnPr, kInvLn10, c);
                     tr_v = fma(-0.14, tr_u, tr_nn);
                     tr_f1 = tr_u / tr_v;
                     tr_den = fma(tr_f1, tr_f1, 1.0);
                     tr_lF = lFc / tr_den;
-                    tr_g = 1.0 / (1.0 + exp(-lnPr));
-                    kf = exp(lnkf) * tr_g * exp(tr_lF * kLn10);
+                    tr_g = 1.0 / (1.0 + fexp(-lnPr, mt));
+                    kf = fexp(lnkf, mt) * tr_g * fexp(tr_lF * kLn10, mt);
                 }
             } else {
-                kf = exp(lnkf);
+                kf = fexp(lnkf, mt);
             }
-            const double E = exp(-lnKc);
+            const double E = fexp(-lnKc, mt);
             const double kr = kf * E;
             const double qc = fma(kf, fw, -kr * rv);
             const double q = (type == NK_RXN_THIRD_BODY) ? qc * M : qc;
 
             // ---- adjoint
-            const double qbar = fma(-hbRT, sumh, wsum);           // sum nu (bar_omega - bar_hrr h)
-            Tbar = fma(-hb * kR * q, sumcp, Tbar);
+            const double qbar = hb_any ? fma(-hbRT, sumh, wsum) : wsum;   // sum nu (bar_omega - bar_hrr h)
+            if (hb_any) Tbar = fma(-hb * kR * q, sumcp, Tbar);
             if (WANT_G) {
                 double gl = valid ? qbar * q : 0.0;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) gl += __shfl_xor_sync(0xffffffffu, gl, o);
-                if (lane == 0) gw[r] += gl;
+                if (lane == 0) gw[orig] += gl;
             }
             double Mbar = 0.0, qcbar = qbar;
             if (type == NK_RXN_THIRD_BODY) {
@@ -190,24 +226,21 @@ __global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t
             for (int e = 0; e < kMaxSide; ++e) {
                 if (e < nr) {
                     const int nu = __ldg(&rec->nu[e]);
-                    double d = (double)nu * ipow(cR[e], nu - 1 > 0 ? nu - 1 : 1);
-                    if (nu == 1) d = 1.0;
-#pragma unroll
-                    for (int f = 0; f < kMaxSide; ++f)
-                        if (f != e && f < nr) d *= pR[f];
+                    double d = exR[e];                           // d fw / d C_e = nu C_e^(nu-1) prod_{f!=e}
+                    if (nu > 1) {
+                        d *= -__ldg(&rec->nud[e]);
+                        for (int j = 1; j < nu; ++j) d *= cR[e];
+                    }
                     const int k = __ldg(&rec->sp[e]);
                     sB[k * BLK] = fma(fwbar, d, sB[k * BLK]);
                 }
-            }
-#pragma unroll
-            for (int e = 0; e < kMaxSide; ++e) {
                 if (e < np) {
                     const int nu = __ldg(&rec->nu[kMaxSide + e]);
-                    double d = (double)nu * ipow(cP[e], nu - 1 > 0 ? nu - 1 : 1);
-                    if (nu == 1) d = 1.0;
-#pragma unroll
-                    for (int f = 0; f < kMaxSide; ++f)
-                        if (f != e && f < np) d *= pP[f];
+                    double d = exP[e];
+                    if (nu > 1) {
+                        d *= __ldg(&rec->nud[kMaxSide + e]);
+                        for (int j = 1; j < nu; ++j) d *= cP[e];
+                    }
                     const int k = __ldg(&rec->sp[kMaxSide + e]);
                     sB[k * BLK] = fma(rvbar, d, sB[k * BLK]);
                 }
@@ -232,7 +265,7 @@ __global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t
             }
             if (type != NK_RXN_ELEMENTARY && Mbar != 0.0) {
                 Tbar = fma(-Mbar * pRT, invT, Tbar);             // sum_k C_k = p/(RT)
-                const int e0 = __ldg(m.eff_ptr + r), e1 = __ldg(m.eff_ptr + r + 1);
+                const int e0 = __ldg(&rec->eff0), e1 = __ldg(&rec->eff1);
                 for (int j = e0; j < e1; ++j) {
                     const int k = __ldg(m.eff_sp + j);
                     sB[k * BLK] = fma(Mbar, __ldg(m.eff_m1 + j), sB[k * BLK]);
@@ -255,7 +288,7 @@ __global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t
 
     if (WANT_G) {
         __syncthreads();
-        const double* g0 = smem + (size_t)5 * K * BLK;
+        const double* g0 = smem + (size_t)5 * K * BLK;   // per-warp sums, indexed by caller order
         for (int r = tid; r < R; r += BLK) {
             double acc = 0.0;
             for (int w = 0; w < BLK / 32; ++w) acc += g0[(size_t)w * R + r];
@@ -276,7 +309,8 @@ template <int BLK>
 cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
                      const double* dlnA, const double* bar_omega, const double* bar_hrr, double* gT, double* gY,
                      double* g_lnA, void* ws, cudaStream_t s) {
-    const size_t smem = (size_t)5 * m.K * BLK * sizeof(double) + (g_lnA ? (size_t)(BLK / 32) * m.R * sizeof(double) : 0);
+    const size_t smem = kMathTabDoubles * sizeof(double) + (size_t)5 * m.K * BLK * sizeof(double) +
+                        (g_lnA ? (size_t)(BLK / 32) * m.R * sizeof(double) : 0);
     const int64_t need = (n + BLK - 1) / BLK;
     cudaError_t e;
     if (g_lnA) {

@@ -93,6 +93,25 @@ int pick_block(size_t bytes_per_thread, size_t budget) {
     return 0;
 }
 
+int pick_block_occupancy(size_t bytes_per_thread, size_t fixed_bytes, size_t bytes_per_warp) {
+    int dev = 0, per_sm = 0, per_block = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int best = 0, best_threads = 0;
+    for (int b : {128, 64, 32}) {
+        const size_t blk_bytes = bytes_per_thread * (size_t)b + fixed_bytes + bytes_per_warp * (size_t)(b / 32);
+        if (blk_bytes > (size_t)per_block) continue;
+        const int blocks = (int)((size_t)per_sm / (blk_bytes + 1024));   // 1 KB reserved per block
+        const int threads = blocks * b;
+        if (threads > best_threads) {
+            best_threads = threads;
+            best = b;
+        }
+    }
+    return best;
+}
+
 namespace {
 struct SmemEntry {
     const void* kernel;
@@ -159,36 +178,50 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
             c[14] = -a[4] / 20.0;
         }
     }
+    // device order of the reactions: elementary, then third-body, then Troe (stable)
+    std::vector<int> order;
+    for (int kind = 0; kind < 3; ++kind)
+        for (int r = 0; r < R; ++r)
+            if (d->rtype[r] == kind) order.push_back(r);
+    int R_el = 0, R_tb = 0;
+    for (int r = 0; r < R; ++r) {
+        R_el += d->rtype[r] == NK_RXN_ELEMENTARY;
+        R_tb += d->rtype[r] == NK_RXN_THIRD_BODY;
+    }
     std::vector<nk::RxnRec> rxn(R);
     std::vector<nk::RxnRecF> rxnf(R);
     std::vector<nk::TroeRec> troe;
     std::vector<nk::TroeRecF> troef;
-    std::vector<int32_t> eff_ptr(R + 1, 0), eff_sp;
+    std::vector<int32_t> eff_sp;
     std::vector<double> eff_m1;
-    for (int r = 0; r < R; ++r) {
-        nk::RxnRec& x = rxn[r];
+    for (int q = 0; q < R; ++q) {
+        const int r = order[q];
+        nk::RxnRec& x = rxn[q];
         std::memset(&x, 0, sizeof x);
         x.lnA = d->lnA[r];
         x.beta = d->beta[r];
         x.EaR = d->Ea[r] / nk::kR;
         x.type = d->rtype[r];
+        x.orig = r;
         x.nr = d->reac_ptr[r + 1] - d->reac_ptr[r];
         x.np = d->prod_ptr[r + 1] - d->prod_ptr[r];
         int dnu = 0, e = 0;
         for (int i = d->reac_ptr[r]; i < d->reac_ptr[r + 1]; ++i, ++e) {
             x.sp[e] = d->reac_sp[i];
             x.nu[e] = d->reac_nu[i];
+            x.nud[e] = -(double)d->reac_nu[i];
             dnu -= d->reac_nu[i];
         }
         e = nk::kMaxSide;
         for (int i = d->prod_ptr[r]; i < d->prod_ptr[r + 1]; ++i, ++e) {
             x.sp[e] = d->prod_sp[i];
             x.nu[e] = d->prod_nu[i];
+            x.nud[e] = (double)d->prod_nu[i];
             dnu += d->prod_nu[i];
         }
         x.dnu = (double)dnu;
         x.aux = -1;
-        rxnf[r] = nk::RxnRecF{(float)x.lnA, (float)x.beta, (float)x.EaR, 0.0f};
+        rxnf[q] = nk::RxnRecF{(float)x.lnA, (float)x.beta, (float)x.EaR, 0.0f};
         if (x.type == NK_RXN_TROE) {
             const double* t = d->troe + 4 * r;
             if (!(t[1] > 0.0) || !(t[2] > 0.0))
@@ -207,6 +240,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
             troef.push_back(nk::TroeRecF{(float)tr.lnA0, (float)tr.beta0, (float)tr.Ea0R, (float)tr.a,
                                          (float)tr.invT3, (float)tr.invT1, (float)tr.T2, (float)tr.hasT2});
         }
+        x.eff0 = (int32_t)eff_sp.size();
         if (x.type != NK_RXN_ELEMENTARY) {
             for (int k = 0; k < K; ++k) {
                 const double eps = d->eff[(size_t)r * K + k];
@@ -216,7 +250,16 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                 }
             }
         }
-        eff_ptr[r + 1] = (int32_t)eff_sp.size();
+        x.eff1 = (int32_t)eff_sp.size();
+    }
+    // exp/log tables (nk_math.cuh), from their definitions in extended precision
+    std::vector<double> mtab(nk::kMathTabDoubles);
+    for (int j = 0; j < nk::kExpTab; ++j) mtab[j] = (double)exp2l((long double)j / nk::kExpTab);
+    for (int j = 0; j < nk::kLogTab; ++j) {
+        const long double c = 1.0L + ((long double)j + 0.5L) / nk::kLogTab;
+        const double rc = (double)(1.0L / c);
+        mtab[nk::kExpTab + j] = rc;
+        mtab[nk::kExpTab + nk::kLogTab + j] = (double)(-logl((long double)rc));
     }
     std::vector<double> wilkeA((size_t)K * K), qrtW(K), sqrtW(K);
     for (int k = 0; k < K; ++k) {
@@ -224,6 +267,32 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
         sqrtW[k] = std::sqrt(d->W[k]);
         for (int j = 0; j < K; ++j) wilkeA[(size_t)k * K + j] = 1.0 / std::sqrt(8.0 * (1.0 + d->W[k] / d->W[j]));
     }
+    // double-float tables: cubic fits re-expanded about ln T = kLnT0, split into float pairs
+    auto split = [](long double v) {
+        const float h = (float)v;
+        return float2{h, (float)(v - (long double)h)};
+    };
+    auto reexpand = [&](const double* a, float2* out) {   // b_i = sum_{m>=i} a_m C(m,i) L0^(m-i)
+        static const int C[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+        for (int i = 0; i < 4; ++i) {
+            long double b = 0.0L;
+            for (int m2 = i; m2 < 4; ++m2) b += (long double)a[m2] * C[m2][i] * powl((long double)nk::kLnT0, m2 - i);
+            out[i] = split(b);
+        }
+    };
+    std::vector<float2> df_mu((size_t)K * 4), df_lam((size_t)K * 4), df_D((size_t)P * 4 + 4), df_A((size_t)K * K),
+        df_qlnW(K), df_sqrtW(K), df_exp(nk::kExpTab);
+    for (int k = 0; k < K; ++k) {
+        reexpand(d->mu_fit + 4 * k, df_mu.data() + 4 * k);
+        reexpand(d->lam_fit + 4 * k, df_lam.data() + 4 * k);
+        df_qlnW[k] = split(0.25L * logl((long double)d->W[k]));
+        df_sqrtW[k] = split(sqrtl((long double)d->W[k]));
+        for (int j = 0; j < K; ++j)
+            df_A[(size_t)k * K + j] = split(1.0L / sqrtl(8.0L * (1.0L + (long double)d->W[k] / d->W[j])));
+    }
+    for (int q = 0; q < P; ++q) reexpand(d->D_fit + 4 * q, df_D.data() + 4 * q);
+    for (int j = 0; j < nk::kExpTab; ++j) df_exp[j] = split(exp2l((long double)j / nk::kExpTab));
+
     auto to_f = [](const double* s, size_t n) {
         std::vector<float> v(n);
         for (size_t i = 0; i < n; ++i) v[i] = (float)s[i];
@@ -238,12 +307,15 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     const size_t o_invW = L.add(K * 8), o_Tmid = L.add(K * 8), o_nasa = L.add(nasa.size() * 8),
                  o_rxn = L.add(R * sizeof(nk::RxnRec)), o_rxnf = L.add(R * sizeof(nk::RxnRecF)),
                  o_troe = L.add(troe.size() * sizeof(nk::TroeRec) + 16),
-                 o_troef = L.add(troef.size() * sizeof(nk::TroeRecF) + 16), o_effp = L.add((R + 1) * 4),
+                 o_troef = L.add(troef.size() * sizeof(nk::TroeRecF) + 16), o_mtab = L.add(mtab.size() * 8),
                  o_effs = L.add(eff_sp.size() * 4 + 16), o_effv = L.add(eff_m1.size() * 8 + 16),
                  o_mu = L.add(K * 32), o_lam = L.add(K * 32), o_D = L.add((size_t)P * 32 + 16),
                  o_A = L.add((size_t)K * K * 8), o_q = L.add(K * 8), o_s = L.add(K * 8),
                  o_fmu = L.add(K * 16), o_flam = L.add(K * 16), o_fD = L.add((size_t)P * 16 + 16),
-                 o_fA = L.add((size_t)K * K * 4), o_fq = L.add(K * 4), o_fs = L.add(K * 4), o_fiw = L.add(K * 4);
+                 o_fA = L.add((size_t)K * K * 4), o_fq = L.add(K * 4), o_fs = L.add(K * 4), o_fiw = L.add(K * 4),
+                 o_dmu = L.add(df_mu.size() * 8), o_dlam = L.add(df_lam.size() * 8), o_dD = L.add(df_D.size() * 8),
+                 o_dA = L.add(df_A.size() * 8), o_dq = L.add(df_qlnW.size() * 8), o_ds = L.add(df_sqrtW.size() * 8),
+                 o_dexp = L.add(df_exp.size() * 8);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -255,7 +327,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_rxnf, rxnf.data(), R * sizeof(nk::RxnRecF));
     put(o_troe, troe.data(), troe.size() * sizeof(nk::TroeRec));
     put(o_troef, troef.data(), troef.size() * sizeof(nk::TroeRecF));
-    put(o_effp, eff_ptr.data(), (R + 1) * 4);
+    put(o_mtab, mtab.data(), mtab.size() * 8);
     put(o_effs, eff_sp.data(), eff_sp.size() * 4);
     put(o_effv, eff_m1.data(), eff_m1.size() * 8);
     put(o_mu, d->mu_fit, K * 32);
@@ -271,6 +343,13 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_fq, f_q.data(), K * 4);
     put(o_fs, f_s.data(), K * 4);
     put(o_fiw, f_iw.data(), K * 4);
+    put(o_dmu, df_mu.data(), df_mu.size() * 8);
+    put(o_dlam, df_lam.data(), df_lam.size() * 8);
+    put(o_dD, df_D.data(), df_D.size() * 8);
+    put(o_dA, df_A.data(), df_A.size() * 8);
+    put(o_dq, df_qlnW.data(), df_qlnW.size() * 8);
+    put(o_ds, df_sqrtW.data(), df_sqrtW.size() * 8);
+    put(o_dexp, df_exp.data(), df_exp.size() * 8);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -297,7 +376,9 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.R = R;
     dm.P = P;
     dm.n_troe = (int32_t)troe.size();
-    dm.n_eff_rows = R;
+    dm.R_el = R_el;
+    dm.R_tb = R_tb;
+    dm.mtab = reinterpret_cast<const double*>(b + o_mtab);
     dm.p_ref = d->p_ref;
     dm.invW = reinterpret_cast<const double*>(b + o_invW);
     dm.Tmid = reinterpret_cast<const double*>(b + o_Tmid);
@@ -306,7 +387,6 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.rxnf = reinterpret_cast<const nk::RxnRecF*>(b + o_rxnf);
     dm.troe = reinterpret_cast<const nk::TroeRec*>(b + o_troe);
     dm.troef = reinterpret_cast<const nk::TroeRecF*>(b + o_troef);
-    dm.eff_ptr = reinterpret_cast<const int32_t*>(b + o_effp);
     dm.eff_sp = reinterpret_cast<const int32_t*>(b + o_effs);
     dm.eff_m1 = reinterpret_cast<const double*>(b + o_effv);
     dm.mu_fit = reinterpret_cast<const double*>(b + o_mu);
@@ -322,6 +402,13 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.f_qrtW = reinterpret_cast<const float*>(b + o_fq);
     dm.f_sqrtW = reinterpret_cast<const float*>(b + o_fs);
     dm.f_invW = reinterpret_cast<const float*>(b + o_fiw);
+    dm.df_mu_fit = reinterpret_cast<const float2*>(b + o_dmu);
+    dm.df_lam_fit = reinterpret_cast<const float2*>(b + o_dlam);
+    dm.df_D_fit = reinterpret_cast<const float2*>(b + o_dD);
+    dm.df_wilkeA = reinterpret_cast<const float2*>(b + o_dA);
+    dm.df_qlnW = reinterpret_cast<const float2*>(b + o_dq);
+    dm.df_sqrtW = reinterpret_cast<const float2*>(b + o_ds);
+    dm.df_exp_tab = reinterpret_cast<const float2*>(b + o_dexp);
     *out = m;
     return ok();
 }
@@ -401,7 +488,8 @@ nk_status nk_rates_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T
     bool skip;
     nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
     if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
-    if (precision != NK_FP64 && precision != NK_MIXED) return fail(NK_EINVAL, "bad precision %d", (int)precision);
+    if (precision != NK_FP64 && precision != NK_MIXED && precision != NK_FP64_NATIVE)
+        return fail(NK_EINVAL, "bad precision %d", (int)precision);
     if (!omega || !hrr) return fail(NK_EINVAL, "omega and hrr must not be NULL");
     if ((st = check_out({omega, hrr, dlnA})) != NK_OK) return st;
     return launched(nk::launch_rates(m->d, n, ld, T, p, Y, dlnA, omega, hrr, (int)precision, (cudaStream_t)stream),
@@ -414,9 +502,13 @@ nk_status nk_transport_eval(const nk_mech* m, int64_t n, int64_t ld, const doubl
     bool skip;
     nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
     if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
-    if (precision != NK_FP64 && precision != NK_MIXED) return fail(NK_EINVAL, "bad precision %d", (int)precision);
+    if (precision != NK_FP64 && precision != NK_MIXED && precision != NK_FP64_NATIVE)
+        return fail(NK_EINVAL, "bad precision %d", (int)precision);
     if ((st = check_out({mu, lambda, Dmix})) != NK_OK) return st;
     if (!mu && !lambda && !Dmix) return ok();
+    if (precision == NK_FP64)
+        return launched(nk::launch_transport_df(m->d, n, ld, T, p, Y, mu, lambda, Dmix, (cudaStream_t)stream),
+                        "transport kernel launch");
     return launched(nk::launch_transport(m->d, n, ld, T, p, Y, mu, lambda, Dmix, (int)precision,
                                          (cudaStream_t)stream),
                     "transport kernel launch");

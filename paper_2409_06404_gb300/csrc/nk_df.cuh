@@ -1,0 +1,113 @@
+// Double-float ("f32x2") arithmetic on the FP32 pipe.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, carrying 48
+// significand bits (relative rounding ~2^-46 per operation for the add/multiply below).
+// On GB300 the FP32 pipe retires ~58x more operations per clock than the FP64 pipe, so sums
+// of positive, bounded terms -- the transport pair sums -- are evaluated here at FP64-class
+// accuracy.  The error-free transformations are the classical ones: Knuth's two-sum,
+// Dekker's fast two-sum (|a| >= |b|), and the FMA two-product (exact product a*b = p + e).
+// Every step uses round-to-nearest intrinsics so the compiler cannot contract or reorder
+// the compensation terms.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace nk {
+
+struct dfl {
+    float h, l;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {   // requires |a| >= |b| (or a == 0)
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_split(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ double df_value(dfl a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+    dfl s = two_sum(x.h, y.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
+    return fast_two_sum(s.h, s.l);
+}
+
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return fast_two_sum(p, e);
+}
+
+// s + a * x
+__device__ __forceinline__ dfl df_fma(dfl a, dfl x, dfl s) {
+    const float p = __fmul_rn(a.h, x.h);
+    float e = __fmaf_rn(a.h, x.h, -p);
+    e = __fmaf_rn(a.h, x.l, __fmaf_rn(a.l, x.h, e));
+    dfl u = two_sum(s.h, p);
+    u.l = __fadd_rn(u.l, __fadd_rn(e, s.l));
+    return fast_two_sum(u.h, u.l);
+}
+
+// x / y (y > 0): quotient of the high parts, corrected once by the pair residual
+__device__ __forceinline__ dfl df_div(dfl x, dfl y) {
+    const float q1 = __fdiv_rn(x.h, y.h);
+    const float p = __fmul_rn(q1, y.h);
+    float e = __fmaf_rn(q1, y.h, -p);
+    e = __fmaf_rn(q1, y.l, e);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.h, p), e), x.l);
+    return fast_two_sum(q1, __fdiv_rn(r, y.h));
+}
+
+// a * 2^m for |m| <= 126 (exact)
+__device__ __forceinline__ dfl df_ldexp(dfl a, int m) {
+    const float s = __int_as_float((m + 127) << 23);
+    return {__fmul_rn(a.h, s), __fmul_rn(a.l, s)};
+}
+
+// exp(x) for a double-float x with |x| <= 22, by Tang's table-driven method in pairs:
+//   x = (128 m + j) ln2/128 + r, |r| <= ln2/256, ln2/128 split into three floats (the first
+//   with 12 significant bits, so N * C1 is exact for |N| < 2^12);
+//   exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24 with r and r^2/2 carried in pairs and the two
+//   small terms in float; result 2^m * T_j * (1 + (exp(r) - 1)), T_j = 2^(j/128) as a pair.
+//   Relative error <= 3.2e-14 on [-22, 22] (checked against 200-bit exp).
+__device__ __forceinline__ dfl df_exp(dfl x, const float2* tab) {
+    constexpr float kInvC = 184.6649652337873f;          // 128 / ln2
+    constexpr float C1 = 5.4149627685546875e-03f;        // ln2/128, 12 significant bits
+    constexpr float C2 = 2.495795570212067e-07f;         // next 24 bits
+    constexpr float C3 = 1.2864023201156725e-14f;        // remainder
+    const float Nf = rintf(x.h * kInvC);
+    const int N = (int)Nf;
+    const float rh = __fmaf_rn(-Nf, C1, x.h);            // exact
+    const float p2 = __fmul_rn(-Nf, C2);
+    const float p2e = __fmaf_rn(-Nf, C2, -p2);
+    dfl r = two_sum(rh, p2);
+    r.l = __fadd_rn(r.l, __fadd_rn(__fadd_rn(x.l, p2e), __fmul_rn(-Nf, C3)));
+    r = fast_two_sum(r.h, r.l);
+    // r^2/2 as a pair, then the float tail
+    const float q = __fmul_rn(r.h, r.h);
+    float qe = __fmaf_rn(r.h, r.h, -q);
+    qe = __fmaf_rn(2.0f * r.h, r.l, qe);
+    const float tail = __fmul_rn(__fmul_rn(q, r.h), __fmaf_rn(r.h, 1.0f / 24.0f, 1.0f / 6.0f));
+    dfl em1 = two_sum(r.h, 0.5f * q);
+    em1.l = __fadd_rn(em1.l, __fadd_rn(r.l, __fmaf_rn(0.5f, qe, tail)));
+    em1 = fast_two_sum(em1.h, em1.l);
+    const float2 t = tab[N & 127];
+    const dfl tj{t.x, t.y};
+    const dfl v = df_fma(tj, em1, tj);
+    return df_ldexp(v, N >> 7);
+}
+
+}  // namespace nk

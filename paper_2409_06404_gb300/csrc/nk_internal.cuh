@@ -7,6 +7,8 @@
 #include <stdint.h>
 
 #include "nkchem.h"
+#include "nk_math.cuh"
+#include "nk_df.cuh"
 
 namespace nk {
 
@@ -23,18 +25,28 @@ constexpr int kMaxSide = 4;                 // reactant / product entries per re
 constexpr int kMaxNu = 8;
 
 // One reaction, read by every thread of a warp at the same address (a broadcast load).
+// The device copy orders reactions by kind (elementary, third-body, Troe) so that each kind
+// runs in its own branch-free loop; `orig` is the caller's reaction index (for ln A shifts
+// and the ln A gradient).
 struct __align__(16) RxnRec {
     double lnA;        // ln A (high-pressure limit for Troe)
     double beta;
     double EaR;        // Ea / R, kelvin
     double dnu;        // sum of net stoichiometric coefficients (products - reactants)
+    double nud[2 * kMaxSide];   // signed coefficients of the entries as doubles: -nu for
+                                // reactants, +nu for products (no int-to-double conversion,
+                                // which runs on the FP64 pipe)
     int32_t type;      // NK_RXN_*
     int32_t nr, np;    // reactant / product entry counts
     int32_t aux;       // Troe record index (type 2), else -1
+    int32_t orig;      // index of the reaction in the caller's description
+    int32_t eff0, eff1;// third-body efficiencies != 1 in [eff0, eff1) of eff_sp / eff_m1
+    int32_t pad;
     int32_t sp[2 * kMaxSide];   // species of entries: reactants at [0, nr),
                                 // products at [kMaxSide, kMaxSide + np)
     int32_t nu[2 * kMaxSide];   // stoichiometric coefficients of the entries
 };
+static_assert(sizeof(RxnRec) == 192, "reaction record layout");
 
 // Single-precision copy of the Arrhenius data for the mixed form.
 struct __align__(16) RxnRecF {
@@ -59,8 +71,11 @@ constexpr int kNasaStride = 16;   // per range; species k: [k][2][16] (low, high
 // Device view of a loaded mechanism (passed by value to every kernel).
 struct DevMech {
     int32_t K, R, P;              // species, reactions, species pairs K(K-1)/2
-    int32_t n_troe, n_eff_rows;
+    int32_t n_troe;
+    int32_t R_el, R_tb;           // reactions [0, R_el) elementary, [R_el, R_el+R_tb) third-body,
+                                  // [R_el+R_tb, R) Troe (device order)
     double p_ref;
+    const double* mtab;           // exp/log tables (kMathTabDoubles, see nk_math.cuh)
     const double* invW;           // [K] 1/W
     const double* Tmid;           // [K]
     const double* nasa;           // [K][2][16]
@@ -68,9 +83,8 @@ struct DevMech {
     const RxnRecF* rxnf;          // [R]
     const TroeRec* troe;          // [n_troe]
     const TroeRecF* troef;        // [n_troe]
-    const int32_t* eff_ptr;       // [R + 1] third-body efficiencies of reaction r, sparse:
-    const int32_t* eff_sp;        //   species with eps != 1 in [eff_ptr[r], eff_ptr[r+1])
-    const double* eff_m1;         //   eps - 1 (all other species have eps = 1)
+    const int32_t* eff_sp;        // third-body efficiencies != 1, ranges given by RxnRec::eff0/eff1:
+    const double* eff_m1;         //   species and eps - 1 (all other species have eps = 1)
     // transport
     const double* mu_fit;         // [K][4]
     const double* lam_fit;        // [K][4]
@@ -85,7 +99,18 @@ struct DevMech {
     const float* f_qrtW;
     const float* f_sqrtW;
     const float* f_invW;
+    // double-float tables of the FP64 transport kernel: fits re-expanded in u = ln T - kLnT0
+    const float2* df_mu_fit;      // [K][4]
+    const float2* df_lam_fit;     // [K][4]
+    const float2* df_D_fit;       // [P][4]
+    const float2* df_wilkeA;      // [K][K]
+    const float2* df_qlnW;        // [K] ln(W)/4
+    const float2* df_sqrtW;       // [K]
+    const float2* df_exp_tab;     // [128] 2^(j/128)
 };
+
+// Centre of the re-expanded transport fits (ln T about 1100 K).
+constexpr double kLnT0 = 7.0;
 
 }  // namespace nk
 
@@ -110,6 +135,9 @@ cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* 
 cudaError_t launch_transport(const DevMech& m, int64_t n, int64_t ld, const double* T,
                              const double* p, const double* Y, double* mu, double* lam,
                              double* Dmix, int precision, cudaStream_t s);
+cudaError_t launch_transport_df(const DevMech& m, int64_t n, int64_t ld, const double* T,
+                                const double* p, const double* Y, double* mu, double* lam,
+                                double* Dmix, cudaStream_t s);
 cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* vT, const double* vY,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s);
@@ -127,6 +155,10 @@ cudaError_t noalloc_scratch(void** ptr);
 // Largest block size in {128, 64, 32} whose per-thread shared-memory scratch
 // (bytes_per_thread * block) stays within the budget; 0 if none fits.
 int pick_block(size_t bytes_per_thread, size_t budget);
+// Block size in {128, 64, 32} that maximises resident threads per SM for a kernel using
+// bytes_per_thread of shared memory per thread, fixed_bytes per block and bytes_per_warp per
+// warp; 0 if none fits.
+int pick_block_occupancy(size_t bytes_per_thread, size_t fixed_bytes, size_t bytes_per_warp = 0);
 // Opt a kernel into `bytes` of dynamic shared memory on the current device (cached).
 cudaError_t ensure_smem(const void* kernel, size_t bytes);
 // Opt-in shared-memory limit per block of the current device.

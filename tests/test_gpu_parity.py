@@ -53,38 +53,46 @@ def _thermo_err(mech, m, T, p, Y):
     }
 
 
-def test_h2_9sp_full_workload_fp64(cuda):
+FP64_FORMS = ["fp64", "fp64_native"]
+
+
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_h2_9sp_full_workload_fp64(cuda, form):
     """9 species / 21 reactions, 64 elements x 512 GLL points (all 32,768 points)."""
     mech = synth.mechanism("h2_9sp_21rx")
     m = gpu_mechanism("h2_9sp_21rx")
     st = synth.workload_states("uniform_64el", mech.K)
-    ew, eh = _rates_err(mech, m, st.T, st.p, st.Y)
+    ew, eh = _rates_err(mech, m, st.T, st.p, st.Y, precision=form)
     assert ew <= TOL64 and eh <= TOL64, (ew, eh)
-    assert max(_transport_err(mech, m, st.T, st.p, st.Y)) <= TOL64
+    et = _transport_err(mech, m, st.T, st.p, st.Y, precision=form)
+    print(f"\n{form}: omega {ew:.1e} hrr {eh:.1e} mu/lambda/D {et[0]:.1e} {et[1]:.1e} {et[2]:.1e}")
+    assert max(et) <= TOL64
     e = _thermo_err(mech, m, st.T, st.p, st.Y)
     assert max(e.values()) <= TOL64, e
 
 
+@pytest.mark.parametrize("form", FP64_FORMS)
 @pytest.mark.parametrize("n", [1, 31, 129, 4096 + 77])
-def test_53sp_tiles_and_ragged_tail_fp64(cuda, n):
+def test_53sp_tiles_and_ragged_tail_fp64(cuda, n, form):
     mech = synth.mechanism("ch4_53sp_325rx")
     m = gpu_mechanism("ch4_53sp_325rx")
     st = synth.states_flame(mech.K, 27, seed=99)          # 3^3 elements: every T regime
     idx = np.linspace(0, st.n - 1, n).astype(int)
     T, p, Y = st.T[idx], st.p[idx], np.ascontiguousarray(st.Y[:, idx])
-    ew, eh = _rates_err(mech, m, T, p, Y)
+    ew, eh = _rates_err(mech, m, T, p, Y, precision=form)
     assert ew <= TOL64 and eh <= TOL64, (ew, eh)
-    assert max(_transport_err(mech, m, T, p, Y)) <= TOL64
+    assert max(_transport_err(mech, m, T, p, Y, precision=form)) <= TOL64
     assert max(_thermo_err(mech, m, T, p, Y).values()) <= TOL64
 
 
-def test_120sp_fp64(cuda):
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_120sp_fp64(cuda, form):
     mech = synth.mechanism("big_120sp_700rx")
     m = gpu_mechanism("big_120sp_700rx")
     st = synth.states_uniform(mech.K, 2048 + 13, seed=120, T_lo=300, T_hi=3400, alpha=0.3)
-    ew, eh = _rates_err(mech, m, st.T, st.p, st.Y)
+    ew, eh = _rates_err(mech, m, st.T, st.p, st.Y, precision=form)
     assert ew <= TOL64 and eh <= TOL64, (ew, eh)
-    assert max(_transport_err(mech, m, st.T, st.p, st.Y)) <= TOL64
+    assert max(_transport_err(mech, m, st.T, st.p, st.Y, precision=form)) <= TOL64
 
 
 def test_lnA_shift(cuda):
@@ -96,7 +104,8 @@ def test_lnA_shift(cuda):
     assert ew <= TOL64 and eh <= TOL64
 
 
-def test_edge_states(cuda):
+@pytest.mark.parametrize("form", FP64_FORMS)
+def test_edge_states(cuda, form):
     mech = synth.mechanism("h2_9sp_21rx")
     m = gpu_mechanism("h2_9sp_21rx")
     K = mech.K
@@ -134,9 +143,9 @@ def test_edge_states(cuda):
     Y = np.stack(cols, axis=1)
     T = np.array(Ts)
     p = np.array(ps)
-    ew, eh = _rates_err(mech, m, T, p, Y)
+    ew, eh = _rates_err(mech, m, T, p, Y, precision=form)
     assert ew <= TOL64 and eh <= TOL64, (ew, eh)
-    assert max(_transport_err(mech, m, T, p, Y)) <= TOL64
+    assert max(_transport_err(mech, m, T, p, Y, precision=form)) <= TOL64
     assert max(_thermo_err(mech, m, T, p, Y).values()) <= TOL64
 
 
@@ -214,6 +223,11 @@ def test_full_size_flame_workload_sampled(cuda):
     T, p, Y = to_dev(st.T, st.p, st.Y)
     w, h = nk.rates_eval(m, T, p, Y)
     mu, lam, D = nk.transport_eval(m, T, p, Y)
+    mu2, lam2, D2 = nk.transport_eval(m, T, p, Y, precision="fp64_native")
+    # the two FP64 transport forms agree everywhere, not only on the sample
+    assert scaled_err(host(mu), host(mu2), host(mu2)) <= TOL64
+    assert scaled_err(host(lam), host(lam2), host(lam2)) <= TOL64
+    assert scaled_err(host(D), host(D2), host(D2)) <= TOL64
     rng = np.random.default_rng(0)
     idx = np.unique(np.concatenate([[0, st.n - 1], rng.choice(st.n, 1500, replace=False)]))
     Ys = np.ascontiguousarray(st.Y[:, idx])
