@@ -8,16 +8,41 @@
 // two independent dependency chains per warp.  The per-point species state (C_k, g_k/RT and
 // the omega_k accumulators) lives in shared memory as [species][thread].
 //
-// FP64 form: every operation in double precision (exp/log from nk_math.cuh).
-// Mixed form: the Arrhenius argument ln A + beta ln T - Ea/(RT), k_f and the whole Troe
-// falloff in single precision; equilibrium constants (the sum of nu_k g_k/RT and its
-// exponential), the forward-minus-reverse difference and the omega accumulation in double.
+// Three arithmetic forms (template PREC):
+//  kNative (NK_FP64_NATIVE): every operation in double (exp/log from nk_math.cuh).
+//  kDF (NK_FP64): the exponent chains -- g_k/RT, the Gibbs sums, ln k_f, ln K_c, the Troe
+//    falloff -- in double-float pairs on the FP32 pipe (nk_df.cuh), each exponential
+//    returned as a double with one FP64 add; concentrations and their products, the
+//    forward-minus-reverse difference and the omega accumulation stay in double.  Results
+//    match the double-precision definition to ~1e-12 (the pairs carry 48 bits).
+//  kMixed (NK_MIXED): the Arrhenius argument ln A + beta ln T - Ea/(RT), k_f and the whole
+//    Troe falloff in single precision; equilibrium constants (the sum of nu_k g_k/RT and its
+//    exponential), the forward-minus-reverse difference and the omega accumulation in double.
 #include "nk_internal.cuh"
 
 namespace nk {
 namespace {
 
 constexpr double kLnP0overR = 9.408091968961747;   // ln(101325 Pa / (8.314462618 J/mol/K))
+
+enum { kNative = 0, kMixed = 1, kDF = 2 };
+
+// double constants of the definitions as float pairs (hi = nearest float, lo = remainder)
+__device__ __forceinline__ dfl dfc_lnp0r() { return {9.40809154510498f, 4.2385676124467864e-07f}; }
+__device__ __forceinline__ dfl dfc_invln10() { return {0.4342944920063019f, -1.0103049952192578e-08f}; }
+__device__ __forceinline__ dfl dfc_ln10() { return {2.3025851249694824f, -3.1975435632602967e-08f}; }
+__device__ __forceinline__ dfl dfc_m0_4() { return {-0.4000000059604645f, 5.9604645663569045e-09f}; }
+__device__ __forceinline__ dfl dfc_m0_67() { return {-0.6700000166893005f, 1.668930060816365e-08f}; }
+__device__ __forceinline__ dfl dfc_m1_27() { return {-1.2699999809265137f, -1.907348590179936e-08f}; }
+__device__ __forceinline__ dfl dfc_m0_14() { return {-0.14000000059604645f, 5.9604643443123e-10f}; }
+__device__ __forceinline__ dfl dfl_of(float2 v) { return {v.x, v.y}; }
+
+// double-float tables staged in shared memory for the kDF form
+struct DfTab {
+    const float2* e2;   // 2^(j/128)
+    const float2* rc;   // 1/c_j
+    const float2* lc;   // -log(1/c_j)
+};
 
 // exp of a single-precision argument, returned in double: x = n ln2 + r (Cody-Waite two-term
 // split of ln 2), expf(r) with |r| <= ln2/2, and 2^n added to the exponent field of the
@@ -75,6 +100,7 @@ __device__ __forceinline__ Rxn load_rxn(const RxnRec* rec) {
 struct Pt {
     double T, lnT, invT, pRT, lnP0RT;
     float Tf, lnTf, invTf;
+    dfl Td, lnTd, invTd, lnP0RTd;    // kDF form
 };
 
 // sum_k nu_k g_k/RT (products minus reactants) and the concentration products of each side;
@@ -133,8 +159,8 @@ __device__ __forceinline__ double troe_factor(const TroeRec* t, double lnkinf, d
 }
 
 // Rate of progress q of one reaction of kind KIND (0 elementary, 1 third-body, 2 Troe);
-// r is the reaction's position in the device order.
-template <int BLK, bool MIXED, int KIND>
+// r is the reaction's position in the device order.  Native and mixed forms.
+template <int BLK, int PREC, int KIND>
 __device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& x, int r, const double* sC,
                                                    const double* sG, const Pt& P, const double* dlnA,
                                                    const MathTab& mt) {
@@ -153,7 +179,7 @@ __device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& 
         for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
     }
     double kf, kr;
-    if constexpr (!MIXED) {
+    if constexpr (PREC == kNative) {
         const double lnkf = fma(-x.EaR, P.invT, fma(x.beta, P.lnT, lnA));
         if constexpr (KIND == 2) {
             const TroeRec* t = m.troe + x.aux;
@@ -196,6 +222,104 @@ __device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& 
     return q;
 }
 
+// kDF form: the Gibbs sum in pairs (g_k/RT stored as pairs in sG), products in double.
+template <int BLK>
+__device__ __forceinline__ void gibbs_products_df(const Rxn& x, const double* sC, const float2* sG, dfl& sumg,
+                                                  double& fw, double& rv) {
+    {
+        const int k = x.sp[0], nu = x.nu[0];
+        const double c = sC[k * BLK];
+        fw = c;
+        for (int j = 1; j < nu; ++j) fw *= c;
+        const dfl g = dfl_of(sG[k * BLK]);
+        sumg = nu == 1 ? df_neg(g) : df_mul_f(g, -__int2float_rn(nu));
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e) {
+        if (e < x.nr) {
+            const int k = x.sp[e], nu = x.nu[e];
+            const double c = sC[k * BLK];
+            for (int j = 0; j < nu; ++j) fw *= c;
+            const dfl g = dfl_of(sG[k * BLK]);
+            sumg = df_add(sumg, nu == 1 ? df_neg(g) : df_mul_f(g, -__int2float_rn(nu)));
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        if (e < x.np) {
+            const int k = x.sp[kMaxSide + e], nu = x.nu[kMaxSide + e];
+            const double c = sC[k * BLK];
+            if (e == 0) {
+                rv = c;
+                for (int j = 1; j < nu; ++j) rv *= c;
+            } else {
+                for (int j = 0; j < nu; ++j) rv *= c;
+            }
+            const dfl g = dfl_of(sG[k * BLK]);
+            sumg = df_add(sumg, nu == 1 ? g : df_mul_f(g, __int2float_rn(nu)));
+        }
+    }
+}
+
+// Troe factor F * P_r/(1+P_r) with the exponent arithmetic in pairs.
+__device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl lnkinf, dfl lnk0, double M,
+                                                 const Pt& P, const DfTab& dt) {
+    const TroeRec* t = m.troe + aux;
+    const float4 t1 = __ldg(m.troe_df + 3 * aux + 1);    // (Ea0/R, 1/T3)
+    const float4 t2 = __ldg(m.troe_df + 3 * aux + 2);    // (1/T1, T2)
+    const dfl lnPr = df_add(df_add(lnk0, df_neg(lnkinf)), log_df(M, dt.rc, dt.lc));
+    const double a = __ldg(&t->a);
+    double Fc = (1.0 - a) * exp_df_d(df_neg(df_mul(P.Td, dfl{t1.z, t1.w})), dt.e2) +
+                a * exp_df_d(df_neg(df_mul(P.Td, dfl{t2.x, t2.y})), dt.e2);
+    if (__ldg(&t->hasT2) != 0.0) Fc += exp_df_d(df_neg(df_mul(dfl{t2.z, t2.w}, P.invTd)), dt.e2);
+    const dfl lFc = df_mul(log_df(Fc, dt.rc, dt.lc), dfc_invln10());
+    const dfl c = df_add(dfc_m0_4(), df_mul(lFc, dfc_m0_67()));
+    const dfl nn = df_add(dfl{0.75f, 0.0f}, df_mul(lFc, dfc_m1_27()));
+    const dfl u = df_add(df_mul(lnPr, dfc_invln10()), c);
+    const dfl f1 = df_div(u, df_add(nn, df_mul(u, dfc_m0_14())));
+    const dfl lF = df_div(lFc, df_fma(f1, f1, dfl{1.0f, 0.0f}));
+    return exp_df_d(df_mul(lF, dfc_ln10()), dt.e2) / (1.0 + exp_df_d(df_neg(lnPr), dt.e2));
+}
+
+template <int BLK, int KIND>
+__device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const double* sC,
+                                                      const float2* sG, const Pt& P, const double* dlnA,
+                                                      const DfTab& dt) {
+    double fw, rv;
+    dfl sumg;
+    gibbs_products_df<BLK>(x, sC, sG, sumg, fw, rv);
+    const float4 a0 = __ldg(m.rxn_df + 2 * r), a1 = __ldg(m.rxn_df + 2 * r + 1);
+    const dfl lnKc = df_add(df_mul_f(P.lnP0RTd, a1.z), df_neg(sumg));   // ln K_c
+    dfl lnkf = df_fma(dfl{a0.z, a0.w}, P.lnTd, dfl{a0.x, a0.y});          // ln A + beta ln T
+    lnkf = df_fma(dfl{-a1.x, -a1.y}, P.invTd, lnkf);                     //   - Ea/(R T)
+    dfl shift{0.0f, 0.0f};
+    if (dlnA) {
+        shift = df_split(__ldg(dlnA + x.orig));
+        lnkf = df_add(lnkf, shift);
+    }
+    double M = 0.0;
+    if (KIND != 0) {
+        M = P.pRT;
+        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
+    }
+    double kf, kr;
+    if constexpr (KIND == 2) {
+        const float4 t0 = __ldg(m.troe_df + 3 * x.aux);          // (lnA0, beta0)
+        const float4 t1 = __ldg(m.troe_df + 3 * x.aux + 1);      // (Ea0/R, 1/T3)
+        dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.lnTd, dfl{t0.x, t0.y});
+        lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.invTd, lnk0);
+        if (dlnA) lnk0 = df_add(lnk0, shift);
+        kf = M == 0.0 ? 0.0 : exp_df_d(lnkf, dt.e2) * troe_factor_df(m, x.aux, lnkf, lnk0, M, P, dt);
+        kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+    } else {
+        kf = exp_df_d(lnkf, dt.e2);
+        kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
+    }
+    double q = fma(kf, fw, -kr * rv);
+    if (KIND == 1) q *= M;
+    return q;
+}
+
 template <int BLK>
 __device__ __forceinline__ void scatter(const Rxn& x, double* sW, double q) {
 #pragma unroll
@@ -212,50 +336,92 @@ __device__ __forceinline__ void scatter(const Rxn& x, double* sW, double q) {
         }
 }
 
+template <int BLK, int PREC, int KIND>
+__device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, const double* sC, const double* sG,
+                                       const Pt& P, const double* dlnA, const MathTab& mt, const DfTab& dt) {
+    if constexpr (PREC == kDF)
+        return rate_of_progress_df<BLK, KIND>(m, x, r, sC, reinterpret_cast<const float2*>(sG), P, dlnA, dt);
+    else
+        return rate_of_progress<BLK, PREC, KIND>(m, x, r, sC, sG, P, dlnA, mt);
+}
+
 // All reactions of one kind, two per iteration.
-template <int BLK, bool MIXED, int KIND>
+template <int BLK, int PREC, int KIND>
 __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1, const double* sC, const double* sG,
-                                               double* sW, const Pt& P, const double* dlnA, const MathTab& mt) {
+                                               double* sW, const Pt& P, const double* dlnA, const MathTab& mt,
+                                               const DfTab& dt) {
     for (int r = r0; r < r1; r += 2) {
         const Rxn a = load_rxn(m.rxn + r);
         if (r + 1 < r1) {
             const Rxn b = load_rxn(m.rxn + r + 1);
-            const double qa = rate_of_progress<BLK, MIXED, KIND>(m, a, r, sC, sG, P, dlnA, mt);
-            const double qb = rate_of_progress<BLK, MIXED, KIND>(m, b, r + 1, sC, sG, P, dlnA, mt);
+            const double qa = q_of<BLK, PREC, KIND>(m, a, r, sC, sG, P, dlnA, mt, dt);
+            const double qb = q_of<BLK, PREC, KIND>(m, b, r + 1, sC, sG, P, dlnA, mt, dt);
             scatter<BLK>(a, sW, qa);
             scatter<BLK>(b, sW, qb);
         } else {
-            scatter<BLK>(a, sW, rate_of_progress<BLK, MIXED, KIND>(m, a, r, sC, sG, P, dlnA, mt));
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND>(m, a, r, sC, sG, P, dlnA, mt, dt));
         }
     }
 }
 
-template <int BLK, bool MIXED>
+// g_k/RT = a1 (1 - ln T) + T (c1 + T (c2 + T (c3 + T c4))) + a6/T - a7, in pairs
+__device__ __forceinline__ dfl nasa_gRT_df(const DevMech& m, int k, const Pt& P) {
+    const float2* c = m.nasa_df + ((size_t)k * 2 + (P.T <= __ldg(m.Tmid + k) ? 0 : 1)) * 8;
+    dfl acc = dfl_of(__ldg(c + 4));
+    acc = df_fma(acc, P.Td, dfl_of(__ldg(c + 3)));
+    acc = df_fma(acc, P.Td, dfl_of(__ldg(c + 2)));
+    acc = df_fma(acc, P.Td, dfl_of(__ldg(c + 1)));
+    acc = df_mul(acc, P.Td);
+    acc = df_fma(dfl_of(__ldg(c + 0)), df_add(dfl{1.0f, 0.0f}, df_neg(P.lnTd)), acc);
+    acc = df_fma(dfl_of(__ldg(c + 5)), P.invTd, acc);
+    return df_add(acc, dfl_of(__ldg(c + 6)));
+}
+
+template <int BLK, int PREC>
 __global__ void __launch_bounds__(BLK) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                     const double* __restrict__ T, const double* __restrict__ p,
                                                     const double* __restrict__ Y,
                                                     const double* __restrict__ dlnA,
                                                     double* __restrict__ omega, double* __restrict__ hrr) {
     extern __shared__ double smem[];
-    const MathTab mt = stage_math_tables(smem, m.mtab);
+    MathTab mt{};
+    DfTab dt{};
+    if constexpr (PREC == kDF) {
+        float2* t = reinterpret_cast<float2*>(smem);
+        for (int j = threadIdx.x; j < kExpTab; j += BLK) {
+            t[j] = __ldg(m.df_exp_tab + j);
+            t[kExpTab + j] = __ldg(m.df_log_rc + j);
+            t[2 * kExpTab + j] = __ldg(m.df_log_lc + j);
+        }
+        dt = DfTab{t, t + kExpTab, t + 2 * kExpTab};
+    } else {
+        mt = stage_math_tables(smem, m.mtab);
+    }
     __syncthreads();
     const int K = m.K;
     const int tid = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * BLK + tid;
     if (i >= n) return;
     double* sC = smem + kMathTabDoubles + tid;                       // C_k       at sC[k * BLK]
-    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + tid;     // g_k / RT
+    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + tid;     // g_k / RT (a pair in the kDF form)
     double* sW = smem + kMathTabDoubles + (size_t)2 * K * BLK + tid; // omega_k accumulators
 
     Pt P;
     P.T = T[i];
-    P.lnT = flog(P.T, mt);
     P.invT = 1.0 / P.T;
     P.pRT = p[i] * P.invT * kInvR;                     // p/(RT) = sum_k C_k
-    P.lnP0RT = kLnP0overR - P.lnT;                     // ln(p0/(R T))
-    P.Tf = (float)P.T;
-    P.lnTf = (float)P.lnT;
-    P.invTf = (float)P.invT;
+    if constexpr (PREC == kDF) {
+        P.Td = df_split(P.T);
+        P.invTd = df_split(P.invT);
+        P.lnTd = log_df(P.T, dt.rc, dt.lc);
+        P.lnP0RTd = df_add(dfc_lnp0r(), df_neg(P.lnTd));
+    } else {
+        P.lnT = flog(P.T, mt);
+        P.lnP0RT = kLnP0overR - P.lnT;                 // ln(p0/(R T))
+        P.Tf = (float)P.T;
+        P.lnTf = (float)P.lnT;
+        P.invTf = (float)P.invT;
+    }
     double s = 0.0;
     for (int k = 0; k < K; ++k) {
         const double yw = Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
@@ -265,13 +431,18 @@ __global__ void __launch_bounds__(BLK) rates_kernel(const DevMech m, const int64
     const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
     for (int k = 0; k < K; ++k) {
         sC[k * BLK] *= rho_w;                          // C_k = rho Y_k / W_k
-        sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
+        if constexpr (PREC == kDF) {
+            const dfl g = nasa_gRT_df(m, k, P);
+            reinterpret_cast<float2*>(sG)[k * BLK] = make_float2(g.h, g.l);   // 8-byte slot, like a double
+        } else {
+            sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
+        }
         sW[k * BLK] = 0.0;
     }
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    reaction_group<BLK, MIXED, 0>(m, 0, e1, sC, sG, sW, P, dlnA, mt);
-    reaction_group<BLK, MIXED, 1>(m, e1, t1, sC, sG, sW, P, dlnA, mt);
-    reaction_group<BLK, MIXED, 2>(m, t1, m.R, sC, sG, sW, P, dlnA, mt);
+    reaction_group<BLK, PREC, 0>(m, 0, e1, sC, sG, sW, P, dlnA, mt, dt);
+    reaction_group<BLK, PREC, 1>(m, e1, t1, sC, sG, sW, P, dlnA, mt, dt);
+    reaction_group<BLK, PREC, 2>(m, t1, m.R, sC, sG, sW, P, dlnA, mt, dt);
 
     double h = 0.0;
     for (int k = 0; k < K; ++k) {
@@ -282,10 +453,10 @@ __global__ void __launch_bounds__(BLK) rates_kernel(const DevMech m, const int64
     hrr[i] = -kR * P.T * h;                            // -sum_k h_k omega_k
 }
 
-template <int BLK, bool MIXED>
+template <int BLK, int PREC>
 cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
                      const double* dlnA, double* omega, double* hrr, size_t smem, cudaStream_t s) {
-    auto kern = rates_kernel<BLK, MIXED>;
+    auto kern = rates_kernel<BLK, PREC>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (n + BLK - 1) / BLK;
@@ -293,28 +464,32 @@ cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, c
     return cudaGetLastError();
 }
 
+template <int PREC>
+cudaError_t launch_prec(int blk, const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                        const double* Y, const double* dlnA, double* omega, double* hrr, size_t smem, cudaStream_t s) {
+    switch (blk) {
+        case 128: return launch_t<128, PREC>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
+        case 64: return launch_t<64, PREC>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
+        case 32: return launch_t<32, PREC>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
 }  // namespace
 
 cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                          const double* Y, const double* dlnA, double* omega, double* hrr, int precision,
                          cudaStream_t s) {
+    // the staged tables (kMathTabDoubles doubles) cover the kDF tables too (3 x 128 pairs)
+    static_assert(3 * kExpTab * sizeof(float2) <= kMathTabDoubles * sizeof(double), "table space");
     const size_t per_thread = (size_t)3 * m.K * sizeof(double);
     const size_t tab = kMathTabDoubles * sizeof(double);
     const int blk = pick_block_occupancy(per_thread, tab);
     if (!blk) return cudaErrorInvalidConfiguration;
     const size_t smem = per_thread * blk + tab;
-    const bool mixed = precision == NK_MIXED;
-#define NK_RATES_CASE(B)                                                                                   \
-    case B:                                                                                                \
-        return mixed ? launch_t<B, true>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s)                     \
-                     : launch_t<B, false>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
-    switch (blk) {
-        NK_RATES_CASE(128)
-        NK_RATES_CASE(64)
-        NK_RATES_CASE(32)
-    }
-#undef NK_RATES_CASE
-    return cudaErrorInvalidConfiguration;
+    if (precision == NK_MIXED) return launch_prec<kMixed>(blk, m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
+    if (precision == NK_FP64_NATIVE) return launch_prec<kNative>(blk, m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
+    return launch_prec<kDF>(blk, m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
 }
 
 }  // namespace nk

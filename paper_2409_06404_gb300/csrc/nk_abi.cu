@@ -292,6 +292,42 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     }
     for (int q = 0; q < P; ++q) reexpand(d->D_fit + 4 * q, df_D.data() + 4 * q);
     for (int j = 0; j < nk::kExpTab; ++j) df_exp[j] = split(exp2l((long double)j / nk::kExpTab));
+    std::vector<float2> df_rc(nk::kLogTab), df_lc(nk::kLogTab);
+    for (int j = 0; j < nk::kLogTab; ++j) {
+        const long double c = 1.0L + ((long double)j + 0.5L) / nk::kLogTab;
+        const double rc = (double)(1.0L / c);
+        df_rc[j] = split(rc);
+        df_lc[j] = split(-logl((long double)rc));
+    }
+    // rates: NASA g/RT coefficients, Arrhenius and Troe parameters as pairs (device order)
+    std::vector<float2> nasa_df((size_t)K * 2 * 8, float2{0.0f, 0.0f});
+    for (int k = 0; k < K; ++k)
+        for (int range = 0; range < 2; ++range) {
+            const double* a = (range == 0 ? d->nasa_lo : d->nasa_hi) + 7 * k;
+            float2* c = nasa_df.data() + ((size_t)k * 2 + range) * 8;
+            c[0] = split(a[0]);
+            c[1] = split(-(long double)a[1] / 2.0L);
+            c[2] = split(-(long double)a[2] / 6.0L);
+            c[3] = split(-(long double)a[3] / 12.0L);
+            c[4] = split(-(long double)a[4] / 20.0L);
+            c[5] = split(a[5]);
+            c[6] = split(-(long double)a[6]);
+        }
+    std::vector<float4> rxn_df((size_t)R * 2), troe_df;
+    for (int q = 0; q < R; ++q) {
+        const int r = order[q];
+        const float2 lA = split(d->lnA[r]), be = split(d->beta[r]), ea = split((long double)d->Ea[r] / nk::kR);
+        rxn_df[2 * q] = float4{lA.x, lA.y, be.x, be.y};
+        rxn_df[2 * q + 1] = float4{ea.x, ea.y, (float)rxn[q].dnu, 0.0f};
+        if (d->rtype[r] == NK_RXN_TROE) {
+            const double* t = d->troe + 4 * r;
+            const float2 a0 = split(d->lnA0[r]), b0 = split(d->beta0[r]), e0 = split((long double)d->Ea0[r] / nk::kR),
+                         i3 = split(1.0L / t[1]), i1 = split(1.0L / t[2]), t2 = split(t[3] > 0.0 ? t[3] : 0.0);
+            troe_df.push_back(float4{a0.x, a0.y, b0.x, b0.y});
+            troe_df.push_back(float4{e0.x, e0.y, i3.x, i3.y});
+            troe_df.push_back(float4{i1.x, i1.y, t2.x, t2.y});
+        }
+    }
 
     auto to_f = [](const double* s, size_t n) {
         std::vector<float> v(n);
@@ -315,7 +351,9 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_fA = L.add((size_t)K * K * 4), o_fq = L.add(K * 4), o_fs = L.add(K * 4), o_fiw = L.add(K * 4),
                  o_dmu = L.add(df_mu.size() * 8), o_dlam = L.add(df_lam.size() * 8), o_dD = L.add(df_D.size() * 8),
                  o_dA = L.add(df_A.size() * 8), o_dq = L.add(df_qlnW.size() * 8), o_ds = L.add(df_sqrtW.size() * 8),
-                 o_dexp = L.add(df_exp.size() * 8);
+                 o_dexp = L.add(df_exp.size() * 8), o_drc = L.add(df_rc.size() * 8), o_dlc = L.add(df_lc.size() * 8),
+                 o_ndf = L.add(nasa_df.size() * 8), o_rdf = L.add(rxn_df.size() * 16),
+                 o_tdf = L.add(troe_df.size() * 16 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -350,6 +388,11 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_dq, df_qlnW.data(), df_qlnW.size() * 8);
     put(o_ds, df_sqrtW.data(), df_sqrtW.size() * 8);
     put(o_dexp, df_exp.data(), df_exp.size() * 8);
+    put(o_drc, df_rc.data(), df_rc.size() * 8);
+    put(o_dlc, df_lc.data(), df_lc.size() * 8);
+    put(o_ndf, nasa_df.data(), nasa_df.size() * 8);
+    put(o_rdf, rxn_df.data(), rxn_df.size() * 16);
+    put(o_tdf, troe_df.data(), troe_df.size() * 16);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -409,6 +452,11 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.df_qlnW = reinterpret_cast<const float2*>(b + o_dq);
     dm.df_sqrtW = reinterpret_cast<const float2*>(b + o_ds);
     dm.df_exp_tab = reinterpret_cast<const float2*>(b + o_dexp);
+    dm.df_log_rc = reinterpret_cast<const float2*>(b + o_drc);
+    dm.df_log_lc = reinterpret_cast<const float2*>(b + o_dlc);
+    dm.nasa_df = reinterpret_cast<const float2*>(b + o_ndf);
+    dm.rxn_df = reinterpret_cast<const float4*>(b + o_rdf);
+    dm.troe_df = reinterpret_cast<const float4*>(b + o_tdf);
     *out = m;
     return ok();
 }

@@ -110,4 +110,97 @@ __device__ __forceinline__ dfl df_exp(dfl x, const float2* tab) {
     return df_ldexp(v, N >> 7);
 }
 
+// ------------------------------------------------------------------ conversions by integer ops
+// The F2F conversion instructions run at the FP64 rate on GB300; rebuilding the bit pattern
+// with integer operations keeps them off the FP64 pipe.  Normal floats and zero only (a
+// subnormal float converts to a signed zero; the kernels never produce one that matters).
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    const unsigned long long bits =
+        sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+// x * s for a float s (pair result)
+__device__ __forceinline__ dfl df_mul_f(dfl x, float s) {
+    const float p = __fmul_rn(x.h, s);
+    float e = __fmaf_rn(x.h, s, -p);
+    e = __fmaf_rn(x.l, s, e);
+    return fast_two_sum(p, e);
+}
+
+// ---------------------------------------------------------------- exp / log over the full range
+// exp(x) returned in double for a pair x with |x| < 708 (NaN and larger |x| fall back to the
+// double exp of x.h + x.l).  Same method as df_exp with ln2/128 split as C1 (7 significant
+// bits, so N*C1 is exact for |N| < 2^17) + C2 + C3; the pair T_j (1 + (e^r - 1)) in [1, 2)
+// becomes a double with one FP64 add and 2^m goes into the exponent field.  Relative error
+// <= 1.7e-13 for |x| <= 100, 2.2e-12 at |x| = 700 (the pair carries x to 2^-48 |x|).
+__device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
+    if (!(fabsf(x.h) < 708.0f)) return exp((double)x.h + (double)x.l);
+    constexpr float kInvC = 184.6649652337873f;          // 128 / ln2
+    constexpr float C1 = 5.43212890625e-03f;
+    constexpr float C2 = -1.691655779723078e-05f;
+    constexpr float C3 = -3.281964814933619e-13f;
+    const float Nf = rintf(x.h * kInvC);
+    const int N = (int)Nf;
+    const float rh = __fmaf_rn(-Nf, C1, x.h);            // exact
+    const float p2 = __fmul_rn(-Nf, C2);
+    const float p2e = __fmaf_rn(-Nf, C2, -p2);
+    dfl r = two_sum(rh, p2);
+    r.l = __fadd_rn(r.l, __fadd_rn(__fadd_rn(x.l, p2e), __fmul_rn(-Nf, C3)));
+    r = fast_two_sum(r.h, r.l);
+    const float q = __fmul_rn(r.h, r.h);
+    float qe = __fmaf_rn(r.h, r.h, -q);
+    qe = __fmaf_rn(2.0f * r.h, r.l, qe);
+    const float tail = __fmul_rn(__fmul_rn(q, r.h), __fmaf_rn(r.h, 1.0f / 24.0f, 1.0f / 6.0f));
+    dfl em1 = two_sum(r.h, 0.5f * q);
+    em1.l = __fadd_rn(em1.l, __fadd_rn(r.l, __fmaf_rn(0.5f, qe, tail)));
+    em1 = fast_two_sum(em1.h, em1.l);
+    const float2 t = tab[N & 127];
+    const dfl tj{t.x, t.y};
+    const dfl v = df_fma(tj, em1, tj);
+    const double d = f2d_bits(v.h) + f2d_bits(v.l);     // the one FP64 operation
+    return __longlong_as_double(__double_as_longlong(d) + ((long long)(N >> 7) << 52));
+}
+
+// log(x) as a pair for a positive normal double x (others fall back to the double log):
+// x = 2^e m, j = top 7 bits of m, r = m / c_j - 1 with the pair 1/c_j, log1p(r) with r and
+// r^2/2 in pairs and the cubic tail in float, plus e ln2 and log(c_j) as pairs.  Absolute
+// error ~1e-14 for |log x| <= 10, 5e-12 at |log x| = 700.
+__device__ __forceinline__ dfl log_df(double x, const float2* rc, const float2* lc) {
+    const long long b = __double_as_longlong(x);
+    const int hi = (int)(b >> 32);
+    if (hi < 0x00100000 || hi >= 0x7ff00000) return df_split(log(x));
+    const int e = (hi >> 20) - 1023;
+    const int j = (hi >> 13) & 127;
+    const unsigned long long mant = (unsigned long long)b & 0x000fffffffffffffULL;
+    const dfl m{__uint_as_float(0x3f800000u | (unsigned int)(mant >> 29)),
+                (float)(unsigned int)(mant & 0x1fffffffULL) * 2.220446049250313e-16f};   // * 2^-52
+    const float2 rcj = rc[j];
+    dfl r = df_mul(m, dfl{rcj.x, rcj.y});
+    r = df_add(r, dfl{-1.0f, 0.0f});
+    const float q = __fmul_rn(r.h, r.h);
+    float qe = __fmaf_rn(r.h, r.h, -q);
+    qe = __fmaf_rn(2.0f * r.h, r.l, qe);
+    const float P = __fmaf_rn(r.h, __fmaf_rn(r.h, __fmaf_rn(r.h, __fmaf_rn(r.h, 1.0f / 7.0f, -1.0f / 6.0f), 0.2f),
+                                             -0.25f), 1.0f / 3.0f);
+    const float cub = __fmul_rn(__fmul_rn(q, r.h), P);
+    dfl l1 = two_sum(r.h, -0.5f * q);
+    l1.l = __fadd_rn(l1.l, __fadd_rn(r.l, __fmaf_rn(-0.5f, qe, cub)));
+    l1 = fast_two_sum(l1.h, l1.l);
+    const float ef = (float)e;
+    constexpr float LN2H = 0.693147182464599609375f, LN2L = -1.9046542121259336e-09f;
+    const float p = __fmul_rn(ef, LN2H);
+    float pe = __fmaf_rn(ef, LN2H, -p);
+    pe = __fmaf_rn(ef, LN2L, pe);
+    const dfl el = two_sum(p, pe);
+    const float2 lcj = lc[j];
+    return df_add(df_add(el, dfl{lcj.x, lcj.y}), l1);
+}
+
 }  // namespace nk

@@ -107,6 +107,12 @@ struct DevMech {
     const float2* df_qlnW;        // [K] ln(W)/4
     const float2* df_sqrtW;       // [K]
     const float2* df_exp_tab;     // [128] 2^(j/128)
+    const float2* df_log_rc;      // [128] 1/c_j (see nk_math.cuh)
+    const float2* df_log_lc;      // [128] -log(1/c_j)
+    // double-float tables of the FP64 rates kernel (exponent arithmetic on the FP32 pipe)
+    const float2* nasa_df;        // [K][2][8] g/RT coefficients a1, -a2/2, -a3/6, -a4/12, -a5/20, a6, -a7
+    const float4* rxn_df;         // [R][2] (lnA, beta) and (Ea/R, dnu, -) as pairs, device order
+    const float4* troe_df;        // [n_troe][3] (lnA0, beta0), (Ea0/R, 1/T3), (1/T1, T2) as pairs
 };
 
 // Centre of the re-expanded transport fits (ln T about 1100 K).
