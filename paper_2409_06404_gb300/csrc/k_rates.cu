@@ -1,12 +1,16 @@
 // Net species production rates omega_k and heat release per point (the "rates" kernel of
 // the paper, Tab. 3-4; omega_k of Eq. 1a, heat release of Eq. 1b).
 //
-// Layout: one thread per point.  Every thread of a warp walks the same reaction at the same
-// time, so reaction records are broadcast loads and control flow is uniform.  The device
-// copy of the mechanism groups reactions by kind (elementary, third-body, Troe); each kind
-// has its own branch-free loop that takes two reactions per iteration, giving the FP64 pipe
-// two independent dependency chains per warp.  The per-point species state (C_k, g_k/RT and
-// the omega_k accumulators) lives in shared memory as [species][thread].
+// Layout: a point is worked on by NP warps ("parts"), one lane per point in each.  All lanes
+// of a warp walk the same reaction at the same time, so reaction records are broadcast loads
+// and control flow is uniform.  The device copy of the mechanism groups reactions by kind
+// (elementary, third-body, Troe); each part walks its own contiguous slice of every kind.
+// The per-point species state (C_k and g_k/RT, shared by the parts, and one row of omega_k
+// partials per part) lives in shared memory as [species][point]; the partials are added in
+// part order at the end.  NP and the points per block come from CUDA's occupancy calculator:
+// shared memory per point bounds the resident warps, and splitting a point's reactions over
+// warps raises them (5 -> 8 warps per SM at K = 53, 2 -> 4 at K = 120), which this
+// latency-bound walk needs.
 //
 // Three arithmetic forms (template PREC):
 //  kNative (NK_FP64_NATIVE): every operation in double (exp/log from nk_math.cuh).
@@ -18,6 +22,10 @@
 //  kMixed (NK_MIXED): the Arrhenius argument ln A + beta ln T - Ea/(RT), k_f and the whole
 //    Troe falloff in single precision; equilibrium constants (the sum of nu_k g_k/RT and its
 //    exponential), the forward-minus-reverse difference and the omega accumulation in double.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "nk_internal.cuh"
 
 namespace nk {
@@ -345,23 +353,25 @@ __device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, co
         return rate_of_progress<BLK, PREC, KIND>(m, x, r, sC, sG, P, dlnA, mt);
 }
 
-// All reactions of one kind, two per iteration.
+// Reactions [r0, r1) of one kind, scattered in reaction order.  (Unrolling by two or four
+// reactions per iteration measured slower once several warps share a point.)
 template <int BLK, int PREC, int KIND>
 __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1, const double* sC, const double* sG,
                                                double* sW, const Pt& P, const double* dlnA, const MathTab& mt,
                                                const DfTab& dt) {
-    for (int r = r0; r < r1; r += 2) {
+    for (int r = r0; r < r1; ++r) {
         const Rxn a = load_rxn(m.rxn + r);
-        if (r + 1 < r1) {
-            const Rxn b = load_rxn(m.rxn + r + 1);
-            const double qa = q_of<BLK, PREC, KIND>(m, a, r, sC, sG, P, dlnA, mt, dt);
-            const double qb = q_of<BLK, PREC, KIND>(m, b, r + 1, sC, sG, P, dlnA, mt, dt);
-            scatter<BLK>(a, sW, qa);
-            scatter<BLK>(b, sW, qb);
-        } else {
-            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND>(m, a, r, sC, sG, P, dlnA, mt, dt));
-        }
+        scatter<BLK>(a, sW, q_of<BLK, PREC, KIND>(m, a, r, sC, sG, P, dlnA, mt, dt));
     }
+}
+
+// Part `part` of NP takes the contiguous slice [a + len*part/NP, a + len*(part+1)/NP) of the
+// kind's range [a, b).
+template <int NP>
+__device__ __forceinline__ void slice(int a, int b, int part, int& r0, int& r1) {
+    const int len = b - a;
+    r0 = a + (len * part) / NP;
+    r1 = a + (len * (part + 1)) / NP;
 }
 
 // g_k/RT = a1 (1 - ln T) + T (c1 + T (c2 + T (c3 + T c4))) + a6/T - a7, in pairs
@@ -377,18 +387,23 @@ __device__ __forceinline__ dfl nasa_gRT_df(const DevMech& m, int k, const Pt& P)
     return df_add(acc, dfl_of(__ldg(c + 6)));
 }
 
-template <int BLK, int PREC>
-__global__ void __launch_bounds__(BLK) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
-                                                    const double* __restrict__ T, const double* __restrict__ p,
-                                                    const double* __restrict__ Y,
-                                                    const double* __restrict__ dlnA,
-                                                    double* __restrict__ omega, double* __restrict__ hrr) {
+// BLK points per block, NP parts (warps) per point: thread (part, slot) works on point
+// blockIdx.x * BLK + slot.  The parts of a point share its C_k and g_k/RT, each walks its own
+// slice of every kind and accumulates into its own omega_k partials; the partials are added in
+// part order, so results do not depend on scheduling.
+template <int BLK, int NP, int PREC>
+__global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                         const double* __restrict__ T, const double* __restrict__ p,
+                                                         const double* __restrict__ Y,
+                                                         const double* __restrict__ dlnA,
+                                                         double* __restrict__ omega, double* __restrict__ hrr) {
+    constexpr int NT = BLK * NP;
     extern __shared__ double smem[];
     MathTab mt{};
     DfTab dt{};
     if constexpr (PREC == kDF) {
         float2* t = reinterpret_cast<float2*>(smem);
-        for (int j = threadIdx.x; j < kExpTab; j += BLK) {
+        for (int j = threadIdx.x; j < kExpTab; j += NT) {
             t[j] = __ldg(m.df_exp_tab + j);
             t[kExpTab + j] = __ldg(m.df_log_rc + j);
             t[2 * kExpTab + j] = __ldg(m.df_log_lc + j);
@@ -399,12 +414,15 @@ __global__ void __launch_bounds__(BLK) rates_kernel(const DevMech m, const int64
     }
     __syncthreads();
     const int K = m.K;
-    const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
-    if (i >= n) return;
-    double* sC = smem + kMathTabDoubles + tid;                       // C_k       at sC[k * BLK]
-    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + tid;     // g_k / RT (a pair in the kDF form)
-    double* sW = smem + kMathTabDoubles + (size_t)2 * K * BLK + tid; // omega_k accumulators
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
+    double* sC = smem + kMathTabDoubles + slot;                       // C_k       at sC[k * BLK]
+    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (a pair in the kDF form)
+    double* sW0 = smem + kMathTabDoubles + (size_t)2 * K * BLK + slot;
+    double* sW = sW0 + (size_t)part * K * BLK;                        // this part's omega_k partials
 
     Pt P;
     P.T = T[i];
@@ -423,56 +441,145 @@ __global__ void __launch_bounds__(BLK) rates_kernel(const DevMech m, const int64
         P.invTf = (float)P.invT;
     }
     double s = 0.0;
-    for (int k = 0; k < K; ++k) {
-        const double yw = Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
-        sC[k * BLK] = yw;
-        s += yw;
-    }
+    for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
-    for (int k = 0; k < K; ++k) {
-        sC[k * BLK] *= rho_w;                          // C_k = rho Y_k / W_k
+    for (int k = part; k < K; k += NP) {
+        sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
         if constexpr (PREC == kDF) {
             const dfl g = nasa_gRT_df(m, k, P);
             reinterpret_cast<float2*>(sG)[k * BLK] = make_float2(g.h, g.l);   // 8-byte slot, like a double
         } else {
             sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
         }
-        sW[k * BLK] = 0.0;
     }
+    for (int k = 0; k < K; ++k) sW[k * BLK] = 0.0;
+    if (NP > 1) __syncthreads();
+
+    int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    reaction_group<BLK, PREC, 0>(m, 0, e1, sC, sG, sW, P, dlnA, mt, dt);
-    reaction_group<BLK, PREC, 1>(m, e1, t1, sC, sG, sW, P, dlnA, mt, dt);
-    reaction_group<BLK, PREC, 2>(m, t1, m.R, sC, sG, sW, P, dlnA, mt, dt);
+    slice<NP>(0, e1, part, a, b);
+    reaction_group<BLK, PREC, 0>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
+    slice<NP>(e1, t1, part, a, b);
+    reaction_group<BLK, PREC, 1>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
+    slice<NP>(t1, m.R, part, a, b);
+    reaction_group<BLK, PREC, 2>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
+    if (NP > 1) __syncthreads();
 
     double h = 0.0;
-    for (int k = 0; k < K; ++k) {
-        const double w = sW[k * BLK];
-        omega[(int64_t)k * ld + i] = w;
+    for (int k = part; k < K; k += NP) {
+        double w = sW0[k * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
+        if (live) omega[(int64_t)k * ld + i] = w;
         h = fma(nasa_hRT(nasa_range(m, k, P.T), P.T, P.invT), w, h);
     }
-    hrr[i] = -kR * P.T * h;                            // -sum_k h_k omega_k
+    if constexpr (NP > 1) {
+        sC[part * BLK] = h;                            // C_k is dead; rows 0..NP-1 (NP <= K) hold the partials
+        __syncthreads();
+        if (part != 0) return;
+        h = sC[0];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) h += sC[q * BLK];
+    }
+    if (live) hrr[i] = -kR * P.T * h;                  // -sum_k h_k omega_k
 }
 
-template <int BLK, int PREC>
-cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
-                     const double* dlnA, double* omega, double* hrr, size_t smem, cudaStream_t s) {
-    auto kern = rates_kernel<BLK, PREC>;
-    cudaError_t e = ensure_smem((const void*)kern, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = (n + BLK - 1) / BLK;
-    kern<<<(unsigned)grid, BLK, smem, s>>>(m, n, ld, T, p, Y, dlnA, omega, hrr);
-    return cudaGetLastError();
+struct Shape {
+    int blk, np;
+};
+
+// Launch shapes the library instantiates (points per block, parts per point).
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <int PREC, int S>
+constexpr auto kernel_of() {
+    return rates_kernel<kShapes[S].blk, kShapes[S].np, PREC>;
+}
+
+template <int PREC, int... S>
+const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
+    const void* ptrs[] = {(const void*)kernel_of<PREC, S>()...};
+    return ptrs[idx];
+}
+
+template <int PREC, int... S>
+cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
+                       const double* T, const double* p, const double* Y, const double* dlnA, double* omega,
+                       double* hrr, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    ((S == idx ? (void)(e = [&] {
+        constexpr Shape sh = kShapes[S];
+        auto kern = kernel_of<PREC, S>();
+        cudaError_t r = ensure_smem((const void*)kern, smem);
+        if (r != cudaSuccess) return r;
+        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega,
+                                                                                  hrr);
+        return cudaGetLastError();
+    }())
+               : (void)0),
+     ...);
+    return e;
+}
+
+// Shared bytes of a block: the staged tables, then C_k and g_k/RT per point and NP rows of
+// omega_k partials per point.
+size_t rates_smem(int K, const Shape& sh) {
+    return (size_t)kMathTabDoubles * sizeof(double) + (size_t)(2 + sh.np) * K * sh.blk * sizeof(double);
+}
+
+// The shape with the most resident warps per SM (CUDA's occupancy calculator: shared memory,
+// registers, threads), fewer parts on ties.  Cached per
+// (device, K, form).
+struct Plan {
+    int dev, K, prec, idx;
+};
+std::mutex g_plan_mu;
+std::vector<Plan> g_plans;
+
+template <int PREC>
+int plan_shape(int K) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const Plan& q : g_plans)
+            if (q.dev == dev && q.K == K && q.prec == PREC) return q.idx;
+    }
+    int per_block = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const auto seq = std::make_integer_sequence<int, kNumShapes>{};
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < kNumShapes; ++c) {
+        const Shape& sh = kShapes[c];
+        if (sh.np > K) continue;
+        const size_t bytes = rates_smem(K, sh);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<PREC>(c, seq);
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
+            continue;
+        const int warps = blocks * sh.blk * sh.np / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best = c;
+        }
+    }
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back({dev, K, PREC, best});
+    }
+    return best;
 }
 
 template <int PREC>
-cudaError_t launch_prec(int blk, const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
-                        const double* Y, const double* dlnA, double* omega, double* hrr, size_t smem, cudaStream_t s) {
-    switch (blk) {
-        case 128: return launch_t<128, PREC>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
-        case 64: return launch_t<64, PREC>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
-        case 32: return launch_t<32, PREC>(m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
-    }
-    return cudaErrorInvalidConfiguration;
+cudaError_t launch_prec(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                        const double* dlnA, double* omega, double* hrr, cudaStream_t s) {
+    const int idx = plan_shape<PREC>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<PREC>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, omega, hrr,
+                            rates_smem(m.K, kShapes[idx]), s);
 }
 
 }  // namespace
@@ -482,14 +589,9 @@ cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* 
                          cudaStream_t s) {
     // the staged tables (kMathTabDoubles doubles) cover the kDF tables too (3 x 128 pairs)
     static_assert(3 * kExpTab * sizeof(float2) <= kMathTabDoubles * sizeof(double), "table space");
-    const size_t per_thread = (size_t)3 * m.K * sizeof(double);
-    const size_t tab = kMathTabDoubles * sizeof(double);
-    const int blk = pick_block_occupancy(per_thread, tab);
-    if (!blk) return cudaErrorInvalidConfiguration;
-    const size_t smem = per_thread * blk + tab;
-    if (precision == NK_MIXED) return launch_prec<kMixed>(blk, m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
-    if (precision == NK_FP64_NATIVE) return launch_prec<kNative>(blk, m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
-    return launch_prec<kDF>(blk, m, n, ld, T, p, Y, dlnA, omega, hrr, smem, s);
+    if (precision == NK_MIXED) return launch_prec<kMixed>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
+    if (precision == NK_FP64_NATIVE) return launch_prec<kNative>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
+    return launch_prec<kDF>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
 }
 
 }  // namespace nk

@@ -140,8 +140,12 @@ __device__ __forceinline__ dfl df_mul_f(dfl x, float s) {
 // bits, so N*C1 is exact for |N| < 2^17) + C2 + C3; the pair T_j (1 + (e^r - 1)) in [1, 2)
 // becomes a double with one FP64 add and 2^m goes into the exponent field.  Relative error
 // <= 1.7e-13 for |x| <= 100, 2.2e-12 at |x| = 700 (the pair carries x to 2^-48 |x|).
+// Out of line, so the rare paths' conversions to double stay off the common path.
+static __device__ __noinline__ double exp_df_d_edge(float h, float l) { return exp((double)h + (double)l); }
+static __device__ __noinline__ dfl log_df_edge(double x) { return df_split(log(x)); }
+
 __device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
-    if (!(fabsf(x.h) < 708.0f)) return exp((double)x.h + (double)x.l);
+    if (!(fabsf(x.h) < 708.0f)) return exp_df_d_edge(x.h, x.l);
     constexpr float kInvC = 184.6649652337873f;          // 128 / ln2
     constexpr float C1 = 5.43212890625e-03f;
     constexpr float C2 = -1.691655779723078e-05f;
@@ -175,7 +179,7 @@ __device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
 __device__ __forceinline__ dfl log_df(double x, const float2* rc, const float2* lc) {
     const long long b = __double_as_longlong(x);
     const int hi = (int)(b >> 32);
-    if (hi < 0x00100000 || hi >= 0x7ff00000) return df_split(log(x));
+    if (hi < 0x00100000 || hi >= 0x7ff00000) return log_df_edge(x);
     const int e = (hi >> 20) - 1023;
     const int j = (hi >> 13) & 127;
     const unsigned long long mant = (unsigned long long)b & 0x000fffffffffffffULL;
