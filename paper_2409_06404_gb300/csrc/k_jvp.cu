@@ -1,240 +1,385 @@
 // Exact Jacobian-vector product of (omega_k, heat release) with respect to (T, Y_k) at fixed
 // p: the product the Newton-GMRES stage of the paper approximates by difference quotients
-// (Sec. 2, Sec. 4).  Forward-mode differentiation written out by hand, one thread per point,
-// rates of progress recomputed in registers (nothing per reaction is stored).
+// (Sec. 2, Sec. 4).  Forward-mode differentiation written out by hand, rates of progress
+// recomputed in registers (nothing per reaction is stored).
 //
 // Tangents: with y_k = Y_k/W_k, s = sum y_k, rho = p/(R T s), C_k = rho y_k:
 //   d rho/rho = -dT/T - ds/s,  dC_k = C_k d rho/rho + rho dY_k/W_k,
-//   d(g_k/RT) = -(h_k/RT) dT/T,  d ln k_f = (beta + Ea/(R T)) dT/T,
-//   d ln K_c = -sum nu d(g/RT) - (sum nu) dT/T,
-//   d hrr = -sum_k (c_p,k dT omega_k + h_k d omega_k).
+//   d ln k_f = (beta + Ea/(R T)) dT/T,
+//   d ln K_c = (dT/T) (sum_k nu_k h_k/RT - sum_k nu_k)     (d(g/RT)/dT = -(h/RT)/T),
 // Troe: d ln k = d ln k_inf + d ln P_r/(1+P_r) + ln10 d log10 F with F from the chain rule
-// through F_cent(T), c, n, f1.
-#include "nk_internal.cuh"
+// through F_cent(T), c, n, f1.  Heat release is accumulated per reaction, which needs no
+// omega_k storage:
+//   hrr = -R T sum_r q_r (sum_k nu_kr h_k/RT),
+//   d hrr = -R sum_r [dT q_r (sum_k nu_kr c_p,k/R) + T dq_r (sum_k nu_kr h_k/RT)].
+//
+// FP64 form as the rates kernel: the exponent chains (ln k_f, the reaction's Gibbs and
+// enthalpy sums, ln K_c) in double-float pairs on the FP32 pipe, concentrations, their
+// products and every tangent in double.  The falloff chain runs in double with pair-based
+// exp/log.  Layout as the rates kernel: NP warps per point share C_k and dC_k in shared
+// memory, each accumulates its own d omega_k (and omega_k when asked for) partials, added in
+// part order.
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "nk_rxn.cuh"
 
 namespace nk {
 namespace {
 
-template <int BLK>
-__global__ void __launch_bounds__(BLK) jvp_kernel(const DevMech m, const int64_t n, const int64_t ld,
-                                                  const double* __restrict__ T, const double* __restrict__ p,
-                                                  const double* __restrict__ Y, const double* __restrict__ dlnA,
-                                                  const double* __restrict__ vT, const double* __restrict__ vY,
-                                                  double* __restrict__ omega, double* __restrict__ hrr,
-                                                  double* __restrict__ d_omega, double* __restrict__ d_hrr) {
-    extern __shared__ double smem_all[];
-    const MathTab mt = stage_math_tables(smem_all, m.mtab);
-    __syncthreads();
-    double* smem = smem_all + kMathTabDoubles;
-    const int K = m.K;
-    const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
-    if (i >= n) return;
-    double* sC = smem + tid;                          // C_k
-    double* sG = smem + (size_t)K * BLK + tid;        // g_k/RT
-    double* sH = smem + (size_t)2 * K * BLK + tid;    // h_k/RT
-    double* sW = smem + (size_t)3 * K * BLK + tid;    // omega_k
-    double* sD = smem + (size_t)4 * K * BLK + tid;    // d omega_k
+struct JvpPoint {
+    TPairs P;
+    double invT, lnT, tT, dT, pRT, dpRT;
+};
 
-    const double Ti = T[i], pi = p[i], dT = vT[i];
-    const double lnT = flog(Ti, mt), invT = 1.0 / Ti;
-    const double tT = dT * invT;                      // dT/T
-    const double pRT = pi * invT * kInvR;
-    double s = 0.0, ds = 0.0;
-    for (int k = 0; k < K; ++k) {
-        const double iw = __ldg(m.invW + k);
-        const double yw = Y[(int64_t)k * ld + i] * iw;
-        ds = fma(vY[(int64_t)k * ld + i], iw, ds);
-        sC[k * BLK] = yw;
-        s += yw;
+struct JvpAcc {
+    double h = 0.0;    // sum_r q_r dH_r/RT
+    double cp = 0.0;   // sum_r q_r dCp_r/R
+    double dh = 0.0;   // sum_r dq_r dH_r/RT
+};
+
+template <int BLK, int KIND, bool OMEGA>
+__device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const double* sC, const double* sdC, double* sW,
+                                             double* sD, const JvpPoint& Q, const double* dlnA, const DfTab& dt,
+                                             JvpAcc& acc) {
+    const Rxn x = load_rxn(m.rxn + r);
+    double fw, dfw, rv, drv;                      // dual-number concentration products
+    {
+        const int k = x.sp[0];
+        const double c = sC[k * BLK], dc = sdC[k * BLK];
+        fw = c;
+        dfw = dc;
+        for (int j = 1; j < x.nu[0]; ++j) {
+            dfw = fma(dfw, c, fw * dc);
+            fw *= c;
+        }
     }
-    const double rho = pRT / s;
-    const double arho = -tT - ds / s;                 // d rho / rho
-    for (int k = 0; k < K; ++k) {
-        const double* c = nasa_range(m, k, Ti);
-        sC[k * BLK] *= rho;
-        sG[k * BLK] = nasa_gRT(c, Ti, lnT, invT);
-        sH[k * BLK] = nasa_hRT(c, Ti, invT);
-        sW[k * BLK] = 0.0;
-        sD[k * BLK] = 0.0;
-    }
-    const double lnP0RT = 9.408091968961747 - lnT;   // ln(p0/(R T)), ln(101325/8.314462618) = 9.408...
-    const double dpRT = -pRT * tT;
-
-    // dC_k on demand: C_k d rho/rho + rho vY_k / W_k
-    auto dC = [&](int k, double Ck) {
-        return fma(Ck, arho, rho * vY[(int64_t)k * ld + i] * __ldg(m.invW + k));
-    };
-
-    for (int r = 0; r < m.R; ++r) {
-        const RxnRec* rec = m.rxn + r;
-        const int type = __ldg(&rec->type), nr = __ldg(&rec->nr), np = __ldg(&rec->np);
-        const double shift = dlnA ? __ldg(dlnA + __ldg(&rec->orig)) : 0.0;
-        double sumg, dsumh;                           // sum nu g/RT, sum nu h/RT
-        double fw, dfw, rv, drv;                      // dual-number concentration products
-        {
-            const int k = __ldg(&rec->sp[0]), nu = __ldg(&rec->nu[0]);
-            const double nd = __ldg(&rec->nud[0]);
-            const double c = sC[k * BLK], dc = dC(k, c);
-            sumg = nd * sG[k * BLK];
-            dsumh = nd * sH[k * BLK];
-            fw = c;
-            dfw = dc;
-            for (int j = 1; j < nu; ++j) {
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            const int k = x.sp[e];
+            const double c = sC[k * BLK], dc = sdC[k * BLK];
+            for (int j = 0; j < x.nu[e]; ++j) {
                 dfw = fma(dfw, c, fw * dc);
                 fw *= c;
             }
         }
-#pragma unroll
-        for (int e = 1; e < kMaxSide; ++e) {
-            if (e < nr) {
-                const int k = __ldg(&rec->sp[e]), nu = __ldg(&rec->nu[e]);
-                const double nd = __ldg(&rec->nud[e]);
-                const double c = sC[k * BLK], dc = dC(k, c);
-                sumg = fma(nd, sG[k * BLK], sumg);
-                dsumh = fma(nd, sH[k * BLK], dsumh);
-                for (int j = 0; j < nu; ++j) {
-                    dfw = fma(dfw, c, fw * dc);
-                    fw *= c;
-                }
-            }
+    {
+        const int k = x.sp[kMaxSide];
+        const double c = sC[k * BLK], dc = sdC[k * BLK];
+        rv = c;
+        drv = dc;
+        for (int j = 1; j < x.nu[kMaxSide]; ++j) {
+            drv = fma(drv, c, rv * dc);
+            rv *= c;
         }
-        {
-            const int k = __ldg(&rec->sp[kMaxSide]), nu = __ldg(&rec->nu[kMaxSide]);
-            const double nd = __ldg(&rec->nud[kMaxSide]);
-            const double c = sC[k * BLK], dc = dC(k, c);
-            sumg = fma(nd, sG[k * BLK], sumg);
-            dsumh = fma(nd, sH[k * BLK], dsumh);
-            rv = c;
-            drv = dc;
-            for (int j = 1; j < nu; ++j) {
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.np) {
+            const int k = x.sp[kMaxSide + e];
+            const double c = sC[k * BLK], dc = sdC[k * BLK];
+            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) {
                 drv = fma(drv, c, rv * dc);
                 rv *= c;
             }
         }
-#pragma unroll
-        for (int e = 1; e < kMaxSide; ++e) {
-            if (e < np) {
-                const int k = __ldg(&rec->sp[kMaxSide + e]), nu = __ldg(&rec->nu[kMaxSide + e]);
-                const double nd = __ldg(&rec->nud[kMaxSide + e]);
-                const double c = sC[k * BLK], dc = dC(k, c);
-                sumg = fma(nd, sG[k * BLK], sumg);
-                dsumh = fma(nd, sH[k * BLK], dsumh);
-                for (int j = 0; j < nu; ++j) {
-                    drv = fma(drv, c, rv * dc);
-                    rv *= c;
-                }
-            }
+    dfl dG, dH, dCp;
+    rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
+    const double sumh = df_to_d(dH), sumcp = df_to_d(dCp);
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, (float)x.dnu), df_neg(dG));
+    const double dlnKc = Q.tT * (sumh - x.dnu);
+
+    double shift = 0.0;
+    dfl shiftd{0.0f, 0.0f};
+    if (dlnA) {
+        shift = __ldg(dlnA + x.orig);
+        shiftd = df_split(shift);
+    }
+    const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
+    double dlnkf = fma(x.EaR, Q.invT, x.beta) * Q.tT;
+
+    double M = 0.0, dM = 0.0;
+    if (KIND != 0) {
+        M = Q.pRT;
+        dM = Q.dpRT;
+        for (int j = x.eff0; j < x.eff1; ++j) {
+            const int k = __ldg(m.eff_sp + j);
+            const double em1 = __ldg(m.eff_m1 + j);
+            M = fma(em1, sC[k * BLK], M);
+            dM = fma(em1, sdC[k * BLK], dM);
         }
-        const double dnu = __ldg(&rec->dnu);
-        const double lnKc = fma(dnu, lnP0RT, -sumg);
-        // d(sum nu g/RT) = -(dT/T) sum nu h/RT;  d ln(p0/RT) = -dT/T
-        const double dlnKc = fma(tT, dsumh, -dnu * tT);
-
-        const double beta = __ldg(&rec->beta), EaR = __ldg(&rec->EaR);
-        const double lnkf = fma(-EaR, invT, fma(beta, lnT, dlnA ? __ldg(&rec->lnA) + shift : __ldg(&rec->lnA)));
-        double dlnkf = fma(EaR, invT, beta) * tT;
-
-        double M = 0.0, dM = 0.0;
-        if (type != NK_RXN_ELEMENTARY) {
-            M = pRT;
-            dM = dpRT;
-            const int e0 = __ldg(&rec->eff0), e1 = __ldg(&rec->eff1);
-            for (int j = e0; j < e1; ++j) {
-                const int k = __ldg(m.eff_sp + j);
-                const double em1 = __ldg(m.eff_m1 + j), c = sC[k * BLK];
-                M = fma(em1, c, M);
-                dM = fma(em1, dC(k, c), dM);
-            }
-        }
-
-        double kf;
-        if (type == NK_RXN_TROE) {
-            const TroeRec* t = m.troe + __ldg(&rec->aux);
-            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
-            const double lnk0 = fma(-Ea0R, invT, fma(beta0, lnT, __ldg(&t->lnA0) + shift));
-            const double dlnk0 = fma(Ea0R, invT, beta0) * tT;
-            if (M == 0.0) {
-                kf = 0.0;
-                dlnkf = 0.0;
-            } else {
-                const double lnPr = lnk0 - lnkf + flog(M, mt);
-                const double dlnPr = dlnk0 - dlnkf + dM / M;
-                const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-                const double e3 = fexp(-Ti * i3, mt), e1 = fexp(-Ti * i1, mt);
-                double Fc = (1.0 - a) * e3 + a * e1;
-                double dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1) * dT;
-                if (__ldg(&t->hasT2) != 0.0) {
-                    const double T2 = __ldg(&t->T2), e2 = fexp(-T2 * invT, mt);
-                    Fc += e2;
-                    dFc = fma(T2 * invT * e2, tT, dFc);
-                }
-                const double lFc = flog(Fc, mt) * kInvLn10, dlFc = dFc / Fc * kInvLn10;
-                const double c = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
-                const double u = fma(lnPr, kInvLn10, c), du = fma(dlnPr, kInvLn10, -0.67 * dlFc);
-                const double v = fma(-0.14, u, nn), dv = fma(-0.14, du, -1.27 * dlFc);
-                const double f1 = u / v, df1 = fma(-f1, dv, du) / v;
-                const double den = fma(f1, f1, 1.0);
-                const double lF = lFc / den;
-                const double dlF = fma(-2.0 * lF * f1, df1, dlFc) / den;
-                const double g = 1.0 / (1.0 + fexp(-lnPr, mt));     // P_r / (1 + P_r)
-                kf = fexp(lnkf, mt) * g * fexp(lF * kLn10, mt);
-                dlnkf = dlnkf + dlnPr * (1.0 - g) + kLn10 * dlF;
-            }
+    }
+    double kf, kr;
+    if constexpr (KIND == 2) {
+        if (M == 0.0) {
+            kf = kr = 0.0;
+            dlnkf = 0.0;
         } else {
-            kf = fexp(lnkf, mt);
+            const TroeRec* t = m.troe + x.aux;
+            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
+            const double lnk0 = fma(-Ea0R, Q.invT, fma(beta0, Q.lnT, __ldg(&t->lnA0) + shift));
+            const double dlnk0 = fma(Ea0R, Q.invT, beta0) * Q.tT;
+            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
+            const double dlnPr = dlnk0 - dlnkf + dM / M;
+            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
+            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
+            double Fc = (1.0 - a) * e3 + a * e1;
+            double dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1) * Q.dT;
+            if (__ldg(&t->hasT2) != 0.0) {
+                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
+                Fc += e2;
+                dFc = fma(T2 * Q.invT * e2, Q.tT, dFc);
+            }
+            const double lFc = dlog_df(Fc, dt) * kInvLn10, dlFc = dFc / Fc * kInvLn10;
+            const double c = fma(-0.67, lFc, -0.4), nn = fma(-1.27, lFc, 0.75);
+            const double u = fma(lnPr, kInvLn10, c), du = fma(dlnPr, kInvLn10, -0.67 * dlFc);
+            const double v = fma(-0.14, u, nn), dv = fma(-0.14, du, -1.27 * dlFc);
+            const double f1 = u / v, df1 = fma(-f1, dv, du) / v;
+            const double den = fma(f1, f1, 1.0);
+            const double lF = lFc / den;
+            const double dlF = fma(-2.0 * lF * f1, df1, dlFc) / den;
+            const double g = 1.0 / (1.0 + dexp_df(-lnPr, dt));       // P_r / (1 + P_r)
+            kf = exp_df_d(lnkf, dt.e2) * g * dexp_df(lF * kLn10, dt);
+            dlnkf = dlnkf + dlnPr * (1.0 - g) + kLn10 * dlF;
+            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
         }
-        const double kr = kf * fexp(-lnKc, mt);
-        const double dkf = kf * dlnkf, dkr = kr * (dlnkf - dlnKc);
-        double q = fma(kf, fw, -kr * rv);
-        double dq = fma(dkf, fw, kf * dfw) - fma(dkr, rv, kr * drv);
-        if (type == NK_RXN_THIRD_BODY) {
-            dq = fma(dq, M, q * dM);
-            q *= M;
+    } else {
+        kf = exp_df_d(lnkf, dt.e2);
+        kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
+    }
+    const double dkf = kf * dlnkf, dkr = kr * (dlnkf - dlnKc);
+    double q = fma(kf, fw, -kr * rv);
+    double dq = fma(dkf, fw, kf * dfw) - fma(dkr, rv, kr * drv);
+    if (KIND == 1) {
+        dq = fma(dq, M, q * dM);
+        q *= M;
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            const int k = x.sp[e];
+            sD[k * BLK] = fma(x.nud[e], dq, sD[k * BLK]);
+            if (OMEGA) sW[k * BLK] = fma(x.nud[e], q, sW[k * BLK]);
         }
 #pragma unroll
-        for (int e = 0; e < kMaxSide; ++e) {
-            if (e < nr) {
-                const int k = __ldg(&rec->sp[e]);
-                const double nd = __ldg(&rec->nud[e]);
-                sW[k * BLK] = fma(nd, q, sW[k * BLK]);
-                sD[k * BLK] = fma(nd, dq, sD[k * BLK]);
-            }
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.np) {
+            const int k = x.sp[kMaxSide + e];
+            sD[k * BLK] = fma(x.nud[kMaxSide + e], dq, sD[k * BLK]);
+            if (OMEGA) sW[k * BLK] = fma(x.nud[kMaxSide + e], q, sW[k * BLK]);
         }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e) {
-            if (e < np) {
-                const int k = __ldg(&rec->sp[kMaxSide + e]);
-                const double nd = __ldg(&rec->nud[kMaxSide + e]);
-                sW[k * BLK] = fma(nd, q, sW[k * BLK]);
-                sD[k * BLK] = fma(nd, dq, sD[k * BLK]);
-            }
-        }
-    }
-
-    double h = 0.0, dh = 0.0;
-    for (int k = 0; k < K; ++k) {
-        const double w = sW[k * BLK], dw = sD[k * BLK];
-        const double cpR = nasa_cpR(nasa_range(m, k, Ti), Ti);
-        h = fma(sH[k * BLK], w, h);
-        dh = fma(sH[k * BLK] * Ti, dw, fma(cpR * dT, w, dh));
-        d_omega[(int64_t)k * ld + i] = dw;
-        if (omega) omega[(int64_t)k * ld + i] = w;
-    }
-    d_hrr[i] = -kR * dh;                              // -sum (c_p,k dT omega_k + h_k d omega_k)
-    if (hrr) hrr[i] = -kR * Ti * h;
+    acc.h = fma(q, sumh, acc.h);
+    acc.cp = fma(q, sumcp, acc.cp);
+    acc.dh = fma(dq, sumh, acc.dh);
 }
 
-template <int BLK>
-cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+template <int BLK, int KIND, bool OMEGA>
+__device__ __forceinline__ void jvp_group(const DevMech& m, int r0, int r1, const double* sC, const double* sdC,
+                                          double* sW, double* sD, const JvpPoint& Q, const double* dlnA,
+                                          const DfTab& dt, JvpAcc& acc) {
+    for (int r = r0; r < r1; ++r) jvp_reaction<BLK, KIND, OMEGA>(m, r, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+}
+
+// Per-point species rows: C_k, dC_k, then NP rows of d omega_k partials and, with OMEGA, NP
+// rows of omega_k partials.
+__host__ __device__ constexpr int jvp_rows(int np, bool omega) { return 2 + np * (omega ? 2 : 1); }
+
+template <int BLK, int NP, bool OMEGA>
+__global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                       const double* __restrict__ T, const double* __restrict__ p,
+                                                       const double* __restrict__ Y, const double* __restrict__ dlnA,
+                                                       const double* __restrict__ vT, const double* __restrict__ vY,
+                                                       double* __restrict__ omega, double* __restrict__ hrr,
+                                                       double* __restrict__ d_omega, double* __restrict__ d_hrr) {
+    extern __shared__ double smem[];
+    const DfTab dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
+    __syncthreads();
+    const int K = m.K;
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
+    double* base = smem + kMathTabDoubles + slot;
+    double* sC = base;                                   // C_k
+    double* sdC = base + (size_t)K * BLK;                // dC_k
+    double* sD0 = base + (size_t)2 * K * BLK;            // d omega_k partials, part q at row q
+    double* sW0 = base + (size_t)(2 + NP) * K * BLK;     // omega_k partials (OMEGA)
+    double* sD = sD0 + (size_t)part * K * BLK;
+    double* sW = sW0 + (size_t)part * K * BLK;
+
+    JvpPoint Q;
+    const double Ti = T[i];
+    Q.dT = vT[i];
+    Q.invT = 1.0 / Ti;
+    Q.tT = Q.dT * Q.invT;                                // dT/T
+    Q.pRT = p[i] * Q.invT * kInvR;
+    Q.dpRT = -Q.pRT * Q.tT;
+    Q.P = make_tpairs(Ti, Q.invT, dt);
+    Q.lnT = df_to_d(Q.P.lnTd);
+    double s = 0.0, ds = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double iw = __ldg(m.invW + k);
+        s += Y[(int64_t)k * ld + i] * iw;
+        ds = fma(vY[(int64_t)k * ld + i], iw, ds);
+    }
+    const double rho = Q.pRT / s;
+    const double arho = -Q.tT - ds / s;                  // d rho / rho
+    for (int k = part; k < K; k += NP) {
+        const double iw = __ldg(m.invW + k);
+        const double c = Y[(int64_t)k * ld + i] * iw * rho;
+        sC[k * BLK] = c;
+        sdC[k * BLK] = fma(c, arho, rho * vY[(int64_t)k * ld + i] * iw);
+    }
+    for (int k = 0; k < K; ++k) {
+        sD[k * BLK] = 0.0;
+        if (OMEGA) sW[k * BLK] = 0.0;
+    }
+    if (NP > 1) __syncthreads();
+
+    JvpAcc acc;
+    int a, b;
+    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+    slice<NP>(0, e1, part, a, b);
+    jvp_group<BLK, 0, OMEGA>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    slice<NP>(e1, t1, part, a, b);
+    jvp_group<BLK, 1, OMEGA>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    slice<NP>(t1, m.R, part, a, b);
+    jvp_group<BLK, 2, OMEGA>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    if (NP > 1) __syncthreads();
+
+    for (int k = part; k < K; k += NP) {
+        double dw = sD0[k * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
+        if (live) d_omega[(int64_t)k * ld + i] = dw;
+        if (OMEGA) {
+            double w = sW0[k * BLK];
+#pragma unroll
+            for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
+            if (live) omega[(int64_t)k * ld + i] = w;
+        }
+    }
+    if constexpr (NP > 1) {
+        // C_k is dead: rows 3q, 3q+1, 3q+2 (3 NP <= K) take part q's sums, added in part order
+        sC[(3 * part) * BLK] = acc.h;
+        sC[(3 * part + 1) * BLK] = acc.cp;
+        sC[(3 * part + 2) * BLK] = acc.dh;
+        __syncthreads();
+        if (part != 0) return;
+        acc.h = sC[0];
+        acc.cp = sC[BLK];
+        acc.dh = sC[2 * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            acc.h += sC[(3 * q) * BLK];
+            acc.cp += sC[(3 * q + 1) * BLK];
+            acc.dh += sC[(3 * q + 2) * BLK];
+        }
+    }
+    if (live) {
+        d_hrr[i] = -kR * fma(Q.dT, acc.cp, Ti * acc.dh);
+        if (hrr) hrr[i] = -kR * Ti * acc.h;
+    }
+}
+
+// ---------------------------------------------------------------- launch shapes
+struct Shape {
+    int blk, np;
+};
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <bool OMEGA, int S>
+constexpr auto kernel_of() {
+    return jvp_kernel<kShapes[S].blk, kShapes[S].np, OMEGA>;
+}
+
+template <bool OMEGA, int... S>
+const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
+    const void* ptrs[] = {(const void*)kernel_of<OMEGA, S>()...};
+    return ptrs[idx];
+}
+
+size_t jvp_smem(int K, const Shape& sh, bool omega) {
+    return (size_t)kMathTabDoubles * sizeof(double) + (size_t)jvp_rows(sh.np, omega) * K * sh.blk * sizeof(double);
+}
+
+struct Plan {
+    int dev, K;
+    bool omega;
+    int idx;
+};
+std::mutex g_plan_mu;
+std::vector<Plan> g_plans;
+
+// The shape with the most resident warps per SM, fewer parts on ties (cached per device, K
+// and output set).
+template <bool OMEGA>
+int plan_shape(int K) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const Plan& q : g_plans)
+            if (q.dev == dev && q.K == K && q.omega == OMEGA) return q.idx;
+    }
+    int per_block = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < kNumShapes; ++c) {
+        const Shape& sh = kShapes[c];
+        if (3 * sh.np > K && sh.np > 1) continue;
+        const size_t bytes = jvp_smem(K, sh, OMEGA);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<OMEGA>(c, std::make_integer_sequence<int, kNumShapes>{});
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
+            continue;
+        const int warps = blocks * sh.blk * sh.np / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best = c;
+        }
+    }
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back({dev, K, OMEGA, best});
+    }
+    return best;
+}
+
+template <bool OMEGA, int... S>
+cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
+                       const double* T, const double* p, const double* Y, const double* dlnA, const double* vT,
+                       const double* vY, double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    ((S == idx ? (void)(e = [&] {
+        constexpr Shape sh = kShapes[S];
+        auto kern = kernel_of<OMEGA, S>();
+        const size_t smem = jvp_smem(m.K, sh, OMEGA);
+        cudaError_t r = ensure_smem((const void*)kern, smem);
+        if (r != cudaSuccess) return r;
+        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, vT, vY,
+                                                                                  omega, hrr, d_omega, d_hrr);
+        return cudaGetLastError();
+    }())
+               : (void)0),
+     ...);
+    return e;
+}
+
+template <bool OMEGA>
+cudaError_t launch_o(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
                      const double* dlnA, const double* vT, const double* vY, double* omega, double* hrr,
-                     double* d_omega, double* d_hrr, size_t smem, cudaStream_t s) {
-    auto kern = jvp_kernel<BLK>;
-    cudaError_t e = ensure_smem((const void*)kern, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = (n + BLK - 1) / BLK;
-    kern<<<(unsigned)grid, BLK, smem, s>>>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr);
-    return cudaGetLastError();
+                     double* d_omega, double* d_hrr, cudaStream_t s) {
+    const int idx = plan_shape<OMEGA>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<OMEGA>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, vT, vY,
+                             omega, hrr, d_omega, d_hrr, s);
 }
 
 }  // namespace
@@ -242,17 +387,9 @@ cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, c
 cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* vT, const double* vY, double* omega,
                        double* hrr, double* d_omega, double* d_hrr, cudaStream_t s) {
-    const size_t per_thread = (size_t)5 * m.K * sizeof(double);
-    const size_t tab = kMathTabDoubles * sizeof(double);
-    const int blk = pick_block_occupancy(per_thread, tab);
-    if (!blk) return cudaErrorInvalidConfiguration;
-    const size_t smem = per_thread * blk + tab;
-    switch (blk) {
-        case 128: return launch_t<128>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, smem, s);
-        case 64: return launch_t<64>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, smem, s);
-        case 32: return launch_t<32>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, smem, s);
-    }
-    return cudaErrorInvalidConfiguration;
+    static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
+    if (omega) return launch_o<true>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
+    return launch_o<false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
 }
 
 }  // namespace nk

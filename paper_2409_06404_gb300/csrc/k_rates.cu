@@ -26,31 +26,12 @@
 #include <utility>
 #include <vector>
 
-#include "nk_internal.cuh"
+#include "nk_rxn.cuh"
 
 namespace nk {
 namespace {
 
-constexpr double kLnP0overR = 9.408091968961747;   // ln(101325 Pa / (8.314462618 J/mol/K))
-
 enum { kNative = 0, kMixed = 1, kDF = 2 };
-
-// double constants of the definitions as float pairs (hi = nearest float, lo = remainder)
-__device__ __forceinline__ dfl dfc_lnp0r() { return {9.40809154510498f, 4.2385676124467864e-07f}; }
-__device__ __forceinline__ dfl dfc_invln10() { return {0.4342944920063019f, -1.0103049952192578e-08f}; }
-__device__ __forceinline__ dfl dfc_ln10() { return {2.3025851249694824f, -3.1975435632602967e-08f}; }
-__device__ __forceinline__ dfl dfc_m0_4() { return {-0.4000000059604645f, 5.9604645663569045e-09f}; }
-__device__ __forceinline__ dfl dfc_m0_67() { return {-0.6700000166893005f, 1.668930060816365e-08f}; }
-__device__ __forceinline__ dfl dfc_m1_27() { return {-1.2699999809265137f, -1.907348590179936e-08f}; }
-__device__ __forceinline__ dfl dfc_m0_14() { return {-0.14000000059604645f, 5.9604643443123e-10f}; }
-__device__ __forceinline__ dfl dfl_of(float2 v) { return {v.x, v.y}; }
-
-// double-float tables staged in shared memory for the kDF form
-struct DfTab {
-    const float2* e2;   // 2^(j/128)
-    const float2* rc;   // 1/c_j
-    const float2* lc;   // -log(1/c_j)
-};
 
 // exp of a single-precision argument, returned in double: x = n ln2 + r (Cody-Waite two-term
 // split of ln 2), expf(r) with |r| <= ln2/2, and 2^n added to the exponent field of the
@@ -65,50 +46,11 @@ __device__ __forceinline__ double exp_f32_to_f64(float x) {
     return __longlong_as_double(__double_as_longlong(e) + ((long long)(int)nf << 52));
 }
 
-struct Rxn {
-    double lnA, beta, EaR, dnu;
-    double nud[2 * kMaxSide];
-    int type, nr, np, aux, orig, eff0, eff1;
-    int sp[2 * kMaxSide];
-    int nu[2 * kMaxSide];
-};
-
-__device__ __forceinline__ Rxn load_rxn(const RxnRec* rec) {
-    Rxn x;
-    const double2* d = reinterpret_cast<const double2*>(rec);
-    const double2 a = __ldg(d), b = __ldg(d + 1);
-    x.lnA = a.x;
-    x.beta = a.y;
-    x.EaR = b.x;
-    x.dnu = b.y;
-#pragma unroll
-    for (int j = 0; j < kMaxSide; ++j) {
-        const double2 v = __ldg(d + 2 + j);
-        x.nud[2 * j] = v.x;
-        x.nud[2 * j + 1] = v.y;
-    }
-    const int4* q = reinterpret_cast<const int4*>(rec) + 6;
-    const int4 h = __ldg(q), h2 = __ldg(q + 1), s0 = __ldg(q + 2), s1 = __ldg(q + 3), u0 = __ldg(q + 4),
-               u1 = __ldg(q + 5);
-    x.type = h.x;
-    x.nr = h.y;
-    x.np = h.z;
-    x.aux = h.w;
-    x.orig = h2.x;
-    x.eff0 = h2.y;
-    x.eff1 = h2.z;
-    x.sp[0] = s0.x; x.sp[1] = s0.y; x.sp[2] = s0.z; x.sp[3] = s0.w;
-    x.sp[4] = s1.x; x.sp[5] = s1.y; x.sp[6] = s1.z; x.sp[7] = s1.w;
-    x.nu[0] = u0.x; x.nu[1] = u0.y; x.nu[2] = u0.z; x.nu[3] = u0.w;
-    x.nu[4] = u1.x; x.nu[5] = u1.y; x.nu[6] = u1.z; x.nu[7] = u1.w;
-    return x;
-}
-
 // Per-point quantities shared by all reactions.
 struct Pt {
     double T, lnT, invT, pRT, lnP0RT;
     float Tf, lnTf, invTf;
-    dfl Td, lnTd, invTd, lnP0RTd;    // kDF form
+    TPairs tp;                       // kDF form
 };
 
 // sum_k nu_k g_k/RT (products minus reactants) and the concentration products of each side;
@@ -230,43 +172,32 @@ __device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& 
     return q;
 }
 
-// kDF form: the Gibbs sum in pairs (g_k/RT stored as pairs in sG), products in double.
+// kDF form: the concentration products of each side in double (the Gibbs sum comes from the
+// reaction's thermo groups).
 template <int BLK>
-__device__ __forceinline__ void gibbs_products_df(const Rxn& x, const double* sC, const float2* sG, dfl& sumg,
-                                                  double& fw, double& rv) {
+__device__ __forceinline__ void products(const Rxn& x, const double* sC, double& fw, double& rv) {
     {
-        const int k = x.sp[0], nu = x.nu[0];
-        const double c = sC[k * BLK];
+        const double c = sC[x.sp[0] * BLK];
         fw = c;
-        for (int j = 1; j < nu; ++j) fw *= c;
-        const dfl g = dfl_of(sG[k * BLK]);
-        sumg = nu == 1 ? df_neg(g) : df_mul_f(g, -__int2float_rn(nu));
+        for (int j = 1; j < x.nu[0]; ++j) fw *= c;
     }
 #pragma unroll
-    for (int e = 1; e < kMaxSide; ++e) {
+    for (int e = 1; e < kMaxSide; ++e)
         if (e < x.nr) {
-            const int k = x.sp[e], nu = x.nu[e];
-            const double c = sC[k * BLK];
-            for (int j = 0; j < nu; ++j) fw *= c;
-            const dfl g = dfl_of(sG[k * BLK]);
-            sumg = df_add(sumg, nu == 1 ? df_neg(g) : df_mul_f(g, -__int2float_rn(nu)));
+            const double c = sC[x.sp[e] * BLK];
+            for (int j = 0; j < x.nu[e]; ++j) fw *= c;
         }
+    {
+        const double c = sC[x.sp[kMaxSide] * BLK];
+        rv = c;
+        for (int j = 1; j < x.nu[kMaxSide]; ++j) rv *= c;
     }
 #pragma unroll
-    for (int e = 0; e < kMaxSide; ++e) {
+    for (int e = 1; e < kMaxSide; ++e)
         if (e < x.np) {
-            const int k = x.sp[kMaxSide + e], nu = x.nu[kMaxSide + e];
-            const double c = sC[k * BLK];
-            if (e == 0) {
-                rv = c;
-                for (int j = 1; j < nu; ++j) rv *= c;
-            } else {
-                for (int j = 0; j < nu; ++j) rv *= c;
-            }
-            const dfl g = dfl_of(sG[k * BLK]);
-            sumg = df_add(sumg, nu == 1 ? g : df_mul_f(g, __int2float_rn(nu)));
+            const double c = sC[x.sp[kMaxSide + e] * BLK];
+            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) rv *= c;
         }
-    }
 }
 
 // Troe factor F * P_r/(1+P_r) with the exponent arithmetic in pairs.
@@ -277,9 +208,9 @@ __device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl 
     const float4 t2 = __ldg(m.troe_df + 3 * aux + 2);    // (1/T1, T2)
     const dfl lnPr = df_add(df_add(lnk0, df_neg(lnkinf)), log_df(M, dt.rc, dt.lc));
     const double a = __ldg(&t->a);
-    double Fc = (1.0 - a) * exp_df_d(df_neg(df_mul(P.Td, dfl{t1.z, t1.w})), dt.e2) +
-                a * exp_df_d(df_neg(df_mul(P.Td, dfl{t2.x, t2.y})), dt.e2);
-    if (__ldg(&t->hasT2) != 0.0) Fc += exp_df_d(df_neg(df_mul(dfl{t2.z, t2.w}, P.invTd)), dt.e2);
+    double Fc = (1.0 - a) * exp_df_d(df_neg(df_mul(P.tp.Td, dfl{t1.z, t1.w})), dt.e2) +
+                a * exp_df_d(df_neg(df_mul(P.tp.Td, dfl{t2.x, t2.y})), dt.e2);
+    if (__ldg(&t->hasT2) != 0.0) Fc += exp_df_d(df_neg(df_mul(dfl{t2.z, t2.w}, P.tp.invTd)), dt.e2);
     const dfl lFc = df_mul(log_df(Fc, dt.rc, dt.lc), dfc_invln10());
     const dfl c = df_add(dfc_m0_4(), df_mul(lFc, dfc_m0_67()));
     const dfl nn = df_add(dfl{0.75f, 0.0f}, df_mul(lFc, dfc_m1_27()));
@@ -291,20 +222,15 @@ __device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl 
 
 template <int BLK, int KIND>
 __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const double* sC,
-                                                      const float2* sG, const Pt& P, const double* dlnA,
-                                                      const DfTab& dt) {
+                                                      const Pt& P, const double* dlnA, const DfTab& dt) {
     double fw, rv;
-    dfl sumg;
-    gibbs_products_df<BLK>(x, sC, sG, sumg, fw, rv);
-    const float4 a0 = __ldg(m.rxn_df + 2 * r), a1 = __ldg(m.rxn_df + 2 * r + 1);
-    const dfl lnKc = df_add(df_mul_f(P.lnP0RTd, a1.z), df_neg(sumg));   // ln K_c
-    dfl lnkf = df_fma(dfl{a0.z, a0.w}, P.lnTd, dfl{a0.x, a0.y});          // ln A + beta ln T
-    lnkf = df_fma(dfl{-a1.x, -a1.y}, P.invTd, lnkf);                     //   - Ea/(R T)
+    products<BLK>(x, sC, fw, rv);
+    dfl sumg, unused_h, unused_cp;
+    rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
+    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, (float)x.dnu), df_neg(sumg));   // ln K_c
     dfl shift{0.0f, 0.0f};
-    if (dlnA) {
-        shift = df_split(__ldg(dlnA + x.orig));
-        lnkf = df_add(lnkf, shift);
-    }
+    if (dlnA) shift = df_split(__ldg(dlnA + x.orig));
+    const dfl lnkf = ln_kf_df(m, r, P.tp, shift, dlnA != nullptr);
     double M = 0.0;
     if (KIND != 0) {
         M = P.pRT;
@@ -314,8 +240,8 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
     if constexpr (KIND == 2) {
         const float4 t0 = __ldg(m.troe_df + 3 * x.aux);          // (lnA0, beta0)
         const float4 t1 = __ldg(m.troe_df + 3 * x.aux + 1);      // (Ea0/R, 1/T3)
-        dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.lnTd, dfl{t0.x, t0.y});
-        lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.invTd, lnk0);
+        dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.tp.lnTd, dfl{t0.x, t0.y});
+        lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.tp.invTd, lnk0);
         if (dlnA) lnk0 = df_add(lnk0, shift);
         kf = M == 0.0 ? 0.0 : exp_df_d(lnkf, dt.e2) * troe_factor_df(m, x.aux, lnkf, lnk0, M, P, dt);
         kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
@@ -348,7 +274,7 @@ template <int BLK, int PREC, int KIND>
 __device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, const double* sC, const double* sG,
                                        const Pt& P, const double* dlnA, const MathTab& mt, const DfTab& dt) {
     if constexpr (PREC == kDF)
-        return rate_of_progress_df<BLK, KIND>(m, x, r, sC, reinterpret_cast<const float2*>(sG), P, dlnA, dt);
+        return rate_of_progress_df<BLK, KIND>(m, x, r, sC, P, dlnA, dt);
     else
         return rate_of_progress<BLK, PREC, KIND>(m, x, r, sC, sG, P, dlnA, mt);
 }
@@ -365,53 +291,30 @@ __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1,
     }
 }
 
-// Part `part` of NP takes the contiguous slice [a + len*part/NP, a + len*(part+1)/NP) of the
-// kind's range [a, b).
-template <int NP>
-__device__ __forceinline__ void slice(int a, int b, int part, int& r0, int& r1) {
-    const int len = b - a;
-    r0 = a + (len * part) / NP;
-    r1 = a + (len * (part + 1)) / NP;
-}
-
-// g_k/RT = a1 (1 - ln T) + T (c1 + T (c2 + T (c3 + T c4))) + a6/T - a7, in pairs
-__device__ __forceinline__ dfl nasa_gRT_df(const DevMech& m, int k, const Pt& P) {
-    const float2* c = m.nasa_df + ((size_t)k * 2 + (P.T <= __ldg(m.Tmid + k) ? 0 : 1)) * 8;
-    dfl acc = dfl_of(__ldg(c + 4));
-    acc = df_fma(acc, P.Td, dfl_of(__ldg(c + 3)));
-    acc = df_fma(acc, P.Td, dfl_of(__ldg(c + 2)));
-    acc = df_fma(acc, P.Td, dfl_of(__ldg(c + 1)));
-    acc = df_mul(acc, P.Td);
-    acc = df_fma(dfl_of(__ldg(c + 0)), df_add(dfl{1.0f, 0.0f}, df_neg(P.lnTd)), acc);
-    acc = df_fma(dfl_of(__ldg(c + 5)), P.invTd, acc);
-    return df_add(acc, dfl_of(__ldg(c + 6)));
+// Per-point species arrays: C_k, then g_k/RT (native and mixed forms only), then NP rows of
+// omega_k partials.
+template <int PREC>
+__host__ __device__ constexpr int shared_rows() {
+    return PREC == kDF ? 1 : 2;
 }
 
 // BLK points per block, NP parts (warps) per point: thread (part, slot) works on point
-// blockIdx.x * BLK + slot.  The parts of a point share its C_k and g_k/RT, each walks its own
-// slice of every kind and accumulates into its own omega_k partials; the partials are added in
-// part order, so results do not depend on scheduling.
+// blockIdx.x * BLK + slot.  The parts of a point share its C_k (and g_k/RT), each walks its
+// own slice of every kind and accumulates into its own omega_k partials; the partials are
+// added in part order, so results do not depend on scheduling.
 template <int BLK, int NP, int PREC>
 __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                          const double* __restrict__ T, const double* __restrict__ p,
                                                          const double* __restrict__ Y,
                                                          const double* __restrict__ dlnA,
                                                          double* __restrict__ omega, double* __restrict__ hrr) {
-    constexpr int NT = BLK * NP;
     extern __shared__ double smem[];
     MathTab mt{};
     DfTab dt{};
-    if constexpr (PREC == kDF) {
-        float2* t = reinterpret_cast<float2*>(smem);
-        for (int j = threadIdx.x; j < kExpTab; j += NT) {
-            t[j] = __ldg(m.df_exp_tab + j);
-            t[kExpTab + j] = __ldg(m.df_log_rc + j);
-            t[2 * kExpTab + j] = __ldg(m.df_log_lc + j);
-        }
-        dt = DfTab{t, t + kExpTab, t + 2 * kExpTab};
-    } else {
+    if constexpr (PREC == kDF)
+        dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
+    else
         mt = stage_math_tables(smem, m.mtab);
-    }
     __syncthreads();
     const int K = m.K;
     const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
@@ -420,8 +323,8 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
     double* sC = smem + kMathTabDoubles + slot;                       // C_k       at sC[k * BLK]
-    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (a pair in the kDF form)
-    double* sW0 = smem + kMathTabDoubles + (size_t)2 * K * BLK + slot;
+    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (not in the kDF form)
+    double* sW0 = smem + kMathTabDoubles + (size_t)shared_rows<PREC>() * K * BLK + slot;
     double* sW = sW0 + (size_t)part * K * BLK;                        // this part's omega_k partials
 
     Pt P;
@@ -429,10 +332,7 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     P.invT = 1.0 / P.T;
     P.pRT = p[i] * P.invT * kInvR;                     // p/(RT) = sum_k C_k
     if constexpr (PREC == kDF) {
-        P.Td = df_split(P.T);
-        P.invTd = df_split(P.invT);
-        P.lnTd = log_df(P.T, dt.rc, dt.lc);
-        P.lnP0RTd = df_add(dfc_lnp0r(), df_neg(P.lnTd));
+        P.tp = make_tpairs(P.T, P.invT, dt);
     } else {
         P.lnT = flog(P.T, mt);
         P.lnP0RT = kLnP0overR - P.lnT;                 // ln(p0/(R T))
@@ -445,12 +345,7 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
     for (int k = part; k < K; k += NP) {
         sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
-        if constexpr (PREC == kDF) {
-            const dfl g = nasa_gRT_df(m, k, P);
-            reinterpret_cast<float2*>(sG)[k * BLK] = make_float2(g.h, g.l);   // 8-byte slot, like a double
-        } else {
-            sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
-        }
+        if constexpr (PREC != kDF) sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
     }
     for (int k = 0; k < K; ++k) sW[k * BLK] = 0.0;
     if (NP > 1) __syncthreads();
@@ -522,10 +417,11 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech&
     return e;
 }
 
-// Shared bytes of a block: the staged tables, then C_k and g_k/RT per point and NP rows of
-// omega_k partials per point.
+// Shared bytes of a block: the staged tables, then the per-point species arrays.
+template <int PREC>
 size_t rates_smem(int K, const Shape& sh) {
-    return (size_t)kMathTabDoubles * sizeof(double) + (size_t)(2 + sh.np) * K * sh.blk * sizeof(double);
+    return (size_t)kMathTabDoubles * sizeof(double) +
+           (size_t)(shared_rows<PREC>() + sh.np) * K * sh.blk * sizeof(double);
 }
 
 // The shape with the most resident warps per SM (CUDA's occupancy calculator: shared memory,
@@ -553,7 +449,7 @@ int plan_shape(int K) {
     for (int c = 0; c < kNumShapes; ++c) {
         const Shape& sh = kShapes[c];
         if (sh.np > K) continue;
-        const size_t bytes = rates_smem(K, sh);
+        const size_t bytes = rates_smem<PREC>(K, sh);
         if (bytes > (size_t)per_block) continue;
         const void* kern = kernel_ptr<PREC>(c, seq);
         if (ensure_smem(kern, bytes) != cudaSuccess) continue;
@@ -579,7 +475,7 @@ cudaError_t launch_prec(const DevMech& m, int64_t n, int64_t ld, const double* T
     const int idx = plan_shape<PREC>(m.K);
     if (idx < 0) return cudaErrorInvalidConfiguration;
     return launch_idx<PREC>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, omega, hrr,
-                            rates_smem(m.K, kShapes[idx]), s);
+                            rates_smem<PREC>(m.K, kShapes[idx]), s);
 }
 
 }  // namespace
@@ -588,7 +484,7 @@ cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* 
                          const double* Y, const double* dlnA, double* omega, double* hrr, int precision,
                          cudaStream_t s) {
     // the staged tables (kMathTabDoubles doubles) cover the kDF tables too (3 x 128 pairs)
-    static_assert(3 * kExpTab * sizeof(float2) <= kMathTabDoubles * sizeof(double), "table space");
+    static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
     if (precision == NK_MIXED) return launch_prec<kMixed>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
     if (precision == NK_FP64_NATIVE) return launch_prec<kNative>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
     return launch_prec<kDF>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);

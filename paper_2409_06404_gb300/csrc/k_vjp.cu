@@ -1,28 +1,32 @@
 // Vector-Jacobian product of (omega_k, heat release): reverse-mode differentiation written
 // out by hand, the exact transpose of the JVP (gradients for mechanism calibration and for
-// adjoint solves).  One thread per point, rates of progress recomputed in registers.
+// adjoint solves).  Rates of progress are recomputed in registers, nothing per reaction is
+// stored.
 //
 // Single pass over the reactions: with hrr = -sum_k h_k omega_k and omega_k = sum_r nu_kr q_r,
-//   qbar_r = sum_k nu_kr (bar_omega_k - bar_hrr h_k)
-//   Tbar  += -bar_hrr R q_r sum_k nu_kr c_p,k/R          (temperature dependence of h_k)
-// so the forward values omega_k are never needed.  The ln A gradient of a point is
-// qbar_r q_r (a shift of ln A_r scales k_f and k_r alike, and both limits of a Troe reaction);
-// it is summed over the points of a warp by shuffles, over the warps of a block in shared
-// memory, and over blocks by a second kernel in a fixed order: deterministic, no atomics.
+//   qbar_r = sum_k nu_kr bar_omega_k - bar_hrr R T (sum_k nu_kr h_k/RT),
+//   Tbar  += -bar_hrr R q_r (sum_k nu_kr c_p,k/R)          (temperature dependence of h_k),
+// so the forward values omega_k are never needed, and the reaction sums of h/RT and c_p/R
+// come from the reaction's thermo groups.  The ln A gradient of a point is qbar_r q_r (a shift
+// of ln A_r scales k_f and k_r alike, and both limits of a Troe reaction); it is summed over
+// the points of a warp by shuffles, over the point tiles of a block in shared memory and over
+// blocks by a second kernel in a fixed order: deterministic, no atomics.
+//
+// FP64 form as the rates kernel (exponent chains in double-float pairs, everything else in
+// double; the falloff chain in double with pair-based exp/log).  Layout: blocks of 32 points,
+// NP warps per point sharing C_k and bar_omega_k in shared memory, each warp accumulating its
+// own Cbar_k partials, added in part order; a persistent grid walks the point tiles.
+#include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
-#include "nk_internal.cuh"
+#include "nk_rxn.cuh"
 
 namespace nk {
 namespace {
 
-constexpr int kVjpMaxBlocks = 1024;
-
-int vjp_block(const DevMech& m) {
-    const size_t per_thread = (size_t)5 * m.K * sizeof(double);
-    // per block the math tables, per warp its ln A accumulators
-    return pick_block_occupancy(per_thread, kMathTabDoubles * sizeof(double), (size_t)m.R * sizeof(double));
-}
+constexpr int kVjpBlk = 32;   // points per block: one warp per part
 
 // prod of p[0..n) (returned) and, in ex[e], the product of all entries but e (n <= 4, uniform)
 __device__ __forceinline__ double exclusive_products(const double* p, int n, double* ex) {
@@ -52,279 +56,382 @@ __device__ __forceinline__ double exclusive_products(const double* p, int n, dou
     }
 }
 
-template <int BLK, bool WANT_G>
-__global__ void __launch_bounds__(BLK) vjp_kernel(const DevMech m, const int64_t n, const int64_t ld,
-                                                  const double* __restrict__ T, const double* __restrict__ p,
-                                                  const double* __restrict__ Y, const double* __restrict__ dlnA,
-                                                  const double* __restrict__ bar_omega,
-                                                  const double* __restrict__ bar_hrr, double* __restrict__ gT,
-                                                  double* __restrict__ gY, double* __restrict__ ws) {
-    extern __shared__ double smem_all[];
-    const MathTab mt = stage_math_tables(smem_all, m.mtab);
-    __syncthreads();
-    double* smem = smem_all + kMathTabDoubles;
-    const int K = m.K, R = m.R;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double* sC = smem + tid;                          // C_k
-    double* sG = smem + (size_t)K * BLK + tid;        // g_k/RT
-    double* sH = smem + (size_t)2 * K * BLK + tid;    // h_k/RT
-    double* sP = smem + (size_t)3 * K * BLK + tid;    // c_p,k/R
-    double* sB = smem + (size_t)4 * K * BLK + tid;    // Cbar_k
-    double* gw = smem + (size_t)5 * K * BLK + (size_t)warp * R;   // per-warp ln A partial sums
-    if (WANT_G) {
-        for (int r = lane; r < R; r += 32) gw[r] = 0.0;
-        __syncwarp();
-    }
+struct VjpPoint {
+    TPairs P;
+    double invT, lnT, pRT, hb, hbRT;
+    bool valid;
+};
 
-    for (int64_t base = (int64_t)blockIdx.x * BLK; base < n; base += (int64_t)gridDim.x * BLK) {
-        const int64_t i0 = base + tid;
-        const bool valid = i0 < n;
-        const int64_t i = valid ? i0 : n - 1;         // idle lanes shadow the last point
-        const double Ti = T[i], pi = p[i];
-        const double lnT = flog(Ti, mt), invT = 1.0 / Ti;
-        const double pRT = pi * invT * kInvR;
-        const bool hb_any = bar_hrr != nullptr;            // uniform: heat-release cotangent given
-        const double hb = hb_any ? bar_hrr[i] : 0.0;
-        const double hbRT = hb * kR * Ti;
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) {
-            const double yw = Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
-            sC[k * BLK] = yw;
-            s += yw;
-        }
-        const double rho = pRT / s;
-        for (int k = 0; k < K; ++k) {
-            const double* c = nasa_range(m, k, Ti);
-            sC[k * BLK] *= rho;
-            sG[k * BLK] = nasa_gRT(c, Ti, lnT, invT);
-            sH[k * BLK] = nasa_hRT(c, Ti, invT);
-            if (hb_any) sP[k * BLK] = nasa_cpR(c, Ti);
-            sB[k * BLK] = 0.0;
-        }
-        const double lnP0RT = 9.408091968961747 - lnT;   // ln(p0/(R T)), ln(101325/8.314462618) = 9.408...
-        double Tbar = 0.0;
-
-        for (int r = 0; r < R; ++r) {
-            const RxnRec* rec = m.rxn + r;
-            const int type = __ldg(&rec->type), nr = __ldg(&rec->nr), np = __ldg(&rec->np);
-            const int orig = __ldg(&rec->orig);
-            double lnA = __ldg(&rec->lnA), shift = 0.0;
-            if (dlnA) {
-                shift = __ldg(dlnA + orig);
-                lnA += shift;
-            }
-            // sums over the entries (signed coefficients) and the concentration powers
-            double sumg = 0.0, sumh = 0.0, sumcp = 0.0, wsum = 0.0;
-            double cR[kMaxSide], pR[kMaxSide], cP[kMaxSide], pP[kMaxSide];
+template <int KIND, bool WANT_G, bool HB>
+__device__ __forceinline__ void vjp_reaction(const DevMech& m, int r, const double* sC, const double* sWb, double* sB,
+                                             double* gw, const VjpPoint& Q, const double* dlnA, const DfTab& dt,
+                                             double& Tbar) {
+    constexpr int BLK = kVjpBlk;
+    const Rxn x = load_rxn(m.rxn + r);
+    // concentration powers of the entries and sum_k nu_k bar_omega_k
+    double wsum = 0.0;
+    double cR[kMaxSide], pR[kMaxSide], cP[kMaxSide], pP[kMaxSide];
 #pragma unroll
-            for (int e = 0; e < kMaxSide; ++e) {
-                cR[e] = pR[e] = cP[e] = pP[e] = 1.0;
-                if (e < nr) {
-                    const int k = __ldg(&rec->sp[e]), nu = __ldg(&rec->nu[e]);
-                    const double nd = __ldg(&rec->nud[e]);
-                    sumg = fma(nd, sG[k * BLK], sumg);
-                    sumh = fma(nd, sH[k * BLK], sumh);
-                    if (hb_any) sumcp = fma(nd, sP[k * BLK], sumcp);
-                    wsum = fma(nd, bar_omega[(int64_t)k * ld + i], wsum);
-                    const double c = sC[k * BLK];
-                    double pw = c;
-                    for (int j = 1; j < nu; ++j) pw *= c;
-                    cR[e] = c;
-                    pR[e] = pw;
-                }
-                if (e < np) {
-                    const int k = __ldg(&rec->sp[kMaxSide + e]), nu = __ldg(&rec->nu[kMaxSide + e]);
-                    const double nd = __ldg(&rec->nud[kMaxSide + e]);
-                    sumg = fma(nd, sG[k * BLK], sumg);
-                    sumh = fma(nd, sH[k * BLK], sumh);
-                    if (hb_any) sumcp = fma(nd, sP[k * BLK], sumcp);
-                    wsum = fma(nd, bar_omega[(int64_t)k * ld + i], wsum);
-                    const double c = sC[k * BLK];
-                    double pw = c;
-                    for (int j = 1; j < nu; ++j) pw *= c;
-                    cP[e] = c;
-                    pP[e] = pw;
-                }
-            }
-            // products of all entries but one: exR[e] = prod_{f != e} pR[f] (uniform switch)
-            double exR[kMaxSide], exP[kMaxSide];
-            double fw = exclusive_products(pR, nr, exR);
-            double rv = exclusive_products(pP, np, exP);
-            const double dnu = __ldg(&rec->dnu);
-            const double lnKc = fma(dnu, lnP0RT, -sumg);
-            const double beta = __ldg(&rec->beta), EaR = __ldg(&rec->EaR);
-            const double lnkf = fma(-EaR, invT, fma(beta, lnT, lnA));
-
-            double M = 0.0;
-            if (type != NK_RXN_ELEMENTARY) {
-                M = pRT;
-                const int e0 = __ldg(&rec->eff0), e1 = __ldg(&rec->eff1);
-                for (int j = e0; j < e1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
-            }
-
-            // ---- primal (kept values for the adjoint)
-            double kf;
-            double tr_g = 0.0, tr_lF = 0.0, tr_f1 = 0.0, tr_den = 1.0, tr_u = 0.0, tr_v = 1.0, tr_nn = 0.0,
-                   tr_Fc = 1.0, tr_dFc = 0.0;
-            const TroeRec* t = nullptr;
-            if (type == NK_RXN_TROE) {
-                t = m.troe + __ldg(&rec->aux);
-                const double lnk0 =
-                    fma(-__ldg(&t->Ea0R), invT, fma(__ldg(&t->beta0), lnT, __ldg(&t->lnA0) + shift));
-                if (M == 0.0) {
-                    kf = 0.0;
-                } else {
-                    const double lnPr = lnk0 - lnkf + flog(M, mt);
-                    const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-                    const double e3 = fexp(-Ti * i3, mt), e1 = fexp(-Ti * i1, mt);
-                    tr_Fc = (1.0 - a) * e3 + a * e1;
-                    tr_dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1);
-                    if (__ldg(&t->hasT2) != 0.0) {
-                        const double T2 = __ldg(&t->T2), e2 = fexp(-T2 * invT, mt);
-                        tr_Fc += e2;
-                        tr_dFc = fma(T2 * invT * invT, e2, tr_dFc);
-                    }
-                    const double lFc = flog(tr_Fc, mt) * kInvLn10;
-                    const double c = fma(-0.67, lFc, -0.4);
-                    tr_nn = fma(-1.27, lFc, 0.75);
-                    tr_u = fma(lnPr, kInvLn10, c);
-                    tr_v = fma(-0.14, tr_u, tr_nn);
-                    tr_f1 = tr_u / tr_v;
-                    tr_den = fma(tr_f1, tr_f1, 1.0);
-                    tr_lF = lFc / tr_den;
-                    tr_g = 1.0 / (1.0 + fexp(-lnPr, mt));
-                    kf = fexp(lnkf, mt) * tr_g * fexp(tr_lF * kLn10, mt);
-                }
-            } else {
-                kf = fexp(lnkf, mt);
-            }
-            const double E = fexp(-lnKc, mt);
-            const double kr = kf * E;
-            const double qc = fma(kf, fw, -kr * rv);
-            const double q = (type == NK_RXN_THIRD_BODY) ? qc * M : qc;
-
-            // ---- adjoint
-            const double qbar = hb_any ? fma(-hbRT, sumh, wsum) : wsum;   // sum nu (bar_omega - bar_hrr h)
-            if (hb_any) Tbar = fma(-hb * kR * q, sumcp, Tbar);
-            if (WANT_G) {
-                double gl = valid ? qbar * q : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) gl += __shfl_xor_sync(0xffffffffu, gl, o);
-                if (lane == 0) gw[orig] += gl;
-            }
-            double Mbar = 0.0, qcbar = qbar;
-            if (type == NK_RXN_THIRD_BODY) {
-                qcbar = qbar * M;
-                Mbar = qbar * qc;
-            }
-            const double krbar = -qcbar * rv;
-            const double kfbar = fma(krbar, E, qcbar * fw);
-            const double fwbar = qcbar * kf, rvbar = -qcbar * kr;
-            const double lnKcbar = -krbar * kr;
-            Tbar = fma(lnKcbar * invT, sumh - dnu, Tbar);        // through g_k/RT(T) and ln(p0/RT)
-#pragma unroll
-            for (int e = 0; e < kMaxSide; ++e) {
-                if (e < nr) {
-                    const int nu = __ldg(&rec->nu[e]);
-                    double d = exR[e];                           // d fw / d C_e = nu C_e^(nu-1) prod_{f!=e}
-                    if (nu > 1) {
-                        d *= -__ldg(&rec->nud[e]);
-                        for (int j = 1; j < nu; ++j) d *= cR[e];
-                    }
-                    const int k = __ldg(&rec->sp[e]);
-                    sB[k * BLK] = fma(fwbar, d, sB[k * BLK]);
-                }
-                if (e < np) {
-                    const int nu = __ldg(&rec->nu[kMaxSide + e]);
-                    double d = exP[e];
-                    if (nu > 1) {
-                        d *= __ldg(&rec->nud[kMaxSide + e]);
-                        for (int j = 1; j < nu; ++j) d *= cP[e];
-                    }
-                    const int k = __ldg(&rec->sp[kMaxSide + e]);
-                    sB[k * BLK] = fma(rvbar, d, sB[k * BLK]);
-                }
-            }
-            const double Lbar = kfbar * kf;                       // cotangent of ln k_f
-            if (type == NK_RXN_TROE) {
-                if (M != 0.0) {
-                    const double lnf = fma(__ldg(&t->Ea0R), invT, __ldg(&t->beta0)) * invT;
-                    // d lF / d log10 Pr and d lF / d log10 F_cent
-                    const double dlF_du = -2.0 * tr_lF * tr_f1 * (tr_nn / (tr_v * tr_v)) / tr_den;
-                    const double df1_dlFc = fma(1.1762, tr_u, -0.67 * tr_v) / (tr_v * tr_v);
-                    const double dlF_dlFc = (1.0 - 2.0 * tr_lF * tr_f1 * df1_dlFc) / tr_den;
-                    const double lnPrbar = Lbar * (1.0 - tr_g + dlF_du);
-                    const double lnkinfbar = Lbar - lnPrbar;
-                    Mbar = fma(lnPrbar, 1.0 / M, Mbar);
-                    Tbar = fma(Lbar * dlF_dlFc, tr_dFc / tr_Fc, Tbar);
-                    Tbar = fma(lnPrbar, lnf, Tbar);
-                    Tbar = fma(lnkinfbar, fma(EaR, invT, beta) * invT, Tbar);
-                }
-            } else {
-                Tbar = fma(Lbar, fma(EaR, invT, beta) * invT, Tbar);
-            }
-            if (type != NK_RXN_ELEMENTARY && Mbar != 0.0) {
-                Tbar = fma(-Mbar * pRT, invT, Tbar);             // sum_k C_k = p/(RT)
-                const int e0 = __ldg(&rec->eff0), e1 = __ldg(&rec->eff1);
-                for (int j = e0; j < e1; ++j) {
-                    const int k = __ldg(m.eff_sp + j);
-                    sB[k * BLK] = fma(Mbar, __ldg(m.eff_m1 + j), sB[k * BLK]);
-                }
-            }
+    for (int e = 0; e < kMaxSide; ++e) {
+        cR[e] = pR[e] = cP[e] = pP[e] = 1.0;
+        if (e < x.nr) {
+            const int k = x.sp[e];
+            const double c = sC[k * BLK];
+            double pw = c;
+            for (int j = 1; j < x.nu[e]; ++j) pw *= c;
+            cR[e] = c;
+            pR[e] = pw;
+            wsum = fma(x.nud[e], sWb[k * BLK], wsum);
         }
-
-        // C_k = rho y_k, rho = p/(R T s), s = sum y_k, y_k = Y_k / W_k
-        double rhobar = 0.0;
-        for (int k = 0; k < K; ++k) rhobar = fma(sB[k * BLK], sC[k * BLK], rhobar);
-        rhobar /= rho;                                          // sum_k Cbar_k y_k
-        const double sbar = -rhobar * rho / s;
-        Tbar = fma(-rhobar * rho, invT, Tbar);
-        if (valid) {
-            gT[i] = Tbar;
-            for (int k = 0; k < K; ++k)
-                gY[(int64_t)k * ld + i] = __ldg(m.invW + k) * fma(rho, sB[k * BLK], sbar);
+        if (e < x.np) {
+            const int k = x.sp[kMaxSide + e];
+            const double c = sC[k * BLK];
+            double pw = c;
+            for (int j = 1; j < x.nu[kMaxSide + e]; ++j) pw *= c;
+            cP[e] = c;
+            pP[e] = pw;
+            wsum = fma(x.nud[kMaxSide + e], sWb[k * BLK], wsum);
         }
     }
+    double exR[kMaxSide], exP[kMaxSide];
+    const double fw = exclusive_products(pR, x.nr, exR);
+    const double rv = exclusive_products(pP, x.np, exP);
 
+    dfl dG, dH, dCp;
+    rxn_thermo<true, HB>(m, x.thermo, Q.P, dG, dH, dCp);
+    const double sumh = df_to_d(dH);
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, (float)x.dnu), df_neg(dG));
+    double shift = 0.0;
+    dfl shiftd{0.0f, 0.0f};
+    if (dlnA) {
+        shift = __ldg(dlnA + x.orig);
+        shiftd = df_split(shift);
+    }
+    const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
+
+    double M = 0.0;
+    if (KIND != 0) {
+        M = Q.pRT;
+        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
+    }
+
+    // ---- primal (values kept for the adjoint)
+    double kf;
+    double tr_g = 0.0, tr_lF = 0.0, tr_f1 = 0.0, tr_den = 1.0, tr_u = 0.0, tr_v = 1.0, tr_nn = 0.0, tr_Fc = 1.0,
+           tr_dFc = 0.0;
+    const TroeRec* t = nullptr;
+    if constexpr (KIND == 2) {
+        t = m.troe + x.aux;
+        if (M == 0.0) {
+            kf = 0.0;
+        } else {
+            const double lnk0 = fma(-__ldg(&t->Ea0R), Q.invT, fma(__ldg(&t->beta0), Q.lnT, __ldg(&t->lnA0) + shift));
+            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
+            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
+            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
+            tr_Fc = (1.0 - a) * e3 + a * e1;
+            tr_dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1);
+            if (__ldg(&t->hasT2) != 0.0) {
+                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
+                tr_Fc += e2;
+                tr_dFc = fma(T2 * Q.invT * Q.invT, e2, tr_dFc);
+            }
+            const double lFc = dlog_df(tr_Fc, dt) * kInvLn10;
+            const double c = fma(-0.67, lFc, -0.4);
+            tr_nn = fma(-1.27, lFc, 0.75);
+            tr_u = fma(lnPr, kInvLn10, c);
+            tr_v = fma(-0.14, tr_u, tr_nn);
+            tr_f1 = tr_u / tr_v;
+            tr_den = fma(tr_f1, tr_f1, 1.0);
+            tr_lF = lFc / tr_den;
+            tr_g = 1.0 / (1.0 + dexp_df(-lnPr, dt));
+            kf = exp_df_d(lnkf, dt.e2) * tr_g * dexp_df(tr_lF * kLn10, dt);
+        }
+    } else {
+        kf = exp_df_d(lnkf, dt.e2);
+    }
+    const double E = exp_df_d(df_neg(lnKc), dt.e2);
+    const double kr = kf * E;
+    const double qc = fma(kf, fw, -kr * rv);
+    const double q = KIND == 1 ? qc * M : qc;
+
+    // ---- adjoint
+    const double qbar = HB ? fma(-Q.hbRT, sumh, wsum) : wsum;   // sum nu (bar_omega - bar_hrr h)
+    if (HB) Tbar = fma(-Q.hb * kR * q, df_to_d(dCp), Tbar);
     if (WANT_G) {
-        __syncthreads();
-        const double* g0 = smem + (size_t)5 * K * BLK;   // per-warp sums, indexed by caller order
-        for (int r = tid; r < R; r += BLK) {
-            double acc = 0.0;
-            for (int w = 0; w < BLK / 32; ++w) acc += g0[(size_t)w * R + r];
-            ws[(size_t)blockIdx.x * R + r] = acc;
+        double gl = Q.valid ? qbar * q : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gl += __shfl_xor_sync(0xffffffffu, gl, o);
+        if ((threadIdx.x & 31) == 0) gw[r] += gl;
+    }
+    double Mbar = 0.0, qcbar = qbar;
+    if (KIND == 1) {
+        qcbar = qbar * M;
+        Mbar = qbar * qc;
+    }
+    const double krbar = -qcbar * rv;
+    const double kfbar = fma(krbar, E, qcbar * fw);
+    const double fwbar = qcbar * kf, rvbar = -qcbar * kr;
+    const double lnKcbar = -krbar * kr;
+    Tbar = fma(lnKcbar * Q.invT, sumh - x.dnu, Tbar);           // through g_k/RT(T) and ln(p0/RT)
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        if (e < x.nr) {
+            double d = exR[e];                                  // d fw / d C_e = nu C_e^(nu-1) prod_{f!=e}
+            if (x.nu[e] > 1) {
+                d *= -x.nud[e];
+                for (int j = 1; j < x.nu[e]; ++j) d *= cR[e];
+            }
+            double* b = sB + x.sp[e] * BLK;
+            *b = fma(fwbar, d, *b);
+        }
+        if (e < x.np) {
+            double d = exP[e];
+            if (x.nu[kMaxSide + e] > 1) {
+                d *= x.nud[kMaxSide + e];
+                for (int j = 1; j < x.nu[kMaxSide + e]; ++j) d *= cP[e];
+            }
+            double* b = sB + x.sp[kMaxSide + e] * BLK;
+            *b = fma(rvbar, d, *b);
+        }
+    }
+    const double Lbar = kfbar * kf;                              // cotangent of ln k_f
+    if constexpr (KIND == 2) {
+        if (M != 0.0) {
+            const double lnf = fma(__ldg(&t->Ea0R), Q.invT, __ldg(&t->beta0)) * Q.invT;
+            // d lF / d log10 Pr and d lF / d log10 F_cent
+            const double dlF_du = -2.0 * tr_lF * tr_f1 * (tr_nn / (tr_v * tr_v)) / tr_den;
+            const double df1_dlFc = fma(1.1762, tr_u, -0.67 * tr_v) / (tr_v * tr_v);
+            const double dlF_dlFc = (1.0 - 2.0 * tr_lF * tr_f1 * df1_dlFc) / tr_den;
+            const double lnPrbar = Lbar * (1.0 - tr_g + dlF_du);
+            const double lnkinfbar = Lbar - lnPrbar;
+            Mbar = fma(lnPrbar, 1.0 / M, Mbar);
+            Tbar = fma(Lbar * dlF_dlFc, tr_dFc / tr_Fc, Tbar);
+            Tbar = fma(lnPrbar, lnf, Tbar);
+            Tbar = fma(lnkinfbar, fma(x.EaR, Q.invT, x.beta) * Q.invT, Tbar);
+        }
+    } else {
+        Tbar = fma(Lbar, fma(x.EaR, Q.invT, x.beta) * Q.invT, Tbar);
+    }
+    if (KIND != 0 && Mbar != 0.0) {
+        Tbar = fma(-Mbar * Q.pRT, Q.invT, Tbar);                 // sum_k C_k = p/(RT)
+        for (int j = x.eff0; j < x.eff1; ++j) {
+            double* b = sB + __ldg(m.eff_sp + j) * BLK;
+            *b = fma(Mbar, __ldg(m.eff_m1 + j), *b);
         }
     }
 }
 
-__global__ void reduce_blocks_kernel(const double* __restrict__ ws, int nblocks, int R, double* __restrict__ g) {
+template <int KIND, bool WANT_G, bool HB>
+__device__ __forceinline__ void vjp_group(const DevMech& m, int r0, int r1, const double* sC, const double* sWb,
+                                          double* sB, double* gw, const VjpPoint& Q, const double* dlnA,
+                                          const DfTab& dt, double& Tbar) {
+    for (int r = r0; r < r1; ++r) vjp_reaction<KIND, WANT_G, HB>(m, r, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+}
+
+// Shared memory of a block: the pair tables, the ln A sums [R] (WANT_G), then per point C_k,
+// bar_omega_k and NP rows of Cbar_k partials.
+size_t vjp_smem(int K, int R, int np, bool want_g) {
+    return (size_t)kMathTabDoubles * sizeof(double) + (want_g ? (size_t)((R + 1) & ~1) * sizeof(double) : 0) +
+           (size_t)(2 + np) * K * kVjpBlk * sizeof(double);
+}
+
+template <int NP, bool WANT_G, bool HB>
+__global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                           const double* __restrict__ T, const double* __restrict__ p,
+                                                           const double* __restrict__ Y,
+                                                           const double* __restrict__ dlnA,
+                                                           const double* __restrict__ bar_omega,
+                                                           const double* __restrict__ bar_hrr,
+                                                           double* __restrict__ gT, double* __restrict__ gY,
+                                                           double* __restrict__ ws) {
+    constexpr int BLK = kVjpBlk, NT = BLK * NP;
+    extern __shared__ double smem[];
+    const DfTab dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
+    const int K = m.K, R = m.R;
+    double* gw = smem + kMathTabDoubles;                          // ln A sums of this block, device order
+    if (WANT_G)
+        for (int r = threadIdx.x; r < R; r += NT) gw[r] = 0.0;
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    double* base = smem + kMathTabDoubles + (WANT_G ? ((R + 1) & ~1) : 0) + slot;
+    double* sC = base;                                            // C_k
+    double* sWb = base + (size_t)K * BLK;                         // bar_omega_k
+    double* sB0 = base + (size_t)2 * K * BLK;                     // Cbar_k partials, part q at row q
+    double* sB = sB0 + (size_t)part * K * BLK;
+    int ra[3], rb[3];
+    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+    slice<NP>(0, e1, part, ra[0], rb[0]);
+    slice<NP>(e1, t1, part, ra[1], rb[1]);
+    slice<NP>(t1, R, part, ra[2], rb[2]);
+    __syncthreads();
+
+    for (int64_t tile = blockIdx.x; tile * BLK < n; tile += gridDim.x) {
+        const int64_t i0 = tile * BLK + slot;
+        VjpPoint Q;
+        Q.valid = i0 < n;
+        const int64_t i = Q.valid ? i0 : n - 1;                   // idle lanes shadow the last point
+        const double Ti = T[i];
+        Q.invT = 1.0 / Ti;
+        Q.pRT = p[i] * Q.invT * kInvR;
+        Q.P = make_tpairs(Ti, Q.invT, dt);
+        Q.lnT = df_to_d(Q.P.lnTd);
+        Q.hb = HB ? bar_hrr[i] : 0.0;
+        Q.hbRT = Q.hb * kR * Ti;
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
+        const double rho = Q.pRT / s;
+        for (int k = part; k < K; k += NP) {
+            sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
+            sWb[k * BLK] = bar_omega[(int64_t)k * ld + i];
+        }
+        for (int k = 0; k < K; ++k) sB[k * BLK] = 0.0;
+        __syncthreads();
+
+        double Tbar = 0.0;
+        vjp_group<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        vjp_group<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        vjp_group<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        __syncthreads();
+
+        // Cbar_k totals (part order) into row 0, and this part's share of sum_k Cbar_k C_k
+        double cc = 0.0;
+        for (int k = part; k < K; k += NP) {
+            double cb = sB0[k * BLK];
+#pragma unroll
+            for (int q = 1; q < NP; ++q) cb += sB0[((size_t)q * K + k) * BLK];
+            sB0[k * BLK] = cb;
+            cc = fma(cb, sC[k * BLK], cc);
+        }
+        if (NP > 1) {
+            // bar_omega is dead: rows 2q, 2q+1 (2 NP <= K) take part q's sums, added in part order
+            sWb[(2 * part) * BLK] = cc;
+            sWb[(2 * part + 1) * BLK] = Tbar;
+            __syncthreads();
+            cc = sWb[0];
+            Tbar = sWb[BLK];
+#pragma unroll
+            for (int q = 1; q < NP; ++q) {
+                cc += sWb[(2 * q) * BLK];
+                Tbar += sWb[(2 * q + 1) * BLK];
+            }
+        }
+        // C_k = rho y_k, rho = p/(R T s), s = sum y_k, y_k = Y_k / W_k:
+        // rhobar = sum_k Cbar_k y_k = cc / rho, sbar = -rhobar rho / s, Tbar -= rhobar rho / T
+        const double sbar = -cc / s;
+        if (Q.valid) {
+            if (part == 0) gT[i] = fma(-cc, Q.invT, Tbar);
+            for (int k = part; k < K; k += NP)
+                gY[(int64_t)k * ld + i] = __ldg(m.invW + k) * fma(rho, sB0[k * BLK], sbar);
+        }
+        __syncthreads();                                          // before the next tile reuses the rows
+    }
+
+    if (WANT_G)
+        for (int r = threadIdx.x; r < R; r += NT) ws[(size_t)blockIdx.x * R + r] = gw[r];
+}
+
+// g[orig(r)] = sum over blocks of ws[b][r], blocks in order
+__global__ void reduce_blocks_kernel(const double* __restrict__ ws, int nblocks, const RxnRec* __restrict__ rxn,
+                                     int R, double* __restrict__ g) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     double acc = 0.0;
     for (int b = 0; b < nblocks; ++b) acc += ws[(size_t)b * R + r];
-    g[r] = acc;
+    g[__ldg(&rxn[r].orig)] = acc;
 }
 
-template <int BLK>
-cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
-                     const double* dlnA, const double* bar_omega, const double* bar_hrr, double* gT, double* gY,
-                     double* g_lnA, void* ws, cudaStream_t s) {
-    const size_t smem = kMathTabDoubles * sizeof(double) + (size_t)5 * m.K * BLK * sizeof(double) +
-                        (g_lnA ? (size_t)(BLK / 32) * m.R * sizeof(double) : 0);
-    const int64_t need = (n + BLK - 1) / BLK;
-    cudaError_t e;
-    if (g_lnA) {
-        auto kern = vjp_kernel<BLK, true>;
-        if ((e = ensure_smem((const void*)kern, smem)) != cudaSuccess) return e;
-        const int grid = (int)(need < kVjpMaxBlocks ? need : kVjpMaxBlocks);
-        double* wsd = static_cast<double*>(ws);
-        kern<<<grid, BLK, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, wsd);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        reduce_blocks_kernel<<<(m.R + 127) / 128, 128, 0, s>>>(wsd, grid, m.R, g_lnA);
-    } else {
-        auto kern = vjp_kernel<BLK, false>;
-        if ((e = ensure_smem((const void*)kern, smem)) != cudaSuccess) return e;
-        kern<<<(unsigned)need, BLK, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, nullptr);
+// ---------------------------------------------------------------- launch plan
+constexpr int kParts[] = {1, 2, 4};
+
+template <bool WANT_G, bool HB>
+const void* kernel_ptr(int c) {
+    switch (c) {
+        case 0: return (const void*)vjp_kernel<1, WANT_G, HB>;
+        case 1: return (const void*)vjp_kernel<2, WANT_G, HB>;
+        default: return (const void*)vjp_kernel<4, WANT_G, HB>;
+    }
+}
+
+struct VjpPlan {
+    int dev, K, R, variant;
+    int parts_idx;   // index into kParts
+    int grid_cap;    // resident blocks on the device (SMs x blocks per SM)
+};
+std::mutex g_plan_mu;
+std::vector<VjpPlan> g_plans;
+
+template <bool WANT_G, bool HB>
+bool plan_variant(int K, int R, VjpPlan& out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const int variant = (WANT_G ? 1 : 0) | (HB ? 2 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const VjpPlan& q : g_plans)
+            if (q.dev == dev && q.K == K && q.R == R && q.variant == variant) {
+                out = q;
+                return true;
+            }
+    }
+    int per_block = 0, sms = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int best = -1, best_warps = 0, best_blocks = 0;
+    for (int c = 0; c < 3; ++c) {
+        const int np = kParts[c];
+        if (np > 1 && 2 * np > K) continue;
+        const size_t bytes = vjp_smem(K, R, np, WANT_G);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<WANT_G, HB>(c);
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kVjpBlk * np, bytes) != cudaSuccess)
+            continue;
+        if (blocks * np > best_warps) {
+            best_warps = blocks * np;
+            best_blocks = blocks;
+            best = c;
+        }
+    }
+    if (best < 0) return false;
+    out = VjpPlan{dev, K, R, variant, best, sms * best_blocks};
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.push_back(out);
+    return true;
+}
+
+bool plan_for(const DevMech& m, bool want_g, bool hb, VjpPlan& out) {
+    if (want_g) return hb ? plan_variant<true, true>(m.K, m.R, out) : plan_variant<true, false>(m.K, m.R, out);
+    return hb ? plan_variant<false, true>(m.K, m.R, out) : plan_variant<false, false>(m.K, m.R, out);
+}
+
+int64_t vjp_grid(const VjpPlan& pl, int64_t n) {
+    const int64_t tiles = (n + kVjpBlk - 1) / kVjpBlk;
+    return tiles < pl.grid_cap ? tiles : pl.grid_cap;
+}
+
+template <bool WANT_G, bool HB>
+cudaError_t launch_v(const VjpPlan& pl, const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                     const double* Y, const double* dlnA, const double* bar_omega, const double* bar_hrr, double* gT,
+                     double* gY, double* ws, cudaStream_t s) {
+    const int np = kParts[pl.parts_idx];
+    const size_t smem = vjp_smem(m.K, m.R, np, WANT_G);
+    const void* kp = kernel_ptr<WANT_G, HB>(pl.parts_idx);
+    cudaError_t e = ensure_smem(kp, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)vjp_grid(pl, n);
+    switch (np) {
+        case 1:
+            vjp_kernel<1, WANT_G, HB><<<grid, kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT,
+                                                                  gY, ws);
+            break;
+        case 2:
+            vjp_kernel<2, WANT_G, HB><<<grid, 2 * kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr,
+                                                                      gT, gY, ws);
+            break;
+        default:
+            vjp_kernel<4, WANT_G, HB><<<grid, 4 * kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr,
+                                                                      gT, gY, ws);
     }
     return cudaGetLastError();
 }
@@ -359,23 +466,34 @@ cudaError_t noalloc_scratch(void** ptr) {
     return cudaSuccess;
 }
 
+
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n) {
-    const int blk = vjp_block(m);
-    if (!blk) return 0;
-    const int64_t need = (n + blk - 1) / blk;
-    const int64_t grid = need < kVjpMaxBlocks ? need : kVjpMaxBlocks;
+    VjpPlan pl;
+    if (!plan_for(m, true, false, pl)) return 0;
+    VjpPlan pl2;
+    if (!plan_for(m, true, true, pl2)) return 0;
+    const int64_t grid = std::max(vjp_grid(pl, n), vjp_grid(pl2, n));   // either cotangent set
     return (size_t)grid * m.R * sizeof(double);
 }
 
 cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
                        const double* dlnA, const double* bar_omega, const double* bar_hrr, double* gT, double* gY,
                        double* g_lnA, void* ws, cudaStream_t s) {
-    switch (vjp_block(m)) {
-        case 128: return launch_t<128>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, g_lnA, ws, s);
-        case 64: return launch_t<64>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, g_lnA, ws, s);
-        case 32: return launch_t<32>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, g_lnA, ws, s);
-    }
-    return cudaErrorInvalidConfiguration;
+    static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
+    const bool want_g = g_lnA != nullptr, hb = bar_hrr != nullptr;
+    VjpPlan pl;
+    if (!plan_for(m, want_g, hb, pl)) return cudaErrorInvalidConfiguration;
+    double* wsd = static_cast<double*>(ws);
+    cudaError_t e;
+    if (want_g)
+        e = hb ? launch_v<true, true>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, wsd, s)
+               : launch_v<true, false>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, wsd, s);
+    else
+        e = hb ? launch_v<false, true>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, nullptr, s)
+               : launch_v<false, false>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, nullptr, s);
+    if (e != cudaSuccess || !want_g) return e;
+    reduce_blocks_kernel<<<(m.R + 127) / 128, 128, 0, s>>>(wsd, (int)vjp_grid(pl, n), m.rxn, m.R, g_lnA);
+    return cudaGetLastError();
 }
 
 }  // namespace nk

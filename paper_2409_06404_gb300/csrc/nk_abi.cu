@@ -1,6 +1,7 @@
 // C-ABI layer of nkchem: argument checking, error reporting, mechanism upload and the
 // dispatch to the kernel launchers.  Every entry point declared in include/nkchem.h is
 // defined here.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -329,6 +330,38 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
         }
     }
 
+    // reaction thermo groups (nk_internal.cuh): net coefficients of each reaction, grouped by
+    // the species' T_mid, combined in extended precision
+    std::vector<float2> grp_df;
+    std::vector<double> grp_Tmid;
+    for (int q = 0; q < R; ++q) {
+        const int r = order[q];
+        std::vector<int> net(K, 0);
+        for (int i = d->reac_ptr[r]; i < d->reac_ptr[r + 1]; ++i) net[d->reac_sp[i]] -= d->reac_nu[i];
+        for (int i = d->prod_ptr[r]; i < d->prod_ptr[r + 1]; ++i) net[d->prod_sp[i]] += d->prod_nu[i];
+        std::vector<double> tm;
+        for (int k = 0; k < K; ++k)
+            if (net[k] != 0 && std::find(tm.begin(), tm.end(), Tmid[k]) == tm.end()) tm.push_back(Tmid[k]);
+        const int g0 = (int)grp_Tmid.size();
+        if (g0 + (int)tm.size() >= (1 << 24)) return fail(NK_EINVAL, "too many reaction thermo groups");
+        rxn[q].thermo = g0 | ((int32_t)tm.size() << 24);
+        for (double t : tm) {
+            grp_Tmid.push_back(t);
+            for (int range = 0; range < 2; ++range) {
+                long double da[7] = {0, 0, 0, 0, 0, 0, 0};
+                for (int k = 0; k < K; ++k)
+                    if (net[k] != 0 && Tmid[k] == t) {
+                        const double* a = (range == 0 ? d->nasa_lo : d->nasa_hi) + 7 * k;
+                        for (int j = 0; j < 7; ++j) da[j] += (long double)net[k] * a[j];
+                    }
+                const long double c[nk::kGrpPairs] = {da[0], -da[1] / 2, -da[2] / 6, -da[3] / 12, -da[4] / 20, da[5],
+                                                      -da[6], da[0], da[1] / 2, da[2] / 3, da[3] / 4, da[4] / 5,
+                                                      da[5], da[0], da[1], da[2], da[3], da[4]};
+                for (int j = 0; j < nk::kGrpPairs; ++j) grp_df.push_back(split(c[j]));
+            }
+        }
+    }
+
     auto to_f = [](const double* s, size_t n) {
         std::vector<float> v(n);
         for (size_t i = 0; i < n; ++i) v[i] = (float)s[i];
@@ -353,7 +386,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_dA = L.add(df_A.size() * 8), o_dq = L.add(df_qlnW.size() * 8), o_ds = L.add(df_sqrtW.size() * 8),
                  o_dexp = L.add(df_exp.size() * 8), o_drc = L.add(df_rc.size() * 8), o_dlc = L.add(df_lc.size() * 8),
                  o_ndf = L.add(nasa_df.size() * 8), o_rdf = L.add(rxn_df.size() * 16),
-                 o_tdf = L.add(troe_df.size() * 16 + 16);
+                 o_tdf = L.add(troe_df.size() * 16 + 16), o_gdf = L.add(grp_df.size() * 8 + 16),
+                 o_gT = L.add(grp_Tmid.size() * 8 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -393,6 +427,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_ndf, nasa_df.data(), nasa_df.size() * 8);
     put(o_rdf, rxn_df.data(), rxn_df.size() * 16);
     put(o_tdf, troe_df.data(), troe_df.size() * 16);
+    put(o_gdf, grp_df.data(), grp_df.size() * 8);
+    put(o_gT, grp_Tmid.data(), grp_Tmid.size() * 8);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -457,6 +493,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.nasa_df = reinterpret_cast<const float2*>(b + o_ndf);
     dm.rxn_df = reinterpret_cast<const float4*>(b + o_rdf);
     dm.troe_df = reinterpret_cast<const float4*>(b + o_tdf);
+    dm.grp_df = reinterpret_cast<const float2*>(b + o_gdf);
+    dm.grp_Tmid = reinterpret_cast<const double*>(b + o_gT);
     *out = m;
     return ok();
 }

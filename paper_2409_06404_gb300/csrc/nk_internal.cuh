@@ -41,7 +41,7 @@ struct __align__(16) RxnRec {
     int32_t aux;       // Troe record index (type 2), else -1
     int32_t orig;      // index of the reaction in the caller's description
     int32_t eff0, eff1;// third-body efficiencies != 1 in [eff0, eff1) of eff_sp / eff_m1
-    int32_t pad;
+    int32_t thermo;    // thermo groups of the reaction: first (low 24 bits), count (high 8)
     int32_t sp[2 * kMaxSide];   // species of entries: reactants at [0, nr),
                                 // products at [kMaxSide, kMaxSide + np)
     int32_t nu[2 * kMaxSide];   // stoichiometric coefficients of the entries
@@ -67,6 +67,19 @@ struct __align__(16) TroeRecF {
 //   c[0..6] = a1..a7; c[7..10] = a2/2, a3/3, a4/4, a5/5 (h/RT);
 //   c[11..14] = -a2/2, -a3/6, -a4/12, -a5/20 (g/RT); c[15] unused.
 constexpr int kNasaStride = 16;   // per range; species k: [k][2][16] (low, high)
+
+// Reaction thermo groups.  The net coefficients nu_k of a reaction (products minus
+// reactants) combine the NASA-7 polynomials of its species into polynomials of the reaction:
+// with da_j = sum_k nu_k a_j,k over species that share one T_mid (a group; almost always the
+// whole reaction),
+//   sum_k nu_k g_k/RT  = da1 (1 - ln T) - da2 T/2 - da3 T^2/6 - da4 T^3/12 - da5 T^4/20 + da6/T - da7,
+//   sum_k nu_k h_k/RT  = da1 + da2 T/2 + da3 T^2/3 + da4 T^3/4 + da5 T^4/5 + da6/T,
+//   sum_k nu_k cp_k/R  = da1 + da2 T + da3 T^2 + da4 T^3 + da5 T^4,
+// each range picked per group by T <= T_mid, as for the species.  Per group and range the
+// pairs hold: [0..6] da1, -da2/2, -da3/6, -da4/12, -da5/20, da6, -da7; [7..12] da1, da2/2,
+// da3/3, da4/4, da5/5, da6; [13..17] da1..da5.  The kernels then need no per-species g, h or
+// c_p in shared memory.
+constexpr int kGrpPairs = 18;
 
 // Device view of a loaded mechanism (passed by value to every kernel).
 struct DevMech {
@@ -113,6 +126,8 @@ struct DevMech {
     const float2* nasa_df;        // [K][2][8] g/RT coefficients a1, -a2/2, -a3/6, -a4/12, -a5/20, a6, -a7
     const float4* rxn_df;         // [R][2] (lnA, beta) and (Ea/R, dnu, -) as pairs, device order
     const float4* troe_df;        // [n_troe][3] (lnA0, beta0), (Ea0/R, 1/T3), (1/T1, T2) as pairs
+    const float2* grp_df;         // [groups][2][kGrpPairs] reaction thermo groups (below), pairs
+    const double* grp_Tmid;       // [groups] the group's T_mid
 };
 
 // Centre of the re-expanded transport fits (ln T about 1100 K).

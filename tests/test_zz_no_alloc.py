@@ -54,7 +54,9 @@ def test_noalloc_vjp_matches_workspace_vjp():
 
 def test_noalloc_vjp_rejects_oversized_reduction_and_handles_empty():
     torch.cuda.set_device(0)
-    big = synth.make_mechanism(K=40, R=1100, n_tb=4, n_troe=4, seed=77)
+    # R large enough that one R-vector per resident block (at least one block per SM) exceeds
+    # the 8 MiB scratch
+    big = synth.make_mechanism(K=40, R=8000, n_tb=4, n_troe=4, seed=77)
     m = nk.mechanism_load(big)
     L = nk.lib()
     n = 1 << 16
