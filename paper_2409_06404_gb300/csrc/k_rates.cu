@@ -13,15 +13,17 @@
 // latency-bound walk needs.
 //
 // Three arithmetic forms (template PREC):
-//  kNative (NK_FP64_NATIVE): every operation in double (exp/log from nk_math.cuh).
-//  kDF (NK_FP64): the exponent chains -- g_k/RT, the Gibbs sums, ln k_f, ln K_c, the Troe
-//    falloff -- in double-float pairs on the FP32 pipe (nk_df.cuh), each exponential
-//    returned as a double with one FP64 add; concentrations and their products, the
-//    forward-minus-reverse difference and the omega accumulation stay in double.  Results
-//    match the double-precision definition to ~1e-12 (the pairs carry 48 bits).
+//  kNative (NK_FP64_NATIVE): every operation in double (exp/log from nk_math.cuh), with the
+//    per-species g_k/RT in shared memory.
+//  kDF (NK_FP64): the exponent chains -- the reaction's Gibbs sum (from its thermo groups),
+//    ln k_f, ln K_c, the Troe falloff -- in double-float pairs on the FP32 pipe (nk_df.cuh),
+//    each exponential returned as a double with one FP64 add; concentrations and their
+//    products, the forward-minus-reverse difference and the omega accumulation stay in
+//    double.  Results match the double-precision definition to ~1e-12 (the pairs carry 48
+//    bits).
 //  kMixed (NK_MIXED): the Arrhenius argument ln A + beta ln T - Ea/(RT), k_f and the whole
-//    Troe falloff in single precision; equilibrium constants (the sum of nu_k g_k/RT and its
-//    exponential), the forward-minus-reverse difference and the omega accumulation in double.
+//    Troe falloff in single precision; the Gibbs sum and K_c as in the kDF form (pairs), the
+//    forward-minus-reverse difference and the omega accumulation in double.
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -39,11 +41,13 @@ enum { kNative = 0, kMixed = 1, kDF = 2 };
 __device__ __forceinline__ double exp_f32_to_f64(float x) {
     if (x < -700.0f) return 0.0;
     if (x > 700.0f) return __longlong_as_double(0x7ff0000000000000LL);
-    const float nf = rintf(x * 1.44269504089f);
+    const float kd = __fmaf_rn(x, 1.44269504089f, 12582912.0f);   // 1.5 * 2^23 shifter: n in the low bits
+    const int ni = __float_as_int(kd) - 0x4B400000;
+    const float nf = __fsub_rn(kd, 12582912.0f);
     float r = fmaf(nf, -0.693359375f, x);
     r = fmaf(nf, 2.12194440054690583e-4f, r);
     const double e = (double)expf(r);
-    return __longlong_as_double(__double_as_longlong(e) + ((long long)(int)nf << 52));
+    return __longlong_as_double(__double_as_longlong(e) + ((long long)ni << 52));
 }
 
 // Per-point quantities shared by all reactions.
@@ -109,9 +113,9 @@ __device__ __forceinline__ double troe_factor(const TroeRec* t, double lnkinf, d
 }
 
 // Rate of progress q of one reaction of kind KIND (0 elementary, 1 third-body, 2 Troe);
-// r is the reaction's position in the device order.  Native and mixed forms.
-template <int BLK, int PREC, int KIND>
-__device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& x, int r, const double* sC,
+// r is the reaction's position in the device order.  Native form: everything in double.
+template <int BLK, int KIND>
+__device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& x, const double* sC,
                                                    const double* sG, const Pt& P, const double* dlnA,
                                                    const MathTab& mt) {
     double sumg, fw, rv;
@@ -129,43 +133,15 @@ __device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& 
         for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
     }
     double kf, kr;
-    if constexpr (PREC == kNative) {
-        const double lnkf = fma(-x.EaR, P.invT, fma(x.beta, P.lnT, lnA));
-        if constexpr (KIND == 2) {
-            const TroeRec* t = m.troe + x.aux;
-            const double lnk0 = fma(-__ldg(&t->Ea0R), P.invT, fma(__ldg(&t->beta0), P.lnT, __ldg(&t->lnA0) + shift));
-            kf = M == 0.0 ? 0.0 : fexp(lnkf, mt) * troe_factor(t, lnkf, lnk0, M, P, mt);
-            kr = kf * fexp(-lnKc, mt);
-        } else {
-            kf = fexp(lnkf, mt);
-            kr = fexp(lnkf - lnKc, mt);
-        }
-    } else {
-        const float4 xf = __ldg(reinterpret_cast<const float4*>(m.rxnf + r));   // lnA, beta, EaR
-        const float shf = (float)shift;
-        const float lnkf = fmaf(-xf.z, P.invTf, fmaf(xf.y, P.lnTf, xf.x + shf));
-        if constexpr (KIND == 2) {
-            const float4 t0 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux));       // lnA0, beta0, Ea0R, a
-            const float4 t1 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux) + 1);   // 1/T3, 1/T1, T2, has
-            if (M == 0.0) {
-                kf = 0.0;
-            } else {
-                const float lnk0 = fmaf(-t0.z, P.invTf, fmaf(t0.y, P.lnTf, t0.x + shf));
-                const float lnPr = lnk0 - lnkf + logf((float)M);
-                float Fc = (1.0f - t0.w) * expf(-P.Tf * t1.x) + t0.w * expf(-P.Tf * t1.y);
-                if (t1.w != 0.0f) Fc += expf(-t1.z * P.invTf);
-                const float lFc = log10f(Fc);
-                const float c = fmaf(-0.67f, lFc, -0.4f);
-                const float nn = fmaf(-1.27f, lFc, 0.75f);
-                const float u = fmaf(lnPr, (float)kInvLn10, c);
-                const float f1 = u / fmaf(-0.14f, u, nn);
-                const float lF = lFc / fmaf(f1, f1, 1.0f);
-                kf = exp_f32_to_f64(lnkf) * (double)(exp10f(lF) / (1.0f + expf(-lnPr)));
-            }
-        } else {
-            kf = exp_f32_to_f64(lnkf);
-        }
+    const double lnkf = fma(-x.EaR, P.invT, fma(x.beta, P.lnT, lnA));
+    if constexpr (KIND == 2) {
+        const TroeRec* t = m.troe + x.aux;
+        const double lnk0 = fma(-__ldg(&t->Ea0R), P.invT, fma(__ldg(&t->beta0), P.lnT, __ldg(&t->lnA0) + shift));
+        kf = M == 0.0 ? 0.0 : fexp(lnkf, mt) * troe_factor(t, lnkf, lnk0, M, P, mt);
         kr = kf * fexp(-lnKc, mt);
+    } else {
+        kf = fexp(lnkf, mt);
+        kr = fexp(lnkf - lnKc, mt);
     }
     double q = fma(kf, fw, -kr * rv);
     if (KIND == 1) q *= M;
@@ -254,6 +230,52 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
     return q;
 }
 
+// Mixed form: k_f and the whole Troe falloff in single precision; the Gibbs sum and K_c from
+// the reaction's thermo groups in pairs, products and the difference in double.
+template <int BLK, int KIND>
+__device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const Rxn& x, int r, const double* sC,
+                                                         const Pt& P, const double* dlnA, const DfTab& dt) {
+    double fw, rv;
+    products<BLK>(x, sC, fw, rv);
+    dfl sumg, unused_h, unused_cp;
+    rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
+    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, (float)x.dnu), df_neg(sumg));   // ln K_c
+    const float shf = dlnA ? (float)__ldg(dlnA + x.orig) : 0.0f;
+    double M = 0.0;
+    if (KIND != 0) {
+        M = P.pRT;
+        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
+    }
+    const float4 xf = __ldg(reinterpret_cast<const float4*>(m.rxnf + r));   // lnA, beta, EaR
+    const float lnkf = fmaf(-xf.z, P.invTf, fmaf(xf.y, P.lnTf, xf.x + shf));
+    double kf;
+    if constexpr (KIND == 2) {
+        const float4 t0 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux));       // lnA0, beta0, Ea0R, a
+        const float4 t1 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux) + 1);   // 1/T3, 1/T1, T2, has
+        if (M == 0.0) {
+            kf = 0.0;
+        } else {
+            const float lnk0 = fmaf(-t0.z, P.invTf, fmaf(t0.y, P.lnTf, t0.x + shf));
+            const float lnPr = lnk0 - lnkf + logf((float)M);
+            float Fc = (1.0f - t0.w) * expf(-P.Tf * t1.x) + t0.w * expf(-P.Tf * t1.y);
+            if (t1.w != 0.0f) Fc += expf(-t1.z * P.invTf);
+            const float lFc = log10f(Fc);
+            const float c = fmaf(-0.67f, lFc, -0.4f);
+            const float nn = fmaf(-1.27f, lFc, 0.75f);
+            const float u = fmaf(lnPr, (float)kInvLn10, c);
+            const float f1 = u / fmaf(-0.14f, u, nn);
+            const float lF = lFc / fmaf(f1, f1, 1.0f);
+            kf = exp_f32_to_f64(lnkf) * (double)(exp10f(lF) / (1.0f + expf(-lnPr)));
+        }
+    } else {
+        kf = exp_f32_to_f64(lnkf);
+    }
+    const double kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+    double q = fma(kf, fw, -kr * rv);
+    if (KIND == 1) q *= M;
+    return q;
+}
+
 template <int BLK>
 __device__ __forceinline__ void scatter(const Rxn& x, double* sW, double q) {
 #pragma unroll
@@ -275,8 +297,10 @@ __device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, co
                                        const Pt& P, const double* dlnA, const MathTab& mt, const DfTab& dt) {
     if constexpr (PREC == kDF)
         return rate_of_progress_df<BLK, KIND>(m, x, r, sC, P, dlnA, dt);
+    else if constexpr (PREC == kMixed)
+        return rate_of_progress_mixed<BLK, KIND>(m, x, r, sC, P, dlnA, dt);
     else
-        return rate_of_progress<BLK, PREC, KIND>(m, x, r, sC, sG, P, dlnA, mt);
+        return rate_of_progress<BLK, KIND>(m, x, sC, sG, P, dlnA, mt);
 }
 
 // Reactions [r0, r1) of one kind, scattered in reaction order.  (Unrolling by two or four
@@ -291,11 +315,11 @@ __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1,
     }
 }
 
-// Per-point species arrays: C_k, then g_k/RT (native and mixed forms only), then NP rows of
-// omega_k partials.
+// Per-point species arrays: C_k, then g_k/RT (native form only), then NP rows of omega_k
+// partials.
 template <int PREC>
 __host__ __device__ constexpr int shared_rows() {
-    return PREC == kDF ? 1 : 2;
+    return PREC == kNative ? 2 : 1;
 }
 
 // BLK points per block, NP parts (warps) per point: thread (part, slot) works on point
@@ -311,10 +335,10 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     extern __shared__ double smem[];
     MathTab mt{};
     DfTab dt{};
-    if constexpr (PREC == kDF)
-        dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
-    else
+    if constexpr (PREC == kNative)
         mt = stage_math_tables(smem, m.mtab);
+    else
+        dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
     __syncthreads();
     const int K = m.K;
     const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
     double* sC = smem + kMathTabDoubles + slot;                       // C_k       at sC[k * BLK]
-    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (not in the kDF form)
+    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (native form)
     double* sW0 = smem + kMathTabDoubles + (size_t)shared_rows<PREC>() * K * BLK + slot;
     double* sW = sW0 + (size_t)part * K * BLK;                        // this part's omega_k partials
 
@@ -331,21 +355,21 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     P.T = T[i];
     P.invT = 1.0 / P.T;
     P.pRT = p[i] * P.invT * kInvR;                     // p/(RT) = sum_k C_k
-    if constexpr (PREC == kDF) {
-        P.tp = make_tpairs(P.T, P.invT, dt);
-    } else {
+    if constexpr (PREC == kNative) {
         P.lnT = flog(P.T, mt);
         P.lnP0RT = kLnP0overR - P.lnT;                 // ln(p0/(R T))
-        P.Tf = (float)P.T;
-        P.lnTf = (float)P.lnT;
-        P.invTf = (float)P.invT;
+    } else {
+        P.tp = make_tpairs(P.T, P.invT, dt);
+        P.Tf = P.tp.Td.h;
+        P.lnTf = P.tp.lnTd.h + P.tp.lnTd.l;
+        P.invTf = P.tp.invTd.h;
     }
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
     for (int k = part; k < K; k += NP) {
         sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
-        if constexpr (PREC != kDF) sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
+        if constexpr (PREC == kNative) sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
     }
     for (int k = 0; k < K; ++k) sW[k * BLK] = 0.0;
     if (NP > 1) __syncthreads();

@@ -14,6 +14,10 @@
 // factor p/p_ref applied to the finished sums, numerators from prefix and suffix sums.  The
 // cubic fits are evaluated in u = ln T - kLnT0 with coefficients re-expanded on the host,
 // which shrinks the cancellation between the terms of the monomial form.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "nk_internal.cuh"
 
 namespace nk {
@@ -36,27 +40,46 @@ __device__ __forceinline__ dfl poly3_df(const float2* c, dfl u) {
     return df_fma(acc, u, ld2(c + 0));
 }
 
-template <int BLK>
-__global__ void __launch_bounds__(BLK) transport_df_kernel(const DevMech m, const int64_t n, const int64_t ld,
-                                                           const double* __restrict__ T,
-                                                           const double* __restrict__ p,
-                                                           const double* __restrict__ Y,
-                                                           double* __restrict__ mu_out,
-                                                           double* __restrict__ lam_out,
-                                                           double* __restrict__ Dmix) {
+// Zigzag ownership of the pair rows j (row j holds the pairs (j, k > j)): in each run of 2 NP
+// rows, part q takes rows q and 2 NP - 1 - q, so the parts get nearly equal pair counts.
+template <int NP>
+__device__ __forceinline__ bool owns_row(int j, int part) {
+    const int q = j % (2 * NP);
+    return (q < NP ? q : 2 * NP - 1 - q) == part;
+}
+
+// Shared rows per point (8 bytes per species): X_k, NP rows of diffusion-sum partials, and one
+// row for the mass-fraction prefix sums (later X tau^2).
+__host__ __device__ constexpr int transport_rows(int np) { return 2 + np; }
+
+// BLK points per block, NP parts (warps) per point, as in the rates kernel: the parts split the
+// species-pair rows of the diffusion sums (each into its own partial row, added in part order)
+// and then the species of the conductivity, diffusion outputs and Wilke sums.
+template <int BLK, int NP>
+__global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                                const double* __restrict__ T,
+                                                                const double* __restrict__ p,
+                                                                const double* __restrict__ Y,
+                                                                double* __restrict__ mu_out,
+                                                                double* __restrict__ lam_out,
+                                                                double* __restrict__ Dmix) {
     extern __shared__ double smem_all[];
     const MathTab mt = stage_math_tables(smem_all, m.mtab);
     float2* etab = reinterpret_cast<float2*>(smem_all + kMathTabDoubles);
-    for (int j = threadIdx.x; j < kExpTab; j += BLK) etab[j] = __ldg(m.df_exp_tab + j);
+    for (int j = threadIdx.x; j < kExpTab; j += BLK * NP) etab[j] = __ldg(m.df_exp_tab + j);
     __syncthreads();
     const int K = m.K;
-    const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
-    if (i >= n) return;
-    float2* base = reinterpret_cast<float2*>(smem_all + kMathTabDoubles + kExpTab);
-    float2* sX = base + tid;                                  // X_k
-    float2* sA = base + (size_t)K * BLK + tid;                // D denominators, then X_k tau_k
-    float2* sB = base + (size_t)2 * K * BLK + tid;            // Y prefix sums (as double), then X_k tau_k^2
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
+    float2* base = reinterpret_cast<float2*>(smem_all + kMathTabDoubles + kExpTab) + slot;
+    float2* sX = base;                                        // X_k
+    float2* sA0 = base + (size_t)K * BLK;                     // diffusion-sum partials, part q at row q;
+                                                              // after them X_k tau_k in row 0
+    float2* sAp = sA0 + (size_t)part * K * BLK;
+    float2* sB = base + (size_t)(1 + NP) * K * BLK;           // Y prefix sums (as double), then X_k tau_k^2
     double* sBd = reinterpret_cast<double*>(sB);
 
     const double Ti = T[i];
@@ -64,53 +87,65 @@ __global__ void __launch_bounds__(BLK) transport_df_kernel(const DevMech m, cons
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double Wbar = 1.0 / s;
-    for (int k = 0; k < K; ++k) sX[k * BLK] = as_f2(df_split(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar));
+    for (int k = part; k < K; k += NP)
+        sX[k * BLK] = as_f2(df_split(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar));
 
     // ---- diffusion: sum_{j != k} X_j / D_jk(p_ref), one exponential per pair
     if (Dmix) {
-        for (int k = 0; k < K; ++k) sA[k * BLK] = make_float2(0.0f, 0.0f);
+        for (int k = 0; k < K; ++k) sAp[k * BLK] = make_float2(0.0f, 0.0f);
+        if (NP > 1) __syncthreads();
         const float2* Dc = m.df_D_fit;
-        int pi = 0;
         for (int j = 0; j < K; ++j) {
+            if (!owns_row<NP>(j, part)) continue;
+            int pi = j * (2 * K - j - 1) / 2;                 // index of the pair (j, j + 1)
             const dfl xj = as_df(sX[j * BLK]);
             dfl acc0{0.0f, 0.0f}, acc1{0.0f, 0.0f};
             int k = j + 1;
             for (; k + 1 < K; k += 2, pi += 2) {
                 const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
                 const dfl i1 = df_exp(dneg(poly3_df(Dc + 4 * pi + 4, u)), etab);
-                sA[k * BLK] = as_f2(df_fma(xj, i0, as_df(sA[k * BLK])));
-                sA[(k + 1) * BLK] = as_f2(df_fma(xj, i1, as_df(sA[(k + 1) * BLK])));
+                sAp[k * BLK] = as_f2(df_fma(xj, i0, as_df(sAp[k * BLK])));
+                sAp[(k + 1) * BLK] = as_f2(df_fma(xj, i1, as_df(sAp[(k + 1) * BLK])));
                 acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
                 acc1 = df_fma(as_df(sX[(k + 1) * BLK]), i1, acc1);
             }
             if (k < K) {
                 const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
-                sA[k * BLK] = as_f2(df_fma(xj, i0, as_df(sA[k * BLK])));
+                sAp[k * BLK] = as_f2(df_fma(xj, i0, as_df(sAp[k * BLK])));
                 acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
-                ++pi;
             }
-            sA[j * BLK] = as_f2(df_add(as_df(sA[j * BLK]), df_add(acc0, acc1)));
+            sAp[j * BLK] = as_f2(df_add(as_df(sAp[j * BLK]), df_add(acc0, acc1)));
+        }
+        if (NP > 1) __syncthreads();
+        // this part's species: the partials in part order into row 0
+        for (int k = part; k < K; k += NP) {
+            dfl d = as_df(sA0[k * BLK]);
+#pragma unroll
+            for (int q = 1; q < NP; ++q) d = df_add(d, as_df(sA0[((size_t)q * K + k) * BLK]));
+            sA0[k * BLK] = as_f2(d);
         }
         // numerators sum_{j != k} Y_j from prefix and suffix sums (no 1 - Y_k cancellation)
         const double pscale = p[i] / m.p_ref;
         double pre = 0.0;
         for (int k = 0; k < K; ++k) {
-            sBd[k * BLK] = pre;
+            if (NP == 1 || k % NP == part) sBd[k * BLK] = pre;
             pre += Y[(int64_t)k * ld + i];
         }
         double suf = 0.0;
         for (int k = K - 1; k >= 0; --k) {
-            const double num = sBd[k * BLK] + suf;
-            double den = df_value(as_df(sA[k * BLK])) * pscale;
-            if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
-            Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
+            if (NP == 1 || k % NP == part) {
+                const double num = sBd[k * BLK] + suf;
+                double den = df_value(as_df(sA0[k * BLK])) * pscale;
+                if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
+                if (live) Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
+            }
             suf += Y[(int64_t)k * ld + i];
         }
     }
 
-    // ---- conductivity (Mathur-Saxena) and the Wilke weights X tau, X tau^2
+    // ---- conductivity (Mathur-Saxena) and the Wilke weights X tau, X tau^2 of this part's species
     dfl s1{0.0f, 0.0f}, s2{0.0f, 0.0f};
-    for (int k = 0; k < K; ++k) {
+    for (int k = part; k < K; k += NP) {
         const dfl x = as_df(sX[k * BLK]);
         const dfl lnlam = poly3_df(m.df_lam_fit + 4 * k, u);
         s1 = df_fma(x, df_exp(lnlam, etab), s1);
@@ -118,59 +153,159 @@ __global__ void __launch_bounds__(BLK) transport_df_kernel(const DevMech m, cons
         const dfl lnmu = poly3_df(m.df_mu_fit + 4 * k, u);
         const dfl tau = df_exp(df_add(ld2(m.df_qlnW + k), dscale(lnmu, -0.5f)), etab);   // W^1/4 / mu^1/2
         const dfl xt = df_mul(x, tau);
-        sA[k * BLK] = as_f2(xt);
+        sA0[k * BLK] = as_f2(xt);
         sB[k * BLK] = as_f2(df_mul(xt, tau));
     }
-    if (lam_out) lam_out[i] = 0.5 * (df_value(s1) + 1.0 / df_value(s2));
 
-    // ---- Wilke viscosity
+    // ---- Wilke viscosity over this part's species
+    dfl mu{0.0f, 0.0f};
     if (mu_out) {
-        dfl mu{0.0f, 0.0f};
-        for (int k = 0; k < K; ++k) {
+        if (NP > 1) __syncthreads();
+        for (int k = part; k < K; k += NP) {
             const dfl lnmu = poly3_df(m.df_mu_fit + 4 * k, u);
             const dfl sig = df_exp(df_add(dscale(lnmu, 0.5f), dneg(ld2(m.df_qlnW + k))), etab);   // mu^1/2 W^-1/4
             const float2* Ak = m.df_wilkeA + (size_t)k * K;
-            dfl S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f};
-            for (int j = 0; j < K; ++j) {
+            // even and odd j in separate sums: six independent chains per thread
+            dfl S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, T1{0.0f, 0.0f}, T2{0.0f, 0.0f};
+            int j = 0;
+            for (; j + 1 < K; j += 2) {
+                const dfl a = ld2(Ak + j), b = ld2(Ak + j + 1);
+                S0 = df_fma(a, as_df(sX[j * BLK]), S0);
+                T0 = df_fma(b, as_df(sX[(j + 1) * BLK]), T0);
+                S1 = df_fma(a, as_df(sA0[j * BLK]), S1);
+                T1 = df_fma(b, as_df(sA0[(j + 1) * BLK]), T1);
+                S2 = df_fma(a, as_df(sB[j * BLK]), S2);
+                T2 = df_fma(b, as_df(sB[(j + 1) * BLK]), T2);
+            }
+            if (j < K) {
                 const dfl a = ld2(Ak + j);
                 S0 = df_fma(a, as_df(sX[j * BLK]), S0);
-                S1 = df_fma(a, as_df(sA[j * BLK]), S1);
+                S1 = df_fma(a, as_df(sA0[j * BLK]), S1);
                 S2 = df_fma(a, as_df(sB[j * BLK]), S2);
             }
+            S0 = df_add(S0, T0);
+            S1 = df_add(S1, T1);
+            S2 = df_add(S2, T2);
             const dfl den = df_fma(sig, df_fma(sig, S2, dscale(S1, 2.0f)), S0);
             const dfl muk = df_exp(lnmu, etab);
             mu = df_add(mu, df_div(df_mul(as_df(sX[k * BLK]), muk), den));
         }
-        mu_out[i] = df_value(mu);
+    }
+    if constexpr (NP > 1) {
+        // the parts' sums in part order, through the (dead) partial row 1: rows 3q .. 3q+2 (3 NP <= K)
+        __syncthreads();
+        float2* r1 = sA0 + (size_t)K * BLK;
+        r1[(3 * part) * BLK] = as_f2(s1);
+        r1[(3 * part + 1) * BLK] = as_f2(s2);
+        r1[(3 * part + 2) * BLK] = as_f2(mu);
+        __syncthreads();
+        if (part != 0) return;
+        s1 = as_df(r1[0]);
+        s2 = as_df(r1[BLK]);
+        mu = as_df(r1[2 * BLK]);
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            s1 = df_add(s1, as_df(r1[(3 * q) * BLK]));
+            s2 = df_add(s2, as_df(r1[(3 * q + 1) * BLK]));
+            mu = df_add(mu, as_df(r1[(3 * q + 2) * BLK]));
+        }
+    }
+    if (live) {
+        if (lam_out) lam_out[i] = 0.5 * (df_value(s1) + 1.0 / df_value(s2));
+        if (mu_out) mu_out[i] = df_value(mu);
     }
 }
 
-template <int BLK>
-cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
-                     double* mu, double* lam, double* D, size_t smem, cudaStream_t s) {
-    auto kern = transport_df_kernel<BLK>;
-    cudaError_t e = ensure_smem((const void*)kern, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = (n + BLK - 1) / BLK;
-    kern<<<(unsigned)grid, BLK, smem, s>>>(m, n, ld, T, p, Y, mu, lam, D);
-    return cudaGetLastError();
+// ---------------------------------------------------------------- launch shapes
+struct Shape {
+    int blk, np;
+};
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <int S>
+constexpr auto kernel_of() {
+    return transport_df_kernel<kShapes[S].blk, kShapes[S].np>;
+}
+
+template <int... S>
+const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
+    const void* ptrs[] = {(const void*)kernel_of<S>()...};
+    return ptrs[idx];
+}
+
+size_t transport_smem(int K, const Shape& sh) {
+    return (size_t)(kMathTabDoubles + kExpTab) * sizeof(double) +
+           (size_t)transport_rows(sh.np) * K * sh.blk * sizeof(double);
+}
+
+struct Plan {
+    int dev, K, idx;
+};
+std::mutex g_plan_mu;
+std::vector<Plan> g_plans;
+
+// The shape with the most resident warps per SM, fewer parts on ties (cached per device and K).
+int plan_shape(int K) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const Plan& q : g_plans)
+            if (q.dev == dev && q.K == K) return q.idx;
+    }
+    int per_block = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < kNumShapes; ++c) {
+        const Shape& sh = kShapes[c];
+        if (sh.np > 1 && 3 * sh.np > K) continue;
+        const size_t bytes = transport_smem(K, sh);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr(c, std::make_integer_sequence<int, kNumShapes>{});
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
+            continue;
+        const int warps = blocks * sh.blk * sh.np / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best = c;
+        }
+    }
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back({dev, K, best});
+    }
+    return best;
+}
+
+template <int... S>
+cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
+                       const double* T, const double* p, const double* Y, double* mu, double* lam, double* D,
+                       cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    ((S == idx ? (void)(e = [&] {
+        constexpr Shape sh = kShapes[S];
+        auto kern = kernel_of<S>();
+        const size_t smem = transport_smem(m.K, sh);
+        cudaError_t r = ensure_smem((const void*)kern, smem);
+        if (r != cudaSuccess) return r;
+        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, mu, lam, D);
+        return cudaGetLastError();
+    }())
+               : (void)0),
+     ...);
+    return e;
 }
 
 }  // namespace
 
 cudaError_t launch_transport_df(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                                 const double* Y, double* mu, double* lam, double* Dmix, cudaStream_t s) {
-    const size_t per_thread = (size_t)3 * m.K * 8;
-    const size_t fixed = (kMathTabDoubles + kExpTab) * sizeof(double);
-    const int blk = pick_block_occupancy(per_thread, fixed);
-    if (!blk) return cudaErrorInvalidConfiguration;
-    const size_t smem = per_thread * blk + fixed;
-    switch (blk) {
-        case 128: return launch_t<128>(m, n, ld, T, p, Y, mu, lam, Dmix, smem, s);
-        case 64: return launch_t<64>(m, n, ld, T, p, Y, mu, lam, Dmix, smem, s);
-        case 32: return launch_t<32>(m, n, ld, T, p, Y, mu, lam, Dmix, smem, s);
-    }
-    return cudaErrorInvalidConfiguration;
+    const int idx = plan_shape(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, mu, lam, Dmix, s);
 }
 
 }  // namespace nk

@@ -88,8 +88,11 @@ __device__ __forceinline__ dfl df_exp(dfl x, const float2* tab) {
     constexpr float C1 = 5.4149627685546875e-03f;        // ln2/128, 12 significant bits
     constexpr float C2 = 2.495795570212067e-07f;         // next 24 bits
     constexpr float C3 = 1.2864023201156725e-14f;        // remainder
-    const float Nf = rintf(x.h * kInvC);
-    const int N = (int)Nf;
+    // N = nearest integer to x.h * 128/ln2 by the 1.5 * 2^23 shifter (|N| < 2^22), read from
+    // the float's bits: FP32 and integer pipe only
+    const float kd = __fmaf_rn(x.h, kInvC, 12582912.0f);
+    const int N = __float_as_int(kd) - 0x4B400000;
+    const float Nf = __fsub_rn(kd, 12582912.0f);
     const float rh = __fmaf_rn(-Nf, C1, x.h);            // exact
     const float p2 = __fmul_rn(-Nf, C2);
     const float p2e = __fmaf_rn(-Nf, C2, -p2);
@@ -150,8 +153,11 @@ __device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
     constexpr float C1 = 5.43212890625e-03f;
     constexpr float C2 = -1.691655779723078e-05f;
     constexpr float C3 = -3.281964814933619e-13f;
-    const float Nf = rintf(x.h * kInvC);
-    const int N = (int)Nf;
+    // N = nearest integer to x.h * 128/ln2 by the 1.5 * 2^23 shifter (|N| < 2^22), read from
+    // the float's bits: FP32 and integer pipe only
+    const float kd = __fmaf_rn(x.h, kInvC, 12582912.0f);
+    const int N = __float_as_int(kd) - 0x4B400000;
+    const float Nf = __fsub_rn(kd, 12582912.0f);
     const float rh = __fmaf_rn(-Nf, C1, x.h);            // exact
     const float p2 = __fmul_rn(-Nf, C2);
     const float p2e = __fmaf_rn(-Nf, C2, -p2);

@@ -111,8 +111,10 @@ __device__ __forceinline__ void rxn_thermo(const DevMech& m, int thermo, const T
     g = h = cp = dfl{0.0f, 0.0f};
     for (int j = 0; j < ng; ++j) {
         const int grp = g0 + j;
-        const float4* c4 = reinterpret_cast<const float4*>(
-            m.grp_df + ((size_t)grp * 2 + (P.T <= __ldg(m.grp_Tmid + grp) ? 0 : 1)) * kGrpPairs);
+        // T <= T_mid on the bit patterns (T_mid > 0: signed 64-bit order is the order of the
+        // doubles; NaN T takes the high range as the double comparison would)
+        const bool lo = __double_as_longlong(P.T) <= __ldg(reinterpret_cast<const long long*>(m.grp_Tmid) + grp);
+        const float4* c4 = reinterpret_cast<const float4*>(m.grp_df + ((size_t)grp * 2 + (lo ? 0 : 1)) * kGrpPairs);
         float2 c[kGrpPairs];
 #pragma unroll
         for (int v = 0; v < kGrpPairs / 2; ++v) {
