@@ -236,6 +236,66 @@ def run_reference(args):
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
+# ---------------------------------------------------------------------------------- implicit stage
+def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
+    """One implicit-stage sweep as a Newton-Krylov stage issues it: one forward (thermo FP64,
+    rates and transport mixed) and n_dir exact JVPs along N(0, 1) directions, against the
+    plain-FP64 forward and n_dir finite-difference JVPs (NITSOL step per point,
+    sigma = sqrt((1 + |x|) eps) / |v|) on the same GPU.  Directions are generated before the
+    timed region; each sweep is timed with CUDA events on the launching stream."""
+    import torch
+    n, K = T.shape[0], Y.shape[0]
+    gen = torch.Generator(device=T.device).manual_seed(5000)
+    dirs = [(torch.randn(n, generator=gen, dtype=torch.float64, device=T.device),
+             torch.randn((K, n), generator=gen, dtype=torch.float64, device=T.device)) for _ in range(n_dir)]
+    eps = 2.220446049250313e-16
+    xnorm = torch.sqrt(T * T + (Y * Y).sum(0))
+
+    def ours():
+        nk.thermo_eval(m, T, p, Y)
+        nk.rates_eval(m, T, p, Y, precision="mixed")
+        nk.transport_eval(m, T, p, Y, precision="mixed")
+        out = None
+        for vT, vY in dirs:
+            out = nk.rates_jvp(m, T, p, Y, vT, vY)
+        return out
+
+    def fd():
+        nk.thermo_eval(m, T, p, Y)
+        w0, h0 = nk.rates_eval(m, T, p, Y)
+        nk.transport_eval(m, T, p, Y)
+        out = None
+        for vT, vY in dirs:
+            sig = torch.sqrt((1.0 + xnorm) * eps) / torch.sqrt(vT * vT + (vY * vY).sum(0))
+            w1, h1 = nk.rates_eval(m, T + sig * vT, p, Y + sig * vY)
+            out = ((w1 - w0) / sig, (h1 - h0) / sig)
+        return out
+
+    def timed(f):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts)
+
+    t_ours, t_fd = timed(ours), timed(fd)
+    # accuracy of the difference quotient against the exact JVP, last direction
+    dw, dh = nk.rates_jvp(m, T, p, Y, *dirs[-1])
+    fw, fh = fd()
+    sc = dw.abs().amax(0).clamp_min(1e-300)
+    fd_err = ((fw - dw).abs().amax(0) / sc).median().item()
+    return {"points": n, "directions": n_dir, "sweep_ms": t_ours, "fd_fp64_sweep_ms": t_fd,
+            "speedup_vs_fd": t_fd / t_ours, "fd_jvp_median_rel_err": fd_err,
+            "sweep": "thermo (FP64) + rates, transport (mixed) + exact JVPs",
+            "fd_sweep": "thermo, rates, transport (FP64) + FP64 rates at x + sigma v per direction"}
+
+
 # ---------------------------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -340,6 +400,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms.update({k: [a.elapsed_time(b) for a, b in fev[k]] for k in forms})
 
+    # ---- implicit-stage sweep (not part of a step)
+    stage = None
+    if args.stage_dirs > 0:
+        if args.stage_elements == args.elements:
+            stage = implicit_stage(nk, m, T, p, Y, args.stage_dirs, 3, s)
+        else:
+            st5 = synth.workload_states("flame_32768el" if args.stage_elements == 32768 else WORKLOAD, K,
+                                        n_elements=args.stage_elements)
+            T5, p5, Y5 = (torch.from_numpy(a).to(dev) for a in (st5.T, st5.p, st5.Y))
+            del st5
+            stage = implicit_stage(nk, m, T5, p5, Y5, args.stage_dirs, 2, s)
+            del T5, p5, Y5
+        stage["workload"] = f"{MECH} on {stage['points']} points"
+
     fwd_ms = sum(ms["rates_fp64"]) + sum(ms["transport_fp64"])
     nat_ms = sum(ms["rates_fp64_native"]) + sum(ms["transport_fp64_native"])
     mix_ms = sum(ms["rates_mixed"]) + sum(ms["transport_mixed"])
@@ -425,6 +499,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
     }
+    if stage is not None:
+        line["implicit_stage"] = stage
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -442,6 +518,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--elements", type=int, default=4096,
                     help="flame field size in elements (a cube; 4096 = the benchmark workload)")
+    ap.add_argument("--stage-dirs", type=int, default=10,
+                    help="JVP directions of the implicit-stage sweep (0 skips it)")
+    ap.add_argument("--stage-elements", type=int, default=4096,
+                    help="elements of the implicit-stage field (32768 = 16,777,216 points)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

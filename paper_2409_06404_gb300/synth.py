@@ -454,6 +454,8 @@ def workload_states(name, K, n_points=None, n_elements=None):
         st = states_uniform(K, 64 * 512, seed=2009, alpha=0.5)
     elif name == "flame_4096el":      # 16^3 elements x 512 = 2,097,152 points
         st = states_flame(K, n_elements or 4096, seed=2053 if K == 53 else 2120)
+    elif name == "flame_32768el":     # 32^3 elements x 512 = 16,777,216 points (implicit stage)
+        st = states_flame(K, n_elements or 32768, seed=2053)
     else:
         raise KeyError(name)
     if n_points is not None:
