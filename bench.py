@@ -160,9 +160,17 @@ def _emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def _sources_sha256(paths):
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _traffic(kernel_row):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if the
-    kernel source is unchanged since the capture; else None."""
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if none of
+    the kernel's source files changed since the capture; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -171,12 +179,11 @@ def _traffic(kernel_row):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, rec["source"])
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+        h = _sources_sha256(rec["sources"])
+    except (OSError, KeyError):
         return None
-    return rec["bytes_per_launch"] if h == rec.get("source_sha256") else None
+    return rec["bytes_per_launch"] if h == rec.get("sources_sha256") else None
 
 
 def _oracle_sample(n_points):
@@ -403,7 +410,7 @@ def run_ours(args):
     # ---- implicit-stage sweep (not part of a step)
     stage = None
     if args.stage_dirs > 0:
-        if args.stage_elements == args.elements:
+        if args.stage_elements in (None, args.elements):
             stage = implicit_stage(nk, m, T, p, Y, args.stage_dirs, 3, s)
         else:
             st5 = synth.workload_states("flame_32768el" if args.stage_elements == 32768 else WORKLOAD, K,
@@ -520,8 +527,8 @@ def main():
                     help="flame field size in elements (a cube; 4096 = the benchmark workload)")
     ap.add_argument("--stage-dirs", type=int, default=10,
                     help="JVP directions of the implicit-stage sweep (0 skips it)")
-    ap.add_argument("--stage-elements", type=int, default=4096,
-                    help="elements of the implicit-stage field (32768 = 16,777,216 points)")
+    ap.add_argument("--stage-elements", type=int, default=None,
+                    help="elements of the implicit-stage field (default: --elements; 32768 = 16,777,216 points)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
