@@ -108,8 +108,11 @@ def _configure(lib):
     lib.or_rates_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, P, ci]
     lib.or_rates_grad_lnA.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
     lib.or_count_ops.argtypes = [M, _c_dbl, _c_dbl, P, ci, P]
+    lib.or_rhs.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
+    lib.or_rhs_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, ci]
     for f in ("or_thermo", "or_nasa7_cs", "or_rates", "or_rates_of_progress", "or_transport",
-              "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops"):
+              "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops", "or_rhs",
+              "or_rhs_jvp"):
         getattr(lib, f).restype = None
     return lib
 
@@ -276,6 +279,35 @@ def grad_lnA(mech, T, p, Y, wbar, hbar=None, dlnA=None, threads: int = 0):
     _lib_handle().or_rates_grad_lnA(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(d), _dp(wbar), _dp(hb),
                                     _dp(g), threads)
     return g
+
+
+def rhs(mech, T, p, Y, threads: int = 0, scales: bool = False):
+    """Implicit-stage chemistry sources at fixed p (Eq. 1a-b): (fT [n] = hrr/(rho c_p),
+    fY [K, n] = W_k omega_k/rho) and, with ``scales``, their cancellation scales."""
+    pk = _Packed(mech)
+    T, p, Y, n = _state(T, p, Y, pk.K)
+    fT = np.empty(n)
+    fY = np.empty((pk.K, n))
+    sT = np.empty(n) if scales else None
+    sY = np.empty((pk.K, n)) if scales else None
+    _lib_handle().or_rhs(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(fT), _dp(fY), _dp(sT), _dp(sY), threads)
+    return (fT, fY, sT, sY) if scales else (fT, fY)
+
+
+def rhs_jvp(mech, T, p, Y, vT, vY, threads: int = 0, scales: bool = False):
+    """Complex-step directional derivative of the sources along (vT, vY): (dfT [n], dfY [K, n])
+    and, with ``scales``, the derivative magnitudes."""
+    pk = _Packed(mech)
+    T, p, Y, n = _state(T, p, Y, pk.K)
+    vT = _f64(vT).ravel()
+    vY = _f64(vY)
+    dfT = np.empty(n)
+    dfY = np.empty((pk.K, n))
+    sT = np.empty(n) if scales else None
+    sY = np.empty((pk.K, n)) if scales else None
+    _lib_handle().or_rhs_jvp(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(vT), _dp(vY), _dp(dfT), _dp(dfY),
+                             _dp(sT), _dp(sY), threads)
+    return (dfT, dfY, sT, sY) if scales else (dfT, dfY)
 
 
 def count_ops(mech, T: float, p: float, Y, which: str = "rates") -> dict:

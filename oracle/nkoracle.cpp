@@ -27,6 +27,9 @@
  *   9. mixture-averaged transport: Wilke viscosity, Mathur conductivity, Hirschfelder-Curtiss
  *      diffusion coefficients D_km = sum_{j!=k} X_j W_j / (Wbar sum_{j!=k} X_j/D_jk)
  *  10. derivatives by complex step (h = 1e-30) through the same templated code.
+ *  11. implicit-stage chemistry sources of Eq. 1a-b at fixed p: dY_k/dt = W_k omega_k / rho,
+ *      dT/dt = hrr / (rho c_p), c_p the mass-based mixture heat capacity; their directional
+ *      derivatives by complex step as in 10.
  *
  * Everything is templated on the scalar type S: double, std::complex<double> (complex-step
  * derivatives) and Cnt (counts the floating-point operations the definition performs).
@@ -296,6 +299,47 @@ void rates_point(const or_mech& m, S T, double p, const S* Y, const S* shift, S*
     }
     if (scale_h) *scale_h = sh;
     if (dscale_h) *dscale_h = dsh;
+}
+
+/* ---------------------------------------------------------------- implicit-stage sources
+ * The chemistry source terms of Eq. 1a-b at fixed p: dY_k/dt = W_k omega_k / rho (omega_k is
+ * molar, so W_k omega_k is the mass production rate) and dT/dt = hrr / (rho c_p) with the
+ * heat release hrr = -sum_k h_k omega_k and the mass-based mixture c_p.
+ * scale_Y/scale_T (nullable): the omega and hrr magnitudes of rates_point carried through the
+ * same factors; with complex S the imaginary parts (dscale_*) give the magnitudes of the
+ * directional derivatives: W_k (|d omega_k| + |omega_k| |d rho|/rho) / rho and
+ * (|d hrr| + |hrr| (|d rho|/rho + |d c_p|/c_p)) / (rho c_p), each term by its own magnitude. */
+template <class S>
+void rhs_point(const or_mech& m, S T, double p, const S* Y, S* fY, S& fT, double* scale_Y, double* scale_T,
+               double* dscale_Y = nullptr, double* dscale_T = nullptr) {
+    const int K = m.K;
+    std::vector<S> w(K);
+    std::vector<double> sc(K), dsc(K);
+    double sh = 0.0, dsh = 0.0;
+    S hrr;
+    const bool want = scale_Y != nullptr;
+    rates_point<S>(m, T, p, Y, nullptr, w.data(), hrr, want ? sc.data() : nullptr, want ? &sh : nullptr,
+                   dscale_Y ? dsc.data() : nullptr, dscale_Y ? &dsh : nullptr);
+    Mixture<S> mx;
+    mixture(m, T, p, Y, mx);
+    S cp = S(0.0);
+    for (int k = 0; k < K; ++k) {
+        S cpR, hRT, sR;
+        nasa7(m, k, T, cpR, hRT, sR);
+        cp += Y[k] * S(RU) * cpR / S(m.W[k]);
+    }
+    for (int k = 0; k < K; ++k) fY[k] = S(m.W[k]) * w[k] / mx.rho;
+    fT = hrr / (mx.rho * cp);
+    if (want) {
+        const double rho = std::fabs(re(mx.rho)), c = std::fabs(re(cp));
+        for (int k = 0; k < K; ++k) scale_Y[k] = m.W[k] * sc[k] / rho;
+        *scale_T = sh / (rho * c);
+        if (dscale_Y) {
+            const double drr = std::fabs(im(mx.rho)) / rho, dcc = std::fabs(im(cp)) / c;
+            for (int k = 0; k < K; ++k) dscale_Y[k] = m.W[k] * (dsc[k] + std::fabs(re(w[k])) * drr) / rho;
+            *dscale_T = (dsh + std::fabs(re(hrr)) * (drr + dcc)) / (rho * c);
+        }
+    }
 }
 
 /* ---------------------------------------------------------------- step 9: transport */
@@ -584,6 +628,48 @@ void or_rates_grad_lnA(const or_mech* m, int64_t n, int64_t ld, const double* T,
         double s = 0.0;
         for (int t = 0; t < nt; ++t) s += part[(size_t)t * R + r];
         g[r] = s;
+    }
+}
+
+/* Implicit-stage chemistry sources (rhs_point): fT [n] (K/s) and fY [K][ld] (1/s); the scales
+ * (nullable) are the magnitudes behind cancellation-aware tolerances. */
+void or_rhs(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+            double* fT, double* fY, double* fT_scale, double* fY_scale, int nthreads) {
+    const int K = m->K;
+#pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<double> y(K), f(K), sc(K);
+        for (int k = 0; k < K; ++k) y[k] = Y[k * ld + i];
+        double ft, st;
+        rhs_point<double>(*m, T[i], p[i], y.data(), f.data(), ft, fY_scale ? sc.data() : nullptr, &st);
+        fT[i] = ft;
+        for (int k = 0; k < K; ++k) fY[k * ld + i] = f[k];
+        if (fY_scale)
+            for (int k = 0; k < K; ++k) fY_scale[k * ld + i] = sc[k];
+        if (fT_scale) fT_scale[i] = fY_scale ? st : 0.0;
+    }
+}
+
+/* Their directional derivative along (vT, vY) at fixed p by one complex-step evaluation per
+ * point, with the derivative magnitudes (nullable) for cancellation-aware tolerances. */
+void or_rhs_jvp(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                const double* vT, const double* vY, double* dfT, double* dfY, double* dfT_scale, double* dfY_scale,
+                int nthreads) {
+    const int K = m->K;
+    const double hstep = 1e-30;
+#pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<cplx> y(K), f(K);
+        std::vector<double> sc(K), dsc(K);
+        for (int k = 0; k < K; ++k) y[k] = cplx(Y[k * ld + i], hstep * vY[k * ld + i]);
+        cplx Tc(T[i], hstep * vT[i]), ft;
+        double st, dst;
+        rhs_point<cplx>(*m, Tc, p[i], y.data(), f.data(), ft, sc.data(), &st, dsc.data(), &dst);
+        dfT[i] = ft.imag() / hstep;
+        for (int k = 0; k < K; ++k) dfY[k * ld + i] = f[k].imag() / hstep;
+        if (dfY_scale)
+            for (int k = 0; k < K; ++k) dfY_scale[k * ld + i] = dsc[k] / hstep;
+        if (dfT_scale) dfT_scale[i] = dst / hstep;
     }
 }
 

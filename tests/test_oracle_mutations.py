@@ -13,6 +13,7 @@ import test_oracle_thermo as th
 import test_oracle_rates as rt
 import test_oracle_transport as tr
 import test_oracle_derivs as dv
+import test_oracle_rhs as rh
 
 SRC = open(os.path.join(os.path.dirname(oracle.__file__), "nkoracle.cpp")).read()
 
@@ -39,6 +40,9 @@ MUTATIONS = {
     "mathur_harmonic": ("lam = S(0.5) * (s1 + S(1.0) / s2);", "lam = S(0.5) * (s1 + S(1.0) * s2);"),
     "diffusion_pressure": ("* S(m.p_ref / p)", "* S(p / m.p_ref)"),
     "diffusion_numerator": ("num += mx.X[j] * S(m.W[j]);", "num += mx.X[j];"),
+    "rhs_missing_W": ("fY[k] = S(m.W[k]) * w[k] / mx.rho;", "fY[k] = w[k] / mx.rho;"),
+    "rhs_cp_molar": ("cp += Y[k] * S(RU) * cpR / S(m.W[k]);", "cp += Y[k] * S(RU) * cpR;"),
+    "rhs_T_sign": ("fT = hrr / (mx.rho * cp);", "fT = -hrr / (mx.rho * cp);"),
 }
 
 
@@ -70,6 +74,10 @@ def _pins():
         lambda: tr.test_mixture_values_within_species_bounds(m53),
         lambda: dv.test_jacobian_matches_central_differences("h2_9sp_21rx"),
         lambda: dv.test_grad_lnA_closed_form_and_fd("h2_9sp_21rx"),
+        lambda: rh.test_mass_conservation("h2_9sp_21rx"),
+        lambda: rh.test_enthalpy_conservation_at_constant_pressure("h2_9sp_21rx"),
+        rh.test_pressure_scaling,
+        rh.test_exothermic_reaction_heats,
     ]
 
 
