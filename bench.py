@@ -13,8 +13,9 @@ Each launch is bracketed by CUDA events on the launching stream.  The headline v
 Mpoints/s of rates + transport in FP64 (points / (t_rates + t_transport) summed over the
 timed steps); the mixed form, JVP/forward and VJP/forward ratios come from the same steps.
 After the timed steps, the all-double forms of rates and transport (NK_FP64_NATIVE, the
-plain-FP64 arithmetic the FP64 form is checked against) are timed the same way in a
-separate loop, for comparison ("fp64_native_value"); they are not part of a step.
+plain-FP64 arithmetic the FP64 form is checked against) and the implicit-stage sources and
+their JVP (nk_rhs_eval, nk_rhs_jvp) are timed the same way in a separate loop
+("fp64_native_value", rows); they are not part of a step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -90,9 +91,11 @@ def algorithmic_flops(mech) -> dict:
     thermo = 2 * t + 4 + K * (3 + 10 + 12 + 14 + 4)
     jvp = pre + K * 16 + per_rxn_d + hrr * 2 + K * 10
     vjp = pre + K * 24 + per_rxn_d + 10 * R + K * 8
+    rhs = rates + K * 12 + 4                        # W_k/rho factors, c_p, 1/(rho c_p)
+    rhs_jvp = jvp + K * 24 + 12                     # primal omega, c_p and d c_p, both source tangents
     return {"thermo": thermo, "rates_fp64": rates, "transport_fp64": transport, "rates_fp64_native": rates,
             "transport_fp64_native": transport, "rates_mixed": rates, "transport_mixed": transport, "jvp": jvp,
-            "vjp": vjp}
+            "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp}
 
 
 # ---------------------------------------------------------------------------------- clocks
@@ -365,6 +368,9 @@ def run_ours(args):
                                                          P(out["hrr"]), 2, sp)),
         "transport_fp64_native": lambda: chk(L.nk_transport_eval(h, n, n, P(T), P(p), P(Y), P(out["mu"]),
                                                                  P(out["lam"]), P(out["D"]), 2, sp)),
+        "rhs_fp64": lambda: chk(L.nk_rhs_eval(h, n, n, P(T), P(p), P(Y), None, P(out["hrr"]), P(out["w"]), 0, sp)),
+        "rhs_jvp": lambda: chk(L.nk_rhs_jvp(h, n, n, P(T), P(p), P(Y), None, P(vT), P(vY), None, None,
+                                            P(out["dh"]), P(out["dw"]), sp)),
     }
     launches_per_step = {"thermo": 1, "rates_fp64": 1, "transport_fp64": 1, "rates_mixed": 1,
                          "transport_mixed": 1, "jvp": 1, "vjp": 2}

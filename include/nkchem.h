@@ -50,13 +50,15 @@ typedef enum {
 
 typedef enum {
     NK_FP64 = 0,        /* results to double precision (1e-10 of the FP64 definition, typically
-                           1e-13): rates in double; transport sums, whose terms are positive
-                           and bounded, in double-float (pairs of floats, 48-bit significands)
-                           on the FP32 pipe, with inputs and outputs in double */
+                           1e-13): exponent chains of the rates (ln k_f, Gibbs sums, ln K_c,
+                           falloff) and all of transport in double-float (pairs of floats,
+                           48-bit significands) on the FP32 pipe; concentrations, products,
+                           the forward-minus-reverse difference and every accumulation in
+                           double; inputs and outputs in double */
     NK_MIXED = 1,       /* rates: Arrhenius/Troe arguments and k_f in single precision,
-                           equilibrium constants, forward-minus-reverse difference and omega
-                           accumulation in double; transport: fits, mixture rules and sums in
-                           single precision (1e-5) */
+                           equilibrium constants (pairs), forward-minus-reverse difference and
+                           omega accumulation in double; transport: fits, mixture rules and
+                           sums in single precision (1e-5) */
     NK_FP64_NATIVE = 2  /* every operation in native double precision (reference form) */
 } nk_precision;
 
@@ -153,7 +155,7 @@ nk_status nk_thermo_eval(const nk_mech* mech, int64_t n, int64_t ld, const doubl
  *   omega[K*ld]  omega_k = sum_r nu_kr q_r, mol/(m^3 s)
  *   hrr[n]       -sum_k h_k(T) omega_k, W/m^3 (positive when exothermic)
  * dlnA: NULL or device [R] shift added to ln A_r (to both limits of a Troe reaction).
- * precision: NK_FP64 / NK_FP64_NATIVE (the same double-precision kernel) or NK_MIXED.
+ * precision: NK_FP64, NK_FP64_NATIVE or NK_MIXED.
  */
 nk_status nk_rates_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
                         const double* p, const double* Y, const double* dlnA, double* omega,
@@ -183,6 +185,31 @@ nk_status nk_rates_jvp(const nk_mech* mech, int64_t n, int64_t ld, const double*
                        const double* p, const double* Y, const double* dlnA, const double* vT,
                        const double* vY, double* omega, double* hrr, double* d_omega,
                        double* d_hrr, nk_stream stream);
+
+/*
+ * Chemistry sources of the implicit thermochemistry stage: the production and heat-release
+ * terms of Eq. 1a-b at fixed pressure (Sec. 2; no dp0/dt term), the right-hand side the
+ * stage's Newton iterations evaluate at every point:
+ *   fT[n]      dT/dt = hrr / (rho c_p), K/s (c_p the mass-based mixture heat capacity)
+ *   fY[K*ld]   dY_k/dt = W_k omega_k / rho, 1/s
+ * with omega_k, hrr as in nk_rates_eval and rho = p Wbar/(R T).  dlnA as in nk_rates_eval.
+ * precision: NK_FP64, NK_FP64_NATIVE or NK_MIXED.
+ */
+nk_status nk_rhs_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                      const double* Y, const double* dlnA, double* fT, double* fY,
+                      nk_precision precision, nk_stream stream);
+
+/*
+ * Exact Jacobian-vector product of those sources with respect to (T, Y_k) at fixed p: the
+ * product the stage's GMRES solve forms by difference quotients (Sec. 2).
+ *   vT[n], vY[K*ld]      direction
+ *   dfT[n], dfY[K*ld]    J v
+ *   fT[n], fY[K*ld]      NULL, or also return the sources
+ * Rates of progress recomputed per point, never stored; FP64 form (as NK_FP64).
+ */
+nk_status nk_rhs_jvp(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                     const double* Y, const double* dlnA, const double* vT, const double* vY,
+                     double* fT, double* fY, double* dfT, double* dfY, nk_stream stream);
 
 /*
  * Bytes of device workspace nk_rates_vjp needs for n points when g_lnA is requested

@@ -66,6 +66,8 @@ _SIGS = {
     "nk_rates_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_transport_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
+    "nk_rhs_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "nk_rhs_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_rates_vjp_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_rates_vjp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [ctypes.c_size_t, _vp]),
     "nk_rates_vjp_noalloc": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 9 + [_vp]),
@@ -281,6 +283,35 @@ def rates_jvp(m: Mechanism, T, p, Y, vT, vY, dlnA=None, primal=False, stream=Non
     if primal:
         return d_omega, d_hrr, omega, hrr
     return d_omega, d_hrr
+
+
+def rhs_eval(m: Mechanism, T, p, Y, dlnA=None, precision="fp64", fT=None, fY=None, stream=None):
+    """nk_rhs_eval: implicit-stage chemistry sources (fT [n] = dT/dt in K/s, fY [K, n] = dY/dt
+    in 1/s) at fixed p."""
+    n, ld = _state(m, T, p, Y)
+    _vec(dlnA, m.R, "dlnA")
+    fY = _species_out(m, n, ld, T, fY)
+    fT = _point_out(n, T, fT)
+    _check(lib().nk_rhs_eval(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(dlnA), _ptr(fT), _ptr(fY),
+                             _PRECISION[precision], _stream(stream)))
+    return fT, fY
+
+
+def rhs_jvp(m: Mechanism, T, p, Y, vT, vY, dlnA=None, primal=False, stream=None):
+    """nk_rhs_jvp: (dfT, dfY) = J_f (vT, vY) of the sources; with primal=True also (fT, fY)."""
+    n, ld = _state(m, T, p, Y)
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    _vec(dlnA, m.R, "dlnA")
+    dfY = _species_out(m, n, ld, T)
+    dfT = _point_out(n, T)
+    fY = _species_out(m, n, ld, T) if primal else None
+    fT = _point_out(n, T) if primal else None
+    _check(lib().nk_rhs_jvp(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(dlnA), _ptr(vT), _ptr(vY),
+                            _ptr(fT), _ptr(fY), _ptr(dfT), _ptr(dfY), _stream(stream)))
+    if primal:
+        return dfT, dfY, fT, fY
+    return dfT, dfY
 
 
 def rates_vjp_workspace(m: Mechanism, n: int) -> int:

@@ -30,7 +30,7 @@ namespace {
 
 struct JvpPoint {
     TPairs P;
-    double invT, lnT, tT, dT, pRT, dpRT;
+    double invT, lnT, tT, dT, pRT, dpRT, arho;   // arho = d rho / rho
 };
 
 struct JvpAcc {
@@ -39,7 +39,7 @@ struct JvpAcc {
     double dh = 0.0;   // sum_r dq_r dH_r/RT
 };
 
-template <int BLK, int KIND, bool OMEGA>
+template <int BLK, int KIND, bool OMEGA, bool RHS>
 __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const double* sC, const double* sdC, double* sW,
                                              double* sD, const JvpPoint& Q, const double* dlnA, const DfTab& dt,
                                              JvpAcc& acc) {
@@ -156,18 +156,21 @@ __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const doub
         dq = fma(dq, M, q * dM);
         q *= M;
     }
+    // the sources' tangent W_k (d omega_k - omega_k d rho/rho) / rho is linear in the
+    // reactions: scatter dq - q d rho/rho and no omega_k row is needed
+    const double dqs = RHS ? fma(-Q.arho, q, dq) : dq;
 #pragma unroll
     for (int e = 0; e < kMaxSide; ++e)
         if (e < x.nr) {
             const int k = x.sp[e];
-            sD[k * BLK] = fma(x.nud[e], dq, sD[k * BLK]);
+            sD[k * BLK] = fma(x.nud[e], dqs, sD[k * BLK]);
             if (OMEGA) sW[k * BLK] = fma(x.nud[e], q, sW[k * BLK]);
         }
 #pragma unroll
     for (int e = 0; e < kMaxSide; ++e)
         if (e < x.np) {
             const int k = x.sp[kMaxSide + e];
-            sD[k * BLK] = fma(x.nud[kMaxSide + e], dq, sD[k * BLK]);
+            sD[k * BLK] = fma(x.nud[kMaxSide + e], dqs, sD[k * BLK]);
             if (OMEGA) sW[k * BLK] = fma(x.nud[kMaxSide + e], q, sW[k * BLK]);
         }
     acc.h = fma(q, sumh, acc.h);
@@ -175,18 +178,20 @@ __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const doub
     acc.dh = fma(dq, sumh, acc.dh);
 }
 
-template <int BLK, int KIND, bool OMEGA>
+template <int BLK, int KIND, bool OMEGA, bool RHS>
 __device__ __forceinline__ void jvp_group(const DevMech& m, int r0, int r1, const double* sC, const double* sdC,
                                           double* sW, double* sD, const JvpPoint& Q, const double* dlnA,
                                           const DfTab& dt, JvpAcc& acc) {
-    for (int r = r0; r < r1; ++r) jvp_reaction<BLK, KIND, OMEGA>(m, r, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    for (int r = r0; r < r1; ++r) jvp_reaction<BLK, KIND, OMEGA, RHS>(m, r, sC, sdC, sW, sD, Q, dlnA, dt, acc);
 }
 
 // Per-point species rows: C_k, dC_k, then NP rows of d omega_k partials and, with OMEGA, NP
 // rows of omega_k partials.
 __host__ __device__ constexpr int jvp_rows(int np, bool omega) { return 2 + np * (omega ? 2 : 1); }
 
-template <int BLK, int NP, bool OMEGA>
+// RHS: the JVP of the implicit-stage sources (omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p)
+// and their tangents in d_omega, d_hrr).
+template <int BLK, int NP, bool OMEGA, bool RHS>
 __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                        const double* __restrict__ T, const double* __restrict__ p,
                                                        const double* __restrict__ Y, const double* __restrict__ dlnA,
@@ -227,6 +232,7 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
     }
     const double rho = Q.pRT / s;
     const double arho = -Q.tT - ds / s;                  // d rho / rho
+    Q.arho = arho;
     for (int k = part; k < K; k += NP) {
         const double iw = __ldg(m.invW + k);
         const double c = Y[(int64_t)k * ld + i] * iw * rho;
@@ -243,45 +249,83 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
     int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
     slice<NP>(0, e1, part, a, b);
-    jvp_group<BLK, 0, OMEGA>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    jvp_group<BLK, 0, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
     slice<NP>(e1, t1, part, a, b);
-    jvp_group<BLK, 1, OMEGA>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    jvp_group<BLK, 1, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
     slice<NP>(t1, m.R, part, a, b);
-    jvp_group<BLK, 2, OMEGA>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    jvp_group<BLK, 2, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
     if (NP > 1) __syncthreads();
 
+    // Implicit-stage sources (RHS): fY_k = W_k omega_k / rho, fT = hrr / (rho c_p) with
+    // c_p = R sum_k Y_k/W_k c_p,k/R; tangents dfY_k = W_k (d omega_k - omega_k d rho/rho) / rho
+    // (the shifted scatter above), dfT = (d hrr - hrr (d rho/rho + d c_p/c_p)) / (rho c_p).
+    double cpm = 0.0, dcpm = 0.0, inv_rho = 0.0;
+    if constexpr (RHS) inv_rho = 1.0 / rho;
     for (int k = part; k < K; k += NP) {
         double dw = sD0[k * BLK];
 #pragma unroll
         for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
-        if (live) d_omega[(int64_t)k * ld + i] = dw;
-        if (OMEGA) {
-            double w = sW0[k * BLK];
+        double w = 0.0;
+        if constexpr (OMEGA) {
+            w = sW0[k * BLK];
 #pragma unroll
             for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
-            if (live) omega[(int64_t)k * ld + i] = w;
+        }
+        if constexpr (RHS) {
+            const double* c = nasa_range(m, k, Ti);
+            const double iw = __ldg(m.invW + k), cpk = nasa_cpR(c, Ti);
+            const double yk = Y[(int64_t)k * ld + i] * iw, vk = vY[(int64_t)k * ld + i] * iw;
+            cpm = fma(yk, cpk, cpm);
+            dcpm = fma(vk, cpk, fma(yk * nasa_dcpR_dT(c, Ti), Q.dT, dcpm));
+            const double wr = __ldg(m.W + k) * inv_rho;
+            dw *= wr;
+            w *= wr;
+        }
+        if (live) {
+            d_omega[(int64_t)k * ld + i] = dw;
+            if (OMEGA) omega[(int64_t)k * ld + i] = w;
         }
     }
     if constexpr (NP > 1) {
-        // C_k is dead: rows 3q, 3q+1, 3q+2 (3 NP <= K) take part q's sums, added in part order
+        // C_k and dC_k are dead: rows 3q .. 3q+2 of C and 2q, 2q+1 of dC (3 NP <= K) take part
+        // q's sums, added in part order
         sC[(3 * part) * BLK] = acc.h;
         sC[(3 * part + 1) * BLK] = acc.cp;
         sC[(3 * part + 2) * BLK] = acc.dh;
+        if constexpr (RHS) {
+            sdC[(2 * part) * BLK] = cpm;
+            sdC[(2 * part + 1) * BLK] = dcpm;
+        }
         __syncthreads();
         if (part != 0) return;
         acc.h = sC[0];
         acc.cp = sC[BLK];
         acc.dh = sC[2 * BLK];
+        if constexpr (RHS) {
+            cpm = sdC[0];
+            dcpm = sdC[BLK];
+        }
 #pragma unroll
         for (int q = 1; q < NP; ++q) {
             acc.h += sC[(3 * q) * BLK];
             acc.cp += sC[(3 * q + 1) * BLK];
             acc.dh += sC[(3 * q + 2) * BLK];
+            if constexpr (RHS) {
+                cpm += sdC[(2 * q) * BLK];
+                dcpm += sdC[(2 * q + 1) * BLK];
+            }
         }
     }
     if (live) {
-        d_hrr[i] = -kR * fma(Q.dT, acc.cp, Ti * acc.dh);
-        if (hrr) hrr[i] = -kR * Ti * acc.h;
+        const double dhr = -kR * fma(Q.dT, acc.cp, Ti * acc.dh), hr = -kR * Ti * acc.h;
+        if constexpr (RHS) {
+            const double irc = inv_rho / (kR * cpm);                 // 1 / (rho c_p)
+            d_hrr[i] = irc * fma(-hr, arho + dcpm / cpm, dhr);
+            if (hrr) hrr[i] = hr * irc;
+        } else {
+            d_hrr[i] = dhr;
+            if (hrr) hrr[i] = hr;
+        }
     }
 }
 
@@ -292,14 +336,14 @@ struct Shape {
 constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <bool OMEGA, int S>
+template <bool OMEGA, bool RHS, int S>
 constexpr auto kernel_of() {
-    return jvp_kernel<kShapes[S].blk, kShapes[S].np, OMEGA>;
+    return jvp_kernel<kShapes[S].blk, kShapes[S].np, OMEGA, RHS>;
 }
 
-template <bool OMEGA, int... S>
+template <bool OMEGA, bool RHS, int... S>
 const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
-    const void* ptrs[] = {(const void*)kernel_of<OMEGA, S>()...};
+    const void* ptrs[] = {(const void*)kernel_of<OMEGA, RHS, S>()...};
     return ptrs[idx];
 }
 
@@ -309,7 +353,7 @@ size_t jvp_smem(int K, const Shape& sh, bool omega) {
 
 struct Plan {
     int dev, K;
-    bool omega;
+    bool omega, rhs;
     int idx;
 };
 std::mutex g_plan_mu;
@@ -317,14 +361,14 @@ std::vector<Plan> g_plans;
 
 // The shape with the most resident warps per SM, fewer parts on ties (cached per device, K
 // and output set).
-template <bool OMEGA>
+template <bool OMEGA, bool RHS>
 int plan_shape(int K) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         for (const Plan& q : g_plans)
-            if (q.dev == dev && q.K == K && q.omega == OMEGA) return q.idx;
+            if (q.dev == dev && q.K == K && q.omega == OMEGA && q.rhs == RHS) return q.idx;
     }
     int per_block = 0;
     cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -334,7 +378,7 @@ int plan_shape(int K) {
         if (3 * sh.np > K && sh.np > 1) continue;
         const size_t bytes = jvp_smem(K, sh, OMEGA);
         if (bytes > (size_t)per_block) continue;
-        const void* kern = kernel_ptr<OMEGA>(c, std::make_integer_sequence<int, kNumShapes>{});
+        const void* kern = kernel_ptr<OMEGA, RHS>(c, std::make_integer_sequence<int, kNumShapes>{});
         if (ensure_smem(kern, bytes) != cudaSuccess) continue;
         int blocks = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
@@ -347,19 +391,20 @@ int plan_shape(int K) {
     }
     if (best >= 0) {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        g_plans.push_back({dev, K, OMEGA, best});
+        g_plans.push_back({dev, K, OMEGA, RHS, best});
     }
     return best;
 }
 
-template <bool OMEGA, int... S>
+template <bool OMEGA, bool RHS, int... S>
 cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
                        const double* T, const double* p, const double* Y, const double* dlnA, const double* vT,
-                       const double* vY, double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t st) {
+                       const double* vY, double* omega, double* hrr, double* d_omega, double* d_hrr,
+                       cudaStream_t st) {
     cudaError_t e = cudaErrorInvalidConfiguration;
     ((S == idx ? (void)(e = [&] {
         constexpr Shape sh = kShapes[S];
-        auto kern = kernel_of<OMEGA, S>();
+        auto kern = kernel_of<OMEGA, RHS, S>();
         const size_t smem = jvp_smem(m.K, sh, OMEGA);
         cudaError_t r = ensure_smem((const void*)kern, smem);
         if (r != cudaSuccess) return r;
@@ -372,24 +417,28 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech&
     return e;
 }
 
-template <bool OMEGA>
+template <bool OMEGA, bool RHS>
 cudaError_t launch_o(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
                      const double* dlnA, const double* vT, const double* vY, double* omega, double* hrr,
                      double* d_omega, double* d_hrr, cudaStream_t s) {
-    const int idx = plan_shape<OMEGA>(m.K);
+    const int idx = plan_shape<OMEGA, RHS>(m.K);
     if (idx < 0) return cudaErrorInvalidConfiguration;
-    return launch_idx<OMEGA>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, vT, vY,
-                             omega, hrr, d_omega, d_hrr, s);
+    return launch_idx<OMEGA, RHS>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, vT,
+                                  vY, omega, hrr, d_omega, d_hrr, s);
 }
 
 }  // namespace
 
 cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* vT, const double* vY, double* omega,
-                       double* hrr, double* d_omega, double* d_hrr, cudaStream_t s) {
+                       double* hrr, double* d_omega, double* d_hrr, cudaStream_t s, int rhs) {
     static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
-    if (omega) return launch_o<true>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
-    return launch_o<false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
+    if (rhs) {
+        if (omega) return launch_o<true, true>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
+        return launch_o<false, true>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
+    }
+    if (omega) return launch_o<true, false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
+    return launch_o<false, false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
 }
 
 }  // namespace nk

@@ -326,7 +326,9 @@ __host__ __device__ constexpr int shared_rows() {
 // blockIdx.x * BLK + slot.  The parts of a point share its C_k (and g_k/RT), each walks its
 // own slice of every kind and accumulates into its own omega_k partials; the partials are
 // added in part order, so results do not depend on scheduling.
-template <int BLK, int NP, int PREC>
+//
+// RHS: write the implicit-stage sources instead: omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p).
+template <int BLK, int NP, int PREC, bool RHS>
 __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                          const double* __restrict__ T, const double* __restrict__ p,
                                                          const double* __restrict__ Y,
@@ -384,23 +386,43 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     reaction_group<BLK, PREC, 2>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
     if (NP > 1) __syncthreads();
 
-    double h = 0.0;
+    // omega_k (or the source W_k omega_k / rho), sum_k h_k/RT omega_k and, for the sources,
+    // c_p/R = sum_k Y_k/W_k c_p,k/R of this part's species
+    double h = 0.0, cpm = 0.0, inv_rho = 0.0;
+    if constexpr (RHS) inv_rho = 1.0 / rho_w;
     for (int k = part; k < K; k += NP) {
         double w = sW0[k * BLK];
 #pragma unroll
         for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
+        const double* c = nasa_range(m, k, P.T);
+        h = fma(nasa_hRT(c, P.T, P.invT), w, h);
+        if constexpr (RHS) {
+            cpm = fma(Y[(int64_t)k * ld + i] * __ldg(m.invW + k), nasa_cpR(c, P.T), cpm);
+            w *= __ldg(m.W + k) * inv_rho;
+        }
         if (live) omega[(int64_t)k * ld + i] = w;
-        h = fma(nasa_hRT(nasa_range(m, k, P.T), P.T, P.invT), w, h);
     }
     if constexpr (NP > 1) {
-        sC[part * BLK] = h;                            // C_k is dead; rows 0..NP-1 (NP <= K) hold the partials
+        // C_k is dead: rows q (and NP + q for the sources; (1 + RHS) NP <= K) take part q's
+        // sums, added in part order
+        sC[part * BLK] = h;
+        if constexpr (RHS) sC[(NP + part) * BLK] = cpm;
         __syncthreads();
         if (part != 0) return;
         h = sC[0];
+        if constexpr (RHS) cpm = sC[NP * BLK];
 #pragma unroll
-        for (int q = 1; q < NP; ++q) h += sC[q * BLK];
+        for (int q = 1; q < NP; ++q) {
+            h += sC[q * BLK];
+            if constexpr (RHS) cpm += sC[(NP + q) * BLK];
+        }
     }
-    if (live) hrr[i] = -kR * P.T * h;                  // -sum_k h_k omega_k
+    const double hr = -kR * P.T * h;                   // heat release -sum_k h_k omega_k
+    if constexpr (RHS) {
+        if (live) hrr[i] = hr * inv_rho / (kR * cpm);  // dT/dt = hrr / (rho c_p)
+    } else {
+        if (live) hrr[i] = hr;
+    }
 }
 
 struct Shape {
@@ -411,25 +433,25 @@ struct Shape {
 constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <int PREC, int S>
+template <int PREC, bool RHS, int S>
 constexpr auto kernel_of() {
-    return rates_kernel<kShapes[S].blk, kShapes[S].np, PREC>;
+    return rates_kernel<kShapes[S].blk, kShapes[S].np, PREC, RHS>;
 }
 
-template <int PREC, int... S>
+template <int PREC, bool RHS, int... S>
 const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
-    const void* ptrs[] = {(const void*)kernel_of<PREC, S>()...};
+    const void* ptrs[] = {(const void*)kernel_of<PREC, RHS, S>()...};
     return ptrs[idx];
 }
 
-template <int PREC, int... S>
+template <int PREC, bool RHS, int... S>
 cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
                        const double* T, const double* p, const double* Y, const double* dlnA, double* omega,
                        double* hrr, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaErrorInvalidConfiguration;
     ((S == idx ? (void)(e = [&] {
         constexpr Shape sh = kShapes[S];
-        auto kern = kernel_of<PREC, S>();
+        auto kern = kernel_of<PREC, RHS, S>();
         cudaError_t r = ensure_smem((const void*)kern, smem);
         if (r != cudaSuccess) return r;
         kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega,
@@ -452,19 +474,19 @@ size_t rates_smem(int K, const Shape& sh) {
 // registers, threads), fewer parts on ties.  Cached per
 // (device, K, form).
 struct Plan {
-    int dev, K, prec, idx;
+    int dev, K, prec, rhs, idx;
 };
 std::mutex g_plan_mu;
 std::vector<Plan> g_plans;
 
-template <int PREC>
+template <int PREC, bool RHS>
 int plan_shape(int K) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         for (const Plan& q : g_plans)
-            if (q.dev == dev && q.K == K && q.prec == PREC) return q.idx;
+            if (q.dev == dev && q.K == K && q.prec == PREC && q.rhs == (int)RHS) return q.idx;
     }
     int per_block = 0;
     cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -472,10 +494,10 @@ int plan_shape(int K) {
     int best = -1, best_warps = 0;
     for (int c = 0; c < kNumShapes; ++c) {
         const Shape& sh = kShapes[c];
-        if (sh.np > K) continue;
+        if ((RHS ? 2 : 1) * sh.np > K && sh.np > 1) continue;
         const size_t bytes = rates_smem<PREC>(K, sh);
         if (bytes > (size_t)per_block) continue;
-        const void* kern = kernel_ptr<PREC>(c, seq);
+        const void* kern = kernel_ptr<PREC, RHS>(c, seq);
         if (ensure_smem(kern, bytes) != cudaSuccess) continue;
         int blocks = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
@@ -488,30 +510,37 @@ int plan_shape(int K) {
     }
     if (best >= 0) {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        g_plans.push_back({dev, K, PREC, best});
+        g_plans.push_back({dev, K, PREC, (int)RHS, best});
     }
     return best;
 }
 
+template <int PREC, bool RHS>
+cudaError_t launch_form(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                        const double* dlnA, double* omega, double* hrr, cudaStream_t s) {
+    const int idx = plan_shape<PREC, RHS>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<PREC, RHS>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, omega,
+                                 hrr, rates_smem<PREC>(m.K, kShapes[idx]), s);
+}
+
 template <int PREC>
 cudaError_t launch_prec(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
-                        const double* dlnA, double* omega, double* hrr, cudaStream_t s) {
-    const int idx = plan_shape<PREC>(m.K);
-    if (idx < 0) return cudaErrorInvalidConfiguration;
-    return launch_idx<PREC>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, omega, hrr,
-                            rates_smem<PREC>(m.K, kShapes[idx]), s);
+                        const double* dlnA, double* omega, double* hrr, cudaStream_t s, int rhs) {
+    if (rhs) return launch_form<PREC, true>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
+    return launch_form<PREC, false>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
 }
 
 }  // namespace
 
 cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                          const double* Y, const double* dlnA, double* omega, double* hrr, int precision,
-                         cudaStream_t s) {
+                         cudaStream_t s, int rhs) {
     // the staged tables (kMathTabDoubles doubles) cover the kDF tables too (3 x 128 pairs)
     static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
-    if (precision == NK_MIXED) return launch_prec<kMixed>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
-    if (precision == NK_FP64_NATIVE) return launch_prec<kNative>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
-    return launch_prec<kDF>(m, n, ld, T, p, Y, dlnA, omega, hrr, s);
+    if (precision == NK_MIXED) return launch_prec<kMixed>(m, n, ld, T, p, Y, dlnA, omega, hrr, s, rhs);
+    if (precision == NK_FP64_NATIVE) return launch_prec<kNative>(m, n, ld, T, p, Y, dlnA, omega, hrr, s, rhs);
+    return launch_prec<kDF>(m, n, ld, T, p, Y, dlnA, omega, hrr, s, rhs);
 }
 
 }  // namespace nk

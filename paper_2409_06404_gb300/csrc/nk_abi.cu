@@ -373,7 +373,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
 
     // ---- one device block for everything
     Layout L;
-    const size_t o_invW = L.add(K * 8), o_Tmid = L.add(K * 8), o_nasa = L.add(nasa.size() * 8),
+    const size_t o_W = L.add(K * 8), o_invW = L.add(K * 8), o_Tmid = L.add(K * 8), o_nasa = L.add(nasa.size() * 8),
                  o_rxn = L.add(R * sizeof(nk::RxnRec)), o_rxnf = L.add(R * sizeof(nk::RxnRecF)),
                  o_troe = L.add(troe.size() * sizeof(nk::TroeRec) + 16),
                  o_troef = L.add(troef.size() * sizeof(nk::TroeRecF) + 16), o_mtab = L.add(mtab.size() * 8),
@@ -392,6 +392,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
     };
+    put(o_W, d->W, K * 8);
     put(o_invW, invW.data(), K * 8);
     put(o_Tmid, Tmid.data(), K * 8);
     put(o_nasa, nasa.data(), nasa.size() * 8);
@@ -460,6 +461,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.mtab = reinterpret_cast<const double*>(b + o_mtab);
     dm.p_ref = d->p_ref;
     dm.invW = reinterpret_cast<const double*>(b + o_invW);
+    dm.W = reinterpret_cast<const double*>(b + o_W);
     dm.Tmid = reinterpret_cast<const double*>(b + o_Tmid);
     dm.nasa = reinterpret_cast<const double*>(b + o_nasa);
     dm.rxn = reinterpret_cast<const nk::RxnRec*>(b + o_rxn);
@@ -610,6 +612,31 @@ nk_status nk_rates_jvp(const nk_mech* m, int64_t n, int64_t ld, const double* T,
     if ((st = check_out({vT, vY, d_omega, d_hrr, omega, hrr, dlnA})) != NK_OK) return st;
     return launched(nk::launch_jvp(m->d, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr,
                                    (cudaStream_t)stream),
+                    "jvp kernel launch");
+}
+
+nk_status nk_rhs_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                      const double* dlnA, double* fT, double* fY, nk_precision precision, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (precision != NK_FP64 && precision != NK_MIXED && precision != NK_FP64_NATIVE)
+        return fail(NK_EINVAL, "bad precision %d", (int)precision);
+    if (!fT || !fY) return fail(NK_EINVAL, "fT and fY must not be NULL");
+    if ((st = check_out({fT, fY, dlnA})) != NK_OK) return st;
+    return launched(nk::launch_rates(m->d, n, ld, T, p, Y, dlnA, fY, fT, (int)precision, (cudaStream_t)stream, 1),
+                    "rates kernel launch");
+}
+
+nk_status nk_rhs_jvp(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                     const double* dlnA, const double* vT, const double* vY, double* fT, double* fY, double* dfT,
+                     double* dfY, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!vT || !vY || !dfT || !dfY) return fail(NK_EINVAL, "vT, vY, dfT and dfY must not be NULL");
+    if ((st = check_out({vT, vY, dfT, dfY, fT, fY, dlnA})) != NK_OK) return st;
+    return launched(nk::launch_jvp(m->d, n, ld, T, p, Y, dlnA, vT, vY, fY, fT, dfY, dfT, (cudaStream_t)stream, 1),
                     "jvp kernel launch");
 }
 

@@ -90,6 +90,7 @@ struct DevMech {
     double p_ref;
     const double* mtab;           // exp/log tables (kMathTabDoubles, see nk_math.cuh)
     const double* invW;           // [K] 1/W
+    const double* W;              // [K] W, kg/mol
     const double* Tmid;           // [K]
     const double* nasa;           // [K][2][16]
     const RxnRec* rxn;            // [R]
@@ -150,18 +151,22 @@ cudaError_t launch_thermo(const DevMech& m, int64_t n, int64_t ld, const double*
                           const double* p, const double* Y, double* cp_mix, double* h_mix,
                           double* Wbar, double* rho, double* cp_k, double* h_k, double* g_k,
                           cudaStream_t s);
+// rhs = 1: write the implicit-stage sources instead (omega -> dY/dt, hrr -> dT/dt).
 cudaError_t launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                          const double* Y, const double* dlnA, double* omega, double* hrr,
-                         int precision, cudaStream_t s);
+                         int precision, cudaStream_t s, int rhs = 0);
 cudaError_t launch_transport(const DevMech& m, int64_t n, int64_t ld, const double* T,
                              const double* p, const double* Y, double* mu, double* lam,
                              double* Dmix, int precision, cudaStream_t s);
 cudaError_t launch_transport_df(const DevMech& m, int64_t n, int64_t ld, const double* T,
                                 const double* p, const double* Y, double* mu, double* lam,
                                 double* Dmix, cudaStream_t s);
+// rhs = 1: the JVP of the implicit-stage sources (omega, hrr -> dY/dt, dT/dt, both nullable;
+// d_omega, d_hrr -> their tangents).
 cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* vT, const double* vY,
-                       double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s);
+                       double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s,
+                       int rhs = 0);
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n);
 cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* bar_omega,
@@ -201,6 +206,10 @@ __device__ __forceinline__ double nasa_hRT(const double* c, double T, double inv
 }
 __device__ __forceinline__ double nasa_cpR(const double* c, double T) {
     return fma(T, fma(T, fma(T, fma(T, __ldg(c + 4), __ldg(c + 3)), __ldg(c + 2)), __ldg(c + 1)), __ldg(c + 0));
+}
+// d(c_p/R)/dT = a2 + 2 a3 T + 3 a4 T^2 + 4 a5 T^3
+__device__ __forceinline__ double nasa_dcpR_dT(const double* c, double T) {
+    return fma(T, fma(T, fma(T, 4.0 * __ldg(c + 4), 3.0 * __ldg(c + 3)), 2.0 * __ldg(c + 2)), __ldg(c + 1));
 }
 
 // x^nu for a small positive integer nu (uniform across the warp)
