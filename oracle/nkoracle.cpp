@@ -26,7 +26,10 @@
  *   8. omega_k = sum_r nu_kr q_r;  hrr = -sum_k h_k omega_k  (molar h_k(T))
  *   9. mixture-averaged transport: Wilke viscosity, Mathur conductivity, Hirschfelder-Curtiss
  *      diffusion coefficients D_km = sum_{j!=k} X_j W_j / (Wbar sum_{j!=k} X_j/D_jk)
- *  10. derivatives by complex step (h = 1e-30) through the same templated code.
+ *  10. derivatives by complex step (h = 1e-100) through the same templated code: Im f(x + i h v)/h
+ *      equals the directional derivative up to a third-derivative term times h^2/6, negligible
+ *      at h = 1e-100 even at pure or nearly pure mixtures, where third derivatives in the
+ *      concentrations reach ~1e80 and a step of 1e-30 would bias the result by ~1e20.
  *  11. implicit-stage chemistry sources of Eq. 1a-b at fixed p: dY_k/dt = W_k omega_k / rho,
  *      dT/dt = hrr / (rho c_p), c_p the mass-based mixture heat capacity; their directional
  *      derivatives by complex step as in 10.
@@ -445,7 +448,7 @@ void or_thermo(const or_mech* m, int64_t n, int64_t ld, const double* T, const d
  * through the same NASA-7 code, at n temperatures, for species k. */
 void or_nasa7_cs(const or_mech* m, int k, int64_t n, const double* T, double* cp, double* h,
                  double* s, double* dh_dT, double* ds_dT) {
-    const double hstep = 1e-30;
+    const double hstep = 1e-100;
     for (int64_t i = 0; i < n; ++i) {
         cplx Tc(T[i], hstep), cpR, hRT, sR;
         nasa7(*m, k, Tc, cpR, hRT, sR);
@@ -524,7 +527,7 @@ void or_transport(const or_mech* m, int64_t n, int64_t ld, const double* T, cons
 void or_rates_jacobian(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, double* J, double* Js, int nthreads) {
     const int K = m->K, R = m->R, N = K + 1;
-    const double hstep = 1e-30;
+    const double hstep = 1e-100;
 #pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
     for (int64_t i = 0; i < n; ++i) {
         std::vector<cplx> y(K), w(K), sh(R);
@@ -554,7 +557,7 @@ void or_rates_jvp(const or_mech* m, int64_t n, int64_t ld, const double* T, cons
                   const double* Y, const double* dlnA, const double* vT, const double* vY,
                   double* d_omega, double* d_hrr, double* d_omega_scale, double* d_hrr_scale, int nthreads) {
     const int K = m->K, R = m->R;
-    const double hstep = 1e-30;
+    const double hstep = 1e-100;
 #pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
     for (int64_t i = 0; i < n; ++i) {
         std::vector<cplx> y(K), w(K), sh(R);
@@ -581,7 +584,7 @@ void or_rates_grad_lnA(const or_mech* m, int64_t n, int64_t ld, const double* T,
                        double* g, int nthreads) {
     const int K = m->K, R = m->R;
     const int nt = nthreads_of(nthreads);
-    const double hstep = 1e-30;
+    const double hstep = 1e-100;
     std::vector<double> part((size_t)nt * R, 0.0);
 #pragma omp parallel num_threads(nt)
     {
@@ -656,7 +659,7 @@ void or_rhs_jvp(const or_mech* m, int64_t n, int64_t ld, const double* T, const 
                 const double* vT, const double* vY, double* dfT, double* dfY, double* dfT_scale, double* dfY_scale,
                 int nthreads) {
     const int K = m->K;
-    const double hstep = 1e-30;
+    const double hstep = 1e-100;
 #pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
     for (int64_t i = 0; i < n; ++i) {
         std::vector<cplx> y(K), f(K);
