@@ -13,8 +13,9 @@ Each launch is bracketed by CUDA events on the launching stream.  The headline v
 Mpoints/s of rates + transport in FP64 (points / (t_rates + t_transport) summed over the
 timed steps); the mixed form, JVP/forward and VJP/forward ratios come from the same steps.
 After the timed steps, the all-double forms of rates and transport (NK_FP64_NATIVE, the
-plain-FP64 arithmetic the FP64 form is checked against) and the implicit-stage sources and
-their JVP (nk_rhs_eval, nk_rhs_jvp) are timed the same way in a separate loop
+plain-FP64 arithmetic the FP64 form is checked against), the implicit-stage sources and their
+JVP (nk_rhs_eval, nk_rhs_jvp) and the stored linearization with one JVP from it
+(nk_rates_linearize, nk_rates_jvp_linearized) are timed the same way in a separate loop
 ("fp64_native_value", rows); they are not part of a step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -93,9 +94,13 @@ def algorithmic_flops(mech) -> dict:
     vjp = pre + K * 24 + per_rxn_d + 10 * R + K * 8
     rhs = rates + K * 12 + 4                        # W_k/rho factors, c_p, 1/(rho c_p)
     rhs_jvp = jvp + K * 24 + 12                     # primal omega, c_p and d c_p, both source tangents
+    # per direction from stored coefficients: dq_r = A tT + sum_e B_e dC_e (+ L d[M]), the scatter
+    n_ent = sum(len(_entries(mech, r)[0]) + len(_entries(mech, r)[1]) for r in range(R))
+    jvp_lin = 2 * R + 2 * n_ent + 2 * n_ent + sum(2 * n_eff[r] + 4 for r in range(R) if mech.rtype[r]) \
+        + K * (6 + 4) + K * 2 + 4
     return {"thermo": thermo, "rates_fp64": rates, "transport_fp64": transport, "rates_fp64_native": rates,
             "transport_fp64_native": transport, "rates_mixed": rates, "transport_mixed": transport, "jvp": jvp,
-            "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp}
+            "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp, "linearize": jvp, "jvp_linearized": jvp_lin}
 
 
 # ---------------------------------------------------------------------------------- clocks
@@ -294,16 +299,37 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
             ts.append(a.elapsed_time(b))
         return sum(ts) / len(ts)
 
+    lin = None
+    try:
+        lin = torch.empty((nk.linearization_slots(m), n), dtype=torch.float64, device=T.device)
+    except RuntimeError:                       # the stored data do not fit: recompute only
+        pass
+
+    def ours_lin():
+        nk.thermo_eval(m, T, p, Y)
+        nk.rates_eval(m, T, p, Y, precision="mixed")
+        nk.transport_eval(m, T, p, Y, precision="mixed")
+        nk.rates_linearize(m, T, p, Y, lin=lin)
+        out = None
+        for vT, vY in dirs:
+            out = nk.rates_jvp_linearized(m, T, p, Y, lin, vT, vY)
+        return out
+
     t_ours, t_fd = timed(ours), timed(fd)
+    t_lin = timed(ours_lin) if lin is not None else None
     # accuracy of the difference quotient against the exact JVP, last direction
     dw, dh = nk.rates_jvp(m, T, p, Y, *dirs[-1])
     fw, fh = fd()
     sc = dw.abs().amax(0).clamp_min(1e-300)
     fd_err = ((fw - dw).abs().amax(0) / sc).median().item()
-    return {"points": n, "directions": n_dir, "sweep_ms": t_ours, "fd_fp64_sweep_ms": t_fd,
-            "speedup_vs_fd": t_fd / t_ours, "fd_jvp_median_rel_err": fd_err,
-            "sweep": "thermo (FP64) + rates, transport (mixed) + exact JVPs",
-            "fd_sweep": "thermo, rates, transport (FP64) + FP64 rates at x + sigma v per direction"}
+    res = {"points": n, "directions": n_dir, "sweep_ms": t_ours, "fd_fp64_sweep_ms": t_fd,
+           "speedup_vs_fd": t_fd / t_ours, "fd_jvp_median_rel_err": fd_err,
+           "sweep": "thermo (FP64) + rates, transport (mixed) + exact JVPs recomputed per direction",
+           "fd_sweep": "thermo, rates, transport (FP64) + FP64 rates at x + sigma v per direction"}
+    if t_lin is not None:
+        res.update({"sweep_linearized_ms": t_lin, "speedup_linearized_vs_fd": t_fd / t_lin,
+                    "sweep_linearized": "the same forward + one stored linearization + exact JVPs from it"})
+    return res
 
 
 # ---------------------------------------------------------------------------------- our arm
@@ -337,6 +363,7 @@ def run_ours(args):
                                                "dh", "gT")}
     out.update({k: torch.empty((K, n), **f64) for k in ("w", "D", "w_m", "D_m", "dw", "gY")})
     g_lnA = torch.empty(R, **f64)
+    lin = torch.empty((nk.linearization_slots(m), n), **f64)    # stored linearization (~15 KB per point)
     wsb = torch.empty(max(nk.rates_vjp_workspace(m, n), 8), dtype=torch.uint8, device=dev)
     L = nk.lib()
     s = torch.cuda.current_stream()
@@ -371,6 +398,9 @@ def run_ours(args):
         "rhs_fp64": lambda: chk(L.nk_rhs_eval(h, n, n, P(T), P(p), P(Y), None, P(out["hrr"]), P(out["w"]), 0, sp)),
         "rhs_jvp": lambda: chk(L.nk_rhs_jvp(h, n, n, P(T), P(p), P(Y), None, P(vT), P(vY), None, None,
                                             P(out["dh"]), P(out["dw"]), sp)),
+        "linearize": lambda: chk(L.nk_rates_linearize(h, n, n, P(T), P(p), P(Y), None, P(lin), n, sp)),
+        "jvp_linearized": lambda: chk(L.nk_rates_jvp_linearized(h, n, n, P(T), P(p), P(Y), P(lin), n, P(vT), P(vY),
+                                                                P(out["dw"]), P(out["dh"]), sp)),
     }
     launches_per_step = {"thermo": 1, "rates_fp64": 1, "transport_fp64": 1, "rates_mixed": 1,
                          "transport_mixed": 1, "jvp": 1, "vjp": 2}

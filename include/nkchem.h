@@ -212,6 +212,26 @@ nk_status nk_rhs_jvp(const nk_mech* mech, int64_t n, int64_t ld, const double* T
                      double* fT, double* fY, double* dfT, double* dfY, nk_stream stream);
 
 /*
+ * Stored linearization of (omega_k, hrr) at one state, for several Jacobian-vector products
+ * at that state (the Newton-Krylov stage issues several per step, Sec. 2 and 4).  The
+ * state-only part of nk_rates_jvp -- exponentials, thermo polynomials, concentration
+ * products -- is evaluated once and kept per point:
+ *   *slots   doubles per point of the stored data (depends on the mechanism only)
+ *   lin      device [slots][ldl], ldl >= n, caller-owned; written by nk_rates_linearize
+ * nk_rates_jvp_linearized then forms (d_omega, d_hrr) = J (vT, vY) from lin and the state,
+ * which must be the one lin was made at (same T, p, Y, dlnA).  Results agree with
+ * nk_rates_jvp to rounding (FP64 form).  Use it when slots * ldl * 8 bytes fit beside the
+ * fields; otherwise nk_rates_jvp recomputes everything per direction.
+ */
+nk_status nk_rates_linearization_slots(const nk_mech* mech, int64_t* slots);
+nk_status nk_rates_linearize(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                             const double* Y, const double* dlnA, double* lin, int64_t ldl, nk_stream stream);
+nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                                  const double* p, const double* Y, const double* lin, int64_t ldl,
+                                  const double* vT, const double* vY, double* d_omega, double* d_hrr,
+                                  nk_stream stream);
+
+/*
  * Bytes of device workspace nk_rates_vjp needs for n points when g_lnA is requested
  * (per-block partial sums of the ln A gradient, reduced in a fixed order).
  */

@@ -68,6 +68,10 @@ _SIGS = {
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_rhs_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rhs_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
+    "nk_rates_linearization_slots": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "nk_rates_linearize": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "nk_rates_jvp_linearized": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                                               _vp]),
     "nk_rates_vjp_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_rates_vjp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [ctypes.c_size_t, _vp]),
     "nk_rates_vjp_noalloc": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 9 + [_vp]),
@@ -312,6 +316,40 @@ def rhs_jvp(m: Mechanism, T, p, Y, vT, vY, dlnA=None, primal=False, stream=None)
     if primal:
         return dfT, dfY, fT, fY
     return dfT, dfY
+
+
+def linearization_slots(m: Mechanism) -> int:
+    """Doubles per point of a stored rates linearization."""
+    v = _i64()
+    _check(lib().nk_rates_linearization_slots(m.handle, ctypes.byref(v)))
+    return v.value
+
+
+def rates_linearize(m: Mechanism, T, p, Y, dlnA=None, lin=None, stream=None):
+    """nk_rates_linearize: the state-only data of the rates JVP at (T, p, Y), a device tensor
+    [slots, n] to pass to rates_jvp_linearized with the same state."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _vec(dlnA, m.R, "dlnA")
+    if lin is None:
+        lin = torch.empty((linearization_slots(m), max(n, 1)), dtype=torch.float64, device=T.device)
+    _check(lib().nk_rates_linearize(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(dlnA), _ptr(lin),
+                                    lin.stride(0), _stream(stream)))
+    return lin
+
+
+def rates_jvp_linearized(m: Mechanism, T, p, Y, lin, vT, vY, stream=None):
+    """nk_rates_jvp_linearized: (d_omega, d_hrr) = J (vT, vY) from a stored linearization."""
+    n, ld = _state(m, T, p, Y)
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    if lin.dim() != 2 or lin.shape[0] != linearization_slots(m) or lin.stride(1) != 1 or lin.shape[1] < n:
+        raise ValueError("lin must be a [slots, >= n] row-major tensor from rates_linearize")
+    d_omega = _species_out(m, n, ld, T)
+    d_hrr = _point_out(n, T)
+    _check(lib().nk_rates_jvp_linearized(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0),
+                                         _ptr(vT), _ptr(vY), _ptr(d_omega), _ptr(d_hrr), _stream(stream)))
+    return d_omega, d_hrr
 
 
 def rates_vjp_workspace(m: Mechanism, n: int) -> int:

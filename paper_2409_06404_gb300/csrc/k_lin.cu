@@ -1,0 +1,470 @@
+// Stored linearization of the net production rates: the JVP of (omega_k, heat release) split
+// into a pass that evaluates everything that depends on the state only, and a cheap pass per
+// direction.  The Newton-Krylov stage of the paper (Sec. 2) asks for several Jacobian-vector
+// products at one state (about 7 per step, Sec. 4); when the per-point data fit in device
+// memory, the exponentials, thermo polynomials and concentration products are evaluated once.
+//
+// At fixed p, with tT = dT/T, the tangent of a rate of progress is linear in (tT, dC, d[M]):
+//   dq_r = A_r tT + sum_e B_re dC_e + L_r d[M],
+// elementary:  A = (q_f - q_r) a_T + q_r D_r,  B_e = k_f dfw/dC_e (reactants), -k_r drv/dC_e
+//              (products), with a_T = beta + Ea/(R T) and D_r = sum_k nu_k h_k/RT - sum_k nu_k
+//              (d ln k_f = a_T tT, d ln K_c = D_r tT);
+// third body:  q = q_c [M]: A, B scaled by [M] and L = q_c;
+// Troe:        d ln k_f = a_T tT + a_M d[M] (the falloff chain of the JVP kernel taken for
+//              the two unit tangents), A as above with that a_T, L = (q_f - q_r) a_M.
+// The concentration derivatives are exclusive products (no division), so zero concentrations
+// are exact.  Per direction: dC_k = C_k d rho/rho + rho dY_k/W_k, d[M] = -p/(RT) tT +
+// sum (eps - 1) dC, dq_r from the stored coefficients, d omega_k = sum_r nu_kr dq_r and
+//   d hrr = -R (dT sum_r q_r (sum_k nu_kr c_p,k/R) + T sum_k (h_k/RT) d omega_k),
+// the first sum and h_k/RT also stored.
+//
+// Per-point slots (double, stored as [slot][ldl] so the points of a warp are contiguous):
+//   [0, R)                    A_r (device order)
+//   [R, R + NB)               B entries: reaction r at R + lin_boff[r], reactants then products
+//   [R + NB, R + NB + R - R_el)  L_r of the third-body and Troe reactions
+//   R + NB + R - R_el         sum_r q_r (sum_k nu_kr c_p,k/R)
+//   then K slots              h_k/RT
+// The linearization pass uses the FP64 form of the rates kernel (exponent chains in
+// double-float pairs, the falloff chain in double); the apply pass is plain double.
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "nk_rxn.cuh"
+
+namespace nk {
+namespace {
+
+__host__ __device__ inline int64_t slot_M(const DevMech& m) { return (int64_t)m.R + m.lin_nb; }
+__host__ __device__ inline int64_t slot_S(const DevMech& m) { return slot_M(m) + (m.R - m.R_el); }
+__host__ __device__ inline int64_t slot_H(const DevMech& m) { return slot_S(m) + 1; }
+
+// prod of p[0..n) (returned) and, in ex[e], the product of all entries but e (n <= 4, uniform)
+__device__ __forceinline__ double exclusive_products(const double* p, int n, double* ex) {
+    switch (n) {
+        case 1:
+            ex[0] = 1.0;
+            return p[0];
+        case 2:
+            ex[0] = p[1];
+            ex[1] = p[0];
+            return p[0] * p[1];
+        case 3: {
+            const double a = p[0] * p[1];
+            ex[0] = p[1] * p[2];
+            ex[1] = p[0] * p[2];
+            ex[2] = a;
+            return a * p[2];
+        }
+        default: {
+            const double a = p[0] * p[1], b = p[2] * p[3];
+            ex[0] = p[1] * b;
+            ex[1] = p[0] * b;
+            ex[2] = a * p[3];
+            ex[3] = a * p[2];
+            return a * b;
+        }
+    }
+}
+
+struct LinPoint {
+    TPairs P;
+    double invT, lnT, pRT;
+};
+
+// ---------------------------------------------------------------- linearization pass
+template <int BLK, int KIND>
+__device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const double* sC, const LinPoint& Q,
+                                             const double* dlnA, const DfTab& dt, double* __restrict__ lin,
+                                             int64_t ldl, int64_t i, bool live, double& S1) {
+    const Rxn x = load_rxn(m.rxn + r);
+    double cR[kMaxSide], pR[kMaxSide], cP[kMaxSide], pP[kMaxSide];
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        cR[e] = pR[e] = cP[e] = pP[e] = 1.0;
+        if (e < x.nr) {
+            const double c = sC[x.sp[e] * BLK];
+            double pw = c;
+            for (int j = 1; j < x.nu[e]; ++j) pw *= c;
+            cR[e] = c;
+            pR[e] = pw;
+        }
+        if (e < x.np) {
+            const double c = sC[x.sp[kMaxSide + e] * BLK];
+            double pw = c;
+            for (int j = 1; j < x.nu[kMaxSide + e]; ++j) pw *= c;
+            cP[e] = c;
+            pP[e] = pw;
+        }
+    }
+    double exR[kMaxSide], exP[kMaxSide];
+    const double fw = exclusive_products(pR, x.nr, exR);
+    const double rv = exclusive_products(pP, x.np, exP);
+
+    dfl dG, dH, dCp;
+    rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
+    const double sumh = df_to_d(dH), sumcp = df_to_d(dCp);
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, (float)x.dnu), df_neg(dG));
+    double shift = 0.0;
+    dfl shiftd{0.0f, 0.0f};
+    if (dlnA) {
+        shift = __ldg(dlnA + x.orig);
+        shiftd = df_split(shift);
+    }
+    const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
+    const double c1 = fma(x.EaR, Q.invT, x.beta);     // d ln k_inf / (dT/T)
+
+    double M = 0.0;
+    if (KIND != 0) {
+        M = Q.pRT;
+        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
+    }
+    double kf, kr, aT = c1, aM = 0.0;
+    if constexpr (KIND == 2) {
+        if (M == 0.0) {
+            kf = kr = aT = 0.0;
+        } else {
+            const TroeRec* t = m.troe + x.aux;
+            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
+            const double lnk0 = fma(-Ea0R, Q.invT, fma(beta0, Q.lnT, __ldg(&t->lnA0) + shift));
+            const double c0 = fma(Ea0R, Q.invT, beta0);
+            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
+            // tangents of the chain for (tT, d[M]) = (1, 0) and (0, 1)
+            const double dPrT = c0 - c1, dPrM = 1.0 / M;
+            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
+            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
+            double Fc = (1.0 - a) * e3 + a * e1;
+            double dFcT = -((1.0 - a) * i3 * e3 + a * i1 * e1) * Q.P.T;
+            if (__ldg(&t->hasT2) != 0.0) {
+                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
+                Fc += e2;
+                dFcT = fma(T2 * Q.invT, e2, dFcT);
+            }
+            const double lFc = dlog_df(Fc, dt) * kInvLn10, dlFcT = dFcT / Fc * kInvLn10;
+            const double c = fma(-0.67, lFc, -0.4), nn = fma(-1.27, lFc, 0.75);
+            const double u = fma(lnPr, kInvLn10, c);
+            const double duT = fma(dPrT, kInvLn10, -0.67 * dlFcT), duM = dPrM * kInvLn10;
+            const double v = fma(-0.14, u, nn);
+            const double dvT = fma(-0.14, duT, -1.27 * dlFcT), dvM = -0.14 * duM;
+            const double f1 = u / v;
+            const double df1T = fma(-f1, dvT, duT) / v, df1M = fma(-f1, dvM, duM) / v;
+            const double den = fma(f1, f1, 1.0);
+            const double lF = lFc / den;
+            const double dlFT = fma(-2.0 * lF * f1, df1T, dlFcT) / den, dlFM = -2.0 * lF * f1 * df1M / den;
+            const double g = 1.0 / (1.0 + dexp_df(-lnPr, dt));       // P_r / (1 + P_r)
+            kf = exp_df_d(lnkf, dt.e2) * g * dexp_df(lF * kLn10, dt);
+            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+            aT = c1 + dPrT * (1.0 - g) + kLn10 * dlFT;
+            aM = dPrM * (1.0 - g) + kLn10 * dlFM;
+        }
+    } else {
+        kf = exp_df_d(lnkf, dt.e2);
+        kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
+    }
+    const double qr = kr * rv;
+    const double qc = fma(kf, fw, -qr);
+    const double D = sumh - x.dnu;
+    const double sc = KIND == 1 ? M : 1.0;              // third body: q = q_c [M]
+    S1 = fma(qc * sc, sumcp, S1);
+    if (!live) return;
+    lin[(int64_t)r * ldl + i] = sc * fma(qc, aT, qr * D);
+    double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            double d = exR[e];                            // d fw / d C_e = nu C_e^(nu-1) prod_{f!=e}
+            if (x.nu[e] > 1) {
+                d *= -x.nud[e];
+                for (int j = 1; j < x.nu[e]; ++j) d *= cR[e];
+            }
+            B[(int64_t)e * ldl] = sc * kf * d;
+        }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.np) {
+            double d = exP[e];
+            if (x.nu[kMaxSide + e] > 1) {
+                d *= x.nud[kMaxSide + e];
+                for (int j = 1; j < x.nu[kMaxSide + e]; ++j) d *= cP[e];
+            }
+            B[(int64_t)(x.nr + e) * ldl] = -sc * kr * d;
+        }
+    if (KIND == 1) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = qc;
+    if (KIND == 2) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = qc * aM;
+}
+
+template <int BLK, int KIND>
+__device__ __forceinline__ void lin_group(const DevMech& m, int r0, int r1, const double* sC, const LinPoint& Q,
+                                          const double* dlnA, const DfTab& dt, double* lin, int64_t ldl, int64_t i,
+                                          bool live, double& S1) {
+    for (int r = r0; r < r1; ++r) lin_reaction<BLK, KIND>(m, r, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+}
+
+template <int BLK, int NP>
+__global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                             const double* __restrict__ T,
+                                                             const double* __restrict__ p,
+                                                             const double* __restrict__ Y,
+                                                             const double* __restrict__ dlnA,
+                                                             double* __restrict__ lin, const int64_t ldl) {
+    extern __shared__ double smem[];
+    const DfTab dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
+    __syncthreads();
+    const int K = m.K;
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;
+    double* sC = smem + kMathTabDoubles + slot;
+
+    LinPoint Q;
+    const double Ti = T[i];
+    Q.invT = 1.0 / Ti;
+    Q.pRT = p[i] * Q.invT * kInvR;
+    Q.P = make_tpairs(Ti, Q.invT, dt);
+    Q.lnT = df_to_d(Q.P.lnTd);
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
+    const double rho = Q.pRT / s;
+    for (int k = part; k < K; k += NP) {
+        sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
+        if (live) lin[(slot_H(m) + k) * ldl + i] = nasa_hRT(nasa_range(m, k, Ti), Ti, Q.invT);
+    }
+    if (NP > 1) __syncthreads();
+
+    double S1 = 0.0;
+    int a, b;
+    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+    slice<NP>(0, e1, part, a, b);
+    lin_group<BLK, 0>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+    slice<NP>(e1, t1, part, a, b);
+    lin_group<BLK, 1>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+    slice<NP>(t1, m.R, part, a, b);
+    lin_group<BLK, 2>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+    if constexpr (NP > 1) {
+        __syncthreads();
+        sC[part * BLK] = S1;                       // C_k is dead; rows 0..NP-1 (NP <= K)
+        __syncthreads();
+        if (part != 0) return;
+        S1 = sC[0];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) S1 += sC[q * BLK];
+    }
+    if (live) lin[slot_S(m) * ldl + i] = S1;
+}
+
+// ---------------------------------------------------------------- apply pass (one direction)
+template <int BLK, int KIND>
+__device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, const double* sdC, double* sD,
+                                            const double* __restrict__ lin, int64_t ldl, int64_t i, double tT,
+                                            double dpRT) {
+    for (int r = r0; r < r1; ++r) {
+        const Rxn x = load_rxn(m.rxn + r);
+        double dq = lin[(int64_t)r * ldl + i] * tT;
+        const double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.nr) dq = fma(B[(int64_t)e * ldl], sdC[x.sp[e] * BLK], dq);
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.np) dq = fma(B[(int64_t)(x.nr + e) * ldl], sdC[x.sp[kMaxSide + e] * BLK], dq);
+        if (KIND != 0) {
+            double dM = dpRT;
+            for (int j = x.eff0; j < x.eff1; ++j) dM = fma(__ldg(m.eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
+            dq = fma(lin[(slot_M(m) + (r - m.R_el)) * ldl + i], dM, dq);
+        }
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.nr) {
+                double* w = sD + x.sp[e] * BLK;
+                *w = fma(x.nud[e], dq, *w);
+            }
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.np) {
+                double* w = sD + x.sp[kMaxSide + e] * BLK;
+                *w = fma(x.nud[kMaxSide + e], dq, *w);
+            }
+    }
+}
+
+template <int BLK, int NP>
+__global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                           const double* __restrict__ T,
+                                                           const double* __restrict__ p,
+                                                           const double* __restrict__ Y,
+                                                           const double* __restrict__ lin, const int64_t ldl,
+                                                           const double* __restrict__ vT,
+                                                           const double* __restrict__ vY,
+                                                           double* __restrict__ d_omega, double* __restrict__ d_hrr) {
+    extern __shared__ double smem[];
+    const int K = m.K;
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;
+    double* sdC = smem + slot;                                   // dC_k
+    double* sD0 = smem + (size_t)K * BLK + slot;                 // d omega_k partials, part q at row q
+    double* sD = sD0 + (size_t)part * K * BLK;
+
+    const double Ti = T[i], dT = vT[i];
+    const double invT = 1.0 / Ti, tT = dT * invT;
+    const double pRT = p[i] * invT * kInvR;
+    double s = 0.0, ds = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double iw = __ldg(m.invW + k);
+        s += Y[(int64_t)k * ld + i] * iw;
+        ds = fma(vY[(int64_t)k * ld + i], iw, ds);
+    }
+    const double rho = pRT / s;
+    const double arho = -tT - ds / s;                            // d rho / rho
+    for (int k = part; k < K; k += NP) {
+        const double iw = __ldg(m.invW + k);
+        sdC[k * BLK] = fma(Y[(int64_t)k * ld + i] * iw * rho, arho, rho * vY[(int64_t)k * ld + i] * iw);
+    }
+    for (int k = 0; k < K; ++k) sD[k * BLK] = 0.0;
+    if (NP > 1) __syncthreads();
+
+    const double dpRT = -pRT * tT;
+    int a, b;
+    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+    slice<NP>(0, e1, part, a, b);
+    apply_group<BLK, 0>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    slice<NP>(e1, t1, part, a, b);
+    apply_group<BLK, 1>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    slice<NP>(t1, m.R, part, a, b);
+    apply_group<BLK, 2>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    if (NP > 1) __syncthreads();
+
+    double hsum = 0.0;
+    for (int k = part; k < K; k += NP) {
+        double dw = sD0[k * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
+        if (live) d_omega[(int64_t)k * ld + i] = dw;
+        hsum = fma(lin[(slot_H(m) + k) * ldl + i], dw, hsum);
+    }
+    if constexpr (NP > 1) {
+        sdC[part * BLK] = hsum;                    // dC_k is dead; rows 0..NP-1 (NP <= K)
+        __syncthreads();
+        if (part != 0) return;
+        hsum = sdC[0];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) hsum += sdC[q * BLK];
+    }
+    if (live) d_hrr[i] = -kR * fma(dT, lin[slot_S(m) * ldl + i], Ti * hsum);
+}
+
+// ---------------------------------------------------------------- launch shapes
+struct Shape {
+    int blk, np;
+};
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <bool APPLY, int S>
+constexpr auto kernel_of() {
+    if constexpr (APPLY)
+        return jvp_lin_kernel<kShapes[S].blk, kShapes[S].np>;
+    else
+        return linearize_kernel<kShapes[S].blk, kShapes[S].np>;
+}
+
+template <bool APPLY, int... S>
+const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
+    const void* ptrs[] = {(const void*)kernel_of<APPLY, S>()...};
+    return ptrs[idx];
+}
+
+// linearization: the pair tables and C_k; apply: dC_k and NP rows of d omega_k partials
+size_t lin_smem(int K, const Shape& sh, bool apply) {
+    return apply ? (size_t)(1 + sh.np) * K * sh.blk * sizeof(double)
+                 : (size_t)kMathTabDoubles * sizeof(double) + (size_t)K * sh.blk * sizeof(double);
+}
+
+struct Plan {
+    int dev, K;
+    bool apply;
+    int idx;
+};
+std::mutex g_plan_mu;
+std::vector<Plan> g_plans;
+
+template <bool APPLY>
+int plan_shape(int K) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const Plan& q : g_plans)
+            if (q.dev == dev && q.K == K && q.apply == APPLY) return q.idx;
+    }
+    int per_block = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < kNumShapes; ++c) {
+        const Shape& sh = kShapes[c];
+        if (sh.np > K) continue;
+        const size_t bytes = lin_smem(K, sh, APPLY);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<APPLY>(c, std::make_integer_sequence<int, kNumShapes>{});
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
+            continue;
+        const int warps = blocks * sh.blk * sh.np / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best = c;
+        }
+    }
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back({dev, K, APPLY, best});
+    }
+    return best;
+}
+
+template <bool APPLY, class... Args, int... S>
+cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, int K, int64_t n, cudaStream_t st,
+                       Args... args) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    ((S == idx ? (void)(e = [&] {
+        constexpr Shape sh = kShapes[S];
+        auto kern = kernel_of<APPLY, S>();
+        const size_t smem = lin_smem(K, sh, APPLY);
+        cudaError_t r = ensure_smem((const void*)kern, smem);
+        if (r != cudaSuccess) return r;
+        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(args...);
+        return cudaGetLastError();
+    }())
+               : (void)0),
+     ...);
+    return e;
+}
+
+}  // namespace
+
+int64_t lin_slots(const DevMech& m) { return slot_H(m) + m.K; }
+
+cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                             const double* Y, const double* dlnA, double* lin, int64_t ldl, cudaStream_t s) {
+    static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
+    const int idx = plan_shape<false>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<false>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y,
+                             dlnA, lin, ldl);
+}
+
+cudaError_t launch_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                  const double* Y, const double* lin, int64_t ldl, const double* vT,
+                                  const double* vY, double* d_omega, double* d_hrr, cudaStream_t s) {
+    const int idx = plan_shape<true>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<true>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin,
+                            ldl, vT, vY, d_omega, d_hrr);
+}
+
+}  // namespace nk

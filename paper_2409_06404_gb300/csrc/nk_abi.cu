@@ -330,6 +330,13 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
         }
     }
 
+    // entry slots of a stored linearization (k_lin.cu): reactants then products, device order
+    std::vector<int32_t> lin_boff(R);
+    int32_t lin_nb = 0;
+    for (int q = 0; q < R; ++q) {
+        lin_boff[q] = lin_nb;
+        lin_nb += rxn[q].nr + rxn[q].np;
+    }
     // reaction thermo groups (nk_internal.cuh): net coefficients of each reaction, grouped by
     // the species' T_mid, combined in extended precision
     std::vector<float2> grp_df;
@@ -387,7 +394,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_dexp = L.add(df_exp.size() * 8), o_drc = L.add(df_rc.size() * 8), o_dlc = L.add(df_lc.size() * 8),
                  o_ndf = L.add(nasa_df.size() * 8), o_rdf = L.add(rxn_df.size() * 16),
                  o_tdf = L.add(troe_df.size() * 16 + 16), o_gdf = L.add(grp_df.size() * 8 + 16),
-                 o_gT = L.add(grp_Tmid.size() * 8 + 16);
+                 o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -430,6 +437,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_tdf, troe_df.data(), troe_df.size() * 16);
     put(o_gdf, grp_df.data(), grp_df.size() * 8);
     put(o_gT, grp_Tmid.data(), grp_Tmid.size() * 8);
+    put(o_lb, lin_boff.data(), (size_t)R * 4);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -497,6 +505,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.troe_df = reinterpret_cast<const float4*>(b + o_tdf);
     dm.grp_df = reinterpret_cast<const float2*>(b + o_gdf);
     dm.grp_Tmid = reinterpret_cast<const double*>(b + o_gT);
+    dm.lin_boff = reinterpret_cast<const int32_t*>(b + o_lb);
+    dm.lin_nb = lin_nb;
     *out = m;
     return ok();
 }
@@ -638,6 +648,39 @@ nk_status nk_rhs_jvp(const nk_mech* m, int64_t n, int64_t ld, const double* T, c
     if ((st = check_out({vT, vY, dfT, dfY, fT, fY, dlnA})) != NK_OK) return st;
     return launched(nk::launch_jvp(m->d, n, ld, T, p, Y, dlnA, vT, vY, fY, fT, dfY, dfT, (cudaStream_t)stream, 1),
                     "jvp kernel launch");
+}
+
+nk_status nk_rates_linearization_slots(const nk_mech* m, int64_t* slots) {
+    if (!m || !slots) return fail(NK_EINVAL, "mech and slots must not be NULL");
+    *slots = nk::lin_slots(m->d);
+    return ok();
+}
+
+nk_status nk_rates_linearize(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                             const double* Y, const double* dlnA, double* lin, int64_t ldl, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin) return fail(NK_EINVAL, "lin must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, dlnA})) != NK_OK) return st;
+    return launched(nk::launch_linearize(m->d, n, ld, T, p, Y, dlnA, lin, ldl, (cudaStream_t)stream),
+                    "linearize kernel launch");
+}
+
+nk_status nk_rates_jvp_linearized(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                  const double* Y, const double* lin, int64_t ldl, const double* vT,
+                                  const double* vY, double* d_omega, double* d_hrr, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !vT || !vY || !d_omega || !d_hrr)
+        return fail(NK_EINVAL, "lin, vT, vY, d_omega and d_hrr must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, vT, vY, d_omega, d_hrr})) != NK_OK) return st;
+    return launched(nk::launch_jvp_linearized(m->d, n, ld, T, p, Y, lin, ldl, vT, vY, d_omega, d_hrr,
+                                              (cudaStream_t)stream),
+                    "linearized jvp kernel launch");
 }
 
 nk_status nk_rates_vjp_workspace(const nk_mech* m, int64_t n, size_t* bytes) {

@@ -129,6 +129,8 @@ struct DevMech {
     const float4* troe_df;        // [n_troe][3] (lnA0, beta0), (Ea0/R, 1/T3), (1/T1, T2) as pairs
     const float2* grp_df;         // [groups][2][kGrpPairs] reaction thermo groups (below), pairs
     const double* grp_Tmid;       // [groups] the group's T_mid
+    const int32_t* lin_boff;      // [R] first entry slot of each reaction in a stored linearization
+    int32_t lin_nb;               // entry slots of all reactions (sum of nr + np)
 };
 
 // Centre of the re-expanded transport fits (ln T about 1100 K).
@@ -168,6 +170,13 @@ cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s,
                        int rhs = 0);
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n);
+// Stored linearization of the rates (k_lin.cu): per-point slots, see lin_slots().
+int64_t lin_slots(const DevMech& m);
+cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                             const double* Y, const double* dlnA, double* lin, int64_t ldl, cudaStream_t s);
+cudaError_t launch_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                  const double* Y, const double* lin, int64_t ldl, const double* vT,
+                                  const double* vY, double* d_omega, double* d_hrr, cudaStream_t s);
 cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* bar_omega,
                        const double* bar_hrr, double* gT, double* gY, double* g_lnA,
