@@ -255,24 +255,53 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
 }
 
 // ---------------------------------------------------------------- apply pass (one direction)
+// The stored coefficients of a reaction (A, its entries' B, L): read for the next reaction
+// while the current one is contracted, so each warp keeps two reactions' HBM loads in flight.
+struct LinCoef {
+    double A, L;
+    double Br[kMaxSide], Bp[kMaxSide];   // reactant and product entries
+};
+
+template <int KIND>
+__device__ __forceinline__ LinCoef load_coef(const DevMech& m, int r, const double* __restrict__ lin, int64_t ldl,
+                                             int64_t i, int nr, int np) {
+    LinCoef c;
+    c.A = lin[(int64_t)r * ldl + i];
+    const double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        c.Br[e] = e < nr ? B[(int64_t)e * ldl] : 0.0;
+        c.Bp[e] = e < np ? B[(int64_t)(nr + e) * ldl] : 0.0;
+    }
+    c.L = KIND != 0 ? lin[(slot_M(m) + (r - m.R_el)) * ldl + i] : 0.0;
+    return c;
+}
+
 template <int BLK, int KIND>
 __device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, const double* sdC, double* sD,
                                             const double* __restrict__ lin, int64_t ldl, int64_t i, double tT,
                                             double dpRT) {
+    if (r0 >= r1) return;
+    Rxn x = load_rxn(m.rxn + r0);
+    LinCoef c = load_coef<KIND>(m, r0, lin, ldl, i, x.nr, x.np);
     for (int r = r0; r < r1; ++r) {
-        const Rxn x = load_rxn(m.rxn + r);
-        double dq = lin[(int64_t)r * ldl + i] * tT;
-        const double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+        Rxn xn;
+        LinCoef cn;
+        if (r + 1 < r1) {
+            xn = load_rxn(m.rxn + r + 1);
+            cn = load_coef<KIND>(m, r + 1, lin, ldl, i, xn.nr, xn.np);
+        }
+        double dq = c.A * tT;
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.nr) dq = fma(B[(int64_t)e * ldl], sdC[x.sp[e] * BLK], dq);
+            if (e < x.nr) dq = fma(c.Br[e], sdC[x.sp[e] * BLK], dq);
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.np) dq = fma(B[(int64_t)(x.nr + e) * ldl], sdC[x.sp[kMaxSide + e] * BLK], dq);
+            if (e < x.np) dq = fma(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
         if (KIND != 0) {
             double dM = dpRT;
             for (int j = x.eff0; j < x.eff1; ++j) dM = fma(__ldg(m.eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
-            dq = fma(lin[(slot_M(m) + (r - m.R_el)) * ldl + i], dM, dq);
+            dq = fma(c.L, dM, dq);
         }
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
@@ -286,6 +315,10 @@ __device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, co
                 double* w = sD + x.sp[kMaxSide + e] * BLK;
                 *w = fma(x.nud[kMaxSide + e], dq, *w);
             }
+        if (r + 1 < r1) {
+            x = xn;
+            c = cn;
+        }
     }
 }
 
