@@ -110,9 +110,10 @@ def _configure(lib):
     lib.or_count_ops.argtypes = [M, _c_dbl, _c_dbl, P, ci, P]
     lib.or_rhs.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
     lib.or_rhs_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, ci]
+    lib.or_diffusion.argtypes = [M, I, I, P, P, P, P, P, P, P, P, ci]
     for f in ("or_thermo", "or_nasa7_cs", "or_rates", "or_rates_of_progress", "or_transport",
               "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops", "or_rhs",
-              "or_rhs_jvp"):
+              "or_rhs_jvp", "or_diffusion"):
         getattr(lib, f).restype = None
     return lib
 
@@ -308,6 +309,23 @@ def rhs_jvp(mech, T, p, Y, vT, vY, threads: int = 0, scales: bool = False):
     _lib_handle().or_rhs_jvp(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(vT), _dp(vY), _dp(dfT), _dp(dfY),
                              _dp(sT), _dp(sY), threads)
     return (dfT, dfY, sT, sY) if scales else (dfT, dfY)
+
+
+def diffusion(mech, T, p, Y, D, gradX, threads: int = 0):
+    """Mixture-averaged diffusion fluxes of Eq. 2 from D [K, n] and grad X [3, K, n]:
+    (j [3, K, n] = rho Y_k V_k, Vc [3, n], hf [3, n] = sum_k c_p,k j_k)."""
+    pk = _Packed(mech)
+    T, p, Y, n = _state(T, p, Y, pk.K)
+    D = _f64(D)
+    gradX = _f64(gradX)
+    if D.shape != (pk.K, n) or gradX.shape != (3, pk.K, n):
+        raise ValueError("D must be [K, n] and gradX [3, K, n]")
+    j = np.empty((3, pk.K, n))
+    Vc = np.empty((3, n))
+    hf = np.empty((3, n))
+    _lib_handle().or_diffusion(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(D), _dp(gradX), _dp(j), _dp(Vc),
+                               _dp(hf), threads)
+    return j, Vc, hf
 
 
 def count_ops(mech, T: float, p: float, Y, which: str = "rates") -> dict:

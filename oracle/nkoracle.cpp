@@ -33,6 +33,8 @@
  *  11. implicit-stage chemistry sources of Eq. 1a-b at fixed p: dY_k/dt = W_k omega_k / rho,
  *      dT/dt = hrr / (rho c_p), c_p the mass-based mixture heat capacity; their directional
  *      derivatives by complex step as in 10.
+ *  12. mixture-averaged diffusion fluxes of Eq. 2: V_k = -(D_k/X_k) grad X_k + V_c with
+ *      V_c = -sum_k Y_k V'_k; j_k = rho Y_k V_k and sum_k c_p,k j_k.
  *
  * Everything is templated on the scalar type S: double, std::complex<double> (complex-step
  * derivatives) and Cnt (counts the floating-point operations the definition performs).
@@ -407,6 +409,41 @@ int nthreads_of(int requested) {
 #endif
 }
 
+/* ---------------------------------------------------------------- step 12: diffusion fluxes
+ * Eq. 2 with the correction velocity defined below it: V_k = -(D_k/X_k) grad X_k + V_c and
+ * V_c = -sum_k Y_k V'_k over the uncorrected velocities V'_k = -(D_k/X_k) grad X_k.  Outputs
+ * per Cartesian component c: the species mass fluxes j_k = rho Y_k V_k, the correction velocity
+ * V_c and sum_k c_p,k j_k (c_p,k mass based; the factor of the enthalpy-flux term of Eq. 1b).
+ * Y_k/X_k is evaluated as written; at X_k = 0 its limit W_k/Wbar is used.
+ * D, gradX: [K] and [3][K]; j: [3][K]; Vc, hf: [3]. */
+void diffusion_point(const or_mech& m, double T, double p, const double* Y, const double* D, const double* gradX,
+                     double* j, double* Vc, double* hf) {
+    const int K = m.K;
+    Mixture<double> mx;
+    mixture(m, T, p, Y, mx);
+    std::vector<double> cpk(K), yv(K);
+    for (int k = 0; k < K; ++k) {
+        double cpR, hRT, sR;
+        nasa7(m, k, T, cpR, hRT, sR);
+        cpk[k] = RU * cpR / m.W[k];
+    }
+    for (int c = 0; c < 3; ++c) {
+        double sum = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double y_over_x = mx.X[k] != 0.0 ? Y[k] / mx.X[k] : m.W[k] / mx.Wbar;
+            yv[k] = -y_over_x * D[k] * gradX[c * K + k];   /* Y_k V'_k */
+            sum += yv[k];
+        }
+        Vc[c] = -sum;
+        double h = 0.0;
+        for (int k = 0; k < K; ++k) {
+            j[c * K + k] = mx.rho * (yv[k] + Y[k] * Vc[c]);
+            h += cpk[k] * j[c * K + k];
+        }
+        hf[c] = h;
+    }
+}
+
 }  // namespace
 
 /* ====================================================================== C entry points */
@@ -673,6 +710,29 @@ void or_rhs_jvp(const or_mech* m, int64_t n, int64_t ld, const double* T, const 
         if (dfY_scale)
             for (int k = 0; k < K; ++k) dfY_scale[k * ld + i] = dsc[k] / hstep;
         if (dfT_scale) dfT_scale[i] = dst / hstep;
+    }
+}
+
+/* Diffusion fluxes (diffusion_point) at n points: D [K][ld], gradX [3][K][ld] in; j [3][K][ld],
+ * Vc [3][ld], hf [3][ld] out. */
+void or_diffusion(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                  const double* D, const double* gradX, double* j, double* Vc, double* hf, int nthreads) {
+    const int K = m->K;
+#pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<double> y(K), d(K), g(3 * K), jj(3 * K);
+        double vc[3], h[3];
+        for (int k = 0; k < K; ++k) {
+            y[k] = Y[k * ld + i];
+            d[k] = D[k * ld + i];
+        }
+        for (int q = 0; q < 3 * K; ++q) g[q] = gradX[q * ld + i];
+        diffusion_point(*m, T[i], p[i], y.data(), d.data(), g.data(), jj.data(), vc, h);
+        for (int q = 0; q < 3 * K; ++q) j[q * ld + i] = jj[q];
+        for (int c = 0; c < 3; ++c) {
+            Vc[c * ld + i] = vc[c];
+            hf[c * ld + i] = h[c];
+        }
     }
 }
 

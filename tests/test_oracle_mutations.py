@@ -14,6 +14,7 @@ import test_oracle_rates as rt
 import test_oracle_transport as tr
 import test_oracle_derivs as dv
 import test_oracle_rhs as rh
+import test_oracle_diffusion as df
 
 SRC = open(os.path.join(os.path.dirname(oracle.__file__), "nkoracle.cpp")).read()
 
@@ -43,6 +44,10 @@ MUTATIONS = {
     "rhs_missing_W": ("fY[k] = S(m.W[k]) * w[k] / mx.rho;", "fY[k] = w[k] / mx.rho;"),
     "rhs_cp_molar": ("cp += Y[k] * S(RU) * cpR / S(m.W[k]);", "cp += Y[k] * S(RU) * cpR;"),
     "rhs_T_sign": ("fT = hrr / (mx.rho * cp);", "fT = -hrr / (mx.rho * cp);"),
+    "diffusion_correction_sign": ("        Vc[c] = -sum;\n", "        Vc[c] = sum;\n"),
+    "diffusion_mole_mass_ratio": ("yv[k] = -y_over_x * D[k] * gradX[c * K + k];", "yv[k] = -D[k] * gradX[c * K + k];"),
+    "diffusion_flux_without_rho": ("j[c * K + k] = mx.rho * (yv[k] + Y[k] * Vc[c]);",
+                                   "j[c * K + k] = (yv[k] + Y[k] * Vc[c]);"),
 }
 
 
@@ -78,6 +83,9 @@ def _pins():
         lambda: rh.test_enthalpy_conservation_at_constant_pressure("h2_9sp_21rx"),
         rh.test_pressure_scaling,
         rh.test_exothermic_reaction_heats,
+        lambda: df.test_fluxes_sum_to_zero("h2_9sp_21rx"),
+        df.test_binary_reduces_to_fick_in_mass_fractions,
+        df.test_trace_species_and_uniform_composition,
     ]
 
 
