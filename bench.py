@@ -14,8 +14,9 @@ Mpoints/s of rates + transport in FP64 (points / (t_rates + t_transport) summed 
 timed steps); the mixed form, JVP/forward and VJP/forward ratios come from the same steps.
 After the timed steps, the all-double forms of rates and transport (NK_FP64_NATIVE, the
 plain-FP64 arithmetic the FP64 form is checked against), the implicit-stage sources and their
-JVP (nk_rhs_eval, nk_rhs_jvp) and the stored linearization with one JVP from it
-(nk_rates_linearize, nk_rates_jvp_linearized) are timed the same way in a separate loop
+JVP (nk_rhs_eval, nk_rhs_jvp), the diffusion fluxes (nk_diffusion_fluxes) and the stored
+linearization with one JVP from it (nk_rates_linearize, nk_rates_jvp_linearized) are timed
+the same way in a separate loop
 ("fp64_native_value", rows); they are not part of a step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -100,7 +101,8 @@ def algorithmic_flops(mech) -> dict:
         + K * (6 + 4) + K * 2 + 4
     return {"thermo": thermo, "rates_fp64": rates, "transport_fp64": transport, "rates_fp64_native": rates,
             "transport_fp64_native": transport, "rates_mixed": rates, "transport_mixed": transport, "jvp": jvp,
-            "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp, "linearize": jvp, "jvp_linearized": jvp_lin}
+            "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp, "linearize": jvp, "jvp_linearized": jvp_lin,
+            "diffusion": K * (3 + 6 + 6 + 9 + 10) + 12}
 
 
 # ---------------------------------------------------------------------------------- clocks
@@ -364,6 +366,10 @@ def run_ours(args):
     out.update({k: torch.empty((K, n), **f64) for k in ("w", "D", "w_m", "D_m", "dw", "gY")})
     g_lnA = torch.empty(R, **f64)
     lin = torch.empty((nk.linearization_slots(m), n), **f64)    # stored linearization (~15 KB per point)
+    gradX = torch.randn((3, K, n), generator=gen, **f64)         # mole-fraction gradients (synthetic)
+    jflux = torch.empty((3, K, n), **f64)
+    Vc = torch.empty((3, n), **f64)
+    hflux = torch.empty((3, n), **f64)
     wsb = torch.empty(max(nk.rates_vjp_workspace(m, n), 8), dtype=torch.uint8, device=dev)
     L = nk.lib()
     s = torch.cuda.current_stream()
@@ -398,6 +404,8 @@ def run_ours(args):
         "rhs_fp64": lambda: chk(L.nk_rhs_eval(h, n, n, P(T), P(p), P(Y), None, P(out["hrr"]), P(out["w"]), 0, sp)),
         "rhs_jvp": lambda: chk(L.nk_rhs_jvp(h, n, n, P(T), P(p), P(Y), None, P(vT), P(vY), None, None,
                                             P(out["dh"]), P(out["dw"]), sp)),
+        "diffusion": lambda: chk(L.nk_diffusion_fluxes(h, n, n, P(T), P(p), P(Y), P(out["D"]), P(gradX), P(jflux),
+                                                        P(Vc), P(hflux), sp)),
         "linearize": lambda: chk(L.nk_rates_linearize(h, n, n, P(T), P(p), P(Y), None, P(lin), n, sp)),
         "jvp_linearized": lambda: chk(L.nk_rates_jvp_linearized(h, n, n, P(T), P(p), P(Y), P(lin), n, P(vT), P(vY),
                                                                 P(out["dw"]), P(out["dh"]), sp)),

@@ -174,6 +174,22 @@ nk_status nk_transport_eval(const nk_mech* mech, int64_t n, int64_t ld, const do
                             double* Dmix, nk_precision precision, nk_stream stream);
 
 /*
+ * Mixture-averaged diffusion fluxes (Eq. 2 with its correction velocity, Sec. 2), the
+ * species and enthalpy fluxes whose divergences enter Eq. 1a-b:
+ *   Dmix[K*ld]      mixture-averaged coefficients D_k (from nk_transport_eval), m^2/s
+ *   gradX[3*K*ld]   mole-fraction gradients: component c of species k at (c*K + k)*ld + i, 1/m
+ *   j[3*K*ld]       species mass fluxes rho Y_k V_k, kg/(m^2 s), same layout, with
+ *                   V_k = -(D_k/X_k) grad X_k + V_c and V_c = -sum_k Y_k V'_k (V'_k uncorrected)
+ *   Vc[3*ld]        correction velocity V_c, m/s (NULL: not written)
+ *   hf[3*ld]        sum_k c_p,k j_k with mass-based c_p,k, W/(m^2 K) (NULL: not written)
+ * Y_k/X_k is taken as W_k/Wbar, so absent species (X_k = 0) have finite fluxes.  Double
+ * precision; the gradients come from the caller's discretisation (not part of this library).
+ */
+nk_status nk_diffusion_fluxes(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                              const double* Y, const double* Dmix, const double* gradX, double* j, double* Vc,
+                              double* hf, nk_stream stream);
+
+/*
  * Exact Jacobian-vector product of (omega_k, hrr) with respect to (T, Y_k) at fixed p: the
  * product the Newton-GMRES stage of the paper forms by difference quotients (Sec. 2 and 4).
  *   vT[n], vY[K*ld]        direction

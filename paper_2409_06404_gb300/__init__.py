@@ -66,6 +66,7 @@ _SIGS = {
     "nk_rates_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_transport_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
+    "nk_diffusion_fluxes": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 8 + [_vp]),
     "nk_rhs_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rhs_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_rates_linearization_slots": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
@@ -287,6 +288,24 @@ def rates_jvp(m: Mechanism, T, p, Y, vT, vY, dlnA=None, primal=False, stream=Non
     if primal:
         return d_omega, d_hrr, omega, hrr
     return d_omega, d_hrr
+
+
+def diffusion_fluxes(m: Mechanism, T, p, Y, Dmix, gradX, want_vc=True, want_hf=True, stream=None):
+    """nk_diffusion_fluxes: (j [3, K, n], Vc [3, n] or None, hf [3, n] or None) from the
+    mixture-averaged D_k [K, n] and mole-fraction gradients [3, K, n]."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    for name, a, shape in (("Dmix", Dmix, (m.K, n)), ("gradX", gradX, (3, m.K, n))):
+        if tuple(a.shape) != shape or not a.is_contiguous() or a.dtype != torch.float64 or a.device != T.device:
+            raise ValueError(f"{name} must be a contiguous float64 {shape} tensor on the state's device")
+    if ld != n:
+        raise ValueError("diffusion_fluxes takes contiguous states (ld = n)")
+    j = torch.empty((3, m.K, n), dtype=torch.float64, device=T.device)
+    Vc = torch.empty((3, n), dtype=torch.float64, device=T.device) if want_vc else None
+    hf = torch.empty((3, n), dtype=torch.float64, device=T.device) if want_hf else None
+    _check(lib().nk_diffusion_fluxes(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Dmix), _ptr(gradX), _ptr(j),
+                                     _ptr(Vc), _ptr(hf), _stream(stream)))
+    return j, Vc, hf
 
 
 def rhs_eval(m: Mechanism, T, p, Y, dlnA=None, precision="fp64", fT=None, fY=None, stream=None):

@@ -612,6 +612,18 @@ nk_status nk_transport_eval(const nk_mech* m, int64_t n, int64_t ld, const doubl
                     "transport kernel launch");
 }
 
+nk_status nk_diffusion_fluxes(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                              const double* Y, const double* Dmix, const double* gradX, double* j, double* Vc,
+                              double* hf, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!Dmix || !gradX || !j) return fail(NK_EINVAL, "Dmix, gradX and j must not be NULL");
+    if ((st = check_out({Dmix, gradX, j, Vc, hf})) != NK_OK) return st;
+    return launched(nk::launch_diffusion(m->d, n, ld, T, p, Y, Dmix, gradX, j, Vc, hf, (cudaStream_t)stream),
+                    "diffusion kernel launch");
+}
+
 nk_status nk_rates_jvp(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* vT, const double* vY,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, nk_stream stream) {

@@ -170,6 +170,9 @@ cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s,
                        int rhs = 0);
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n);
+cudaError_t launch_diffusion(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                             const double* Y, const double* D, const double* gradX, double* j, double* Vc,
+                             double* hf, cudaStream_t s);
 // Stored linearization of the rates (k_lin.cu): per-point slots, see lin_slots().
 int64_t lin_slots(const DevMech& m);
 cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
