@@ -248,6 +248,47 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
                                   nk_stream stream);
 
 /*
+ * One implicit (backward) Euler step of dt seconds of the homogeneous constant-pressure
+ * reactor at every point: solves x1 - x0 - dt f(x1) = 0, x = (T, Y_k), f the sources of
+ * nk_rhs_eval, the nonlinear system of the paper's implicit thermochemistry stage (Sec. 2),
+ * here without the transport terms.  Newton's method with one GMRES solve over all points per
+ * iteration, as the paper's stage: exact Jacobian-vector products (nk_rhs_jvp) instead of
+ * difference quotients, the Krylov basis in single precision, classical Gram-Schmidt with the
+ * projections in one reduction and the new vector's norm in a second.  Norms are weighted RMS
+ * norms with weights 1/(rtol |x0_i| + atol_i).
+ *   T[n], Y[K*n]   in: the state x0; out: the step's result (contiguous: Y rows of stride n)
+ *   workspace      device, nk_reactor_workspace bytes (holds (K+1) n doubles x 7 and
+ *                  (krylov_dim + 1) (K+1) n floats)
+ * The call returns when the step is done (it reads a few scalars back per GMRES iteration);
+ * non-convergence is reported in stats, not as an error.
+ */
+#define NK_REACTOR_MAX_KRYLOV 30
+typedef struct {
+    double rtol;          /* relative tolerance of the error weights */
+    double atol_T;        /* absolute tolerance for T, K */
+    double atol_Y;        /* absolute tolerance for the mass fractions */
+    double newton_tol;    /* converged when (weighted RMS norm of the Newton update) x
+                             min(1, its contraction rate) is below this, the update test of a
+                             stiff ODE solver */
+    double lin_tol;       /* each GMRES solve stops when its residual has fallen by this factor
+                             (or after krylov_dim iterations; the partial solution is used) */
+    int32_t max_newton;   /* Newton iterations at most */
+    int32_t krylov_dim;   /* GMRES iterations per Newton iteration, 1..NK_REACTOR_MAX_KRYLOV */
+} nk_reactor_opts;
+typedef struct {
+    int32_t converged;    /* 1 when the update test was met (0: max_newton reached, or the
+                             updates grew: diverging) */
+    int32_t newton_iters;
+    int32_t krylov_iters; /* summed over the Newton iterations */
+    double update_wrms;   /* weighted RMS norm of the last Newton update */
+    double residual_wrms; /* weighted RMS norm of the residual before the last update */
+} nk_reactor_stats;
+nk_status nk_reactor_workspace(const nk_mech* mech, int64_t n, int32_t krylov_dim, size_t* bytes);
+nk_status nk_reactor_step(const nk_mech* mech, int64_t n, double* T, const double* p, double* Y, double dt,
+                          const nk_reactor_opts* opts, nk_reactor_stats* stats, void* workspace,
+                          size_t workspace_bytes, nk_stream stream);
+
+/*
  * Bytes of device workspace nk_rates_vjp needs for n points when g_lnA is requested
  * (per-block partial sums of the ln A gradient, reduced in a fixed order).
  */

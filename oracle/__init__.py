@@ -111,9 +111,10 @@ def _configure(lib):
     lib.or_rhs.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
     lib.or_rhs_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, ci]
     lib.or_diffusion.argtypes = [M, I, I, P, P, P, P, P, P, P, P, ci]
+    lib.or_reactor_step.argtypes = [M, I, I, P, P, P, _c_dbl, _c_dbl, _c_dbl, P, P, ctypes.POINTER(ctypes.c_int), ci]
     for f in ("or_thermo", "or_nasa7_cs", "or_rates", "or_rates_of_progress", "or_transport",
               "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops", "or_rhs",
-              "or_rhs_jvp", "or_diffusion"):
+              "or_rhs_jvp", "or_diffusion", "or_reactor_step"):
         getattr(lib, f).restype = None
     return lib
 
@@ -326,6 +327,20 @@ def diffusion(mech, T, p, Y, D, gradX, threads: int = 0):
     _lib_handle().or_diffusion(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(D), _dp(gradX), _dp(j), _dp(Vc),
                                _dp(hf), threads)
     return j, Vc, hf
+
+
+def reactor_step(mech, T, p, Y, dt: float, atol_T: float = 1e-8, atol_Y: float = 1e-16, threads: int = 0):
+    """One implicit Euler step of dt (s) of the homogeneous constant-pressure reactor at every
+    point, by dense Newton: (T1 [n], Y1 [K, n], Newton iterations [n], negative if not
+    converged)."""
+    pk = _Packed(mech)
+    T, p, Y, n = _state(T, p, Y, pk.K)
+    T1 = np.empty(n)
+    Y1 = np.empty((pk.K, n))
+    it = np.empty(n, dtype=np.intc)
+    _lib_handle().or_reactor_step(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), float(dt), float(atol_T), float(atol_Y),
+                                  _dp(T1), _dp(Y1), it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), threads)
+    return T1, Y1, it
 
 
 def count_ops(mech, T: float, p: float, Y, which: str = "rates") -> dict:

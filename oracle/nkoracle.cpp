@@ -35,6 +35,8 @@
  *      derivatives by complex step as in 10.
  *  12. mixture-averaged diffusion fluxes of Eq. 2: V_k = -(D_k/X_k) grad X_k + V_c with
  *      V_c = -sum_k Y_k V'_k; j_k = rho Y_k V_k and sum_k c_p,k j_k.
+ *  13. one implicit Euler step of the homogeneous constant-pressure reactor, x1 - x0 - dt f(x1)
+ *      = 0 with the sources of 11, by dense Newton per point.
  *
  * Everything is templated on the scalar type S: double, std::complex<double> (complex-step
  * derivatives) and Cnt (counts the floating-point operations the definition performs).
@@ -444,6 +446,71 @@ void diffusion_point(const or_mech& m, double T, double p, const double* Y, cons
     }
 }
 
+/* ---------------------------------------------------------------- step 13: implicit reactor step
+ * One implicit (backward) Euler step of a homogeneous constant-pressure reactor, the
+ * nonlinear system the paper's implicit thermochemistry stage solves at every point (Sec. 2,
+ * there by Newton-GMRES over the whole mesh): x1 - x0 - dt f(x1) = 0 with x = (T, Y_k) and f
+ * the sources of step 11.  Solved per point by Newton's method on the dense system with the
+ * complex-step Jacobian of f and Gaussian elimination with partial pivoting, until the update
+ * is below 1e-14 of (|x| + atol) in every component.  Returns the iterations used (negative:
+ * not converged in 100). */
+int reactor_point(const or_mech& m, double T0, double p, const double* Y0, double dt, double atolT,
+                  double atolY, double* x1) {
+    const int K = m.K, N = K + 1;
+    const double hstep = 1e-100;
+    std::vector<double> x0(N), x(N), G(N), A((size_t)N * N), d(N);
+    x0[0] = T0;
+    for (int k = 0; k < K; ++k) x0[k + 1] = Y0[k];
+    x = x0;
+    std::vector<cplx> yc(K), fY(K);
+    for (int it = 1; it <= 100; ++it) {
+        // f(x) and its Jacobian, one complex-step evaluation per input
+        for (int j = 0; j < N; ++j) {
+            for (int k = 0; k < K; ++k) yc[k] = cplx(x[k + 1], j == k + 1 ? hstep : 0.0);
+            cplx fT;
+            rhs_point<cplx>(m, cplx(x[0], j == 0 ? hstep : 0.0), p, yc.data(), fY.data(), fT, nullptr, nullptr);
+            if (j == 0) {
+                G[0] = x[0] - x0[0] - dt * fT.real();
+                for (int k = 0; k < K; ++k) G[k + 1] = x[k + 1] - x0[k + 1] - dt * fY[k].real();
+            }
+            A[(size_t)0 * N + j] = (j == 0 ? 1.0 : 0.0) - dt * fT.imag() / hstep;
+            for (int k = 0; k < K; ++k) A[(size_t)(k + 1) * N + j] = (j == k + 1 ? 1.0 : 0.0) - dt * fY[k].imag() / hstep;
+        }
+        // solve A d = -G
+        for (int i = 0; i < N; ++i) d[i] = -G[i];
+        for (int c = 0; c < N; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < N; ++r)
+                if (std::fabs(A[(size_t)r * N + c]) > std::fabs(A[(size_t)piv * N + c])) piv = r;
+            if (piv != c) {
+                for (int q = 0; q < N; ++q) std::swap(A[(size_t)c * N + q], A[(size_t)piv * N + q]);
+                std::swap(d[c], d[piv]);
+            }
+            for (int r = c + 1; r < N; ++r) {
+                const double f = A[(size_t)r * N + c] / A[(size_t)c * N + c];
+                for (int q = c; q < N; ++q) A[(size_t)r * N + q] -= f * A[(size_t)c * N + q];
+                d[r] -= f * d[c];
+            }
+        }
+        for (int c = N - 1; c >= 0; --c) {
+            double acc = d[c];
+            for (int q = c + 1; q < N; ++q) acc -= A[(size_t)c * N + q] * d[q];
+            d[c] = acc / A[(size_t)c * N + c];
+        }
+        double worst = 0.0;
+        for (int i = 0; i < N; ++i) {
+            x[i] += d[i];
+            worst = std::fmax(worst, std::fabs(d[i]) / (std::fabs(x[i]) + (i == 0 ? atolT : atolY)));
+        }
+        if (worst <= 1e-14) {
+            for (int i = 0; i < N; ++i) x1[i] = x[i];
+            return it;
+        }
+    }
+    for (int i = 0; i < N; ++i) x1[i] = x[i];
+    return -100;
+}
+
 }  // namespace
 
 /* ====================================================================== C entry points */
@@ -733,6 +800,21 @@ void or_diffusion(const or_mech* m, int64_t n, int64_t ld, const double* T, cons
             Vc[c * ld + i] = vc[c];
             hf[c * ld + i] = h[c];
         }
+    }
+}
+
+/* One implicit Euler step of dt at every point (reactor_point): T1 [n], Y1 [K][ld] out, the
+ * Newton iterations per point in iters [n] (negative: not converged). */
+void or_reactor_step(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                     double dt, double atolT, double atolY, double* T1, double* Y1, int* iters, int nthreads) {
+    const int K = m->K;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads_of(nthreads))
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<double> y(K), x1(K + 1);
+        for (int k = 0; k < K; ++k) y[k] = Y[k * ld + i];
+        iters[i] = reactor_point(*m, T[i], p[i], y.data(), dt, atolT, atolY, x1.data());
+        T1[i] = x1[0];
+        for (int k = 0; k < K; ++k) Y1[k * ld + i] = x1[k + 1];
     }
 }
 

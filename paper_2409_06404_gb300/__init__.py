@@ -56,6 +56,17 @@ class _Desc(ctypes.Structure):
     ]
 
 
+class _ReactorOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol_T", ctypes.c_double), ("atol_Y", ctypes.c_double),
+                ("newton_tol", ctypes.c_double), ("lin_tol", ctypes.c_double), ("max_newton", _i32),
+                ("krylov_dim", _i32)]
+
+
+class _ReactorStats(ctypes.Structure):
+    _fields_ = [("converged", _i32), ("newton_iters", _i32), ("krylov_iters", _i32),
+                ("update_wrms", ctypes.c_double), ("residual_wrms", ctypes.c_double)]
+
+
 _SIGS = {
     "nk_version": (_i32, []),
     "nk_last_error": (ctypes.c_char_p, []),
@@ -67,6 +78,9 @@ _SIGS = {
     "nk_transport_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_diffusion_fluxes": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 8 + [_vp]),
+    "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_reactor_step": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_ReactorOpts),
+                                       ctypes.POINTER(_ReactorStats), _vp, ctypes.c_size_t, _vp]),
     "nk_rhs_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rhs_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_rates_linearization_slots": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
@@ -306,6 +320,35 @@ def diffusion_fluxes(m: Mechanism, T, p, Y, Dmix, gradX, want_vc=True, want_hf=T
     _check(lib().nk_diffusion_fluxes(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Dmix), _ptr(gradX), _ptr(j),
                                      _ptr(Vc), _ptr(hf), _stream(stream)))
     return j, Vc, hf
+
+
+def reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-14, newton_tol=0.1, lin_tol=1e-3, max_newton=10,
+                 krylov_dim=20) -> _ReactorOpts:
+    """Options of nk_reactor_step (weighted RMS tolerances; see include/nkchem.h)."""
+    return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim)
+
+
+def reactor_workspace(m: Mechanism, n: int, krylov_dim: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nk_reactor_workspace(m.handle, int(n), int(krylov_dim), ctypes.byref(b)))
+    return b.value
+
+
+def reactor_step(m: Mechanism, T, p, Y, dt: float, opts: _ReactorOpts = None, workspace=None, stream=None) -> dict:
+    """nk_reactor_step: one implicit Euler step of dt at every point, in place on T [n] and the
+    contiguous Y [K, n]; returns the solver statistics."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    if ld != n:
+        raise ValueError("reactor_step takes a contiguous Y [K, n]")
+    opts = opts or reactor_opts()
+    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30:
+        workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim), dtype=torch.uint8, device=T.device)
+    st = _ReactorStats()
+    _check(lib().nk_reactor_step(m.handle, n, _ptr(T), _ptr(p), _ptr(Y), float(dt), ctypes.byref(opts),
+                                 ctypes.byref(st), _ptr(workspace), 0 if workspace is None else workspace.numel(),
+                                 _stream(stream)))
+    return {f: getattr(st, f) for f, _ in _ReactorStats._fields_}
 
 
 def rhs_eval(m: Mechanism, T, p, Y, dlnA=None, precision="fp64", fT=None, fY=None, stream=None):

@@ -624,6 +624,42 @@ nk_status nk_diffusion_fluxes(const nk_mech* m, int64_t n, int64_t ld, const dou
                     "diffusion kernel launch");
 }
 
+nk_status nk_reactor_workspace(const nk_mech* m, int64_t n, int32_t krylov_dim, size_t* bytes) {
+    if (!m || !bytes) return fail(NK_EINVAL, "mech and bytes must not be NULL");
+    if (n < 0) return fail(NK_EINVAL, "n < 0");
+    if (krylov_dim < 1 || krylov_dim > NK_REACTOR_MAX_KRYLOV)
+        return fail(NK_EINVAL, "krylov_dim=%d outside 1..%d", krylov_dim, NK_REACTOR_MAX_KRYLOV);
+    *bytes = n == 0 ? 0 : nk::reactor_workspace_bytes(m->d, n, krylov_dim);
+    return ok();
+}
+
+nk_status nk_reactor_step(const nk_mech* m, int64_t n, double* T, const double* p, double* Y, double dt,
+                          const nk_reactor_opts* opts, nk_reactor_stats* stats, void* workspace,
+                          size_t workspace_bytes, nk_stream stream) {
+    if (!opts || !stats) return fail(NK_EINVAL, "opts and stats must not be NULL");
+    bool skip;
+    nk_status st = check_eval(m, n, n, T, p, Y, &skip);
+    if (st != NK_OK) return st;
+    if (skip) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->converged = 1;
+        return ok();
+    }
+    const nk_reactor_opts& o = *opts;
+    if (o.krylov_dim < 1 || o.krylov_dim > NK_REACTOR_MAX_KRYLOV)
+        return fail(NK_EINVAL, "krylov_dim=%d outside 1..%d", o.krylov_dim, NK_REACTOR_MAX_KRYLOV);
+    if (!(o.rtol >= 0.0) || !(o.atol_T > 0.0) || !(o.atol_Y > 0.0) || !(o.newton_tol > 0.0) || !(o.lin_tol > 0.0) ||
+        o.max_newton < 1 || !(dt >= 0.0) || !std::isfinite(dt))
+        return fail(NK_EINVAL, "bad reactor options (tolerances > 0, max_newton >= 1, finite dt >= 0)");
+    const size_t need = nk::reactor_workspace_bytes(m->d, n, o.krylov_dim);
+    if (!workspace || workspace_bytes < need)
+        return fail(NK_EINVAL, "the reactor step needs %zu bytes of workspace, got %zu", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if (misaligned(workspace)) return fail(NK_EALIGN, "workspace must be 8-byte aligned");
+    return launched(nk::reactor_step(m->d, n, T, p, Y, dt, o, *stats, workspace, (cudaStream_t)stream),
+                    "reactor step");
+}
+
 nk_status nk_rates_jvp(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* vT, const double* vY,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, nk_stream stream) {

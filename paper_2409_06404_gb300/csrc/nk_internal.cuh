@@ -170,6 +170,9 @@ cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s,
                        int rhs = 0);
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n);
+size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim);
+cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p, double* Y, double dt,
+                         const nk_reactor_opts& o, nk_reactor_stats& st, void* ws, cudaStream_t s);
 cudaError_t launch_diffusion(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* D, const double* gradX, double* j, double* Vc,
                              double* hf, cudaStream_t s);

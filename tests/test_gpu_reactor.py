@@ -1,0 +1,80 @@
+"""Implicit Euler step of the homogeneous reactor (nk_reactor_step: Newton with one GMRES solve
+over all points per iteration, exact JVPs, single-precision Krylov basis) against the oracle's
+dense per-point Newton solution of the same nonlinear system.
+
+States: chemical equilibria from element potentials (as in the rates pins) at flame-like
+temperatures, perturbed by 1e-3 in the mass fractions and by ~1 K, so that the step relaxes a
+stiff perturbation; dt from 1e-9 s (a few Krylov iterations) to 1e-5 s (stiffer)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2409_06404_gb300 as nk
+from paper_2409_06404_gb300 import synth
+from conftest import gpu_mechanism, to_dev, host, P_ATM
+from test_oracle_rates import equilibrium_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _near_equilibrium(mech, n, seed):
+    rng = np.random.default_rng(seed)
+    T = rng.uniform(1300.0, 2600.0, n)
+    p = np.full(n, P_ATM)
+    Y = np.stack([equilibrium_state(mech, T[i], p[i], rng) for i in range(n)], axis=1)
+    Y = Y * (1.0 + 1e-3 * rng.standard_normal(Y.shape))
+    Y /= Y.sum(0)
+    T = T + rng.standard_normal(n)
+    return T, p, np.ascontiguousarray(Y)
+
+
+def _step(m, T, p, Y, dt, **kw):
+    o = nk.reactor_opts(**kw)
+    T1, Y1 = T.clone(), Y.clone()
+    st = nk.reactor_step(m, T1, p, Y1, dt, o)
+    return T1, Y1, st
+
+
+# Without a preconditioner the global Krylov solve must resolve every point's stiff modes at
+# once; these steps stay in the regime where it converges within a few cycles (the paper's
+# small DNS steps, Sec. 2).
+@pytest.mark.parametrize("name,n,dt", [("h2_9sp_21rx", 600, 1e-11), ("h2_9sp_21rx", 600, 1e-9),
+                                       ("h2_9sp_21rx", 600, 1e-7), ("ch4_53sp_325rx", 160, 1e-9),
+                                       ("ch4_53sp_325rx", 160, 1e-7), ("ch4_53sp_325rx", 160, 1e-5)])
+def test_reactor_step_vs_dense_newton(cuda, name, n, dt):
+    mech = synth.mechanism(name)
+    m = gpu_mechanism(name)
+    T, p, Y = _near_equilibrium(mech, n, seed=17)
+    rtol, atolT, atolY = 1e-6, 1e-6, 1e-12
+    T1, Y1, st = _step(m, *to_dev(T, p, Y), dt, rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4,
+                       lin_tol=1e-6, max_newton=50, krylov_dim=30)
+    assert st["converged"] == 1, st
+    T_o, Y_o, it = oracle.reactor_step(mech, T, p, Y, dt, atol_T=atolT, atol_Y=atolY)
+    assert np.all(it > 0)
+    # weighted RMS difference with the step's own weights (rtol |x0| + atol)
+    wT = 1.0 / (rtol * np.abs(T) + atolT)
+    wY = 1.0 / (rtol * np.abs(Y) + atolY)
+    d = np.concatenate([((host(T1) - T_o) * wT)[None], (host(Y1) - Y_o) * wY])
+    wrms = np.sqrt(np.mean(d ** 2))
+    print(f"\n{name} dt={dt:g}: newton {st['newton_iters']}, krylov {st['krylov_iters']}, wrms diff {wrms:.2e}")
+    assert wrms <= 1e-3                                    # 1e-3 of the weights: ~1e-9 relative
+
+
+def test_reactor_step_edge_cases(cuda):
+    mech = synth.mechanism("h2_9sp_21rx")
+    m = gpu_mechanism("h2_9sp_21rx")
+    T, p, Y = _near_equilibrium(mech, 64, seed=3)
+    Tt, pt, Yt = to_dev(T, p, Y)
+    # dt = 0: the state is the solution
+    T1, Y1, st = _step(m, Tt, pt, Yt, 0.0)
+    assert st["converged"] == 1 and torch.equal(T1, Tt) and torch.equal(Y1, Yt)
+    # bad options are argument errors
+    with pytest.raises(nk.NkError):
+        _step(m, Tt, pt, Yt, 1e-9, krylov_dim=0)
+    with pytest.raises(nk.NkError):
+        _step(m, Tt, pt, Yt, -1.0)
+    # workspace size grows with the Krylov dimension
+    assert nk.reactor_workspace(m, 64, 30) > nk.reactor_workspace(m, 64, 5) > 0
