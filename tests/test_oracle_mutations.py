@@ -15,6 +15,7 @@ import test_oracle_transport as tr
 import test_oracle_derivs as dv
 import test_oracle_rhs as rh
 import test_oracle_diffusion as df
+import test_oracle_reactor as rx
 
 SRC = open(os.path.join(os.path.dirname(oracle.__file__), "nkoracle.cpp")).read()
 
@@ -48,6 +49,10 @@ MUTATIONS = {
     "diffusion_mole_mass_ratio": ("yv[k] = -y_over_x * D[k] * gradX[c * K + k];", "yv[k] = -D[k] * gradX[c * K + k];"),
     "diffusion_flux_without_rho": ("j[c * K + k] = mx.rho * (yv[k] + Y[k] * Vc[c]);",
                                    "j[c * K + k] = (yv[k] + Y[k] * Vc[c]);"),
+    "reactor_step_sign": ("G[k + 1] = x[k + 1] - x0[k + 1] - dt * fY[k].real();",
+                          "G[k + 1] = x[k + 1] - x0[k + 1] + dt * fY[k].real();"),
+    "reactor_jacobian_sign": ("(j == k + 1 ? 1.0 : 0.0) - dt * fY[k].imag() / hstep",
+                              "(j == k + 1 ? 1.0 : 0.0) + dt * fY[k].imag() / hstep"),
 }
 
 
@@ -86,6 +91,8 @@ def _pins():
         lambda: df.test_fluxes_sum_to_zero("h2_9sp_21rx"),
         df.test_binary_reduces_to_fick_in_mass_fractions,
         df.test_trace_species_and_uniform_composition,
+        rx.test_isomerization_closed_form,
+        rx.test_equilibrium_is_a_fixed_point,
     ]
 
 
