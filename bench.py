@@ -334,6 +334,69 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
     return res
 
 
+# ---------------------------------------------------------------------------------- reactor step
+def reactor_states(nk, m, mech, n, dev, seed=6053):
+    """Near-equilibrium states for the implicit reactor step: chemical equilibria at 512
+    temperatures in [1300, 2600] K and 1 atm from element potentials (X_k proportional to
+    exp(-g_k/RT + sum_e lambda_e a_ek), normalised by a uniform shift found by bisection; g_k
+    from nk_thermo_eval), tiled over the n points and perturbed by 1e-3 in Y and ~1 K in T."""
+    import numpy as np
+    import torch
+    nu, K = 512, mech.K
+    rng = np.random.default_rng(seed)
+    Tu = np.linspace(1300.0, 2600.0, nu)
+    f64 = dict(dtype=torch.float64, device=dev)
+    th = nk.thermo_eval(m, torch.tensor(Tu, **f64), torch.full((nu,), 101325.0, **f64),
+                        torch.full((K, nu), 1.0 / K, **f64))
+    gRT = th["g_k"].cpu().numpy() / (8.314462618 * Tu[None, :])            # [K, nu]
+    a = mech.atoms.astype(float)
+    lam = np.linalg.lstsq(np.hstack([a, np.ones((K, 1))]), gRT, rcond=None)[0][:-1]
+    lam = lam + 0.5 * rng.standard_normal(lam.shape)
+    base = -gRT + a @ lam
+    na = a.sum(axis=1)[:, None]
+    lo, hi = np.full(nu, -1e4), np.full(nu, 1e4)
+    for _ in range(200):                                                  # sum_k X_k(t) = 1, monotone in t
+        t = 0.5 * (lo + hi)
+        z = base + t[None, :] * na
+        zm = z.max(axis=0)
+        big = zm + np.log(np.exp(z - zm).sum(axis=0)) > 0.0
+        hi, lo = np.where(big, t, hi), np.where(big, lo, t)
+    X = np.exp(base + 0.5 * (lo + hi)[None, :] * na)
+    Yu = X * mech.W[:, None]
+    Yu /= Yu.sum(axis=0)
+    idx = torch.arange(n, device=dev) % nu
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    T = torch.tensor(Tu, **f64)[idx] + torch.randn(n, generator=gen, **f64)
+    Y = torch.tensor(Yu, **f64)[:, idx] * (1.0 + 1e-3 * torch.randn((K, n), generator=gen, **f64))
+    Y /= Y.sum(0)
+    return T, torch.full((n,), 101325.0, **f64), Y.contiguous()
+
+
+def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9):
+    """One implicit Euler step of dt over n near-equilibrium points (nk_reactor_step), after one
+    untimed step from the same states; CUDA events on the launching stream."""
+    import torch
+    T0, p, Y0 = reactor_states(nk, m, mech, n, dev)
+    o = nk.reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=20,
+                        krylov_dim=30)
+    ws = torch.empty(nk.reactor_workspace(m, n, o.krylov_dim), dtype=torch.uint8, device=dev)
+    T, Y = T0.clone(), Y0.clone()
+    nk.reactor_step(m, T, p, Y, dt, o, workspace=ws)
+    T.copy_(T0)
+    Y.copy_(Y0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st = nk.reactor_step(m, T, p, Y, dt, o, workspace=ws)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"points": n, "dt_s": dt, "ms": ms, "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters"],
+            "converged": st["converged"], "ms_per_krylov_iter": ms / max(st["krylov_iters"], 1),
+            "workload": f"{MECH}, near-equilibrium states (1300-2600 K, perturbed 1e-3), implicit Euler step "
+                        f"of {dt:g} s, GMRES(30), tolerances rtol 1e-6"}
+
+
 # ---------------------------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -451,6 +514,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms.update({k: [a.elapsed_time(b) for a, b in fev[k]] for k in forms})
 
+    # ---- implicit reactor step (not part of a step)
+    reactor = reactor_row(nk, m, mech, n, dev, s) if args.reactor else None
+
     # ---- implicit-stage sweep (not part of a step)
     stage = None
     if args.stage_dirs > 0:
@@ -552,6 +618,8 @@ def run_ours(args):
     }
     if stage is not None:
         line["implicit_stage"] = stage
+    if reactor is not None:
+        line["reactor_step"] = reactor
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -569,6 +637,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--elements", type=int, default=4096,
                     help="flame field size in elements (a cube; 4096 = the benchmark workload)")
+    ap.add_argument("--no-reactor", dest="reactor", action="store_false",
+                    help="skip the implicit reactor step measurement")
     ap.add_argument("--stage-dirs", type=int, default=10,
                     help="JVP directions of the implicit-stage sweep (0 skips it)")
     ap.add_argument("--stage-elements", type=int, default=None,
