@@ -109,11 +109,12 @@ def _configure(lib):
     lib.or_rates_grad_lnA.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
     lib.or_count_ops.argtypes = [M, _c_dbl, _c_dbl, P, ci, P]
     lib.or_rhs.argtypes = [M, I, I, P, P, P, P, P, P, P, ci]
+    lib.or_rhs_jacobian.argtypes = [M, I, I, P, P, P, P, P, ci]
     lib.or_rhs_jvp.argtypes = [M, I, I, P, P, P, P, P, P, P, P, P, ci]
     lib.or_diffusion.argtypes = [M, I, I, P, P, P, P, P, P, P, P, ci]
     lib.or_reactor_step.argtypes = [M, I, I, P, P, P, _c_dbl, _c_dbl, _c_dbl, P, P, ctypes.POINTER(ctypes.c_int), ci]
     for f in ("or_thermo", "or_nasa7_cs", "or_rates", "or_rates_of_progress", "or_transport",
-              "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops", "or_rhs",
+              "or_rates_jacobian", "or_rates_jvp", "or_rates_grad_lnA", "or_count_ops", "or_rhs", "or_rhs_jacobian",
               "or_rhs_jvp", "or_diffusion", "or_reactor_step"):
         getattr(lib, f).restype = None
     return lib
@@ -310,6 +311,17 @@ def rhs_jvp(mech, T, p, Y, vT, vY, threads: int = 0, scales: bool = False):
     _lib_handle().or_rhs_jvp(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(vT), _dp(vY), _dp(dfT), _dp(dfY),
                              _dp(sT), _dp(sY), threads)
     return (dfT, dfY, sT, sY) if scales else (dfT, dfY)
+
+
+def rhs_jacobian(mech, T, p, Y, threads: int = 0, scales: bool = False):
+    """Dense complex-step Jacobian [n, K+1, K+1] of the sources: rows (fT, fY_k), columns
+    (T, Y_j); with ``scales`` also the per-entry derivative magnitudes."""
+    pk = _Packed(mech)
+    T, p, Y, n = _state(T, p, Y, pk.K)
+    J = np.empty((n, pk.K + 1, pk.K + 1))
+    Js = np.empty_like(J) if scales else None
+    _lib_handle().or_rhs_jacobian(pk.ptr(), n, n, _dp(T), _dp(p), _dp(Y), _dp(J), _dp(Js), threads)
+    return (J, Js) if scales else J
 
 
 def diffusion(mech, T, p, Y, D, gradX, threads: int = 0):

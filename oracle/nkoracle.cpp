@@ -32,7 +32,8 @@
  *      concentrations reach ~1e80 and a step of 1e-30 would bias the result by ~1e20.
  *  11. implicit-stage chemistry sources of Eq. 1a-b at fixed p: dY_k/dt = W_k omega_k / rho,
  *      dT/dt = hrr / (rho c_p), c_p the mass-based mixture heat capacity; their directional
- *      derivatives by complex step as in 10.
+ *      derivatives and their dense Jacobian (one unit direction per column) by complex step as
+ *      in 10.
  *  12. mixture-averaged diffusion fluxes of Eq. 2: V_k = -(D_k/X_k) grad X_k + V_c with
  *      V_c = -sum_k Y_k V'_k; j_k = rho Y_k V_k and sum_k c_p,k j_k.
  *  13. one implicit Euler step of the homogeneous constant-pressure reactor, x1 - x0 - dt f(x1)
@@ -777,6 +778,36 @@ void or_rhs_jvp(const or_mech* m, int64_t n, int64_t ld, const double* T, const 
         if (dfY_scale)
             for (int k = 0; k < K; ++k) dfY_scale[k * ld + i] = dsc[k] / hstep;
         if (dfT_scale) dfT_scale[i] = dst / hstep;
+    }
+}
+
+/* Dense Jacobian of the sources of 11 with respect to (T, Y_0..Y_{K-1}) at fixed p, one complex
+ * step per column.  J: [n][(K+1)*(K+1)], row = output (0: dT/dt, k+1: dY_k/dt), column = input
+ * (0: T, j+1: Y_j), the ordering of the reactor unknowns of 13.  Js (nullable), same shape: the
+ * derivative magnitudes of or_rhs_jvp along each unit direction. */
+void or_rhs_jacobian(const or_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                     double* J, double* Js, int nthreads) {
+    const int K = m->K, N = K + 1;
+    const double hstep = 1e-100;
+#pragma omp parallel for schedule(static) num_threads(nthreads_of(nthreads))
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<cplx> y(K), f(K);
+        std::vector<double> sc(K), dsc(K);
+        double* Ji = J + (size_t)i * N * N;
+        double* Si = Js ? Js + (size_t)i * N * N : nullptr;
+        for (int j = 0; j < N; ++j) {
+            for (int k = 0; k < K; ++k) y[k] = cplx(Y[k * ld + i], j == k + 1 ? hstep : 0.0);
+            cplx ft;
+            double st, dst;
+            rhs_point<cplx>(*m, cplx(T[i], j == 0 ? hstep : 0.0), p[i], y.data(), f.data(), ft, sc.data(), &st,
+                            dsc.data(), &dst);
+            Ji[j] = ft.imag() / hstep;
+            for (int k = 0; k < K; ++k) Ji[(size_t)(k + 1) * N + j] = f[k].imag() / hstep;
+            if (Si) {
+                Si[j] = dst / hstep;
+                for (int k = 0; k < K; ++k) Si[(size_t)(k + 1) * N + j] = dsc[k] / hstep;
+            }
+        }
     }
 }
 

@@ -16,6 +16,7 @@ import test_oracle_derivs as dv
 import test_oracle_rhs as rh
 import test_oracle_diffusion as df
 import test_oracle_reactor as rx
+import test_oracle_rhs_jacobian as rj
 
 SRC = open(os.path.join(os.path.dirname(oracle.__file__), "nkoracle.cpp")).read()
 
@@ -53,6 +54,10 @@ MUTATIONS = {
                           "G[k + 1] = x[k + 1] - x0[k + 1] + dt * fY[k].real();"),
     "reactor_jacobian_sign": ("(j == k + 1 ? 1.0 : 0.0) - dt * fY[k].imag() / hstep",
                               "(j == k + 1 ? 1.0 : 0.0) + dt * fY[k].imag() / hstep"),
+    "rhs_jacobian_transposed": ("Ji[(size_t)(k + 1) * N + j] = f[k].imag() / hstep;",
+                                "Ji[(size_t)j * N + k + 1] = f[k].imag() / hstep;"),
+    "rhs_jacobian_T_row_column_shift": ("            Ji[j] = ft.imag() / hstep;",
+                                        "            Ji[j > 0 ? j - 1 : 0] = ft.imag() / hstep;"),
 }
 
 
@@ -93,6 +98,9 @@ def _pins():
         df.test_trace_species_and_uniform_composition,
         rx.test_isomerization_closed_form,
         rx.test_equilibrium_is_a_fixed_point,
+        lambda: rj.test_columns_match_central_differences("h2_9sp_21rx"),
+        lambda: rj.test_enthalpy_balance_ties_the_temperature_row("h2_9sp_21rx"),
+        rj.test_isomerization_closed_form,
     ]
 
 
