@@ -372,29 +372,39 @@ def reactor_states(nk, m, mech, n, dev, seed=6053):
     return T, torch.full((n,), 101325.0, **f64), Y.contiguous()
 
 
-def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9):
-    """One implicit Euler step of dt over n near-equilibrium points (nk_reactor_step), after one
-    untimed step from the same states; CUDA events on the launching stream."""
+def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9, dt_large=1e-5):
+    """One implicit Euler step over n near-equilibrium points (nk_reactor_step), each after one
+    untimed step from the same states; CUDA events on the launching stream.  Three runs: the
+    paper's unpreconditioned GMRES at dt, and with the per-point block-Jacobi preconditioner at
+    dt and at dt_large."""
     import torch
     T0, p, Y0 = reactor_states(nk, m, mech, n, dev)
-    o = nk.reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=20,
-                        krylov_dim=30)
-    ws = torch.empty(nk.reactor_workspace(m, n, o.krylov_dim), dtype=torch.uint8, device=dev)
+    kw = dict(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=20, krylov_dim=30)
+    ws = torch.empty(nk.reactor_workspace(m, n, kw["krylov_dim"], 1), dtype=torch.uint8, device=dev)
     T, Y = T0.clone(), Y0.clone()
-    nk.reactor_step(m, T, p, Y, dt, o, workspace=ws)
-    T.copy_(T0)
-    Y.copy_(Y0)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    st = nk.reactor_step(m, T, p, Y, dt, o, workspace=ws)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    return {"points": n, "dt_s": dt, "ms": ms, "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters"],
-            "converged": st["converged"], "ms_per_krylov_iter": ms / max(st["krylov_iters"], 1),
-            "workload": f"{MECH}, near-equilibrium states (1300-2600 K, perturbed 1e-3), implicit Euler step "
-                        f"of {dt:g} s, GMRES(30), tolerances rtol 1e-6"}
+
+    def run(step, precond):
+        o = nk.reactor_opts(precond=precond, **kw)
+        for timed in (False, True):
+            T.copy_(T0)
+            Y.copy_(Y0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = nk.reactor_step(m, T, p, Y, step, o, workspace=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        return {"dt_s": step, "ms": ms, "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters"],
+                "converged": st["converged"], "ms_per_krylov_iter": ms / max(st["krylov_iters"], 1)}
+
+    res = {"points": n,
+           "workload": f"{MECH}, near-equilibrium states (1300-2600 K, perturbed 1e-3), one implicit Euler step, "
+                       f"GMRES(30), rtol 1e-6, atol_T 1e-6, atol_Y 1e-12, newton_tol 1e-4, lin_tol 1e-6"}
+    res.update(run(dt, 0))
+    res["block_jacobi"] = run(dt, 1)
+    res["block_jacobi_large_dt"] = run(dt_large, 1)
+    return res
 
 
 # ---------------------------------------------------------------------------------- our arm

@@ -248,6 +248,45 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
                                   nk_stream stream);
 
 /*
+ * Dense Jacobian of the sources of nk_rhs_eval with respect to x = (T, Y_0..Y_{K-1}) at fixed p,
+ * assembled from a stored linearization (nk_rates_linearize, dlnA = NULL) and the sources
+ * (nk_rhs_eval, NK_FP64) at the same state: the per-point blocks of the Jacobian of the
+ * paper's implicit thermochemistry stage (Sec. 2), exact to rounding.
+ *   lin[slots*ldl]        stored linearization at (T, p, Y)
+ *   fT[n], fY[K*ld]       the sources at (T, p, Y)
+ *   J[(K+1)*(K+1)*ldJ]    out: entry (r, c) of point i at J[(r (K+1) + c) ldJ + i]; r, c = 0 for T,
+ *                         k + 1 for Y_k (row = source, column = variable); ldJ >= n
+ * Double precision.
+ */
+nk_status nk_rhs_jacobian(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                          const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
+                          double* J, int64_t ldJ, nk_stream stream);
+
+/*
+ * Per-point block-Jacobi preconditioner of an implicit stage's Newton-Krylov solve (an option
+ * beside the paper's unpreconditioned GMRES, Sec. 2): with w the error weights of the solve,
+ * the blocks P = I - dt diag(w) J diag(1/w) (J as in nk_rhs_jacobian) are formed and factored
+ * in place, LU with partial pivoting per point, in double precision (the blocks of stiff
+ * chemistry in these weights are far too ill-conditioned for single-precision factors).  Each
+ * row r of P is first scaled by 2^-e_r, its largest entry then in [1/2, 1).
+ *   w[(K+1)*ldw]          weights, row 0 for T, row k + 1 for Y_k
+ *   F[(K+1)*(K+1)*ldF]    out: the factors of the scaled block, entry (r, c) of point i at
+ *                         F[(r (K+1) + c) ldF + i], in pivot order: row k holds the
+ *                         unit-lower part L_k,0..k-1 and U_k,k+1.. of the k-th pivot row, with
+ *                         1/U_kk at (k, k) (a zero pivot is replaced by 1)
+ *   piv[(K+1)*ldF]        out: for the k-th pivot row of point i, piv[k ldF + i] = its row
+ *                         index (low 16 bits) | e_row << 16 (signed)
+ * nk_block_jacobi_apply then computes z = P^-1 v for vectors v, z of (K+1) rows of ldv / ldz
+ * (row r of point i at r ld + i; z may alias v).  K + 1 <= 160; ldF >= n.
+ */
+nk_status nk_block_jacobi_factor(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                                 const double* Y, const double* lin, int64_t ldl, const double* fT,
+                                 const double* fY, const double* w, int64_t ldw, double dt, double* F,
+                                 int32_t* piv, int64_t ldF, nk_stream stream);
+nk_status nk_block_jacobi_apply(const nk_mech* mech, int64_t n, const double* F, const int32_t* piv, int64_t ldF,
+                                const double* v, int64_t ldv, double* z, int64_t ldz, nk_stream stream);
+
+/*
  * One implicit (backward) Euler step of dt seconds of the homogeneous constant-pressure
  * reactor at every point: solves x1 - x0 - dt f(x1) = 0, x = (T, Y_k), f the sources of
  * nk_rhs_eval, the nonlinear system of the paper's implicit thermochemistry stage (Sec. 2),
@@ -258,7 +297,13 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
  * norms with weights 1/(rtol |x0_i| + atol_i).
  *   T[n], Y[K*n]   in: the state x0; out: the step's result (contiguous: Y rows of stride n)
  *   workspace      device, nk_reactor_workspace bytes (holds (K+1) n doubles x 7 and
- *                  (krylov_dim + 1) (K+1) n floats)
+ *                  (krylov_dim + 1) (K+1) n floats; with the preconditioner also (K+1)^2 n
+ *                  doubles of factors, (K+1) n pivot words and a stored linearization of up to
+ *                  about 2 GB, filled chunk by chunk)
+ * With precond = 1 the solve is left-preconditioned by the per-point blocks of
+ * nk_block_jacobi_factor, made once per step at x0: GMRES minimises P^-1 (r - A z), which
+ * tracks the error of the update (the unpreconditioned residual of stiff chemistry is dominated
+ * by its stiff components), and lin_tol applies to it.
  * The call returns when the step is done (it reads a few scalars back per GMRES iteration);
  * non-convergence is reported in stats, not as an error.
  */
@@ -274,6 +319,7 @@ typedef struct {
                              (or after krylov_dim iterations; the partial solution is used) */
     int32_t max_newton;   /* Newton iterations at most */
     int32_t krylov_dim;   /* GMRES iterations per Newton iteration, 1..NK_REACTOR_MAX_KRYLOV */
+    int32_t precond;      /* 0: none (the paper's stage); 1: per-point block Jacobi (K + 1 <= 160) */
 } nk_reactor_opts;
 typedef struct {
     int32_t converged;    /* 1 when the update test was met (0: max_newton reached, or the
@@ -283,7 +329,7 @@ typedef struct {
     double update_wrms;   /* weighted RMS norm of the last Newton update */
     double residual_wrms; /* weighted RMS norm of the residual before the last update */
 } nk_reactor_stats;
-nk_status nk_reactor_workspace(const nk_mech* mech, int64_t n, int32_t krylov_dim, size_t* bytes);
+nk_status nk_reactor_workspace(const nk_mech* mech, int64_t n, int32_t krylov_dim, int32_t precond, size_t* bytes);
 nk_status nk_reactor_step(const nk_mech* mech, int64_t n, double* T, const double* p, double* Y, double dt,
                           const nk_reactor_opts* opts, nk_reactor_stats* stats, void* workspace,
                           size_t workspace_bytes, nk_stream stream);

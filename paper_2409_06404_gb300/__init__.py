@@ -59,7 +59,7 @@ class _Desc(ctypes.Structure):
 class _ReactorOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol_T", ctypes.c_double), ("atol_Y", ctypes.c_double),
                 ("newton_tol", ctypes.c_double), ("lin_tol", ctypes.c_double), ("max_newton", _i32),
-                ("krylov_dim", _i32)]
+                ("krylov_dim", _i32), ("precond", _i32)]
 
 
 class _ReactorStats(ctypes.Structure):
@@ -78,7 +78,11 @@ _SIGS = {
     "nk_transport_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_diffusion_fluxes": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 8 + [_vp]),
-    "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_rhs_jacobian": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "nk_block_jacobi_factor": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64,
+                                              ctypes.c_double, _vp, _vp, _i64, _vp]),
+    "nk_block_jacobi_apply": (ctypes.c_int, [_vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "nk_reactor_step": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_ReactorOpts),
                                        ctypes.POINTER(_ReactorStats), _vp, ctypes.c_size_t, _vp]),
     "nk_rhs_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
@@ -323,14 +327,15 @@ def diffusion_fluxes(m: Mechanism, T, p, Y, Dmix, gradX, want_vc=True, want_hf=T
 
 
 def reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-14, newton_tol=0.1, lin_tol=1e-3, max_newton=10,
-                 krylov_dim=20) -> _ReactorOpts:
-    """Options of nk_reactor_step (weighted RMS tolerances; see include/nkchem.h)."""
-    return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim)
+                 krylov_dim=20, precond=0) -> _ReactorOpts:
+    """Options of nk_reactor_step (weighted RMS tolerances; precond 1 = per-point block Jacobi;
+    see include/nkchem.h)."""
+    return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim, precond)
 
 
-def reactor_workspace(m: Mechanism, n: int, krylov_dim: int) -> int:
+def reactor_workspace(m: Mechanism, n: int, krylov_dim: int, precond: int = 0) -> int:
     b = ctypes.c_size_t()
-    _check(lib().nk_reactor_workspace(m.handle, int(n), int(krylov_dim), ctypes.byref(b)))
+    _check(lib().nk_reactor_workspace(m.handle, int(n), int(krylov_dim), int(precond), ctypes.byref(b)))
     return b.value
 
 
@@ -342,8 +347,9 @@ def reactor_step(m: Mechanism, T, p, Y, dt: float, opts: _ReactorOpts = None, wo
     if ld != n:
         raise ValueError("reactor_step takes a contiguous Y [K, n]")
     opts = opts or reactor_opts()
-    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30:
-        workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim), dtype=torch.uint8, device=T.device)
+    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30 and opts.precond in (0, 1):
+        workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim, opts.precond), dtype=torch.uint8,
+                                device=T.device)
     st = _ReactorStats()
     _check(lib().nk_reactor_step(m.handle, n, _ptr(T), _ptr(p), _ptr(Y), float(dt), ctypes.byref(opts),
                                  ctypes.byref(st), _ptr(workspace), 0 if workspace is None else workspace.numel(),
@@ -412,6 +418,64 @@ def rates_jvp_linearized(m: Mechanism, T, p, Y, lin, vT, vY, stream=None):
     _check(lib().nk_rates_jvp_linearized(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0),
                                          _ptr(vT), _ptr(vY), _ptr(d_omega), _ptr(d_hrr), _stream(stream)))
     return d_omega, d_hrr
+
+
+def rhs_jacobian(m: Mechanism, T, p, Y, lin, fT, fY, stream=None):
+    """nk_rhs_jacobian: the dense Jacobian [K+1, K+1, n] of the sources (rows fT, fY_k; columns
+    T, Y_j) from a stored linearization (rates_linearize) and the sources (rhs_eval, fp64) at
+    the same state."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _check_lin(m, lin, n)
+    _vec(fT, n, "fT")
+    _species_in(m, fY, n, ld, "fY")
+    N = m.K + 1
+    J = torch.empty((N, N, max(n, 1)), dtype=torch.float64, device=T.device)
+    _check(lib().nk_rhs_jacobian(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0), _ptr(fT),
+                                 _ptr(fY), _ptr(J), J.stride(1), _stream(stream)))
+    return J[:, :, :n]
+
+
+def block_jacobi_factor(m: Mechanism, T, p, Y, lin, fT, fY, w, dt: float, stream=None):
+    """nk_block_jacobi_factor: LU factors (float64 [K+1, K+1, n], pivot order) of the row-scaled
+    per-point blocks I - dt diag(w) J diag(1/w), w [K+1, n] (row 0 for T), and the pivot words
+    (int32 [K+1, n]: row index | row exponent << 16)."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _check_lin(m, lin, n)
+    _vec(fT, n, "fT")
+    _species_in(m, fY, n, ld, "fY")
+    N = m.K + 1
+    if w.dtype != torch.float64 or w.dim() != 2 or w.shape[0] != N or w.shape[1] < n or w.stride(1) != 1:
+        raise ValueError("w must be a float64 [K+1, >= n] row-major tensor")
+    F = torch.empty((N, N, max(n, 1)), dtype=torch.float64, device=T.device)
+    piv = torch.empty((N, max(n, 1)), dtype=torch.int32, device=T.device)
+    _check(lib().nk_block_jacobi_factor(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0),
+                                        _ptr(fT), _ptr(fY), _ptr(w), w.stride(0), float(dt), _ptr(F), _ptr(piv),
+                                        F.stride(1), _stream(stream)))
+    return F[:, :, :n], piv[:, :n]
+
+
+def block_jacobi_apply(m: Mechanism, F, piv, v, stream=None):
+    """nk_block_jacobi_apply: z = P^-1 v per point for float64 v [K+1, n]."""
+    import torch
+    N = m.K + 1
+    if F.dtype != torch.float64 or F.dim() != 3 or F.shape[:2] != (N, N) or F.stride(2) != 1:
+        raise ValueError("F must be float64 [K+1, K+1, n] from block_jacobi_factor")
+    n = F.shape[2]
+    if piv.dtype != torch.int32 or piv.shape != (N, n) or piv.stride(0) != F.stride(1):
+        raise ValueError("piv must be the int32 [K+1, n] tensor from the same block_jacobi_factor call")
+    if v.dtype != torch.float64 or v.shape != (N, n) or v.stride(1) != 1:
+        raise ValueError("v must be a float64 [K+1, n] row-major tensor")
+    z = torch.empty_like(v)
+    _check(lib().nk_block_jacobi_apply(m.handle, n, _ptr(F), _ptr(piv), F.stride(1), _ptr(v), v.stride(0),
+                                       _ptr(z), z.stride(0), _stream(stream)))
+    return z
+
+
+def _check_lin(m, lin, n):
+    if lin.dim() != 2 or lin.shape[0] != linearization_slots(m) or lin.stride(1) != 1 or lin.shape[1] < n:
+        raise ValueError("lin must be a [slots, >= n] row-major tensor from rates_linearize")
 
 
 def rates_vjp_workspace(m: Mechanism, n: int) -> int:

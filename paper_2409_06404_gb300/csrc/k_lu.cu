@@ -1,0 +1,145 @@
+// Per-point block-Jacobi preconditioner of the implicit stage's GMRES solve: LU factors with
+// partial pivoting of the (K+1) x (K+1) block P = I - dt diag(w) J diag(1/w) of every point
+// (k_jac.cu writes P), and their application z = P^-1 v.  Double precision: the blocks of
+// stiff chemistry in the solver's weights are so ill-conditioned that single-precision factors
+// (even of row- and column-equilibrated blocks) missed the solution by orders of magnitude in
+// testing, while double-precision ones stay within tens of per cent -- enough to steer GMRES.
+//
+// Storage, entry (r, c) of point i at F[(r N + c) ldF + i] (N = K + 1, all points of one
+// entry contiguous): the factorization reads the row-scaled block D P there (D = diag(2^-e_r),
+// e_r at piv[r ldq + i], both from k_jac.cu) and overwrites it with the factors of D P in pivot
+// order -- row k holds L_k,0..k-1 (unit lower part) and U_k,k..N-1 of the k-th pivot row, with
+// 1/U_kk in place of U_kk -- and piv[k ldq + i] with that row's index (low 16 bits) and its
+// exponent e (high 16 bits, signed): P z = v is then L U z = (D v) in pivot order.
+//
+// Factorization: one warp per point with its block in shared memory (nk_lu.cuh; row stride
+// N + 1), a block of `pts` points loaded and stored entry by entry for all its points at once
+// (pts x 8 bytes contiguous per entry).
+// Application: one thread per point, forward then backward substitution with the vector in
+// shared memory and the factors read once, in order (coalesced across the warp's points).
+// Shared memory bounds the block: N (N + 1) doubles per point, N = K + 1 <= kMaxPrecondN.
+#include <algorithm>
+#include <cstdint>
+
+#include "nk_lu.cuh"
+
+namespace nk {
+namespace {
+
+__global__ void lu_kernel(const int N, const int pts, const int64_t n, double* __restrict__ F, const int64_t ldF,
+                          int32_t* __restrict__ piv, const int64_t ldq) {
+    extern __shared__ double sa[];
+    const int S = N + 1;
+    const int64_t NN = (int64_t)N * N;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * pts;
+    const int np = (int)(n - i0 < pts ? n - i0 : pts);         // points of this block
+    int32_t* sperm = reinterpret_cast<int32_t*>(sa + (size_t)pts * N * S);   // [pts][N] pivot rows
+    int32_t* sexp = sperm + (size_t)pts * N;                                  // [pts][N] row exponents
+    for (int64_t f = threadIdx.x; f < NN * np; f += blockDim.x) {
+        const int64_t e = f / np;
+        const int q = (int)(f - e * np);
+        sa[(size_t)q * N * S + (e / N) * S + e % N] = F[e * ldF + i0 + q];
+    }
+    for (int f = threadIdx.x; f < N * np; f += blockDim.x) {
+        const int r = f / np, q = f % np;
+        sexp[q * N + r] = piv[(int64_t)r * ldq + i0 + q];
+    }
+    __syncthreads();
+    if (wp < np) warp_lu(sa + (size_t)wp * N * S, N, S, lane, sperm + wp * N);
+    __syncthreads();
+    for (int64_t f = threadIdx.x; f < NN * np; f += blockDim.x) {
+        const int64_t e = f / np;
+        const int q = (int)(f - e * np);
+        const int k = (int)(e / N), j = (int)(e % N);
+        F[e * ldF + i0 + q] = sa[(size_t)q * N * S + sperm[q * N + k] * S + j];
+    }
+    for (int f = threadIdx.x; f < N * np; f += blockDim.x) {
+        const int k = f / np, q = f % np;
+        const int r = sperm[q * N + k];
+        piv[(int64_t)k * ldq + i0 + q] = (r & 0xffff) | (int32_t)((uint32_t)sexp[q * N + r] << 16);
+    }
+}
+
+constexpr int kApplyBlk = 128;
+
+// sum_{j0 <= j < j1} f[j ldF] y[j]: four independent partial sums, so that four factor loads
+// per thread are in flight (the loads, not the arithmetic, bound the substitutions)
+__device__ __forceinline__ double dot_run(const double* __restrict__ f, int64_t ldF, const double* y, int j0, int j1) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = j0;
+    for (; j + 3 < j1; j += 4) {
+        const double f0 = f[(int64_t)j * ldF], f1 = f[(int64_t)(j + 1) * ldF], f2 = f[(int64_t)(j + 2) * ldF],
+                     f3 = f[(int64_t)(j + 3) * ldF];
+        s0 = fma(f0, y[j * kApplyBlk], s0);
+        s1 = fma(f1, y[(j + 1) * kApplyBlk], s1);
+        s2 = fma(f2, y[(j + 2) * kApplyBlk], s2);
+        s3 = fma(f3, y[(j + 3) * kApplyBlk], s3);
+    }
+    for (; j < j1; ++j) s0 = fma(f[(int64_t)j * ldF], y[j * kApplyBlk], s0);
+    return (s0 + s1) + (s2 + s3);
+}
+
+// z = P^-1 v per point: v and z rows of ldv / ldz (row r of point i at r ld + i), of type TI and
+// TO, arithmetic in double.  z may alias v: every thread reads its point's entries of v before
+// it writes z.
+template <class TI, class TO>
+__global__ void __launch_bounds__(kApplyBlk) lu_apply_kernel(const int N, const int64_t n, const double* __restrict__ F,
+                                                             const int64_t ldF, const int32_t* __restrict__ piv,
+                                                             const int64_t ldq, const TI* v, const int64_t ldv, TO* z,
+                                                             const int64_t ldz) {
+    extern __shared__ double sy[];
+    const int64_t i = (int64_t)blockIdx.x * kApplyBlk + threadIdx.x;
+    if (i >= n) return;
+    double* y = sy + threadIdx.x;
+    const double* f = F + i;
+    for (int k = 0; k < N; ++k) {                              // L y = (D v)(perm), unit diagonal
+        const int32_t pk = piv[(int64_t)k * ldq + i];
+        const double* fk = f + (int64_t)k * N * ldF;
+        y[k * kApplyBlk] = ldexp((double)v[(int64_t)(pk & 0xffff) * ldv + i], -(pk >> 16)) -
+                           dot_run(fk, ldF, y, 0, k);
+    }
+    for (int k = N - 1; k >= 0; --k) {                         // U x = y, 1/U_kk stored
+        const double* fk = f + (int64_t)k * N * ldF;
+        y[k * kApplyBlk] = (y[k * kApplyBlk] - dot_run(fk, ldF, y, k + 1, N)) * fk[(int64_t)k * ldF];
+    }
+    for (int k = 0; k < N; ++k) z[(int64_t)k * ldz + i] = (TO)y[k * kApplyBlk];
+}
+
+template <class TI, class TO>
+cudaError_t apply(int N, int64_t n, const double* F, int64_t ldF, const int32_t* piv, int64_t ldq, const TI* v,
+                  int64_t ldv, TO* z, int64_t ldz, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t bytes = (size_t)N * kApplyBlk * sizeof(double);
+    auto kern = lu_apply_kernel<TI, TO>;
+    cudaError_t e = ensure_smem((const void*)kern, bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)((n + kApplyBlk - 1) / kApplyBlk), kApplyBlk, bytes, s>>>(N, n, F, ldF, piv, ldq, v, ldv, z, ldz);
+    return cudaGetLastError();
+}
+
+size_t lu_smem(int N, int pts) { return (size_t)pts * N * (N + 1) * sizeof(double) + (size_t)pts * N * 8 + 16; }
+
+}  // namespace
+
+cudaError_t launch_precond_factor(int N, int64_t n, double* F, int64_t ldF, int32_t* piv, int64_t ldq,
+                                  cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (N < 1 || N > kMaxPrecondN) return cudaErrorInvalidValue;
+    // points per block: up to 4 (32-byte runs per entry), within the shared-memory limit
+    int pts = 4;
+    while (pts > 1 && lu_smem(N, pts) > smem_limit()) --pts;
+    const size_t bytes = lu_smem(N, pts);
+    if (bytes > smem_limit()) return cudaErrorInvalidConfiguration;
+    cudaError_t e = ensure_smem((const void*)lu_kernel, bytes);
+    if (e != cudaSuccess) return e;
+    lu_kernel<<<(unsigned)((n + pts - 1) / pts), 32 * pts, bytes, s>>>(N, pts, n, F, ldF, piv, ldq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precond_apply(int N, int64_t n, const double* F, int64_t ldF, const int32_t* piv, int64_t ldq,
+                                 const double* v, int64_t ldv, double* z, int64_t ldz, cudaStream_t s) {
+    return apply<double, double>(N, n, F, ldF, piv, ldq, v, ldv, z, ldz, s);
+}
+
+}  // namespace nk

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <map>
 #include <vector>
 
 #include "nk_internal.cuh"
@@ -337,6 +338,41 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
         lin_boff[q] = lin_nb;
         lin_nb += rxn[q].nr + rxn[q].np;
     }
+    // Jacobian assembly terms (nk_internal.cuh): for every entry a of reaction q (species k,
+    // signed coefficient nu), V_k gets nu A_q; G_k,j gets nu B_q,b for every entry b (species j)
+    // and, for third-body and Troe reactions, Lam_k gets nu L_q and G_k,j nu (eps_j - 1) L_q for
+    // every listed efficiency.  Terms of one entry in reaction order.
+    std::vector<int32_t> jac_row(K + 1), jac_col, jac_ent{0};
+    std::vector<nk::JacTerm> jac_term;
+    {
+        std::map<std::pair<int, int>, std::vector<nk::JacTerm>> ent;
+        for (int q = 0; q < R; ++q) {
+            const nk::RxnRec& x = rxn[q];
+            const int32_t sB = R + lin_boff[q], sL = R + lin_nb + (q - R_el);
+            for (int a = 0; a < x.nr + x.np; ++a) {
+                const int ia = a < x.nr ? a : nk::kMaxSide + (a - x.nr);
+                const int k = x.sp[ia];
+                const double nu = x.nud[ia];
+                ent[{k, -1}].push_back({nu, q, 0});
+                for (int b = 0; b < x.nr + x.np; ++b) {
+                    const int ib = b < x.nr ? b : nk::kMaxSide + (b - x.nr);
+                    ent[{k, x.sp[ib]}].push_back({nu, sB + b, 0});
+                }
+                if (x.type != NK_RXN_ELEMENTARY) {
+                    ent[{k, -2}].push_back({nu, sL, 0});
+                    for (int j = x.eff0; j < x.eff1; ++j) ent[{k, eff_sp[j]}].push_back({nu * eff_m1[j], sL, 0});
+                }
+            }
+        }
+        int row = 0;
+        for (const auto& kv : ent) {
+            while (row <= kv.first.first) jac_row[row++] = (int32_t)jac_col.size();
+            jac_col.push_back(kv.first.second);
+            jac_term.insert(jac_term.end(), kv.second.begin(), kv.second.end());
+            jac_ent.push_back((int32_t)jac_term.size());
+        }
+        while (row <= K) jac_row[row++] = (int32_t)jac_col.size();
+    }
     // reaction thermo groups (nk_internal.cuh): net coefficients of each reaction, grouped by
     // the species' T_mid, combined in extended precision
     std::vector<float2> grp_df;
@@ -394,7 +430,9 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_dexp = L.add(df_exp.size() * 8), o_drc = L.add(df_rc.size() * 8), o_dlc = L.add(df_lc.size() * 8),
                  o_ndf = L.add(nasa_df.size() * 8), o_rdf = L.add(rxn_df.size() * 16),
                  o_tdf = L.add(troe_df.size() * 16 + 16), o_gdf = L.add(grp_df.size() * 8 + 16),
-                 o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16);
+                 o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16),
+                 o_jr = L.add(jac_row.size() * 4 + 16), o_jc = L.add(jac_col.size() * 4 + 16),
+                 o_je = L.add(jac_ent.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -438,6 +476,10 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_gdf, grp_df.data(), grp_df.size() * 8);
     put(o_gT, grp_Tmid.data(), grp_Tmid.size() * 8);
     put(o_lb, lin_boff.data(), (size_t)R * 4);
+    put(o_jr, jac_row.data(), jac_row.size() * 4);
+    put(o_jc, jac_col.data(), jac_col.size() * 4);
+    put(o_je, jac_ent.data(), jac_ent.size() * 4);
+    put(o_jt, jac_term.data(), jac_term.size() * sizeof(nk::JacTerm));
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -507,6 +549,10 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.grp_Tmid = reinterpret_cast<const double*>(b + o_gT);
     dm.lin_boff = reinterpret_cast<const int32_t*>(b + o_lb);
     dm.lin_nb = lin_nb;
+    dm.jac_row = reinterpret_cast<const int32_t*>(b + o_jr);
+    dm.jac_col = reinterpret_cast<const int32_t*>(b + o_jc);
+    dm.jac_ent = reinterpret_cast<const int32_t*>(b + o_je);
+    dm.jac_term = reinterpret_cast<const nk::JacTerm*>(b + o_jt);
     *out = m;
     return ok();
 }
@@ -624,13 +670,69 @@ nk_status nk_diffusion_fluxes(const nk_mech* m, int64_t n, int64_t ld, const dou
                     "diffusion kernel launch");
 }
 
-nk_status nk_reactor_workspace(const nk_mech* m, int64_t n, int32_t krylov_dim, size_t* bytes) {
+nk_status check_precond(const nk_mech* m, int32_t precond) {
+    if (precond != 0 && precond != 1) return fail(NK_EINVAL, "precond=%d is not 0 or 1", precond);
+    if (precond && m->d.K + 1 > nk::kMaxPrecondN)
+        return fail(NK_EUNSUPPORTED, "the block-Jacobi preconditioner takes K + 1 <= %d (K=%d)", nk::kMaxPrecondN,
+                    m->d.K);
+    return NK_OK;
+}
+
+nk_status nk_reactor_workspace(const nk_mech* m, int64_t n, int32_t krylov_dim, int32_t precond, size_t* bytes) {
     if (!m || !bytes) return fail(NK_EINVAL, "mech and bytes must not be NULL");
     if (n < 0) return fail(NK_EINVAL, "n < 0");
     if (krylov_dim < 1 || krylov_dim > NK_REACTOR_MAX_KRYLOV)
         return fail(NK_EINVAL, "krylov_dim=%d outside 1..%d", krylov_dim, NK_REACTOR_MAX_KRYLOV);
-    *bytes = n == 0 ? 0 : nk::reactor_workspace_bytes(m->d, n, krylov_dim);
+    nk_status st = check_precond(m, precond);
+    if (st != NK_OK) return st;
+    *bytes = n == 0 ? 0 : nk::reactor_workspace_bytes(m->d, n, krylov_dim, precond);
     return ok();
+}
+
+nk_status nk_rhs_jacobian(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                          const double* lin, int64_t ldl, const double* fT, const double* fY, double* J, int64_t ldJ,
+                          nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !fT || !fY || !J) return fail(NK_EINVAL, "lin, fT, fY and J must not be NULL");
+    if (ldl < n || ldJ < n) return fail(NK_EINVAL, "ldl and ldJ must be >= n=%lld", (long long)n);
+    if ((st = check_out({lin, fT, fY, J})) != NK_OK) return st;
+    return launched(nk::launch_rhs_jacobian(m->d, n, ld, T, p, Y, lin, ldl, fT, fY, J, ldJ, (cudaStream_t)stream),
+                    "jacobian kernel launch");
+}
+
+nk_status nk_block_jacobi_factor(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                 const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
+                                 const double* w, int64_t ldw, double dt, double* F, int32_t* piv, int64_t ldF,
+                                 nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if ((st = check_precond(m, 1)) != NK_OK) return st;
+    if (!lin || !fT || !fY || !w || !F || !piv) return fail(NK_EINVAL, "lin, fT, fY, w, F and piv must not be NULL");
+    if (ldl < n || ldw < n || ldF < n) return fail(NK_EINVAL, "ldl, ldw and ldF must be >= n=%lld", (long long)n);
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(NK_EINVAL, "dt must be finite and >= 0");
+    if ((st = check_out({lin, fT, fY, w, F})) != NK_OK) return st;
+    if (reinterpret_cast<uintptr_t>(piv) & 3u) return fail(NK_EALIGN, "piv must be 4-byte aligned");
+    const cudaStream_t s = (cudaStream_t)stream;
+    return launched(nk::launch_precond_setup(m->d, n, ld, T, p, Y, lin, ldl, fT, fY, ld, w, ldw, dt, F, piv, ldF, s),
+                    "block-Jacobi factor kernel launch");
+}
+
+nk_status nk_block_jacobi_apply(const nk_mech* m, int64_t n, const double* F, const int32_t* piv, int64_t ldF,
+                                const double* v, int64_t ldv, double* z, int64_t ldz, nk_stream stream) {
+    if (!m) return fail(NK_EINVAL, "mech is NULL");
+    if (n < 0) return fail(NK_EINVAL, "n=%lld < 0", (long long)n);
+    if (n == 0) return ok();
+    nk_status st = check_precond(m, 1);
+    if (st != NK_OK) return st;
+    if (!F || !piv || !v || !z) return fail(NK_EINVAL, "F, piv, v and z must not be NULL");
+    if (ldF < n || ldv < n || ldz < n) return fail(NK_EINVAL, "ldF, ldv and ldz must be >= n=%lld", (long long)n);
+    if ((st = check_out({F, v, z})) != NK_OK) return st;
+    if (reinterpret_cast<uintptr_t>(piv) & 3u) return fail(NK_EALIGN, "piv must be 4-byte aligned");
+    return launched(nk::launch_precond_apply(m->d.K + 1, n, F, ldF, piv, ldF, v, ldv, z, ldz, (cudaStream_t)stream),
+                    "block-Jacobi apply kernel launch");
 }
 
 nk_status nk_reactor_step(const nk_mech* m, int64_t n, double* T, const double* p, double* Y, double dt,
@@ -651,7 +753,8 @@ nk_status nk_reactor_step(const nk_mech* m, int64_t n, double* T, const double* 
     if (!(o.rtol >= 0.0) || !(o.atol_T > 0.0) || !(o.atol_Y > 0.0) || !(o.newton_tol > 0.0) || !(o.lin_tol > 0.0) ||
         o.max_newton < 1 || !(dt >= 0.0) || !std::isfinite(dt))
         return fail(NK_EINVAL, "bad reactor options (tolerances > 0, max_newton >= 1, finite dt >= 0)");
-    const size_t need = nk::reactor_workspace_bytes(m->d, n, o.krylov_dim);
+    if ((st = check_precond(m, o.precond)) != NK_OK) return st;
+    const size_t need = nk::reactor_workspace_bytes(m->d, n, o.krylov_dim, o.precond);
     if (!workspace || workspace_bytes < need)
         return fail(NK_EINVAL, "the reactor step needs %zu bytes of workspace, got %zu", need,
                     workspace ? workspace_bytes : (size_t)0);

@@ -15,6 +15,14 @@
 // (weighted RMS norm of d times min(1, contraction rate) below newton_tol).  A cycle that stops
 // short still updates x, and the next Newton iteration restarts GMRES at the new residual.
 //
+// Optional left preconditioning by the per-point blocks P of I - dt W J W^-1 (block Jacobi,
+// k_jac.cu and k_lu.cu), made once per step at x0 from a stored linearization (filled chunk by
+// chunk) and the sources there: GMRES then solves P^-1 A z = P^-1 r and its stopping test
+// measures P^-1 (r - A z), close to the error of the update.  (With stiff chemistry the
+// unpreconditioned residual is dominated by its stiff components -- many orders of magnitude
+// above the update -- so a test on it, as right preconditioning keeps, says little about the
+// update's accuracy.)
+//
 // Vectors of the workspace hold (K+1) rows of n doubles (row 0 = T, rows 1..K = Y_k); the
 // basis m+1 rows of (K+1) n floats.  Reductions go through per-block partial sums added in a
 // fixed order (deterministic).  The host keeps the (m+1) x m Hessenberg matrix and the Givens
@@ -94,7 +102,16 @@ __global__ void unscale_kernel(int64_t N, const float* __restrict__ v, const dou
         u[e] = (double)v[e] / W[e];
 }
 
-// w = v - dt W (J u), then per-block partial sums of <v_q, w> (q < nv) and |w|^2
+// w = A v_j = v_j - dt W (J u), u = v_j / W
+__global__ void form_kernel(int64_t N, const float* __restrict__ vj, const double* __restrict__ Ju,
+                            const double* __restrict__ W, double dt, double* __restrict__ w) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+        w[e] = fma(-dt * W[e], Ju[e], (double)vj[e]);
+}
+
+// FORM: w = A v_j (as form_kernel); else w as given.  Then per-block partial sums of <v_q, w>
+// (q < nv) and |w|^2
+template <bool FORM>
 __global__ void __launch_bounds__(kRedBlk) apply_dots_kernel(int64_t N, const float* __restrict__ V, int64_t vstride,
                                                              int nv, const double* __restrict__ Ju,
                                                              const double* __restrict__ W, double dt,
@@ -105,8 +122,13 @@ __global__ void __launch_bounds__(kRedBlk) apply_dots_kernel(int64_t N, const fl
     for (int q = 0; q < kMaxDots; ++q) acc[q] = 0.0;
     const float* vj = V + (int64_t)(nv - 1) * vstride;         // the vector the operator was applied to
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-        const double we = fma(-dt * W[e], Ju[e], (double)vj[e]);
-        w[e] = we;
+        double we;
+        if constexpr (FORM) {
+            we = fma(-dt * W[e], Ju[e], (double)vj[e]);
+            w[e] = we;
+        } else {
+            we = w[e];
+        }
 #pragma unroll
         for (int q = 0; q < kMaxDots - 1; ++q)
             if (q < nv) acc[q] = fma((double)V[(int64_t)q * vstride + e], we, acc[q]);
@@ -209,7 +231,10 @@ __global__ void __launch_bounds__(kRedBlk) update_kernel(int64_t n, int64_t N, i
 struct Work {
     double *x0, *W, *f, *r, *u, *Ju, *w, *part, *dots;
     float* V;
-    int64_t N, vstride;
+    double* F;                // block factors (precond only)
+    int32_t* piv;             // pivot rows and row exponents of the factors
+    double* lin;              // stored linearization of one chunk of points
+    int64_t N, vstride, nchunk;
     int nred;
 };
 
@@ -222,12 +247,25 @@ int reduction_blocks() {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-size_t work_bytes(int64_t N, int m, int nred) {
-    return 7 * align256((size_t)N * sizeof(double)) + align256((size_t)(m + 1) * N * sizeof(float)) +
-           align256((size_t)nred * kMaxDots * sizeof(double)) + align256(kMaxDots * sizeof(double));
+// points per chunk of the stored linearization (about 2 GB, whole warps)
+int64_t lin_chunk(const DevMech& mech, int64_t n) {
+    const int64_t per = lin_slots(mech) * (int64_t)sizeof(double);
+    const int64_t c = std::max<int64_t>(128, ((int64_t(2) << 30) / per) / 128 * 128);
+    return std::min(n, c);
 }
 
-Work carve(void* ws, int64_t N, int m, int nred) {
+size_t work_bytes(const DevMech& mech, int64_t n, int m, int nred, int precond) {
+    const int64_t N = (int64_t)(mech.K + 1) * n;
+    size_t b = 7 * align256((size_t)N * sizeof(double)) + align256((size_t)(m + 1) * N * sizeof(float)) +
+               align256((size_t)nred * kMaxDots * sizeof(double)) + align256(kMaxDots * sizeof(double));
+    if (precond)
+        b += align256((size_t)(mech.K + 1) * N * sizeof(double)) + align256((size_t)N * sizeof(int32_t)) +
+             align256((size_t)lin_slots(mech) * lin_chunk(mech, n) * sizeof(double));
+    return b;
+}
+
+Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precond) {
+    const int64_t N = (int64_t)(mech.K + 1) * n;
     Work w;
     char* b = static_cast<char*>(ws);
     auto take = [&](size_t bytes) {
@@ -246,6 +284,16 @@ Work carve(void* ws, int64_t N, int m, int nred) {
     w.V = reinterpret_cast<float*>(take((size_t)(m + 1) * N * sizeof(float)));
     w.part = reinterpret_cast<double*>(take((size_t)nred * kMaxDots * sizeof(double)));
     w.dots = reinterpret_cast<double*>(take(kMaxDots * sizeof(double)));
+    w.F = nullptr;
+    w.piv = nullptr;
+    w.lin = nullptr;
+    w.nchunk = 0;
+    if (precond) {
+        w.F = reinterpret_cast<double*>(take((size_t)(mech.K + 1) * N * sizeof(double)));
+        w.piv = reinterpret_cast<int32_t*>(take((size_t)N * sizeof(int32_t)));
+        w.nchunk = lin_chunk(mech, n);
+        w.lin = reinterpret_cast<double*>(take((size_t)lin_slots(mech) * w.nchunk * sizeof(double)));
+    }
     w.N = N;
     w.vstride = N;
     w.nred = nred;
@@ -254,9 +302,9 @@ Work carve(void* ws, int64_t N, int m, int nred) {
 
 }  // namespace
 
-size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim) {
+size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim, int precond) {
     // (the reduction-block count depends on the device's SM count)
-    return work_bytes((int64_t)(m.K + 1) * n, krylov_dim, reduction_blocks());
+    return work_bytes(m, n, krylov_dim, reduction_blocks(), precond);
 }
 
 // One implicit Euler step (contiguous state: Y rows of stride n).  Returns cudaSuccess and
@@ -268,7 +316,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
     const int64_t N = (int64_t)(K + 1) * n;
     const int mk = o.krylov_dim;
     const int nred = reduction_blocks();
-    Work w = carve(ws, N, mk, nred);
+    Work w = carve(m, ws, n, mk, nred, o.precond);
     const int eg = (int)std::min<int64_t>((N + kElemBlk - 1) / kElemBlk, (int64_t)nred * 8);
     cudaError_t e;
     std::vector<double> hbuf(kMaxDots);
@@ -297,18 +345,49 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
             st.converged = beta == 0.0;
             return cudaSuccess;
         }
-        // GMRES: A z = r with A z = z - dt W J (z / W); one cycle of at most m iterations
-        start_kernel<<<eg, kElemBlk, 0, s>>>(N, w.r, 1.0 / beta, w.V);
+        if (o.precond && it == 0) {                // blocks of I - dt W J W^-1 at x0, factored
+            for (int64_t c0 = 0; c0 < n; c0 += w.nchunk) {
+                const int64_t nc = std::min(w.nchunk, n - c0);
+                if ((e = launch_linearize(m, nc, ld, T + c0, p + c0, Y + c0, nullptr, w.lin, nc, s)) != cudaSuccess)
+                    return e;
+                if ((e = launch_precond_setup(m, nc, ld, T + c0, p + c0, Y + c0, w.lin, nc, w.f + c0, w.f + n + c0,
+                                              n, w.W + c0, n, dt, w.F + c0, w.piv + c0, n, s)) != cudaSuccess)
+                    return e;
+            }
+        }
+        // GMRES: A z = r with A z = z - dt W J (z / W) (preconditioned: P^-1 A z = P^-1 r); one
+        // cycle of at most m iterations
+        double beta_lin = beta;                    // norm of the (preconditioned) initial residual
+        if (o.precond) {
+            if ((e = launch_precond_apply(K + 1, n, w.F, n, w.piv, n, w.r, n, w.r, n, s)) != cudaSuccess) return e;
+            orth_kernel<<<nred, kRedBlk, 0, s>>>(N, w.V, w.vstride, 0, w.dots, w.r, w.part);   // |P^-1 r|^2
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = fetch(1, 1, w.dots + kMaxDots - 1, hbuf.data())) != cudaSuccess) return e;
+            beta_lin = std::sqrt(hbuf[0]);
+            if (!(beta_lin > 0.0)) {               // the preconditioned residual vanished
+                st.converged = beta_lin == 0.0;
+                return cudaSuccess;
+            }
+        }
+        start_kernel<<<eg, kElemBlk, 0, s>>>(N, w.r, 1.0 / beta_lin, w.V);
         std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
+        g[0] = beta_lin;
         int j = 0;
         bool solved = false;                       // GMRES met lin_tol (or broke down exactly)
         while (j < mk) {
-            unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, w.V + (int64_t)j * w.vstride, w.W, w.u);
+            const float* vj = w.V + (int64_t)j * w.vstride;
+            unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.W, w.u);
             if ((e = launch_jvp(m, n, ld, T, p, Y, nullptr, w.u, w.u + n, nullptr, nullptr, w.Ju + n, w.Ju, s, 1)) !=
                 cudaSuccess)
                 return e;
-            apply_dots_kernel<<<nred, kRedBlk, 0, s>>>(N, w.V, w.vstride, j + 1, w.Ju, w.W, dt, w.w, w.part);
+            if (o.precond) {                          // w = P^-1 A v_j
+                form_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.Ju, w.W, dt, w.w);
+                if ((e = launch_precond_apply(K + 1, n, w.F, n, w.piv, n, w.w, n, w.w, n, s)) != cudaSuccess)
+                    return e;
+                apply_dots_kernel<false><<<nred, kRedBlk, 0, s>>>(N, w.V, w.vstride, j + 1, w.Ju, w.W, dt, w.w, w.part);
+            } else {
+                apply_dots_kernel<true><<<nred, kRedBlk, 0, s>>>(N, w.V, w.vstride, j + 1, w.Ju, w.W, dt, w.w, w.part);
+            }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if ((e = fetch(kMaxDots, j + 2, w.dots, hbuf.data())) != cudaSuccess) return e;
             ++st.krylov_iters;
@@ -344,7 +423,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
             ++j;
-            if (std::fabs(g[j]) <= o.lin_tol * beta) {    // relative to this iteration's residual
+            if (std::fabs(g[j]) <= o.lin_tol * beta_lin) {    // relative to this iteration's residual
                 solved = true;
                 break;
             }

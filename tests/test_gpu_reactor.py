@@ -78,3 +78,65 @@ def test_reactor_step_edge_cases(cuda):
         _step(m, Tt, pt, Yt, -1.0)
     # workspace size grows with the Krylov dimension
     assert nk.reactor_workspace(m, 64, 30) > nk.reactor_workspace(m, 64, 5) > 0
+
+
+def _perturbed_equilibrium(mech, n, seed, pert=0.3):
+    """Equilibria with log-normal perturbations of pert in the mass fractions and 30 pert K in
+    T: with the 9-species mechanism the step then relaxes active chemistry (the weighted change
+    over 1e-3 s is O(0.1))."""
+    rng = np.random.default_rng(seed)
+    T = rng.uniform(1300.0, 2600.0, n)
+    p = np.full(n, P_ATM)
+    Y = np.stack([equilibrium_state(mech, T[i], p[i], rng) for i in range(n)], axis=1)
+    Y = Y * np.exp(pert * rng.standard_normal(Y.shape))
+    Y /= Y.sum(0)
+    T = T + 30.0 * pert * rng.standard_normal(n)
+    return T, p, np.ascontiguousarray(Y)
+
+
+# With the per-point block-Jacobi preconditioner the Krylov solve no longer has to resolve the
+# stiff modes itself: large steps converge within a few iterations per Newton iteration.
+@pytest.mark.parametrize("name,n,dt", [("h2_9sp_21rx", 600, 1e-9), ("h2_9sp_21rx", 600, 1e-6),
+                                       ("h2_9sp_21rx", 600, 1e-4), ("h2_9sp_21rx", 600, 1e-3),
+                                       ("ch4_53sp_325rx", 160, 1e-5), ("ch4_53sp_325rx", 160, 1e-3),
+                                       ("big_120sp_700rx", 40, 1e-5)])
+def test_preconditioned_step_vs_dense_newton(cuda, name, n, dt):
+    mech = synth.mechanism(name)
+    m = gpu_mechanism(name)
+    T, p, Y = _perturbed_equilibrium(mech, n, seed=29)
+    rtol, atolT, atolY = 1e-6, 1e-6, 1e-12
+    T1, Y1, st = _step(m, *to_dev(T, p, Y), dt, rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4,
+                       lin_tol=1e-6, max_newton=30, krylov_dim=10, precond=1)
+    assert st["converged"] == 1, st
+    T_o, Y_o, it = oracle.reactor_step(mech, T, p, Y, dt, atol_T=atolT, atol_Y=atolY)
+    assert np.all(it > 0)
+    wT = 1.0 / (rtol * np.abs(T) + atolT)
+    wY = 1.0 / (rtol * np.abs(Y) + atolY)
+    d = np.concatenate([((host(T1) - T_o) * wT)[None], (host(Y1) - Y_o) * wY])
+    wrms = np.sqrt(np.mean(d ** 2))
+    change = np.sqrt(np.mean(np.concatenate([((T_o - T) * wT)[None], (Y_o - Y) * wY]) ** 2))
+    print(f"\n{name} dt={dt:g}: newton {st['newton_iters']}, krylov {st['krylov_iters']}, "
+          f"step change {change:.2e}, wrms diff {wrms:.2e}")
+    assert wrms <= 1e-3
+    assert st["krylov_iters"] <= 10 * st["newton_iters"]
+
+
+def test_preconditioned_and_plain_solves_agree(cuda):
+    """Where both converge (small steps) the two solves reach the same solution."""
+    mech = synth.mechanism("h2_9sp_21rx")
+    m = gpu_mechanism("h2_9sp_21rx")
+    T, p, Y = _perturbed_equilibrium(mech, 300, seed=31)
+    kw = dict(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-5, lin_tol=1e-7, max_newton=30, krylov_dim=30)
+    Ta, Ya, sa = _step(m, *to_dev(T, p, Y), 1e-9, **kw)
+    Tb, Yb, sb = _step(m, *to_dev(T, p, Y), 1e-9, precond=1, **kw)
+    assert sa["converged"] == 1 and sb["converged"] == 1
+    wY = 1.0 / (1e-6 * np.abs(Y) + 1e-12)
+    assert np.sqrt(np.mean(((host(Ya) - host(Yb)) * wY) ** 2)) <= 1e-3
+    assert np.sqrt(np.mean(((host(Ta) - host(Tb)) / (1e-6 * T + 1e-6)) ** 2)) <= 1e-3
+
+
+def test_preconditioned_workspace_and_limits(cuda):
+    m = gpu_mechanism("h2_9sp_21rx")
+    assert nk.reactor_workspace(m, 64, 10, 1) > nk.reactor_workspace(m, 64, 10, 0)
+    with pytest.raises(nk.NkError):
+        nk.reactor_workspace(m, 64, 10, 2)
