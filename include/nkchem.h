@@ -256,7 +256,7 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
  *   fT[n], fY[K*ld]       the sources at (T, p, Y)
  *   J[(K+1)*(K+1)*ldJ]    out: entry (r, c) of point i at J[(r (K+1) + c) ldJ + i]; r, c = 0 for T,
  *                         k + 1 for Y_k (row = source, column = variable); ldJ >= n
- * Double precision.
+ * Double precision; K + 1 <= 160 (a point's block is assembled in shared memory).
  */
 nk_status nk_rhs_jacobian(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
                           const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
@@ -303,7 +303,10 @@ nk_status nk_block_jacobi_apply(const nk_mech* mech, int64_t n, const double* F,
  * With precond = 1 the solve is left-preconditioned by the per-point blocks of
  * nk_block_jacobi_factor, made once per step at x0: GMRES minimises P^-1 (r - A z), which
  * tracks the error of the update (the unpreconditioned residual of stiff chemistry is dominated
- * by its stiff components), and lin_tol applies to it.
+ * by its stiff components), and lin_tol applies to it.  precond = 2 reuses the factors left in
+ * the workspace by the last call with precond 1 (same mechanism, n and workspace), as a stiff
+ * ODE solver keeps its Newton matrix over several steps; the caller refreshes them (precond 1)
+ * when the state or dt has moved far.
  * The call returns when the step is done (it reads a few scalars back per GMRES iteration);
  * non-convergence is reported in stats, not as an error.
  */
@@ -319,7 +322,8 @@ typedef struct {
                              (or after krylov_dim iterations; the partial solution is used) */
     int32_t max_newton;   /* Newton iterations at most */
     int32_t krylov_dim;   /* GMRES iterations per Newton iteration, 1..NK_REACTOR_MAX_KRYLOV */
-    int32_t precond;      /* 0: none (the paper's stage); 1: per-point block Jacobi (K + 1 <= 160) */
+    int32_t precond;      /* 0: none (the paper's stage); 1: per-point block Jacobi made at x0;
+                             2: block Jacobi from the factors of an earlier call (K + 1 <= 160) */
 } nk_reactor_opts;
 typedef struct {
     int32_t converged;    /* 1 when the update test was met (0: max_newton reached, or the

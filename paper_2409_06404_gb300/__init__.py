@@ -328,8 +328,8 @@ def diffusion_fluxes(m: Mechanism, T, p, Y, Dmix, gradX, want_vc=True, want_hf=T
 
 def reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-14, newton_tol=0.1, lin_tol=1e-3, max_newton=10,
                  krylov_dim=20, precond=0) -> _ReactorOpts:
-    """Options of nk_reactor_step (weighted RMS tolerances; precond 1 = per-point block Jacobi;
-    see include/nkchem.h)."""
+    """Options of nk_reactor_step (weighted RMS tolerances; precond 1 = per-point block Jacobi
+    made at x0, 2 = its factors from the last call reused; see include/nkchem.h)."""
     return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim, precond)
 
 
@@ -347,7 +347,7 @@ def reactor_step(m: Mechanism, T, p, Y, dt: float, opts: _ReactorOpts = None, wo
     if ld != n:
         raise ValueError("reactor_step takes a contiguous Y [K, n]")
     opts = opts or reactor_opts()
-    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30 and opts.precond in (0, 1):
+    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30 and opts.precond in (0, 1, 2):
         workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim, opts.precond), dtype=torch.uint8,
                                 device=T.device)
     st = _ReactorStats()

@@ -1,65 +1,23 @@
-// Per-point block-Jacobi preconditioner of the implicit stage's GMRES solve: LU factors with
-// partial pivoting of the (K+1) x (K+1) block P = I - dt diag(w) J diag(1/w) of every point
-// (k_jac.cu writes P), and their application z = P^-1 v.  Double precision: the blocks of
-// stiff chemistry in the solver's weights are so ill-conditioned that single-precision factors
-// (even of row- and column-equilibrated blocks) missed the solution by orders of magnitude in
-// testing, while double-precision ones stay within tens of per cent -- enough to steer GMRES.
+// Application of the per-point block-Jacobi preconditioner of the implicit stage's GMRES
+// solve: z = P^-1 v from the LU factors that k_jac.cu leaves (double precision: the blocks of
+// stiff chemistry in the solver's weights are so ill-conditioned that single-precision factors,
+// even of row- and column-equilibrated blocks, missed the solution by orders of magnitude in
+// testing, while double-precision ones stay within tens of per cent -- enough to steer GMRES).
 //
-// Storage, entry (r, c) of point i at F[(r N + c) ldF + i] (N = K + 1, all points of one
-// entry contiguous): the factorization reads the row-scaled block D P there (D = diag(2^-e_r),
-// e_r at piv[r ldq + i], both from k_jac.cu) and overwrites it with the factors of D P in pivot
-// order -- row k holds L_k,0..k-1 (unit lower part) and U_k,k..N-1 of the k-th pivot row, with
-// 1/U_kk in place of U_kk -- and piv[k ldq + i] with that row's index (low 16 bits) and its
-// exponent e (high 16 bits, signed): P z = v is then L U z = (D v) in pivot order.
-//
-// Factorization: one warp per point with its block in shared memory (nk_lu.cuh; row stride
-// N + 1), a block of `pts` points loaded and stored entry by entry for all its points at once
-// (pts x 8 bytes contiguous per entry).
-// Application: one thread per point, forward then backward substitution with the vector in
-// shared memory and the factors read once, in order (coalesced across the warp's points).
-// Shared memory bounds the block: N (N + 1) doubles per point, N = K + 1 <= kMaxPrecondN.
+// Storage, entry (r, c) of point i at F[(r N + c) ldF + i] (N = K + 1, all points of one entry
+// contiguous), rows in pivot order: row k holds L_k,0..k-1 (unit lower part) and U_k,k..N-1 of
+// the row-scaled block D P, with 1/U_kk in place of U_kk; piv[k ldq + i] holds that row's
+// original index (low 16 bits) and its exponent e (high 16 bits, signed), D = diag(2^-e).  P z = v
+// is then L U z = (D v) in pivot order.  One thread per point, forward then backward
+// substitution with the vector in shared memory and the factors read once, in order (coalesced
+// across the warp's points).
 #include <algorithm>
 #include <cstdint>
 
-#include "nk_lu.cuh"
+#include "nk_internal.cuh"
 
 namespace nk {
 namespace {
-
-__global__ void lu_kernel(const int N, const int pts, const int64_t n, double* __restrict__ F, const int64_t ldF,
-                          int32_t* __restrict__ piv, const int64_t ldq) {
-    extern __shared__ double sa[];
-    const int S = N + 1;
-    const int64_t NN = (int64_t)N * N;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int64_t i0 = (int64_t)blockIdx.x * pts;
-    const int np = (int)(n - i0 < pts ? n - i0 : pts);         // points of this block
-    int32_t* sperm = reinterpret_cast<int32_t*>(sa + (size_t)pts * N * S);   // [pts][N] pivot rows
-    int32_t* sexp = sperm + (size_t)pts * N;                                  // [pts][N] row exponents
-    for (int64_t f = threadIdx.x; f < NN * np; f += blockDim.x) {
-        const int64_t e = f / np;
-        const int q = (int)(f - e * np);
-        sa[(size_t)q * N * S + (e / N) * S + e % N] = F[e * ldF + i0 + q];
-    }
-    for (int f = threadIdx.x; f < N * np; f += blockDim.x) {
-        const int r = f / np, q = f % np;
-        sexp[q * N + r] = piv[(int64_t)r * ldq + i0 + q];
-    }
-    __syncthreads();
-    if (wp < np) warp_lu(sa + (size_t)wp * N * S, N, S, lane, sperm + wp * N);
-    __syncthreads();
-    for (int64_t f = threadIdx.x; f < NN * np; f += blockDim.x) {
-        const int64_t e = f / np;
-        const int q = (int)(f - e * np);
-        const int k = (int)(e / N), j = (int)(e % N);
-        F[e * ldF + i0 + q] = sa[(size_t)q * N * S + sperm[q * N + k] * S + j];
-    }
-    for (int f = threadIdx.x; f < N * np; f += blockDim.x) {
-        const int k = f / np, q = f % np;
-        const int r = sperm[q * N + k];
-        piv[(int64_t)k * ldq + i0 + q] = (r & 0xffff) | (int32_t)((uint32_t)sexp[q * N + r] << 16);
-    }
-}
 
 constexpr int kApplyBlk = 128;
 
@@ -118,24 +76,7 @@ cudaError_t apply(int N, int64_t n, const double* F, int64_t ldF, const int32_t*
     return cudaGetLastError();
 }
 
-size_t lu_smem(int N, int pts) { return (size_t)pts * N * (N + 1) * sizeof(double) + (size_t)pts * N * 8 + 16; }
-
 }  // namespace
-
-cudaError_t launch_precond_factor(int N, int64_t n, double* F, int64_t ldF, int32_t* piv, int64_t ldq,
-                                  cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    if (N < 1 || N > kMaxPrecondN) return cudaErrorInvalidValue;
-    // points per block: up to 4 (32-byte runs per entry), within the shared-memory limit
-    int pts = 4;
-    while (pts > 1 && lu_smem(N, pts) > smem_limit()) --pts;
-    const size_t bytes = lu_smem(N, pts);
-    if (bytes > smem_limit()) return cudaErrorInvalidConfiguration;
-    cudaError_t e = ensure_smem((const void*)lu_kernel, bytes);
-    if (e != cudaSuccess) return e;
-    lu_kernel<<<(unsigned)((n + pts - 1) / pts), 32 * pts, bytes, s>>>(N, pts, n, F, ldF, piv, ldq);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_precond_apply(int N, int64_t n, const double* F, int64_t ldF, const int32_t* piv, int64_t ldq,
                                  const double* v, int64_t ldv, double* z, int64_t ldz, cudaStream_t s) {

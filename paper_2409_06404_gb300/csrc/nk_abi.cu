@@ -341,11 +341,11 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     // Jacobian assembly terms (nk_internal.cuh): for every entry a of reaction q (species k,
     // signed coefficient nu), V_k gets nu A_q; G_k,j gets nu B_q,b for every entry b (species j)
     // and, for third-body and Troe reactions, Lam_k gets nu L_q and G_k,j nu (eps_j - 1) L_q for
-    // every listed efficiency.  Terms of one entry in reaction order.
-    std::vector<int32_t> jac_row(K + 1), jac_col, jac_ent{0};
+    // every listed efficiency.  Per row, terms by destination, each destination in reaction order.
+    std::vector<int32_t> jac_row(K + 1);
     std::vector<nk::JacTerm> jac_term;
     {
-        std::map<std::pair<int, int>, std::vector<nk::JacTerm>> ent;
+        std::map<std::pair<int, int>, std::vector<nk::JacTerm>> ent;      // (row, dst) -> terms
         for (int q = 0; q < R; ++q) {
             const nk::RxnRec& x = rxn[q];
             const int32_t sB = R + lin_boff[q], sL = R + lin_nb + (q - R_el);
@@ -353,25 +353,24 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                 const int ia = a < x.nr ? a : nk::kMaxSide + (a - x.nr);
                 const int k = x.sp[ia];
                 const double nu = x.nud[ia];
-                ent[{k, -1}].push_back({nu, q, 0});
+                ent[{k, 0}].push_back({nu, q, 0});
                 for (int b = 0; b < x.nr + x.np; ++b) {
                     const int ib = b < x.nr ? b : nk::kMaxSide + (b - x.nr);
-                    ent[{k, x.sp[ib]}].push_back({nu, sB + b, 0});
+                    ent[{k, x.sp[ib] + 1}].push_back({nu, sB + b, x.sp[ib] + 1});
                 }
                 if (x.type != NK_RXN_ELEMENTARY) {
-                    ent[{k, -2}].push_back({nu, sL, 0});
-                    for (int j = x.eff0; j < x.eff1; ++j) ent[{k, eff_sp[j]}].push_back({nu * eff_m1[j], sL, 0});
+                    ent[{k, K + 1}].push_back({nu, sL, K + 1});
+                    for (int j = x.eff0; j < x.eff1; ++j)
+                        ent[{k, eff_sp[j] + 1}].push_back({nu * eff_m1[j], sL, eff_sp[j] + 1});
                 }
             }
         }
         int row = 0;
         for (const auto& kv : ent) {
-            while (row <= kv.first.first) jac_row[row++] = (int32_t)jac_col.size();
-            jac_col.push_back(kv.first.second);
+            while (row <= kv.first.first) jac_row[row++] = (int32_t)jac_term.size();
             jac_term.insert(jac_term.end(), kv.second.begin(), kv.second.end());
-            jac_ent.push_back((int32_t)jac_term.size());
         }
-        while (row <= K) jac_row[row++] = (int32_t)jac_col.size();
+        while (row <= K) jac_row[row++] = (int32_t)jac_term.size();
     }
     // reaction thermo groups (nk_internal.cuh): net coefficients of each reaction, grouped by
     // the species' T_mid, combined in extended precision
@@ -431,8 +430,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_ndf = L.add(nasa_df.size() * 8), o_rdf = L.add(rxn_df.size() * 16),
                  o_tdf = L.add(troe_df.size() * 16 + 16), o_gdf = L.add(grp_df.size() * 8 + 16),
                  o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16),
-                 o_jr = L.add(jac_row.size() * 4 + 16), o_jc = L.add(jac_col.size() * 4 + 16),
-                 o_je = L.add(jac_ent.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16);
+                 o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -477,8 +475,6 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_gT, grp_Tmid.data(), grp_Tmid.size() * 8);
     put(o_lb, lin_boff.data(), (size_t)R * 4);
     put(o_jr, jac_row.data(), jac_row.size() * 4);
-    put(o_jc, jac_col.data(), jac_col.size() * 4);
-    put(o_je, jac_ent.data(), jac_ent.size() * 4);
     put(o_jt, jac_term.data(), jac_term.size() * sizeof(nk::JacTerm));
 
     int dev = 0;
@@ -550,8 +546,6 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.lin_boff = reinterpret_cast<const int32_t*>(b + o_lb);
     dm.lin_nb = lin_nb;
     dm.jac_row = reinterpret_cast<const int32_t*>(b + o_jr);
-    dm.jac_col = reinterpret_cast<const int32_t*>(b + o_jc);
-    dm.jac_ent = reinterpret_cast<const int32_t*>(b + o_je);
     dm.jac_term = reinterpret_cast<const nk::JacTerm*>(b + o_jt);
     *out = m;
     return ok();
@@ -671,10 +665,9 @@ nk_status nk_diffusion_fluxes(const nk_mech* m, int64_t n, int64_t ld, const dou
 }
 
 nk_status check_precond(const nk_mech* m, int32_t precond) {
-    if (precond != 0 && precond != 1) return fail(NK_EINVAL, "precond=%d is not 0 or 1", precond);
+    if (precond < 0 || precond > 2) return fail(NK_EINVAL, "precond=%d is not 0, 1 or 2", precond);
     if (precond && m->d.K + 1 > nk::kMaxPrecondN)
-        return fail(NK_EUNSUPPORTED, "the block-Jacobi preconditioner takes K + 1 <= %d (K=%d)", nk::kMaxPrecondN,
-                    m->d.K);
+        return fail(NK_EUNSUPPORTED, "dense per-point blocks take K + 1 <= %d (K=%d)", nk::kMaxPrecondN, m->d.K);
     return NK_OK;
 }
 
@@ -696,6 +689,7 @@ nk_status nk_rhs_jacobian(const nk_mech* m, int64_t n, int64_t ld, const double*
     nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
     if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
     if (!lin || !fT || !fY || !J) return fail(NK_EINVAL, "lin, fT, fY and J must not be NULL");
+    if ((st = check_precond(m, 1)) != NK_OK) return st;        // (the same block size limit)
     if (ldl < n || ldJ < n) return fail(NK_EINVAL, "ldl and ldJ must be >= n=%lld", (long long)n);
     if ((st = check_out({lin, fT, fY, J})) != NK_OK) return st;
     return launched(nk::launch_rhs_jacobian(m->d, n, ld, T, p, Y, lin, ldl, fT, fY, J, ldJ, (cudaStream_t)stream),

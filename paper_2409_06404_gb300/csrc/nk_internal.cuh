@@ -82,12 +82,13 @@ constexpr int kNasaStride = 16;   // per range; species k: [k][2][16] (low, high
 constexpr int kGrpPairs = 18;
 
 // One term of the dense Jacobian assembly from a stored linearization (k_jac.cu): coefficient
-// times stored slot.  Entry (k, j) of G_kj = sum_r nu_kr (B_rj + L_r (eps_rj - 1)) (the
-// concentration Jacobian of omega_k at fixed T, with [M] = p/(RT) + sum_j (eps_j - 1) C_j), and
-// the row sums V_k = sum_r nu_kr A_r, Lam_k = sum_r nu_kr L_r, are each a list of such terms.
+// times stored slot, added to position dst of the row.  Entry (k, j) of
+// G_kj = sum_r nu_kr (B_rj + L_r (eps_rj - 1)) (the concentration Jacobian of omega_k at fixed
+// T, with [M] = p/(RT) + sum_j (eps_j - 1) C_j) goes to dst = j + 1, the row sums
+// V_k = sum_r nu_kr A_r to dst = 0 and Lam_k = sum_r nu_kr L_r to dst = K + 1.
 struct __align__(16) JacTerm {
     double coef;
-    int32_t slot, pad;
+    int32_t slot, dst;
 };
 
 // Device view of a loaded mechanism (passed by value to every kernel).
@@ -140,12 +141,9 @@ struct DevMech {
     const double* grp_Tmid;       // [groups] the group's T_mid
     const int32_t* lin_boff;      // [R] first entry slot of each reaction in a stored linearization
     int32_t lin_nb;               // entry slots of all reactions (sum of nr + np)
-    // Jacobian assembly: species row k has entries [jac_row[k], jac_row[k+1]); entry e is column
-    // jac_col[e] (a species j >= 0, or -1 for V_k, -2 for Lam_k) with the terms
-    // [jac_ent[e], jac_ent[e+1]) of jac_term
+    // Jacobian assembly: species row k has the terms [jac_row[k], jac_row[k+1]) of jac_term,
+    // grouped by destination in increasing order, each group in reaction order
     const int32_t* jac_row;       // [K+1]
-    const int32_t* jac_col;       // [entries]
-    const int32_t* jac_ent;       // [entries+1]
     const JacTerm* jac_term;      // [terms]
 };
 
@@ -193,18 +191,10 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
 cudaError_t launch_rhs_jacobian(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                                 const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
                                 double* J, int64_t ldJ, cudaStream_t s);
-// Block-Jacobi preconditioner (k_jac.cu, k_lu.cu): blocks P = I - dt diag(w) J diag(1/w) with
-// power-of-two row scales (exponents to piv), their LU factors in place (pivot rows and
-// exponents to piv), and z = P^-1 v (z may alias v).  N = K + 1 <= kMaxPrecondN.
+// Block-Jacobi preconditioner (k_jac.cu, k_lu.cu): the blocks P = I - dt diag(w) J diag(1/w)
+// with power-of-two row scales, factored (pivot rows and row exponents to piv), and z = P^-1 v
+// (z may alias v).  N = K + 1 <= kMaxPrecondN (one block must fit in shared memory).
 constexpr int kMaxPrecondN = 160;
-cudaError_t launch_precond_blocks(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
-                                  const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
-                                  int64_t ldf, const double* w, int64_t ldw, double dt, double* P, int32_t* piv,
-                                  int64_t ldP, cudaStream_t s);
-cudaError_t launch_precond_factor(int N, int64_t n, double* F, int64_t ldF, int32_t* piv, int64_t ldq,
-                                  cudaStream_t s);
-// blocks and factors in one pass (one kernel when a point's linearization and block fit in
-// shared memory, else the two above)
 cudaError_t launch_precond_setup(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                                  const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
                                  int64_t ldf, const double* w, int64_t ldw, double dt, double* F, int32_t* piv,

@@ -17,7 +17,8 @@
 //
 // Optional left preconditioning by the per-point blocks P of I - dt W J W^-1 (block Jacobi,
 // k_jac.cu and k_lu.cu), made once per step at x0 from a stored linearization (filled chunk by
-// chunk) and the sources there: GMRES then solves P^-1 A z = P^-1 r and its stopping test
+// chunk) and the sources there, or kept from an earlier call (as a stiff ODE solver reuses its
+// Newton matrix over steps): GMRES then solves P^-1 A z = P^-1 r and its stopping test
 // measures P^-1 (r - A z), close to the error of the update.  (With stiff chemistry the
 // unpreconditioned residual is dominated by its stiff components -- many orders of magnitude
 // above the update -- so a test on it, as right preconditioning keeps, says little about the
@@ -345,7 +346,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
             st.converged = beta == 0.0;
             return cudaSuccess;
         }
-        if (o.precond && it == 0) {                // blocks of I - dt W J W^-1 at x0, factored
+        if (o.precond == 1 && it == 0) {           // blocks of I - dt W J W^-1 at x0, factored
             for (int64_t c0 = 0; c0 < n; c0 += w.nchunk) {
                 const int64_t nc = std::min(w.nchunk, n - c0);
                 if ((e = launch_linearize(m, nc, ld, T + c0, p + c0, Y + c0, nullptr, w.lin, nc, s)) != cudaSuccess)

@@ -137,10 +137,9 @@ def test_block_jacobi_argument_errors(cuda):
         nk.block_jacobi_factor(m, Tt, pt, Yt, lin, fT, fY, w, float("nan"))
 
 
-def test_block_jacobi_without_fused_setup(cuda):
-    """A mechanism whose per-point linearization and block do not fit in shared memory together
-    (K = 159): the blocks come from the assembly kernel and the factors from the separate
-    factorization kernel; the same checks as above."""
+def test_largest_supported_block(cuda):
+    """K = 159 (K + 1 = 160, the largest block that fits in shared memory): factors and solve as
+    above, with the blocks from nk_rhs_jacobian; K = 160 is refused."""
     mech = synth.make_mechanism(159, 400, 20, 20, seed=7)
     m = gpu_mechanism(mech)
     N, n, dt = mech.K + 1, 40, 1e-8
@@ -159,9 +158,16 @@ def test_block_jacobi_without_fused_setup(cuda):
     L = np.tril(Fh, -1) + np.eye(N)[None]
     U = np.triu(Fh, 1) + np.eye(N)[None] / np.diagonal(Fh, axis1=1, axis2=2)[:, :, None] * np.eye(N)[None]
     scale = np.abs(L) @ np.abs(U)
-    assert np.all(np.abs(L @ U - Pp) <= 1e-10 * scale + 1e-300)
+    # (P from the Jacobian kernel, the factors from the set-up kernel: the same expressions, so
+    # the entries agree to rounding, except where an entry is a cancellation; the 9-digit
+    # tolerance on |L| |U| covers those)
+    assert np.all(np.abs(L @ U - Pp) <= 1e-9 * scale + 1e-300)
     v = synth.normal((N, n), 92)
     z = host(nk.block_jacobi_apply(m, F, perm, torch.from_numpy(v).cuda()))
     Dv = np.take_along_axis(v.T, ph, axis=1) * np.ldexp(1.0, -ex)
-    r = np.einsum("nrc,nc->nr", Pp, z.T) - Dv
+    r = np.einsum("nrc,nc->nr", L @ U, z.T) - Dv
     assert np.all(np.abs(r) <= 1e-12 * (np.einsum("nrc,nc->nr", scale, np.abs(z.T)) + np.abs(Dv)) + 1e-300)
+    big = synth.make_mechanism(160, 300, 10, 10, seed=8)
+    mb = gpu_mechanism(big)
+    with pytest.raises(nk.NkError):
+        nk.reactor_workspace(mb, 16, 10, 1)

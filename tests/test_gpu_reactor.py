@@ -139,4 +139,22 @@ def test_preconditioned_workspace_and_limits(cuda):
     m = gpu_mechanism("h2_9sp_21rx")
     assert nk.reactor_workspace(m, 64, 10, 1) > nk.reactor_workspace(m, 64, 10, 0)
     with pytest.raises(nk.NkError):
-        nk.reactor_workspace(m, 64, 10, 2)
+        nk.reactor_workspace(m, 64, 10, 3)
+
+
+def test_reused_factors(cuda):
+    """precond = 2 keeps the factors of the previous call: a second step from the same states
+    reaches the same solution without the set-up."""
+    mech = synth.mechanism("h2_9sp_21rx")
+    m = gpu_mechanism("h2_9sp_21rx")
+    T, p, Y = _perturbed_equilibrium(mech, 400, seed=37)
+    kw = dict(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=30, krylov_dim=10)
+    Tt, pt, Yt = to_dev(T, p, Y)
+    ws = torch.empty(nk.reactor_workspace(m, 400, 10, 1), dtype=torch.uint8, device="cuda")
+    Ta, Ya = Tt.clone(), Yt.clone()
+    sa = nk.reactor_step(m, Ta, pt, Ya, 1e-5, nk.reactor_opts(precond=1, **kw), workspace=ws)
+    Tb, Yb = Tt.clone(), Yt.clone()
+    sb = nk.reactor_step(m, Tb, pt, Yb, 1e-5, nk.reactor_opts(precond=2, **kw), workspace=ws)
+    assert sa["converged"] == 1 and sb["converged"] == 1
+    wY = 1.0 / (1e-6 * np.abs(Y) + 1e-12)
+    assert np.sqrt(np.mean(((host(Ya) - host(Yb)) * wY) ** 2)) <= 1e-3
