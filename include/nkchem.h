@@ -59,7 +59,11 @@ typedef enum {
                            equilibrium constants (pairs), forward-minus-reverse difference and
                            omega accumulation in double; transport: fits, mixture rules and
                            sums in single precision (1e-5) */
-    NK_FP64_NATIVE = 2  /* every operation in native double precision (reference form) */
+    NK_FP64_NATIVE = 2, /* every operation in native double precision (reference form) */
+    NK_JIT = 3          /* nk_rates_eval only: NK_FP64_NATIVE's arithmetic in a kernel generated
+                           for the loaded mechanism (straight-line code, the mechanism's data as
+                           literals) and compiled at first use with NVRTC, as the paper generates
+                           its kernels from the mechanism (Sec. 2); see nk_mechanism_jit */
 } nk_precision;
 
 /* Reaction kinds of nk_mech_desc.rtype */
@@ -155,7 +159,7 @@ nk_status nk_thermo_eval(const nk_mech* mech, int64_t n, int64_t ld, const doubl
  *   omega[K*ld]  omega_k = sum_r nu_kr q_r, mol/(m^3 s)
  *   hrr[n]       -sum_k h_k(T) omega_k, W/m^3 (positive when exothermic)
  * dlnA: NULL or device [R] shift added to ln A_r (to both limits of a Troe reaction).
- * precision: NK_FP64, NK_FP64_NATIVE or NK_MIXED.
+ * precision: NK_FP64, NK_FP64_NATIVE, NK_MIXED or NK_JIT.
  */
 nk_status nk_rates_eval(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
                         const double* p, const double* Y, const double* dlnA, double* omega,
@@ -246,6 +250,18 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
                                   const double* p, const double* Y, const double* lin, int64_t ldl,
                                   const double* vT, const double* vY, double* d_omega, double* d_hrr,
                                   nk_stream stream);
+
+/*
+ * The mechanism-specialised rates kernel behind NK_JIT.  nk_mechanism_jit compiles it now
+ * (otherwise the first NK_JIT call does): NVRTC (libnvrtc.so.13, loaded at run time) builds a
+ * cubin for the current device's architecture, which the runtime loads; NK_EUNSUPPORTED with
+ * the compiler's message when NVRTC is missing or the compilation fails.  nk_jit_source writes
+ * the generated CUDA source for a mechanism description (host only, no device needed): *len is
+ * the buffer size on entry and the size needed (with the terminating NUL) on return; the text
+ * is copied when it fits, else NK_EINVAL.
+ */
+nk_status nk_mechanism_jit(nk_mech* mech);
+nk_status nk_jit_source(const nk_mech_desc* desc, char* buf, size_t* len);
 
 /*
  * Dense Jacobian of the sources of nk_rhs_eval with respect to x = (T, Y_0..Y_{K-1}) at fixed p,

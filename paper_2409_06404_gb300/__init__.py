@@ -25,9 +25,9 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libnkchem.so")
 _lock = threading.Lock()
 _lib = None
 
-NK_FP64, NK_MIXED, NK_FP64_NATIVE = 0, 1, 2
-_PRECISION = {"fp64": NK_FP64, "mixed": NK_MIXED, "fp64_native": NK_FP64_NATIVE,
-              NK_FP64: NK_FP64, NK_MIXED: NK_MIXED, NK_FP64_NATIVE: NK_FP64_NATIVE}
+NK_FP64, NK_MIXED, NK_FP64_NATIVE, NK_JIT = 0, 1, 2, 3
+_PRECISION = {"fp64": NK_FP64, "mixed": NK_MIXED, "fp64_native": NK_FP64_NATIVE, "jit": NK_JIT,
+              NK_FP64: NK_FP64, NK_MIXED: NK_MIXED, NK_FP64_NATIVE: NK_FP64_NATIVE, NK_JIT: NK_JIT}
 _STATUS = {0: "NK_OK", 1: "NK_EINVAL", 2: "NK_EALIGN", 3: "NK_ECUDA", 4: "NK_ENOMEM", 5: "NK_EUNSUPPORTED"}
 
 _vp = ctypes.c_void_p
@@ -79,6 +79,8 @@ _SIGS = {
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_diffusion_fluxes": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 8 + [_vp]),
     "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_mechanism_jit": (ctypes.c_int, [_vp]),
+    "nk_jit_source": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_rhs_jacobian": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
     "nk_block_jacobi_factor": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64,
                                               ctypes.c_double, _vp, _vp, _i64, _vp]),
@@ -182,6 +184,22 @@ class Mechanism:
 
 def mechanism_load(mech) -> Mechanism:
     return Mechanism(mech)
+
+
+def mechanism_jit(m: Mechanism) -> None:
+    """nk_mechanism_jit: compile the mechanism-specialised rates kernel (precision "jit") now."""
+    _check(lib().nk_mechanism_jit(m.handle))
+
+
+def jit_source(mech) -> str:
+    """nk_jit_source: the CUDA source the library generates for a mechanism (host only)."""
+    d, keep = _desc_from(mech)
+    n = ctypes.c_size_t(0)
+    lib().nk_jit_source(ctypes.byref(d), None, ctypes.byref(n))     # the size, then the text
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().nk_jit_source(ctypes.byref(d), buf, ctypes.byref(n)))
+    del keep
+    return buf.value.decode()
 
 
 # ------------------------------------------------------------------------------ helpers

@@ -22,7 +22,22 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libnkchem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+GEN = os.path.join(OUT, "gen")
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-I", GEN]
+
+
+def _write_embedded_sources():
+    """The run-time compiled kernel (jit.cu) includes the text of nk_math.cuh: write it as a raw
+    string literal into the build directory."""
+    os.makedirs(GEN, exist_ok=True)
+    with open(os.path.join(CSRC, "nk_math.cuh")) as f:
+        text = f.read()
+    assert ")nkmathsrc" not in text
+    body = 'static const char kNkMathSrc[] = R"nkmathsrc(' + text + ')nkmathsrc";\n'
+    path = os.path.join(GEN, "nk_math_src.inc")
+    if not os.path.exists(path) or open(path).read() != body:
+        with open(path, "w") as f:
+            f.write(body)
 
 
 def nvcc() -> str:
@@ -51,6 +66,7 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
     if not force and not ptxas_verbose and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)
+    _write_embedded_sources()
     cc = nvcc()
     srcs = _sources()
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
@@ -72,7 +88,7 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
     with open(os.path.join(OUT, "build.log"), "w") as f:
         f.write("\n".join(log))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o, _ in results]]
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o, _ in results], "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -496,6 +496,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     m->device = dev;
     m->block = block;
     m->bytes = L.bytes;
+    m->jit_src = nk::jit_source(d);
     unsigned char* b = static_cast<unsigned char*>(block);
     nk::DevMech& dm = m->d;
     dm.K = K;
@@ -553,6 +554,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
 
 nk_status nk_mechanism_free(nk_mech* m) {
     if (!m) return ok();
+    nk::jit_unload(m->jit);
     cudaError_t e = cudaFree(m->block);
     delete m;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -620,16 +622,62 @@ nk_status nk_thermo_eval(const nk_mech* m, int64_t n, int64_t ld, const double* 
                     "thermo kernel launch");
 }
 
+// builds the mechanism-specialised kernel once (the handle caches it; the build is serialised)
+nk_status ensure_jit(nk_mech* m) {
+    std::lock_guard<std::mutex> lk(m->jit_mu);
+    if (m->jit_state == 0) {
+        int dev = -1;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        e = nk::jit_build(m->jit_src, dev, m->jit, m->jit_err);
+        m->jit_state = e == cudaSuccess ? 1 : -1;
+    }
+    if (m->jit_state < 0) return fail(NK_EUNSUPPORTED, "mechanism-specialised kernel: %s", m->jit_err.c_str());
+    return NK_OK;
+}
+
+nk_status nk_mechanism_jit(nk_mech* m) {
+    if (!m) return fail(NK_EINVAL, "mech is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != m->device)
+        return fail(NK_EINVAL, "mechanism lives on device %d but device %d is current", m->device, dev);
+    nk_status st = ensure_jit(m);
+    return st == NK_OK ? ok() : st;
+}
+
+nk_status nk_jit_source(const nk_mech_desc* d, char* buf, size_t* len) {
+    if (!len) return fail(NK_EINVAL, "len must not be NULL");
+    nk_status st = check_mech_desc(d);
+    if (st != NK_OK) return st;
+    const std::string src = nk::jit_source(d);
+    const size_t need = src.size() + 1;
+    const size_t have = *len;
+    *len = need;
+    if (!buf || have < need) return fail(NK_EINVAL, "the source needs %zu bytes", need);
+    std::memcpy(buf, src.c_str(), need);
+    return ok();
+}
+
 nk_status nk_rates_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
                         const double* Y, const double* dlnA, double* omega, double* hrr,
                         nk_precision precision, nk_stream stream) {
     bool skip;
     nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
     if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
-    if (precision != NK_FP64 && precision != NK_MIXED && precision != NK_FP64_NATIVE)
+    if (precision != NK_FP64 && precision != NK_MIXED && precision != NK_FP64_NATIVE && precision != NK_JIT)
         return fail(NK_EINVAL, "bad precision %d", (int)precision);
     if (!omega || !hrr) return fail(NK_EINVAL, "omega and hrr must not be NULL");
     if ((st = check_out({omega, hrr, dlnA})) != NK_OK) return st;
+    if (precision == NK_JIT) {
+        // (the handle is logically const: the compiled kernel is a cache of its source)
+        nk_mech* mm = const_cast<nk_mech*>(m);
+        if ((st = ensure_jit(mm)) != NK_OK) return st;
+        return launched(nk::jit_launch_rates(mm->jit, m->d, m->device, n, ld, T, p, Y, dlnA, omega, hrr,
+                                             (cudaStream_t)stream),
+                        "specialised rates kernel launch");
+    }
     return launched(nk::launch_rates(m->d, n, ld, T, p, Y, dlnA, omega, hrr, (int)precision, (cudaStream_t)stream),
                     "rates kernel launch");
 }

@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <string>
+
 #include "nkchem.h"
 #include "nk_math.cuh"
 #include "nk_df.cuh"
@@ -152,12 +155,26 @@ constexpr double kLnT0 = 7.0;
 
 }  // namespace nk
 
+namespace nk {
+// A run-time compiled, mechanism-specialised kernel (jit.cu).
+struct JitModule {
+    void* lib = nullptr;    // cudaLibrary_t
+    void* kern = nullptr;   // cudaKernel_t
+};
+}  // namespace nk
+
 // The opaque handle of the public ABI.
 struct nk_mech {
     nk::DevMech d;
     int device;
     void* block;        // single device allocation holding every table
     size_t bytes;
+    // the mechanism-specialised rates kernel: source written at load, compiled at first use
+    std::string jit_src;
+    nk::JitModule jit;
+    int jit_state = 0;  // 0 not built, 1 built, -1 failed (jit_err says why)
+    std::string jit_err;
+    std::mutex jit_mu;
 };
 
 namespace nk {
@@ -204,6 +221,14 @@ cudaError_t launch_precond_apply(int N, int64_t n, const double* F, int64_t ldF,
 cudaError_t launch_diffusion(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* D, const double* gradX, double* j, double* Vc,
                              double* hf, cudaStream_t s);
+// Mechanism-specialised rates kernel (jit.cu): source from the host description, NVRTC
+// compilation and loading, launch (all-double form, results as nk_rates_eval's).
+std::string jit_source(const nk_mech_desc* d);
+cudaError_t jit_build(const std::string& src, int device, JitModule& mod, std::string& why);
+void jit_unload(JitModule& mod);
+cudaError_t jit_launch_rates(const JitModule& mod, const DevMech& m, int device, int64_t n, int64_t ld,
+                             const double* T, const double* p, const double* Y, const double* dlnA, double* omega,
+                             double* hrr, cudaStream_t s);
 // Stored linearization of the rates (k_lin.cu): per-point slots, see lin_slots().
 int64_t lin_slots(const DevMech& m);
 cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,

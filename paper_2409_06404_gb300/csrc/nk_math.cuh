@@ -20,7 +20,9 @@
 // memory by stage_math_tables().
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 namespace nk {
 
