@@ -21,20 +21,22 @@ namespace {
 
 constexpr int kApplyBlk = 128;
 
-// sum_{j0 <= j < j1} f[j ldF] y[j]: eight independent partial sums, so that eight factor loads
-// per thread are in flight (the loads, not the arithmetic, bound the substitutions)
+// sum_{j0 <= j < j1} f[j ldF] y[j]: four independent partial sums, so that four factor loads
+// per thread are in flight (the loads, not the arithmetic, bound the substitutions; eight
+// measured slower)
 __device__ __forceinline__ double dot_run(const double* __restrict__ f, int64_t ldF, const double* y, int j0, int j1) {
-    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int j = j0;
-    for (; j + 7 < j1; j += 8) {
-        double fv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) fv[u] = f[(int64_t)(j + u) * ldF];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s[u] = fma(fv[u], y[(j + u) * kApplyBlk], s[u]);
+    for (; j + 3 < j1; j += 4) {
+        const double f0 = f[(int64_t)j * ldF], f1 = f[(int64_t)(j + 1) * ldF], f2 = f[(int64_t)(j + 2) * ldF],
+                     f3 = f[(int64_t)(j + 3) * ldF];
+        s0 = fma(f0, y[j * kApplyBlk], s0);
+        s1 = fma(f1, y[(j + 1) * kApplyBlk], s1);
+        s2 = fma(f2, y[(j + 2) * kApplyBlk], s2);
+        s3 = fma(f3, y[(j + 3) * kApplyBlk], s3);
     }
-    for (; j < j1; ++j) s[0] = fma(f[(int64_t)j * ldF], y[j * kApplyBlk], s[0]);
-    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    for (; j < j1; ++j) s0 = fma(f[(int64_t)j * ldF], y[j * kApplyBlk], s0);
+    return (s0 + s1) + (s2 + s3);
 }
 
 // z = P^-1 v per point: v and z rows of ldv / ldz (row r of point i at r ld + i), of type TI and
