@@ -252,6 +252,24 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
                                   nk_stream stream);
 
 /*
+ * Rates (nk_rates_eval) and transport (nk_transport_eval) of fields that live in host memory,
+ * the library's end-to-end entry: the points are cut into chunks of `chunk`, each copied to
+ * the device, evaluated and copied back, the chunks cycling over three internal streams so that
+ * both copy directions overlap the kernels.
+ *   T[n], p[n], Y[K*n]                       host, contiguous SoA (species rows of n)
+ *   omega[K*n], hrr[n], mu[n], lambda[n], Dmix[K*n]   host outputs, any may be NULL
+ *   workspace   device, nk_host_eval_workspace(mech, min(chunk, n)) bytes
+ * Page-locked host memory makes the copies asynchronous.  The caller's stream is ordered
+ * before and after the evaluation; the call returns when the outputs are in host memory.
+ * precision: NK_FP64, NK_FP64_NATIVE or NK_MIXED (both kernels).
+ */
+nk_status nk_host_eval_workspace(const nk_mech* mech, int64_t chunk, size_t* bytes);
+nk_status nk_host_eval(const nk_mech* mech, int64_t n, const double* T, const double* p, const double* Y,
+                       double* omega, double* hrr, double* mu, double* lambda, double* Dmix,
+                       nk_precision precision, int64_t chunk, void* workspace, size_t workspace_bytes,
+                       nk_stream stream);
+
+/*
  * The mechanism-specialised rates kernel behind NK_JIT.  nk_mechanism_jit compiles it now
  * (otherwise the first NK_JIT call does): NVRTC (libnvrtc.so.13, loaded at run time) builds a
  * cubin for the current device's architecture, which the runtime loads; NK_EUNSUPPORTED with

@@ -80,6 +80,8 @@ _SIGS = {
     "nk_diffusion_fluxes": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 8 + [_vp]),
     "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_mechanism_jit": (ctypes.c_int, [_vp]),
+    "nk_host_eval_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_host_eval": (ctypes.c_int, [_vp, _i64] + [_vp] * 8 + [ctypes.c_int, _i64, _vp, ctypes.c_size_t, _vp]),
     "nk_jit_source": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_rhs_jacobian": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
     "nk_block_jacobi_factor": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64,
@@ -296,6 +298,35 @@ def rates_eval(m: Mechanism, T, p, Y, dlnA=None, precision="fp64", omega=None, h
     _check(lib().nk_rates_eval(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(dlnA), _ptr(omega), _ptr(hrr),
                                _PRECISION[precision], _stream(stream)))
     return omega, hrr
+
+
+def host_eval_workspace(m: Mechanism, chunk: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().nk_host_eval_workspace(m.handle, int(chunk), ctypes.byref(b)))
+    return b.value
+
+
+def host_eval(m: Mechanism, T, p, Y, precision="fp64", chunk=65536, workspace=None, outputs=None, stream=None):
+    """nk_host_eval: rates and transport of host-resident CPU tensors (float64, contiguous; T, p [n],
+    Y [K, n]), chunked over streams.  Returns the host outputs (omega, hrr, mu, lambda, Dmix);
+    pass page-locked tensors (and preallocated ``outputs``) for asynchronous copies."""
+    import torch
+    for name, t in (("T", T), ("p", p), ("Y", Y)):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous host float64 tensor")
+    n = T.shape[0]
+    if p.shape != (n,) or Y.shape != (m.K, n):
+        raise ValueError("T, p must be [n] and Y [K, n]")
+    if outputs is None:
+        pin = T.is_pinned()
+        mk = (lambda *s: torch.empty(*s, dtype=torch.float64, pin_memory=pin))
+        outputs = (mk(m.K, n), mk(n), mk(n), mk(n), mk(m.K, n))
+    if workspace is None and n > 0:
+        workspace = torch.empty(host_eval_workspace(m, min(chunk, n)), dtype=torch.uint8, device="cuda")
+    _check(lib().nk_host_eval(m.handle, n, _ptr(T), _ptr(p), _ptr(Y), *[_ptr(o) for o in outputs],
+                              _PRECISION[precision], int(chunk), _ptr(workspace),
+                              0 if workspace is None else workspace.numel(), _stream(stream)))
+    return outputs
 
 
 def transport_eval(m: Mechanism, T, p, Y, precision="fp64", mu=None, lam=None, Dmix=None, stream=None):

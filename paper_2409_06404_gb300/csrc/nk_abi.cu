@@ -682,6 +682,41 @@ nk_status nk_rates_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T
                     "rates kernel launch");
 }
 
+nk_status nk_host_eval_workspace(const nk_mech* m, int64_t chunk, size_t* bytes) {
+    if (!m || !bytes) return fail(NK_EINVAL, "mech and bytes must not be NULL");
+    if (chunk < 1) return fail(NK_EINVAL, "chunk=%lld < 1", (long long)chunk);
+    *bytes = nk::host_eval_workspace_bytes(m->d, chunk);
+    return ok();
+}
+
+nk_status nk_host_eval(const nk_mech* m, int64_t n, const double* T, const double* p, const double* Y,
+                       double* omega, double* hrr, double* mu, double* lambda, double* Dmix, nk_precision precision,
+                       int64_t chunk, void* workspace, size_t workspace_bytes, nk_stream stream) {
+    if (!m) return fail(NK_EINVAL, "mech is NULL");
+    if (n < 0) return fail(NK_EINVAL, "n=%lld < 0", (long long)n);
+    if (n == 0) return ok();
+    if (!T || !p || !Y) return fail(NK_EINVAL, "T, p and Y must not be NULL");
+    if (precision != NK_FP64 && precision != NK_MIXED && precision != NK_FP64_NATIVE)
+        return fail(NK_EINVAL, "bad precision %d", (int)precision);
+    if (chunk < 1) return fail(NK_EINVAL, "chunk=%lld < 1", (long long)chunk);
+    if (misaligned(T) || misaligned(p) || misaligned(Y)) return fail(NK_EALIGN, "T, p, Y must be 8-byte aligned");
+    nk_status st = check_out({omega, hrr, mu, lambda, Dmix, workspace});
+    if (st != NK_OK) return st;
+    const int64_t c = std::min(chunk, n);
+    const size_t need = nk::host_eval_workspace_bytes(m->d, c);
+    if (!workspace || workspace_bytes < need)
+        return fail(NK_EINVAL, "nk_host_eval needs %zu bytes of workspace for chunks of %lld, got %zu", need,
+                    (long long)c, workspace ? workspace_bytes : (size_t)0);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != m->device)
+        return fail(NK_EINVAL, "mechanism lives on device %d but device %d is current", m->device, dev);
+    return launched(nk::host_eval(m->d, n, T, p, Y, omega, hrr, mu, lambda, Dmix, (int)precision, c, workspace,
+                                  (cudaStream_t)stream),
+                    "host evaluation");
+}
+
 nk_status nk_transport_eval(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
                             const double* Y, double* mu, double* lambda, double* Dmix,
                             nk_precision precision, nk_stream stream) {

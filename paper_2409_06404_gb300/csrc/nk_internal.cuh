@@ -221,6 +221,11 @@ cudaError_t launch_precond_apply(int N, int64_t n, const double* F, int64_t ldF,
 cudaError_t launch_diffusion(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* D, const double* gradX, double* j, double* Vc,
                              double* hf, cudaStream_t s);
+// Rates and transport of host-resident fields, chunked over streams (host_eval.cu).
+size_t host_eval_workspace_bytes(const DevMech& m, int64_t chunk);
+cudaError_t host_eval(const DevMech& m, int64_t n, const double* T, const double* p, const double* Y, double* omega,
+                      double* hrr, double* mu, double* lam, double* Dmix, int precision, int64_t chunk, void* ws,
+                      cudaStream_t caller);
 // Mechanism-specialised rates kernel (jit.cu): source from the host description, NVRTC
 // compilation and loading, launch (all-double form, results as nk_rates_eval's).
 std::string jit_source(const nk_mech_desc* d);
