@@ -5,7 +5,8 @@ against the oracle:
   the mixed form's error per output (maximum and 99.9th percentile);
 * the implicit-stage workload: 53 species on 32^3 elements x 512 points = 16,777,216 points,
   one mixed forward (thermo, rates, transport) and ten JVPs along seeded N(0, 1) directions,
-  as a Newton-Krylov stage issues them, rates of progress recomputed for each.
+  as a Newton-Krylov stage issues them, rates of progress recomputed for each;
+* the reactor step on 2,097,152 near-equilibrium points, unpreconditioned and block-Jacobi.
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ import torch
 import oracle
 import paper_2409_06404_gb300 as nk
 from paper_2409_06404_gb300 import synth
-from conftest import gpu_mechanism, to_dev, host, scaled_err
+from conftest import gpu_mechanism, to_dev, host, scaled_err, P_ATM
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 TOL64 = 1e-10
@@ -109,3 +110,43 @@ def test_implicit_stage_16M_points_sampled(cuda):
             assert scaled_err(host(dh[sub]), dh_o, dhs) <= TOL64, d
         assert torch.isfinite(dh).all()
         del dw, dh
+
+
+def test_reactor_step_full_size_sampled(cuda):
+    """The reactor step at the benchmark's size (2,097,152 points, 53 species), unpreconditioned
+    and block-Jacobi, on near-equilibrium states built as the benchmark builds them (512
+    equilibria from element potentials, here with the oracle's Gibbs energies, tiled over the
+    points and perturbed by 1e-3 in Y and ~1 K in T); 100 sampled points against the oracle's
+    dense Newton solution (weighted RMS difference within 1e-3 of the tolerance weights)."""
+    from test_oracle_rates import equilibrium_state
+    mech = synth.mechanism("ch4_53sp_325rx")
+    m = gpu_mechanism("ch4_53sp_325rx")
+    n, nu = 2097152, 512
+    rng = np.random.default_rng(6053)
+    Tu = np.linspace(1300.0, 2600.0, nu)
+    Yu = np.stack([equilibrium_state(mech, Tu[j], P_ATM, rng) for j in range(nu)], axis=1)
+    idx = np.arange(n) % nu
+    T = Tu[idx] + rng.standard_normal(n)
+    Y = Yu[:, idx] * (1.0 + 1e-3 * rng.standard_normal((mech.K, n)))
+    Y /= Y.sum(0)
+    Y = np.ascontiguousarray(Y)
+    p = np.full(n, P_ATM)
+    rtol, atolT, atolY, dt = 1e-6, 1e-6, 1e-12, 1e-9
+    samp = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 98, replace=False)]))
+    T_o, Y_o, it = oracle.reactor_step(mech, T[samp], p[samp], np.ascontiguousarray(Y[:, samp]), dt,
+                                       atol_T=atolT, atol_Y=atolY)
+    assert np.all(it > 0)
+    wT = 1.0 / (rtol * np.abs(T[samp]) + atolT)
+    wY = 1.0 / (rtol * np.abs(Y[:, samp]) + atolY)
+    pt = torch.from_numpy(p).cuda()
+    for precond in (0, 1):
+        Tt, Yt = to_dev(T, Y)
+        o = nk.reactor_opts(rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4, lin_tol=1e-6, max_newton=20,
+                            krylov_dim=30, precond=precond)
+        st = nk.reactor_step(m, Tt, pt, Yt, dt, o)
+        assert st["converged"] == 1, (precond, st)
+        sub = torch.from_numpy(samp).cuda()
+        d = np.concatenate([((host(Tt[sub]) - T_o) * wT)[None], (host(Yt[:, sub]) - Y_o) * wY])
+        assert np.sqrt(np.mean(d ** 2)) <= 1e-3, precond
+        del Tt, Yt
+        torch.cuda.empty_cache()
