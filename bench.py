@@ -376,17 +376,18 @@ def reactor_states(nk, m, mech, n, dev, seed=6053):
 def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9, dt_large=1e-5):
     """One implicit Euler step over n near-equilibrium points (nk_reactor_step), each after one
     untimed step from the same states; CUDA events on the launching stream.  The paper's
-    unpreconditioned GMRES at dt, and with the per-point block-Jacobi preconditioner at dt and at
+    unpreconditioned GMRES at dt (products recomputing the rates, and from a stored linearization
+    per Newton iteration), and with the per-point block-Jacobi preconditioner at dt and at
     dt_large, each with its set-up (precond 1) and with the factors of the previous call reused
     (precond 2, as a stiff ODE solver keeps its Newton matrix over steps)."""
     import torch
     T0, p, Y0 = reactor_states(nk, m, mech, n, dev)
     kw = dict(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=20, krylov_dim=30)
-    ws = torch.empty(nk.reactor_workspace(m, n, kw["krylov_dim"], 1), dtype=torch.uint8, device=dev)
+    ws = torch.empty(nk.reactor_workspace(m, n, kw["krylov_dim"], 1, 1), dtype=torch.uint8, device=dev)
     T, Y = T0.clone(), Y0.clone()
 
-    def run(step, precond):
-        o = nk.reactor_opts(precond=precond, **kw)
+    def run(step, precond, linearized=0):
+        o = nk.reactor_opts(precond=precond, linearized=linearized, **kw)
         for timed in (False, True):
             T.copy_(T0)
             Y.copy_(Y0)
@@ -404,7 +405,9 @@ def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9, dt_large=1e-5):
            "workload": f"{MECH}, near-equilibrium states (1300-2600 K, perturbed 1e-3), one implicit Euler step, "
                        f"GMRES(30), rtol 1e-6, atol_T 1e-6, atol_Y 1e-12, newton_tol 1e-4, lin_tol 1e-6"}
     res.update(run(dt, 0))
+    res["linearized"] = run(dt, 0, 1)
     res["block_jacobi"] = run(dt, 1)
+    res["block_jacobi_linearized"] = run(dt, 1, 1)
     res["block_jacobi_reused"] = run(dt, 2)
     res["block_jacobi_large_dt"] = run(dt_large, 1)
     res["block_jacobi_large_dt_reused"] = run(dt_large, 2)

@@ -321,6 +321,17 @@ nk_status nk_block_jacobi_apply(const nk_mech* mech, int64_t n, const double* F,
                                 const double* v, int64_t ldv, double* z, int64_t ldz, nk_stream stream);
 
 /*
+ * The JVP of nk_rhs_jvp from a stored linearization (nk_rates_linearize at the same state,
+ * dlnA = NULL) and the sources there (nk_rhs_eval, NK_FP64): the cheap per-direction pass for a
+ * Newton-Krylov solve that forms several products at one state.
+ *   fT[n], fY[K*ld]   the sources at (T, p, Y);  vT, vY the direction;  dfT[n], dfY[K*ld] out
+ */
+nk_status nk_rhs_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                                const double* Y, const double* lin, int64_t ldl, const double* fT,
+                                const double* fY, const double* vT, const double* vY, double* dfT, double* dfY,
+                                nk_stream stream);
+
+/*
  * One implicit (backward) Euler step of dt seconds of the homogeneous constant-pressure
  * reactor at every point: solves x1 - x0 - dt f(x1) = 0, x = (T, Y_k), f the sources of
  * nk_rhs_eval, the nonlinear system of the paper's implicit thermochemistry stage (Sec. 2),
@@ -330,10 +341,12 @@ nk_status nk_block_jacobi_apply(const nk_mech* mech, int64_t n, const double* F,
  * projections in one reduction and the new vector's norm in a second.  Norms are weighted RMS
  * norms with weights 1/(rtol |x0_i| + atol_i).
  *   T[n], Y[K*n]   in: the state x0; out: the step's result (contiguous: Y rows of stride n)
- *   workspace      device, nk_reactor_workspace bytes (holds (K+1) n doubles x 7 and
- *                  (krylov_dim + 1) (K+1) n floats; with the preconditioner also (K+1)^2 n
- *                  doubles of factors, (K+1) n pivot words and a stored linearization of up to
- *                  about 2 GB, filled chunk by chunk)
+ *   workspace      device, nk_reactor_workspace bytes for the same options (holds (K+1) n
+ *                  doubles x 7 and (krylov_dim + 1) (K+1) n floats; with the preconditioner
+ *                  also (K+1)^2 n doubles of factors, (K+1) n pivot words and a stored
+ *                  linearization of up to about 2 GB, filled chunk by chunk; with linearized
+ *                  products the full stored linearization, nk_rates_linearization_slots x n
+ *                  doubles)
  * With precond = 1 the solve is left-preconditioned by the per-point blocks of
  * nk_block_jacobi_factor, made once per step at x0: GMRES minimises P^-1 (r - A z), which
  * tracks the error of the update (the unpreconditioned residual of stiff chemistry is dominated
@@ -358,6 +371,10 @@ typedef struct {
     int32_t krylov_dim;   /* GMRES iterations per Newton iteration, 1..NK_REACTOR_MAX_KRYLOV */
     int32_t precond;      /* 0: none (the paper's stage); 1: per-point block Jacobi made at x0;
                              2: block Jacobi from the factors of an earlier call (K + 1 <= 160) */
+    int32_t linearized;   /* 0: every GMRES product recomputes the rates (nk_rhs_jvp); 1: the rates
+                             are linearized once per Newton iteration and the products come from
+                             the stored data (nk_rhs_jvp_linearized): cheaper once a Newton
+                             iteration takes more than one or two GMRES iterations */
 } nk_reactor_opts;
 typedef struct {
     int32_t converged;    /* 1 when the update test was met (0: max_newton reached, or the
@@ -367,7 +384,7 @@ typedef struct {
     double update_wrms;   /* weighted RMS norm of the last Newton update */
     double residual_wrms; /* weighted RMS norm of the residual before the last update */
 } nk_reactor_stats;
-nk_status nk_reactor_workspace(const nk_mech* mech, int64_t n, int32_t krylov_dim, int32_t precond, size_t* bytes);
+nk_status nk_reactor_workspace(const nk_mech* mech, int64_t n, const nk_reactor_opts* opts, size_t* bytes);
 nk_status nk_reactor_step(const nk_mech* mech, int64_t n, double* T, const double* p, double* Y, double dt,
                           const nk_reactor_opts* opts, nk_reactor_stats* stats, void* workspace,
                           size_t workspace_bytes, nk_stream stream);

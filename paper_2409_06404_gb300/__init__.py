@@ -59,7 +59,7 @@ class _Desc(ctypes.Structure):
 class _ReactorOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol_T", ctypes.c_double), ("atol_Y", ctypes.c_double),
                 ("newton_tol", ctypes.c_double), ("lin_tol", ctypes.c_double), ("max_newton", _i32),
-                ("krylov_dim", _i32), ("precond", _i32)]
+                ("krylov_dim", _i32), ("precond", _i32), ("linearized", _i32)]
 
 
 class _ReactorStats(ctypes.Structure):
@@ -78,7 +78,8 @@ _SIGS = {
     "nk_transport_eval": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "nk_rates_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_diffusion_fluxes": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 8 + [_vp]),
-    "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_reactor_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(_ReactorOpts), ctypes.POINTER(ctypes.c_size_t)]),
+    "nk_rhs_jvp_linearized": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64] + [_vp] * 6 + [_vp]),
     "nk_mechanism_jit": (ctypes.c_int, [_vp]),
     "nk_host_eval_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_host_eval": (ctypes.c_int, [_vp, _i64] + [_vp] * 8 + [ctypes.c_int, _i64, _vp, ctypes.c_size_t, _vp]),
@@ -376,15 +377,17 @@ def diffusion_fluxes(m: Mechanism, T, p, Y, Dmix, gradX, want_vc=True, want_hf=T
 
 
 def reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-14, newton_tol=0.1, lin_tol=1e-3, max_newton=10,
-                 krylov_dim=20, precond=0) -> _ReactorOpts:
+                 krylov_dim=20, precond=0, linearized=0) -> _ReactorOpts:
     """Options of nk_reactor_step (weighted RMS tolerances; precond 1 = per-point block Jacobi
-    made at x0, 2 = its factors from the last call reused; see include/nkchem.h)."""
-    return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim, precond)
+    made at x0, 2 = its factors from the last call reused; linearized 1 = GMRES products from a
+    stored linearization per Newton iteration; see include/nkchem.h)."""
+    return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim, precond, linearized)
 
 
-def reactor_workspace(m: Mechanism, n: int, krylov_dim: int, precond: int = 0) -> int:
+def reactor_workspace(m: Mechanism, n: int, krylov_dim: int = 20, precond: int = 0, linearized: int = 0) -> int:
     b = ctypes.c_size_t()
-    _check(lib().nk_reactor_workspace(m.handle, int(n), int(krylov_dim), int(precond), ctypes.byref(b)))
+    o = reactor_opts(krylov_dim=krylov_dim, precond=precond, linearized=linearized)
+    _check(lib().nk_reactor_workspace(m.handle, int(n), ctypes.byref(o), ctypes.byref(b)))
     return b.value
 
 
@@ -396,9 +399,10 @@ def reactor_step(m: Mechanism, T, p, Y, dt: float, opts: _ReactorOpts = None, wo
     if ld != n:
         raise ValueError("reactor_step takes a contiguous Y [K, n]")
     opts = opts or reactor_opts()
-    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30 and opts.precond in (0, 1, 2):
-        workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim, opts.precond), dtype=torch.uint8,
-                                device=T.device)
+    if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30 and opts.precond in (0, 1, 2) \
+            and opts.linearized in (0, 1):
+        workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim, opts.precond, opts.linearized),
+                                dtype=torch.uint8, device=T.device)
     st = _ReactorStats()
     _check(lib().nk_reactor_step(m.handle, n, _ptr(T), _ptr(p), _ptr(Y), float(dt), ctypes.byref(opts),
                                  ctypes.byref(st), _ptr(workspace), 0 if workspace is None else workspace.numel(),
@@ -432,6 +436,22 @@ def rhs_jvp(m: Mechanism, T, p, Y, vT, vY, dlnA=None, primal=False, stream=None)
                             _ptr(fT), _ptr(fY), _ptr(dfT), _ptr(dfY), _stream(stream)))
     if primal:
         return dfT, dfY, fT, fY
+    return dfT, dfY
+
+
+def rhs_jvp_linearized(m: Mechanism, T, p, Y, lin, fT, fY, vT, vY, stream=None):
+    """nk_rhs_jvp_linearized: (dfT, dfY) = J_f (vT, vY) from a stored linearization and the
+    sources at the same state."""
+    n, ld = _state(m, T, p, Y)
+    _check_lin(m, lin, n)
+    _vec(fT, n, "fT")
+    _species_in(m, fY, n, ld, "fY")
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    dfY = _species_out(m, n, ld, T)
+    dfT = _point_out(n, T)
+    _check(lib().nk_rhs_jvp_linearized(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0),
+                                       _ptr(fT), _ptr(fY), _ptr(vT), _ptr(vY), _ptr(dfT), _ptr(dfY), _stream(stream)))
     return dfT, dfY
 
 

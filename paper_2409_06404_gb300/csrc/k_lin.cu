@@ -322,7 +322,10 @@ __device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, co
     }
 }
 
-template <int BLK, int NP>
+// RHS: the tangent of the implicit-stage sources instead, given the sources fT, fY at the same
+// state: dfY_k = (W_k/rho) d omega_k - fY_k d rho/rho, dfT = d hrr/(rho c_p) - fT (d rho/rho +
+// d c_p/c_p) (d_omega, d_hrr then receive dfY, dfT).
+template <int BLK, int NP, bool RHS>
 __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                            const double* __restrict__ T,
                                                            const double* __restrict__ p,
@@ -330,7 +333,9 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
                                                            const double* __restrict__ lin, const int64_t ldl,
                                                            const double* __restrict__ vT,
                                                            const double* __restrict__ vY,
-                                                           double* __restrict__ d_omega, double* __restrict__ d_hrr) {
+                                                           double* __restrict__ d_omega, double* __restrict__ d_hrr,
+                                                           const double* __restrict__ fT,
+                                                           const double* __restrict__ fY, const int64_t ldf) {
     extern __shared__ double smem[];
     const int K = m.K;
     const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
@@ -371,23 +376,53 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
     apply_group<BLK, 2>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
     if (NP > 1) __syncthreads();
 
-    double hsum = 0.0;
+    double hsum = 0.0, cpm = 0.0, dcpm = 0.0, inv_rho = 0.0;
+    if constexpr (RHS) inv_rho = 1.0 / rho;
     for (int k = part; k < K; k += NP) {
         double dw = sD0[k * BLK];
 #pragma unroll
         for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
-        if (live) d_omega[(int64_t)k * ld + i] = dw;
         hsum = fma(lin[(slot_H(m) + k) * ldl + i], dw, hsum);
+        if constexpr (RHS) {
+            const double* c = nasa_range(m, k, Ti);
+            const double iw = __ldg(m.invW + k), cpk = nasa_cpR(c, Ti);
+            const double yk = Y[(int64_t)k * ld + i] * iw, vk = vY[(int64_t)k * ld + i] * iw;
+            cpm = fma(yk, cpk, cpm);
+            dcpm = fma(vk, cpk, fma(yk * nasa_dcpR_dT(c, Ti), dT, dcpm));
+            dw = fma(__ldg(m.W + k) * inv_rho, dw, -fY[(int64_t)k * ldf + i] * arho);
+        }
+        if (live) d_omega[(int64_t)k * ld + i] = dw;
     }
     if constexpr (NP > 1) {
-        sdC[part * BLK] = hsum;                    // dC_k is dead; rows 0..NP-1 (NP <= K)
+        // dC_k is dead: rows q, NP + q, 2 NP + q take part q's sums ((1 + 2 RHS) NP <= K)
+        sdC[part * BLK] = hsum;
+        if constexpr (RHS) {
+            sdC[(NP + part) * BLK] = cpm;
+            sdC[(2 * NP + part) * BLK] = dcpm;
+        }
         __syncthreads();
         if (part != 0) return;
         hsum = sdC[0];
+        if constexpr (RHS) {
+            cpm = sdC[NP * BLK];
+            dcpm = sdC[2 * NP * BLK];
+        }
 #pragma unroll
-        for (int q = 1; q < NP; ++q) hsum += sdC[q * BLK];
+        for (int q = 1; q < NP; ++q) {
+            hsum += sdC[q * BLK];
+            if constexpr (RHS) {
+                cpm += sdC[(NP + q) * BLK];
+                dcpm += sdC[(2 * NP + q) * BLK];
+            }
+        }
     }
-    if (live) d_hrr[i] = -kR * fma(dT, lin[slot_S(m) * ldl + i], Ti * hsum);
+    if (live) {
+        const double dhr = -kR * fma(dT, lin[slot_S(m) * ldl + i], Ti * hsum);
+        if constexpr (RHS)
+            d_hrr[i] = fma(dhr, inv_rho / (kR * cpm), -fT[i] * (arho + dcpm / cpm));
+        else
+            d_hrr[i] = dhr;
+    }
 }
 
 // ---------------------------------------------------------------- launch shapes
@@ -397,17 +432,20 @@ struct Shape {
 constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <bool APPLY, int S>
+// MODE 0: the linearization pass; 1: the JVP from it; 2: the sources' JVP from it
+template <int MODE, int S>
 constexpr auto kernel_of() {
-    if constexpr (APPLY)
-        return jvp_lin_kernel<kShapes[S].blk, kShapes[S].np>;
+    if constexpr (MODE == 1)
+        return jvp_lin_kernel<kShapes[S].blk, kShapes[S].np, false>;
+    else if constexpr (MODE == 2)
+        return jvp_lin_kernel<kShapes[S].blk, kShapes[S].np, true>;
     else
         return linearize_kernel<kShapes[S].blk, kShapes[S].np>;
 }
 
-template <bool APPLY, int... S>
+template <int MODE, int... S>
 const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
-    const void* ptrs[] = {(const void*)kernel_of<APPLY, S>()...};
+    const void* ptrs[] = {(const void*)kernel_of<MODE, S>()...};
     return ptrs[idx];
 }
 
@@ -418,31 +456,31 @@ size_t lin_smem(int K, const Shape& sh, bool apply) {
 }
 
 struct Plan {
-    int dev, K;
-    bool apply;
+    int dev, K, mode;
     int idx;
 };
 std::mutex g_plan_mu;
 std::vector<Plan> g_plans;
 
-template <bool APPLY>
+template <int MODE>
 int plan_shape(int K) {
+    constexpr bool APPLY = MODE != 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         for (const Plan& q : g_plans)
-            if (q.dev == dev && q.K == K && q.apply == APPLY) return q.idx;
+            if (q.dev == dev && q.K == K && q.mode == MODE) return q.idx;
     }
     int per_block = 0;
     cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int best = -1, best_warps = 0;
     for (int c = 0; c < kNumShapes; ++c) {
         const Shape& sh = kShapes[c];
-        if (sh.np > K) continue;
+        if ((MODE == 2 ? 3 : 1) * sh.np > K) continue;
         const size_t bytes = lin_smem(K, sh, APPLY);
         if (bytes > (size_t)per_block) continue;
-        const void* kern = kernel_ptr<APPLY>(c, std::make_integer_sequence<int, kNumShapes>{});
+        const void* kern = kernel_ptr<MODE>(c, std::make_integer_sequence<int, kNumShapes>{});
         if (ensure_smem(kern, bytes) != cudaSuccess) continue;
         int blocks = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
@@ -455,19 +493,19 @@ int plan_shape(int K) {
     }
     if (best >= 0) {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        g_plans.push_back({dev, K, APPLY, best});
+        g_plans.push_back({dev, K, MODE, best});
     }
     return best;
 }
 
-template <bool APPLY, class... Args, int... S>
+template <int MODE, class... Args, int... S>
 cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, int K, int64_t n, cudaStream_t st,
                        Args... args) {
     cudaError_t e = cudaErrorInvalidConfiguration;
     ((S == idx ? (void)(e = [&] {
         constexpr Shape sh = kShapes[S];
-        auto kern = kernel_of<APPLY, S>();
-        const size_t smem = lin_smem(K, sh, APPLY);
+        auto kern = kernel_of<MODE, S>();
+        const size_t smem = lin_smem(K, sh, MODE != 0);
         cudaError_t r = ensure_smem((const void*)kern, smem);
         if (r != cudaSuccess) return r;
         kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(args...);
@@ -485,19 +523,30 @@ int64_t lin_slots(const DevMech& m) { return slot_H(m) + m.K; }
 cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* dlnA, double* lin, int64_t ldl, cudaStream_t s) {
     static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
-    const int idx = plan_shape<false>(m.K);
+    const int idx = plan_shape<0>(m.K);
     if (idx < 0) return cudaErrorInvalidConfiguration;
-    return launch_idx<false>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y,
-                             dlnA, lin, ldl);
+    return launch_idx<0>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, dlnA,
+                         lin, ldl);
 }
 
 cudaError_t launch_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                                   const double* Y, const double* lin, int64_t ldl, const double* vT,
                                   const double* vY, double* d_omega, double* d_hrr, cudaStream_t s) {
-    const int idx = plan_shape<true>(m.K);
+    const int idx = plan_shape<1>(m.K);
     if (idx < 0) return cudaErrorInvalidConfiguration;
-    return launch_idx<true>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin,
-                            ldl, vT, vY, d_omega, d_hrr);
+    const double* none = nullptr;
+    return launch_idx<1>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin, ldl,
+                         vT, vY, d_omega, d_hrr, none, none, (int64_t)0);
+}
+
+cudaError_t launch_rhs_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                      const double* Y, const double* lin, int64_t ldl, const double* fT,
+                                      const double* fY, int64_t ldf, const double* vT, const double* vY, double* dfT,
+                                      double* dfY, cudaStream_t s) {
+    const int idx = plan_shape<2>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<2>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin, ldl,
+                         vT, vY, dfY, dfT, fT, fY, ldf);
 }
 
 }  // namespace nk

@@ -754,15 +754,31 @@ nk_status check_precond(const nk_mech* m, int32_t precond) {
     return NK_OK;
 }
 
-nk_status nk_reactor_workspace(const nk_mech* m, int64_t n, int32_t krylov_dim, int32_t precond, size_t* bytes) {
-    if (!m || !bytes) return fail(NK_EINVAL, "mech and bytes must not be NULL");
+nk_status nk_reactor_workspace(const nk_mech* m, int64_t n, const nk_reactor_opts* o, size_t* bytes) {
+    if (!m || !bytes || !o) return fail(NK_EINVAL, "mech, opts and bytes must not be NULL");
     if (n < 0) return fail(NK_EINVAL, "n < 0");
-    if (krylov_dim < 1 || krylov_dim > NK_REACTOR_MAX_KRYLOV)
-        return fail(NK_EINVAL, "krylov_dim=%d outside 1..%d", krylov_dim, NK_REACTOR_MAX_KRYLOV);
-    nk_status st = check_precond(m, precond);
+    if (o->krylov_dim < 1 || o->krylov_dim > NK_REACTOR_MAX_KRYLOV)
+        return fail(NK_EINVAL, "krylov_dim=%d outside 1..%d", o->krylov_dim, NK_REACTOR_MAX_KRYLOV);
+    nk_status st = check_precond(m, o->precond);
     if (st != NK_OK) return st;
-    *bytes = n == 0 ? 0 : nk::reactor_workspace_bytes(m->d, n, krylov_dim, precond);
+    if (o->linearized != 0 && o->linearized != 1) return fail(NK_EINVAL, "linearized=%d is not 0 or 1", o->linearized);
+    *bytes = n == 0 ? 0 : nk::reactor_workspace_bytes(m->d, n, o->krylov_dim, o->precond, o->linearized);
     return ok();
+}
+
+nk_status nk_rhs_jvp_linearized(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                const double* Y, const double* lin, int64_t ldl, const double* fT, const double* fY,
+                                const double* vT, const double* vY, double* dfT, double* dfY, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !fT || !fY || !vT || !vY || !dfT || !dfY)
+        return fail(NK_EINVAL, "lin, fT, fY, vT, vY, dfT and dfY must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, fT, fY, vT, vY, dfT, dfY})) != NK_OK) return st;
+    return launched(nk::launch_rhs_jvp_linearized(m->d, n, ld, T, p, Y, lin, ldl, fT, fY, ld, vT, vY, dfT, dfY,
+                                                  (cudaStream_t)stream),
+                    "linearized sources jvp kernel launch");
 }
 
 nk_status nk_rhs_jacobian(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
@@ -831,7 +847,8 @@ nk_status nk_reactor_step(const nk_mech* m, int64_t n, double* T, const double* 
         o.max_newton < 1 || !(dt >= 0.0) || !std::isfinite(dt))
         return fail(NK_EINVAL, "bad reactor options (tolerances > 0, max_newton >= 1, finite dt >= 0)");
     if ((st = check_precond(m, o.precond)) != NK_OK) return st;
-    const size_t need = nk::reactor_workspace_bytes(m->d, n, o.krylov_dim, o.precond);
+    if (o.linearized != 0 && o.linearized != 1) return fail(NK_EINVAL, "linearized=%d is not 0 or 1", o.linearized);
+    const size_t need = nk::reactor_workspace_bytes(m->d, n, o.krylov_dim, o.precond, o.linearized);
     if (!workspace || workspace_bytes < need)
         return fail(NK_EINVAL, "the reactor step needs %zu bytes of workspace, got %zu", need,
                     workspace ? workspace_bytes : (size_t)0);

@@ -201,7 +201,7 @@ cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        double* omega, double* hrr, double* d_omega, double* d_hrr, cudaStream_t s,
                        int rhs = 0);
 size_t vjp_workspace_bytes(const DevMech& m, int64_t n);
-size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim, int precond);
+size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim, int precond, int linearized);
 cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p, double* Y, double dt,
                          const nk_reactor_opts& o, nk_reactor_stats& st, void* ws, cudaStream_t s);
 // Dense Jacobian of the sources from a stored linearization and the sources (k_jac.cu).
@@ -226,6 +226,12 @@ size_t host_eval_workspace_bytes(const DevMech& m, int64_t chunk);
 cudaError_t host_eval(const DevMech& m, int64_t n, const double* T, const double* p, const double* Y, double* omega,
                       double* hrr, double* mu, double* lam, double* Dmix, int precision, int64_t chunk, void* ws,
                       cudaStream_t caller);
+// The implicit-stage sources' JVP from a stored linearization and the sources at the state
+// (k_lin.cu).
+cudaError_t launch_rhs_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                      const double* Y, const double* lin, int64_t ldl, const double* fT,
+                                      const double* fY, int64_t ldf, const double* vT, const double* vY, double* dfT,
+                                      double* dfY, cudaStream_t s);
 // Mechanism-specialised rates kernel (jit.cu): source from the host description, NVRTC
 // compilation and loading, launch (all-double form, results as nk_rates_eval's).
 std::string jit_source(const nk_mech_desc* d);

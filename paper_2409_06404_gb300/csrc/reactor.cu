@@ -248,24 +248,27 @@ int reduction_blocks() {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// points per chunk of the stored linearization (about 2 GB, whole warps)
-int64_t lin_chunk(const DevMech& mech, int64_t n) {
+// points per chunk of the stored linearization: all of them for linearized products, else
+// about 2 GB (whole warps) for the preconditioner's set-up
+int64_t lin_chunk(const DevMech& mech, int64_t n, int linearized) {
+    if (linearized) return n;
     const int64_t per = lin_slots(mech) * (int64_t)sizeof(double);
     const int64_t c = std::max<int64_t>(128, ((int64_t(2) << 30) / per) / 128 * 128);
     return std::min(n, c);
 }
 
-size_t work_bytes(const DevMech& mech, int64_t n, int m, int nred, int precond) {
+size_t work_bytes(const DevMech& mech, int64_t n, int m, int nred, int precond, int linearized) {
     const int64_t N = (int64_t)(mech.K + 1) * n;
     size_t b = 7 * align256((size_t)N * sizeof(double)) + align256((size_t)(m + 1) * N * sizeof(float)) +
                align256((size_t)nred * kMaxDots * sizeof(double)) + align256(kMaxDots * sizeof(double));
     if (precond)
-        b += align256((size_t)(mech.K + 1) * N * sizeof(double)) + align256((size_t)N * sizeof(int32_t)) +
-             align256((size_t)lin_slots(mech) * lin_chunk(mech, n) * sizeof(double));
+        b += align256((size_t)(mech.K + 1) * N * sizeof(double)) + align256((size_t)N * sizeof(int32_t));
+    if (precond || linearized)
+        b += align256((size_t)lin_slots(mech) * lin_chunk(mech, n, linearized) * sizeof(double));
     return b;
 }
 
-Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precond) {
+Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precond, int linearized) {
     const int64_t N = (int64_t)(mech.K + 1) * n;
     Work w;
     char* b = static_cast<char*>(ws);
@@ -292,7 +295,9 @@ Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precon
     if (precond) {
         w.F = reinterpret_cast<double*>(take((size_t)(mech.K + 1) * N * sizeof(double)));
         w.piv = reinterpret_cast<int32_t*>(take((size_t)N * sizeof(int32_t)));
-        w.nchunk = lin_chunk(mech, n);
+    }
+    if (precond || linearized) {
+        w.nchunk = lin_chunk(mech, n, linearized);
         w.lin = reinterpret_cast<double*>(take((size_t)lin_slots(mech) * w.nchunk * sizeof(double)));
     }
     w.N = N;
@@ -303,9 +308,9 @@ Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precon
 
 }  // namespace
 
-size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim, int precond) {
+size_t reactor_workspace_bytes(const DevMech& m, int64_t n, int krylov_dim, int precond, int linearized) {
     // (the reduction-block count depends on the device's SM count)
-    return work_bytes(m, n, krylov_dim, reduction_blocks(), precond);
+    return work_bytes(m, n, krylov_dim, reduction_blocks(), precond, linearized);
 }
 
 // One implicit Euler step (contiguous state: Y rows of stride n).  Returns cudaSuccess and
@@ -317,7 +322,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
     const int64_t N = (int64_t)(K + 1) * n;
     const int mk = o.krylov_dim;
     const int nred = reduction_blocks();
-    Work w = carve(m, ws, n, mk, nred, o.precond);
+    Work w = carve(m, ws, n, mk, nred, o.precond, o.linearized);
     const int eg = (int)std::min<int64_t>((N + kElemBlk - 1) / kElemBlk, (int64_t)nred * 8);
     cudaError_t e;
     std::vector<double> hbuf(kMaxDots);
@@ -346,13 +351,19 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
             st.converged = beta == 0.0;
             return cudaSuccess;
         }
+        if (o.linearized &&                        // the rates' tangent data at this iterate
+            (e = launch_linearize(m, n, ld, T, p, Y, nullptr, w.lin, n, s)) != cudaSuccess)
+            return e;
         if (o.precond == 1 && it == 0) {           // blocks of I - dt W J W^-1 at x0, factored
             for (int64_t c0 = 0; c0 < n; c0 += w.nchunk) {
                 const int64_t nc = std::min(w.nchunk, n - c0);
-                if ((e = launch_linearize(m, nc, ld, T + c0, p + c0, Y + c0, nullptr, w.lin, nc, s)) != cudaSuccess)
+                if (!o.linearized &&
+                    (e = launch_linearize(m, nc, ld, T + c0, p + c0, Y + c0, nullptr, w.lin, nc, s)) != cudaSuccess)
                     return e;
-                if ((e = launch_precond_setup(m, nc, ld, T + c0, p + c0, Y + c0, w.lin, nc, w.f + c0, w.f + n + c0,
-                                              n, w.W + c0, n, dt, w.F + c0, w.piv + c0, n, s)) != cudaSuccess)
+                const double* lc = o.linearized ? w.lin + c0 : w.lin;     // (the full data: stride n)
+                if ((e = launch_precond_setup(m, nc, ld, T + c0, p + c0, Y + c0, lc, o.linearized ? n : nc, w.f + c0,
+                                              w.f + n + c0, n, w.W + c0, n, dt, w.F + c0, w.piv + c0, n, s)) !=
+                    cudaSuccess)
                     return e;
             }
         }
@@ -378,9 +389,11 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         while (j < mk) {
             const float* vj = w.V + (int64_t)j * w.vstride;
             unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.W, w.u);
-            if ((e = launch_jvp(m, n, ld, T, p, Y, nullptr, w.u, w.u + n, nullptr, nullptr, w.Ju + n, w.Ju, s, 1)) !=
-                cudaSuccess)
-                return e;
+            e = o.linearized ? launch_rhs_jvp_linearized(m, n, ld, T, p, Y, w.lin, n, w.f, w.f + n, n, w.u, w.u + n,
+                                                         w.Ju, w.Ju + n, s)
+                             : launch_jvp(m, n, ld, T, p, Y, nullptr, w.u, w.u + n, nullptr, nullptr, w.Ju + n, w.Ju,
+                                          s, 1);
+            if (e != cudaSuccess) return e;
             if (o.precond) {                          // w = P^-1 A v_j
                 form_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.Ju, w.W, dt, w.w);
                 if ((e = launch_precond_apply(K + 1, n, w.F, n, w.piv, n, w.w, n, w.w, n, s)) != cudaSuccess)

@@ -115,3 +115,25 @@ def test_linearized_full_size_sampled(cuda):
     assert scaled_err(host(dh[sub]), dh_o, dhs) <= TOL
     assert torch.isfinite(dh).all()
     del lin
+
+
+@pytest.mark.parametrize("name,n", [("ch4_53sp_325rx", 2000 + 33), ("h2_9sp_21rx", 1000), ("big_120sp_700rx", 300)])
+def test_sources_jvp_from_linearization(cuda, name, n):
+    """nk_rhs_jvp_linearized against the oracle's complex-step JVP of the sources (1e-10 of the
+    derivative magnitudes) and against the recomputing nk_rhs_jvp."""
+    mech = synth.mechanism(name)
+    m = gpu_mechanism(name)
+    T, p, Y = _flame(mech, n, seed=8)
+    Tt, pt, Yt = to_dev(T, p, Y)
+    lin = nk.rates_linearize(m, Tt, pt, Yt)
+    fT, fY = nk.rhs_eval(m, Tt, pt, Yt)
+    for d in range(2):
+        vT = synth.normal(n, 4400 + 2 * d) * 30.0
+        vY = synth.normal((mech.K, n), 4401 + 2 * d) * (Y + 1e-12)
+        vTt, vYt = to_dev(vT, vY)
+        dfT, dfY = nk.rhs_jvp_linearized(m, Tt, pt, Yt, lin, fT, fY, vTt, vYt)
+        dT_o, dY_o, sT, sY = oracle.rhs_jvp(mech, T, p, Y, vT, vY, scales=True)
+        assert scaled_err(host(dfT), dT_o, sT) <= TOL
+        assert scaled_err(host(dfY), dY_o, sY) <= TOL
+        dfT2, dfY2 = nk.rhs_jvp(m, Tt, pt, Yt, vTt, vYt)
+        assert scaled_err(host(dfT), host(dfT2), sT) <= TOL and scaled_err(host(dfY), host(dfY2), sY) <= TOL

@@ -121,6 +121,26 @@ def test_preconditioned_step_vs_dense_newton(cuda, name, n, dt):
     assert st["krylov_iters"] <= 10 * st["newton_iters"]
 
 
+@pytest.mark.parametrize("name,n,dt,precond", [("h2_9sp_21rx", 600, 1e-9, 0), ("ch4_53sp_325rx", 160, 1e-7, 0),
+                                               ("h2_9sp_21rx", 600, 1e-4, 1)])
+def test_linearized_products_vs_dense_newton(cuda, name, n, dt, precond):
+    """GMRES products from a stored linearization refreshed per Newton iteration: the same
+    solution as the oracle's dense Newton (and as the recomputing products)."""
+    mech = synth.mechanism(name)
+    m = gpu_mechanism(name)
+    T, p, Y = _perturbed_equilibrium(mech, n, seed=41) if precond else _near_equilibrium(mech, n, seed=41)
+    rtol, atolT, atolY = 1e-6, 1e-6, 1e-12
+    T1, Y1, st = _step(m, *to_dev(T, p, Y), dt, rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4,
+                       lin_tol=1e-6, max_newton=30, krylov_dim=30, precond=precond, linearized=1)
+    assert st["converged"] == 1, st
+    T_o, Y_o, it = oracle.reactor_step(mech, T, p, Y, dt, atol_T=atolT, atol_Y=atolY)
+    assert np.all(it > 0)
+    wT = 1.0 / (rtol * np.abs(T) + atolT)
+    wY = 1.0 / (rtol * np.abs(Y) + atolY)
+    d = np.concatenate([((host(T1) - T_o) * wT)[None], (host(Y1) - Y_o) * wY])
+    assert np.sqrt(np.mean(d ** 2)) <= 1e-3
+
+
 def test_preconditioned_and_plain_solves_agree(cuda):
     """Where both converge (small steps) the two solves reach the same solution."""
     mech = synth.mechanism("h2_9sp_21rx")
@@ -140,6 +160,9 @@ def test_preconditioned_workspace_and_limits(cuda):
     assert nk.reactor_workspace(m, 64, 10, 1) > nk.reactor_workspace(m, 64, 10, 0)
     with pytest.raises(nk.NkError):
         nk.reactor_workspace(m, 64, 10, 3)
+    assert nk.reactor_workspace(m, 64, 10, 0, 1) > nk.reactor_workspace(m, 64, 10, 0, 0)
+    with pytest.raises(nk.NkError):
+        nk.reactor_workspace(m, 64, 10, 0, 2)
 
 
 def test_reused_factors(cuda):
