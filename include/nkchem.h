@@ -342,7 +342,7 @@ nk_status nk_rhs_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, cons
  * norms with weights 1/(rtol |x0_i| + atol_i).
  *   T[n], Y[K*n]   in: the state x0; out: the step's result (contiguous: Y rows of stride n)
  *   workspace      device, nk_reactor_workspace bytes for the same options (holds (K+1) n
- *                  doubles x 7 and (krylov_dim + 1) (K+1) n floats; with the preconditioner
+ *                  doubles x 8 and (krylov_dim + 1) (K+1) n floats; with the preconditioner
  *                  also (K+1)^2 n doubles of factors, (K+1) n pivot words and a stored
  *                  linearization of up to about 2 GB, filled chunk by chunk; with linearized
  *                  products the full stored linearization, nk_rates_linearization_slots x n

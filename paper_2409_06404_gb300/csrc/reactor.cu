@@ -49,15 +49,31 @@ __device__ __forceinline__ int64_t row_of(int64_t e, int64_t n, int64_t& i) {
     return r;
 }
 
+// A basis entry widened to double with integer operations: on GB300 the float-to-double
+// conversion instruction runs on the FP64 pipe, which the vector kernels are short of.  Exact
+// for normal floats, infinities and NaN; a subnormal float (|v| < 1.2e-38 in a unit vector)
+// becomes a signed zero.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long ee = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+    const unsigned long long bits = e == 0u ? sign : sign | (ee << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// x0, the weights W = 1/(rtol |x0| + atol) and their reciprocals iW = rtol |x0| + atol
 __global__ void init_kernel(int64_t n, int64_t N, int64_t ld, const double* __restrict__ T,
                             const double* __restrict__ Y, double rtol, double atolT, double atolY,
-                            double* __restrict__ x0, double* __restrict__ W) {
+                            double* __restrict__ x0, double* __restrict__ W, double* __restrict__ iW) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t i;
         const int64_t r = row_of(e, n, i);
         const double v = r == 0 ? T[i] : Y[(r - 1) * ld + i];
+        const double d = rtol * fabs(v) + (r == 0 ? atolT : atolY);
         x0[e] = v;
-        W[e] = 1.0 / (rtol * fabs(v) + (r == 0 ? atolT : atolY));
+        W[e] = 1.0 / d;
+        iW[e] = d;
     }
 }
 
@@ -97,60 +113,92 @@ __global__ void start_kernel(int64_t N, const double* __restrict__ r, double inv
 }
 
 // u = v / W (the unweighted direction)
-__global__ void unscale_kernel(int64_t N, const float* __restrict__ v, const double* __restrict__ W,
+__global__ void unscale_kernel(int64_t N, const float* __restrict__ v, const double* __restrict__ iW,
                                double* __restrict__ u) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-        u[e] = (double)v[e] / W[e];
+        u[e] = widen(v[e]) * iW[e];
 }
 
 // w = A v_j = v_j - dt W (J u), u = v_j / W
 __global__ void form_kernel(int64_t N, const float* __restrict__ vj, const double* __restrict__ Ju,
                             const double* __restrict__ W, double dt, double* __restrict__ w) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-        w[e] = fma(-dt * W[e], Ju[e], (double)vj[e]);
+        w[e] = fma(-dt * W[e], Ju[e], widen(vj[e]));
 }
 
-// FORM: w = A v_j (as form_kernel); else w as given.  Then per-block partial sums of <v_q, w>
-// (q < nv) and |w|^2
-template <bool FORM>
+// Dots <v_q, w> for q in [q0, q0 + nq) (nq <= NVC): per-block partial sums into part[b][q].
+// FORM: this launch first forms w = A v_j = v_j - dt W (J u) (u = v_j / W); else w is read.
+// NORM: also the partial sums of |w|^2, into part[b][nv] (nv = j + 1 basis vectors in all).
+// The dots of a GMRES iteration take ceil(nv / 8) launches of at most 8 vectors each, which
+// keeps the accumulators few and the SMs full (predicated-off double FMAs would still take the
+// FP64 pipe, so the loop bound is NVC, nq rounded up to 4 or 8).
+template <bool FORM, bool NORM, int NVC>
 __global__ void __launch_bounds__(kRedBlk) apply_dots_kernel(int64_t N, const float* __restrict__ V, int64_t vstride,
-                                                             int nv, const double* __restrict__ Ju,
+                                                             int q0, int nq, int nv, const double* __restrict__ Ju,
                                                              const double* __restrict__ W, double dt,
                                                              double* __restrict__ w, double* __restrict__ part) {
-    __shared__ double red[kRedBlk / 32][kMaxDots];
-    double acc[kMaxDots];
+    __shared__ double red[kRedBlk / 32][NVC + 1];
+    double acc[NVC + 1];
 #pragma unroll
-    for (int q = 0; q < kMaxDots; ++q) acc[q] = 0.0;
+    for (int q = 0; q <= NVC; ++q) acc[q] = 0.0;
+    const float* Vq = V + (int64_t)q0 * vstride;
     const float* vj = V + (int64_t)(nv - 1) * vstride;         // the vector the operator was applied to
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
         double we;
         if constexpr (FORM) {
-            we = fma(-dt * W[e], Ju[e], (double)vj[e]);
+            we = fma(-dt * W[e], Ju[e], widen(vj[e]));
             w[e] = we;
         } else {
             we = w[e];
         }
+        if constexpr (NORM) acc[NVC] = fma(we, we, acc[NVC]);
 #pragma unroll
-        for (int q = 0; q < kMaxDots - 1; ++q)
-            if (q < nv) acc[q] = fma((double)V[(int64_t)q * vstride + e], we, acc[q]);
-        acc[kMaxDots - 1] = fma(we, we, acc[kMaxDots - 1]);
+        for (int q = 0; q < NVC; ++q)
+            if (q < nq) acc[q] = fma(widen(Vq[(int64_t)q * vstride + e]), we, acc[q]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < kMaxDots; ++q) {
-        if (q >= nv && q != kMaxDots - 1) continue;
+    for (int q = 0; q <= NVC; ++q) {
+        if (q < NVC ? q >= nq : !NORM) continue;
         double a = acc[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (lane == 0) red[warp][q] = a;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q <= nv; q += blockDim.x) {
-        const int src = q == nv ? kMaxDots - 1 : q;
-        double s = 0.0;
-        for (int w2 = 0; w2 < kRedBlk / 32; ++w2) s += red[w2][src];
-        part[(int64_t)blockIdx.x * kMaxDots + q] = s;
+    const int nout = nq + (NORM ? 1 : 0);
+    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+        const int src = t < nq ? t : NVC;
+        double sum = 0.0;
+        for (int w2 = 0; w2 < kRedBlk / 32; ++w2) sum += red[w2][src];
+        part[(int64_t)blockIdx.x * kMaxDots + (t < nq ? q0 + t : nv)] = sum;
     }
+}
+
+template <bool FORM, bool NORM>
+void dots_launch(int nq, unsigned grid, cudaStream_t s, int64_t N, const float* V, int64_t vstride, int q0, int nv,
+                 const double* Ju, const double* W, double dt, double* w, double* part) {
+    if (nq > 4)
+        apply_dots_kernel<FORM, NORM, 8><<<grid, kRedBlk, 0, s>>>(N, V, vstride, q0, nq, nv, Ju, W, dt, w, part);
+    else
+        apply_dots_kernel<FORM, NORM, 4><<<grid, kRedBlk, 0, s>>>(N, V, vstride, q0, nq, nv, Ju, W, dt, w, part);
+}
+
+// every dot of iteration j (nv = j + 1 basis vectors) and |w|^2 with the first group;
+// FORM: w = A v_j formed by the first launch, else w as given
+template <bool FORM>
+cudaError_t apply_dots(int nv, unsigned grid, cudaStream_t s, int64_t N, const float* V, int64_t vstride,
+                       const double* Ju, const double* W, double dt, double* w, double* part) {
+    for (int q0 = 0; q0 < nv; q0 += 8) {
+        const int nq = std::min(8, nv - q0);
+        if (q0 == 0)
+            dots_launch<FORM, true>(nq, grid, s, N, V, vstride, q0, nv, Ju, W, dt, w, part);
+        else
+            dots_launch<false, false>(nq, grid, s, N, V, vstride, q0, nv, Ju, W, dt, w, part);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // out[q] = sum over blocks of part[b][q], blocks in order (q < nq)
@@ -174,7 +222,7 @@ __global__ void __launch_bounds__(kRedBlk) orth_kernel(int64_t N, const float* _
     double acc = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
         double we = w[e];
-        for (int q = 0; q < nv; ++q) we = fma(-hs[q], (double)V[(int64_t)q * vstride + e], we);
+        for (int q = 0; q < nv; ++q) we = fma(-hs[q], widen(V[(int64_t)q * vstride + e]), we);
         w[e] = we;
         acc = fma(we, we, acc);
     }
@@ -198,7 +246,7 @@ __global__ void normalize_kernel(int64_t N, const double* __restrict__ w, double
 // d = (sum_q y_q v_q) / W; x += d; per-block partial sums of (W d)^2
 __global__ void __launch_bounds__(kRedBlk) update_kernel(int64_t n, int64_t N, int64_t ld, const float* __restrict__ V,
                                                          int64_t vstride, int nv, const double* __restrict__ y,
-                                                         const double* __restrict__ W, double* __restrict__ T,
+                                                         const double* __restrict__ iW, double* __restrict__ T,
                                                          double* __restrict__ Y, double* __restrict__ part) {
     __shared__ double ys[kMaxDots];
     __shared__ double red[kRedBlk / 32];
@@ -207,10 +255,10 @@ __global__ void __launch_bounds__(kRedBlk) update_kernel(int64_t n, int64_t N, i
     double acc = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
         double z = 0.0;
-        for (int q = 0; q < nv; ++q) z = fma(ys[q], (double)V[(int64_t)q * vstride + e], z);
+        for (int q = 0; q < nv; ++q) z = fma(ys[q], widen(V[(int64_t)q * vstride + e]), z);
         int64_t i;
         const int64_t row = row_of(e, n, i);
-        const double d = z / W[e];
+        const double d = z * iW[e];
         if (row == 0)
             T[i] += d;
         else
@@ -230,7 +278,7 @@ __global__ void __launch_bounds__(kRedBlk) update_kernel(int64_t n, int64_t N, i
 
 // ---------------------------------------------------------------- workspace
 struct Work {
-    double *x0, *W, *f, *r, *u, *Ju, *w, *part, *dots;
+    double *x0, *W, *iW, *f, *r, *u, *Ju, *w, *part, *dots;
     float* V;
     double* F;                // block factors (precond only)
     int32_t* piv;             // pivot rows and row exponents of the factors
@@ -259,7 +307,7 @@ int64_t lin_chunk(const DevMech& mech, int64_t n, int linearized) {
 
 size_t work_bytes(const DevMech& mech, int64_t n, int m, int nred, int precond, int linearized) {
     const int64_t N = (int64_t)(mech.K + 1) * n;
-    size_t b = 7 * align256((size_t)N * sizeof(double)) + align256((size_t)(m + 1) * N * sizeof(float)) +
+    size_t b = 8 * align256((size_t)N * sizeof(double)) + align256((size_t)(m + 1) * N * sizeof(float)) +
                align256((size_t)nred * kMaxDots * sizeof(double)) + align256(kMaxDots * sizeof(double));
     if (precond)
         b += align256((size_t)(mech.K + 1) * N * sizeof(double)) + align256((size_t)N * sizeof(int32_t));
@@ -280,6 +328,7 @@ Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precon
     const size_t vb = (size_t)N * sizeof(double);
     w.x0 = reinterpret_cast<double*>(take(vb));
     w.W = reinterpret_cast<double*>(take(vb));
+    w.iW = reinterpret_cast<double*>(take(vb));
     w.f = reinterpret_cast<double*>(take(vb));
     w.r = reinterpret_cast<double*>(take(vb));
     w.u = reinterpret_cast<double*>(take(vb));
@@ -334,7 +383,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         return cudaStreamSynchronize(s);
     };
     std::memset(&st, 0, sizeof st);
-    init_kernel<<<eg, kElemBlk, 0, s>>>(n, N, ld, T, Y, o.rtol, o.atol_T, o.atol_Y, w.x0, w.W);
+    init_kernel<<<eg, kElemBlk, 0, s>>>(n, N, ld, T, Y, o.rtol, o.atol_T, o.atol_Y, w.x0, w.W, w.iW);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const double sqrtN = std::sqrt((double)N);
     std::vector<double> H((size_t)(mk + 1) * mk), cs(mk), sn(mk), g(mk + 1), yv(mk);
@@ -388,7 +437,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         bool solved = false;                       // GMRES met lin_tol (or broke down exactly)
         while (j < mk) {
             const float* vj = w.V + (int64_t)j * w.vstride;
-            unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.W, w.u);
+            unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.iW, w.u);
             e = o.linearized ? launch_rhs_jvp_linearized(m, n, ld, T, p, Y, w.lin, n, w.f, w.f + n, n, w.u, w.u + n,
                                                          w.Ju, w.Ju + n, s)
                              : launch_jvp(m, n, ld, T, p, Y, nullptr, w.u, w.u + n, nullptr, nullptr, w.Ju + n, w.Ju,
@@ -398,11 +447,11 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
                 form_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.Ju, w.W, dt, w.w);
                 if ((e = launch_precond_apply(K + 1, n, w.F, n, w.piv, n, w.w, n, w.w, n, s)) != cudaSuccess)
                     return e;
-                apply_dots_kernel<false><<<nred, kRedBlk, 0, s>>>(N, w.V, w.vstride, j + 1, w.Ju, w.W, dt, w.w, w.part);
+                e = apply_dots<false>(j + 1, nred, s, N, w.V, w.vstride, w.Ju, w.W, dt, w.w, w.part);
             } else {
-                apply_dots_kernel<true><<<nred, kRedBlk, 0, s>>>(N, w.V, w.vstride, j + 1, w.Ju, w.W, dt, w.w, w.part);
+                e = apply_dots<true>(j + 1, nred, s, N, w.V, w.vstride, w.Ju, w.W, dt, w.w, w.part);
             }
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (e != cudaSuccess) return e;
             if ((e = fetch(kMaxDots, j + 2, w.dots, hbuf.data())) != cudaSuccess) return e;
             ++st.krylov_iters;
             // column j of the Hessenberg matrix: the projections, then the norm of the
@@ -451,7 +500,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         }
         if ((e = cudaMemcpyAsync(w.dots, yv.data(), j * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return e;
-        update_kernel<<<nred, kRedBlk, 0, s>>>(n, N, ld, w.V, w.vstride, j, w.dots, w.W, T, Y, w.part);
+        update_kernel<<<nred, kRedBlk, 0, s>>>(n, N, ld, w.V, w.vstride, j, w.dots, w.iW, T, Y, w.part);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = fetch(1, 1, w.dots + kMaxDots - 1, hbuf.data())) != cudaSuccess) return e;
         ++st.newton_iters;
