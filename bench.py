@@ -15,8 +15,8 @@ timed steps); the mixed form, JVP/forward and VJP/forward ratios come from the s
 After the timed steps, the all-double forms of rates and transport (NK_FP64_NATIVE, the
 plain-FP64 arithmetic the FP64 form is checked against), the implicit-stage sources and their
 JVP (nk_rhs_eval, nk_rhs_jvp), the diffusion fluxes (nk_diffusion_fluxes) and the stored
-linearization with one JVP from it (nk_rates_linearize, nk_rates_jvp_linearized) are timed
-the same way in a separate loop
+linearization with one JVP from it (nk_rates_linearize, nk_rates_jvp_linearized; and rounded
+to float with a single-precision JVP, the _f32 entries) are timed the same way in a separate loop
 ("fp64_native_value", rows); they are not part of a step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -103,6 +103,7 @@ def algorithmic_flops(mech) -> dict:
             "rates_jit": rates,
             "transport_fp64_native": transport, "rates_mixed": rates, "transport_mixed": transport, "jvp": jvp,
             "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp, "linearize": jvp, "jvp_linearized": jvp_lin,
+            "linearize_f32": jvp, "jvp_linearized_f32": jvp_lin,
             "diffusion": K * (3 + 6 + 6 + 9 + 10) + 12}
 
 
@@ -376,14 +377,15 @@ def reactor_states(nk, m, mech, n, dev, seed=6053):
 def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9, dt_large=1e-5):
     """One implicit Euler step over n near-equilibrium points (nk_reactor_step), each after one
     untimed step from the same states; CUDA events on the launching stream.  The paper's
-    unpreconditioned GMRES at dt (products recomputing the rates, and from a stored linearization
-    per Newton iteration), and with the per-point block-Jacobi preconditioner at dt and at
+    unpreconditioned GMRES at dt (products recomputing the rates, from a stored linearization per
+    Newton iteration, and from that linearization rounded to float in single precision), and with the per-point block-Jacobi preconditioner at dt and at
     dt_large, each with its set-up (precond 1) and with the factors of the previous call reused
     (precond 2, as a stiff ODE solver keeps its Newton matrix over steps)."""
     import torch
     T0, p, Y0 = reactor_states(nk, m, mech, n, dev)
     kw = dict(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=20, krylov_dim=30)
-    ws = torch.empty(nk.reactor_workspace(m, n, kw["krylov_dim"], 1, 1), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(nk.reactor_workspace(m, n, kw["krylov_dim"], 1, 1),
+                         nk.reactor_workspace(m, n, kw["krylov_dim"], 0, 2)), dtype=torch.uint8, device=dev)
     T, Y = T0.clone(), Y0.clone()
 
     def run(step, precond, linearized=0):
@@ -406,6 +408,7 @@ def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9, dt_large=1e-5):
                        f"GMRES(30), rtol 1e-6, atol_T 1e-6, atol_Y 1e-12, newton_tol 1e-4, lin_tol 1e-6"}
     res.update(run(dt, 0))
     res["linearized"] = run(dt, 0, 1)
+    res["linearized_f32"] = run(dt, 0, 2)
     res["block_jacobi"] = run(dt, 1)
     res["block_jacobi_linearized"] = run(dt, 1, 1)
     res["block_jacobi_reused"] = run(dt, 2)
@@ -445,7 +448,8 @@ def run_ours(args):
                                                "dh", "gT")}
     out.update({k: torch.empty((K, n), **f64) for k in ("w", "D", "w_m", "D_m", "dw", "gY")})
     g_lnA = torch.empty(R, **f64)
-    lin = torch.empty((nk.linearization_slots(m), n), **f64)    # stored linearization (~15 KB per point)
+    lin = torch.empty((nk.linearization_slots(m), n), **f64)    # stored linearization (~18 KB per point)
+    lin32 = torch.empty((nk.linearization_slots_f32(m), n), dtype=torch.float32, device=dev)   # single precision
     gradX = torch.randn((3, K, n), generator=gen, **f64)         # mole-fraction gradients (synthetic)
     jflux = torch.empty((3, K, n), **f64)
     Vc = torch.empty((3, n), **f64)
@@ -490,6 +494,10 @@ def run_ours(args):
         "jvp_linearized": lambda: chk(L.nk_rates_jvp_linearized(h, n, n, P(T), P(p), P(Y), P(lin), n, P(vT), P(vY),
                                                                 P(out["dw"]), P(out["dh"]), sp)),
         "rates_jit": lambda: chk(L.nk_rates_eval(h, n, n, P(T), P(p), P(Y), None, P(out["w"]), P(out["hrr"]), 3, sp)),
+        "linearize_f32": lambda: chk(L.nk_rates_linearize_f32(h, n, n, P(T), P(p), P(Y), None, P(lin32), n, sp)),
+        "jvp_linearized_f32": lambda: chk(L.nk_rates_jvp_linearized_f32(h, n, n, P(T), P(p), P(Y), P(lin32), n,
+                                                                        P(vT), P(vY), P(out["dw"]), P(out["dh"]),
+                                                                        sp)),
     }
     # the mechanism-specialised kernel is compiled (NVRTC) before any timing
     t_jit = time.perf_counter()

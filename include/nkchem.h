@@ -252,6 +252,32 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
                                   nk_stream stream);
 
 /*
+ * The same stored linearization in single precision, and products from it with the reaction
+ * terms in single precision (FP32 pipe) and their sums per species in double.  For Krylov
+ * solvers whose basis is single precision (as the paper's GMRES, Sec. 2): the products then
+ * carry rounding of the order the basis already has.
+ *   *slots   32-bit words per point (nk_rates_linearization_slots_f32; about half the bytes)
+ *   lin      device float [slots][ldl], ldl >= n, caller-owned; written by nk_rates_linearize_f32
+ * Each reaction's coefficients are stored rounded to float after scaling by a power of two
+ * per reaction and point (kept beside them), so rates of any magnitude fit; coefficients below
+ * 2^-126 of their reaction's largest are dropped.  Each result is within about (8 + 2) 2^-24 of
+ * the sum of the magnitudes of the terms it adds (against 2^-53 for the double entries); the
+ * inputs are rounded to float without subnormals.  The rhs form takes the sources at the
+ * state, as nk_rhs_jvp_linearized.
+ */
+nk_status nk_rates_linearization_slots_f32(const nk_mech* mech, int64_t* slots);
+nk_status nk_rates_linearize_f32(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                                 const double* Y, const double* dlnA, float* lin, int64_t ldl, nk_stream stream);
+nk_status nk_rates_jvp_linearized_f32(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                                      const double* p, const double* Y, const float* lin, int64_t ldl,
+                                      const double* vT, const double* vY, double* d_omega, double* d_hrr,
+                                      nk_stream stream);
+nk_status nk_rhs_jvp_linearized_f32(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                                    const double* Y, const float* lin, int64_t ldl, const double* fT,
+                                    const double* fY, const double* vT, const double* vY, double* dfT,
+                                    double* dfY, nk_stream stream);
+
+/*
  * Rates (nk_rates_eval) and transport (nk_transport_eval) of fields that live in host memory,
  * the library's end-to-end entry: the points are cut into chunks of `chunk`, each copied to
  * the device, evaluated and copied back, the chunks cycling over three internal streams so that
@@ -346,7 +372,7 @@ nk_status nk_rhs_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, cons
  *                  also (K+1)^2 n doubles of factors, (K+1) n pivot words and a stored
  *                  linearization of up to about 2 GB, filled chunk by chunk; with linearized
  *                  products the full stored linearization, nk_rates_linearization_slots x n
- *                  doubles)
+ *                  doubles, or floats for linearized = 2)
  * With precond = 1 the solve is left-preconditioned by the per-point blocks of
  * nk_block_jacobi_factor, made once per step at x0: GMRES minimises P^-1 (r - A z), which
  * tracks the error of the update (the unpreconditioned residual of stiff chemistry is dominated
@@ -374,7 +400,12 @@ typedef struct {
     int32_t linearized;   /* 0: every GMRES product recomputes the rates (nk_rhs_jvp); 1: the rates
                              are linearized once per Newton iteration and the products come from
                              the stored data (nk_rhs_jvp_linearized): cheaper once a Newton
-                             iteration takes more than one or two GMRES iterations */
+                             iteration takes more than one or two GMRES iterations; 2: as 1 with
+                             the linearization in single precision and the products from it
+                             (nk_rhs_jvp_linearized_f32), matching the FP32 basis; the residuals,
+                             and so the converged state, stay double.  2 needs precond = 0: the
+                             preconditioned operator P^-1 A would amplify the products' rounding
+                             by the blocks' condition numbers (~1e29 for stiff chemistry) */
 } nk_reactor_opts;
 typedef struct {
     int32_t converged;    /* 1 when the update test was met (0: max_newton reached, or the

@@ -94,6 +94,11 @@ _SIGS = {
     "nk_rhs_jvp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [_vp]),
     "nk_rates_linearization_slots": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "nk_rates_linearize": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "nk_rates_linearize_f32": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "nk_rates_linearization_slots_f32": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "nk_rates_jvp_linearized_f32": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                                                   _vp]),
+    "nk_rhs_jvp_linearized_f32": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64] + [_vp] * 6 + [_vp]),
     "nk_rates_jvp_linearized": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                                _vp]),
     "nk_rates_vjp_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
@@ -380,7 +385,8 @@ def reactor_opts(rtol=1e-6, atol_T=1e-6, atol_Y=1e-14, newton_tol=0.1, lin_tol=1
                  krylov_dim=20, precond=0, linearized=0) -> _ReactorOpts:
     """Options of nk_reactor_step (weighted RMS tolerances; precond 1 = per-point block Jacobi
     made at x0, 2 = its factors from the last call reused; linearized 1 = GMRES products from a
-    stored linearization per Newton iteration; see include/nkchem.h)."""
+    stored linearization per Newton iteration, 2 = the same rounded to float with
+    single-precision products; see include/nkchem.h)."""
     return _ReactorOpts(rtol, atol_T, atol_Y, newton_tol, lin_tol, max_newton, krylov_dim, precond, linearized)
 
 
@@ -400,7 +406,7 @@ def reactor_step(m: Mechanism, T, p, Y, dt: float, opts: _ReactorOpts = None, wo
         raise ValueError("reactor_step takes a contiguous Y [K, n]")
     opts = opts or reactor_opts()
     if workspace is None and n > 0 and 1 <= opts.krylov_dim <= 30 and opts.precond in (0, 1, 2) \
-            and opts.linearized in (0, 1):
+            and opts.linearized in (0, 1, 2):
         workspace = torch.empty(reactor_workspace(m, n, opts.krylov_dim, opts.precond, opts.linearized),
                                 dtype=torch.uint8, device=T.device)
     st = _ReactorStats()
@@ -489,6 +495,60 @@ def rates_jvp_linearized(m: Mechanism, T, p, Y, lin, vT, vY, stream=None):
     return d_omega, d_hrr
 
 
+def linearization_slots_f32(m: Mechanism) -> int:
+    """32-bit words per point of the single-precision rates linearization."""
+    v = _i64()
+    _check(lib().nk_rates_linearization_slots_f32(m.handle, ctypes.byref(v)))
+    return v.value
+
+
+def rates_linearize_f32(m: Mechanism, T, p, Y, dlnA=None, lin=None, stream=None):
+    """nk_rates_linearize_f32: the rates linearization in single precision (per-reaction power-
+    of-two scales), a device float32 tensor [slots_f32, n] for the single-precision products."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _vec(dlnA, m.R, "dlnA")
+    if lin is None:
+        lin = torch.empty((linearization_slots_f32(m), max(n, 1)), dtype=torch.float32, device=T.device)
+    _check_lin(m, lin, n, torch.float32)
+    _check(lib().nk_rates_linearize_f32(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(dlnA), _ptr(lin),
+                                        lin.stride(0), _stream(stream)))
+    return lin
+
+
+def rates_jvp_linearized_f32(m: Mechanism, T, p, Y, lin, vT, vY, stream=None):
+    """nk_rates_jvp_linearized_f32: (d_omega, d_hrr) = J (vT, vY) in single precision from
+    rates_linearize_f32 (results in float64 tensors)."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    _check_lin(m, lin, n, torch.float32)
+    d_omega = _species_out(m, n, ld, T)
+    d_hrr = _point_out(n, T)
+    _check(lib().nk_rates_jvp_linearized_f32(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0),
+                                             _ptr(vT), _ptr(vY), _ptr(d_omega), _ptr(d_hrr), _stream(stream)))
+    return d_omega, d_hrr
+
+
+def rhs_jvp_linearized_f32(m: Mechanism, T, p, Y, lin, fT, fY, vT, vY, stream=None):
+    """nk_rhs_jvp_linearized_f32: (dfT, dfY) = J_f (vT, vY) in single precision from
+    rates_linearize_f32 and the sources at the same state."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _check_lin(m, lin, n, torch.float32)
+    _vec(fT, n, "fT")
+    _species_in(m, fY, n, ld, "fY")
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    dfY = _species_out(m, n, ld, T)
+    dfT = _point_out(n, T)
+    _check(lib().nk_rhs_jvp_linearized_f32(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin), lin.stride(0),
+                                           _ptr(fT), _ptr(fY), _ptr(vT), _ptr(vY), _ptr(dfT), _ptr(dfY),
+                                           _stream(stream)))
+    return dfT, dfY
+
+
 def rhs_jacobian(m: Mechanism, T, p, Y, lin, fT, fY, stream=None):
     """nk_rhs_jacobian: the dense Jacobian [K+1, K+1, n] of the sources (rows fT, fY_k; columns
     T, Y_j) from a stored linearization (rates_linearize) and the sources (rhs_eval, fp64) at
@@ -542,9 +602,14 @@ def block_jacobi_apply(m: Mechanism, F, piv, v, stream=None):
     return z
 
 
-def _check_lin(m, lin, n):
-    if lin.dim() != 2 or lin.shape[0] != linearization_slots(m) or lin.stride(1) != 1 or lin.shape[1] < n:
-        raise ValueError("lin must be a [slots, >= n] row-major tensor from rates_linearize")
+def _check_lin(m, lin, n, dtype=None):
+    import torch
+    dtype = dtype or torch.float64
+    slots = linearization_slots(m) if dtype == torch.float64 else linearization_slots_f32(m)
+    if lin.dtype != dtype:
+        raise ValueError(f"lin must be {dtype}, got {lin.dtype}")
+    if lin.dim() != 2 or lin.shape[0] != slots or lin.stride(1) != 1 or lin.shape[1] < n:
+        raise ValueError("lin must be a [slots, >= n] row-major tensor from rates_linearize(_f32)")
 
 
 def rates_vjp_workspace(m: Mechanism, n: int) -> int:

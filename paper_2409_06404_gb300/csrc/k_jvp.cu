@@ -88,7 +88,7 @@ __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const doub
     dfl dG, dH, dCp;
     rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
     const double sumh = df_to_d(dH), sumcp = df_to_d(dCp);
-    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, (float)x.dnu), df_neg(dG));
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
     const double dlnKc = Q.tT * (sumh - x.dnu);
 
     double shift = 0.0;

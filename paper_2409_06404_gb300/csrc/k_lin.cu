@@ -38,6 +38,10 @@ namespace {
 __host__ __device__ inline int64_t slot_M(const DevMech& m) { return (int64_t)m.R + m.lin_nb; }
 __host__ __device__ inline int64_t slot_S(const DevMech& m) { return slot_M(m) + (m.R - m.R_el); }
 __host__ __device__ inline int64_t slot_H(const DevMech& m) { return slot_S(m) + 1; }
+// the float format: S1 as the two 32-bit words of its double, h_k/RT, then one exponent word per
+// reaction (the reaction's coefficients are stored scaled by 2^-e_r)
+__host__ __device__ inline int64_t slot_H32(const DevMech& m) { return slot_S(m) + 2; }
+__host__ __device__ inline int64_t slot_E32(const DevMech& m) { return slot_H32(m) + m.K; }
 
 // prod of p[0..n) (returned) and, in ex[e], the product of all entries but e (n <= 4, uniform)
 __device__ __forceinline__ double exclusive_products(const double* p, int n, double* ex) {
@@ -72,10 +76,68 @@ struct LinPoint {
     double invT, lnT, pRT;
 };
 
+// a stored value: as is, or rounded to float (integer operations: no FP64-pipe conversion)
+__device__ __forceinline__ void put(double* q, double v) { *q = v; }
+__device__ __forceinline__ void put(float* q, double v) { *q = narrow(v); }
+
+// biased exponent field of a double (0 for zero and subnormals)
+__device__ __forceinline__ int bexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7ff); }
+
+// v 2^-e rounded to float, by integer operations on the bits (v's exponent field minus e; below
+// the normal float range a signed zero; infinities and NaN as they are)
+__device__ __forceinline__ float narrow_scaled(double v, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int field = (int)((b >> 52) & 0x7ff);
+    if (field == 0x7ff) return narrow(v);
+    const int ex = field - e;
+    if (field == 0 || ex < 897) return __uint_as_float((unsigned int)(b >> 32) & 0x80000000u);
+    return narrow(__longlong_as_double((long long)((b & ~(0x7ffULL << 52)) | ((unsigned long long)ex << 52))));
+}
+
+// The coefficients of reaction r at point i: A (slot r), the entries' B (reactants at Bv[e],
+// products at Bv[kMaxSide + e]), L (third-body and Troe).  Double storage as computed; float
+// storage scaled by 2^-e_r, e_r the largest binary exponent among them (so they fit the float
+// range whatever the reaction's magnitude -- rates of progress of stiff mechanisms span far more
+// than it), with e_r in the reaction's exponent word.
+template <int KIND>
+__device__ __forceinline__ void store_coef(const DevMech& m, int r, double* lin, int64_t ldl, int64_t i, int nr,
+                                           int np, double Av, const double* Bv, double Lv) {
+    lin[(int64_t)r * ldl + i] = Av;
+    double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        if (e < nr) B[(int64_t)e * ldl] = Bv[e];
+        if (e < np) B[(int64_t)(nr + e) * ldl] = Bv[kMaxSide + e];
+    }
+    if (KIND != 0) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = Lv;
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_coef(const DevMech& m, int r, float* lin, int64_t ldl, int64_t i, int nr,
+                                           int np, double Av, const double* Bv, double Lv) {
+    int mx = bexp(Av);
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        if (e < nr) mx = max(mx, bexp(Bv[e]));
+        if (e < np) mx = max(mx, bexp(Bv[kMaxSide + e]));
+    }
+    if (KIND != 0) mx = max(mx, bexp(Lv));
+    const int er = mx == 0 ? 0 : mx - 1023;           // largest |coefficient| in [1, 2) after scaling
+    lin[(int64_t)r * ldl + i] = narrow_scaled(Av, er);
+    float* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        if (e < nr) B[(int64_t)e * ldl] = narrow_scaled(Bv[e], er);
+        if (e < np) B[(int64_t)(nr + e) * ldl] = narrow_scaled(Bv[kMaxSide + e], er);
+    }
+    if (KIND != 0) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = narrow_scaled(Lv, er);
+    reinterpret_cast<int32_t*>(lin)[(slot_E32(m) + r) * ldl + i] = er;
+}
+
 // ---------------------------------------------------------------- linearization pass
-template <int BLK, int KIND>
+template <int BLK, int KIND, class TS>
 __device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const double* sC, const LinPoint& Q,
-                                             const double* dlnA, const DfTab& dt, double* __restrict__ lin,
+                                             const double* dlnA, const DfTab& dt, TS* __restrict__ lin,
                                              int64_t ldl, int64_t i, bool live, double& S1) {
     const Rxn x = load_rxn(m.rxn + r);
     double cR[kMaxSide], pR[kMaxSide], cP[kMaxSide], pP[kMaxSide];
@@ -104,7 +166,7 @@ __device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const doub
     dfl dG, dH, dCp;
     rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
     const double sumh = df_to_d(dH), sumcp = df_to_d(dCp);
-    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, (float)x.dnu), df_neg(dG));
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
     double shift = 0.0;
     dfl shiftd{0.0f, 0.0f};
     if (dlnA) {
@@ -167,46 +229,47 @@ __device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const doub
     const double sc = KIND == 1 ? M : 1.0;              // third body: q = q_c [M]
     S1 = fma(qc * sc, sumcp, S1);
     if (!live) return;
-    lin[(int64_t)r * ldl + i] = sc * fma(qc, aT, qr * D);
-    double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+    double Bv[2 * kMaxSide];
 #pragma unroll
-    for (int e = 0; e < kMaxSide; ++e)
+    for (int e = 0; e < kMaxSide; ++e) {
+        Bv[e] = Bv[kMaxSide + e] = 0.0;
         if (e < x.nr) {
             double d = exR[e];                            // d fw / d C_e = nu C_e^(nu-1) prod_{f!=e}
             if (x.nu[e] > 1) {
                 d *= -x.nud[e];
                 for (int j = 1; j < x.nu[e]; ++j) d *= cR[e];
             }
-            B[(int64_t)e * ldl] = sc * kf * d;
+            Bv[e] = sc * kf * d;
         }
-#pragma unroll
-    for (int e = 0; e < kMaxSide; ++e)
         if (e < x.np) {
             double d = exP[e];
             if (x.nu[kMaxSide + e] > 1) {
                 d *= x.nud[kMaxSide + e];
                 for (int j = 1; j < x.nu[kMaxSide + e]; ++j) d *= cP[e];
             }
-            B[(int64_t)(x.nr + e) * ldl] = -sc * kr * d;
+            Bv[kMaxSide + e] = -sc * kr * d;
         }
-    if (KIND == 1) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = qc;
-    if (KIND == 2) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = qc * aM;
+    }
+    store_coef<KIND>(m, r, lin, ldl, i, x.nr, x.np, sc * fma(qc, aT, qr * D), Bv,
+                     KIND == 1 ? qc : (KIND == 2 ? qc * aM : 0.0));
 }
 
-template <int BLK, int KIND>
+template <int BLK, int KIND, class TS>
 __device__ __forceinline__ void lin_group(const DevMech& m, int r0, int r1, const double* sC, const LinPoint& Q,
-                                          const double* dlnA, const DfTab& dt, double* lin, int64_t ldl, int64_t i,
+                                          const double* dlnA, const DfTab& dt, TS* lin, int64_t ldl, int64_t i,
                                           bool live, double& S1) {
     for (int r = r0; r < r1; ++r) lin_reaction<BLK, KIND>(m, r, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
 }
 
-template <int BLK, int NP>
+// TS: the stored type (double, or float for the single-precision products)
+template <int BLK, int NP, class TS>
 __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                              const double* __restrict__ T,
                                                              const double* __restrict__ p,
                                                              const double* __restrict__ Y,
                                                              const double* __restrict__ dlnA,
-                                                             double* __restrict__ lin, const int64_t ldl) {
+                                                             TS* __restrict__ lin, const int64_t ldl) {
+    constexpr bool F32 = sizeof(TS) == sizeof(float);
     extern __shared__ double smem[];
     const DfTab dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
     __syncthreads();
@@ -229,7 +292,8 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
     const double rho = Q.pRT / s;
     for (int k = part; k < K; k += NP) {
         sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
-        if (live) lin[(slot_H(m) + k) * ldl + i] = nasa_hRT(nasa_range(m, k, Ti), Ti, Q.invT);
+        if (live)
+            put(lin + ((F32 ? slot_H32(m) : slot_H(m)) + k) * ldl + i, nasa_hRT(nasa_range(m, k, Ti), Ti, Q.invT));
     }
     if (NP > 1) __syncthreads();
 
@@ -251,7 +315,14 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
 #pragma unroll
         for (int q = 1; q < NP; ++q) S1 += sC[q * BLK];
     }
-    if (live) lin[slot_S(m) * ldl + i] = S1;
+    if (!live) return;
+    if constexpr (F32) {                           // S1 in full: the two words of the double
+        const unsigned long long b = (unsigned long long)__double_as_longlong(S1);
+        reinterpret_cast<uint32_t*>(lin)[slot_S(m) * ldl + i] = (uint32_t)b;
+        reinterpret_cast<uint32_t*>(lin)[(slot_S(m) + 1) * ldl + i] = (uint32_t)(b >> 32);
+    } else {
+        lin[slot_S(m) * ldl + i] = S1;
+    }
 }
 
 // ---------------------------------------------------------------- apply pass (one direction)
@@ -425,6 +496,239 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
     }
 }
 
+// ---------------------------------------------------------------- FP32 apply pass
+// The same contraction from the float linearization: each reaction's dq_r in single precision
+// from its scaled coefficients (FP32 pipe, about 60 times the FP64 pipe's rate on GB300, and half
+// the bytes), brought to double with its exponent e_r by integer operations, and scattered into
+// the omega_k tangents in double (the only FP64 arithmetic per reaction).  Meant for Krylov
+// solvers whose basis is FP32 anyway: the products carry rounding of the order the basis
+// already has.  The point terms (rho, d rho/rho, dC_k, c_p) are formed in float from the double
+// inputs, rounded by integer operations.
+constexpr float kInvRf = (float)(1.0 / 8.314462618);
+
+struct Rxn32 {
+    int nr, np, eff0, eff1;
+    int sp[2 * kMaxSide];
+    float nud[2 * kMaxSide];
+};
+
+__device__ __forceinline__ Rxn32 load_rxn32(const DevMech& m, int r) {
+    Rxn32 x;
+    const int4* q = reinterpret_cast<const int4*>(m.rxn + r) + 6;
+    const int4 h = __ldg(q), h2 = __ldg(q + 1), s0 = __ldg(q + 2), s1 = __ldg(q + 3);
+    x.nr = h.y;
+    x.np = h.z;
+    x.eff0 = h2.y;
+    x.eff1 = h2.z;
+    x.sp[0] = s0.x; x.sp[1] = s0.y; x.sp[2] = s0.z; x.sp[3] = s0.w;
+    x.sp[4] = s1.x; x.sp[5] = s1.y; x.sp[6] = s1.z; x.sp[7] = s1.w;
+    const float4* f = reinterpret_cast<const float4*>(m.f_nud + (size_t)r * 2 * kMaxSide);
+    const float4 a = __ldg(f), b = __ldg(f + 1);
+    x.nud[0] = a.x; x.nud[1] = a.y; x.nud[2] = a.z; x.nud[3] = a.w;
+    x.nud[4] = b.x; x.nud[5] = b.y; x.nud[6] = b.z; x.nud[7] = b.w;
+    return x;
+}
+
+struct LinCoef32 {
+    float A, L;
+    float Br[kMaxSide], Bp[kMaxSide];
+    int e;                                  // the reaction's exponent: coefficients x 2^e
+};
+
+template <int KIND>
+__device__ __forceinline__ LinCoef32 load_coef32(const DevMech& m, int r, const float* __restrict__ lin, int64_t ldl,
+                                                 int64_t i, int nr, int np) {
+    LinCoef32 c;
+    c.A = lin[(int64_t)r * ldl + i];
+    const float* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {
+        c.Br[e] = e < nr ? B[(int64_t)e * ldl] : 0.0f;
+        c.Bp[e] = e < np ? B[(int64_t)(nr + e) * ldl] : 0.0f;
+    }
+    c.L = KIND != 0 ? lin[(slot_M(m) + (r - m.R_el)) * ldl + i] : 0.0f;
+    c.e = reinterpret_cast<const int32_t*>(lin)[(slot_E32(m) + r) * ldl + i];
+    return c;
+}
+
+// v 2^e for a double v, by adding e to its exponent field (zero stays zero; the result flushes to
+// a signed zero below the normal range and becomes inf above it)
+__device__ __forceinline__ double scale2(double v, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int field = (int)((b >> 52) & 0x7ff);
+    if (field == 0 || field == 0x7ff) return v;
+    const int ex = field + e;
+    const unsigned long long sign = b & 0x8000000000000000ULL;
+    if (ex <= 0) return __longlong_as_double((long long)sign);
+    if (ex >= 0x7ff) return __longlong_as_double((long long)(sign | (0x7ffULL << 52)));
+    return __longlong_as_double((long long)((b & ~(0x7ffULL << 52)) | ((unsigned long long)ex << 52)));
+}
+
+template <int BLK, int KIND>
+__device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, const float* sdC, double* sD,
+                                              const float* __restrict__ lin, int64_t ldl, int64_t i, float tT,
+                                              float dpRT) {
+    if (r0 >= r1) return;
+    Rxn32 x = load_rxn32(m, r0);
+    LinCoef32 c = load_coef32<KIND>(m, r0, lin, ldl, i, x.nr, x.np);
+    for (int r = r0; r < r1; ++r) {
+        Rxn32 xn;
+        LinCoef32 cn;
+        if (r + 1 < r1) {
+            xn = load_rxn32(m, r + 1);
+            cn = load_coef32<KIND>(m, r + 1, lin, ldl, i, xn.nr, xn.np);
+        }
+        float dq = c.A * tT;
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.nr) dq = fmaf(c.Br[e], sdC[x.sp[e] * BLK], dq);
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.np) dq = fmaf(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
+        if (KIND != 0) {
+            float dM = dpRT;
+            for (int j = x.eff0; j < x.eff1; ++j)
+                dM = fmaf(__ldg(m.f_eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
+            dq = fmaf(c.L, dM, dq);
+        }
+        const double dqd = scale2(widen(dq), c.e);
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.nr) {
+                double* w = sD + x.sp[e] * BLK;
+                *w = fma(widen(x.nud[e]), dqd, *w);
+            }
+#pragma unroll
+        for (int e = 0; e < kMaxSide; ++e)
+            if (e < x.np) {
+                double* w = sD + x.sp[kMaxSide + e] * BLK;
+                *w = fma(widen(x.nud[kMaxSide + e]), dqd, *w);
+            }
+        if (r + 1 < r1) {
+            x = xn;
+            c = cn;
+        }
+    }
+}
+
+// Shared memory: NP rows of d omega_k partials (double), dC_k (float), 3 NP sums per point.
+__host__ __device__ constexpr size_t lin32_smem(int K, int blk, int np) {
+    return (size_t)np * K * blk * sizeof(double) + (((size_t)K * blk * sizeof(float) + 7) & ~size_t(7)) +
+           (size_t)3 * np * blk * sizeof(double);
+}
+
+template <int BLK, int NP, bool RHS>
+__global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                             const double* __restrict__ T,
+                                                             const double* __restrict__ p,
+                                                             const double* __restrict__ Y,
+                                                             const float* __restrict__ lin, const int64_t ldl,
+                                                             const double* __restrict__ vT,
+                                                             const double* __restrict__ vY,
+                                                             double* __restrict__ d_omega,
+                                                             double* __restrict__ d_hrr,
+                                                             const double* __restrict__ fT,
+                                                             const double* __restrict__ fY, const int64_t ldf) {
+    extern __shared__ double smd[];
+    const int K = m.K;
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;
+    double* sD0 = smd + slot;                                    // d omega_k partials, part q at row q
+    double* sD = sD0 + (size_t)part * K * BLK;
+    float* sdC = reinterpret_cast<float*>(smd + (size_t)NP * K * BLK) + slot;   // dC_k
+    double* sR = smd + (lin32_smem(K, BLK, NP) / sizeof(double) - (size_t)3 * NP * BLK) + slot;  // part sums
+
+    const double Td = T[i], dTd = vT[i];
+    const float Ti = narrow(Td), dT = narrow(dTd);
+    const float invT = 1.0f / Ti, tT = dT * invT;
+    const float pRT = narrow(p[i]) * invT * kInvRf;
+    float s = 0.0f, ds = 0.0f;
+    for (int k = 0; k < K; ++k) {
+        const float iw = __ldg(m.f_invW + k);
+        s = fmaf(narrow(Y[(int64_t)k * ld + i]), iw, s);
+        ds = fmaf(narrow(vY[(int64_t)k * ld + i]), iw, ds);
+    }
+    const float rho = pRT / s;
+    const float arho = -tT - ds / s;                             // d rho / rho
+    for (int k = part; k < K; k += NP) {
+        const float iw = __ldg(m.f_invW + k);
+        sdC[k * BLK] = fmaf(narrow(Y[(int64_t)k * ld + i]) * iw * rho, arho, rho * narrow(vY[(int64_t)k * ld + i]) * iw);
+    }
+    for (int k = 0; k < K; ++k) sD[k * BLK] = 0.0;
+    if (NP > 1) __syncthreads();
+
+    const float dpRT = -pRT * tT;
+    int a, b;
+    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+    slice<NP>(0, e1, part, a, b);
+    apply_group32<BLK, 0>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    slice<NP>(e1, t1, part, a, b);
+    apply_group32<BLK, 1>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    slice<NP>(t1, m.R, part, a, b);
+    apply_group32<BLK, 2>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    if (NP > 1) __syncthreads();
+
+    double hsum = 0.0;
+    float cpm = 0.0f, dcpm = 0.0f;
+    const float inv_rho = RHS ? 1.0f / rho : 0.0f;
+    const double arho_d = widen(arho);
+    for (int k = part; k < K; k += NP) {
+        double dw = sD0[k * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
+        hsum = fma(widen(lin[(slot_H32(m) + k) * ldl + i]), dw, hsum);
+        if constexpr (RHS) {
+            // NASA range on the doubles' bit patterns (T, T_mid > 0), as the double kernels choose it
+            const bool lo = __double_as_longlong(Td) <= __ldg(reinterpret_cast<const long long*>(m.Tmid) + k);
+            const float* cf = m.f_cp + ((size_t)k * 2 + (lo ? 0 : 1)) * 8;
+            const float4 c = __ldg(reinterpret_cast<const float4*>(cf));
+            const float a5 = __ldg(cf + 4);
+            const float cpk = fmaf(Ti, fmaf(Ti, fmaf(Ti, fmaf(Ti, a5, c.w), c.z), c.y), c.x);
+            const float dcpk = fmaf(Ti, fmaf(Ti, fmaf(Ti, 4.0f * a5, 3.0f * c.w), 2.0f * c.z), c.y);
+            const float iw = __ldg(m.f_invW + k);
+            const float yk = narrow(Y[(int64_t)k * ld + i]) * iw, vk = narrow(vY[(int64_t)k * ld + i]) * iw;
+            cpm = fmaf(yk, cpk, cpm);
+            dcpm = fmaf(vk, cpk, fmaf(yk * dcpk, dT, dcpm));
+            dw = fma(widen(inv_rho / iw), dw, -fY[(int64_t)k * ldf + i] * arho_d);
+        }
+        if (live) d_omega[(int64_t)k * ld + i] = dw;
+    }
+    if constexpr (NP > 1) {
+        sR[part * BLK] = hsum;
+        if constexpr (RHS) {
+            sR[(NP + part) * BLK] = widen(cpm);
+            sR[(2 * NP + part) * BLK] = widen(dcpm);
+        }
+        __syncthreads();
+        if (part != 0) return;
+        hsum = sR[0];
+        double cpd = RHS ? sR[NP * BLK] : 0.0, dcpd = RHS ? sR[2 * NP * BLK] : 0.0;
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            hsum += sR[q * BLK];
+            if constexpr (RHS) {
+                cpd += sR[(NP + q) * BLK];
+                dcpd += sR[(2 * NP + q) * BLK];
+            }
+        }
+        cpm = narrow(cpd);
+        dcpm = narrow(dcpd);
+    }
+    if (live) {
+        const uint32_t lo = reinterpret_cast<const uint32_t*>(lin)[slot_S(m) * ldl + i];
+        const uint32_t hi = reinterpret_cast<const uint32_t*>(lin)[(slot_S(m) + 1) * ldl + i];
+        const double S1 = __hiloint2double((int)hi, (int)lo);
+        const double dhr = -kR * fma(dTd, S1, Td * hsum);
+        if constexpr (RHS)
+            d_hrr[i] = fma(dhr, widen(inv_rho / (8.314462618f * cpm)), -fT[i] * widen(arho + dcpm / cpm));
+        else
+            d_hrr[i] = dhr;
+    }
+}
+
 // ---------------------------------------------------------------- launch shapes
 struct Shape {
     int blk, np;
@@ -432,15 +736,22 @@ struct Shape {
 constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-// MODE 0: the linearization pass; 1: the JVP from it; 2: the sources' JVP from it
+// MODE 0: the linearization pass; 1: the JVP from it; 2: the sources' JVP from it; 3, 4: the
+// same two in single precision from 5: the linearization rounded to float
 template <int MODE, int S>
 constexpr auto kernel_of() {
     if constexpr (MODE == 1)
         return jvp_lin_kernel<kShapes[S].blk, kShapes[S].np, false>;
     else if constexpr (MODE == 2)
         return jvp_lin_kernel<kShapes[S].blk, kShapes[S].np, true>;
+    else if constexpr (MODE == 3)
+        return jvp_lin32_kernel<kShapes[S].blk, kShapes[S].np, false>;
+    else if constexpr (MODE == 4)
+        return jvp_lin32_kernel<kShapes[S].blk, kShapes[S].np, true>;
+    else if constexpr (MODE == 5)
+        return linearize_kernel<kShapes[S].blk, kShapes[S].np, float>;
     else
-        return linearize_kernel<kShapes[S].blk, kShapes[S].np>;
+        return linearize_kernel<kShapes[S].blk, kShapes[S].np, double>;
 }
 
 template <int MODE, int... S>
@@ -449,10 +760,12 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
     return ptrs[idx];
 }
 
-// linearization: the pair tables and C_k; apply: dC_k and NP rows of d omega_k partials
-size_t lin_smem(int K, const Shape& sh, bool apply) {
-    return apply ? (size_t)(1 + sh.np) * K * sh.blk * sizeof(double)
-                 : (size_t)kMathTabDoubles * sizeof(double) + (size_t)K * sh.blk * sizeof(double);
+// linearization: the pair tables and C_k; apply: dC_k and NP rows of d omega_k partials (and
+// the part sums of the single-precision apply)
+size_t lin_smem(int K, const Shape& sh, int mode) {
+    if (mode == 0 || mode == 5) return (size_t)kMathTabDoubles * sizeof(double) + (size_t)K * sh.blk * sizeof(double);
+    if (mode == 3 || mode == 4) return lin32_smem(K, sh.blk, sh.np);
+    return (size_t)(1 + sh.np) * K * sh.blk * sizeof(double);
 }
 
 struct Plan {
@@ -464,7 +777,6 @@ std::vector<Plan> g_plans;
 
 template <int MODE>
 int plan_shape(int K) {
-    constexpr bool APPLY = MODE != 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     {
@@ -478,7 +790,7 @@ int plan_shape(int K) {
     for (int c = 0; c < kNumShapes; ++c) {
         const Shape& sh = kShapes[c];
         if ((MODE == 2 ? 3 : 1) * sh.np > K) continue;
-        const size_t bytes = lin_smem(K, sh, APPLY);
+        const size_t bytes = lin_smem(K, sh, MODE);
         if (bytes > (size_t)per_block) continue;
         const void* kern = kernel_ptr<MODE>(c, std::make_integer_sequence<int, kNumShapes>{});
         if (ensure_smem(kern, bytes) != cudaSuccess) continue;
@@ -505,7 +817,7 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, int K, int64_t
     ((S == idx ? (void)(e = [&] {
         constexpr Shape sh = kShapes[S];
         auto kern = kernel_of<MODE, S>();
-        const size_t smem = lin_smem(K, sh, MODE != 0);
+        const size_t smem = lin_smem(K, sh, MODE);
         cudaError_t r = ensure_smem((const void*)kern, smem);
         if (r != cudaSuccess) return r;
         kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(args...);
@@ -519,6 +831,7 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, int K, int64_t
 }  // namespace
 
 int64_t lin_slots(const DevMech& m) { return slot_H(m) + m.K; }
+int64_t lin_slots_f32(const DevMech& m) { return slot_E32(m) + m.R; }
 
 cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* dlnA, double* lin, int64_t ldl, cudaStream_t s) {
@@ -537,6 +850,31 @@ cudaError_t launch_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const
     const double* none = nullptr;
     return launch_idx<1>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin, ldl,
                          vT, vY, d_omega, d_hrr, none, none, (int64_t)0);
+}
+
+cudaError_t launch_linearize_f32(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                 const double* Y, const double* dlnA, float* lin, int64_t ldl, cudaStream_t s) {
+    const int idx = plan_shape<5>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<5>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, dlnA,
+                         lin, ldl);
+}
+
+cudaError_t launch_jvp_linearized_f32(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                      const double* Y, const float* lin, int64_t ldl, const double* fT,
+                                      const double* fY, int64_t ldf, const double* vT, const double* vY,
+                                      double* d_T, double* d_Y, cudaStream_t s, int rhs) {
+    if (rhs) {
+        const int idx = plan_shape<4>(m.K);
+        if (idx < 0) return cudaErrorInvalidConfiguration;
+        return launch_idx<4>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin,
+                             ldl, vT, vY, d_Y, d_T, fT, fY, ldf);
+    }
+    const int idx = plan_shape<3>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    const double* none = nullptr;
+    return launch_idx<3>(idx, std::make_integer_sequence<int, kNumShapes>{}, m.K, n, s, m, n, ld, T, p, Y, lin, ldl,
+                         vT, vY, d_Y, d_T, none, none, (int64_t)0);
 }
 
 cudaError_t launch_rhs_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,

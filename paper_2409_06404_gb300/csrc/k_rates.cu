@@ -203,7 +203,7 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
     products<BLK>(x, sC, fw, rv);
     dfl sumg, unused_h, unused_cp;
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
-    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, (float)x.dnu), df_neg(sumg));   // ln K_c
+    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
     dfl shift{0.0f, 0.0f};
     if (dlnA) shift = df_split(__ldg(dlnA + x.orig));
     const dfl lnkf = ln_kf_df(m, r, P.tp, shift, dlnA != nullptr);
@@ -239,7 +239,7 @@ __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const
     products<BLK>(x, sC, fw, rv);
     dfl sumg, unused_h, unused_cp;
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
-    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, (float)x.dnu), df_neg(sumg));   // ln K_c
+    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
     const float shf = dlnA ? (float)__ldg(dlnA + x.orig) : 0.0f;
     double M = 0.0;
     if (KIND != 0) {

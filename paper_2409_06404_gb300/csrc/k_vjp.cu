@@ -100,7 +100,7 @@ __device__ __forceinline__ void vjp_reaction(const DevMech& m, int r, const doub
     dfl dG, dH, dCp;
     rxn_thermo<true, HB>(m, x.thermo, Q.P, dG, dH, dCp);
     const double sumh = df_to_d(dH);
-    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, (float)x.dnu), df_neg(dG));
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
     double shift = 0.0;
     dfl shiftd{0.0f, 0.0f};
     if (dlnA) {

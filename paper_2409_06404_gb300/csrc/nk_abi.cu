@@ -412,6 +412,14 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     std::vector<float> f_mu = to_f(d->mu_fit, (size_t)K * 4), f_lam = to_f(d->lam_fit, (size_t)K * 4),
                        f_D = to_f(P ? d->D_fit : nullptr, (size_t)P * 4), f_A = to_f(wilkeA.data(), wilkeA.size()),
                        f_q = to_f(qrtW.data(), K), f_s = to_f(sqrtW.data(), K), f_iw = to_f(invW.data(), K);
+    std::vector<float> f_nud((size_t)R * 2 * nk::kMaxSide, 0.0f), f_effm1 = to_f(eff_m1.data(), eff_m1.size()),
+                       f_cp((size_t)K * 2 * 8, 0.0f);
+    for (int q = 0; q < R; ++q)
+        for (int e = 0; e < 2 * nk::kMaxSide; ++e) f_nud[(size_t)q * 2 * nk::kMaxSide + e] = (float)rxn[q].nud[e];
+    for (int k = 0; k < K; ++k)
+        for (int range = 0; range < 2; ++range)
+            for (int j = 0; j < 5; ++j)
+                f_cp[((size_t)k * 2 + range) * 8 + j] = (float)nasa[((size_t)k * 2 + range) * nk::kNasaStride + j];
 
     // ---- one device block for everything
     Layout L;
@@ -430,7 +438,9 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_ndf = L.add(nasa_df.size() * 8), o_rdf = L.add(rxn_df.size() * 16),
                  o_tdf = L.add(troe_df.size() * 16 + 16), o_gdf = L.add(grp_df.size() * 8 + 16),
                  o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16),
-                 o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16);
+                 o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16),
+                 o_fnud = L.add(f_nud.size() * 4), o_feff = L.add(f_effm1.size() * 4 + 16),
+                 o_fcp = L.add(f_cp.size() * 4);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -476,6 +486,9 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_lb, lin_boff.data(), (size_t)R * 4);
     put(o_jr, jac_row.data(), jac_row.size() * 4);
     put(o_jt, jac_term.data(), jac_term.size() * sizeof(nk::JacTerm));
+    put(o_fnud, f_nud.data(), f_nud.size() * 4);
+    put(o_feff, f_effm1.data(), f_effm1.size() * 4);
+    put(o_fcp, f_cp.data(), f_cp.size() * 4);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -548,6 +561,9 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.lin_nb = lin_nb;
     dm.jac_row = reinterpret_cast<const int32_t*>(b + o_jr);
     dm.jac_term = reinterpret_cast<const nk::JacTerm*>(b + o_jt);
+    dm.f_nud = reinterpret_cast<const float*>(b + o_fnud);
+    dm.f_eff_m1 = reinterpret_cast<const float*>(b + o_feff);
+    dm.f_cp = reinterpret_cast<const float*>(b + o_fcp);
     *out = m;
     return ok();
 }
@@ -761,7 +777,10 @@ nk_status nk_reactor_workspace(const nk_mech* m, int64_t n, const nk_reactor_opt
         return fail(NK_EINVAL, "krylov_dim=%d outside 1..%d", o->krylov_dim, NK_REACTOR_MAX_KRYLOV);
     nk_status st = check_precond(m, o->precond);
     if (st != NK_OK) return st;
-    if (o->linearized != 0 && o->linearized != 1) return fail(NK_EINVAL, "linearized=%d is not 0 or 1", o->linearized);
+    if (o->linearized < 0 || o->linearized > 2)
+        return fail(NK_EINVAL, "linearized=%d is not 0, 1 or 2", o->linearized);
+    if (o->linearized == 2 && o->precond != 0)
+        return fail(NK_EINVAL, "single-precision products (linearized=2) need precond=0");
     *bytes = n == 0 ? 0 : nk::reactor_workspace_bytes(m->d, n, o->krylov_dim, o->precond, o->linearized);
     return ok();
 }
@@ -847,7 +866,9 @@ nk_status nk_reactor_step(const nk_mech* m, int64_t n, double* T, const double* 
         o.max_newton < 1 || !(dt >= 0.0) || !std::isfinite(dt))
         return fail(NK_EINVAL, "bad reactor options (tolerances > 0, max_newton >= 1, finite dt >= 0)");
     if ((st = check_precond(m, o.precond)) != NK_OK) return st;
-    if (o.linearized != 0 && o.linearized != 1) return fail(NK_EINVAL, "linearized=%d is not 0 or 1", o.linearized);
+    if (o.linearized < 0 || o.linearized > 2) return fail(NK_EINVAL, "linearized=%d is not 0, 1 or 2", o.linearized);
+    if (o.linearized == 2 && o.precond != 0)
+        return fail(NK_EINVAL, "single-precision products (linearized=2) need precond=0");
     const size_t need = nk::reactor_workspace_bytes(m->d, n, o.krylov_dim, o.precond, o.linearized);
     if (!workspace || workspace_bytes < need)
         return fail(NK_EINVAL, "the reactor step needs %zu bytes of workspace, got %zu", need,
@@ -926,6 +947,55 @@ nk_status nk_rates_jvp_linearized(const nk_mech* m, int64_t n, int64_t ld, const
     return launched(nk::launch_jvp_linearized(m->d, n, ld, T, p, Y, lin, ldl, vT, vY, d_omega, d_hrr,
                                               (cudaStream_t)stream),
                     "linearized jvp kernel launch");
+}
+
+nk_status nk_rates_linearization_slots_f32(const nk_mech* m, int64_t* slots) {
+    if (!m || !slots) return fail(NK_EINVAL, "mech and slots must not be NULL");
+    *slots = nk::lin_slots_f32(m->d);
+    return ok();
+}
+
+nk_status nk_rates_linearize_f32(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                 const double* Y, const double* dlnA, float* lin, int64_t ldl, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin) return fail(NK_EINVAL, "lin must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, dlnA})) != NK_OK) return st;
+    return launched(nk::launch_linearize_f32(m->d, n, ld, T, p, Y, dlnA, lin, ldl, (cudaStream_t)stream),
+                    "linearize (float) kernel launch");
+}
+
+nk_status nk_rates_jvp_linearized_f32(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                      const double* Y, const float* lin, int64_t ldl, const double* vT,
+                                      const double* vY, double* d_omega, double* d_hrr, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !vT || !vY || !d_omega || !d_hrr)
+        return fail(NK_EINVAL, "lin, vT, vY, d_omega and d_hrr must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, vT, vY, d_omega, d_hrr})) != NK_OK) return st;
+    return launched(nk::launch_jvp_linearized_f32(m->d, n, ld, T, p, Y, lin, ldl, nullptr, nullptr, 0, vT, vY, d_hrr,
+                                                  d_omega, (cudaStream_t)stream, 0),
+                    "linearized jvp (float) kernel launch");
+}
+
+nk_status nk_rhs_jvp_linearized_f32(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                    const double* Y, const float* lin, int64_t ldl, const double* fT,
+                                    const double* fY, const double* vT, const double* vY, double* dfT, double* dfY,
+                                    nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !fT || !fY || !vT || !vY || !dfT || !dfY)
+        return fail(NK_EINVAL, "lin, fT, fY, vT, vY, dfT and dfY must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, fT, fY, vT, vY, dfT, dfY})) != NK_OK) return st;
+    return launched(nk::launch_jvp_linearized_f32(m->d, n, ld, T, p, Y, lin, ldl, fT, fY, ld, vT, vY, dfT, dfY,
+                                                  (cudaStream_t)stream, 1),
+                    "linearized sources jvp (float) kernel launch");
 }
 
 nk_status nk_rates_vjp_workspace(const nk_mech* m, int64_t n, size_t* bytes) {

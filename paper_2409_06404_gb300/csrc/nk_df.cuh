@@ -30,9 +30,35 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {   // requires |a
     return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
-__device__ __forceinline__ dfl df_split(double x) {
+// a double as a pair with the conversion instructions (F2F, on the FP64 pipe)
+__device__ __forceinline__ dfl df_split_cvt(double x) {
     const float h = __double2float_rn(x);
     return {h, __double2float_rn(x - (double)h)};
+}
+static __device__ __noinline__ dfl df_split_edge(double x) { return df_split_cvt(x); }
+
+// float of a double's bits whose low 29 significand bits are zero and whose exponent lies in
+// the normal float range (exact: sign, rebiased exponent, top 23 significand bits)
+__device__ __forceinline__ float d2f_exact_bits(unsigned long long u) {
+    return __uint_as_float(((unsigned int)(u >> 32) & 0x80000000u) | (((unsigned int)(u >> 52) & 0x7ffu) - 896u) << 23 |
+                           ((unsigned int)(u >> 29) & 0x7fffffu));
+}
+
+// a double as a pair by integer operations: h = x rounded to 24 significant bits on its bit
+// pattern (half-way cases away from zero), l = x - h (exact in double) rounded the same way.
+// For 2^-73 <= |x| < 2^127, where any nonzero l is a normal float; other x (zero, tiny, huge,
+// non-finite) take the conversion instructions out of line.  This keeps the FP64 pipe to the
+// one subtraction.
+__device__ __forceinline__ dfl df_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int e = (unsigned int)(b >> 52) & 0x7ffu;
+    if (e < 1023u - 73u || e > 1023u + 126u) return df_split_edge(x);
+    constexpr unsigned long long kHalf = 1ULL << 28, kMask = ~((1ULL << 29) - 1);
+    const unsigned long long hb = (b + kHalf) & kMask;           // a carry may raise the exponent by one
+    const double ld = x - __longlong_as_double((long long)hb);
+    const unsigned long long lb = (unsigned long long)__double_as_longlong(ld);
+    const float l = (lb << 1) == 0 ? 0.0f : d2f_exact_bits((lb + kHalf) & kMask);
+    return {d2f_exact_bits(hb), l};
 }
 
 __device__ __forceinline__ double df_value(dfl a) { return (double)a.h + (double)a.l; }
@@ -127,6 +153,29 @@ __device__ __forceinline__ double f2d_bits(float f) {
     return __longlong_as_double((long long)bits);
 }
 
+// A float widened to double with integer operations.  Exact for normal floats, infinities and
+// NaN; a subnormal float (|f| < 1.2e-38) becomes a signed zero.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long ee = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+    const unsigned long long bits = e == 0u ? sign : sign | (ee << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// A double rounded to float with integer operations (half-way cases away from zero).  Results
+// in the normal float range are correctly rounded otherwise; |x| < 2^-126 gives a signed zero
+// (no subnormals), larger than the float range gives +-inf, NaN stays NaN.
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned int e = (unsigned int)(b >> 52) & 0x7ffu;
+    if (e < 897u) return __uint_as_float(sign);
+    if (e > 1150u) return __uint_as_float(sign | 0x7f800000u | (e == 0x7ffu && (b << 12) != 0 ? 0x400000u : 0u));
+    return d2f_exact_bits((b + (1ULL << 28)) & ~((1ULL << 29) - 1));   // a carry at the top rounds to inf
+}
+
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
 
 // x * s for a float s (pair result)
@@ -145,7 +194,7 @@ __device__ __forceinline__ dfl df_mul_f(dfl x, float s) {
 // <= 1.7e-13 for |x| <= 100, 2.2e-12 at |x| = 700 (the pair carries x to 2^-48 |x|).
 // Out of line, so the rare paths' conversions to double stay off the common path.
 static __device__ __noinline__ double exp_df_d_edge(float h, float l) { return exp((double)h + (double)l); }
-static __device__ __noinline__ dfl log_df_edge(double x) { return df_split(log(x)); }
+static __device__ __noinline__ dfl log_df_edge(double x) { return df_split_cvt(log(x)); }
 
 __device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
     if (!(fabsf(x.h) < 708.0f)) return exp_df_d_edge(x.h, x.l);

@@ -144,6 +144,12 @@ struct DevMech {
     const double* grp_Tmid;       // [groups] the group's T_mid
     const int32_t* lin_boff;      // [R] first entry slot of each reaction in a stored linearization
     int32_t lin_nb;               // entry slots of all reactions (sum of nr + np)
+    // single-precision products from an FP32 linearization: signed coefficients of each
+    // reaction's entries (RxnRec::nud order, device order), efficiencies - 1 (eff_m1 order),
+    // c_p/R coefficients a1..a5 per species and range ([K][2][8], low then high)
+    const float* f_nud;           // [R][2 kMaxSide]
+    const float* f_eff_m1;
+    const float* f_cp;
     // Jacobian assembly: species row k has the terms [jac_row[k], jac_row[k+1]) of jac_term,
     // grouped by destination in increasing order, each group in reaction order
     const int32_t* jac_row;       // [K+1]
@@ -242,11 +248,20 @@ cudaError_t jit_launch_rates(const JitModule& mod, const DevMech& m, int device,
                              double* hrr, cudaStream_t s);
 // Stored linearization of the rates (k_lin.cu): per-point slots, see lin_slots().
 int64_t lin_slots(const DevMech& m);
+int64_t lin_slots_f32(const DevMech& m);   // the float format's 32-bit words per point
 cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* dlnA, double* lin, int64_t ldl, cudaStream_t s);
 cudaError_t launch_jvp_linearized(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                                   const double* Y, const double* lin, int64_t ldl, const double* vT,
                                   const double* vY, double* d_omega, double* d_hrr, cudaStream_t s);
+// The same linearization rounded to float, and the products from it in single precision
+// (results widened to double): rhs = 0 the rates' JVP, rhs = 1 the sources' (fT, fY given).
+cudaError_t launch_linearize_f32(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                 const double* Y, const double* dlnA, float* lin, int64_t ldl, cudaStream_t s);
+cudaError_t launch_jvp_linearized_f32(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                      const double* Y, const float* lin, int64_t ldl, const double* fT,
+                                      const double* fY, int64_t ldf, const double* vT, const double* vY,
+                                      double* d_T, double* d_Y, cudaStream_t s, int rhs);
 cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* bar_omega,
                        const double* bar_hrr, double* gT, double* gY, double* g_lnA,

@@ -160,6 +160,12 @@ __device__ __forceinline__ dfl ln_kf_df(const DevMech& m, int r, const TPairs& P
     return shifted ? df_add(l, shift) : l;
 }
 
+// sum_k nu_k of reaction r (device order) as a float, from the pair record (converting the
+// double in the reaction record would take an F2F instruction on the FP64 pipe per reaction)
+__device__ __forceinline__ float dnu_f(const DevMech& m, int r) {
+    return __ldg(reinterpret_cast<const float*>(m.rxn_df + 2 * r + 1) + 2);
+}
+
 // Part `part` of NP takes the contiguous slice [a + len*part/NP, a + len*(part+1)/NP) of the
 // range [a, b).
 template <int NP>

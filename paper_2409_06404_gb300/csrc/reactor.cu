@@ -24,6 +24,12 @@
 // above the update -- so a test on it, as right preconditioning keeps, says little about the
 // update's accuracy.)
 //
+// Products: recomputed from the state per direction (nk_rhs_jvp), or from a linearization
+// stored once per Newton iteration (nk_rhs_jvp_linearized), or from that linearization
+// rounded to float with single-precision arithmetic (linearized = 2): the basis is FP32, so
+// products rounded at that level change the Krylov solve about as much as the basis itself
+// does, while the residual -- and with it the converged state -- stays double.
+//
 // Vectors of the workspace hold (K+1) rows of n doubles (row 0 = T, rows 1..K = Y_k); the
 // basis m+1 rows of (K+1) n floats.  Reductions go through per-block partial sums added in a
 // fixed order (deterministic).  The host keeps the (m+1) x m Hessenberg matrix and the Givens
@@ -47,19 +53,6 @@ __device__ __forceinline__ int64_t row_of(int64_t e, int64_t n, int64_t& i) {
     const int64_t r = e / n;
     i = e - r * n;
     return r;
-}
-
-// A basis entry widened to double with integer operations: on GB300 the float-to-double
-// conversion instruction runs on the FP64 pipe, which the vector kernels are short of.  Exact
-// for normal floats, infinities and NaN; a subnormal float (|v| < 1.2e-38 in a unit vector)
-// becomes a signed zero.
-__device__ __forceinline__ double widen(float f) {
-    const unsigned int b = __float_as_uint(f);
-    const unsigned int e = (b >> 23) & 0xffu;
-    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    const unsigned long long ee = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
-    const unsigned long long bits = e == 0u ? sign : sign | (ee << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
 }
 
 // x0, the weights W = 1/(rtol |x0| + atol) and their reciprocals iW = rtol |x0| + atol
@@ -282,7 +275,9 @@ struct Work {
     float* V;
     double* F;                // block factors (precond only)
     int32_t* piv;             // pivot rows and row exponents of the factors
-    double* lin;              // stored linearization of one chunk of points
+    double* lin;              // stored linearization of one chunk of points (all points for
+                              // double linearized products)
+    float* linf;              // the linearization rounded to float (single-precision products)
     int64_t N, vstride, nchunk;
     int nred;
 };
@@ -296,10 +291,10 @@ int reduction_blocks() {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// points per chunk of the stored linearization: all of them for linearized products, else
-// about 2 GB (whole warps) for the preconditioner's set-up
+// points per chunk of the stored (double) linearization: all of them for double linearized
+// products, else about 2 GB (whole warps) for the preconditioner's set-up
 int64_t lin_chunk(const DevMech& mech, int64_t n, int linearized) {
-    if (linearized) return n;
+    if (linearized == 1) return n;
     const int64_t per = lin_slots(mech) * (int64_t)sizeof(double);
     const int64_t c = std::max<int64_t>(128, ((int64_t(2) << 30) / per) / 128 * 128);
     return std::min(n, c);
@@ -311,8 +306,9 @@ size_t work_bytes(const DevMech& mech, int64_t n, int m, int nred, int precond, 
                align256((size_t)nred * kMaxDots * sizeof(double)) + align256(kMaxDots * sizeof(double));
     if (precond)
         b += align256((size_t)(mech.K + 1) * N * sizeof(double)) + align256((size_t)N * sizeof(int32_t));
-    if (precond || linearized)
+    if (precond || linearized == 1)
         b += align256((size_t)lin_slots(mech) * lin_chunk(mech, n, linearized) * sizeof(double));
+    if (linearized == 2) b += align256((size_t)lin_slots_f32(mech) * n * sizeof(float));
     return b;
 }
 
@@ -340,15 +336,17 @@ Work carve(const DevMech& mech, void* ws, int64_t n, int m, int nred, int precon
     w.F = nullptr;
     w.piv = nullptr;
     w.lin = nullptr;
+    w.linf = nullptr;
     w.nchunk = 0;
     if (precond) {
         w.F = reinterpret_cast<double*>(take((size_t)(mech.K + 1) * N * sizeof(double)));
         w.piv = reinterpret_cast<int32_t*>(take((size_t)N * sizeof(int32_t)));
     }
-    if (precond || linearized) {
+    if (precond || linearized == 1) {
         w.nchunk = lin_chunk(mech, n, linearized);
         w.lin = reinterpret_cast<double*>(take((size_t)lin_slots(mech) * w.nchunk * sizeof(double)));
     }
+    if (linearized == 2) w.linf = reinterpret_cast<float*>(take((size_t)lin_slots_f32(mech) * n * sizeof(float)));
     w.N = N;
     w.vstride = N;
     w.nred = nred;
@@ -400,17 +398,21 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
             st.converged = beta == 0.0;
             return cudaSuccess;
         }
-        if (o.linearized &&                        // the rates' tangent data at this iterate
+        if (o.linearized == 1 &&                   // the rates' tangent data at this iterate
             (e = launch_linearize(m, n, ld, T, p, Y, nullptr, w.lin, n, s)) != cudaSuccess)
+            return e;
+        if (o.linearized == 2 &&                   // the same, rounded to float
+            (e = launch_linearize_f32(m, n, ld, T, p, Y, nullptr, w.linf, n, s)) != cudaSuccess)
             return e;
         if (o.precond == 1 && it == 0) {           // blocks of I - dt W J W^-1 at x0, factored
             for (int64_t c0 = 0; c0 < n; c0 += w.nchunk) {
                 const int64_t nc = std::min(w.nchunk, n - c0);
-                if (!o.linearized &&
+                const bool full = o.linearized == 1;    // the full double data: stride n
+                if (!full &&
                     (e = launch_linearize(m, nc, ld, T + c0, p + c0, Y + c0, nullptr, w.lin, nc, s)) != cudaSuccess)
                     return e;
-                const double* lc = o.linearized ? w.lin + c0 : w.lin;     // (the full data: stride n)
-                if ((e = launch_precond_setup(m, nc, ld, T + c0, p + c0, Y + c0, lc, o.linearized ? n : nc, w.f + c0,
+                const double* lc = full ? w.lin + c0 : w.lin;
+                if ((e = launch_precond_setup(m, nc, ld, T + c0, p + c0, Y + c0, lc, full ? n : nc, w.f + c0,
                                               w.f + n + c0, n, w.W + c0, n, dt, w.F + c0, w.piv + c0, n, s)) !=
                     cudaSuccess)
                     return e;
@@ -438,10 +440,14 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         while (j < mk) {
             const float* vj = w.V + (int64_t)j * w.vstride;
             unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.iW, w.u);
-            e = o.linearized ? launch_rhs_jvp_linearized(m, n, ld, T, p, Y, w.lin, n, w.f, w.f + n, n, w.u, w.u + n,
-                                                         w.Ju, w.Ju + n, s)
-                             : launch_jvp(m, n, ld, T, p, Y, nullptr, w.u, w.u + n, nullptr, nullptr, w.Ju + n, w.Ju,
-                                          s, 1);
+            if (o.linearized == 1)
+                e = launch_rhs_jvp_linearized(m, n, ld, T, p, Y, w.lin, n, w.f, w.f + n, n, w.u, w.u + n, w.Ju,
+                                              w.Ju + n, s);
+            else if (o.linearized == 2)
+                e = launch_jvp_linearized_f32(m, n, ld, T, p, Y, w.linf, n, w.f, w.f + n, n, w.u, w.u + n, w.Ju,
+                                              w.Ju + n, s, 1);
+            else
+                e = launch_jvp(m, n, ld, T, p, Y, nullptr, w.u, w.u + n, nullptr, nullptr, w.Ju + n, w.Ju, s, 1);
             if (e != cudaSuccess) return e;
             if (o.precond) {                          // w = P^-1 A v_j
                 form_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.Ju, w.W, dt, w.w);

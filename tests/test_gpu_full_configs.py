@@ -6,7 +6,8 @@ against the oracle:
 * the implicit-stage workload: 53 species on 32^3 elements x 512 points = 16,777,216 points,
   one mixed forward (thermo, rates, transport) and ten JVPs along seeded N(0, 1) directions,
   as a Newton-Krylov stage issues them, rates of progress recomputed for each;
-* the reactor step on 2,097,152 near-equilibrium points, unpreconditioned and block-Jacobi.
+* the reactor step on 2,097,152 near-equilibrium points, unpreconditioned, block-Jacobi and with
+  single-precision products from the float linearization.
 """
 import numpy as np
 import pytest
@@ -113,8 +114,8 @@ def test_implicit_stage_16M_points_sampled(cuda):
 
 
 def test_reactor_step_full_size_sampled(cuda):
-    """The reactor step at the benchmark's size (2,097,152 points, 53 species), unpreconditioned
-    and block-Jacobi, on near-equilibrium states built as the benchmark builds them (512
+    """The reactor step at the benchmark's size (2,097,152 points, 53 species), unpreconditioned,
+    block-Jacobi and with single-precision products (linearized 2), on near-equilibrium states built as the benchmark builds them (512
     equilibria from element potentials, here with the oracle's Gibbs energies, tiled over the
     points and perturbed by 1e-3 in Y and ~1 K in T); 100 sampled points against the oracle's
     dense Newton solution (weighted RMS difference within 1e-3 of the tolerance weights)."""
@@ -139,14 +140,14 @@ def test_reactor_step_full_size_sampled(cuda):
     wT = 1.0 / (rtol * np.abs(T[samp]) + atolT)
     wY = 1.0 / (rtol * np.abs(Y[:, samp]) + atolY)
     pt = torch.from_numpy(p).cuda()
-    for precond in (0, 1):
+    for precond, linearized in ((0, 0), (1, 0), (0, 2)):
         Tt, Yt = to_dev(T, Y)
         o = nk.reactor_opts(rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4, lin_tol=1e-6, max_newton=20,
-                            krylov_dim=30, precond=precond)
+                            krylov_dim=30, precond=precond, linearized=linearized)
         st = nk.reactor_step(m, Tt, pt, Yt, dt, o)
-        assert st["converged"] == 1, (precond, st)
+        assert st["converged"] == 1, (precond, linearized, st)
         sub = torch.from_numpy(samp).cuda()
         d = np.concatenate([((host(Tt[sub]) - T_o) * wT)[None], (host(Yt[:, sub]) - Y_o) * wY])
-        assert np.sqrt(np.mean(d ** 2)) <= 1e-3, precond
+        assert np.sqrt(np.mean(d ** 2)) <= 1e-3, (precond, linearized)
         del Tt, Yt
         torch.cuda.empty_cache()

@@ -121,17 +121,19 @@ def test_preconditioned_step_vs_dense_newton(cuda, name, n, dt):
     assert st["krylov_iters"] <= 10 * st["newton_iters"]
 
 
-@pytest.mark.parametrize("name,n,dt,precond", [("h2_9sp_21rx", 600, 1e-9, 0), ("ch4_53sp_325rx", 160, 1e-7, 0),
-                                               ("h2_9sp_21rx", 600, 1e-4, 1)])
-def test_linearized_products_vs_dense_newton(cuda, name, n, dt, precond):
-    """GMRES products from a stored linearization refreshed per Newton iteration: the same
-    solution as the oracle's dense Newton (and as the recomputing products)."""
+@pytest.mark.parametrize("name,n,dt,precond,linearized", [
+    ("h2_9sp_21rx", 600, 1e-9, 0, 1), ("ch4_53sp_325rx", 160, 1e-7, 0, 1), ("h2_9sp_21rx", 600, 1e-4, 1, 1),
+    ("h2_9sp_21rx", 600, 1e-9, 0, 2), ("ch4_53sp_325rx", 160, 1e-7, 0, 2), ("big_120sp_700rx", 64, 1e-8, 0, 2)])
+def test_linearized_products_vs_dense_newton(cuda, name, n, dt, precond, linearized):
+    """GMRES products from a stored linearization refreshed per Newton iteration, in double
+    (linearized 1) or rounded to float with single-precision products (2): the same solution
+    as the oracle's dense Newton (the residual, and so the converged state, is double in both)."""
     mech = synth.mechanism(name)
     m = gpu_mechanism(name)
     T, p, Y = _perturbed_equilibrium(mech, n, seed=41) if precond else _near_equilibrium(mech, n, seed=41)
     rtol, atolT, atolY = 1e-6, 1e-6, 1e-12
     T1, Y1, st = _step(m, *to_dev(T, p, Y), dt, rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4,
-                       lin_tol=1e-6, max_newton=30, krylov_dim=30, precond=precond, linearized=1)
+                       lin_tol=1e-6, max_newton=30, krylov_dim=30, precond=precond, linearized=linearized)
     assert st["converged"] == 1, st
     T_o, Y_o, it = oracle.reactor_step(mech, T, p, Y, dt, atol_T=atolT, atol_Y=atolY)
     assert np.all(it > 0)
@@ -160,9 +162,12 @@ def test_preconditioned_workspace_and_limits(cuda):
     assert nk.reactor_workspace(m, 64, 10, 1) > nk.reactor_workspace(m, 64, 10, 0)
     with pytest.raises(nk.NkError):
         nk.reactor_workspace(m, 64, 10, 3)
-    assert nk.reactor_workspace(m, 64, 10, 0, 1) > nk.reactor_workspace(m, 64, 10, 0, 0)
+    assert nk.reactor_workspace(m, 64, 10, 0, 1) > nk.reactor_workspace(m, 64, 10, 0, 2) > \
+        nk.reactor_workspace(m, 64, 10, 0, 0)
     with pytest.raises(nk.NkError):
-        nk.reactor_workspace(m, 64, 10, 0, 2)
+        nk.reactor_workspace(m, 64, 10, 0, 3)
+    with pytest.raises(nk.NkError):                    # single-precision products, no preconditioner
+        nk.reactor_workspace(m, 64, 10, 1, 2)
 
 
 def test_reused_factors(cuda):
