@@ -252,18 +252,20 @@ nk_status nk_rates_jvp_linearized(const nk_mech* mech, int64_t n, int64_t ld, co
                                   nk_stream stream);
 
 /*
- * The same stored linearization in single precision, and products from it with the reaction
- * terms in single precision (FP32 pipe) and their sums per species in double.  For Krylov
- * solvers whose basis is single precision (as the paper's GMRES, Sec. 2): the products then
- * carry rounding of the order the basis already has.
+ * The same stored linearization in single precision, and products from it in single
+ * precision (FP32 pipe).  For Krylov solvers whose basis is single precision (as the paper's
+ * GMRES, Sec. 2): the products then carry rounding of the order the basis already has.
  *   *slots   32-bit words per point (nk_rates_linearization_slots_f32; about half the bytes)
  *   lin      device float [slots][ldl], ldl >= n, caller-owned; written by nk_rates_linearize_f32
  * Each reaction's coefficients are stored rounded to float after scaling by a power of two
- * per reaction and point (kept beside them), so rates of any magnitude fit; coefficients below
- * 2^-126 of their reaction's largest are dropped.  Each result is within about (8 + 2) 2^-24 of
- * the sum of the magnitudes of the terms it adds (against 2^-53 for the double entries); the
- * inputs are rounded to float without subnormals.  The rhs form takes the sources at the
- * state, as nk_rhs_jvp_linearized.
+ * per reaction and point, and each species' tangent is summed at a power-of-two scale of its
+ * own (both kept beside the coefficients), so rates of any magnitude fit; coefficients below
+ * 2^-126 of their reaction's largest, and terms below 2^-126 of their species' scale, drop
+ * out.  Result k is within about (terms_k + 8) 2^-24 of the sum of the magnitudes of the
+ * terms it adds, terms_k the reactions species k takes part in (against 2^-53 for the double
+ * entries); the inputs are rounded to float without subnormals, the heat-release and source
+ * epilogues run in double.  The rhs form takes the sources at the state, as
+ * nk_rhs_jvp_linearized.
  */
 nk_status nk_rates_linearization_slots_f32(const nk_mech* mech, int64_t* slots);
 nk_status nk_rates_linearize_f32(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,

@@ -38,10 +38,13 @@ namespace {
 __host__ __device__ inline int64_t slot_M(const DevMech& m) { return (int64_t)m.R + m.lin_nb; }
 __host__ __device__ inline int64_t slot_S(const DevMech& m) { return slot_M(m) + (m.R - m.R_el); }
 __host__ __device__ inline int64_t slot_H(const DevMech& m) { return slot_S(m) + 1; }
-// the float format: S1 as the two 32-bit words of its double, h_k/RT, then one exponent word per
-// reaction (the reaction's coefficients are stored scaled by 2^-e_r)
+// the float format: S1 as the two 32-bit words of its double, h_k/RT, one exponent word per
+// reaction (the reaction's coefficients are stored scaled by 2^-e_r), then one per species
+// (E_k = the largest e_r of the reactions it takes part in, the scale of its tangent sums)
 __host__ __device__ inline int64_t slot_H32(const DevMech& m) { return slot_S(m) + 2; }
 __host__ __device__ inline int64_t slot_E32(const DevMech& m) { return slot_H32(m) + m.K; }
+__host__ __device__ inline int64_t slot_EK32(const DevMech& m) { return slot_E32(m) + m.R; }
+constexpr int kNoExp = -2000;                  // E_k of a species without reactions
 
 // prod of p[0..n) (returned) and, in ex[e], the product of all entries but e (n <= 4, uniform)
 __device__ __forceinline__ double exclusive_products(const double* p, int n, double* ex) {
@@ -99,9 +102,9 @@ __device__ __forceinline__ float narrow_scaled(double v, int e) {
 // storage scaled by 2^-e_r, e_r the largest binary exponent among them (so they fit the float
 // range whatever the reaction's magnitude -- rates of progress of stiff mechanisms span far more
 // than it), with e_r in the reaction's exponent word.
-template <int KIND>
+template <int BLK, int KIND>
 __device__ __forceinline__ void store_coef(const DevMech& m, int r, double* lin, int64_t ldl, int64_t i, int nr,
-                                           int np, double Av, const double* Bv, double Lv) {
+                                           int np, const int*, int*, double Av, const double* Bv, double Lv) {
     lin[(int64_t)r * ldl + i] = Av;
     double* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
 #pragma unroll
@@ -112,9 +115,9 @@ __device__ __forceinline__ void store_coef(const DevMech& m, int r, double* lin,
     if (KIND != 0) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = Lv;
 }
 
-template <int KIND>
+template <int BLK, int KIND>
 __device__ __forceinline__ void store_coef(const DevMech& m, int r, float* lin, int64_t ldl, int64_t i, int nr,
-                                           int np, double Av, const double* Bv, double Lv) {
+                                           int np, const int* sp, int* sE, double Av, const double* Bv, double Lv) {
     int mx = bexp(Av);
 #pragma unroll
     for (int e = 0; e < kMaxSide; ++e) {
@@ -132,13 +135,18 @@ __device__ __forceinline__ void store_coef(const DevMech& m, int r, float* lin, 
     }
     if (KIND != 0) lin[(slot_M(m) + (r - m.R_el)) * ldl + i] = narrow_scaled(Lv, er);
     reinterpret_cast<int32_t*>(lin)[(slot_E32(m) + r) * ldl + i] = er;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e) {               // the species' scales (parts share them)
+        if (e < nr) atomicMax(sE + sp[e] * BLK, er);
+        if (e < np) atomicMax(sE + sp[kMaxSide + e] * BLK, er);
+    }
 }
 
 // ---------------------------------------------------------------- linearization pass
 template <int BLK, int KIND, class TS>
 __device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const double* sC, const LinPoint& Q,
                                              const double* dlnA, const DfTab& dt, TS* __restrict__ lin,
-                                             int64_t ldl, int64_t i, bool live, double& S1) {
+                                             int64_t ldl, int64_t i, bool live, double& S1, int* sE) {
     const Rxn x = load_rxn(m.rxn + r);
     double cR[kMaxSide], pR[kMaxSide], cP[kMaxSide], pP[kMaxSide];
 #pragma unroll
@@ -250,15 +258,15 @@ __device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const doub
             Bv[kMaxSide + e] = -sc * kr * d;
         }
     }
-    store_coef<KIND>(m, r, lin, ldl, i, x.nr, x.np, sc * fma(qc, aT, qr * D), Bv,
-                     KIND == 1 ? qc : (KIND == 2 ? qc * aM : 0.0));
+    store_coef<BLK, KIND>(m, r, lin, ldl, i, x.nr, x.np, x.sp, sE, sc * fma(qc, aT, qr * D), Bv,
+                          KIND == 1 ? qc : (KIND == 2 ? qc * aM : 0.0));
 }
 
 template <int BLK, int KIND, class TS>
 __device__ __forceinline__ void lin_group(const DevMech& m, int r0, int r1, const double* sC, const LinPoint& Q,
                                           const double* dlnA, const DfTab& dt, TS* lin, int64_t ldl, int64_t i,
-                                          bool live, double& S1) {
-    for (int r = r0; r < r1; ++r) lin_reaction<BLK, KIND>(m, r, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+                                          bool live, double& S1, int* sE) {
+    for (int r = r0; r < r1; ++r) lin_reaction<BLK, KIND>(m, r, sC, Q, dlnA, dt, lin, ldl, i, live, S1, sE);
 }
 
 // TS: the stored type (double, or float for the single-precision products)
@@ -280,6 +288,8 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;
     double* sC = smem + kMathTabDoubles + slot;
+    // float format: the species' exponent scales E_k (K ints per point after C_k)
+    int* sE = F32 ? reinterpret_cast<int*>(smem + kMathTabDoubles + (size_t)K * BLK) + slot : nullptr;
 
     LinPoint Q;
     const double Ti = T[i];
@@ -294,6 +304,7 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
         sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
         if (live)
             put(lin + ((F32 ? slot_H32(m) : slot_H(m)) + k) * ldl + i, nasa_hRT(nasa_range(m, k, Ti), Ti, Q.invT));
+        if constexpr (F32) sE[k * BLK] = kNoExp;
     }
     if (NP > 1) __syncthreads();
 
@@ -301,13 +312,17 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
     int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
     slice<NP>(0, e1, part, a, b);
-    lin_group<BLK, 0>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+    lin_group<BLK, 0>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1, sE);
     slice<NP>(e1, t1, part, a, b);
-    lin_group<BLK, 1>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+    lin_group<BLK, 1>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1, sE);
     slice<NP>(t1, m.R, part, a, b);
-    lin_group<BLK, 2>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1);
+    lin_group<BLK, 2>(m, a, b, sC, Q, dlnA, dt, lin, ldl, i, live, S1, sE);
+    if (NP > 1) __syncthreads();
+    if constexpr (F32)
+        if (live)
+            for (int k = part; k < K; k += NP)
+                reinterpret_cast<int32_t*>(lin)[(slot_EK32(m) + k) * ldl + i] = sE[k * BLK];
     if constexpr (NP > 1) {
-        __syncthreads();
         sC[part * BLK] = S1;                       // C_k is dead; rows 0..NP-1 (NP <= K)
         __syncthreads();
         if (part != 0) return;
@@ -497,13 +512,15 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
 }
 
 // ---------------------------------------------------------------- FP32 apply pass
-// The same contraction from the float linearization: each reaction's dq_r in single precision
-// from its scaled coefficients (FP32 pipe, about 60 times the FP64 pipe's rate on GB300, and half
-// the bytes), brought to double with its exponent e_r by integer operations, and scattered into
-// the omega_k tangents in double (the only FP64 arithmetic per reaction).  Meant for Krylov
-// solvers whose basis is FP32 anyway: the products carry rounding of the order the basis
-// already has.  The point terms (rho, d rho/rho, dC_k, c_p) are formed in float from the double
-// inputs, rounded by integer operations.
+// The same contraction from the float linearization, on the FP32 pipe (about 60 times the FP64
+// pipe's rate on GB300) and from half the bytes: each reaction's dq_r' = dq_r 2^-e_r in single
+// precision from its scaled coefficients, scattered into species sums kept at the species'
+// scale, omega_k' = sum_r nu_kr dq_r' 2^(e_r - E_k) (powers of two built by integer operations;
+// e_r <= E_k, so nothing overflows, and terms below 2^-126 of the species' scale drop out),
+// and each sum brought to double with its E_k at the end.  Meant for Krylov solvers whose
+// basis is FP32 anyway: the products carry rounding of the order the basis already has.  The
+// point terms (rho, d rho/rho, dC_k, c_p) are formed in float from the double inputs, rounded
+// by integer operations; the heat-release and source epilogues run in double.
 constexpr float kInvRf = (float)(1.0 / 8.314462618);
 
 struct Rxn32 {
@@ -564,10 +581,13 @@ __device__ __forceinline__ double scale2(double v, int e) {
     return __longlong_as_double((long long)((b & ~(0x7ffULL << 52)) | ((unsigned long long)ex << 52)));
 }
 
+// 2^d as a float for an integer d <= 0 (zero below -126)
+__device__ __forceinline__ float pow2f(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.0f; }
+
 template <int BLK, int KIND>
-__device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, const float* sdC, double* sD,
-                                              const float* __restrict__ lin, int64_t ldl, int64_t i, float tT,
-                                              float dpRT) {
+__device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, const float* sdC, float* sD,
+                                              const int* sE, const float* __restrict__ lin, int64_t ldl, int64_t i,
+                                              float tT, float dpRT) {
     if (r0 >= r1) return;
     Rxn32 x = load_rxn32(m, r0);
     LinCoef32 c = load_coef32<KIND>(m, r0, lin, ldl, i, x.nr, x.np);
@@ -591,18 +611,17 @@ __device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, 
                 dM = fmaf(__ldg(m.f_eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
             dq = fmaf(c.L, dM, dq);
         }
-        const double dqd = scale2(widen(dq), c.e);
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
             if (e < x.nr) {
-                double* w = sD + x.sp[e] * BLK;
-                *w = fma(widen(x.nud[e]), dqd, *w);
+                const int k = x.sp[e] * BLK;
+                sD[k] = fmaf(x.nud[e] * pow2f(c.e - sE[k]), dq, sD[k]);
             }
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
             if (e < x.np) {
-                double* w = sD + x.sp[kMaxSide + e] * BLK;
-                *w = fma(widen(x.nud[kMaxSide + e]), dqd, *w);
+                const int k = x.sp[kMaxSide + e] * BLK;
+                sD[k] = fmaf(x.nud[kMaxSide + e] * pow2f(c.e - sE[k]), dq, sD[k]);
             }
         if (r + 1 < r1) {
             x = xn;
@@ -611,10 +630,10 @@ __device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, 
     }
 }
 
-// Shared memory: NP rows of d omega_k partials (double), dC_k (float), 3 NP sums per point.
+// Shared memory: 3 NP sums per point (double), NP rows of scaled d omega_k partials, dC_k, E_k
+// (4-byte words).
 __host__ __device__ constexpr size_t lin32_smem(int K, int blk, int np) {
-    return (size_t)np * K * blk * sizeof(double) + (((size_t)K * blk * sizeof(float) + 7) & ~size_t(7)) +
-           (size_t)3 * np * blk * sizeof(double);
+    return (size_t)3 * np * blk * sizeof(double) + (size_t)(np + 2) * K * blk * sizeof(float);
 }
 
 template <int BLK, int NP, bool RHS>
@@ -636,10 +655,12 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, co
     if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;
-    double* sD0 = smd + slot;                                    // d omega_k partials, part q at row q
-    double* sD = sD0 + (size_t)part * K * BLK;
-    float* sdC = reinterpret_cast<float*>(smd + (size_t)NP * K * BLK) + slot;   // dC_k
-    double* sR = smd + (lin32_smem(K, BLK, NP) / sizeof(double) - (size_t)3 * NP * BLK) + slot;  // part sums
+    double* sR = smd + slot;                                     // part sums
+    float* sD0 = reinterpret_cast<float*>(smd + (size_t)3 * NP * BLK) + slot;   // scaled partials, part q at row q
+    float* sD = sD0 + (size_t)part * K * BLK;
+    float* sdC = sD0 + (size_t)NP * K * BLK;                     // dC_k
+    int* sE = reinterpret_cast<int*>(sdC + (size_t)K * BLK);     // E_k
+    const int32_t* linE = reinterpret_cast<const int32_t*>(lin) + slot_EK32(m) * ldl + i;
 
     const double Td = T[i], dTd = vT[i];
     const float Ti = narrow(Td), dT = narrow(dTd);
@@ -656,19 +677,20 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, co
     for (int k = part; k < K; k += NP) {
         const float iw = __ldg(m.f_invW + k);
         sdC[k * BLK] = fmaf(narrow(Y[(int64_t)k * ld + i]) * iw * rho, arho, rho * narrow(vY[(int64_t)k * ld + i]) * iw);
+        sE[k * BLK] = linE[(int64_t)k * ldl];
     }
-    for (int k = 0; k < K; ++k) sD[k * BLK] = 0.0;
+    for (int k = 0; k < K; ++k) sD[k * BLK] = 0.0f;
     if (NP > 1) __syncthreads();
 
     const float dpRT = -pRT * tT;
     int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
     slice<NP>(0, e1, part, a, b);
-    apply_group32<BLK, 0>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    apply_group32<BLK, 0>(m, a, b, sdC, sD, sE, lin, ldl, i, tT, dpRT);
     slice<NP>(e1, t1, part, a, b);
-    apply_group32<BLK, 1>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    apply_group32<BLK, 1>(m, a, b, sdC, sD, sE, lin, ldl, i, tT, dpRT);
     slice<NP>(t1, m.R, part, a, b);
-    apply_group32<BLK, 2>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
+    apply_group32<BLK, 2>(m, a, b, sdC, sD, sE, lin, ldl, i, tT, dpRT);
     if (NP > 1) __syncthreads();
 
     double hsum = 0.0;
@@ -676,9 +698,10 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, co
     const float inv_rho = RHS ? 1.0f / rho : 0.0f;
     const double arho_d = widen(arho);
     for (int k = part; k < K; k += NP) {
-        double dw = sD0[k * BLK];
+        float dws = sD0[k * BLK];
 #pragma unroll
-        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
+        for (int q = 1; q < NP; ++q) dws += sD0[((size_t)q * K + k) * BLK];
+        double dw = scale2(widen(dws), sE[k * BLK]);
         hsum = fma(widen(lin[(slot_H32(m) + k) * ldl + i]), dw, hsum);
         if constexpr (RHS) {
             // NASA range on the doubles' bit patterns (T, T_mid > 0), as the double kernels choose it
@@ -763,7 +786,8 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
 // linearization: the pair tables and C_k; apply: dC_k and NP rows of d omega_k partials (and
 // the part sums of the single-precision apply)
 size_t lin_smem(int K, const Shape& sh, int mode) {
-    if (mode == 0 || mode == 5) return (size_t)kMathTabDoubles * sizeof(double) + (size_t)K * sh.blk * sizeof(double);
+    if (mode == 0 || mode == 5)
+        return (size_t)kMathTabDoubles * sizeof(double) + (size_t)K * sh.blk * (mode == 5 ? 12 : 8);
     if (mode == 3 || mode == 4) return lin32_smem(K, sh.blk, sh.np);
     return (size_t)(1 + sh.np) * K * sh.blk * sizeof(double);
 }
@@ -831,7 +855,7 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, int K, int64_t
 }  // namespace
 
 int64_t lin_slots(const DevMech& m) { return slot_H(m) + m.K; }
-int64_t lin_slots_f32(const DevMech& m) { return slot_E32(m) + m.R; }
+int64_t lin_slots_f32(const DevMech& m) { return slot_EK32(m) + m.K; }
 
 cudaError_t launch_linearize(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, const double* dlnA, double* lin, int64_t ldl, cudaStream_t s) {

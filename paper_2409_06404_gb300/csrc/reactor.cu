@@ -46,6 +46,7 @@ namespace {
 
 constexpr int kElemBlk = 256;
 constexpr int kRedBlk = 256;
+constexpr int kRedPerSM = 4;                 // resident reduction blocks per SM (the grid's size)
 constexpr int kMaxDots = NK_REACTOR_MAX_KRYLOV + 2;
 
 // row (0 = T, k + 1 = Y_k) and point of entry e of a (K+1)-row vector of n points
@@ -124,12 +125,15 @@ __global__ void form_kernel(int64_t N, const float* __restrict__ vj, const doubl
 // NORM: also the partial sums of |w|^2, into part[b][nv] (nv = j + 1 basis vectors in all).
 // The dots of a GMRES iteration take ceil(nv / 8) launches of at most 8 vectors each, which
 // keeps the accumulators few and the SMs full (predicated-off double FMAs would still take the
-// FP64 pipe, so the loop bound is NVC, nq rounded up to 4 or 8).
+// FP64 pipe, so the loop bound is NVC, nq rounded up to 4 or 8).  (Double-float products on
+// the FP32 pipe measured no faster here: the kernel is not bound by the FP64 pipe alone.)
 template <bool FORM, bool NORM, int NVC>
-__global__ void __launch_bounds__(kRedBlk) apply_dots_kernel(int64_t N, const float* __restrict__ V, int64_t vstride,
-                                                             int q0, int nq, int nv, const double* __restrict__ Ju,
-                                                             const double* __restrict__ W, double dt,
-                                                             double* __restrict__ w, double* __restrict__ part) {
+__global__ void __launch_bounds__(kRedBlk, kRedPerSM) apply_dots_kernel(int64_t N, const float* __restrict__ V,
+                                                                        int64_t vstride, int q0, int nq, int nv,
+                                                                        const double* __restrict__ Ju,
+                                                                        const double* __restrict__ W, double dt,
+                                                                        double* __restrict__ w,
+                                                                        double* __restrict__ part) {
     __shared__ double red[kRedBlk / 32][NVC + 1];
     double acc[NVC + 1];
 #pragma unroll
@@ -286,7 +290,7 @@ int reduction_blocks() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(1, sms * 4);
+    return std::max(1, sms * kRedPerSM);
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
