@@ -440,7 +440,6 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta_lin;
         int j = 0;
-        bool solved = false;                       // GMRES met lin_tol (or broke down exactly)
         while (j < mk) {
             const float* vj = w.V + (int64_t)j * w.vstride;
             unscale_kernel<<<eg, kElemBlk, 0, s>>>(N, vj, w.iW, w.u);
@@ -496,10 +495,7 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
             ++j;
-            if (std::fabs(g[j]) <= o.lin_tol * beta_lin) {    // relative to this iteration's residual
-                solved = true;
-                break;
-            }
+            if (std::fabs(g[j]) <= o.lin_tol * beta_lin) break;   // relative to this iteration's residual
             if (lost) break;
         }
         // y = R^{-1} g (j columns), then x += (V y) / W
@@ -514,7 +510,6 @@ cudaError_t reactor_step(const DevMech& m, int64_t n, double* T, const double* p
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = fetch(1, 1, w.dots + kMaxDots - 1, hbuf.data())) != cudaSuccess) return e;
         ++st.newton_iters;
-        (void)solved;
         const double del = std::sqrt(hbuf[0]) / sqrtN;
         // convergence test of a stiff ODE solver on the updates (the residual of a stiff
         // system is dominated by rounding long before the iterate stops moving): converged when
