@@ -62,6 +62,31 @@ def test_null_mechanism_is_rejected(lib):
     assert st == 1
 
 
+def test_null_mechanism_is_rejected_by_every_point_entry(lib):
+    """Each entry that takes a mechanism returns NK_EINVAL for NULL before touching the device
+    (the single-precision linearization, its products, the reactor, the Jacobian and
+    block-Jacobi entries, the host-resident evaluation)."""
+    calls = {
+        "nk_rates_linearize": (None, 8, 8, None, None, None, None, None, 8, None),
+        "nk_rates_jvp_linearized": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None),
+        "nk_rates_linearize_f32": (None, 8, 8, None, None, None, None, None, 8, None),
+        "nk_rates_jvp_linearized_f32": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None),
+        "nk_rhs_jvp_linearized": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None, None, None),
+        "nk_rhs_jvp_linearized_f32": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None, None,
+                                      None),
+        "nk_rhs_jacobian": (None, 8, 8, None, None, None, None, 8, None, None, None, 8, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == 1, name
+        assert b"NULL" in lib.nk_last_error() or b"mech" in lib.nk_last_error(), name
+    slots = ctypes.c_int64()
+    assert lib.nk_rates_linearization_slots(None, ctypes.byref(slots)) == 1
+    assert lib.nk_rates_linearization_slots_f32(None, ctypes.byref(slots)) == 1
+    b = ctypes.c_size_t()
+    o = nk.reactor_opts(linearized=2)
+    assert lib.nk_reactor_workspace(None, 8, ctypes.byref(o), ctypes.byref(b)) == 1
+
+
 def _desc(mech):
     d, keep = nk._desc_from(mech)
     return d, keep
