@@ -56,6 +56,13 @@ MUTATIONS = {
                               "(j == k + 1 ? 1.0 : 0.0) + dt * fY[k].imag() / hstep"),
     "rhs_jacobian_transposed": ("Ji[(size_t)(k + 1) * N + j] = f[k].imag() / hstep;",
                                 "Ji[(size_t)j * N + k + 1] = f[k].imag() / hstep;"),
+    "Kc_pressure_factor_inverted": ("ipow(S(P0) / (S(RU) * T), sum_nu)", "ipow(S(RU) * T / S(P0), sum_nu)"),
+    "third_body_factor_on_troe": ("    if (m.rtype[r] == 1) {\n        fwd = fwd * M;",
+                                  "    if (m.rtype[r] != 0) {\n        fwd = fwd * M;"),
+    "troe_Pr_inverted": ("S Pr = k0 * M / kf;", "S Pr = kf * M / k0;"),
+    "efficiencies_ignored": ("M += S(m.eff[(size_t)r * K + k]) * C[k];", "M += C[k];"),
+    "cp_T2_term": ("S(a[2]) * T2 + S(a[3]) * T3", "S(a[2]) * T3 + S(a[3]) * T3"),
+    "mole_fraction_inverted": ("mx.X[k] = Y[k] * mx.Wbar / S(m.W[k]);", "mx.X[k] = Y[k] * S(m.W[k]) / mx.Wbar;"),
     "rhs_jacobian_T_row_column_shift": ("            Ji[j] = ft.imag() / hstep;",
                                         "            Ji[j > 0 ? j - 1 : 0] = ft.imag() / hstep;"),
 }
