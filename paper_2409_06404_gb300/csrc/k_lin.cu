@@ -523,28 +523,41 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
 // by integer operations; the heat-release and source epilogues run in double.
 constexpr float kInvRf = (float)(1.0 / 8.314462618);
 
-// One reaction of the single-precision apply: its compact record (counts, efficiency range,
-// first entry slot, species packed 8 bits each) and its stored words.  The signed coefficients
-// are read from the float table when scattering (L1-resident, not carried across iterations).
-struct Step32 {
-    int nrnp, eff0, eff1, spR, spP, e;     // e: the reaction's exponent (coefficients x 2^e)
+struct Rxn32 {
+    int nr, np, eff0, eff1;
+    int sp[2 * kMaxSide];
+    float nud[2 * kMaxSide];
+};
+
+__device__ __forceinline__ Rxn32 load_rxn32(const DevMech& m, int r) {
+    Rxn32 x;
+    const int4* q = reinterpret_cast<const int4*>(m.rxn + r) + 6;
+    const int4 h = __ldg(q), h2 = __ldg(q + 1), s0 = __ldg(q + 2), s1 = __ldg(q + 3);
+    x.nr = h.y;
+    x.np = h.z;
+    x.eff0 = h2.y;
+    x.eff1 = h2.z;
+    x.sp[0] = s0.x; x.sp[1] = s0.y; x.sp[2] = s0.z; x.sp[3] = s0.w;
+    x.sp[4] = s1.x; x.sp[5] = s1.y; x.sp[6] = s1.z; x.sp[7] = s1.w;
+    const float4* f = reinterpret_cast<const float4*>(m.f_nud + (size_t)r * 2 * kMaxSide);
+    const float4 a = __ldg(f), b = __ldg(f + 1);
+    x.nud[0] = a.x; x.nud[1] = a.y; x.nud[2] = a.z; x.nud[3] = a.w;
+    x.nud[4] = b.x; x.nud[5] = b.y; x.nud[6] = b.z; x.nud[7] = b.w;
+    return x;
+}
+
+struct LinCoef32 {
     float A, L;
     float Br[kMaxSide], Bp[kMaxSide];
+    int e;                                  // the reaction's exponent: coefficients x 2^e
 };
 
 template <int KIND>
-__device__ __forceinline__ Step32 load_step32(const DevMech& m, int r, const float* __restrict__ lin, int64_t ldl,
-                                              int64_t i) {
-    Step32 c;
-    const int4 a = __ldg(m.f_rec + 2 * r), b = __ldg(m.f_rec + 2 * r + 1);
-    c.nrnp = a.x;
-    c.eff0 = a.y;
-    c.eff1 = a.z;
-    c.spR = b.x;
-    c.spP = b.y;
-    const int nr = a.x & 0xff, np = a.x >> 8;
+__device__ __forceinline__ LinCoef32 load_coef32(const DevMech& m, int r, const float* __restrict__ lin, int64_t ldl,
+                                                 int64_t i, int nr, int np) {
+    LinCoef32 c;
     c.A = lin[(int64_t)r * ldl + i];
-    const float* B = lin + (int64_t)a.w * ldl + i;
+    const float* B = lin + ((int64_t)m.R + __ldg(m.lin_boff + r)) * ldl + i;
 #pragma unroll
     for (int e = 0; e < kMaxSide; ++e) {
         c.Br[e] = e < nr ? B[(int64_t)e * ldl] : 0.0f;
@@ -571,49 +584,49 @@ __device__ __forceinline__ double scale2(double v, int e) {
 // 2^d as a float for an integer d <= 0 (zero below -126)
 __device__ __forceinline__ float pow2f(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.0f; }
 
-// Reactions [r0, r1) of one kind; the stored words of the next two reactions are in flight
-// while one is contracted (the loop is bound by load latency, not arithmetic).
 template <int BLK, int KIND>
 __device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, const float* sdC, float* sD,
                                               const int* sE, const float* __restrict__ lin, int64_t ldl, int64_t i,
                                               float tT, float dpRT) {
     if (r0 >= r1) return;
-    Step32 c0 = load_step32<KIND>(m, r0, lin, ldl, i), c1;
-    if (r0 + 1 < r1) c1 = load_step32<KIND>(m, r0 + 1, lin, ldl, i);
+    Rxn32 x = load_rxn32(m, r0);
+    LinCoef32 c = load_coef32<KIND>(m, r0, lin, ldl, i, x.nr, x.np);
     for (int r = r0; r < r1; ++r) {
-        Step32 c2;
-        if (r + 2 < r1) c2 = load_step32<KIND>(m, r + 2, lin, ldl, i);
-        const int nr = c0.nrnp & 0xff, np = c0.nrnp >> 8;
-        float dq = c0.A * tT;
+        Rxn32 xn;
+        LinCoef32 cn;
+        if (r + 1 < r1) {
+            xn = load_rxn32(m, r + 1);
+            cn = load_coef32<KIND>(m, r + 1, lin, ldl, i, xn.nr, xn.np);
+        }
+        float dq = c.A * tT;
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
-            if (e < nr) dq = fmaf(c0.Br[e], sdC[((c0.spR >> (8 * e)) & 0xff) * BLK], dq);
+            if (e < x.nr) dq = fmaf(c.Br[e], sdC[x.sp[e] * BLK], dq);
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
-            if (e < np) dq = fmaf(c0.Bp[e], sdC[((c0.spP >> (8 * e)) & 0xff) * BLK], dq);
+            if (e < x.np) dq = fmaf(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
         if (KIND != 0) {
             float dM = dpRT;
-            for (int j = c0.eff0; j < c0.eff1; ++j)
+            for (int j = x.eff0; j < x.eff1; ++j)
                 dM = fmaf(__ldg(m.f_eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
-            dq = fmaf(c0.L, dM, dq);
+            dq = fmaf(c.L, dM, dq);
         }
-        const float4* nf = reinterpret_cast<const float4*>(m.f_nud + (size_t)r * 2 * kMaxSide);
-        const float4 na = __ldg(nf), nb = __ldg(nf + 1);
-        const float nuR[kMaxSide] = {na.x, na.y, na.z, na.w}, nuP[kMaxSide] = {nb.x, nb.y, nb.z, nb.w};
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
-            if (e < nr) {
-                const int k = ((c0.spR >> (8 * e)) & 0xff) * BLK;
-                sD[k] = fmaf(nuR[e] * pow2f(c0.e - sE[k]), dq, sD[k]);
+            if (e < x.nr) {
+                const int k = x.sp[e] * BLK;
+                sD[k] = fmaf(x.nud[e] * pow2f(c.e - sE[k]), dq, sD[k]);
             }
 #pragma unroll
         for (int e = 0; e < kMaxSide; ++e)
-            if (e < np) {
-                const int k = ((c0.spP >> (8 * e)) & 0xff) * BLK;
-                sD[k] = fmaf(nuP[e] * pow2f(c0.e - sE[k]), dq, sD[k]);
+            if (e < x.np) {
+                const int k = x.sp[kMaxSide + e] * BLK;
+                sD[k] = fmaf(x.nud[kMaxSide + e] * pow2f(c.e - sE[k]), dq, sD[k]);
             }
-        c0 = c1;
-        c1 = c2;
+        if (r + 1 < r1) {
+            x = xn;
+            c = cn;
+        }
     }
 }
 

@@ -338,14 +338,6 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
         lin_boff[q] = lin_nb;
         lin_nb += rxn[q].nr + rxn[q].np;
     }
-    std::vector<int4> f_rec((size_t)2 * R);            // (species indices < kMaxK = 256 fit 8 bits)
-    for (int q = 0; q < R; ++q) {
-        int spR = 0, spP = 0;
-        for (int e = 0; e < rxn[q].nr; ++e) spR |= rxn[q].sp[e] << (8 * e);
-        for (int e = 0; e < rxn[q].np; ++e) spP |= rxn[q].sp[nk::kMaxSide + e] << (8 * e);
-        f_rec[2 * q] = int4{rxn[q].nr | (rxn[q].np << 8), rxn[q].eff0, rxn[q].eff1, R + lin_boff[q]};
-        f_rec[2 * q + 1] = int4{spR, spP, 0, 0};
-    }
     // Jacobian assembly terms (nk_internal.cuh): for every entry a of reaction q (species k,
     // signed coefficient nu), V_k gets nu A_q; G_k,j gets nu B_q,b for every entry b (species j)
     // and, for third-body and Troe reactions, Lam_k gets nu L_q and G_k,j nu (eps_j - 1) L_q for
@@ -448,7 +440,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16),
                  o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16),
                  o_fnud = L.add(f_nud.size() * 4), o_feff = L.add(f_effm1.size() * 4 + 16),
-                 o_fcp = L.add(f_cp.size() * 4), o_frec = L.add(f_rec.size() * sizeof(int4));
+                 o_fcp = L.add(f_cp.size() * 4);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -497,7 +489,6 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_fnud, f_nud.data(), f_nud.size() * 4);
     put(o_feff, f_effm1.data(), f_effm1.size() * 4);
     put(o_fcp, f_cp.data(), f_cp.size() * 4);
-    put(o_frec, f_rec.data(), f_rec.size() * sizeof(int4));
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -573,7 +564,6 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.f_nud = reinterpret_cast<const float*>(b + o_fnud);
     dm.f_eff_m1 = reinterpret_cast<const float*>(b + o_feff);
     dm.f_cp = reinterpret_cast<const float*>(b + o_fcp);
-    dm.f_rec = reinterpret_cast<const int4*>(b + o_frec);
     *out = m;
     return ok();
 }

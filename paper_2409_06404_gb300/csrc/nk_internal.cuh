@@ -150,9 +150,6 @@ struct DevMech {
     const float* f_nud;           // [R][2 kMaxSide]
     const float* f_eff_m1;
     const float* f_cp;
-    // compact reaction records of the single-precision apply, [R][2]: (nr | np << 8, eff0, eff1,
-    // first entry slot R + lin_boff), (reactant species, 8 bits each; product species; -, -)
-    const int4* f_rec;
     // Jacobian assembly: species row k has the terms [jac_row[k], jac_row[k+1]) of jac_term,
     // grouped by destination in increasing order, each group in reaction order
     const int32_t* jac_row;       // [K+1]
