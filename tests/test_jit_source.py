@@ -36,9 +36,10 @@ def test_too_small_buffer_is_an_error(mech9):
 
 
 @pytest.mark.skipif(not os.path.exists(NVRTC), reason="NVRTC not installed")
-def test_source_compiles_with_nvrtc(mech9):
+@pytest.mark.parametrize("name", ["h2_9sp_21rx", "ch4_53sp_325rx"])
+def test_source_compiles_with_nvrtc(name):
     lib = ctypes.CDLL(NVRTC)
-    src = nk.jit_source(mech9).encode()
+    src = nk.jit_source(synth.mechanism(name)).encode()
     hdr = open(os.path.join(os.path.dirname(nk.__file__), "csrc", "nk_math.cuh")).read().encode()
     prog = ctypes.c_void_p()
     hs = (ctypes.c_char_p * 1)(hdr)
