@@ -280,6 +280,39 @@ nk_status nk_rhs_jvp_linearized_f32(const nk_mech* mech, int64_t n, int64_t ld, 
                                     double* dfY, nk_stream stream);
 
 /*
+ * The stored linearization in a per-reaction ("compact") form, for fields whose per-entry data
+ * (nk_rates_linearize) would not fit: the Newton-Krylov stage's several products at one state
+ * (Sec. 2 and 4) on the largest fields.  Kept per point: per reaction the forward and reverse
+ * terms (k_f prod C^nu' and k_r prod C^nu'', times [M] for third-body reactions), the
+ * coefficient of dT/T and, for third-body and Troe reactions, of d[M]; per species h_k/RT, 1/Y_k
+ * and C_k -- about half the per-entry form's doubles (1,180 per point at 53 species and 325
+ * reactions, against 2,112).  The products then need no concentration product: each side's
+ * tangent is its term times sum_e nu_e dC_e/C_e, with dC_e/C_e = d rho/rho + dY_e/Y_e.  Sides
+ * with a mass fraction below 2^-200 in magnitude, zero or non-finite keep k without the
+ * product and are formed by exclusive products instead, so zero and absent species are exact.
+ *   *slots   doubles per point (nk_rates_linearization_slots_compact; depends on the mechanism)
+ *   lin      device [slots][ldl], ldl >= n, caller-owned; written by nk_rates_linearize_compact
+ *   omega[K*ld], hrr[n]   both NULL, or also written: the rates at the state, as nk_rates_eval
+ *            (NK_FP64) computes them, from the same pass (NK_EINVAL if only one is given)
+ * nk_rates_jvp_linearized_compact forms (d_omega, d_hrr) = J (vT, vY) from lin and the state lin
+ * was made at (same T, p, Y, dlnA); nk_rhs_jvp_linearized_compact the sources' JVP given the
+ * sources there, as nk_rhs_jvp_linearized.  Results agree with nk_rates_jvp to rounding (the
+ * FP64 form's linearization, plain double products).
+ */
+nk_status nk_rates_linearization_slots_compact(const nk_mech* mech, int64_t* slots);
+nk_status nk_rates_linearize_compact(const nk_mech* mech, int64_t n, int64_t ld, const double* T, const double* p,
+                                     const double* Y, const double* dlnA, double* lin, int64_t ldl, double* omega,
+                                     double* hrr, nk_stream stream);
+nk_status nk_rates_jvp_linearized_compact(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                                          const double* p, const double* Y, const double* lin, int64_t ldl,
+                                          const double* vT, const double* vY, double* d_omega, double* d_hrr,
+                                          nk_stream stream);
+nk_status nk_rhs_jvp_linearized_compact(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
+                                        const double* p, const double* Y, const double* lin, int64_t ldl,
+                                        const double* fT, const double* fY, const double* vT, const double* vY,
+                                        double* dfT, double* dfY, nk_stream stream);
+
+/*
  * Rates (nk_rates_eval) and transport (nk_transport_eval) of fields that live in host memory,
  * the library's end-to-end entry: the points are cut into chunks of `chunk`, each copied to
  * the device, evaluated and copied back, the chunks cycling over three internal streams so that
@@ -454,15 +487,20 @@ nk_status nk_rates_vjp(const nk_mech* mech, int64_t n, int64_t ld, const double*
  * which a caller in the middle of asynchronous work on several streams must avoid.
  *
  * Same arguments, results and errors as nk_rates_vjp, except that the per-block ln A partial
- * sums go to a fixed scratch array compiled into the library (8 MiB, held on every GPU that
- * loads the library until the process exits).  If g_lnA would need more than that (more than
- * 1024 reactions at full occupancy; see nk_rates_vjp_workspace), the call returns
- * NK_EUNSUPPORTED and enqueues nothing.  The first call on a device looks up the scratch
- * address on that device (make that first call before any stream capture); later calls only
- * read a cached pointer.  All calls share the one scratch array: calls that overlap on the
- * GPU (on different streams, or from different host threads without ordering) race and
- * corrupt each other's g_lnA; order them on one stream.  Every call overwrites the partial
- * sums it reads, so nothing needs clearing between calls.
+ * sums go to a fixed scratch array compiled into the library (2^20 doubles = 8 MiB, held on
+ * every GPU that loads the library until the process exits).  g_lnA needs one R-vector per
+ * block of the VJP's persistent grid (SMs x resident VJP blocks, at most the blocks n needs):
+ * on a 152-SM GB300 that allows about 3,400 reactions when 2 VJP blocks are resident per SM
+ * (53 species), about 1,700 with 4.  nk_rates_vjp_workspace gives the exact bytes a call
+ * needs; above 8 MiB the call returns NK_EUNSUPPORTED and enqueues nothing.  The first call on
+ * a device looks up the scratch address on that device (make that first call before any
+ * stream capture); later calls read the cached pointer.  The cache lives as long as the
+ * process: after cudaDeviceReset (or anything else that destroys the device's primary
+ * context) the cached address is stale, so do not call this entry again in that process.
+ * All calls share the one scratch array: calls that overlap on the GPU (on different
+ * streams, or from different host threads without ordering) race and corrupt each other's
+ * g_lnA; order them on one stream.  Every call overwrites the partial sums it reads, so
+ * nothing needs clearing between calls.
  */
 nk_status nk_rates_vjp_noalloc(const nk_mech* mech, int64_t n, int64_t ld, const double* T,
                                const double* p, const double* Y, const double* dlnA,

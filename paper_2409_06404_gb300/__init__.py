@@ -101,6 +101,11 @@ _SIGS = {
     "nk_rhs_jvp_linearized_f32": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64] + [_vp] * 6 + [_vp]),
     "nk_rates_jvp_linearized": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                                _vp]),
+    "nk_rates_linearization_slots_compact": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "nk_rates_linearize_compact": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "nk_rates_jvp_linearized_compact": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp,
+                                                       _vp, _vp]),
+    "nk_rhs_jvp_linearized_compact": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64] + [_vp] * 6 + [_vp]),
     "nk_rates_vjp_workspace": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "nk_rates_vjp": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 10 + [ctypes.c_size_t, _vp]),
     "nk_rates_vjp_noalloc": (ctypes.c_int, [_vp, _i64, _i64] + [_vp] * 9 + [_vp]),
@@ -495,6 +500,61 @@ def rates_jvp_linearized(m: Mechanism, T, p, Y, lin, vT, vY, stream=None):
     return d_omega, d_hrr
 
 
+def linearization_slots_compact(m: Mechanism) -> int:
+    """Doubles per point of the per-reaction (compact) rates linearization."""
+    v = _i64()
+    _check(lib().nk_rates_linearization_slots_compact(m.handle, ctypes.byref(v)))
+    return v.value
+
+
+def rates_linearize_compact(m: Mechanism, T, p, Y, dlnA=None, lin=None, primal=False, stream=None):
+    """nk_rates_linearize_compact: the per-reaction linearization at (T, p, Y), a device tensor
+    [slots_compact, n]; with primal=True also (omega, hrr) at the state from the same pass:
+    returns (lin, omega, hrr)."""
+    import torch
+    n, ld = _state(m, T, p, Y)
+    _vec(dlnA, m.R, "dlnA")
+    if lin is None:
+        lin = torch.empty((linearization_slots_compact(m), max(n, 1)), dtype=torch.float64, device=T.device)
+    _check_lin(m, lin, n, compact=True)
+    omega = _species_out(m, n, ld, T) if primal else None
+    hrr = _point_out(n, T) if primal else None
+    _check(lib().nk_rates_linearize_compact(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(dlnA), _ptr(lin),
+                                            lin.stride(0), _ptr(omega), _ptr(hrr), _stream(stream)))
+    return (lin, omega, hrr) if primal else lin
+
+
+def rates_jvp_linearized_compact(m: Mechanism, T, p, Y, lin, vT, vY, stream=None):
+    """nk_rates_jvp_linearized_compact: (d_omega, d_hrr) = J (vT, vY) from rates_linearize_compact."""
+    n, ld = _state(m, T, p, Y)
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    _check_lin(m, lin, n, compact=True)
+    d_omega = _species_out(m, n, ld, T)
+    d_hrr = _point_out(n, T)
+    _check(lib().nk_rates_jvp_linearized_compact(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin),
+                                                 lin.stride(0), _ptr(vT), _ptr(vY), _ptr(d_omega), _ptr(d_hrr),
+                                                 _stream(stream)))
+    return d_omega, d_hrr
+
+
+def rhs_jvp_linearized_compact(m: Mechanism, T, p, Y, lin, fT, fY, vT, vY, stream=None):
+    """nk_rhs_jvp_linearized_compact: (dfT, dfY) = J_f (vT, vY) from rates_linearize_compact and the
+    sources at the same state."""
+    n, ld = _state(m, T, p, Y)
+    _check_lin(m, lin, n, compact=True)
+    _vec(fT, n, "fT")
+    _species_in(m, fY, n, ld, "fY")
+    _vec(vT, n, "vT")
+    _species_in(m, vY, n, ld, "vY")
+    dfY = _species_out(m, n, ld, T)
+    dfT = _point_out(n, T)
+    _check(lib().nk_rhs_jvp_linearized_compact(m.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(lin),
+                                               lin.stride(0), _ptr(fT), _ptr(fY), _ptr(vT), _ptr(vY), _ptr(dfT),
+                                               _ptr(dfY), _stream(stream)))
+    return dfT, dfY
+
+
 def linearization_slots_f32(m: Mechanism) -> int:
     """32-bit words per point of the single-precision rates linearization."""
     v = _i64()
@@ -602,10 +662,13 @@ def block_jacobi_apply(m: Mechanism, F, piv, v, stream=None):
     return z
 
 
-def _check_lin(m, lin, n, dtype=None):
+def _check_lin(m, lin, n, dtype=None, compact=False):
     import torch
     dtype = dtype or torch.float64
-    slots = linearization_slots(m) if dtype == torch.float64 else linearization_slots_f32(m)
+    if compact:
+        slots = linearization_slots_compact(m)
+    else:
+        slots = linearization_slots(m) if dtype == torch.float64 else linearization_slots_f32(m)
     if lin.dtype != dtype:
         raise ValueError(f"lin must be {dtype}, got {lin.dtype}")
     if lin.dim() != 2 or lin.shape[0] != slots or lin.stride(1) != 1 or lin.shape[1] < n:

@@ -30,7 +30,7 @@
 #include <utility>
 #include <vector>
 
-#include "nk_rxn.cuh"
+#include "nk_lin.cuh"
 
 namespace nk {
 namespace {
@@ -73,11 +73,6 @@ __device__ __forceinline__ double exclusive_products(const double* p, int n, dou
         }
     }
 }
-
-struct LinPoint {
-    TPairs P;
-    double invT, lnT, pRT;
-};
 
 // a stored value: as is, or rounded to float (integer operations: no FP64-pipe conversion)
 __device__ __forceinline__ void put(double* q, double v) { *q = v; }
@@ -171,69 +166,11 @@ __device__ __forceinline__ void lin_reaction(const DevMech& m, int r, const doub
     const double fw = exclusive_products(pR, x.nr, exR);
     const double rv = exclusive_products(pP, x.np, exP);
 
-    dfl dG, dH, dCp;
-    rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
-    const double sumh = df_to_d(dH), sumcp = df_to_d(dCp);
-    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
-    double shift = 0.0;
-    dfl shiftd{0.0f, 0.0f};
-    if (dlnA) {
-        shift = __ldg(dlnA + x.orig);
-        shiftd = df_split(shift);
-    }
-    const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
-    const double c1 = fma(x.EaR, Q.invT, x.beta);     // d ln k_inf / (dT/T)
-
-    double M = 0.0;
-    if (KIND != 0) {
-        M = Q.pRT;
-        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
-    }
-    double kf, kr, aT = c1, aM = 0.0;
-    if constexpr (KIND == 2) {
-        if (M == 0.0) {
-            kf = kr = aT = 0.0;
-        } else {
-            const TroeRec* t = m.troe + x.aux;
-            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
-            const double lnk0 = fma(-Ea0R, Q.invT, fma(beta0, Q.lnT, __ldg(&t->lnA0) + shift));
-            const double c0 = fma(Ea0R, Q.invT, beta0);
-            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
-            // tangents of the chain for (tT, d[M]) = (1, 0) and (0, 1)
-            const double dPrT = c0 - c1, dPrM = 1.0 / M;
-            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
-            double Fc = (1.0 - a) * e3 + a * e1;
-            double dFcT = -((1.0 - a) * i3 * e3 + a * i1 * e1) * Q.P.T;
-            if (__ldg(&t->hasT2) != 0.0) {
-                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
-                Fc += e2;
-                dFcT = fma(T2 * Q.invT, e2, dFcT);
-            }
-            const double lFc = dlog_df(Fc, dt) * kInvLn10, dlFcT = dFcT / Fc * kInvLn10;
-            const double c = fma(-0.67, lFc, -0.4), nn = fma(-1.27, lFc, 0.75);
-            const double u = fma(lnPr, kInvLn10, c);
-            const double duT = fma(dPrT, kInvLn10, -0.67 * dlFcT), duM = dPrM * kInvLn10;
-            const double v = fma(-0.14, u, nn);
-            const double dvT = fma(-0.14, duT, -1.27 * dlFcT), dvM = -0.14 * duM;
-            const double f1 = u / v;
-            const double df1T = fma(-f1, dvT, duT) / v, df1M = fma(-f1, dvM, duM) / v;
-            const double den = fma(f1, f1, 1.0);
-            const double lF = lFc / den;
-            const double dlFT = fma(-2.0 * lF * f1, df1T, dlFcT) / den, dlFM = -2.0 * lF * f1 * df1M / den;
-            const double g = 1.0 / (1.0 + dexp_df(-lnPr, dt));       // P_r / (1 + P_r)
-            kf = exp_df_d(lnkf, dt.e2) * g * dexp_df(lF * kLn10, dt);
-            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
-            aT = c1 + dPrT * (1.0 - g) + kLn10 * dlFT;
-            aM = dPrM * (1.0 - g) + kLn10 * dlFM;
-        }
-    } else {
-        kf = exp_df_d(lnkf, dt.e2);
-        kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
-    }
+    const RateTerms rt = rate_terms<BLK, KIND>(m, r, x, sC, Q, dlnA, dt);
+    const double kf = rt.kf, kr = rt.kr, aT = rt.aT, aM = rt.aM, M = rt.M, sumcp = rt.sumcp;
     const double qr = kr * rv;
     const double qc = fma(kf, fw, -qr);
-    const double D = sumh - x.dnu;
+    const double D = rt.D;
     const double sc = KIND == 1 ? M : 1.0;              // third body: q = q_c [M]
     S1 = fma(qc * sc, sumcp, S1);
     if (!live) return;
@@ -291,12 +228,8 @@ __global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, co
     // float format: the species' exponent scales E_k (K ints per point after C_k)
     int* sE = F32 ? reinterpret_cast<int*>(smem + kMathTabDoubles + (size_t)K * BLK) + slot : nullptr;
 
-    LinPoint Q;
     const double Ti = T[i];
-    Q.invT = 1.0 / Ti;
-    Q.pRT = p[i] * Q.invT * kInvR;
-    Q.P = make_tpairs(Ti, Q.invT, dt);
-    Q.lnT = df_to_d(Q.P.lnTd);
+    const LinPoint Q = make_lin_point(Ti, p[i], dt);
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double rho = Q.pRT / s;
@@ -462,53 +395,8 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
     apply_group<BLK, 2>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
     if (NP > 1) __syncthreads();
 
-    double hsum = 0.0, cpm = 0.0, dcpm = 0.0, inv_rho = 0.0;
-    if constexpr (RHS) inv_rho = 1.0 / rho;
-    for (int k = part; k < K; k += NP) {
-        double dw = sD0[k * BLK];
-#pragma unroll
-        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
-        hsum = fma(lin[(slot_H(m) + k) * ldl + i], dw, hsum);
-        if constexpr (RHS) {
-            const double* c = nasa_range(m, k, Ti);
-            const double iw = __ldg(m.invW + k), cpk = nasa_cpR(c, Ti);
-            const double yk = Y[(int64_t)k * ld + i] * iw, vk = vY[(int64_t)k * ld + i] * iw;
-            cpm = fma(yk, cpk, cpm);
-            dcpm = fma(vk, cpk, fma(yk * nasa_dcpR_dT(c, Ti), dT, dcpm));
-            dw = fma(__ldg(m.W + k) * inv_rho, dw, -fY[(int64_t)k * ldf + i] * arho);
-        }
-        if (live) d_omega[(int64_t)k * ld + i] = dw;
-    }
-    if constexpr (NP > 1) {
-        // dC_k is dead: rows q, NP + q, 2 NP + q take part q's sums ((1 + 2 RHS) NP <= K)
-        sdC[part * BLK] = hsum;
-        if constexpr (RHS) {
-            sdC[(NP + part) * BLK] = cpm;
-            sdC[(2 * NP + part) * BLK] = dcpm;
-        }
-        __syncthreads();
-        if (part != 0) return;
-        hsum = sdC[0];
-        if constexpr (RHS) {
-            cpm = sdC[NP * BLK];
-            dcpm = sdC[2 * NP * BLK];
-        }
-#pragma unroll
-        for (int q = 1; q < NP; ++q) {
-            hsum += sdC[q * BLK];
-            if constexpr (RHS) {
-                cpm += sdC[(NP + q) * BLK];
-                dcpm += sdC[(2 * NP + q) * BLK];
-            }
-        }
-    }
-    if (live) {
-        const double dhr = -kR * fma(dT, lin[slot_S(m) * ldl + i], Ti * hsum);
-        if constexpr (RHS)
-            d_hrr[i] = fma(dhr, inv_rho / (kR * cpm), -fT[i] * (arho + dcpm / cpm));
-        else
-            d_hrr[i] = dhr;
-    }
+    lin_epilogue<BLK, NP, RHS>(m, part, live, i, Ti, dT, rho, arho, sD0, sdC, lin + slot_H(m) * ldl + i,
+                               lin + slot_S(m) * ldl + i, ldl, Y, vY, ld, fT, fY, ldf, d_omega, d_hrr);
 }
 
 // ---------------------------------------------------------------- FP32 apply pass

@@ -445,7 +445,9 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles
 
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {};   // device address of the array, per device ordinal
+// device address of the array, per device ordinal, for the life of the process (a device reset
+// would invalidate it; the entry point's documentation says not to call it after one)
+void* g_noalloc_ptr[64] = {};
 }  // namespace
 
 cudaError_t noalloc_scratch(void** ptr) {

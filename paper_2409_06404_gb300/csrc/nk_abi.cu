@@ -416,6 +416,13 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                        f_cp((size_t)K * 2 * 8, 0.0f);
     for (int q = 0; q < R; ++q)
         for (int e = 0; e < 2 * nk::kMaxSide; ++e) f_nud[(size_t)q * 2 * nk::kMaxSide + e] = (float)rxn[q].nud[e];
+    std::vector<double> lc_w((size_t)R * 2 * nk::kMaxSide, 0.0);
+    for (int q = 0; q < R; ++q)
+        for (int side = 0; side < 2; ++side) {
+            const int ne = side ? rxn[q].np : rxn[q].nr, b = side * nk::kMaxSide;
+            for (int e = 0; e < ne; ++e)
+                lc_w[(size_t)q * 2 * nk::kMaxSide + b + e] = (double)rxn[q].nu[b + e] / (double)rxn[q].nu[b];
+        }
     for (int k = 0; k < K; ++k)
         for (int range = 0; range < 2; ++range)
             for (int j = 0; j < 5; ++j)
@@ -440,7 +447,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16),
                  o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16),
                  o_fnud = L.add(f_nud.size() * 4), o_feff = L.add(f_effm1.size() * 4 + 16),
-                 o_fcp = L.add(f_cp.size() * 4);
+                 o_fcp = L.add(f_cp.size() * 4 + 16), o_lcw = L.add(lc_w.size() * 8);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -489,6 +496,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_fnud, f_nud.data(), f_nud.size() * 4);
     put(o_feff, f_effm1.data(), f_effm1.size() * 4);
     put(o_fcp, f_cp.data(), f_cp.size() * 4);
+    put(o_lcw, lc_w.data(), lc_w.size() * 8);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -564,6 +572,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.f_nud = reinterpret_cast<const float*>(b + o_fnud);
     dm.f_eff_m1 = reinterpret_cast<const float*>(b + o_feff);
     dm.f_cp = reinterpret_cast<const float*>(b + o_fcp);
+    dm.lc_w = reinterpret_cast<const double*>(b + o_lcw);
     *out = m;
     return ok();
 }
@@ -620,6 +629,21 @@ nk_status check_out(std::initializer_list<const void*> ptrs) {
 nk_status launched(cudaError_t e, const char* what) {
     if (e != cudaSuccess) return cuda_fail(e, what);
     return ok();
+}
+
+// g_lnA of a VJP over no points: zero, after the checks the other calls make (the mechanism's
+// device is current, the array aligned).  NULL g_lnA: nothing to do.
+nk_status zero_grad(const nk_mech* m, double* g_lnA, nk_stream stream) {
+    if (!g_lnA) return ok();
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != m->device)
+        return fail(NK_EINVAL, "mechanism lives on device %d but device %d is current", m->device, dev);
+    nk_status st = check_out({g_lnA});
+    if (st != NK_OK) return st;
+    return launched(cudaMemsetAsync(g_lnA, 0, sizeof(double) * m->d.R, (cudaStream_t)stream),
+                    "cudaMemsetAsync(g_lnA)");
 }
 
 }  // namespace
@@ -949,6 +973,58 @@ nk_status nk_rates_jvp_linearized(const nk_mech* m, int64_t n, int64_t ld, const
                     "linearized jvp kernel launch");
 }
 
+nk_status nk_rates_linearization_slots_compact(const nk_mech* m, int64_t* slots) {
+    if (!m || !slots) return fail(NK_EINVAL, "mech and slots must not be NULL");
+    *slots = nk::linc_slots(m->d);
+    return ok();
+}
+
+nk_status nk_rates_linearize_compact(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                     const double* Y, const double* dlnA, double* lin, int64_t ldl, double* omega,
+                                     double* hrr, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin) return fail(NK_EINVAL, "lin must not be NULL");
+    if ((omega == nullptr) != (hrr == nullptr)) return fail(NK_EINVAL, "omega and hrr are both given or both NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, dlnA, omega, hrr})) != NK_OK) return st;
+    return launched(nk::launch_linearize_compact(m->d, n, ld, T, p, Y, dlnA, lin, ldl, omega, hrr,
+                                                 (cudaStream_t)stream),
+                    "compact linearize kernel launch");
+}
+
+nk_status nk_rates_jvp_linearized_compact(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                          const double* Y, const double* lin, int64_t ldl, const double* vT,
+                                          const double* vY, double* d_omega, double* d_hrr, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !vT || !vY || !d_omega || !d_hrr)
+        return fail(NK_EINVAL, "lin, vT, vY, d_omega and d_hrr must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, vT, vY, d_omega, d_hrr})) != NK_OK) return st;
+    return launched(nk::launch_jvp_linearized_compact(m->d, n, ld, T, p, Y, lin, ldl, nullptr, nullptr, 0, vT, vY,
+                                                      d_hrr, d_omega, (cudaStream_t)stream, 0),
+                    "compact linearized jvp kernel launch");
+}
+
+nk_status nk_rhs_jvp_linearized_compact(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
+                                        const double* Y, const double* lin, int64_t ldl, const double* fT,
+                                        const double* fY, const double* vT, const double* vY, double* dfT,
+                                        double* dfY, nk_stream stream) {
+    bool skip;
+    nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
+    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (!lin || !fT || !fY || !vT || !vY || !dfT || !dfY)
+        return fail(NK_EINVAL, "lin, fT, fY, vT, vY, dfT and dfY must not be NULL");
+    if (ldl < n) return fail(NK_EINVAL, "ldl=%lld < n=%lld", (long long)ldl, (long long)n);
+    if ((st = check_out({lin, fT, fY, vT, vY, dfT, dfY})) != NK_OK) return st;
+    return launched(nk::launch_jvp_linearized_compact(m->d, n, ld, T, p, Y, lin, ldl, fT, fY, ld, vT, vY, dfT, dfY,
+                                                      (cudaStream_t)stream, 1),
+                    "compact linearized sources jvp kernel launch");
+}
+
 nk_status nk_rates_linearization_slots_f32(const nk_mech* m, int64_t* slots) {
     if (!m || !slots) return fail(NK_EINVAL, "mech and slots must not be NULL");
     *slots = nk::lin_slots_f32(m->d);
@@ -1009,14 +1085,10 @@ nk_status nk_rates_vjp(const nk_mech* m, int64_t n, int64_t ld, const double* T,
                        const double* Y, const double* dlnA, const double* bar_omega, const double* bar_hrr,
                        double* gT, double* gY, double* g_lnA, void* workspace, size_t workspace_bytes,
                        nk_stream stream) {
-    if (m && g_lnA && n == 0) {
-        // the gradient of an empty sum is zero
-        cudaError_t e = cudaMemsetAsync(g_lnA, 0, sizeof(double) * m->d.R, (cudaStream_t)stream);
-        return launched(e, "cudaMemsetAsync(g_lnA)");
-    }
     bool skip;
     nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
-    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (st != NK_OK) return st;
+    if (skip) return zero_grad(m, g_lnA, stream);           // the gradient of an empty sum is zero
     if (!bar_omega || !gT || !gY) return fail(NK_EINVAL, "bar_omega, gT and gY must not be NULL");
     if ((st = check_out({bar_omega, bar_hrr, gT, gY, g_lnA, dlnA, workspace})) != NK_OK) return st;
     if (g_lnA) {
@@ -1033,13 +1105,10 @@ nk_status nk_rates_vjp(const nk_mech* m, int64_t n, int64_t ld, const double* T,
 nk_status nk_rates_vjp_noalloc(const nk_mech* m, int64_t n, int64_t ld, const double* T, const double* p,
                                const double* Y, const double* dlnA, const double* bar_omega,
                                const double* bar_hrr, double* gT, double* gY, double* g_lnA, nk_stream stream) {
-    if (m && g_lnA && n == 0) {
-        cudaError_t e = cudaMemsetAsync(g_lnA, 0, sizeof(double) * m->d.R, (cudaStream_t)stream);
-        return launched(e, "cudaMemsetAsync(g_lnA)");
-    }
     bool skip;
     nk_status st = check_eval(m, n, ld, T, p, Y, &skip);
-    if (st != NK_OK || skip) return st == NK_OK ? ok() : st;
+    if (st != NK_OK) return st;
+    if (skip) return zero_grad(m, g_lnA, stream);
     if (!bar_omega || !gT || !gY) return fail(NK_EINVAL, "bar_omega, gT and gY must not be NULL");
     if ((st = check_out({bar_omega, bar_hrr, gT, gY, g_lnA, dlnA})) != NK_OK) return st;
     void* scratch = nullptr;

@@ -154,6 +154,9 @@ struct DevMech {
     // grouped by destination in increasing order, each group in reaction order
     const int32_t* jac_row;       // [K+1]
     const JacTerm* jac_term;      // [terms]
+    // per-reaction stored linearization (k_linc.cu): entry weights nu_e / nu_first of each side
+    // (reactants at [0, nr), products at [kMaxSide, kMaxSide + np); nu_first the side's first entry)
+    const double* lc_w;           // [R][2 kMaxSide]
 };
 
 // Centre of the re-expanded transport fits (ln T about 1100 K).
@@ -262,6 +265,18 @@ cudaError_t launch_jvp_linearized_f32(const DevMech& m, int64_t n, int64_t ld, c
                                       const double* Y, const float* lin, int64_t ldl, const double* fT,
                                       const double* fY, int64_t ldf, const double* vT, const double* vY,
                                       double* d_T, double* d_Y, cudaStream_t s, int rhs);
+// Per-reaction (compact) stored linearization (k_linc.cu): per reaction the rate constants and
+// the coefficients of their tangents, per species 1/Y_k and C_k; the concentration products are
+// formed again per direction.  omega, hrr: NULL, or also the rates at the state (FP64 form).
+// rhs = 1 in the product: the sources' JVP (fT, fY given), as launch_rhs_jvp_linearized.
+int64_t linc_slots(const DevMech& m);
+cudaError_t launch_linearize_compact(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                     const double* Y, const double* dlnA, double* lin, int64_t ldl, double* omega,
+                                     double* hrr, cudaStream_t s);
+cudaError_t launch_jvp_linearized_compact(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                                          const double* Y, const double* lin, int64_t ldl, const double* fT,
+                                          const double* fY, int64_t ldf, const double* vT, const double* vY,
+                                          double* d_T, double* d_Y, cudaStream_t s, int rhs);
 cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                        const double* Y, const double* dlnA, const double* bar_omega,
                        const double* bar_hrr, double* gT, double* gY, double* g_lnA,

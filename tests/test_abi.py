@@ -75,6 +75,10 @@ def test_null_mechanism_is_rejected_by_every_point_entry(lib):
         "nk_rhs_jvp_linearized_f32": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None, None,
                                       None),
         "nk_rhs_jacobian": (None, 8, 8, None, None, None, None, 8, None, None, None, 8, None),
+        "nk_rates_linearize_compact": (None, 8, 8, None, None, None, None, None, 8, None, None, None),
+        "nk_rates_jvp_linearized_compact": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None),
+        "nk_rhs_jvp_linearized_compact": (None, 8, 8, None, None, None, None, 8, None, None, None, None, None, None,
+                                          None),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == 1, name
@@ -82,6 +86,7 @@ def test_null_mechanism_is_rejected_by_every_point_entry(lib):
     slots = ctypes.c_int64()
     assert lib.nk_rates_linearization_slots(None, ctypes.byref(slots)) == 1
     assert lib.nk_rates_linearization_slots_f32(None, ctypes.byref(slots)) == 1
+    assert lib.nk_rates_linearization_slots_compact(None, ctypes.byref(slots)) == 1
     b = ctypes.c_size_t()
     o = nk.reactor_opts(linearized=2)
     assert lib.nk_reactor_workspace(None, 8, ctypes.byref(o), ctypes.byref(b)) == 1

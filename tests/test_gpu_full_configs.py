@@ -113,6 +113,46 @@ def test_implicit_stage_16M_points_sampled(cuda):
         del dw, dh
 
 
+def test_implicit_stage_16M_points_compact_sampled(cuda):
+    """The implicit-stage workload with the per-reaction stored linearization (158 GB at
+    16,777,216 points, beside the 7.4 GB state): one pass giving the rates at the state and the
+    stored data, then ten JVPs along the same seeded directions as the recomputing sweep, three
+    of them sampled against the oracle (1e-10)."""
+    mech = synth.mechanism("ch4_53sp_325rx")
+    m = gpu_mechanism("ch4_53sp_325rx")
+    st = synth.workload_states("flame_32768el", mech.K)
+    n, K = st.n, mech.K
+    assert n == 16_777_216
+    T, p, Y = to_dev(st.T, st.p, st.Y)
+    rng = np.random.default_rng(55)
+    idx = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 800, replace=False)]))
+    Ts, ps, Ys = st.T[idx], st.p[idx], np.ascontiguousarray(st.Y[:, idx])
+    del st
+    sub = torch.from_numpy(idx).cuda()
+    lin, w, h = nk.rates_linearize_compact(m, T, p, Y, primal=True)
+    w_o, h_o, ws, hs = oracle.rates(mech, Ts, ps, Ys, scales=True)
+    assert scaled_err(host(w[:, sub]), w_o, ws) <= TOL64
+    assert scaled_err(host(h[sub]), h_o, hs) <= TOL64
+    assert torch.isfinite(h).all()
+    del w, h
+    vT = torch.empty(n, dtype=torch.float64, device="cuda")
+    vY = torch.empty((K, n), dtype=torch.float64, device="cuda")
+    for d in range(10):
+        g = torch.Generator(device="cuda").manual_seed(5000 + d)
+        torch.randn(n, generator=g, out=vT)
+        torch.randn((K, n), generator=g, out=vY)
+        dw, dh = nk.rates_jvp_linearized_compact(m, T, p, Y, lin, vT, vY)
+        if d in (0, 4, 9):
+            vTs, vYs = host(vT[sub]), np.ascontiguousarray(host(vY[:, sub]))
+            dw_o, dh_o, dws, dhs = oracle.jvp(mech, Ts, ps, Ys, vTs, vYs, scales=True)
+            assert scaled_err(host(dw[:, sub]), dw_o, dws) <= TOL64, d
+            assert scaled_err(host(dh[sub]), dh_o, dhs) <= TOL64, d
+        assert torch.isfinite(dh).all()
+        del dw, dh
+    del lin
+    torch.cuda.empty_cache()
+
+
 def test_reactor_step_full_size_sampled(cuda):
     """The reactor step at the benchmark's size (2,097,152 points, 53 species), unpreconditioned,
     block-Jacobi and with single-precision products (linearized 2), on near-equilibrium states built as the benchmark builds them (512
