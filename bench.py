@@ -43,68 +43,78 @@ METRIC = "Mpoints/s rates+transport (FP64 vs mixed), % roofline; VJP/forward tim
 UNIT = "Mpoints/s"
 MECH = "ch4_53sp_325rx"
 WORKLOAD = "flame_4096el"
-# FP64 peak of GB300: 1.25 TFLOP/s nominal dense FP64 (vendor figure at the maximum SM clock)
-FP64_PEAK_TFLOPS = 1.25
-# flops charged per exp/log/pow: table-driven exponential after Tang (1989): argument
-# reduction (2 FMA), degree-5 polynomial (5 FMA), table scaling (1 multiply) = 15 flops
-TRANSC_FLOPS = 15.0
+# nominal dense FP64 of GB300 (vendor figure), for context beside the measured pipe rates
+FP64_NOMINAL_TFLOPS = 1.25
 
 
-# ---------------------------------------------------------------------------------- flop model
-def _entries(mech, r):
-    reac = [(int(mech.reac_sp[i]), int(mech.reac_nu[i])) for i in range(mech.reac_ptr[r], mech.reac_ptr[r + 1])]
-    prod = [(int(mech.prod_sp[i]), int(mech.prod_nu[i])) for i in range(mech.prod_ptr[r], mech.prod_ptr[r + 1])]
-    return reac, prod
+# ---------------------------------------------------------------------------------- roofline inputs
+# Kernels of this library are bound by the FP64 pipe or the FP32 (FMA) pipes.  Their per-pipe
+# roofline: the pipe operations a kernel issues per point (ncu counters of the same kernels,
+# profiles/pipe_counts.json) x points / CUDA-event time, against the pipe's operation rate measured
+# in this run by the probe library.  The algorithmic operation counts of the definitions (the
+# oracle's instrumented scalar, profiles/algorithmic_ops.json) are reported beside them.
+PROBE_KINDS = {"dfma": 0, "dmul": 1, "dadd": 2, "ffma": 3, "fmul": 4, "fadd": 5}
 
 
-def algorithmic_flops(mech) -> dict:
-    """FP64 flops per point of each row (FMA = 2, exp/log = TRANSC_FLOPS).  Minimal arithmetic
-    of the evaluated definitions, independent of how a kernel organises it."""
-    import numpy as np
-    t = TRANSC_FLOPS
-    K, R = mech.K, mech.R
-    P = K * (K - 1) // 2
-    n_eff = [int(np.sum(mech.eff[r] != 1.0)) if mech.rtype[r] else 0 for r in range(R)]
-    pre = 2 * t + 4 + K * (3 + 14)                 # ln T, 1/T, rho; y_k, sum, C_k, g_k/RT
-    per_rxn, per_rxn_d = 0.0, 0.0
-    for r in range(R):
-        reac, prod = _entries(mech, r)
-        ne = len(reac) + len(prod)
-        nu_r = sum(nu for _, nu in reac)
-        nu_p = sum(nu for _, nu in prod)
-        f = 4 + 2 * ne + 2 + (nu_r - 1) + (nu_p - 1) + 2 * t + 3 + 2 * ne
-        if mech.rtype[r] == 1:
-            f += 1 + 2 * n_eff[r]
-        if mech.rtype[r] == 2:
-            f += 2 * n_eff[r] + 4 + 2 + t + (3 if mech.troe[r, 3] > 0 else 2) * t + 4 + t + 12 + 3 + t + 2 + t + 2
-        per_rxn += f
-        # tangent (JVP) or adjoint (VJP) of the same operations: the product rule doubles every
-        # multiply, plus the chain factors of each exponential
-        per_rxn_d += f + (4 + 2 * ne + 2 + 2 * (nu_r + nu_p) + 8 + 2 * ne) + (40 if mech.rtype[r] == 2 else 0)
-    hrr = K * 14 + 2
-    rates = pre + per_rxn + hrr
-    transport = (t + 4 + 3 * K                      # ln T, Wbar, X_k
-                 + P * (6 + t + 1 + 4)              # ln D_jk cubic, exp, pressure scale, two FMA
-                 + K * 4                            # numerators (prefix/suffix) and division
-                 + K * (6 + 2 * t + 4)              # lambda_k, 1/lambda_k, two FMA
-                 + K * (6 + t + 2)                  # mu_k^1/2, sigma_k, tau_k
-                 + K * 4 + K * K * 6                # X tau, X tau^2; three FMA per pair
-                 + K * 8)                           # Wilke denominators and the mixture sum
-    thermo = 2 * t + 4 + K * (3 + 10 + 12 + 14 + 4)
-    jvp = pre + K * 16 + per_rxn_d + hrr * 2 + K * 10
-    vjp = pre + K * 24 + per_rxn_d + 10 * R + K * 8
-    rhs = rates + K * 12 + 4                        # W_k/rho factors, c_p, 1/(rho c_p)
-    rhs_jvp = jvp + K * 24 + 12                     # primal omega, c_p and d c_p, both source tangents
-    # per direction from stored coefficients: dq_r = A tT + sum_e B_e dC_e (+ L d[M]), the scatter
-    n_ent = sum(len(_entries(mech, r)[0]) + len(_entries(mech, r)[1]) for r in range(R))
-    jvp_lin = 2 * R + 2 * n_ent + 2 * n_ent + sum(2 * n_eff[r] + 4 for r in range(R) if mech.rtype[r]) \
-        + K * (6 + 4) + K * 2 + 4
-    return {"thermo": thermo, "rates_fp64": rates, "transport_fp64": transport, "rates_fp64_native": rates,
-            "rates_jit": rates,
-            "transport_fp64_native": transport, "rates_mixed": rates, "transport_mixed": transport, "jvp": jvp,
-            "vjp": vjp, "rhs_fp64": rhs, "rhs_jvp": rhs_jvp, "linearize": jvp, "jvp_linearized": jvp_lin,
-            "linearize_f32": jvp, "jvp_linearized_f32": jvp_lin,
-            "diffusion": K * (3 + 6 + 6 + 9 + 10) + 12}
+def pipe_peaks():
+    """Thread-level operations per second of the FP64 pipe (double multiply-add, multiply, add) and
+    the FP32 FMA pipes (float), measured now: independent streams on every SM, 8 blocks of 256
+    threads per SM, best of 5 CUDA-event-timed launches (libnkprobe.so)."""
+    import ctypes
+    from paper_2409_06404_gb300 import build as nkbuild
+    L = ctypes.CDLL(nkbuild.PROBE_LIB)
+    L.nkp_pipe_rate.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_double)]
+    L.nkp_pipe_rate.restype = ctypes.c_int
+    out = {}
+    for name, kind in PROBE_KINDS.items():
+        v = ctypes.c_double()
+        st = L.nkp_pipe_rate(kind, 8, 2048 if kind < 3 else 32768, 5, ctypes.byref(v))
+        if st != 0:
+            raise RuntimeError(f"pipe probe {name} failed ({st})")
+        out[name] = v.value
+    return out
+
+
+def _json_profile(name):
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def pipe_counts():
+    """Per-point pipe operation counts of each row's kernels (profiles/pipe_counts.json), for the rows
+    none of whose source files changed since the capture."""
+    rec = _json_profile("pipe_counts.json") or {}
+    good = {}
+    for row, r in rec.get("rows", {}).items():
+        try:
+            if _sources_sha256(r["sources"]) == r["sources_sha256"]:
+                good[row] = r
+        except (OSError, KeyError):
+            continue
+    return good
+
+
+def row_pipes(row_counts, n, ms, peaks):
+    """Per-pipe fractions of one row: warp instructions per point x 32 lanes x n / time, against the
+    probe's multiply-add rate of that pipe (a warp instruction occupies the pipe for a full warp,
+    whatever its active lanes)."""
+    t = ms * 1e-3
+    res = {}
+    for pipe, peak in (("fp64", peaks["dfma"]), ("fma", peaks["ffma"])):
+        ops = row_counts[f"{pipe}_warp_inst_per_point"] * 32.0
+        achieved = ops * n / t
+        res[pipe] = {"ops_per_point": ops, "gops": achieved / 1e9, "peak_gops": peak / 1e9, "frac": achieved / peak}
+    return res
+
+
+def algorithmic(mech_name):
+    rec = _json_profile("algorithmic_ops.json")
+    if not rec:
+        return {}
+    return rec.get("mechanisms", {}).get(mech_name, {}).get("per_point", {})
 
 
 # ---------------------------------------------------------------------------------- clocks
@@ -207,21 +217,44 @@ def _oracle_sample(n_points):
     return oracle, mech, st
 
 
+def _oracle_rate(oracle, mech, T, p, Y, threads):
+    t0 = time.perf_counter()
+    oracle.rates(mech, T, p, Y, threads=threads)
+    oracle.transport(mech, T, p, Y, threads=threads)
+    dt = time.perf_counter() - t0
+    return T.shape[0] / dt / 1e6, dt
+
+
 def cpu_baseline(st_full, n_points=524288):
-    """Oracle rates + transport (FP64) on the first n_points points, all host cores."""
+    """The oracle as it stands (rates + transport, FP64) on bounded samples of the workloads, on all
+    host cores (OpenMP over points) and on one thread: the benchmark field (first n_points points)
+    and the configurations of the 9- and 120-species mechanisms."""
     import numpy as np
     import oracle
     from paper_2409_06404_gb300 import synth
     mech = synth.mechanism(MECH)
     n_points = min(n_points, st_full.n)
     T, p, Y = st_full.T[:n_points], st_full.p[:n_points], np.ascontiguousarray(st_full.Y[:, :n_points])
-    t0 = time.perf_counter()
-    oracle.rates(mech, T, p, Y)
-    oracle.transport(mech, T, p, Y)
-    dt = time.perf_counter() - t0
-    return {"value": n_points / dt / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"first {n_points} points ({n_points // 512} elements) of the {WORKLOAD} workload, "
-                      f"rates + transport FP64, OpenMP over points, {dt:.1f} s"}
+    v, dt = _oracle_rate(oracle, mech, T, p, Y, 0)
+    n1 = min(16384, n_points)
+    v1, dt1 = _oracle_rate(oracle, mech, T[:n1], p[:n1], np.ascontiguousarray(Y[:, :n1]), 1)
+    res = {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "nproc": os.cpu_count(), "kind": "oracle",
+           "sample": f"first {n_points} points ({n_points // 512} elements) of the {WORKLOAD} workload, "
+                     f"rates + transport FP64, OpenMP over points, {dt:.1f} s",
+           "one_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                          "sample": f"first {n1} points of {WORKLOAD}, {dt1:.1f} s"}}
+    configs = {}
+    for name, wl, n_all, n_one in (("h2_9sp_21rx", "uniform_64el", 32768, 32768),
+                                   ("big_120sp_700rx", "flame_4096el", 65536, 4096)):
+        mc = synth.mechanism(name)
+        sc = synth.workload_states(wl, mc.K, n_points=n_all)
+        va, da = _oracle_rate(oracle, mc, sc.T, sc.p, sc.Y, 0)
+        vo, do = _oracle_rate(oracle, mc, sc.T[:n_one], sc.p[:n_one], np.ascontiguousarray(sc.Y[:, :n_one]), 1)
+        configs[name] = {"all_cores": va, "one_thread": vo, "unit": UNIT,
+                         "sample": f"first {n_all} points of {wl} ({da:.1f} s); one thread: first {n_one} "
+                                   f"({do:.1f} s)"}
+    res["configs"] = configs
+    return res
 
 
 # ---------------------------------------------------------------------------------- reference arm
@@ -257,82 +290,190 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------------- implicit stage
 def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
-    """One implicit-stage sweep as a Newton-Krylov stage issues it: one forward (thermo FP64,
-    rates and transport mixed) and n_dir exact JVPs along N(0, 1) directions, against the
-    plain-FP64 forward and n_dir finite-difference JVPs (NITSOL step per point,
-    sigma = sqrt((1 + |x|) eps) / |v|) on the same GPU.  Directions are generated before the
-    timed region; each sweep is timed with CUDA events on the launching stream."""
+    """Implicit-stage sweeps as a Newton-Krylov stage issues them: a forward at the state and n_dir
+    exact JVPs along seeded N(0, 1) directions, against the plain-FP64 forward and n_dir
+    finite-difference JVPs (NITSOL step per point, sigma = sqrt((1 + |x|) eps) / |v|) on the same
+    GPU.  Exact sweeps:
+      recompute  thermo (FP64), rates and transport (mixed), then nk_rates_jvp per direction (the
+                 rates of progress formed again for every product);
+      compact    thermo (FP64), transport (mixed), nk_rates_linearize_compact, which also gives the
+                 rates at the state (FP64), then nk_rates_jvp_linearized_compact per direction;
+      per-entry  the same forward as recompute plus nk_rates_linearize, then
+                 nk_rates_jvp_linearized per direction (only where its data fit: not at 16.8M points).
+    Each direction is drawn (seeded, on the device) before its product, outside the timed spans;
+    a sweep's time is the sum of CUDA-event spans around its forward and its n_dir products on the
+    launching stream (one direction buffer stays resident instead of n_dir)."""
     import torch
     n, K = T.shape[0], Y.shape[0]
-    gen = torch.Generator(device=T.device).manual_seed(5000)
-    dirs = [(torch.randn(n, generator=gen, dtype=torch.float64, device=T.device),
-             torch.randn((K, n), generator=gen, dtype=torch.float64, device=T.device)) for _ in range(n_dir)]
+    f64 = dict(dtype=torch.float64, device=T.device)
+    vT = torch.empty(n, **f64)
+    vY = torch.empty((K, n), **f64)
     eps = 2.220446049250313e-16
-    xnorm = torch.sqrt(T * T + (Y * Y).sum(0))
 
-    def ours():
-        nk.thermo_eval(m, T, p, Y)
-        nk.rates_eval(m, T, p, Y, precision="mixed")
-        nk.transport_eval(m, T, p, Y, precision="mixed")
-        out = None
-        for vT, vY in dirs:
-            out = nk.rates_jvp(m, T, p, Y, vT, vY)
-        return out
+    def direction(d):
+        g = torch.Generator(device=T.device).manual_seed(5000 + d)
+        torch.randn(n, generator=g, out=vT)
+        torch.randn((K, n), generator=g, out=vY)
 
-    def fd():
-        nk.thermo_eval(m, T, p, Y)
-        w0, h0 = nk.rates_eval(m, T, p, Y)
-        nk.transport_eval(m, T, p, Y)
-        out = None
-        for vT, vY in dirs:
-            sig = torch.sqrt((1.0 + xnorm) * eps) / torch.sqrt(vT * vT + (vY * vY).sum(0))
-            w1, h1 = nk.rates_eval(m, T + sig * vT, p, Y + sig * vY)
-            out = ((w1 - w0) / sig, (h1 - h0) / sig)
-        return out
+    def sweep(forward, product):
+        spans = []
 
-    def timed(f):
-        f()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(steps):
+        def span(fn):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            f()
+            out = fn()
             b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return sum(ts) / len(ts)
+            spans.append((a, b))
+            return out
 
-    lin = None
-    try:
-        lin = torch.empty((nk.linearization_slots(m), n), dtype=torch.float64, device=T.device)
-    except RuntimeError:                       # the stored data do not fit: recompute only
-        pass
+        ctx = span(forward)
+        for d in range(n_dir):
+            direction(d)
+            span(lambda: product(ctx))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in spans)
 
-    def ours_lin():
-        nk.thermo_eval(m, T, p, Y)
+    def timed(forward, product):
+        sweep(forward, product)                       # warm-up
+        return sum(sweep(forward, product) for _ in range(steps)) / steps
+
+    def fwd_mixed():
+        nk.thermo_eval(m, T, p, Y, species=False)
         nk.rates_eval(m, T, p, Y, precision="mixed")
         nk.transport_eval(m, T, p, Y, precision="mixed")
-        nk.rates_linearize(m, T, p, Y, lin=lin)
-        out = None
-        for vT, vY in dirs:
-            out = nk.rates_jvp_linearized(m, T, p, Y, lin, vT, vY)
-        return out
 
-    t_ours, t_fd = timed(ours), timed(fd)
-    t_lin = timed(ours_lin) if lin is not None else None
-    # accuracy of the difference quotient against the exact JVP, last direction
-    dw, dh = nk.rates_jvp(m, T, p, Y, *dirs[-1])
-    fw, fh = fd()
-    sc = dw.abs().amax(0).clamp_min(1e-300)
-    fd_err = ((fw - dw).abs().amax(0) / sc).median().item()
-    res = {"points": n, "directions": n_dir, "sweep_ms": t_ours, "fd_fp64_sweep_ms": t_fd,
-           "speedup_vs_fd": t_fd / t_ours, "fd_jvp_median_rel_err": fd_err,
-           "sweep": "thermo (FP64) + rates, transport (mixed) + exact JVPs recomputed per direction",
-           "fd_sweep": "thermo, rates, transport (FP64) + FP64 rates at x + sigma v per direction"}
-    if t_lin is not None:
-        res.update({"sweep_linearized_ms": t_lin, "speedup_linearized_vs_fd": t_fd / t_lin,
-                    "sweep_linearized": "the same forward + one stored linearization + exact JVPs from it"})
+    def recompute(_):
+        return nk.rates_jvp(m, T, p, Y, vT, vY)
+
+    def fwd_fd():
+        xnorm = torch.sqrt(T * T + (Y * Y).sum(0))
+        nk.thermo_eval(m, T, p, Y, species=False)
+        w0, h0 = nk.rates_eval(m, T, p, Y)
+        nk.transport_eval(m, T, p, Y)
+        return xnorm, w0, h0
+
+    def fd(ctx):
+        xnorm, w0, h0 = ctx
+        sig = torch.sqrt((1.0 + xnorm) * eps) / torch.sqrt(vT * vT + (vY * vY).sum(0))
+        w1, h1 = nk.rates_eval(m, T + sig * vT, p, Y + sig * vY)
+        return (w1 - w0) / sig, (h1 - h0) / sig
+
+    res = {"points": n, "directions": n_dir,
+           "timing": "sum of CUDA-event spans around the forward and each product; directions drawn "
+                     "outside the spans", "steps": steps}
+    res["fd_fp64_sweep_ms"] = t_fd = timed(fwd_fd, fd)
+    res["sweep_recompute_ms"] = t_re = timed(fwd_mixed, recompute)
+    res["speedup_recompute_vs_fd"] = t_fd / t_re
+
+    # the per-reaction stored linearization, where it fits beside the field
+    slots_c = nk.linearization_slots_compact(m)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    linc = None
+    if slots_c * n * 8 < free - 6 * (K + 2) * n * 8:
+        linc = torch.empty((slots_c, n), **f64)
+
+    if linc is not None:
+        def fwd_compact():
+            nk.thermo_eval(m, T, p, Y, species=False)
+            nk.transport_eval(m, T, p, Y, precision="mixed")
+            return nk.rates_linearize_compact(m, T, p, Y, lin=linc, primal=True)
+
+        def compact(_):
+            return nk.rates_jvp_linearized_compact(m, T, p, Y, linc, vT, vY)
+
+        res["sweep_compact_ms"] = t_c = timed(fwd_compact, compact)
+        res["speedup_compact_vs_fd"] = t_fd / t_c
+        res["compact_bytes"] = slots_c * n * 8
+        # accuracy of the difference quotient against the exact JVP, last direction
+        direction(n_dir - 1)
+        dw, _ = compact(None)
+        fw, _ = fd(fwd_fd())
+        sc = dw.abs().amax(0).clamp_min(1e-300)
+        res["fd_jvp_median_rel_err"] = ((fw - dw).abs().amax(0) / sc).median().item()
+        del dw, fw, sc
+        del linc
+        torch.cuda.empty_cache()
+    lin = None
+    try:
+        lin = torch.empty((nk.linearization_slots(m), n), **f64)
+    except RuntimeError:                           # the per-entry data do not fit
+        pass
+    if lin is not None:
+        def fwd_lin():
+            fwd_mixed()
+            nk.rates_linearize(m, T, p, Y, lin=lin)
+
+        def per_entry(_):
+            return nk.rates_jvp_linearized(m, T, p, Y, lin, vT, vY)
+
+        res["sweep_linearized_ms"] = t_l = timed(fwd_lin, per_entry)
+        res["speedup_linearized_vs_fd"] = t_fd / t_l
+        del lin
+        torch.cuda.empty_cache()
+    best = min((k for k in ("sweep_compact_ms", "sweep_linearized_ms", "sweep_recompute_ms") if k in res),
+               key=lambda k: res[k])
+    res["sweep_ms"] = res[best]
+    res["sweep_form"] = best[len("sweep_"):-len("_ms")]
+    res["speedup_vs_fd"] = t_fd / res[best]
+    return res
+
+
+# ---------------------------------------------------------------------------------- other configurations
+def config_rows(nk, dev, stream):
+    """Rates + transport of the other mechanisms, each launch through the C ABI, CUDA events on the
+    launching stream around `reps` back-to-back launches (after 3 untimed ones):
+      h2_9sp_21rx on 64 elements x 512 = 32,768 points (uniform states), FP64: inputs 2.9 MB, L2-resident,
+        so the per-launch times include launch latency;
+      big_120sp_700rx on the 4,096-element flame field (2,097,152 points), FP64 and mixed."""
+    import torch
+    from paper_2409_06404_gb300 import synth
+    L = nk.lib()
+    sp = nk._vp(stream.cuda_stream)
+    P = lambda t: nk._vp(t.data_ptr())
+    res = {}
+    for name, wl, reps, forms in (("h2_9sp_21rx", "uniform_64el", 50, ("fp64",)),
+                                  ("big_120sp_700rx", "flame_4096el", 5, ("fp64", "mixed"))):
+        mech = synth.mechanism(name)
+        st = synth.workload_states(wl, mech.K)
+        n, K = st.n, mech.K
+        m = nk.mechanism_load(mech)
+        T, p, Y = (torch.from_numpy(a).to(dev) for a in (st.T, st.p, st.Y))
+        f64 = dict(dtype=torch.float64, device=dev)
+        w, D = torch.empty((K, n), **f64), torch.empty((K, n), **f64)
+        h, mu, lam = torch.empty(n, **f64), torch.empty(n, **f64), torch.empty(n, **f64)
+        rec = {"points": n, "K": K, "R": mech.R, "workload": wl, "reps": reps}
+        for form in forms:
+            prec = nk._PRECISION[form]
+
+            def rates():
+                st_ = L.nk_rates_eval(m.handle, n, n, P(T), P(p), P(Y), None, P(w), P(h), prec, sp)
+                if st_ != 0:
+                    raise nk.NkError(st_, L.nk_last_error().decode())
+
+            def trans():
+                st_ = L.nk_transport_eval(m.handle, n, n, P(T), P(p), P(Y), P(mu), P(lam), P(D), prec, sp)
+                if st_ != 0:
+                    raise nk.NkError(st_, L.nk_last_error().decode())
+
+            t = {}
+            for key, f in (("rates", rates), ("transport", trans)):
+                for _ in range(3):
+                    f()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    f()
+                b.record(stream)
+                torch.cuda.synchronize()
+                t[key] = a.elapsed_time(b) / reps
+            rec[form] = {"rates_ms": t["rates"], "transport_ms": t["transport"],
+                         "mpts": n / ((t["rates"] + t["transport"]) * 1e-3) / 1e6}
+        m.close()
+        del T, p, Y, w, D, h, mu, lam
+        torch.cuda.empty_cache()
+        res[name] = rec
     return res
 
 
@@ -450,6 +591,7 @@ def run_ours(args):
     g_lnA = torch.empty(R, **f64)
     lin = torch.empty((nk.linearization_slots(m), n), **f64)    # stored linearization (~18 KB per point)
     lin32 = torch.empty((nk.linearization_slots_f32(m), n), dtype=torch.float32, device=dev)   # single precision
+    linc = torch.empty((nk.linearization_slots_compact(m), n), **f64)   # per-reaction form (~9.4 KB per point)
     gradX = torch.randn((3, K, n), generator=gen, **f64)         # mole-fraction gradients (synthetic)
     jflux = torch.empty((3, K, n), **f64)
     Vc = torch.empty((3, n), **f64)
@@ -498,6 +640,11 @@ def run_ours(args):
         "jvp_linearized_f32": lambda: chk(L.nk_rates_jvp_linearized_f32(h, n, n, P(T), P(p), P(Y), P(lin32), n,
                                                                         P(vT), P(vY), P(out["dw"]), P(out["dh"]),
                                                                         sp)),
+        "linearize_compact": lambda: chk(L.nk_rates_linearize_compact(h, n, n, P(T), P(p), P(Y), None, P(linc), n,
+                                                                      P(out["w"]), P(out["hrr"]), sp)),
+        "jvp_linearized_compact": lambda: chk(L.nk_rates_jvp_linearized_compact(h, n, n, P(T), P(p), P(Y), P(linc),
+                                                                                n, P(vT), P(vY), P(out["dw"]),
+                                                                                P(out["dh"]), sp)),
     }
     # the mechanism-specialised kernel is compiled (NVRTC) before any timing
     t_jit = time.perf_counter()
@@ -511,6 +658,7 @@ def run_ours(args):
         for f in rows.values():
             f()
     torch.cuda.synchronize()
+    peaks = pipe_peaks()
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)] for k in names}
     if ws > 1:
@@ -544,22 +692,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms.update({k: [a.elapsed_time(b) for a, b in fev[k]] for k in forms})
 
+    # ---- the other mechanisms' configurations (not part of a step)
+    configs = config_rows(nk, dev, s) if args.configs else None
+
     # ---- implicit reactor step (not part of a step)
     reactor = reactor_row(nk, m, mech, n, dev, s) if args.reactor else None
-
-    # ---- implicit-stage sweep (not part of a step)
-    stage = None
-    if args.stage_dirs > 0:
-        if args.stage_elements in (None, args.elements):
-            stage = implicit_stage(nk, m, T, p, Y, args.stage_dirs, 3, s)
-        else:
-            st5 = synth.workload_states("flame_32768el" if args.stage_elements == 32768 else WORKLOAD, K,
-                                        n_elements=args.stage_elements)
-            T5, p5, Y5 = (torch.from_numpy(a).to(dev) for a in (st5.T, st5.p, st5.Y))
-            del st5
-            stage = implicit_stage(nk, m, T5, p5, Y5, args.stage_dirs, 2, s)
-            del T5, p5, Y5
-        stage["workload"] = f"{MECH} on {stage['points']} points"
 
     fwd_ms = sum(ms["rates_fp64"]) + sum(ms["transport_fp64"])
     nat_ms = sum(ms["rates_fp64_native"]) + sum(ms["transport_fp64_native"])
@@ -608,24 +745,62 @@ def run_ours(args):
                "api": f"nk_host_eval: page-locked host T, p, Y in and omega, hrr, mu, lambda, D_k out; chunks of "
                       f"{chunk} points over three streams (copies overlap the FP64 kernels)"}
 
+    # ---- implicit-stage sweep (not part of a step), after the workload's buffers are released
+    stage = None
+    if args.stage_dirs > 0:
+        del lin, lin32, linc, gradX, jflux, Vc, hflux, out, wsb, vT, vY, wbar
+        torch.cuda.empty_cache()
+        if args.stage_elements in (0, args.elements):
+            stage = implicit_stage(nk, m, T, p, Y, args.stage_dirs, 3, s)
+        else:
+            st5 = synth.workload_states("flame_32768el" if args.stage_elements == 32768 else WORKLOAD, K,
+                                        n_elements=args.stage_elements)
+            T5, p5, Y5 = (torch.from_numpy(a).to(dev) for a in (st5.T, st5.p, st5.Y))
+            del st5
+            stage = implicit_stage(nk, m, T5, p5, Y5, args.stage_dirs, 2, s)
+            del T5, p5, Y5
+        torch.cuda.empty_cache()
+        stage["workload"] = f"{MECH} on {stage['points']} points"
+
     if rank != 0:
         return
-    # ---- roofline of the dominant kernel (ALU bound: FP64 pipe)
-    fl = algorithmic_flops(mech)
+    # ---- per-pipe rooflines of every row with committed pipe counts, and the dominant kernel's
     avg = {k: sum(v) / len(v) for k, v in ms.items() if k in names}
     avg_f = {k: sum(v) / len(v) for k, v in ms.items() if k in forms}
-    dom = max(names, key=lambda k: avg[k])
-    achieved = fl[dom] * n / (avg[dom] * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic(dom),
-            "peak_source": "nominal dense FP64 of GB300 (1.25 TFLOP/s), no measured FP64 peak in MEASURED_PEAKS.json",
-            "basis": "FP64 flops of the evaluated definitions (FMA = 2, exp/log = 15) per point x points / "
-                     "kernel time; the FP64 form evaluates its exponent chains as float pairs on the FP32 "
-                     "pipe, so it is not confined to the FP64 pipe's rate",
-            "flops_per_point": fl[dom]}
     both = {**avg, **avg_f}
-    rows_out = {k: {"ms": both[k], "mpts": n / (both[k] * 1e-3) / 1e6,
-                    "tflops": fl[k] * n / (both[k] * 1e-3) / 1e12} for k in names + list(forms)}
+    counts = pipe_counts()
+    alg = algorithmic(MECH)
+    rows_out = {}
+    for k in names + list(forms):
+        r = {"ms": both[k], "mpts": n / (both[k] * 1e-3) / 1e6}
+        if k in counts:
+            pp = row_pipes(counts[k], n, both[k], peaks)
+            r["pipe_frac"] = {q: v["frac"] for q, v in pp.items()}
+            r["pipe"] = max(pp, key=lambda q: pp[q]["frac"])
+            r["frac"] = pp[r["pipe"]]["frac"]
+        base = k.split("_")[0]
+        if base in ("rates", "transport") and base in alg and k != "rates_jit":
+            r["alg_tflops"] = alg[base]["flops"] * n / (both[k] * 1e-3) / 1e12
+        rows_out[k] = r
+    dom = max(names, key=lambda k: avg[k])
+    peak_src = ("measured in this run: libnkprobe.so, independent multiply-add streams on every SM "
+                "(profiles/pipe_peaks_gb300.md has a committed run); MEASURED_PEAKS.json has no FP64 or "
+                "FP32-pipe figure")
+    if dom in counts:
+        pp = row_pipes(counts[dom], n, avg[dom], peaks)
+        bind = max(pp, key=lambda q: pp[q]["frac"])
+        roof = {"bound": "alu", "kernel": dom, "pipe": bind, "achieved": pp[bind]["gops"],
+                "peak": pp[bind]["peak_gops"], "unit": "Gop/s", "frac": pp[bind]["frac"], "traffic": _traffic(dom),
+                "pipes": pp, "peak_source": peak_src,
+                "basis": "pipe operations per point (ncu warp instructions of the row's kernels x 32 lanes, "
+                         "profiles/pipe_counts.json) x points / CUDA-event time of the launch, against the "
+                         "pipe's multiply-add rate; frac = the largest over the FP64 and FMA pipes"}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "pipe": None, "achieved": None, "peak": peaks["dfma"] / 1e9,
+                "unit": "Gop/s", "frac": None, "traffic": _traffic(dom), "peak_source": peak_src,
+                "basis": "no pipe counts for the current sources of this kernel"}
+    roof["algorithmic"] = {"source": "profiles/algorithmic_ops.json (oracle's instrumented scalar)",
+                           "per_point": alg}
     fwd_avg = avg["rates_fp64"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -641,6 +816,8 @@ def run_ours(args):
         "vjp_over_fwd": avg["vjp"] / fwd_avg, "jvp_over_fwd": avg["jvp"] / fwd_avg,
         "rows": rows_out,
         "roofline": roof,
+        "pipe_peaks_gops": {k: v / 1e9 for k, v in peaks.items()},
+        "fp64_tflops_measured": 2.0 * peaks["dfma"] / 1e12, "fp64_tflops_nominal": FP64_NOMINAL_TFLOPS,
         "gpu_launches": sum(launches_per_step.values()) * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
@@ -653,6 +830,8 @@ def run_ours(args):
         line["implicit_stage"] = stage
     if reactor is not None:
         line["reactor_step"] = reactor
+    if configs is not None:
+        line["configs"] = configs
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -672,10 +851,13 @@ def main():
                     help="flame field size in elements (a cube; 4096 = the benchmark workload)")
     ap.add_argument("--no-reactor", dest="reactor", action="store_false",
                     help="skip the implicit reactor step measurement")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the 9- and 120-species configuration rows")
     ap.add_argument("--stage-dirs", type=int, default=10,
                     help="JVP directions of the implicit-stage sweep (0 skips it)")
-    ap.add_argument("--stage-elements", type=int, default=None,
-                    help="elements of the implicit-stage field (default: --elements; 32768 = 16,777,216 points)")
+    ap.add_argument("--stage-elements", type=int, default=32768,
+                    help="elements of the implicit-stage field (a cube; 32768 = 16,777,216 points, the "
+                         "implicit-stage workload; 0 = the benchmark field)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

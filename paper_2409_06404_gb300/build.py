@@ -3,7 +3,8 @@
     python -m paper_2409_06404_gb300.build [--force] [--ptxas-v]
 
 Each .cu under csrc/ is compiled by its own nvcc process (in parallel), then linked into
-paper_2409_06404_gb300/_build/libnkchem.so with the CUDA runtime linked statically.
+paper_2409_06404_gb300/_build/libnkchem.so with the CUDA runtime linked statically.  The
+benchmark's pipe-throughput probe (probe/pipe_peaks.cu) is built beside it as libnkprobe.so.
 """
 from __future__ import annotations
 
@@ -21,6 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libnkchem.so")
+PROBE_SRC = os.path.join(HERE, "probe", "pipe_peaks.cu")
+PROBE_LIB = os.path.join(OUT, "libnkprobe.so")     # pipe-throughput probe of the benchmark
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 GEN = os.path.join(OUT, "gen")
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-I", GEN]
@@ -56,10 +59,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    return all(os.path.getmtime(d) <= t for d in _deps()) and os.path.getmtime(PROBE_SRC) <= os.path.getmtime(PROBE_LIB)
 
 
 def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) -> str:
@@ -77,8 +80,22 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, obj, r
 
-    with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+    def build_probe():
+        tmp = PROBE_LIB + f".tmp{os.getpid()}"
+        cmd = [cc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "static", PROBE_SRC,
+               "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, PROBE_LIB)
+        return r
+
+    with ThreadPoolExecutor(max_workers=min(len(srcs) + 1, os.cpu_count() or 4)) as ex:
+        probe = ex.submit(build_probe)
         results = list(ex.map(compile_one, srcs))
+        rp = probe.result()
+    if rp.returncode != 0:
+        sys.stderr.write(rp.stdout + rp.stderr)
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}")
     log = []
     for src, obj, r in results:
         log.append(f"== {os.path.basename(src)}\n{r.stdout}{r.stderr}")
