@@ -31,6 +31,7 @@ namespace {
 struct JvpPoint {
     TPairs P;
     double invT, lnT, tT, dT, pRT, dpRT, arho;   // arho = d rho / rho
+    dfl tTd, pRTd, dpRTd;                        // the logarithmic form's pairs
 };
 
 struct JvpAcc {
@@ -178,6 +179,121 @@ __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const doub
     acc.dh = fma(dq, sumh, acc.dh);
 }
 
+// The logarithmic form (blocks whose mass fractions are all at least 2^-100 and whose direction
+// the pairs can carry; see the kernel).  The point's rows hold ln C_k and r_k = dC_k/C_k =
+// d rho/rho + dY_k/Y_k as pairs, and with F the falloff factor (1 but for Troe reactions)
+//   q_f = F exp(ln k_f + sum_reac nu ln C),   q_r = F exp(ln k_f - ln K_c + sum_prod nu ln C),
+//   dq  = q_f (d ln k_f + sum_reac nu r) - q_r (d ln k_f - d ln K_c + sum_prod nu r),
+// the exponent and tangent sums in pairs; the exponentials' results, the difference, dq, [M]
+// scaling, the scatter and the heat-release sums in double.  No concentration product is
+// formed.
+template <int BLK, int KIND, bool OMEGA, bool RHS>
+__device__ __forceinline__ void jvp_reaction_log(const DevMech& m, int r, const float2* sL, const float2* sR,
+                                                 double* sW, double* sD, const JvpPoint& Q, const double* dlnA,
+                                                 const DfTab& dt, JvpAcc& acc) {
+    const Rxn x = load_rxn(m.rxn + r);
+    const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+    const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+    const dfl gf = side_sum_df<BLK>(sR, x.sp, x.nu, x.nr);
+    const dfl gb = side_sum_df<BLK>(sR, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+    dfl dG, dH, dCp;
+    rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
+    const float dnu = dnu_f(m, r);
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu), df_neg(dG));
+    double shift = 0.0;
+    dfl shiftd{0.0f, 0.0f};
+    if (dlnA) {
+        shift = __ldg(dlnA + x.orig);
+        shiftd = df_split(shift);
+    }
+    const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
+    const float4 a0 = __ldg(m.rxn_df + 2 * r), a1 = __ldg(m.rxn_df + 2 * r + 1);
+    const dfl dlnkf = df_mul(df_fma(dfl{a1.x, a1.y}, Q.P.invTd, dfl{a0.z, a0.w}), Q.tTd);   // (beta + Ea/RT) dT/T
+    const dfl dlnKc = df_mul(Q.tTd, df_add(dH, dfl{-dnu, 0.0f}));                            // (sum nu h/RT - sum nu) dT/T
+
+    double M = 0.0, dM = 0.0;
+    if (KIND != 0) {
+        dfl Mp = Q.pRTd, dMp = Q.dpRTd;
+        for (int j = x.eff0; j < x.eff1; ++j) {
+            const int k = __ldg(m.eff_sp + j);
+            const dfl ec = df_mul(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[k * BLK]), dt.e2));
+            Mp = df_add(Mp, ec);
+            dMp = df_fma(ec, dfl_of(sR[k * BLK]), dMp);
+        }
+        M = df_to_d(Mp);
+        dM = df_to_d(dMp);
+    }
+    double F = 1.0, dlnF = 0.0;                   // Troe: F = g 10^lF and d ln F
+    if constexpr (KIND == 2) {
+        if (M == 0.0) {
+            F = 0.0;
+        } else {
+            const TroeRec* t = m.troe + x.aux;
+            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
+            const double lnk0 = fma(-Ea0R, Q.invT, fma(beta0, Q.lnT, __ldg(&t->lnA0) + shift));
+            const double dlnk0 = fma(Ea0R, Q.invT, beta0) * Q.tT;
+            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
+            const double dlnPr = dlnk0 - df_to_d(dlnkf) + dM / M;
+            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
+            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
+            double Fc = (1.0 - a) * e3 + a * e1;
+            double dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1) * Q.dT;
+            if (__ldg(&t->hasT2) != 0.0) {
+                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
+                Fc += e2;
+                dFc = fma(T2 * Q.invT * e2, Q.tT, dFc);
+            }
+            const double lFc = dlog_df(Fc, dt) * kInvLn10, dlFc = dFc / Fc * kInvLn10;
+            const double c = fma(-0.67, lFc, -0.4), nn = fma(-1.27, lFc, 0.75);
+            const double u = fma(lnPr, kInvLn10, c), du = fma(dlnPr, kInvLn10, -0.67 * dlFc);
+            const double v = fma(-0.14, u, nn), dv = fma(-0.14, du, -1.27 * dlFc);
+            const double f1 = u / v, df1 = fma(-f1, dv, du) / v;
+            const double den = fma(f1, f1, 1.0);
+            const double lF = lFc / den;
+            const double dlF = fma(-2.0 * lF * f1, df1, dlFc) / den;
+            const double g = 1.0 / (1.0 + dexp_df(-lnPr, dt));       // P_r / (1 + P_r)
+            F = g * dexp_df(lF * kLn10, dt);
+            dlnF = dlnPr * (1.0 - g) + kLn10 * dlF;
+        }
+    }
+    double qf = exp_df_d(df_add(lnkf, sf), dt.e2);
+    double qr = exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
+    double Gf = df_to_d(df_add(dlnkf, gf));
+    double Gb = df_to_d(df_add(df_add(dlnkf, df_neg(dlnKc)), gb));
+    if constexpr (KIND == 2) {
+        qf *= F;
+        qr *= F;
+        Gf += dlnF;
+        Gb += dlnF;
+    }
+    double q = qf - qr;
+    double dq = fma(qf, Gf, -qr * Gb);
+    if (KIND == 1) {
+        dq = fma(dq, M, q * dM);
+        q *= M;
+    }
+    const double dqs = RHS ? fma(-Q.arho, q, dq) : dq;
+    scatter_side<BLK>(x.sp, x.nud, x.nr, sD, dqs);
+    scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sD, dqs);
+    if (OMEGA) {
+        scatter_side<BLK>(x.sp, x.nud, x.nr, sW, q);
+        scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sW, q);
+    }
+    const double sumh = df_to_d(dH);
+    acc.h = fma(q, sumh, acc.h);
+    acc.cp = fma(q, df_to_d(dCp), acc.cp);
+    acc.dh = fma(dq, sumh, acc.dh);
+}
+
+template <int BLK, int KIND, bool OMEGA, bool RHS>
+__device__ __forceinline__ void jvp_group_log(const DevMech& m, int r0, int r1, const double* sC, const double* sdC,
+                                              double* sW, double* sD, const JvpPoint& Q, const double* dlnA,
+                                              const DfTab& dt, JvpAcc& acc) {
+    const float2* sL = reinterpret_cast<const float2*>(sC);
+    const float2* sR = reinterpret_cast<const float2*>(sdC);
+    for (int r = r0; r < r1; ++r) jvp_reaction_log<BLK, KIND, OMEGA, RHS>(m, r, sL, sR, sW, sD, Q, dlnA, dt, acc);
+}
+
 template <int BLK, int KIND, bool OMEGA, bool RHS>
 __device__ __forceinline__ void jvp_group(const DevMech& m, int r0, int r1, const double* sC, const double* sdC,
                                           double* sW, double* sD, const JvpPoint& Q, const double* dlnA,
@@ -233,11 +349,38 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
     const double rho = Q.pRT / s;
     const double arho = -Q.tT - ds / s;                  // d rho / rho
     Q.arho = arho;
+    // The logarithmic form needs every Y_k >= 2^-100 (positive, finite) and direction values the
+    // pairs can carry (dY_k/Y_k, dT/T and d rho/rho within 2^+-100 or zero); a block with a point
+    // that has neither takes the dual products in double (C_k, dC_k in the rows) instead.
+    bool bad = !(pair_range_ok(Q.tT) && pair_range_ok(arho));
     for (int k = part; k < K; k += NP) {
-        const double iw = __ldg(m.invW + k);
-        const double c = Y[(int64_t)k * ld + i] * iw * rho;
-        sC[k * BLK] = c;
-        sdC[k * BLK] = fma(c, arho, rho * vY[(int64_t)k * ld + i] * iw);
+        const double y = Y[(int64_t)k * ld + i], v = vY[(int64_t)k * ld + i];
+        bad |= !(log_form_ok(y) && pair_range_ok(v) && quot_range_ok(v, y));
+    }
+    bool direct;
+    if constexpr (NP > 1)
+        direct = __syncthreads_or(bad) != 0;
+    else
+        direct = __any_sync(__activemask(), bad);
+    if (direct) {
+        for (int k = part; k < K; k += NP) {
+            const double iw = __ldg(m.invW + k);
+            const double c = Y[(int64_t)k * ld + i] * iw * rho;
+            sC[k * BLK] = c;
+            sdC[k * BLK] = fma(c, arho, rho * vY[(int64_t)k * ld + i] * iw);
+        }
+    } else {
+        Q.tTd = df_split(Q.tT);
+        Q.pRTd = df_split(Q.pRT);
+        Q.dpRTd = df_neg(df_mul(Q.pRTd, Q.tTd));
+        const dfl ar = df_split(arho);
+        for (int k = part; k < K; k += NP) {
+            const double y = Y[(int64_t)k * ld + i];
+            const dfl l = log_df(y * __ldg(m.invW + k) * rho, dt.rc, dt.lc);
+            const dfl rk = df_add(ar, df_div(df_split(vY[(int64_t)k * ld + i]), df_split(y)));
+            reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
+            reinterpret_cast<float2*>(sdC)[k * BLK] = make_float2(rk.h, rk.l);
+        }
     }
     for (int k = 0; k < K; ++k) {
         sD[k * BLK] = 0.0;
@@ -248,12 +391,21 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
     JvpAcc acc;
     int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    slice<NP>(0, e1, part, a, b);
-    jvp_group<BLK, 0, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
-    slice<NP>(e1, t1, part, a, b);
-    jvp_group<BLK, 1, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
-    slice<NP>(t1, m.R, part, a, b);
-    jvp_group<BLK, 2, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    if (direct) {
+        slice<NP>(0, e1, part, a, b);
+        jvp_group<BLK, 0, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        slice<NP>(e1, t1, part, a, b);
+        jvp_group<BLK, 1, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        slice<NP>(t1, m.R, part, a, b);
+        jvp_group<BLK, 2, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    } else {
+        slice<NP>(0, e1, part, a, b);
+        jvp_group_log<BLK, 0, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        slice<NP>(e1, t1, part, a, b);
+        jvp_group_log<BLK, 1, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        slice<NP>(t1, m.R, part, a, b);
+        jvp_group_log<BLK, 2, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    }
     if (NP > 1) __syncthreads();
 
     // Implicit-stage sources (RHS): fY_k = W_k omega_k / rho, fT = hrr / (rho c_p) with

@@ -88,17 +88,8 @@ __device__ __forceinline__ void linc_reaction(const DevMech& m, int r, const dou
     S1 = fma(qc * sc, rt.sumcp, S1);
     if constexpr (OUT) {
         const double q = qc * sc;
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e) {
-            if (e < x.nr) {
-                double* w = sW + x.sp[e] * BLK;
-                *w = fma(x.nud[e], q, *w);
-            }
-            if (e < x.np) {
-                double* w = sW + x.sp[kMaxSide + e] * BLK;
-                *w = fma(x.nud[kMaxSide + e], q, *w);
-            }
-        }
+        scatter_side<BLK>(x.sp, x.nud, x.nr, sW, q);
+        scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sW, q);
     }
     if (!live) return;
     const double skf = sc * rt.kf, skr = sc * rt.kr;
@@ -294,16 +285,25 @@ __device__ __noinline__ double side_tangent_exact(const double* __restrict__ inv
     return t;
 }
 
-// sum_e w_e r_e over one side (w_0 = 1, w_e = nu_e/nu_0: the stored V carries nu_0)
+// sum_e w_e r_e over one side (w_0 = 1, w_e = nu_e/nu_0: the stored V carries nu_0); a switch on
+// the entry count with each case unrolled exactly (no predicated-off FP64 instructions)
+template <int BLK, int N>
+__device__ __forceinline__ double side_sum_n(const double* w, const double* sR, const int* sp) {
+    double g = sR[sp[0] * BLK];
+#pragma unroll
+    for (int e = 1; e < N; ++e) g = fma(__ldg(w + e), sR[sp[e] * BLK], g);
+    return g;
+}
 template <int BLK>
 __device__ __forceinline__ double side_sum(const DevMech& m, int r, int side, const double* sR, const int* sp,
                                            int ne) {
     const double* w = m.lc_w + ((size_t)r * 2 + side) * kMaxSide;
-    double g = sR[sp[0] * BLK];
-#pragma unroll
-    for (int e = 1; e < kMaxSide; ++e)
-        if (e < ne) g = fma(__ldg(w + e), sR[sp[e] * BLK], g);
-    return g;
+    switch (ne) {
+        case 1: return sR[sp[0] * BLK];
+        case 2: return side_sum_n<BLK, 2>(w, sR, sp);
+        case 3: return side_sum_n<BLK, 3>(w, sR, sp);
+        default: return side_sum_n<BLK, kMaxSide>(w, sR, sp);
+    }
 }
 
 // One side's contribution V g, or, where g is not finite, the exact tangent of a side with a tiny
@@ -352,18 +352,8 @@ __device__ __forceinline__ void applyc_group(const DevMech& m, int r0, int r1, c
             }
             dq = fma(c.L, dM, dq);
         }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.nr) {
-                double* w = sD + x.sp[e] * BLK;
-                *w = fma(x.nud[e], dq, *w);
-            }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.np) {
-                double* w = sD + x.sp[kMaxSide + e] * BLK;
-                *w = fma(x.nud[kMaxSide + e], dq, *w);
-            }
+        scatter_side<BLK>(x.sp, x.nud, x.nr, sD, dq);
+        scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sD, dq);
         if (r + 1 < r1) {
             x = xn;
             c = cn;

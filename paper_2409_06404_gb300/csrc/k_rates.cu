@@ -176,6 +176,63 @@ __device__ __forceinline__ void products(const Rxn& x, const double* sC, double&
         }
 }
 
+// Logarithmic form of the concentration products (kDF and kMixed forms).  The C_k row holds
+// ln C_k as pairs (a zero concentration as -2^100, whose exponential is 0), and each side's
+// product enters its rate term through the exponent:
+//   q_f = exp(ln k_f + sum_reactants nu ln C),  q_r = exp(ln k_f - ln K_c + sum_products nu ln C),
+// one pair exponential each (as k_f and k_r alone took), so no concentration product is formed
+// in double: the FP64 pipe keeps the exponentials' final additions, the forward-minus-reverse
+// difference, [M] and the scatter.  A block with a negative concentration (a negative mass
+// fraction) takes the products in double instead, from the state (Conc).
+// The point's concentrations C_k = rho Y_k / W_k from the state (the products in double).
+struct Conc {
+    const double* Y;
+    const double* invW;
+    int64_t ld, i;
+    double rho;
+    __device__ __forceinline__ double operator()(int k) const {
+        return Y[(int64_t)k * ld + i] * __ldg(invW + k) * rho;
+    }
+};
+
+// Both sides' products in double from the state (Conc).
+__device__ __forceinline__ void products_direct(const Rxn& x, const Conc& cs, double& fw, double& rv) {
+    {
+        const double c = cs(x.sp[0]);
+        fw = c;
+        for (int j = 1; j < x.nu[0]; ++j) fw *= c;
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            const double c = cs(x.sp[e]);
+            for (int j = 0; j < x.nu[e]; ++j) fw *= c;
+        }
+    {
+        const double c = cs(x.sp[kMaxSide]);
+        rv = c;
+        for (int j = 1; j < x.nu[kMaxSide]; ++j) rv *= c;
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.np) {
+            const double c = cs(x.sp[kMaxSide + e]);
+            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) rv *= c;
+        }
+}
+
+// [M] = p/(RT) + sum (eps - 1) C_j: C_j from the logarithms (LOG) or the state
+template <int BLK, bool LOG>
+__device__ __forceinline__ double third_body(const DevMech& m, const Rxn& x, const float2* sL, const Conc& cs,
+                                             const Pt& P, const DfTab& dt) {
+    double M = P.pRT;
+    for (int j = x.eff0; j < x.eff1; ++j) {
+        const int k = __ldg(m.eff_sp + j);
+        M = fma(__ldg(m.eff_m1 + j), LOG ? exp_df_d(dfl_of(sL[k * BLK]), dt.e2) : cs(k), M);
+    }
+    return M;
+}
+
 // Troe factor F * P_r/(1+P_r) with the exponent arithmetic in pairs.
 __device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl lnkinf, dfl lnk0, double M,
                                                  const Pt& P, const DfTab& dt) {
@@ -196,67 +253,72 @@ __device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl 
     return exp_df_d(df_mul(lF, dfc_ln10()), dt.e2) / (1.0 + exp_df_d(df_neg(lnPr), dt.e2));
 }
 
-template <int BLK, int KIND>
-__device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const double* sC,
-                                                      const Pt& P, const double* dlnA, const DfTab& dt) {
-    double fw, rv;
-    products<BLK>(x, sC, fw, rv);
+template <int BLK, int KIND, bool LOG>
+__device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const float2* sL,
+                                                      const Conc& cs, const Pt& P, const double* dlnA,
+                                                      const DfTab& dt) {
     dfl sumg, unused_h, unused_cp;
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
     const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
     dfl shift{0.0f, 0.0f};
     if (dlnA) shift = df_split(__ldg(dlnA + x.orig));
     const dfl lnkf = ln_kf_df(m, r, P.tp, shift, dlnA != nullptr);
-    double M = 0.0;
-    if (KIND != 0) {
-        M = P.pRT;
-        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
-    }
-    double kf, kr;
+    const double M = KIND != 0 ? third_body<BLK, LOG>(m, x, sL, cs, P, dt) : 0.0;
+    double F = 1.0;                                              // Troe: F P_r/(1 + P_r)
     if constexpr (KIND == 2) {
         const float4 t0 = __ldg(m.troe_df + 3 * x.aux);          // (lnA0, beta0)
         const float4 t1 = __ldg(m.troe_df + 3 * x.aux + 1);      // (Ea0/R, 1/T3)
         dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.tp.lnTd, dfl{t0.x, t0.y});
         lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.tp.invTd, lnk0);
         if (dlnA) lnk0 = df_add(lnk0, shift);
-        kf = M == 0.0 ? 0.0 : exp_df_d(lnkf, dt.e2) * troe_factor_df(m, x.aux, lnkf, lnk0, M, P, dt);
-        kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
-    } else {
-        kf = exp_df_d(lnkf, dt.e2);
-        kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
+        F = M == 0.0 ? 0.0 : troe_factor_df(m, x.aux, lnkf, lnk0, M, P, dt);
     }
-    double q = fma(kf, fw, -kr * rv);
+    double q;
+    if constexpr (LOG) {
+        const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+        const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+        q = exp_df_d(df_add(lnkf, sf), dt.e2) - exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
+        if (KIND == 2) q *= F;
+    } else {
+        double fw, rv, kf, kr;
+        products_direct(x, cs, fw, rv);
+        if constexpr (KIND == 2) {
+            kf = F == 0.0 ? 0.0 : exp_df_d(lnkf, dt.e2) * F;
+            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+        } else {
+            kf = exp_df_d(lnkf, dt.e2);
+            kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
+        }
+        q = fma(kf, fw, -kr * rv);
+    }
     if (KIND == 1) q *= M;
     return q;
 }
 
 // Mixed form: k_f and the whole Troe falloff in single precision; the Gibbs sum and K_c from
-// the reaction's thermo groups in pairs, products and the difference in double.
-template <int BLK, int KIND>
-__device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const Rxn& x, int r, const double* sC,
-                                                         const Pt& P, const double* dlnA, const DfTab& dt) {
-    double fw, rv;
-    products<BLK>(x, sC, fw, rv);
+// the reaction's thermo groups in pairs, the exponent sums of the rate terms in pairs (the
+// single-precision ln k_f enters both terms alike, so q keeps the FP64 difference of
+// K_c-consistent terms), the difference in double.
+template <int BLK, int KIND, bool LOG>
+__device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const Rxn& x, int r, const float2* sL,
+                                                         const Conc& cs, const Pt& P, const double* dlnA,
+                                                         const DfTab& dt) {
     dfl sumg, unused_h, unused_cp;
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
     const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
     const float shf = dlnA ? (float)__ldg(dlnA + x.orig) : 0.0f;
-    double M = 0.0;
-    if (KIND != 0) {
-        M = P.pRT;
-        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
-    }
+    const double M = KIND != 0 ? third_body<BLK, LOG>(m, x, sL, cs, P, dt) : 0.0;
     const float4 xf = __ldg(reinterpret_cast<const float4*>(m.rxnf + r));   // lnA, beta, EaR
     const float lnkf = fmaf(-xf.z, P.invTf, fmaf(xf.y, P.lnTf, xf.x + shf));
-    double kf;
+    float Ff = 1.0f;                                             // Troe: F P_r/(1 + P_r)
     if constexpr (KIND == 2) {
         const float4 t0 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux));       // lnA0, beta0, Ea0R, a
         const float4 t1 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux) + 1);   // 1/T3, 1/T1, T2, has
         if (M == 0.0) {
-            kf = 0.0;
+            Ff = 0.0f;
         } else {
             const float lnk0 = fmaf(-t0.z, P.invTf, fmaf(t0.y, P.lnTf, t0.x + shf));
-            const float lnPr = lnk0 - lnkf + logf((float)M);
+            const float lnPr = lnk0 - lnkf + logf(narrow(M));
             float Fc = (1.0f - t0.w) * expf(-P.Tf * t1.x) + t0.w * expf(-P.Tf * t1.y);
             if (t1.w != 0.0f) Fc += expf(-t1.z * P.invTf);
             const float lFc = log10f(Fc);
@@ -265,53 +327,65 @@ __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const
             const float u = fmaf(lnPr, (float)kInvLn10, c);
             const float f1 = u / fmaf(-0.14f, u, nn);
             const float lF = lFc / fmaf(f1, f1, 1.0f);
-            kf = exp_f32_to_f64(lnkf) * (double)(exp10f(lF) / (1.0f + expf(-lnPr)));
+            Ff = exp10f(lF) / (1.0f + expf(-lnPr));
         }
-    } else {
-        kf = exp_f32_to_f64(lnkf);
     }
-    const double kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
-    double q = fma(kf, fw, -kr * rv);
+    double q;
+    if constexpr (LOG) {
+        const dfl lkf{lnkf, 0.0f};
+        const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+        const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+        q = exp_df_d(df_add(lkf, sf), dt.e2) - exp_df_d(df_add(df_add(lkf, df_neg(lnKc)), sb), dt.e2);
+        if (KIND == 2) q *= widen(Ff);
+    } else {
+        double fw, rv;
+        products_direct(x, cs, fw, rv);
+        double kf = exp_f32_to_f64(lnkf);
+        if (KIND == 2) kf = M == 0.0 ? 0.0 : kf * (double)Ff;
+        const double kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+        q = fma(kf, fw, -kr * rv);
+    }
     if (KIND == 1) q *= M;
     return q;
 }
 
 template <int BLK>
 __device__ __forceinline__ void scatter(const Rxn& x, double* sW, double q) {
-#pragma unroll
-    for (int e = 0; e < kMaxSide; ++e)
-        if (e < x.nr) {
-            double* w = sW + x.sp[e] * BLK;
-            *w = fma(x.nud[e], q, *w);
-        }
-#pragma unroll
-    for (int e = 0; e < kMaxSide; ++e)
-        if (e < x.np) {
-            double* w = sW + x.sp[kMaxSide + e] * BLK;
-            *w = fma(x.nud[kMaxSide + e], q, *w);
-        }
+    scatter_side<BLK>(x.sp, x.nud, x.nr, sW, q);
+    scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sW, q);
 }
 
-template <int BLK, int PREC, int KIND>
+template <int BLK, int PREC, int KIND, bool LOG>
 __device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, const double* sC, const double* sG,
-                                       const Pt& P, const double* dlnA, const MathTab& mt, const DfTab& dt) {
+                                       const Conc& cs, const Pt& P, const double* dlnA, const MathTab& mt,
+                                       const DfTab& dt) {
+    const float2* sL = reinterpret_cast<const float2*>(sC);
     if constexpr (PREC == kDF)
-        return rate_of_progress_df<BLK, KIND>(m, x, r, sC, P, dlnA, dt);
+        return rate_of_progress_df<BLK, KIND, LOG>(m, x, r, sL, cs, P, dlnA, dt);
     else if constexpr (PREC == kMixed)
-        return rate_of_progress_mixed<BLK, KIND>(m, x, r, sC, P, dlnA, dt);
+        return rate_of_progress_mixed<BLK, KIND, LOG>(m, x, r, sL, cs, P, dlnA, dt);
     else
         return rate_of_progress<BLK, KIND>(m, x, sC, sG, P, dlnA, mt);
 }
 
 // Reactions [r0, r1) of one kind, scattered in reaction order.  (Unrolling by two or four
-// reactions per iteration measured slower once several warps share a point.)
+// reactions per iteration measured slower once several warps share a point.)  direct: the
+// block's products in double (a negative concentration); else the logarithmic form (kDF and
+// kMixed; the native form always takes its own).
 template <int BLK, int PREC, int KIND>
 __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1, const double* sC, const double* sG,
-                                               double* sW, const Pt& P, const double* dlnA, const MathTab& mt,
-                                               const DfTab& dt) {
-    for (int r = r0; r < r1; ++r) {
-        const Rxn a = load_rxn(m.rxn + r);
-        scatter<BLK>(a, sW, q_of<BLK, PREC, KIND>(m, a, r, sC, sG, P, dlnA, mt, dt));
+                                               double* sW, const Conc& cs, bool direct, const Pt& P,
+                                               const double* dlnA, const MathTab& mt, const DfTab& dt) {
+    if (PREC == kNative || direct) {
+        for (int r = r0; r < r1; ++r) {
+            const Rxn a = load_rxn(m.rxn + r);
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, false>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
+        }
+    } else {
+        for (int r = r0; r < r1; ++r) {
+            const Rxn a = load_rxn(m.rxn + r);
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, true>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
+        }
     }
 }
 
@@ -369,21 +443,40 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
+    const Conc cs{Y, m.invW, ld, i, rho_w};
+    bool neg = false;
     for (int k = part; k < K; k += NP) {
-        sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
-        if constexpr (PREC == kNative) sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
+        const double c = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
+        if constexpr (PREC == kNative) {
+            sC[k * BLK] = c;
+            sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
+        } else {
+            // ln C_k as a pair in the C_k row (zero: -2^100; negative: the block takes the products
+            // in double)
+            neg |= c < 0.0;
+            const dfl l = c == 0.0 ? dfl{-0x1p100f, 0.0f} : log_df(c, dt.rc, dt.lc);
+            reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
+        }
     }
     for (int k = 0; k < K; ++k) sW[k * BLK] = 0.0;
-    if (NP > 1) __syncthreads();
+    bool direct = false;
+    if constexpr (NP > 1) {
+        if constexpr (PREC == kNative)
+            __syncthreads();
+        else
+            direct = __syncthreads_or(neg) != 0;
+    } else if constexpr (PREC != kNative) {
+        direct = __any_sync(__activemask(), neg);
+    }
 
     int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
     slice<NP>(0, e1, part, a, b);
-    reaction_group<BLK, PREC, 0>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
+    reaction_group<BLK, PREC, 0>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
     slice<NP>(e1, t1, part, a, b);
-    reaction_group<BLK, PREC, 1>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
+    reaction_group<BLK, PREC, 1>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
     slice<NP>(t1, m.R, part, a, b);
-    reaction_group<BLK, PREC, 2>(m, a, b, sC, sG, sW, P, dlnA, mt, dt);
+    reaction_group<BLK, PREC, 2>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
     if (NP > 1) __syncthreads();
 
     // omega_k (or the source W_k omega_k / rho), sum_k h_k/RT omega_k and, for the sources,

@@ -59,6 +59,7 @@ __device__ __forceinline__ double exclusive_products(const double* p, int n, dou
 struct VjpPoint {
     TPairs P;
     double invT, lnT, pRT, hb, hbRT;
+    dfl pRTd;
     bool valid;
 };
 
@@ -222,6 +223,137 @@ __device__ __forceinline__ void vjp_reaction(const DevMech& m, int r, const doub
     }
 }
 
+// The logarithmic form (tiles whose mass fractions are all within 2^+-100; see the kernel).  The C_k
+// row holds ln C_k as pairs; with F the falloff factor (1 but for Troe reactions)
+//   q_f = F exp(ln k_f + sum_reac nu ln C),  q_r = F exp(ln k_f - ln K_c + sum_prod nu ln C),
+// so d q_c / d ln C_k = nu (q_f or -q_r), d q_c / d ln k_f = q_c and d q_c / d ln K_c = q_r.  The
+// species rows accumulate S_k = Cbar_k C_k (the cotangent of ln C_k), turned into Cbar_k = S_k/C_k
+// once per point at the end; the third-body terms Mbar (eps - 1) enter as Mbar (eps - 1) C_k.
+template <int KIND, bool WANT_G, bool HB>
+__device__ __forceinline__ void vjp_reaction_log(const DevMech& m, int r, const float2* sL, const double* sWb,
+                                                 double* sS, double* gw, const VjpPoint& Q, const double* dlnA,
+                                                 const DfTab& dt, double& Tbar) {
+    constexpr int BLK = kVjpBlk;
+    const Rxn x = load_rxn(m.rxn + r);
+    const double wsum = gather_side<BLK>(x.sp, x.nud, x.nr, sWb) +
+                        gather_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sWb);
+    const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+    const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+    dfl dG, dH, dCp;
+    rxn_thermo<true, HB>(m, x.thermo, Q.P, dG, dH, dCp);
+    const double sumh = df_to_d(dH);
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
+    double shift = 0.0;
+    dfl shiftd{0.0f, 0.0f};
+    if (dlnA) {
+        shift = __ldg(dlnA + x.orig);
+        shiftd = df_split(shift);
+    }
+    const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
+    double M = 0.0;
+    if (KIND != 0) {
+        dfl Mp = Q.pRTd;
+        for (int j = x.eff0; j < x.eff1; ++j)
+            Mp = df_fma(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[__ldg(m.eff_sp + j) * BLK]), dt.e2), Mp);
+        M = df_to_d(Mp);
+    }
+
+    // ---- primal
+    double F = 1.0;
+    double tr_g = 0.0, tr_lF = 0.0, tr_f1 = 0.0, tr_den = 1.0, tr_u = 0.0, tr_v = 1.0, tr_nn = 0.0, tr_Fc = 1.0,
+           tr_dFc = 0.0;
+    const TroeRec* t = nullptr;
+    if constexpr (KIND == 2) {
+        t = m.troe + x.aux;
+        if (M == 0.0) {
+            F = 0.0;
+        } else {
+            const double lnk0 = fma(-__ldg(&t->Ea0R), Q.invT, fma(__ldg(&t->beta0), Q.lnT, __ldg(&t->lnA0) + shift));
+            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
+            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
+            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
+            tr_Fc = (1.0 - a) * e3 + a * e1;
+            tr_dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1);
+            if (__ldg(&t->hasT2) != 0.0) {
+                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
+                tr_Fc += e2;
+                tr_dFc = fma(T2 * Q.invT * Q.invT, e2, tr_dFc);
+            }
+            const double lFc = dlog_df(tr_Fc, dt) * kInvLn10;
+            const double c = fma(-0.67, lFc, -0.4);
+            tr_nn = fma(-1.27, lFc, 0.75);
+            tr_u = fma(lnPr, kInvLn10, c);
+            tr_v = fma(-0.14, tr_u, tr_nn);
+            tr_f1 = tr_u / tr_v;
+            tr_den = fma(tr_f1, tr_f1, 1.0);
+            tr_lF = lFc / tr_den;
+            tr_g = 1.0 / (1.0 + dexp_df(-lnPr, dt));
+            F = tr_g * dexp_df(tr_lF * kLn10, dt);
+        }
+    }
+    double qf = exp_df_d(df_add(lnkf, sf), dt.e2);
+    double qr = exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
+    if constexpr (KIND == 2) {
+        qf *= F;
+        qr *= F;
+    }
+    const double qc = qf - qr;
+    const double q = KIND == 1 ? qc * M : qc;
+
+    // ---- adjoint
+    const double qbar = HB ? fma(-Q.hbRT, sumh, wsum) : wsum;   // sum nu (bar_omega - bar_hrr h)
+    if (HB) Tbar = fma(-Q.hb * kR * q, df_to_d(dCp), Tbar);
+    if (WANT_G) {
+        double gl = Q.valid ? qbar * q : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gl += __shfl_xor_sync(0xffffffffu, gl, o);
+        if ((threadIdx.x & 31) == 0) gw[r] += gl;
+    }
+    double Mbar = 0.0, qcbar = qbar;
+    if (KIND == 1) {
+        qcbar = qbar * M;
+        Mbar = qbar * qc;
+    }
+    // S_k += nu_k (q_f or -q_r) qcbar: with the signed coefficients nud (-nu for reactants)
+    scatter_side<BLK>(x.sp, x.nud, x.nr, sS, -qcbar * qf);
+    scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sS, -qcbar * qr);
+    const double lnKcbar = qcbar * qr;
+    Tbar = fma(lnKcbar * Q.invT, sumh - x.dnu, Tbar);           // through g_k/RT(T) and ln(p0/RT)
+    const double Lbar = qcbar * qc;                              // cotangent of ln k_f (with the falloff)
+    if constexpr (KIND == 2) {
+        if (M != 0.0) {
+            const double lnf = fma(__ldg(&t->Ea0R), Q.invT, __ldg(&t->beta0)) * Q.invT;
+            const double dlF_du = -2.0 * tr_lF * tr_f1 * (tr_nn / (tr_v * tr_v)) / tr_den;
+            const double df1_dlFc = fma(1.1762, tr_u, -0.67 * tr_v) / (tr_v * tr_v);
+            const double dlF_dlFc = (1.0 - 2.0 * tr_lF * tr_f1 * df1_dlFc) / tr_den;
+            const double lnPrbar = Lbar * (1.0 - tr_g + dlF_du);
+            const double lnkinfbar = Lbar - lnPrbar;
+            Mbar = fma(lnPrbar, 1.0 / M, Mbar);
+            Tbar = fma(Lbar * dlF_dlFc, tr_dFc / tr_Fc, Tbar);
+            Tbar = fma(lnPrbar, lnf, Tbar);
+            Tbar = fma(lnkinfbar, fma(x.EaR, Q.invT, x.beta) * Q.invT, Tbar);
+        }
+    } else {
+        Tbar = fma(Lbar, fma(x.EaR, Q.invT, x.beta) * Q.invT, Tbar);
+    }
+    if (KIND != 0 && Mbar != 0.0) {
+        Tbar = fma(-Mbar * Q.pRT, Q.invT, Tbar);                 // sum_k C_k = p/(RT)
+        for (int j = x.eff0; j < x.eff1; ++j) {
+            const int k = __ldg(m.eff_sp + j);
+            double* b = sS + k * BLK;
+            *b = fma(Mbar * __ldg(m.eff_m1 + j), exp_df_d(dfl_of(sL[k * BLK]), dt.e2), *b);
+        }
+    }
+}
+
+template <int KIND, bool WANT_G, bool HB>
+__device__ __forceinline__ void vjp_group_log(const DevMech& m, int r0, int r1, const double* sC, const double* sWb,
+                                              double* sB, double* gw, const VjpPoint& Q, const double* dlnA,
+                                              const DfTab& dt, double& Tbar) {
+    const float2* sL = reinterpret_cast<const float2*>(sC);
+    for (int r = r0; r < r1; ++r) vjp_reaction_log<KIND, WANT_G, HB>(m, r, sL, sWb, sB, gw, Q, dlnA, dt, Tbar);
+}
+
 template <int KIND, bool WANT_G, bool HB>
 __device__ __forceinline__ void vjp_group(const DevMech& m, int r0, int r1, const double* sC, const double* sWb,
                                           double* sB, double* gw, const VjpPoint& Q, const double* dlnA,
@@ -280,27 +412,46 @@ __global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, cons
         double s = 0.0;
         for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
         const double rho = Q.pRT / s;
+        // logarithmic form unless a point of the tile has a mass fraction outside 2^+-100 (zero,
+        // negative, tiny or non-finite): then the products in double (C_k in the row)
+        bool bad = false;
+        for (int k = part; k < K; k += NP) bad |= !log_form_ok(Y[(int64_t)k * ld + i]);
+        const bool direct = __syncthreads_or(bad) != 0;
+        Q.pRTd = df_split(Q.pRT);
         for (int k = part; k < K; k += NP) {
-            sC[k * BLK] = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
+            const double c = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
+            if (direct) {
+                sC[k * BLK] = c;
+            } else {
+                const dfl l = log_df(c, dt.rc, dt.lc);
+                reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
+            }
             sWb[k * BLK] = bar_omega[(int64_t)k * ld + i];
         }
         for (int k = 0; k < K; ++k) sB[k * BLK] = 0.0;
         __syncthreads();
 
         double Tbar = 0.0;
-        vjp_group<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-        vjp_group<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-        vjp_group<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        if (direct) {
+            vjp_group<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_group<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_group<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        } else {
+            vjp_group_log<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_group_log<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_group_log<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        }
         __syncthreads();
 
-        // Cbar_k totals (part order) into row 0, and this part's share of sum_k Cbar_k C_k
+        // Cbar_k totals (part order) into row 0 (in the logarithmic form S_k = Cbar_k C_k), and
+        // this part's share of sum_k Cbar_k C_k
         double cc = 0.0;
         for (int k = part; k < K; k += NP) {
             double cb = sB0[k * BLK];
 #pragma unroll
             for (int q = 1; q < NP; ++q) cb += sB0[((size_t)q * K + k) * BLK];
             sB0[k * BLK] = cb;
-            cc = fma(cb, sC[k * BLK], cc);
+            cc = direct ? fma(cb, sC[k * BLK], cc) : cc + cb;
         }
         if (NP > 1) {
             // bar_omega is dead: rows 2q, 2q+1 (2 NP <= K) take part q's sums, added in part order
@@ -320,8 +471,12 @@ __global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, cons
         const double sbar = -cc / s;
         if (Q.valid) {
             if (part == 0) gT[i] = fma(-cc, Q.invT, Tbar);
-            for (int k = part; k < K; k += NP)
-                gY[(int64_t)k * ld + i] = __ldg(m.invW + k) * fma(rho, sB0[k * BLK], sbar);
+            for (int k = part; k < K; k += NP) {
+                // rho Cbar_k / W_k = S_k / Y_k in the logarithmic form (C_k = rho Y_k / W_k)
+                const double iw = __ldg(m.invW + k);
+                gY[(int64_t)k * ld + i] = direct ? iw * fma(rho, sB0[k * BLK], sbar)
+                                                 : fma(sB0[k * BLK], recip_nr(Y[(int64_t)k * ld + i]), iw * sbar);
+            }
         }
         __syncthreads();                                          // before the next tile reuses the rows
     }

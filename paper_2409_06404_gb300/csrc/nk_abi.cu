@@ -416,6 +416,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                        f_cp((size_t)K * 2 * 8, 0.0f);
     for (int q = 0; q < R; ++q)
         for (int e = 0; e < 2 * nk::kMaxSide; ++e) f_nud[(size_t)q * 2 * nk::kMaxSide + e] = (float)rxn[q].nud[e];
+    std::vector<float2> df_effm1(eff_m1.size());
+    for (size_t j = 0; j < eff_m1.size(); ++j) df_effm1[j] = split((long double)eff_m1[j]);
     std::vector<double> lc_w((size_t)R * 2 * nk::kMaxSide, 0.0);
     for (int q = 0; q < R; ++q)
         for (int side = 0; side < 2; ++side) {
@@ -447,7 +449,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_gT = L.add(grp_Tmid.size() * 8 + 16), o_lb = L.add((size_t)R * 4 + 16),
                  o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16),
                  o_fnud = L.add(f_nud.size() * 4), o_feff = L.add(f_effm1.size() * 4 + 16),
-                 o_fcp = L.add(f_cp.size() * 4 + 16), o_lcw = L.add(lc_w.size() * 8);
+                 o_fcp = L.add(f_cp.size() * 4 + 16), o_lcw = L.add(lc_w.size() * 8),
+                 o_dfe = L.add(df_effm1.size() * 8 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -497,6 +500,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_feff, f_effm1.data(), f_effm1.size() * 4);
     put(o_fcp, f_cp.data(), f_cp.size() * 4);
     put(o_lcw, lc_w.data(), lc_w.size() * 8);
+    put(o_dfe, df_effm1.data(), df_effm1.size() * 8);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -573,6 +577,7 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.f_eff_m1 = reinterpret_cast<const float*>(b + o_feff);
     dm.f_cp = reinterpret_cast<const float*>(b + o_fcp);
     dm.lc_w = reinterpret_cast<const double*>(b + o_lcw);
+    dm.df_eff_m1 = reinterpret_cast<const float2*>(b + o_dfe);
     *out = m;
     return ok();
 }

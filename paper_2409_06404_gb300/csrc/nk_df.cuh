@@ -196,8 +196,8 @@ __device__ __forceinline__ dfl df_mul_f(dfl x, float s) {
 static __device__ __noinline__ double exp_df_d_edge(float h, float l) { return exp((double)h + (double)l); }
 static __device__ __noinline__ dfl log_df_edge(double x) { return df_split_cvt(log(x)); }
 
-__device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
-    if (!(fabsf(x.h) < 708.0f)) return exp_df_d_edge(x.h, x.l);
+// The common part: exp(x) = v 2^(N >> 7) with the pair v = T_j (1 + (e^r - 1)) in [1, 2).
+__device__ __forceinline__ dfl exp_df_core(dfl x, const float2* tab, int& N) {
     constexpr float kInvC = 184.6649652337873f;          // 128 / ln2
     constexpr float C1 = 5.43212890625e-03f;
     constexpr float C2 = -1.691655779723078e-05f;
@@ -205,7 +205,7 @@ __device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
     // N = nearest integer to x.h * 128/ln2 by the 1.5 * 2^23 shifter (|N| < 2^22), read from
     // the float's bits: FP32 and integer pipe only
     const float kd = __fmaf_rn(x.h, kInvC, 12582912.0f);
-    const int N = __float_as_int(kd) - 0x4B400000;
+    N = __float_as_int(kd) - 0x4B400000;
     const float Nf = __fsub_rn(kd, 12582912.0f);
     const float rh = __fmaf_rn(-Nf, C1, x.h);            // exact
     const float p2 = __fmul_rn(-Nf, C2);
@@ -222,9 +222,27 @@ __device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
     em1 = fast_two_sum(em1.h, em1.l);
     const float2 t = tab[N & 127];
     const dfl tj{t.x, t.y};
-    const dfl v = df_fma(tj, em1, tj);
+    return df_fma(tj, em1, tj);
+}
+
+__device__ __forceinline__ double exp_df_d(dfl x, const float2* tab) {
+    if (!(fabsf(x.h) < 708.0f)) return exp_df_d_edge(x.h, x.l);
+    int N;
+    const dfl v = exp_df_core(x, tab, N);
     const double d = f2d_bits(v.h) + f2d_bits(v.l);     // the one FP64 operation
     return __longlong_as_double(__double_as_longlong(d) + ((long long)(N >> 7) << 52));
+}
+
+// exp(x) as a pair, for results in the normal float range: 0 below it (x < -87), +inf above it
+// (x >= 88) and NaN for NaN.  No FP64 operation.
+__device__ __forceinline__ dfl exp_df_pair(dfl x, const float2* tab) {
+    if (!(x.h > -87.0f && x.h < 88.0f)) {
+        const float z = x.h > 0.0f ? __int_as_float(0x7f800000) : 0.0f;
+        return x.h != x.h ? dfl{x.h, x.h} : dfl{z, 0.0f};
+    }
+    int N;
+    const dfl v = exp_df_core(x, tab, N);
+    return df_ldexp(v, N >> 7);
 }
 
 // log(x) as a pair for a positive normal double x (others fall back to the double log):

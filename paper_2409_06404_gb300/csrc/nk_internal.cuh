@@ -157,6 +157,7 @@ struct DevMech {
     // per-reaction stored linearization (k_linc.cu): entry weights nu_e / nu_first of each side
     // (reactants at [0, nr), products at [kMaxSide, kMaxSide + np); nu_first the side's first entry)
     const double* lc_w;           // [R][2 kMaxSide]
+    const float2* df_eff_m1;      // efficiencies - 1 as pairs (eff_m1 order)
 };
 
 // Centre of the re-expanded transport fits (ln T about 1100 K).

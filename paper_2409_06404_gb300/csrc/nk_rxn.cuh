@@ -166,6 +166,91 @@ __device__ __forceinline__ float dnu_f(const DevMech& m, int r) {
     return __ldg(reinterpret_cast<const float*>(m.rxn_df + 2 * r + 1) + 2);
 }
 
+// sum_e nu_e l_e over one side of a reaction (ne entries, species sp[e], coefficients nu[e]) for
+// pair values l_k at l[k * BLK]: the logarithm of a concentration product, or its tangent
+template <int BLK>
+__device__ __forceinline__ dfl side_sum_df(const float2* l, const int* sp, const int* nu, int ne) {
+    dfl s = dfl_of(l[sp[0] * BLK]);
+    if (nu[0] != 1) s = df_mul_f(s, (float)nu[0]);
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < ne) {
+            dfl t = dfl_of(l[sp[e] * BLK]);
+            if (nu[e] != 1) t = df_mul_f(t, (float)nu[e]);
+            s = df_add(s, t);
+        }
+    return s;
+}
+
+// w[sp[e] * BLK] += nud[e] q over one side's ne entries (1..kMaxSide).  A switch on the
+// (warp-uniform) entry count, each case unrolled exactly: guarding an unrolled loop by e < ne
+// instead leaves the compiler predicated FP64 instructions that occupy the FP64 pipe with every
+// lane off (a third of the rates kernel's FP64-pipe time, measured).
+template <int BLK, int N>
+__device__ __forceinline__ void scatter_n(const int* sp, const double* nud, double* w, double q) {
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+        double* t = w + sp[e] * BLK;
+        *t = fma(nud[e], q, *t);
+    }
+}
+template <int BLK>
+__device__ __forceinline__ void scatter_side(const int* sp, const double* nud, int ne, double* w, double q) {
+    switch (ne) {
+        case 1: scatter_n<BLK, 1>(sp, nud, w, q); break;
+        case 2: scatter_n<BLK, 2>(sp, nud, w, q); break;
+        case 3: scatter_n<BLK, 3>(sp, nud, w, q); break;
+        default: scatter_n<BLK, kMaxSide>(sp, nud, w, q); break;
+    }
+}
+
+// The logarithmic form holds for a mass fraction y when y is a positive double of at least
+// 2^-100 (finite): its logarithm and the pair quotients dY/Y then stay within the float range of
+// the pairs.  Integer operations on the exponent field.
+__device__ __forceinline__ bool log_form_ok(double y) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    return (b >> 63) == 0 && e >= 1023u - 100u && e < 1023u + 100u;
+}
+
+// 1/y for a positive double within 2^+-100: the float reciprocal refined by one Newton step in
+// double (relative error ~2^-46; two FP64 operations instead of a division)
+__device__ __forceinline__ double recip_nr(double y) {
+    const double r0 = widen(__frcp_rn(narrow(y)));
+    return fma(r0, fma(-y, r0, 1.0), r0);
+}
+
+// sum_e nud[e] w[sp[e] * BLK] over one side's ne entries (1..kMaxSide), a switch on the count
+// with each case unrolled exactly (as scatter_side)
+template <int BLK, int N>
+__device__ __forceinline__ double gather_n(const int* sp, const double* nud, const double* w) {
+    double a = nud[0] * w[sp[0] * BLK];
+#pragma unroll
+    for (int e = 1; e < N; ++e) a = fma(nud[e], w[sp[e] * BLK], a);
+    return a;
+}
+template <int BLK>
+__device__ __forceinline__ double gather_side(const int* sp, const double* nud, int ne, const double* w) {
+    switch (ne) {
+        case 1: return gather_n<BLK, 1>(sp, nud, w);
+        case 2: return gather_n<BLK, 2>(sp, nud, w);
+        case 3: return gather_n<BLK, 3>(sp, nud, w);
+        default: return gather_n<BLK, kMaxSide>(sp, nud, w);
+    }
+}
+// |v| in [2^-100, 2^100) or v == 0 (a direction or cotangent value the pairs can carry)
+__device__ __forceinline__ bool pair_range_ok(double v) {
+    const unsigned e = (unsigned)(__double_as_longlong(v) >> 52) & 0x7ffu;
+    return e == 0 ? (__double_as_longlong(v) << 1) == 0 : (e >= 1023u - 100u && e < 1023u + 100u);
+}
+
+// v / y within 2^+-120 (exponent fields; y a normal double, v == 0 allowed): the quotient a pair
+// can carry
+__device__ __forceinline__ bool quot_range_ok(double v, double y) {
+    const int ev = (int)((__double_as_longlong(v) >> 52) & 0x7ff), ey = (int)((__double_as_longlong(y) >> 52) & 0x7ff);
+    return ev == 0 ? (__double_as_longlong(v) << 1) == 0 : (ev - ey >= -120 && ev - ey <= 120);
+}
+
 // Part `part` of NP takes the contiguous slice [a + len*part/NP, a + len*(part+1)/NP) of the
 // range [a, b).
 template <int NP>
