@@ -1,0 +1,624 @@
+// Kernels of the net species production rates omega_k and heat release per point (the "rates" kernel of
+// the paper, Tab. 3-4; omega_k of Eq. 1a, heat release of Eq. 1b).
+//
+// Layout: a point is worked on by NP warps ("parts"), one lane per point in each.  All lanes
+// of a warp walk the same reaction at the same time, so reaction records are broadcast loads
+// and control flow is uniform.  The device copy of the mechanism groups reactions by kind
+// (elementary, third-body, Troe); each part walks its own contiguous slice of every kind.
+// The per-point species state (C_k and g_k/RT, shared by the parts, and one row of omega_k
+// partials per part) lives in shared memory as [species][point]; the partials are added in
+// part order at the end.  NP and the points per block come from CUDA's occupancy calculator:
+// shared memory per point bounds the resident warps, and splitting a point's reactions over
+// warps raises them (5 -> 8 warps per SM at K = 53, 2 -> 4 at K = 120), which this
+// latency-bound walk needs.
+//
+// Three arithmetic forms (template PREC):
+//  kNative (NK_FP64_NATIVE): every operation in double (exp/log from nk_math.cuh), with the
+//    per-species g_k/RT in shared memory.
+//  kDF (NK_FP64): the exponent chains -- the reaction's Gibbs sum (from its thermo groups),
+//    ln k_f, ln K_c, the Troe falloff -- in double-float pairs on the FP32 pipe (nk_df.cuh),
+//    each exponential returned as a double with one FP64 add; concentrations and their
+//    products, the forward-minus-reverse difference and the omega accumulation stay in
+//    double.  Results match the double-precision definition to ~1e-12 (the pairs carry 48
+//    bits).
+//  kMixed (NK_MIXED): the Arrhenius argument ln A + beta ln T - Ea/(RT), k_f and the whole
+//    Troe falloff in single precision; the Gibbs sum and K_c as in the kDF form (pairs), the
+//    forward-minus-reverse difference and the omega accumulation in double.
+#pragma once
+
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "nk_rxn.cuh"
+
+namespace nk {
+namespace {
+
+enum { kNative = 0, kMixed = 1, kDF = 2 };
+
+// exp of a single-precision argument, returned in double: x = n ln2 + r (Cody-Waite two-term
+// split of ln 2), expf(r) with |r| <= ln2/2, and 2^n added to the exponent field of the
+// double, so results beyond the single-precision range stay representable.
+__device__ __forceinline__ double exp_f32_to_f64(float x) {
+    if (x < -700.0f) return 0.0;
+    if (x > 700.0f) return __longlong_as_double(0x7ff0000000000000LL);
+    const float kd = __fmaf_rn(x, 1.44269504089f, 12582912.0f);   // 1.5 * 2^23 shifter: n in the low bits
+    const int ni = __float_as_int(kd) - 0x4B400000;
+    const float nf = __fsub_rn(kd, 12582912.0f);
+    float r = fmaf(nf, -0.693359375f, x);
+    r = fmaf(nf, 2.12194440054690583e-4f, r);
+    const double e = (double)expf(r);
+    return __longlong_as_double(__double_as_longlong(e) + ((long long)ni << 52));
+}
+
+// Per-point quantities shared by all reactions.
+struct Pt {
+    double T, lnT, invT, pRT, lnP0RT;
+    float Tf, lnTf, invTf;
+    TPairs tp;                       // kDF form
+};
+
+// sum_k nu_k g_k/RT (products minus reactants) and the concentration products of each side;
+// every reaction has at least one entry per side, which initialises the product.
+template <int BLK>
+__device__ __forceinline__ void gibbs_products(const Rxn& x, const double* sC, const double* sG, double& sumg,
+                                               double& fw, double& rv) {
+    {
+        const int k = x.sp[0];
+        const double c = sC[k * BLK];
+        fw = c;
+        for (int j = 1; j < x.nu[0]; ++j) fw *= c;
+        sumg = x.nud[0] * sG[k * BLK];
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e) {
+        if (e < x.nr) {
+            const int k = x.sp[e];
+            const double c = sC[k * BLK];
+            for (int j = 0; j < x.nu[e]; ++j) fw *= c;
+            sumg = fma(x.nud[e], sG[k * BLK], sumg);
+        }
+    }
+    {
+        const int k = x.sp[kMaxSide];
+        const double c = sC[k * BLK];
+        rv = c;
+        for (int j = 1; j < x.nu[kMaxSide]; ++j) rv *= c;
+        sumg = fma(x.nud[kMaxSide], sG[k * BLK], sumg);
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e) {
+        if (e < x.np) {
+            const int k = x.sp[kMaxSide + e];
+            const double c = sC[k * BLK];
+            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) rv *= c;
+            sumg = fma(x.nud[kMaxSide + e], sG[k * BLK], sumg);
+        }
+    }
+}
+
+// Troe falloff factor F * P_r/(1+P_r) in double precision, given ln k_inf, ln k_0 and [M].
+__device__ __forceinline__ double troe_factor(const TroeRec* t, double lnkinf, double lnk0, double M, const Pt& P,
+                                              const MathTab& mt) {
+    const double lnPr = lnk0 - lnkinf + flog(M, mt);
+    const double a = __ldg(&t->a);
+    double Fc = (1.0 - a) * fexp(-P.T * __ldg(&t->invT3), mt) + a * fexp(-P.T * __ldg(&t->invT1), mt);
+    if (__ldg(&t->hasT2) != 0.0) Fc += fexp(-__ldg(&t->T2) * P.invT, mt);
+    const double lFc = flog(Fc, mt) * kInvLn10;
+    const double c = fma(-0.67, lFc, -0.4);
+    const double nn = fma(-1.27, lFc, 0.75);
+    const double u = fma(lnPr, kInvLn10, c);
+    const double f1 = u / fma(-0.14, u, nn);
+    const double lF = lFc / fma(f1, f1, 1.0);
+    return fexp(lF * kLn10, mt) / (1.0 + fexp(-lnPr, mt));   // P_r/(1+P_r) = 1/(1+1/P_r)
+}
+
+// Rate of progress q of one reaction of kind KIND (0 elementary, 1 third-body, 2 Troe);
+// r is the reaction's position in the device order.  Native form: everything in double.
+template <int BLK, int KIND>
+__device__ __forceinline__ double rate_of_progress(const DevMech& m, const Rxn& x, const double* sC,
+                                                   const double* sG, const Pt& P, const double* dlnA,
+                                                   const MathTab& mt) {
+    double sumg, fw, rv;
+    gibbs_products<BLK>(x, sC, sG, sumg, fw, rv);
+    const double lnKc = fma(x.dnu, P.lnP0RT, -sumg);   // ln K_c = -sum nu g/RT + sum nu ln(p0/RT)
+    double lnA = x.lnA;                                  // ln A + shift (uniform branch)
+    double shift = 0.0;
+    if (dlnA) {
+        shift = __ldg(dlnA + x.orig);
+        lnA += shift;
+    }
+    double M = 0.0;
+    if (KIND != 0) {
+        M = P.pRT;                                       // sum_k C_k = p/(R T)
+        for (int j = x.eff0; j < x.eff1; ++j) M = fma(__ldg(m.eff_m1 + j), sC[__ldg(m.eff_sp + j) * BLK], M);
+    }
+    double kf, kr;
+    const double lnkf = fma(-x.EaR, P.invT, fma(x.beta, P.lnT, lnA));
+    if constexpr (KIND == 2) {
+        const TroeRec* t = m.troe + x.aux;
+        const double lnk0 = fma(-__ldg(&t->Ea0R), P.invT, fma(__ldg(&t->beta0), P.lnT, __ldg(&t->lnA0) + shift));
+        kf = M == 0.0 ? 0.0 : fexp(lnkf, mt) * troe_factor(t, lnkf, lnk0, M, P, mt);
+        kr = kf * fexp(-lnKc, mt);
+    } else {
+        kf = fexp(lnkf, mt);
+        kr = fexp(lnkf - lnKc, mt);
+    }
+    double q = fma(kf, fw, -kr * rv);
+    if (KIND == 1) q *= M;
+    return q;
+}
+
+// kDF form: the concentration products of each side in double (the Gibbs sum comes from the
+// reaction's thermo groups).
+template <int BLK>
+__device__ __forceinline__ void products(const Rxn& x, const double* sC, double& fw, double& rv) {
+    {
+        const double c = sC[x.sp[0] * BLK];
+        fw = c;
+        for (int j = 1; j < x.nu[0]; ++j) fw *= c;
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            const double c = sC[x.sp[e] * BLK];
+            for (int j = 0; j < x.nu[e]; ++j) fw *= c;
+        }
+    {
+        const double c = sC[x.sp[kMaxSide] * BLK];
+        rv = c;
+        for (int j = 1; j < x.nu[kMaxSide]; ++j) rv *= c;
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.np) {
+            const double c = sC[x.sp[kMaxSide + e] * BLK];
+            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) rv *= c;
+        }
+}
+
+// Logarithmic form of the concentration products (kDF and kMixed forms).  The C_k row holds
+// ln C_k as pairs (a zero concentration as -2^100, whose exponential is 0), and each side's
+// product enters its rate term through the exponent:
+//   q_f = exp(ln k_f + sum_reactants nu ln C),  q_r = exp(ln k_f - ln K_c + sum_products nu ln C),
+// one pair exponential each (as k_f and k_r alone took), so no concentration product is formed
+// in double: the FP64 pipe keeps the exponentials' final additions, the forward-minus-reverse
+// difference, [M] and the scatter.  A block with a negative concentration (a negative mass
+// fraction) takes the products in double instead, from the state (Conc).
+// The point's concentrations C_k = rho Y_k / W_k from the state (the products in double).
+struct Conc {
+    const double* Y;
+    const double* invW;
+    int64_t ld, i;
+    double rho;
+    __device__ __forceinline__ double operator()(int k) const {
+        return Y[(int64_t)k * ld + i] * __ldg(invW + k) * rho;
+    }
+};
+
+// Both sides' products in double from the state (Conc).
+__device__ __forceinline__ void products_direct(const Rxn& x, const Conc& cs, double& fw, double& rv) {
+    {
+        const double c = cs(x.sp[0]);
+        fw = c;
+        for (int j = 1; j < x.nu[0]; ++j) fw *= c;
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            const double c = cs(x.sp[e]);
+            for (int j = 0; j < x.nu[e]; ++j) fw *= c;
+        }
+    {
+        const double c = cs(x.sp[kMaxSide]);
+        rv = c;
+        for (int j = 1; j < x.nu[kMaxSide]; ++j) rv *= c;
+    }
+#pragma unroll
+    for (int e = 1; e < kMaxSide; ++e)
+        if (e < x.np) {
+            const double c = cs(x.sp[kMaxSide + e]);
+            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) rv *= c;
+        }
+}
+
+// [M] = p/(RT) + sum (eps - 1) C_j: C_j from the logarithms (LOG) or the state
+template <int BLK, bool LOG>
+__device__ __forceinline__ double third_body(const DevMech& m, const Rxn& x, const float2* sL, const Conc& cs,
+                                             const Pt& P, const DfTab& dt) {
+    double M = P.pRT;
+    for (int j = x.eff0; j < x.eff1; ++j) {
+        const int k = __ldg(m.eff_sp + j);
+        M = fma(__ldg(m.eff_m1 + j), LOG ? exp_df_d(dfl_of(sL[k * BLK]), dt.e2) : cs(k), M);
+    }
+    return M;
+}
+
+// Troe factor F * P_r/(1+P_r) with the exponent arithmetic in pairs.
+__device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl lnkinf, dfl lnk0, double M,
+                                                 const Pt& P, const DfTab& dt) {
+    const TroeRec* t = m.troe + aux;
+    const float4 t1 = __ldg(m.troe_df + 3 * aux + 1);    // (Ea0/R, 1/T3)
+    const float4 t2 = __ldg(m.troe_df + 3 * aux + 2);    // (1/T1, T2)
+    const dfl lnPr = df_add(df_add(lnk0, df_neg(lnkinf)), log_df(M, dt.rc, dt.lc));
+    const double a = __ldg(&t->a);
+    double Fc = (1.0 - a) * exp_df_d(df_neg(df_mul(P.tp.Td, dfl{t1.z, t1.w})), dt.e2) +
+                a * exp_df_d(df_neg(df_mul(P.tp.Td, dfl{t2.x, t2.y})), dt.e2);
+    if (__ldg(&t->hasT2) != 0.0) Fc += exp_df_d(df_neg(df_mul(dfl{t2.z, t2.w}, P.tp.invTd)), dt.e2);
+    const dfl lFc = df_mul(log_df(Fc, dt.rc, dt.lc), dfc_invln10());
+    const dfl c = df_add(dfc_m0_4(), df_mul(lFc, dfc_m0_67()));
+    const dfl nn = df_add(dfl{0.75f, 0.0f}, df_mul(lFc, dfc_m1_27()));
+    const dfl u = df_add(df_mul(lnPr, dfc_invln10()), c);
+    const dfl f1 = df_div(u, df_add(nn, df_mul(u, dfc_m0_14())));
+    const dfl lF = df_div(lFc, df_fma(f1, f1, dfl{1.0f, 0.0f}));
+    return exp_df_d(df_mul(lF, dfc_ln10()), dt.e2) / (1.0 + exp_df_d(df_neg(lnPr), dt.e2));
+}
+
+template <int BLK, int KIND, bool LOG>
+__device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const float2* sL,
+                                                      const Conc& cs, const Pt& P, const double* dlnA,
+                                                      const DfTab& dt) {
+    dfl sumg, unused_h, unused_cp;
+    rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
+    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
+    dfl shift{0.0f, 0.0f};
+    if (dlnA) shift = df_split(__ldg(dlnA + x.orig));
+    const dfl lnkf = ln_kf_df(m, r, P.tp, shift, dlnA != nullptr);
+    const double M = KIND != 0 ? third_body<BLK, LOG>(m, x, sL, cs, P, dt) : 0.0;
+    double F = 1.0;                                              // Troe: F P_r/(1 + P_r)
+    if constexpr (KIND == 2) {
+        const float4 t0 = __ldg(m.troe_df + 3 * x.aux);          // (lnA0, beta0)
+        const float4 t1 = __ldg(m.troe_df + 3 * x.aux + 1);      // (Ea0/R, 1/T3)
+        dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.tp.lnTd, dfl{t0.x, t0.y});
+        lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.tp.invTd, lnk0);
+        if (dlnA) lnk0 = df_add(lnk0, shift);
+        F = M == 0.0 ? 0.0 : troe_factor_df(m, x.aux, lnkf, lnk0, M, P, dt);
+    }
+    double q;
+    if constexpr (LOG) {
+        const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+        const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+        q = exp_df_d(df_add(lnkf, sf), dt.e2) - exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
+        if (KIND == 2) q *= F;
+    } else {
+        double fw, rv, kf, kr;
+        products_direct(x, cs, fw, rv);
+        if constexpr (KIND == 2) {
+            kf = F == 0.0 ? 0.0 : exp_df_d(lnkf, dt.e2) * F;
+            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+        } else {
+            kf = exp_df_d(lnkf, dt.e2);
+            kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
+        }
+        q = fma(kf, fw, -kr * rv);
+    }
+    if (KIND == 1) q *= M;
+    return q;
+}
+
+// Mixed form: k_f and the whole Troe falloff in single precision; the Gibbs sum and K_c from
+// the reaction's thermo groups in pairs, the exponent sums of the rate terms in pairs (the
+// single-precision ln k_f enters both terms alike, so q keeps the FP64 difference of
+// K_c-consistent terms), the difference in double.
+template <int BLK, int KIND, bool LOG>
+__device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const Rxn& x, int r, const float2* sL,
+                                                         const Conc& cs, const Pt& P, const double* dlnA,
+                                                         const DfTab& dt) {
+    dfl sumg, unused_h, unused_cp;
+    rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
+    const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
+    const float shf = dlnA ? (float)__ldg(dlnA + x.orig) : 0.0f;
+    const double M = KIND != 0 ? third_body<BLK, LOG>(m, x, sL, cs, P, dt) : 0.0;
+    const float4 xf = __ldg(reinterpret_cast<const float4*>(m.rxnf + r));   // lnA, beta, EaR
+    const float lnkf = fmaf(-xf.z, P.invTf, fmaf(xf.y, P.lnTf, xf.x + shf));
+    float Ff = 1.0f;                                             // Troe: F P_r/(1 + P_r)
+    if constexpr (KIND == 2) {
+        const float4 t0 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux));       // lnA0, beta0, Ea0R, a
+        const float4 t1 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux) + 1);   // 1/T3, 1/T1, T2, has
+        if (M == 0.0) {
+            Ff = 0.0f;
+        } else {
+            const float lnk0 = fmaf(-t0.z, P.invTf, fmaf(t0.y, P.lnTf, t0.x + shf));
+            const float lnPr = lnk0 - lnkf + logf(narrow(M));
+            float Fc = (1.0f - t0.w) * expf(-P.Tf * t1.x) + t0.w * expf(-P.Tf * t1.y);
+            if (t1.w != 0.0f) Fc += expf(-t1.z * P.invTf);
+            const float lFc = log10f(Fc);
+            const float c = fmaf(-0.67f, lFc, -0.4f);
+            const float nn = fmaf(-1.27f, lFc, 0.75f);
+            const float u = fmaf(lnPr, (float)kInvLn10, c);
+            const float f1 = u / fmaf(-0.14f, u, nn);
+            const float lF = lFc / fmaf(f1, f1, 1.0f);
+            Ff = exp10f(lF) / (1.0f + expf(-lnPr));
+        }
+    }
+    double q;
+    if constexpr (LOG) {
+        const dfl lkf{lnkf, 0.0f};
+        const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+        const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+        q = exp_df_d(df_add(lkf, sf), dt.e2) - exp_df_d(df_add(df_add(lkf, df_neg(lnKc)), sb), dt.e2);
+        if (KIND == 2) q *= widen(Ff);
+    } else {
+        double fw, rv;
+        products_direct(x, cs, fw, rv);
+        double kf = exp_f32_to_f64(lnkf);
+        if (KIND == 2) kf = M == 0.0 ? 0.0 : kf * (double)Ff;
+        const double kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
+        q = fma(kf, fw, -kr * rv);
+    }
+    if (KIND == 1) q *= M;
+    return q;
+}
+
+template <int BLK>
+__device__ __forceinline__ void scatter(const Rxn& x, double* sW, double q) {
+    scatter_side<BLK>(x.sp, x.nud, x.nr, sW, q);
+    scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sW, q);
+}
+
+template <int BLK, int PREC, int KIND, bool LOG>
+__device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, const double* sC, const double* sG,
+                                       const Conc& cs, const Pt& P, const double* dlnA, const MathTab& mt,
+                                       const DfTab& dt) {
+    const float2* sL = reinterpret_cast<const float2*>(sC);
+    if constexpr (PREC == kDF)
+        return rate_of_progress_df<BLK, KIND, LOG>(m, x, r, sL, cs, P, dlnA, dt);
+    else if constexpr (PREC == kMixed)
+        return rate_of_progress_mixed<BLK, KIND, LOG>(m, x, r, sL, cs, P, dlnA, dt);
+    else
+        return rate_of_progress<BLK, KIND>(m, x, sC, sG, P, dlnA, mt);
+}
+
+// Reactions [r0, r1) of one kind, scattered in reaction order.  (Unrolling by two or four
+// reactions per iteration measured slower once several warps share a point.)  direct: the
+// block's products in double (a negative concentration); else the logarithmic form (kDF and
+// kMixed; the native form always takes its own).
+template <int BLK, int PREC, int KIND>
+__device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1, const double* sC, const double* sG,
+                                               double* sW, const Conc& cs, bool direct, const Pt& P,
+                                               const double* dlnA, const MathTab& mt, const DfTab& dt) {
+    if (PREC == kNative || direct) {
+        for (int r = r0; r < r1; ++r) {
+            const Rxn a = load_rxn(m.rxn + r);
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, false>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
+        }
+    } else {
+        for (int r = r0; r < r1; ++r) {
+            const Rxn a = load_rxn(m.rxn + r);
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, true>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
+        }
+    }
+}
+
+// Per-point species arrays: C_k, then g_k/RT (native form only), then NP rows of omega_k
+// partials.
+template <int PREC>
+__host__ __device__ constexpr int shared_rows() {
+    return PREC == kNative ? 2 : 1;
+}
+
+// BLK points per block, NP parts (warps) per point: thread (part, slot) works on point
+// blockIdx.x * BLK + slot.  The parts of a point share its C_k (and g_k/RT), each walks its
+// own slice of every kind and accumulates into its own omega_k partials; the partials are
+// added in part order, so results do not depend on scheduling.
+//
+// RHS: write the implicit-stage sources instead: omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p).
+template <int BLK, int NP, int PREC, bool RHS>
+__global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                         const double* __restrict__ T, const double* __restrict__ p,
+                                                         const double* __restrict__ Y,
+                                                         const double* __restrict__ dlnA,
+                                                         double* __restrict__ omega, double* __restrict__ hrr) {
+    extern __shared__ double smem[];
+    MathTab mt{};
+    DfTab dt{};
+    if constexpr (PREC == kNative)
+        mt = stage_math_tables(smem, m.mtab);
+    else
+        dt = stage_df_tables(reinterpret_cast<float2*>(smem), m);
+    __syncthreads();
+    const int K = m.K;
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
+    double* sC = smem + kMathTabDoubles + slot;                       // C_k       at sC[k * BLK]
+    double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (native form)
+    double* sW0 = smem + kMathTabDoubles + (size_t)shared_rows<PREC>() * K * BLK + slot;
+    double* sW = sW0 + (size_t)part * K * BLK;                        // this part's omega_k partials
+
+    Pt P;
+    P.T = T[i];
+    P.invT = 1.0 / P.T;
+    P.pRT = p[i] * P.invT * kInvR;                     // p/(RT) = sum_k C_k
+    if constexpr (PREC == kNative) {
+        P.lnT = flog(P.T, mt);
+        P.lnP0RT = kLnP0overR - P.lnT;                 // ln(p0/(R T))
+    } else {
+        P.tp = make_tpairs(P.T, P.invT, dt);
+        P.Tf = P.tp.Td.h;
+        P.lnTf = P.tp.lnTd.h + P.tp.lnTd.l;
+        P.invTf = P.tp.invTd.h;
+    }
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
+    const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
+    const Conc cs{Y, m.invW, ld, i, rho_w};
+    bool neg = false;
+    for (int k = part; k < K; k += NP) {
+        const double c = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
+        if constexpr (PREC == kNative) {
+            sC[k * BLK] = c;
+            sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
+        } else {
+            // ln C_k as a pair in the C_k row (zero: -2^100; negative: the block takes the products
+            // in double)
+            neg |= c < 0.0;
+            const dfl l = c == 0.0 ? dfl{-0x1p100f, 0.0f} : log_df(c, dt.rc, dt.lc);
+            reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
+        }
+    }
+    for (int k = 0; k < K; ++k) sW[k * BLK] = 0.0;
+    bool direct = false;
+    if constexpr (NP > 1) {
+        if constexpr (PREC == kNative)
+            __syncthreads();
+        else
+            direct = __syncthreads_or(neg) != 0;
+    } else if constexpr (PREC != kNative) {
+        direct = __any_sync(__activemask(), neg);
+    }
+
+    int a, b;
+    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+    slice<NP>(0, e1, part, a, b);
+    reaction_group<BLK, PREC, 0>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+    slice<NP>(e1, t1, part, a, b);
+    reaction_group<BLK, PREC, 1>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+    slice<NP>(t1, m.R, part, a, b);
+    reaction_group<BLK, PREC, 2>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+    if (NP > 1) __syncthreads();
+
+    // omega_k (or the source W_k omega_k / rho), sum_k h_k/RT omega_k and, for the sources,
+    // c_p/R = sum_k Y_k/W_k c_p,k/R of this part's species
+    double h = 0.0, cpm = 0.0, inv_rho = 0.0;
+    if constexpr (RHS) inv_rho = 1.0 / rho_w;
+    for (int k = part; k < K; k += NP) {
+        double w = sW0[k * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
+        const double* c = nasa_range(m, k, P.T);
+        h = fma(nasa_hRT(c, P.T, P.invT), w, h);
+        if constexpr (RHS) {
+            cpm = fma(Y[(int64_t)k * ld + i] * __ldg(m.invW + k), nasa_cpR(c, P.T), cpm);
+            w *= __ldg(m.W + k) * inv_rho;
+        }
+        if (live) omega[(int64_t)k * ld + i] = w;
+    }
+    if constexpr (NP > 1) {
+        // C_k is dead: rows q (and NP + q for the sources; (1 + RHS) NP <= K) take part q's
+        // sums, added in part order
+        sC[part * BLK] = h;
+        if constexpr (RHS) sC[(NP + part) * BLK] = cpm;
+        __syncthreads();
+        if (part != 0) return;
+        h = sC[0];
+        if constexpr (RHS) cpm = sC[NP * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            h += sC[q * BLK];
+            if constexpr (RHS) cpm += sC[(NP + q) * BLK];
+        }
+    }
+    const double hr = -kR * P.T * h;                   // heat release -sum_k h_k omega_k
+    if constexpr (RHS) {
+        if (live) hrr[i] = hr * inv_rho / (kR * cpm);  // dT/dt = hrr / (rho c_p)
+    } else {
+        if (live) hrr[i] = hr;
+    }
+}
+
+struct Shape {
+    int blk, np;
+};
+
+// Launch shapes the library instantiates (points per block, parts per point).
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <int PREC, bool RHS, int S>
+constexpr auto kernel_of() {
+    return rates_kernel<kShapes[S].blk, kShapes[S].np, PREC, RHS>;
+}
+
+template <int PREC, bool RHS, int... S>
+const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
+    const void* ptrs[] = {(const void*)kernel_of<PREC, RHS, S>()...};
+    return ptrs[idx];
+}
+
+template <int PREC, bool RHS, int... S>
+cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
+                       const double* T, const double* p, const double* Y, const double* dlnA, double* omega,
+                       double* hrr, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    ((S == idx ? (void)(e = [&] {
+        constexpr Shape sh = kShapes[S];
+        auto kern = kernel_of<PREC, RHS, S>();
+        cudaError_t r = ensure_smem((const void*)kern, smem);
+        if (r != cudaSuccess) return r;
+        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega,
+                                                                                  hrr);
+        return cudaGetLastError();
+    }())
+               : (void)0),
+     ...);
+    return e;
+}
+
+// Shared bytes of a block: the staged tables, then the per-point species arrays.
+template <int PREC>
+size_t rates_smem(int K, const Shape& sh) {
+    return (size_t)kMathTabDoubles * sizeof(double) +
+           (size_t)(shared_rows<PREC>() + sh.np) * K * sh.blk * sizeof(double);
+}
+
+// The shape with the most resident warps per SM (CUDA's occupancy calculator: shared memory,
+// registers, threads), fewer parts on ties.  Cached per
+// (device, K, form).
+struct Plan {
+    int dev, K, prec, rhs, idx;
+};
+std::mutex g_plan_mu;
+std::vector<Plan> g_plans;
+
+template <int PREC, bool RHS>
+int plan_shape(int K) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const Plan& q : g_plans)
+            if (q.dev == dev && q.K == K && q.prec == PREC && q.rhs == (int)RHS) return q.idx;
+    }
+    int per_block = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const auto seq = std::make_integer_sequence<int, kNumShapes>{};
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < kNumShapes; ++c) {
+        const Shape& sh = kShapes[c];
+        if ((RHS ? 2 : 1) * sh.np > K && sh.np > 1) continue;
+        const size_t bytes = rates_smem<PREC>(K, sh);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<PREC, RHS>(c, seq);
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
+            continue;
+        const int warps = blocks * sh.blk * sh.np / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best = c;
+        }
+    }
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back({dev, K, PREC, (int)RHS, best});
+    }
+    return best;
+}
+
+template <int PREC, bool RHS>
+cudaError_t launch_form(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                        const double* dlnA, double* omega, double* hrr, cudaStream_t s) {
+    const int idx = plan_shape<PREC, RHS>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<PREC, RHS>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, dlnA, omega,
+                                 hrr, rates_smem<PREC>(m.K, kShapes[idx]), s);
+}
+
+}  // namespace
+
+}  // namespace nk

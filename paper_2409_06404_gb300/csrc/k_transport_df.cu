@@ -99,22 +99,30 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
             if (!owns_row<NP>(j, part)) continue;
             int pi = j * (2 * K - j - 1) / 2;                 // index of the pair (j, j + 1)
             const dfl xj = as_df(sX[j * BLK]);
-            dfl acc0{0.0f, 0.0f}, acc1{0.0f, 0.0f};
+            // four pairs per iteration: four independent exponential chains per thread (the loop is
+            // latency bound at the few warps the pair rows leave resident)
+            dfl acc0{0.0f, 0.0f}, acc1{0.0f, 0.0f}, acc2{0.0f, 0.0f}, acc3{0.0f, 0.0f};
             int k = j + 1;
-            for (; k + 1 < K; k += 2, pi += 2) {
+            for (; k + 3 < K; k += 4, pi += 4) {
                 const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
                 const dfl i1 = df_exp(dneg(poly3_df(Dc + 4 * pi + 4, u)), etab);
+                const dfl i2 = df_exp(dneg(poly3_df(Dc + 4 * pi + 8, u)), etab);
+                const dfl i3 = df_exp(dneg(poly3_df(Dc + 4 * pi + 12, u)), etab);
                 sAp[k * BLK] = as_f2(df_fma(xj, i0, as_df(sAp[k * BLK])));
                 sAp[(k + 1) * BLK] = as_f2(df_fma(xj, i1, as_df(sAp[(k + 1) * BLK])));
+                sAp[(k + 2) * BLK] = as_f2(df_fma(xj, i2, as_df(sAp[(k + 2) * BLK])));
+                sAp[(k + 3) * BLK] = as_f2(df_fma(xj, i3, as_df(sAp[(k + 3) * BLK])));
                 acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
                 acc1 = df_fma(as_df(sX[(k + 1) * BLK]), i1, acc1);
+                acc2 = df_fma(as_df(sX[(k + 2) * BLK]), i2, acc2);
+                acc3 = df_fma(as_df(sX[(k + 3) * BLK]), i3, acc3);
             }
-            if (k < K) {
+            for (; k < K; ++k, ++pi) {
                 const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
                 sAp[k * BLK] = as_f2(df_fma(xj, i0, as_df(sAp[k * BLK])));
                 acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
             }
-            sAp[j * BLK] = as_f2(df_add(as_df(sAp[j * BLK]), df_add(acc0, acc1)));
+            sAp[j * BLK] = as_f2(df_add(as_df(sAp[j * BLK]), df_add(df_add(acc0, acc1), df_add(acc2, acc3))));
         }
         if (NP > 1) __syncthreads();
         // this part's species: the partials in part order into row 0
@@ -165,27 +173,34 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
             const dfl lnmu = poly3_df(m.df_mu_fit + 4 * k, u);
             const dfl sig = df_exp(df_add(dscale(lnmu, 0.5f), dneg(ld2(m.df_qlnW + k))), etab);   // mu^1/2 W^-1/4
             const float2* Ak = m.df_wilkeA + (size_t)k * K;
-            // even and odd j in separate sums: six independent chains per thread
+            // j in four interleaved sums: twelve independent chains per thread
             dfl S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, T1{0.0f, 0.0f}, T2{0.0f, 0.0f};
+            dfl U0{0.0f, 0.0f}, U1{0.0f, 0.0f}, U2{0.0f, 0.0f}, V0{0.0f, 0.0f}, V1{0.0f, 0.0f}, V2{0.0f, 0.0f};
             int j = 0;
-            for (; j + 1 < K; j += 2) {
-                const dfl a = ld2(Ak + j), b = ld2(Ak + j + 1);
+            for (; j + 3 < K; j += 4) {
+                const dfl a = ld2(Ak + j), b = ld2(Ak + j + 1), c = ld2(Ak + j + 2), d = ld2(Ak + j + 3);
                 S0 = df_fma(a, as_df(sX[j * BLK]), S0);
                 T0 = df_fma(b, as_df(sX[(j + 1) * BLK]), T0);
+                U0 = df_fma(c, as_df(sX[(j + 2) * BLK]), U0);
+                V0 = df_fma(d, as_df(sX[(j + 3) * BLK]), V0);
                 S1 = df_fma(a, as_df(sA0[j * BLK]), S1);
                 T1 = df_fma(b, as_df(sA0[(j + 1) * BLK]), T1);
+                U1 = df_fma(c, as_df(sA0[(j + 2) * BLK]), U1);
+                V1 = df_fma(d, as_df(sA0[(j + 3) * BLK]), V1);
                 S2 = df_fma(a, as_df(sB[j * BLK]), S2);
                 T2 = df_fma(b, as_df(sB[(j + 1) * BLK]), T2);
+                U2 = df_fma(c, as_df(sB[(j + 2) * BLK]), U2);
+                V2 = df_fma(d, as_df(sB[(j + 3) * BLK]), V2);
             }
-            if (j < K) {
+            for (; j < K; ++j) {
                 const dfl a = ld2(Ak + j);
                 S0 = df_fma(a, as_df(sX[j * BLK]), S0);
                 S1 = df_fma(a, as_df(sA0[j * BLK]), S1);
                 S2 = df_fma(a, as_df(sB[j * BLK]), S2);
             }
-            S0 = df_add(S0, T0);
-            S1 = df_add(S1, T1);
-            S2 = df_add(S2, T2);
+            S0 = df_add(df_add(S0, T0), df_add(U0, V0));
+            S1 = df_add(df_add(S1, T1), df_add(U1, V1));
+            S2 = df_add(df_add(S2, T2), df_add(U2, V2));
             const dfl den = df_fma(sig, df_fma(sig, S2, dscale(S1, 2.0f)), S0);
             const dfl muk = df_exp(lnmu, etab);
             mu = df_add(mu, df_div(df_mul(as_df(sX[k * BLK]), muk), den));

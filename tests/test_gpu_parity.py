@@ -241,6 +241,38 @@ def test_full_size_flame_workload_sampled(cuda):
     assert np.all(np.isfinite(host(h))) and np.all(np.isfinite(host(mu)))
 
 
+def test_full_size_all_points_cross_forms(cuda):
+    """Every point of the 2,097,152-point field, between independent code paths (the oracle checks a
+    sample above): the FP64 rates (logarithmic products in double-float pairs) against the
+    all-double form (products in double, the library's double exp/log); the JVP (logarithmic
+    tangents) against the per-entry stored linearization's product (exclusive products in double).
+    Without the oracle's cancellation scales at every point, each point's differences are measured
+    against its largest |omega_k| (|d omega_k|) and the heat release against sum_k |h_k omega_k|
+    (sum_k |h_k d omega_k|); the flame-field states are far from equilibrium, where these are of the
+    order of the scales."""
+    mech = synth.mechanism("ch4_53sp_325rx")
+    m = gpu_mechanism("ch4_53sp_325rx")
+    st = synth.workload_states("flame_4096el", mech.K)
+    T, p, Y = to_dev(st.T, st.p, st.Y)
+    hk = nk.thermo_eval(m, T, p, Y)["h_k"]
+    w, h = nk.rates_eval(m, T, p, Y)
+    w2, h2 = nk.rates_eval(m, T, p, Y, precision="fp64_native")
+    sw = w2.abs().amax(0)
+    assert float(((w - w2).abs().amax(0) / sw).max()) <= TOL64
+    assert float(((h - h2).abs() / (hk * w2).abs().sum(0)).max()) <= TOL64
+    del w, w2, h, h2
+    g = torch.Generator(device="cuda").manual_seed(77)
+    vT = torch.randn(st.n, generator=g, dtype=torch.float64, device="cuda")
+    vY = torch.randn((mech.K, st.n), generator=g, dtype=torch.float64, device="cuda")
+    dw, dh = nk.rates_jvp(m, T, p, Y, vT, vY)
+    lin = nk.rates_linearize(m, T, p, Y)
+    dw2, dh2 = nk.rates_jvp_linearized(m, T, p, Y, lin, vT, vY)
+    del lin
+    assert float(((dw - dw2).abs().amax(0) / dw2.abs().amax(0)).max()) <= TOL64
+    assert float(((dh - dh2).abs() / (hk * dw2).abs().sum(0)).max()) <= TOL64
+    assert torch.isfinite(dh).all()
+
+
 @pytest.mark.parametrize("name,n", [("ch4_53sp_325rx", 4096), ("big_120sp_700rx", 2048), ("h2_9sp_21rx", 4096)])
 def test_mixed_form_per_output_errors(cuda, name, n):
     mech = synth.mechanism(name)

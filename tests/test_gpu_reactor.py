@@ -63,6 +63,36 @@ def test_reactor_step_vs_dense_newton(cuda, name, n, dt):
     assert wrms <= 1e-3                                    # 1e-3 of the weights: ~1e-9 relative
 
 
+def test_reactor_step_moving_states_53sp(cuda):
+    """53 species on states where chemistry moves: the synthetic mechanism's equilibria hold most
+    species near 1e-157 (net rates ~1e-25/s, a frozen step), so they are blended with 1e-20 of a
+    Dirichlet(0.3) composition (those species at ~1e-22).  The block-Jacobi step at dt = 1e-10 s
+    then needs several Newton and Krylov iterations; its result against the oracle's dense Newton
+    solution."""
+    mech = synth.mechanism("ch4_53sp_325rx")
+    m = gpu_mechanism("ch4_53sp_325rx")
+    T, p, Y = _near_equilibrium(mech, 96, seed=23)
+    rng = np.random.default_rng(24)
+    Y = (1.0 - 1e-20) * Y + 1e-20 * rng.dirichlet(np.full(mech.K, 0.3), size=96).T
+    Y = np.ascontiguousarray(Y / Y.sum(0))
+    rtol, atolT, atolY, dt = 1e-6, 1e-6, 1e-12, 1e-10
+    T1, Y1, st = _step(m, *to_dev(T, p, Y), dt, rtol=rtol, atol_T=atolT, atol_Y=atolY, newton_tol=1e-4,
+                       lin_tol=1e-6, max_newton=20, krylov_dim=30, precond=1)
+    assert st["converged"] == 1, st
+    assert st["krylov_iters"] > 1 and st["newton_iters"] > 1, st
+    T_o, Y_o, it = oracle.reactor_step(mech, T, p, Y, dt, atol_T=atolT, atol_Y=atolY)
+    assert np.all(it > 0)
+    wT = 1.0 / (rtol * np.abs(T) + atolT)
+    wY = 1.0 / (rtol * np.abs(Y) + atolY)
+    d = np.concatenate([((host(T1) - T_o) * wT)[None], (host(Y1) - Y_o) * wY])
+    assert np.sqrt(np.mean(d ** 2)) <= 1e-3
+    # the step moved the state (the oracle's own change, in the same weights)
+    moved = np.concatenate([((T_o - T) * wT)[None], (Y_o - Y) * wY])
+    print(f"\n53 species moving: newton {st['newton_iters']}, krylov {st['krylov_iters']}, "
+          f"oracle change {np.sqrt(np.mean(moved ** 2)):.2e}")
+    assert np.max(np.abs(moved)) > 0.0
+
+
 def test_reactor_step_edge_cases(cuda):
     mech = synth.mechanism("h2_9sp_21rx")
     m = gpu_mechanism("h2_9sp_21rx")
