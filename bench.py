@@ -300,14 +300,26 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
                  rates at the state (FP64), then nk_rates_jvp_linearized_compact per direction;
       per-entry  the same forward as recompute plus nk_rates_linearize, then
                  nk_rates_jvp_linearized per direction (only where its data fit: not at 16.8M points).
-    Each direction is drawn (seeded, on the device) before its product, outside the timed spans;
-    a sweep's time is the sum of CUDA-event spans around its forward and its n_dir products on the
+    Every call goes through the C ABI into buffers allocated before timing, and the difference
+    quotients use in-place operations, so no arm waits on the allocator inside its spans.  Each
+    direction is drawn (seeded, on the device) before its product, outside the timed spans; a
+    sweep's time is the sum of CUDA-event spans around its forward and its n_dir products on the
     launching stream (one direction buffer stays resident instead of n_dir)."""
     import torch
     n, K = T.shape[0], Y.shape[0]
     f64 = dict(dtype=torch.float64, device=T.device)
-    vT = torch.empty(n, **f64)
-    vY = torch.empty((K, n), **f64)
+    L = nk.lib()
+    sp = nk._vp(stream.cuda_stream)
+    P = lambda t: nk._vp(t.data_ptr())
+    h = m.handle
+
+    def chk(st_):
+        if st_ != 0:
+            raise nk.NkError(st_, L.nk_last_error().decode())
+
+    vT, dh, hrr, cp, hm, mu, lam, Tp, h1 = (torch.empty(n, **f64) for _ in range(9))
+    vY, dw, w, D, Yp, w1 = (torch.empty((K, n), **f64) for _ in range(6))
+    w0, h0 = torch.empty((K, n), **f64), torch.empty(n, **f64)
     eps = 2.220446049250313e-16
 
     def direction(d):
@@ -337,62 +349,73 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
         sweep(forward, product)                       # warm-up
         return sum(sweep(forward, product) for _ in range(steps)) / steps
 
+    def thermo():
+        chk(L.nk_thermo_eval(h, n, n, P(T), P(p), P(Y), P(cp), P(hm), None, None, None, None, None, sp))
+
+    def rates(prec, Tx, Yx, wo, ho):
+        chk(L.nk_rates_eval(h, n, n, P(Tx), P(p), P(Yx), None, P(wo), P(ho), prec, sp))
+
+    def transport(prec):
+        chk(L.nk_transport_eval(h, n, n, P(T), P(p), P(Y), P(mu), P(lam), P(D), prec, sp))
+
     def fwd_mixed():
-        nk.thermo_eval(m, T, p, Y, species=False)
-        nk.rates_eval(m, T, p, Y, precision="mixed")
-        nk.transport_eval(m, T, p, Y, precision="mixed")
+        thermo()
+        rates(1, T, Y, w, hrr)
+        transport(1)
 
     def recompute(_):
-        return nk.rates_jvp(m, T, p, Y, vT, vY)
+        chk(L.nk_rates_jvp(h, n, n, P(T), P(p), P(Y), None, P(vT), P(vY), None, None, P(dw), P(dh), sp))
 
     def fwd_fd():
-        xnorm = torch.sqrt(T * T + (Y * Y).sum(0))
-        nk.thermo_eval(m, T, p, Y, species=False)
-        w0, h0 = nk.rates_eval(m, T, p, Y)
-        nk.transport_eval(m, T, p, Y)
-        return xnorm, w0, h0
+        xnorm = torch.sqrt(T * T + torch.linalg.vector_norm(Y, dim=0) ** 2)
+        thermo()
+        rates(0, T, Y, w0, h0)
+        transport(0)
+        return xnorm
 
-    def fd(ctx):
-        xnorm, w0, h0 = ctx
-        sig = torch.sqrt((1.0 + xnorm) * eps) / torch.sqrt(vT * vT + (vY * vY).sum(0))
-        w1, h1 = nk.rates_eval(m, T + sig * vT, p, Y + sig * vY)
-        return (w1 - w0) / sig, (h1 - h0) / sig
+    def fd(xnorm):
+        sig = torch.sqrt((1.0 + xnorm) * eps) / torch.sqrt(vT * vT + torch.linalg.vector_norm(vY, dim=0) ** 2)
+        torch.addcmul(T, sig, vT, out=Tp)
+        torch.addcmul(Y, sig, vY, out=Yp)
+        rates(0, Tp, Yp, w1, h1)
+        torch.sub(w1, w0, out=dw).div_(sig)
+        torch.sub(h1, h0, out=dh).div_(sig)
 
-    res = {"points": n, "directions": n_dir,
+    res = {"points": n, "directions": n_dir, "steps": steps,
            "timing": "sum of CUDA-event spans around the forward and each product; directions drawn "
-                     "outside the spans", "steps": steps}
+                     "outside the spans; every arm into preallocated buffers"}
     res["fd_fp64_sweep_ms"] = t_fd = timed(fwd_fd, fd)
     res["sweep_recompute_ms"] = t_re = timed(fwd_mixed, recompute)
     res["speedup_recompute_vs_fd"] = t_fd / t_re
 
-    # the per-reaction stored linearization, where it fits beside the field
+    # the per-reaction stored linearization, where it fits beside the field and the buffers above
     slots_c = nk.linearization_slots_compact(m)
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
     linc = None
-    if slots_c * n * 8 < free - 6 * (K + 2) * n * 8:
+    if slots_c * n * 8 < free - (4 << 30):
         linc = torch.empty((slots_c, n), **f64)
-
     if linc is not None:
         def fwd_compact():
-            nk.thermo_eval(m, T, p, Y, species=False)
-            nk.transport_eval(m, T, p, Y, precision="mixed")
-            return nk.rates_linearize_compact(m, T, p, Y, lin=linc, primal=True)
+            thermo()
+            transport(1)
+            chk(L.nk_rates_linearize_compact(h, n, n, P(T), P(p), P(Y), None, P(linc), n, P(w), P(hrr), sp))
 
         def compact(_):
-            return nk.rates_jvp_linearized_compact(m, T, p, Y, linc, vT, vY)
+            chk(L.nk_rates_jvp_linearized_compact(h, n, n, P(T), P(p), P(Y), P(linc), n, P(vT), P(vY), P(dw),
+                                                  P(dh), sp))
 
         res["sweep_compact_ms"] = t_c = timed(fwd_compact, compact)
         res["speedup_compact_vs_fd"] = t_fd / t_c
         res["compact_bytes"] = slots_c * n * 8
         # accuracy of the difference quotient against the exact JVP, last direction
         direction(n_dir - 1)
-        dw, _ = compact(None)
-        fw, _ = fd(fwd_fd())
-        sc = dw.abs().amax(0).clamp_min(1e-300)
-        res["fd_jvp_median_rel_err"] = ((fw - dw).abs().amax(0) / sc).median().item()
-        del dw, fw, sc
-        del linc
+        compact(None)
+        exact = dw.clone()
+        fd(fwd_fd())
+        sc = exact.abs().amax(0).clamp_min(1e-300)
+        res["fd_jvp_median_rel_err"] = ((dw - exact).abs().amax(0) / sc).median().item()
+        del exact, sc, linc
         torch.cuda.empty_cache()
     lin = None
     try:
@@ -402,10 +425,10 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
     if lin is not None:
         def fwd_lin():
             fwd_mixed()
-            nk.rates_linearize(m, T, p, Y, lin=lin)
+            chk(L.nk_rates_linearize(h, n, n, P(T), P(p), P(Y), None, P(lin), n, sp))
 
         def per_entry(_):
-            return nk.rates_jvp_linearized(m, T, p, Y, lin, vT, vY)
+            chk(L.nk_rates_jvp_linearized(h, n, n, P(T), P(p), P(Y), P(lin), n, P(vT), P(vY), P(dw), P(dh), sp))
 
         res["sweep_linearized_ms"] = t_l = timed(fwd_lin, per_entry)
         res["speedup_linearized_vs_fd"] = t_fd / t_l
@@ -565,15 +588,40 @@ def reactor_row(nk, m, mech, n, dev, stream, dt=1e-9, dt_large=1e-5):
     res["block_jacobi_reused"] = run(dt, 2)
     res["block_jacobi_large_dt"] = run(dt_large, 1)
     res["block_jacobi_large_dt_reused"] = run(dt_large, 2)
-    # states where chemistry moves (blend 1e-20), block-Jacobi at dt = 1e-10 s
-    T0b, _, Y0b = reactor_states(nk, m, mech, n, dev, blend=1e-20)
-    T0.copy_(T0b)
-    Y0.copy_(Y0b)
-    del T0b, Y0b
-    res["moving_block_jacobi"] = run(1e-10, 1)
-    res["moving_block_jacobi"]["states"] = "near-equilibrium states blended with 1e-20 of a Dirichlet(0.3) composition"
-    res["moving_block_jacobi_reused"] = run(1e-10, 2)
+    res["moving"] = reactor_moving_row(nk, m, mech, dev, stream)
     return res
+
+
+def reactor_moving_row(nk, m, mech, dev, stream, n=65536, dt=1e-10):
+    """The block-Jacobi reactor step on states where chemistry moves: the near-equilibrium states
+    blended with 1e-20 of a Dirichlet(0.3) composition (reactor_states), on n points (the Newton-
+    Krylov solve over all points is global: the more points, the stiffer the hardest one it must
+    resolve), each after one untimed step from the same states."""
+    import torch
+    T0, p, Y0 = reactor_states(nk, m, mech, n, dev, blend=1e-20)
+    kw = dict(rtol=1e-6, atol_T=1e-6, atol_Y=1e-12, newton_tol=1e-4, lin_tol=1e-6, max_newton=20, krylov_dim=30)
+    ws = torch.empty(nk.reactor_workspace(m, n, kw["krylov_dim"], 1, 0), dtype=torch.uint8, device=dev)
+    T, Y = T0.clone(), Y0.clone()
+    out = {"points": n, "dt_s": dt, "states": "near-equilibrium states blended with 1e-20 of a Dirichlet(0.3) "
+                                              "composition (species lifted from ~1e-157 to ~1e-22)"}
+    for name, precond in (("block_jacobi", 1), ("block_jacobi_reused", 2)):
+        o = nk.reactor_opts(precond=precond, **kw)
+        for _ in (0, 1):
+            T.copy_(T0)
+            Y.copy_(Y0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = nk.reactor_step(m, T, p, Y, dt, o, workspace=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+        wT = 1.0 / (kw["rtol"] * T0.abs() + kw["atol_T"])
+        wY = 1.0 / (kw["rtol"] * Y0.abs() + kw["atol_Y"])
+        chg = torch.sqrt((((T - T0) * wT) ** 2).sum() + (((Y - Y0) * wY) ** 2).sum()) / (((Y.shape[0] + 1) * n) ** 0.5)
+        out[name] = {"ms": a.elapsed_time(b), "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters"],
+                     "converged": st["converged"], "update_wrms": st["update_wrms"],
+                     "step_change_wrms": float(chg)}
+    return out
 
 
 # ---------------------------------------------------------------------------------- our arm
