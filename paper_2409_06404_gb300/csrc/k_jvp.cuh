@@ -184,11 +184,11 @@ __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const doub
 // The logarithmic form (blocks whose mass fractions are all at least 2^-100 and whose direction
 // the pairs can carry; see the kernel).  The point's rows hold ln C_k and r_k = dC_k/C_k =
 // d rho/rho + dY_k/Y_k as pairs, and with F the falloff factor (1 but for Troe reactions)
-//   q_f = F exp(ln k_f + sum_reac nu ln C),   q_r = F exp(ln k_f - ln K_c + sum_prod nu ln C),
-//   dq  = q_f (d ln k_f + sum_reac nu r) - q_r (d ln k_f - d ln K_c + sum_prod nu r),
-// the exponent and tangent sums in pairs; the exponentials' results, the difference, dq, [M]
-// scaling, the scatter and the heat-release sums in double.  No concentration product is
-// formed.
+//   q_f = exp(ln k_f + ln F + sum_reac nu ln C),   q_r = exp(ln k_f + ln F - ln K_c + sum_prod nu ln C),
+//   dq  = q_f (d ln k_f + d ln F + sum_reac nu r) - q_r (d ln k_f + d ln F - d ln K_c + sum_prod nu r),
+// the exponent and tangent sums (with the whole falloff chain) in pairs; the exponentials'
+// results, the difference, dq, [M] scaling, the scatter and the heat-release sums in double.
+// No concentration product is formed.
 template <int BLK, int KIND, bool OMEGA, bool RHS>
 __device__ __forceinline__ void jvp_reaction_log(const DevMech& m, int r, const float2* sL, const float2* sR,
                                                  double* sW, double* sD, const JvpPoint& Q, const double* dlnA,
@@ -202,72 +202,52 @@ __device__ __forceinline__ void jvp_reaction_log(const DevMech& m, int r, const 
     rxn_thermo<true, true>(m, x.thermo, Q.P, dG, dH, dCp);
     const float dnu = dnu_f(m, r);
     const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu), df_neg(dG));
-    double shift = 0.0;
     dfl shiftd{0.0f, 0.0f};
-    if (dlnA) {
-        shift = __ldg(dlnA + x.orig);
-        shiftd = df_split(shift);
-    }
+    if (dlnA) shiftd = df_split(__ldg(dlnA + x.orig));
     const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
-    const float4 a0 = __ldg(m.rxn_df + 2 * r), a1 = __ldg(m.rxn_df + 2 * r + 1);
-    const dfl dlnkf = df_mul(df_fma(dfl{a1.x, a1.y}, Q.P.invTd, dfl{a0.z, a0.w}), Q.tTd);   // (beta + Ea/RT) dT/T
+    const dfl dlnkf = df_mul(arrh_slope_df(m, r, Q.P), Q.tTd);                               // (beta + Ea/RT) dT/T
     const dfl dlnKc = df_mul(Q.tTd, df_add(dH, dfl{-dnu, 0.0f}));                            // (sum nu h/RT - sum nu) dT/T
 
     double M = 0.0, dM = 0.0;
+    dfl Mp{0.0f, 0.0f}, dMp{0.0f, 0.0f};
     if (KIND != 0) {
-        dfl Mp = Q.pRTd, dMp = Q.dpRTd;
+        Mp = Q.pRTd;
+        dMp = Q.dpRTd;
         for (int j = x.eff0; j < x.eff1; ++j) {
             const int k = __ldg(m.eff_sp + j);
             const dfl ec = df_mul(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[k * BLK]), dt.e2));
             Mp = df_add(Mp, ec);
             dMp = df_fma(ec, dfl_of(sR[k * BLK]), dMp);
         }
-        M = df_to_d(Mp);
-        dM = df_to_d(dMp);
-    }
-    double F = 1.0, dlnF = 0.0;                   // Troe: F = g 10^lF and d ln F
-    if constexpr (KIND == 2) {
-        if (M == 0.0) {
-            F = 0.0;
-        } else {
-            const TroeRec* t = m.troe + x.aux;
-            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
-            const double lnk0 = fma(-Ea0R, Q.invT, fma(beta0, Q.lnT, __ldg(&t->lnA0) + shift));
-            const double dlnk0 = fma(Ea0R, Q.invT, beta0) * Q.tT;
-            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
-            const double dlnPr = dlnk0 - df_to_d(dlnkf) + dM / M;
-            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
-            double Fc = (1.0 - a) * e3 + a * e1;
-            double dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1) * Q.dT;
-            if (__ldg(&t->hasT2) != 0.0) {
-                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
-                Fc += e2;
-                dFc = fma(T2 * Q.invT * e2, Q.tT, dFc);
-            }
-            const double lFc = dlog_df(Fc, dt) * kInvLn10, dlFc = dFc / Fc * kInvLn10;
-            const double c = fma(-0.67, lFc, -0.4), nn = fma(-1.27, lFc, 0.75);
-            const double u = fma(lnPr, kInvLn10, c), du = fma(dlnPr, kInvLn10, -0.67 * dlFc);
-            const double v = fma(-0.14, u, nn), dv = fma(-0.14, du, -1.27 * dlFc);
-            const double f1 = u / v, df1 = fma(-f1, dv, du) / v;
-            const double den = fma(f1, f1, 1.0);
-            const double lF = lFc / den;
-            const double dlF = fma(-2.0 * lF * f1, df1, dlFc) / den;
-            const double g = 1.0 / (1.0 + dexp_df(-lnPr, dt));       // P_r / (1 + P_r)
-            F = g * dexp_df(lF * kLn10, dt);
-            dlnF = dlnPr * (1.0 - g) + kLn10 * dlF;
+        if (KIND == 1) {
+            M = df_to_d(Mp);
+            dM = df_to_d(dMp);
         }
     }
-    double qf = exp_df_d(df_add(lnkf, sf), dt.e2);
-    double qr = exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
-    double Gf = df_to_d(df_add(dlnkf, gf));
-    double Gb = df_to_d(df_add(df_add(dlnkf, df_neg(dlnKc)), gb));
+    // Troe: ln F and its tangent in pairs, folded into the exponents and the tangent sums
+    //   d ln F = Px d ln P_r + PL dL,  d ln P_r = (c0 - c1) dT/T + d[M]/[M],  dL = LT dT/T
+    dfl lnF{0.0f, 0.0f}, dlnF{0.0f, 0.0f};
+    bool noF = false;                             // [M] = 0: no falloff term
     if constexpr (KIND == 2) {
-        qf *= F;
-        qr *= F;
-        Gf += dlnF;
-        Gb += dlnF;
+        if (Mp.h == 0.0f) {
+            noF = true;
+        } else {
+            dfl c0;
+            const dfl lnPr = troe_lnPr(m, x.aux, Q.P, lnkf, shiftd, dlnA != nullptr, Mp, dt, &c0);
+            const TroeCent c = troe_cent(m, x.aux, Q.P, dt);
+            const TroeLog f = troe_log(lnPr, c.L, dt);
+            lnF = f.lnF;
+            const dfl dx = df_add(df_add(df_mul(c0, Q.tTd), df_neg(dlnkf)), df_div(dMp, Mp));
+            dlnF = df_fma(f.Px, dx, df_mul(f.PL, df_mul(c.LT, Q.tTd)));
+        }
     }
+    const dfl lnkF = KIND == 2 ? df_add(lnkf, lnF) : lnkf;
+    const dfl dlnkF = KIND == 2 ? df_add(dlnkf, dlnF) : dlnkf;
+    double qf = exp_df_d(df_add(lnkF, sf), dt.e2);
+    double qr = exp_df_d(df_add(df_add(lnkF, df_neg(lnKc)), sb), dt.e2);
+    const double Gf = df_to_d(df_add(dlnkF, gf));
+    const double Gb = df_to_d(df_add(df_add(dlnkF, df_neg(dlnKc)), gb));
+    if (KIND == 2 && noF) qf = qr = 0.0;
     double q = qf - qr;
     double dq = fma(qf, Gf, -qr * Gb);
     if (KIND == 1) {

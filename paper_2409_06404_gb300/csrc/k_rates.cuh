@@ -57,6 +57,7 @@ struct Pt {
     double T, lnT, invT, pRT, lnP0RT;
     float Tf, lnTf, invTf;
     TPairs tp;                       // kDF form
+    dfl pRTd;                        // kDF form: p/(RT) as a pair
 };
 
 // sum_k nu_k g_k/RT (products minus reactants) and the concentration products of each side;
@@ -235,26 +236,20 @@ __device__ __forceinline__ double third_body(const DevMech& m, const Rxn& x, con
     return M;
 }
 
-// Troe factor F * P_r/(1+P_r) with the exponent arithmetic in pairs.
-__device__ __forceinline__ double troe_factor_df(const DevMech& m, int aux, dfl lnkinf, dfl lnk0, double M,
-                                                 const Pt& P, const DfTab& dt) {
-    const TroeRec* t = m.troe + aux;
-    const float4 t1 = __ldg(m.troe_df + 3 * aux + 1);    // (Ea0/R, 1/T3)
-    const float4 t2 = __ldg(m.troe_df + 3 * aux + 2);    // (1/T1, T2)
-    const dfl lnPr = df_add(df_add(lnk0, df_neg(lnkinf)), log_df(M, dt.rc, dt.lc));
-    const double a = __ldg(&t->a);
-    double Fc = (1.0 - a) * exp_df_d(df_neg(df_mul(P.tp.Td, dfl{t1.z, t1.w})), dt.e2) +
-                a * exp_df_d(df_neg(df_mul(P.tp.Td, dfl{t2.x, t2.y})), dt.e2);
-    if (__ldg(&t->hasT2) != 0.0) Fc += exp_df_d(df_neg(df_mul(dfl{t2.z, t2.w}, P.tp.invTd)), dt.e2);
-    const dfl lFc = df_mul(log_df(Fc, dt.rc, dt.lc), dfc_invln10());
-    const dfl c = df_add(dfc_m0_4(), df_mul(lFc, dfc_m0_67()));
-    const dfl nn = df_add(dfl{0.75f, 0.0f}, df_mul(lFc, dfc_m1_27()));
-    const dfl u = df_add(df_mul(lnPr, dfc_invln10()), c);
-    const dfl f1 = df_div(u, df_add(nn, df_mul(u, dfc_m0_14())));
-    const dfl lF = df_div(lFc, df_fma(f1, f1, dfl{1.0f, 0.0f}));
-    return exp_df_d(df_mul(lF, dfc_ln10()), dt.e2) / (1.0 + exp_df_d(df_neg(lnPr), dt.e2));
+// [M] = p/(RT) + sum (eps - 1) C_j as a pair from the logarithms ln C_j (terms below the float
+// range drop out: they are under 1e-37 against p/(RT))
+template <int BLK>
+__device__ __forceinline__ dfl third_body_pair(const DevMech& m, const Rxn& x, const float2* sL, const Pt& P,
+                                               const DfTab& dt) {
+    dfl M = P.pRTd;
+    for (int j = x.eff0; j < x.eff1; ++j)
+        M = df_fma(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[__ldg(m.eff_sp + j) * BLK]), dt.e2), M);
+    return M;
 }
 
+// FP64 form.  The exponent of each rate term, ln k_f (+ ln F, the Troe falloff factor, whose
+// whole chain runs in pairs: troe_log) + the concentration logarithms (LOG) - ln K_c, in pairs;
+// the terms, their difference and the [M] factor of third-body reactions in double.
 template <int BLK, int KIND, bool LOG>
 __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const float2* sL,
                                                       const Conc& cs, const Pt& P, const double* dlnA,
@@ -265,32 +260,38 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
     dfl shift{0.0f, 0.0f};
     if (dlnA) shift = df_split(__ldg(dlnA + x.orig));
     const dfl lnkf = ln_kf_df(m, r, P.tp, shift, dlnA != nullptr);
-    const double M = KIND != 0 ? third_body<BLK, LOG>(m, x, sL, cs, P, dt) : 0.0;
-    double F = 1.0;                                              // Troe: F P_r/(1 + P_r)
+    double M = 0.0;
+    dfl Mp{0.0f, 0.0f};
+    if constexpr (KIND != 0) {
+        if constexpr (LOG) {
+            Mp = third_body_pair<BLK>(m, x, sL, P, dt);
+            if (KIND == 1) M = df_to_d(Mp);
+        } else {
+            M = third_body<BLK, false>(m, x, sL, cs, P, dt);
+            if (KIND == 2) Mp = df_split(M);
+        }
+    }
+    dfl lnkF = lnkf;                                             // ln k_f + ln F
+    bool noF = false;                                            // Troe with [M] = 0: no rate
     if constexpr (KIND == 2) {
-        const float4 t0 = __ldg(m.troe_df + 3 * x.aux);          // (lnA0, beta0)
-        const float4 t1 = __ldg(m.troe_df + 3 * x.aux + 1);      // (Ea0/R, 1/T3)
-        dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.tp.lnTd, dfl{t0.x, t0.y});
-        lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.tp.invTd, lnk0);
-        if (dlnA) lnk0 = df_add(lnk0, shift);
-        F = M == 0.0 ? 0.0 : troe_factor_df(m, x.aux, lnkf, lnk0, M, P, dt);
+        if (Mp.h == 0.0f) {
+            noF = true;
+        } else {
+            const dfl lnPr = troe_lnPr(m, x.aux, P.tp, lnkf, shift, dlnA != nullptr, Mp, dt, nullptr);
+            lnkF = df_add(lnkf, troe_log(lnPr, troe_cent(m, x.aux, P.tp, dt).L, dt).lnF);
+        }
     }
     double q;
     if constexpr (LOG) {
         const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
         const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
-        q = exp_df_d(df_add(lnkf, sf), dt.e2) - exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
-        if (KIND == 2) q *= F;
+        q = exp_df_d(df_add(lnkF, sf), dt.e2) - exp_df_d(df_add(df_add(lnkF, df_neg(lnKc)), sb), dt.e2);
+        if (KIND == 2 && noF) q = 0.0;
     } else {
-        double fw, rv, kf, kr;
+        double fw, rv;
         products_direct(x, cs, fw, rv);
-        if constexpr (KIND == 2) {
-            kf = F == 0.0 ? 0.0 : exp_df_d(lnkf, dt.e2) * F;
-            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
-        } else {
-            kf = exp_df_d(lnkf, dt.e2);
-            kr = exp_df_d(df_add(lnkf, df_neg(lnKc)), dt.e2);
-        }
+        double kf = exp_df_d(lnkF, dt.e2), kr = exp_df_d(df_add(lnkF, df_neg(lnKc)), dt.e2);
+        if (KIND == 2 && noF) kf = kr = 0.0;
         q = fma(kf, fw, -kr * rv);
     }
     if (KIND == 1) q *= M;
@@ -309,18 +310,29 @@ __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
     const dfl lnKc = df_add(df_mul_f(P.tp.lnP0RTd, dnu_f(m, r)), df_neg(sumg));   // ln K_c
     const float shf = dlnA ? (float)__ldg(dlnA + x.orig) : 0.0f;
-    const double M = KIND != 0 ? third_body<BLK, LOG>(m, x, sL, cs, P, dt) : 0.0;
+    double M = 0.0;                                              // [M] in double (third-body rows)
+    float Mf = 0.0f;                                             // and in float (the falloff)
+    if constexpr (KIND != 0) {
+        if constexpr (LOG) {
+            const dfl Mp = third_body_pair<BLK>(m, x, sL, P, dt);
+            Mf = Mp.h;
+            if (KIND == 1) M = df_to_d(Mp);
+        } else {
+            M = third_body<BLK, false>(m, x, sL, cs, P, dt);
+            Mf = narrow(M);
+        }
+    }
     const float4 xf = __ldg(reinterpret_cast<const float4*>(m.rxnf + r));   // lnA, beta, EaR
     const float lnkf = fmaf(-xf.z, P.invTf, fmaf(xf.y, P.lnTf, xf.x + shf));
     float Ff = 1.0f;                                             // Troe: F P_r/(1 + P_r)
     if constexpr (KIND == 2) {
         const float4 t0 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux));       // lnA0, beta0, Ea0R, a
         const float4 t1 = __ldg(reinterpret_cast<const float4*>(m.troef + x.aux) + 1);   // 1/T3, 1/T1, T2, has
-        if (M == 0.0) {
+        if (Mf == 0.0f) {
             Ff = 0.0f;
         } else {
             const float lnk0 = fmaf(-t0.z, P.invTf, fmaf(t0.y, P.lnTf, t0.x + shf));
-            const float lnPr = lnk0 - lnkf + logf(narrow(M));
+            const float lnPr = lnk0 - lnkf + logf(Mf);
             float Fc = (1.0f - t0.w) * expf(-P.Tf * t1.x) + t0.w * expf(-P.Tf * t1.y);
             if (t1.w != 0.0f) Fc += expf(-t1.z * P.invTf);
             const float lFc = log10f(Fc);
@@ -343,7 +355,7 @@ __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const
         double fw, rv;
         products_direct(x, cs, fw, rv);
         double kf = exp_f32_to_f64(lnkf);
-        if (KIND == 2) kf = M == 0.0 ? 0.0 : kf * (double)Ff;
+        if (KIND == 2) kf = Mf == 0.0f ? 0.0 : kf * widen(Ff);
         const double kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
         q = fma(kf, fw, -kr * rv);
     }
@@ -441,6 +453,7 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
         P.Tf = P.tp.Td.h;
         P.lnTf = P.tp.lnTd.h + P.tp.lnTd.l;
         P.invTf = P.tp.invTd.h;
+        P.pRTd = df_split(P.pRT);
     }
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);

@@ -40,21 +40,71 @@ __device__ __forceinline__ dfl poly3_df(const float2* c, dfl u) {
     return df_fma(acc, u, ld2(c + 0));
 }
 
-// Zigzag ownership of the pair rows j (row j holds the pairs (j, k > j)): in each run of 2 NP
-// rows, part q takes rows q and 2 NP - 1 - q, so the parts get nearly equal pair counts.
+// Shared rows per point (8 bytes per species): X_k, the diffusion sums (later X_k tau_k) and
+// one row for the mass-fraction prefix sums (later X_k tau_k^2).
+constexpr int kTransportRows = 3;
+
+// The species-pair triangle of the diffusion sums in G = 2 NP contiguous species groups.  In
+// each of the first G - 1 rounds the NP parts take NP group pairs that share no species (the
+// circle method of a round-robin schedule: group G - 1 meets group r, groups (r + q) and
+// (r - q) mod (G - 1) meet for q = 1 .. NP - 1); in the last round part q takes the pairs within
+// groups 2q and 2q + 1.  So within a round no two parts touch one species, every part adds
+// straight into the one row of sums, and the order of each sum is fixed by the schedule.
 template <int NP>
-__device__ __forceinline__ bool owns_row(int j, int part) {
-    const int q = j % (2 * NP);
-    return (q < NP ? q : 2 * NP - 1 - q) == part;
+__device__ __forceinline__ void round_groups(int r, int part, int& ga, int& gb) {
+    constexpr int G = 2 * NP;
+    if (part == 0) {
+        ga = r;
+        gb = G - 1;
+    } else {
+        ga = (r + part) % (G - 1);
+        gb = (r - part + G - 1) % (G - 1);
+    }
+    if (ga > gb) {
+        const int t = ga;
+        ga = gb;
+        gb = t;
+    }
 }
 
-// Shared rows per point (8 bytes per species): X_k, NP rows of diffusion-sum partials, and one
-// row for the mass-fraction prefix sums (later X tau^2).
-__host__ __device__ constexpr int transport_rows(int np) { return 2 + np; }
+// The pairs (j, k) with j in [j0, j1) and k in [k0, k1), k > j (k0 = j0, k1 = j1 for a group with
+// itself): S_j += X_k / D_jk in registers, S_k += X_j / D_jk in the row, one exponential per pair,
+// four pairs per iteration (four independent exponential chains per thread).
+template <int BLK>
+__device__ __forceinline__ void diffusion_pairs(int K, int j0, int j1, int k0, int k1, bool same, const float2* Dc,
+                                                dfl u, const float2* etab, const float2* sX, float2* sS) {
+    for (int j = j0; j < j1; ++j) {
+        const int kb = same ? j + 1 : k0;
+        int pi = j * (2 * K - j - 1) / 2 + (kb - j - 1);       // index of the pair (j, kb)
+        const dfl xj = as_df(sX[j * BLK]);
+        dfl acc0{0.0f, 0.0f}, acc1{0.0f, 0.0f}, acc2{0.0f, 0.0f}, acc3{0.0f, 0.0f};
+        int k = kb;
+        for (; k + 3 < k1; k += 4, pi += 4) {
+            const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
+            const dfl i1 = df_exp(dneg(poly3_df(Dc + 4 * pi + 4, u)), etab);
+            const dfl i2 = df_exp(dneg(poly3_df(Dc + 4 * pi + 8, u)), etab);
+            const dfl i3 = df_exp(dneg(poly3_df(Dc + 4 * pi + 12, u)), etab);
+            sS[k * BLK] = as_f2(df_fma(xj, i0, as_df(sS[k * BLK])));
+            sS[(k + 1) * BLK] = as_f2(df_fma(xj, i1, as_df(sS[(k + 1) * BLK])));
+            sS[(k + 2) * BLK] = as_f2(df_fma(xj, i2, as_df(sS[(k + 2) * BLK])));
+            sS[(k + 3) * BLK] = as_f2(df_fma(xj, i3, as_df(sS[(k + 3) * BLK])));
+            acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
+            acc1 = df_fma(as_df(sX[(k + 1) * BLK]), i1, acc1);
+            acc2 = df_fma(as_df(sX[(k + 2) * BLK]), i2, acc2);
+            acc3 = df_fma(as_df(sX[(k + 3) * BLK]), i3, acc3);
+        }
+        for (; k < k1; ++k, ++pi) {
+            const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
+            sS[k * BLK] = as_f2(df_fma(xj, i0, as_df(sS[k * BLK])));
+            acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
+        }
+        sS[j * BLK] = as_f2(df_add(as_df(sS[j * BLK]), df_add(df_add(acc0, acc1), df_add(acc2, acc3))));
+    }
+}
 
 // BLK points per block, NP parts (warps) per point, as in the rates kernel: the parts split the
-// species-pair rows of the diffusion sums (each into its own partial row, added in part order)
-// and then the species of the conductivity, diffusion outputs and Wilke sums.
+// species-pair triangle of the diffusion sums by the round schedule above and then the species
+// of the conductivity, diffusion outputs and Wilke sums.
 template <int BLK, int NP>
 __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                                 const double* __restrict__ T,
@@ -76,10 +126,8 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
     const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
     float2* base = reinterpret_cast<float2*>(smem_all + kMathTabDoubles + kExpTab) + slot;
     float2* sX = base;                                        // X_k
-    float2* sA0 = base + (size_t)K * BLK;                     // diffusion-sum partials, part q at row q;
-                                                              // after them X_k tau_k in row 0
-    float2* sAp = sA0 + (size_t)part * K * BLK;
-    float2* sB = base + (size_t)(1 + NP) * K * BLK;           // Y prefix sums (as double), then X_k tau_k^2
+    float2* sA0 = base + (size_t)K * BLK;                     // diffusion sums, then X_k tau_k
+    float2* sB = base + (size_t)2 * K * BLK;                  // Y prefix sums (as double), then X_k tau_k^2
     double* sBd = reinterpret_cast<double*>(sB);
 
     const double Ti = T[i];
@@ -92,46 +140,21 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
 
     // ---- diffusion: sum_{j != k} X_j / D_jk(p_ref), one exponential per pair
     if (Dmix) {
-        for (int k = 0; k < K; ++k) sAp[k * BLK] = make_float2(0.0f, 0.0f);
+        for (int k = part; k < K; k += NP) sA0[k * BLK] = make_float2(0.0f, 0.0f);
         if (NP > 1) __syncthreads();
         const float2* Dc = m.df_D_fit;
-        for (int j = 0; j < K; ++j) {
-            if (!owns_row<NP>(j, part)) continue;
-            int pi = j * (2 * K - j - 1) / 2;                 // index of the pair (j, j + 1)
-            const dfl xj = as_df(sX[j * BLK]);
-            // four pairs per iteration: four independent exponential chains per thread (the loop is
-            // latency bound at the few warps the pair rows leave resident)
-            dfl acc0{0.0f, 0.0f}, acc1{0.0f, 0.0f}, acc2{0.0f, 0.0f}, acc3{0.0f, 0.0f};
-            int k = j + 1;
-            for (; k + 3 < K; k += 4, pi += 4) {
-                const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
-                const dfl i1 = df_exp(dneg(poly3_df(Dc + 4 * pi + 4, u)), etab);
-                const dfl i2 = df_exp(dneg(poly3_df(Dc + 4 * pi + 8, u)), etab);
-                const dfl i3 = df_exp(dneg(poly3_df(Dc + 4 * pi + 12, u)), etab);
-                sAp[k * BLK] = as_f2(df_fma(xj, i0, as_df(sAp[k * BLK])));
-                sAp[(k + 1) * BLK] = as_f2(df_fma(xj, i1, as_df(sAp[(k + 1) * BLK])));
-                sAp[(k + 2) * BLK] = as_f2(df_fma(xj, i2, as_df(sAp[(k + 2) * BLK])));
-                sAp[(k + 3) * BLK] = as_f2(df_fma(xj, i3, as_df(sAp[(k + 3) * BLK])));
-                acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
-                acc1 = df_fma(as_df(sX[(k + 1) * BLK]), i1, acc1);
-                acc2 = df_fma(as_df(sX[(k + 2) * BLK]), i2, acc2);
-                acc3 = df_fma(as_df(sX[(k + 3) * BLK]), i3, acc3);
-            }
-            for (; k < K; ++k, ++pi) {
-                const dfl i0 = df_exp(dneg(poly3_df(Dc + 4 * pi, u)), etab);
-                sAp[k * BLK] = as_f2(df_fma(xj, i0, as_df(sAp[k * BLK])));
-                acc0 = df_fma(as_df(sX[k * BLK]), i0, acc0);
-            }
-            sAp[j * BLK] = as_f2(df_add(as_df(sAp[j * BLK]), df_add(df_add(acc0, acc1), df_add(acc2, acc3))));
+        constexpr int G = 2 * NP;
+        for (int r = 0; r < G - 1; ++r) {
+            int ga, gb;
+            round_groups<NP>(r, part, ga, gb);
+            diffusion_pairs<BLK>(K, K * ga / G, K * (ga + 1) / G, K * gb / G, K * (gb + 1) / G, false, Dc, u, etab,
+                                 sX, sA0);
+            if (NP > 1) __syncthreads();
         }
+        for (int g = 2 * part; g < 2 * part + 2; ++g)
+            diffusion_pairs<BLK>(K, K * g / G, K * (g + 1) / G, K * g / G, K * (g + 1) / G, true, Dc, u, etab, sX,
+                                 sA0);
         if (NP > 1) __syncthreads();
-        // this part's species: the partials in part order into row 0
-        for (int k = part; k < K; k += NP) {
-            dfl d = as_df(sA0[k * BLK]);
-#pragma unroll
-            for (int q = 1; q < NP; ++q) d = df_add(d, as_df(sA0[((size_t)q * K + k) * BLK]));
-            sA0[k * BLK] = as_f2(d);
-        }
         // numerators sum_{j != k} Y_j from prefix and suffix sums (no 1 - Y_k cancellation)
         const double pscale = p[i] / m.p_ref;
         double pre = 0.0;
@@ -207,9 +230,9 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
         }
     }
     if constexpr (NP > 1) {
-        // the parts' sums in part order, through the (dead) partial row 1: rows 3q .. 3q+2 (3 NP <= K)
+        // the parts' sums in part order, through the (dead) X row: rows 3q .. 3q+2 (3 NP <= K)
         __syncthreads();
-        float2* r1 = sA0 + (size_t)K * BLK;
+        float2* r1 = sX;
         r1[(3 * part) * BLK] = as_f2(s1);
         r1[(3 * part + 1) * BLK] = as_f2(s2);
         r1[(3 * part + 2) * BLK] = as_f2(mu);
@@ -235,7 +258,7 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
 struct Shape {
     int blk, np;
 };
-constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {32, 2}, {64, 2}, {32, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 template <int S>
@@ -251,7 +274,7 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
 
 size_t transport_smem(int K, const Shape& sh) {
     return (size_t)(kMathTabDoubles + kExpTab) * sizeof(double) +
-           (size_t)transport_rows(sh.np) * K * sh.blk * sizeof(double);
+           (size_t)kTransportRows * K * sh.blk * sizeof(double);
 }
 
 struct Plan {

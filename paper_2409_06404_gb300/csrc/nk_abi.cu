@@ -328,6 +328,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
             troe_df.push_back(float4{a0.x, a0.y, b0.x, b0.y});
             troe_df.push_back(float4{e0.x, e0.y, i3.x, i3.y});
             troe_df.push_back(float4{i1.x, i1.y, t2.x, t2.y});
+            const float2 ta = split(t[0]), tb = split(1.0L - (long double)t[0]);
+            troe_df.push_back(float4{ta.x, ta.y, tb.x, tb.y});
         }
     }
 

@@ -245,19 +245,9 @@ __device__ __forceinline__ dfl exp_df_pair(dfl x, const float2* tab) {
     return df_ldexp(v, N >> 7);
 }
 
-// log(x) as a pair for a positive normal double x (others fall back to the double log):
-// x = 2^e m, j = top 7 bits of m, r = m / c_j - 1 with the pair 1/c_j, log1p(r) with r and
-// r^2/2 in pairs and the cubic tail in float, plus e ln2 and log(c_j) as pairs.  Absolute
-// error ~1e-14 for |log x| <= 10, 5e-12 at |log x| = 700.
-__device__ __forceinline__ dfl log_df(double x, const float2* rc, const float2* lc) {
-    const long long b = __double_as_longlong(x);
-    const int hi = (int)(b >> 32);
-    if (hi < 0x00100000 || hi >= 0x7ff00000) return log_df_edge(x);
-    const int e = (hi >> 20) - 1023;
-    const int j = (hi >> 13) & 127;
-    const unsigned long long mant = (unsigned long long)b & 0x000fffffffffffffULL;
-    const dfl m{__uint_as_float(0x3f800000u | (unsigned int)(mant >> 29)),
-                (float)(unsigned int)(mant & 0x1fffffffULL) * 2.220446049250313e-16f};   // * 2^-52
+// log(2^e m) for a pair m in about [1, 2) (m.h in [1, 2)) whose top 7 fraction bits are j: the
+// part of log_df after the decomposition, shared with log_df_pair
+__device__ __forceinline__ dfl log_df_tail(dfl m, int e, int j, const float2* rc, const float2* lc) {
     const float2 rcj = rc[j];
     dfl r = df_mul(m, dfl{rcj.x, rcj.y});
     r = df_add(r, dfl{-1.0f, 0.0f});
@@ -278,6 +268,32 @@ __device__ __forceinline__ dfl log_df(double x, const float2* rc, const float2* 
     const dfl el = two_sum(p, pe);
     const float2 lcj = lc[j];
     return df_add(df_add(el, dfl{lcj.x, lcj.y}), l1);
+}
+
+// log(x) as a pair for a positive normal double x (others fall back to the double log):
+// x = 2^e m, j = top 7 bits of m, r = m / c_j - 1 with the pair 1/c_j, log1p(r) with r and
+// r^2/2 in pairs and the cubic tail in float, plus e ln2 and log(c_j) as pairs.  Absolute
+// error ~1e-14 for |log x| <= 10, 5e-12 at |log x| = 700.
+__device__ __forceinline__ dfl log_df(double x, const float2* rc, const float2* lc) {
+    const long long b = __double_as_longlong(x);
+    const int hi = (int)(b >> 32);
+    if (hi < 0x00100000 || hi >= 0x7ff00000) return log_df_edge(x);
+    const int e = (hi >> 20) - 1023;
+    const int j = (hi >> 13) & 127;
+    const unsigned long long mant = (unsigned long long)b & 0x000fffffffffffffULL;
+    const dfl m{__uint_as_float(0x3f800000u | (unsigned int)(mant >> 29)),
+                (float)(unsigned int)(mant & 0x1fffffffULL) * 2.220446049250313e-16f};   // * 2^-52
+    return log_df_tail(m, e, j, rc, lc);
+}
+
+// log(x) as a pair for a pair x with x.h in [2^-126, 2^126): x = 2^e m with m = x 2^-e exact
+// (m.h in [1, 2)), then the steps of log_df.  No FP64 operation.
+__device__ __forceinline__ dfl log_df_pair(dfl x, const float2* rc, const float2* lc) {
+    const unsigned int b = __float_as_uint(x.h);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    const float s = __uint_as_float((unsigned int)(127 - e) << 23);     // 2^-e
+    const dfl m{__uint_as_float((b & 0x7fffffu) | 0x3f800000u), __fmul_rn(x.l, s)};
+    return log_df_tail(m, e, (int)((b >> 16) & 127u), rc, lc);
 }
 
 }  // namespace nk

@@ -94,6 +94,8 @@ struct __align__(16) JacTerm {
     int32_t slot, dst;
 };
 
+constexpr int kTroeDf = 4;       // float4 records per Troe reaction in DevMech::troe_df
+
 // Device view of a loaded mechanism (passed by value to every kernel).
 struct DevMech {
     int32_t K, R, P;              // species, reactions, species pairs K(K-1)/2
@@ -139,7 +141,7 @@ struct DevMech {
     // double-float tables of the FP64 rates kernel (exponent arithmetic on the FP32 pipe)
     const float2* nasa_df;        // [K][2][8] g/RT coefficients a1, -a2/2, -a3/6, -a4/12, -a5/20, a6, -a7
     const float4* rxn_df;         // [R][2] (lnA, beta) and (Ea/R, dnu, -) as pairs, device order
-    const float4* troe_df;        // [n_troe][3] (lnA0, beta0), (Ea0/R, 1/T3), (1/T1, T2) as pairs
+    const float4* troe_df;        // [n_troe][kTroeDf] (lnA0, beta0), (Ea0/R, 1/T3), (1/T1, T2), (a, 1 - a) as pairs
     const float2* grp_df;         // [groups][2][kGrpPairs] reaction thermo groups (below), pairs
     const double* grp_Tmid;       // [groups] the group's T_mid
     const int32_t* lin_boff;      // [R] first entry slot of each reaction in a stored linearization

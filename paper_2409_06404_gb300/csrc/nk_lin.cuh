@@ -4,8 +4,8 @@
 //   d ln k_f = aT tT + aM d[M]        (aM only for Troe reactions: the falloff chain)
 //   d ln K_c = D tT,  D = sum_k nu_k h_k/RT - sum_k nu_k
 // and the rate constants themselves, k_f (with the falloff factor for Troe reactions) and
-// k_r = k_f / K_c.  The exponent chains run in double-float pairs as in the FP64 rates kernel;
-// the falloff chain and its two tangents in double.
+// k_r = k_f / K_c.  The exponent chains, the falloff chain and its two tangents run in
+// double-float pairs as in the FP64 rates kernel.
 #pragma once
 
 #include "nk_rxn.cuh"
@@ -35,12 +35,8 @@ __device__ __forceinline__ RateTerms rate_terms(const DevMech& m, int r, const R
     const double sumh = df_to_d(dH);
     o.sumcp = df_to_d(dCp);
     const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
-    double shift = 0.0;
     dfl shiftd{0.0f, 0.0f};
-    if (dlnA) {
-        shift = __ldg(dlnA + x.orig);
-        shiftd = df_split(shift);
-    }
+    if (dlnA) shiftd = df_split(__ldg(dlnA + x.orig));
     const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
     const double c1 = fma(x.EaR, Q.invT, x.beta);     // d ln k_inf / (dT/T)
 
@@ -54,38 +50,17 @@ __device__ __forceinline__ RateTerms rate_terms(const DevMech& m, int r, const R
         if (M == 0.0) {
             kf = kr = aT = 0.0;
         } else {
-            const TroeRec* t = m.troe + x.aux;
-            const double beta0 = __ldg(&t->beta0), Ea0R = __ldg(&t->Ea0R);
-            const double lnk0 = fma(-Ea0R, Q.invT, fma(beta0, Q.lnT, __ldg(&t->lnA0) + shift));
-            const double c0 = fma(Ea0R, Q.invT, beta0);
-            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
-            // tangents of the chain for (tT, d[M]) = (1, 0) and (0, 1)
-            const double dPrT = c0 - c1, dPrM = 1.0 / M;
-            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
-            double Fc = (1.0 - a) * e3 + a * e1;
-            double dFcT = -((1.0 - a) * i3 * e3 + a * i1 * e1) * Q.P.T;
-            if (__ldg(&t->hasT2) != 0.0) {
-                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
-                Fc += e2;
-                dFcT = fma(T2 * Q.invT, e2, dFcT);
-            }
-            const double lFc = dlog_df(Fc, dt) * kInvLn10, dlFcT = dFcT / Fc * kInvLn10;
-            const double c = fma(-0.67, lFc, -0.4), nn = fma(-1.27, lFc, 0.75);
-            const double u = fma(lnPr, kInvLn10, c);
-            const double duT = fma(dPrT, kInvLn10, -0.67 * dlFcT), duM = dPrM * kInvLn10;
-            const double v = fma(-0.14, u, nn);
-            const double dvT = fma(-0.14, duT, -1.27 * dlFcT), dvM = -0.14 * duM;
-            const double f1 = u / v;
-            const double df1T = fma(-f1, dvT, duT) / v, df1M = fma(-f1, dvM, duM) / v;
-            const double den = fma(f1, f1, 1.0);
-            const double lF = lFc / den;
-            const double dlFT = fma(-2.0 * lF * f1, df1T, dlFcT) / den, dlFM = -2.0 * lF * f1 * df1M / den;
-            const double g = 1.0 / (1.0 + dexp_df(-lnPr, dt));       // P_r / (1 + P_r)
-            kf = exp_df_d(lnkf, dt.e2) * g * dexp_df(lF * kLn10, dt);
-            kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
-            aT = c1 + dPrT * (1.0 - g) + kLn10 * dlFT;
-            aM = dPrM * (1.0 - g) + kLn10 * dlFM;
+            // the falloff chain in pairs: ln F, and d ln k_f = (c1 + Px (c0 - c1) + PL LT) dT/T + (Px/[M]) d[M]
+            const dfl Mp = df_split(M);
+            dfl c0;
+            const dfl lnPr = troe_lnPr(m, x.aux, Q.P, lnkf, shiftd, dlnA != nullptr, Mp, dt, &c0);
+            const TroeCent c = troe_cent(m, x.aux, Q.P, dt);
+            const TroeLog f = troe_log(lnPr, c.L, dt);
+            const dfl lnkF = df_add(lnkf, f.lnF), c1d = arrh_slope_df(m, r, Q.P);
+            kf = exp_df_d(lnkF, dt.e2);
+            kr = exp_df_d(df_add(lnkF, df_neg(lnKc)), dt.e2);
+            aT = df_to_d(df_add(df_fma(f.Px, df_add(c0, df_neg(c1d)), c1d), df_mul(f.PL, c.LT)));
+            aM = df_to_d(df_div(f.Px, Mp));
         }
     } else {
         kf = exp_df_d(lnkf, dt.e2);

@@ -160,6 +160,103 @@ __device__ __forceinline__ dfl ln_kf_df(const DevMech& m, int r, const TPairs& P
     return shifted ? df_add(l, shift) : l;
 }
 
+// c = beta + (Ea/R)/T = T d ln k / dT of reaction r (device order) as a pair
+__device__ __forceinline__ dfl arrh_slope_df(const DevMech& m, int r, const TPairs& P) {
+    const float4 a0 = __ldg(m.rxn_df + 2 * r), a1 = __ldg(m.rxn_df + 2 * r + 1);
+    return df_fma(dfl{a1.x, a1.y}, P.invTd, dfl{a0.z, a0.w});
+}
+
+// ---------------------------------------------------------------- Troe falloff in pairs
+// ln x for a pair x > 0: the pair logarithm for x.h in [2^-100, 2^100), the double log out of
+// line otherwise (concentrations and falloff centres that small or large do not occur in the
+// workloads; the edge keeps the result defined)
+static __device__ __noinline__ dfl log_pair_edge(float h, float l) { return df_split_cvt(log((double)h + (double)l)); }
+__device__ __forceinline__ dfl log_pos_pair(dfl x, const DfTab& dt) {
+    if (!(x.h >= 7.888609052210118e-31f && x.h < 1.2676506002282294e30f)) return log_pair_edge(x.h, x.l);
+    return log_df_pair(x, dt.rc, dt.lc);
+}
+
+// L = log10 F_cent and LT = T dL/dT of a Troe reaction, with
+//   F_cent = (1 - a) exp(-T/T3) + a exp(-T/T1) + exp(-T2/T)     (the last term when T2 > 0),
+//   T dF_cent/dT = -(1 - a)(T/T3) exp(-T/T3) - a (T/T1) exp(-T/T1) + (T2/T) exp(-T2/T),
+// in pairs (terms below the float range drop out; an F_cent below 2^-100 takes the double
+// edge path out of line).
+struct TroeCent {
+    dfl L, LT;
+};
+static __device__ __noinline__ TroeCent troe_cent_edge(const TroeRec* t, double T) {
+    const double a = t->a, x3 = T * t->invT3, x1 = T * t->invT1, x2 = t->hasT2 != 0.0 ? t->T2 / T : 0.0;
+    const double e3 = (1.0 - a) * exp(-x3), e1 = a * exp(-x1), e2 = t->hasT2 != 0.0 ? exp(-x2) : 0.0;
+    const double Fc = e3 + e1 + e2, FT = e2 * x2 - e3 * x3 - e1 * x1;
+    return TroeCent{df_split_cvt(log10(Fc)), df_split_cvt(FT / (Fc * 2.302585092994046))};
+}
+__device__ __forceinline__ TroeCent troe_cent(const DevMech& m, int aux, const TPairs& P, const DfTab& dt) {
+    const float4 t1 = __ldg(m.troe_df + kTroeDf * aux + 1);    // (Ea0/R, 1/T3)
+    const float4 t2 = __ldg(m.troe_df + kTroeDf * aux + 2);    // (1/T1, T2)
+    const float4 t3 = __ldg(m.troe_df + kTroeDf * aux + 3);    // (a, 1 - a)
+    const dfl x3 = df_mul(P.Td, dfl{t1.z, t1.w}), x1 = df_mul(P.Td, dfl{t2.x, t2.y});
+    const dfl e3 = df_mul(dfl{t3.z, t3.w}, exp_df_pair(df_neg(x3), dt.e2));
+    const dfl e1 = df_mul(dfl{t3.x, t3.y}, exp_df_pair(df_neg(x1), dt.e2));
+    dfl Fc = df_add(e3, e1);
+    dfl FT = df_neg(df_fma(e3, x3, df_mul(e1, x1)));
+    if (t2.z != 0.0f) {
+        const dfl x2 = df_mul(dfl{t2.z, t2.w}, P.invTd);
+        const dfl e2 = exp_df_pair(df_neg(x2), dt.e2);
+        Fc = df_add(Fc, e2);
+        FT = df_fma(e2, x2, FT);
+    }
+    if (!(Fc.h >= 7.888609052210118e-31f)) return troe_cent_edge(m.troe + aux, P.T);
+    return TroeCent{df_mul(log_df_pair(Fc, dt.rc, dt.lc), dfc_invln10()), df_mul(df_div(FT, Fc), dfc_invln10())};
+}
+
+// The Troe falloff factor in logarithmic form: for x = ln P_r and L = log10 F_cent,
+//   u = x/ln10 - 0.4 - 0.67 L,  v = 0.75 - 1.27 L - 0.14 u,  f1 = u/v,
+//   log10 F_T = L/(1 + f1^2),  ln F = ln(P_r/(1 + P_r)) + ln10 log10 F_T,
+// and its partial derivatives Px = d ln F/dx = 1/(1 + P_r) + ln10 d log10 F_T/dx and
+// PL = d ln F/dL = ln10 d log10 F_T/dL, from
+//   d f1 = (du - f1 dv)/v,  d log10 F_T = (dL - 2 log10 F_T f1 d f1)/(1 + f1^2)
+// with du/dx = 1/ln10, dv/dx = -0.14/ln10, du/dL = -0.67, dv/dL = -1.27 + 0.14 * 0.67.
+// ln(P_r/(1 + P_r)) = -log(1 + e^-x) for x >= 0 and x - log(1 + e^x) below, from z = e^-|x|
+// (z underflows to 0 past |x| = 87, dropping terms below 2^-125).  All in pairs.
+struct TroeLog {
+    dfl lnF, Px, PL;
+};
+__device__ __forceinline__ TroeLog troe_log(dfl x, dfl L, const DfTab& dt) {
+    const dfl one{1.0f, 0.0f};
+    const dfl u = df_add(df_fma(L, dfc_m0_67(), dfc_m0_4()), df_mul(x, dfc_invln10()));
+    const dfl v = df_fma(u, dfc_m0_14(), df_fma(L, dfc_m1_27(), dfl{0.75f, 0.0f}));
+    const dfl iv = df_div(one, v);
+    const dfl f1 = df_mul(u, iv);
+    const dfl iden = df_div(one, df_fma(f1, f1, one));
+    const dfl lF = df_mul(L, iden);
+    const dfl t = df_mul(df_mul(lF, f1), dfl{-2.0f, 0.0f});                              // -2 log10 F_T f1
+    const dfl f1x = df_mul(df_mul(df_fma(f1, df_neg(dfc_m0_14()), one), iv), dfc_invln10());
+    const dfl f1L = df_mul(df_fma(f1, dfl{1.17620003223419189453125f, -3.2234190427971043e-08f}, dfc_m0_67()), iv);
+    const bool neg = x.h < 0.0f;
+    const dfl z = exp_df_pair(neg ? x : df_neg(x), dt.e2);
+    const dfl opz = df_add(one, z);
+    const dfl s = log_df_pair(opz, dt.rc, dt.lc);
+    TroeLog o;
+    o.lnF = df_fma(lF, dfc_ln10(), neg ? df_add(x, df_neg(s)) : df_neg(s));
+    o.Px = df_fma(df_mul(df_mul(t, f1x), iden), dfc_ln10(), df_div(neg ? one : z, opz));
+    o.PL = df_mul(df_mul(df_fma(t, f1L, one), iden), dfc_ln10());
+    return o;
+}
+
+// ln P_r = ln k_0 - ln k_inf + ln [M] of Troe reaction r (aux its Troe row) as a pair, with
+// ln k_0 = ln A_0 + beta_0 ln T - (Ea_0/R)/T (+ the caller's shift of ln A) and the pair ln k_inf
+// (which carries the same shift), for [M] > 0 as a pair; c0 = beta_0 + (Ea_0/R)/T.
+__device__ __forceinline__ dfl troe_lnPr(const DevMech& m, int aux, const TPairs& P, dfl lnkinf, dfl shift,
+                                         bool shifted, dfl Mp, const DfTab& dt, dfl* c0) {
+    const float4 t0 = __ldg(m.troe_df + kTroeDf * aux);        // (lnA0, beta0)
+    const float4 t1 = __ldg(m.troe_df + kTroeDf * aux + 1);    // (Ea0/R, 1/T3)
+    dfl lnk0 = df_fma(dfl{t0.z, t0.w}, P.lnTd, dfl{t0.x, t0.y});
+    lnk0 = df_fma(dfl{-t1.x, -t1.y}, P.invTd, lnk0);
+    if (shifted) lnk0 = df_add(lnk0, shift);
+    if (c0) *c0 = df_fma(dfl{t1.x, t1.y}, P.invTd, dfl{t0.z, t0.w});
+    return df_add(df_add(lnk0, df_neg(lnkinf)), log_pos_pair(Mp, dt));
+}
+
 // sum_k nu_k of reaction r (device order) as a float, from the pair record (converting the
 // double in the reaction record would take an F2F instruction on the FP64 pipe per reaction)
 __device__ __forceinline__ float dnu_f(const DevMech& m, int r) {
