@@ -225,14 +225,21 @@ __device__ __forceinline__ void vjp_reaction(const DevMech& m, int r, const doub
 
 // The logarithmic form (tiles whose mass fractions are all within 2^+-100; see the kernel).  The C_k
 // row holds ln C_k as pairs; with F the falloff factor (1 but for Troe reactions)
-//   q_f = F exp(ln k_f + sum_reac nu ln C),  q_r = F exp(ln k_f - ln K_c + sum_prod nu ln C),
-// so d q_c / d ln C_k = nu (q_f or -q_r), d q_c / d ln k_f = q_c and d q_c / d ln K_c = q_r.  The
-// species rows accumulate S_k = Cbar_k C_k (the cotangent of ln C_k), turned into Cbar_k = S_k/C_k
-// once per point at the end; the third-body terms Mbar (eps - 1) enter as Mbar (eps - 1) C_k.
+//   q_f = exp(ln k_f + ln F + sum_reac nu ln C),  q_r = exp(ln k_f + ln F - ln K_c + sum_prod nu ln C),
+// so d q_c / d ln C_k = nu (q_f or -q_r), d q_c / d (ln k_f + ln F) = q_c and d q_c / d ln K_c = q_r.
+// The species rows accumulate S_k = Cbar_k C_k (the cotangent of ln C_k), turned into
+// Cbar_k = S_k/C_k once per point at the end; the third-body terms Mbar (eps - 1) enter as
+// Mbar (eps - 1) C_k.  The temperature cotangent is accumulated times T (TbarT), term by term:
+// Lbar kT through ln k_f + ln F (Lbar = qcbar q_c; kT = T d(ln k_f + ln F)/dT at fixed [M], which
+// is c1 = beta + Ea/(RT) but for Troe reactions), qcbar q_r (sum nu h/RT - sum nu) through ln K_c,
+// -Mbar p/(RT) through sum_k C_k and -bar_hrr R T q sum nu c_p/R through h_k.  The falloff chain
+// runs in pairs (troe_log).
+// Returns this point's term qbar_r q_r of the ln A gradient (0 without WANT_G); the caller sums
+// it over the warp.
 template <int KIND, bool WANT_G, bool HB>
-__device__ __forceinline__ void vjp_reaction_log(const DevMech& m, int r, const float2* sL, const double* sWb,
-                                                 double* sS, double* gw, const VjpPoint& Q, const double* dlnA,
-                                                 const DfTab& dt, double& Tbar) {
+__device__ __forceinline__ double vjp_reaction_log(const DevMech& m, int r, const float2* sL, const double* sWb,
+                                                   double* sS, const VjpPoint& Q, const double* dlnA,
+                                                   const DfTab& dt, double& TbarT) {
     constexpr int BLK = kVjpBlk;
     const Rxn x = load_rxn(m.rxn + r);
     const double wsum = gather_side<BLK>(x.sp, x.nud, x.nr, sWb) +
@@ -241,74 +248,48 @@ __device__ __forceinline__ void vjp_reaction_log(const DevMech& m, int r, const 
     const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
     dfl dG, dH, dCp;
     rxn_thermo<true, HB>(m, x.thermo, Q.P, dG, dH, dCp);
-    const double sumh = df_to_d(dH);
-    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu_f(m, r)), df_neg(dG));
-    double shift = 0.0;
+    const float dnu = dnu_f(m, r);
+    const dfl lnKc = df_add(df_mul_f(Q.P.lnP0RTd, dnu), df_neg(dG));
     dfl shiftd{0.0f, 0.0f};
-    if (dlnA) {
-        shift = __ldg(dlnA + x.orig);
-        shiftd = df_split(shift);
-    }
+    if (dlnA) shiftd = df_split(__ldg(dlnA + x.orig));
     const dfl lnkf = ln_kf_df(m, r, Q.P, shiftd, dlnA != nullptr);
-    double M = 0.0;
+    const dfl c1 = arrh_slope_df(m, r, Q.P);
+    dfl Mp{0.0f, 0.0f};
     if (KIND != 0) {
-        dfl Mp = Q.pRTd;
+        Mp = Q.pRTd;
         for (int j = x.eff0; j < x.eff1; ++j)
             Mp = df_fma(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[__ldg(m.eff_sp + j) * BLK]), dt.e2), Mp);
-        M = df_to_d(Mp);
     }
 
-    // ---- primal
-    double F = 1.0;
-    double tr_g = 0.0, tr_lF = 0.0, tr_f1 = 0.0, tr_den = 1.0, tr_u = 0.0, tr_v = 1.0, tr_nn = 0.0, tr_Fc = 1.0,
-           tr_dFc = 0.0;
-    const TroeRec* t = nullptr;
+    // ---- primal; for Troe reactions ln F and the coefficients of its adjoint in pairs:
+    //   kT = c1 + Px (c0 - c1) + PL LT (T d(ln k_f + ln F)/dT at fixed [M]), kM = Px/[M]
+    dfl lnkF = lnkf, kT = c1, kM{0.0f, 0.0f};
+    bool noF = false;
     if constexpr (KIND == 2) {
-        t = m.troe + x.aux;
-        if (M == 0.0) {
-            F = 0.0;
+        if (Mp.h == 0.0f) {
+            noF = true;
         } else {
-            const double lnk0 = fma(-__ldg(&t->Ea0R), Q.invT, fma(__ldg(&t->beta0), Q.lnT, __ldg(&t->lnA0) + shift));
-            const double lnPr = lnk0 - df_to_d(lnkf) + dlog_df(M, dt);
-            const double a = __ldg(&t->a), i3 = __ldg(&t->invT3), i1 = __ldg(&t->invT1);
-            const double e3 = dexp_df(-Q.P.T * i3, dt), e1 = dexp_df(-Q.P.T * i1, dt);
-            tr_Fc = (1.0 - a) * e3 + a * e1;
-            tr_dFc = -((1.0 - a) * i3 * e3 + a * i1 * e1);
-            if (__ldg(&t->hasT2) != 0.0) {
-                const double T2 = __ldg(&t->T2), e2 = dexp_df(-T2 * Q.invT, dt);
-                tr_Fc += e2;
-                tr_dFc = fma(T2 * Q.invT * Q.invT, e2, tr_dFc);
-            }
-            const double lFc = dlog_df(tr_Fc, dt) * kInvLn10;
-            const double c = fma(-0.67, lFc, -0.4);
-            tr_nn = fma(-1.27, lFc, 0.75);
-            tr_u = fma(lnPr, kInvLn10, c);
-            tr_v = fma(-0.14, tr_u, tr_nn);
-            tr_f1 = tr_u / tr_v;
-            tr_den = fma(tr_f1, tr_f1, 1.0);
-            tr_lF = lFc / tr_den;
-            tr_g = 1.0 / (1.0 + dexp_df(-lnPr, dt));
-            F = tr_g * dexp_df(tr_lF * kLn10, dt);
+            dfl c0;
+            const dfl lnPr = troe_lnPr(m, x.aux, Q.P, lnkf, shiftd, dlnA != nullptr, Mp, dt, &c0);
+            const TroeCent c = troe_cent(m, x.aux, Q.P, dt);
+            const TroeLog f = troe_log(lnPr, c.L, dt);
+            lnkF = df_add(lnkf, f.lnF);
+            kT = df_add(df_fma(f.Px, df_add(c0, df_neg(c1)), c1), df_mul(f.PL, c.LT));
+            kM = df_div(f.Px, Mp);
         }
     }
-    double qf = exp_df_d(df_add(lnkf, sf), dt.e2);
-    double qr = exp_df_d(df_add(df_add(lnkf, df_neg(lnKc)), sb), dt.e2);
-    if constexpr (KIND == 2) {
-        qf *= F;
-        qr *= F;
-    }
+    double qf = exp_df_d(df_add(lnkF, sf), dt.e2);
+    double qr = exp_df_d(df_add(df_add(lnkF, df_neg(lnKc)), sb), dt.e2);
+    if (KIND == 2 && noF) qf = qr = 0.0;
     const double qc = qf - qr;
+    double M = 0.0;
+    if (KIND == 1) M = df_to_d(Mp);
     const double q = KIND == 1 ? qc * M : qc;
 
     // ---- adjoint
-    const double qbar = HB ? fma(-Q.hbRT, sumh, wsum) : wsum;   // sum nu (bar_omega - bar_hrr h)
-    if (HB) Tbar = fma(-Q.hb * kR * q, df_to_d(dCp), Tbar);
-    if (WANT_G) {
-        double gl = Q.valid ? qbar * q : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gl += __shfl_xor_sync(0xffffffffu, gl, o);
-        if ((threadIdx.x & 31) == 0) gw[r] += gl;
-    }
+    const double qbar = HB ? fma(-Q.hbRT, df_to_d(dH), wsum) : wsum;   // sum nu (bar_omega - bar_hrr h)
+    if (HB) TbarT = fma(-Q.hbRT * q, df_to_d(dCp), TbarT);
+    const double gl = WANT_G && Q.valid ? qbar * q : 0.0;
     double Mbar = 0.0, qcbar = qbar;
     if (KIND == 1) {
         qcbar = qbar * M;
@@ -317,41 +298,70 @@ __device__ __forceinline__ void vjp_reaction_log(const DevMech& m, int r, const 
     // S_k += nu_k (q_f or -q_r) qcbar: with the signed coefficients nud (-nu for reactants)
     scatter_side<BLK>(x.sp, x.nud, x.nr, sS, -qcbar * qf);
     scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sS, -qcbar * qr);
-    const double lnKcbar = qcbar * qr;
-    Tbar = fma(lnKcbar * Q.invT, sumh - x.dnu, Tbar);           // through g_k/RT(T) and ln(p0/RT)
-    const double Lbar = qcbar * qc;                              // cotangent of ln k_f (with the falloff)
-    if constexpr (KIND == 2) {
-        if (M != 0.0) {
-            const double lnf = fma(__ldg(&t->Ea0R), Q.invT, __ldg(&t->beta0)) * Q.invT;
-            const double dlF_du = -2.0 * tr_lF * tr_f1 * (tr_nn / (tr_v * tr_v)) / tr_den;
-            const double df1_dlFc = fma(1.1762, tr_u, -0.67 * tr_v) / (tr_v * tr_v);
-            const double dlF_dlFc = (1.0 - 2.0 * tr_lF * tr_f1 * df1_dlFc) / tr_den;
-            const double lnPrbar = Lbar * (1.0 - tr_g + dlF_du);
-            const double lnkinfbar = Lbar - lnPrbar;
-            Mbar = fma(lnPrbar, 1.0 / M, Mbar);
-            Tbar = fma(Lbar * dlF_dlFc, tr_dFc / tr_Fc, Tbar);
-            Tbar = fma(lnPrbar, lnf, Tbar);
-            Tbar = fma(lnkinfbar, fma(x.EaR, Q.invT, x.beta) * Q.invT, Tbar);
-        }
-    } else {
-        Tbar = fma(Lbar, fma(x.EaR, Q.invT, x.beta) * Q.invT, Tbar);
-    }
+    // through ln K_c (g_k/RT(T) and ln(p0/RT)) and through ln k_f + ln F
+    const double Lbar = qcbar * qc;
+    TbarT = fma(qcbar * qr, df_to_d(df_add(dH, dfl{-dnu, 0.0f})), TbarT);
+    TbarT = fma(Lbar, df_to_d(kT), TbarT);
+    if constexpr (KIND == 2) Mbar = Lbar * df_to_d(kM);
     if (KIND != 0 && Mbar != 0.0) {
-        Tbar = fma(-Mbar * Q.pRT, Q.invT, Tbar);                 // sum_k C_k = p/(RT)
+        TbarT = fma(-Mbar, Q.pRT, TbarT);                       // sum_k C_k = p/(RT)
         for (int j = x.eff0; j < x.eff1; ++j) {
             const int k = __ldg(m.eff_sp + j);
             double* b = sS + k * BLK;
-            *b = fma(Mbar * __ldg(m.eff_m1 + j), exp_df_d(dfl_of(sL[k * BLK]), dt.e2), *b);
+            const dfl ec = df_mul(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[k * BLK]), dt.e2));
+            *b = fma(Mbar, df_to_d(ec), *b);
         }
     }
+    return gl;
 }
 
+// gw[j] += the warp sum of a_j for the first nv of four consecutive reactions: one transposed
+// butterfly (the lanes trade halves of the four values, then of the two left, then reduce
+// within groups of eight), so lane 8 j ends with the sum of a_j.  Every sum is the same
+// pairwise tree as a butterfly all-reduce of a_j alone (bit-identical), at 7 FP64 additions for
+// the four instead of 24.
+__device__ __forceinline__ void warp_sum4_add(double* gw, double a0, double a1, double a2, double a3, int nv) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool hi = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    double k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
+    const double s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
+    k0 += __shfl_xor_sync(kAll, s0, 16);
+    k1 += __shfl_xor_sync(kAll, s1, 16);
+    double k = b3 ? k1 : k0;
+    k += __shfl_xor_sync(kAll, b3 ? k0 : k1, 8);
+    k += __shfl_xor_sync(kAll, k, 4);
+    k += __shfl_xor_sync(kAll, k, 2);
+    k += __shfl_xor_sync(kAll, k, 1);
+    const int j = lane >> 3;
+    if ((lane & 7) == 0 && j < nv) gw[j] += k;
+}
+
+// The ln A gradient terms of consecutive reactions are held in threes and summed over the warp
+// four at a time (warp_sum4_add); the slice's last one to three go out with the remaining slots
+// zero.
 template <int KIND, bool WANT_G, bool HB>
 __device__ __forceinline__ void vjp_group_log(const DevMech& m, int r0, int r1, const double* sC, const double* sWb,
                                               double* sB, double* gw, const VjpPoint& Q, const double* dlnA,
                                               const DfTab& dt, double& Tbar) {
     const float2* sL = reinterpret_cast<const float2*>(sC);
-    for (int r = r0; r < r1; ++r) vjp_reaction_log<KIND, WANT_G, HB>(m, r, sL, sWb, sB, gw, Q, dlnA, dt, Tbar);
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    int nb = 0;                                                   // terms held (warp-uniform)
+    for (int r = r0; r < r1; ++r) {
+        const double g = vjp_reaction_log<KIND, WANT_G, HB>(m, r, sL, sWb, sB, Q, dlnA, dt, Tbar);
+        if (WANT_G) {
+            if (nb == 3) {
+                warp_sum4_add(gw + r - 3, g0, g1, g2, g, 4);
+                nb = 0;
+            } else {
+                if (nb == 0) g0 = g;
+                else if (nb == 1) g1 = g;
+                else g2 = g;
+                ++nb;
+            }
+        }
+    }
+    if (WANT_G && nb > 0) warp_sum4_add(gw + r1 - nb, g0, nb > 1 ? g1 : 0.0, nb > 2 ? g2 : 0.0, 0.0, nb);
 }
 
 template <int KIND, bool WANT_G, bool HB>
@@ -440,6 +450,7 @@ __global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, cons
             vjp_group_log<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
             vjp_group_log<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
             vjp_group_log<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            Tbar *= Q.invT;                                       // the logarithmic form sums T Tbar
         }
         __syncthreads();
 
