@@ -17,8 +17,8 @@
 // enthalpy sums, ln K_c) in double-float pairs on the FP32 pipe, concentrations, their
 // products and every tangent in double.  The falloff chain runs in double with pair-based
 // exp/log.  Layout as the rates kernel: NP warps per point share C_k and dC_k in shared
-// memory, each accumulates its own d omega_k (and omega_k when asked for) partials, added in
-// part order.
+// memory and its d omega_k (and omega_k when asked for) rows, into which they scatter in rounds
+// of reactions that share no species (for_rounds): every sum in an order fixed by the schedule.
 #pragma once
 
 #include <mutex>
@@ -283,14 +283,32 @@ __device__ __forceinline__ void jvp_group(const DevMech& m, int r0, int r1, cons
     for (int r = r0; r < r1; ++r) jvp_reaction<BLK, KIND, OMEGA, RHS>(m, r, sC, sdC, sW, sD, Q, dlnA, dt, acc);
 }
 
-// Per-point species rows: C_k, dC_k, then NP rows of d omega_k partials and, with OMEGA, NP
-// rows of omega_k partials.
-__host__ __device__ constexpr int jvp_rows(int np, bool omega) { return 2 + np * (omega ? 2 : 1); }
+// The reactions of one kind for NP > 1 parts per point, round by round (for_rounds): the parts'
+// reactions of a round share no species, so all scatter into the point's one d omega_k (and
+// omega_k) row.
+template <int BLK, int NP, int KIND, bool OMEGA, bool RHS>
+__device__ __forceinline__ void jvp_rounds(const DevMech& m, int part, bool direct, const double* sC,
+                                           const double* sdC, double* sW, double* sD, const JvpPoint& Q,
+                                           const double* dlnA, const DfTab& dt, JvpAcc& acc) {
+    if (direct) {
+        for_rounds<NP>(m, KIND, part,
+                       [&](int r) { jvp_reaction<BLK, KIND, OMEGA, RHS>(m, r, sC, sdC, sW, sD, Q, dlnA, dt, acc); });
+    } else {
+        const float2* sL = reinterpret_cast<const float2*>(sC);
+        const float2* sR = reinterpret_cast<const float2*>(sdC);
+        for_rounds<NP>(m, KIND, part, [&](int r) {
+            jvp_reaction_log<BLK, KIND, OMEGA, RHS>(m, r, sL, sR, sW, sD, Q, dlnA, dt, acc);
+        });
+    }
+}
+
+// Per-point species rows: C_k, dC_k, the d omega_k row and, with OMEGA, the omega_k row.
+__host__ __device__ constexpr int jvp_rows(bool omega) { return omega ? 4 : 3; }
 
 // RHS: the JVP of the implicit-stage sources (omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p)
 // and their tangents in d_omega, d_hrr).
 template <int BLK, int NP, bool OMEGA, bool RHS>
-__global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const int64_t n, const int64_t ld,
+__global__ void __launch_bounds__(BLK * NP, 512 / (BLK * NP)) jvp_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                        const double* __restrict__ T, const double* __restrict__ p,
                                                        const double* __restrict__ Y, const double* __restrict__ dlnA,
                                                        const double* __restrict__ vT, const double* __restrict__ vY,
@@ -308,10 +326,10 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
     double* base = smem + kMathTabDoubles + slot;
     double* sC = base;                                   // C_k
     double* sdC = base + (size_t)K * BLK;                // dC_k
-    double* sD0 = base + (size_t)2 * K * BLK;            // d omega_k partials, part q at row q
-    double* sW0 = base + (size_t)(2 + NP) * K * BLK;     // omega_k partials (OMEGA)
-    double* sD = sD0 + (size_t)part * K * BLK;
-    double* sW = sW0 + (size_t)part * K * BLK;
+    double* sD0 = base + (size_t)2 * K * BLK;            // d omega_k
+    double* sW0 = base + (size_t)3 * K * BLK;            // omega_k (OMEGA)
+    double* sD = sD0;
+    double* sW = sW0;
 
     JvpPoint Q;
     const double Ti = T[i];
@@ -364,31 +382,30 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
             reinterpret_cast<float2*>(sdC)[k * BLK] = make_float2(rk.h, rk.l);
         }
     }
-    for (int k = 0; k < K; ++k) {
+    for (int k = part; k < K; k += NP) {
         sD[k * BLK] = 0.0;
         if (OMEGA) sW[k * BLK] = 0.0;
     }
     if (NP > 1) __syncthreads();
 
     JvpAcc acc;
-    int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    if (direct) {
-        slice<NP>(0, e1, part, a, b);
-        jvp_group<BLK, 0, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
-        slice<NP>(e1, t1, part, a, b);
-        jvp_group<BLK, 1, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
-        slice<NP>(t1, m.R, part, a, b);
-        jvp_group<BLK, 2, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+    if constexpr (NP == 1) {
+        if (direct) {
+            jvp_group<BLK, 0, OMEGA, RHS>(m, 0, e1, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+            jvp_group<BLK, 1, OMEGA, RHS>(m, e1, t1, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+            jvp_group<BLK, 2, OMEGA, RHS>(m, t1, m.R, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        } else {
+            jvp_group_log<BLK, 0, OMEGA, RHS>(m, 0, e1, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+            jvp_group_log<BLK, 1, OMEGA, RHS>(m, e1, t1, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+            jvp_group_log<BLK, 2, OMEGA, RHS>(m, t1, m.R, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        }
     } else {
-        slice<NP>(0, e1, part, a, b);
-        jvp_group_log<BLK, 0, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
-        slice<NP>(e1, t1, part, a, b);
-        jvp_group_log<BLK, 1, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
-        slice<NP>(t1, m.R, part, a, b);
-        jvp_group_log<BLK, 2, OMEGA, RHS>(m, a, b, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        // (each round ends with a barrier: the rows are complete after the last one)
+        jvp_rounds<BLK, NP, 0, OMEGA, RHS>(m, part, direct, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        jvp_rounds<BLK, NP, 1, OMEGA, RHS>(m, part, direct, sC, sdC, sW, sD, Q, dlnA, dt, acc);
+        jvp_rounds<BLK, NP, 2, OMEGA, RHS>(m, part, direct, sC, sdC, sW, sD, Q, dlnA, dt, acc);
     }
-    if (NP > 1) __syncthreads();
 
     // Implicit-stage sources (RHS): fY_k = W_k omega_k / rho, fT = hrr / (rho c_p) with
     // c_p = R sum_k Y_k/W_k c_p,k/R; tangents dfY_k = W_k (d omega_k - omega_k d rho/rho) / rho
@@ -397,14 +414,8 @@ __global__ void __launch_bounds__(BLK * NP) jvp_kernel(const DevMech m, const in
     if constexpr (RHS) inv_rho = 1.0 / rho;
     for (int k = part; k < K; k += NP) {
         double dw = sD0[k * BLK];
-#pragma unroll
-        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
         double w = 0.0;
-        if constexpr (OMEGA) {
-            w = sW0[k * BLK];
-#pragma unroll
-            for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
-        }
+        if constexpr (OMEGA) w = sW0[k * BLK];
         if constexpr (RHS) {
             const double* c = nasa_range(m, k, Ti);
             const double iw = __ldg(m.invW + k), cpk = nasa_cpR(c, Ti);
@@ -482,7 +493,7 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
 }
 
 size_t jvp_smem(int K, const Shape& sh, bool omega) {
-    return (size_t)kMathTabDoubles * sizeof(double) + (size_t)jvp_rows(sh.np, omega) * K * sh.blk * sizeof(double);
+    return (size_t)kMathTabDoubles * sizeof(double) + (size_t)jvp_rows(omega) * K * sh.blk * sizeof(double);
 }
 
 struct Plan {

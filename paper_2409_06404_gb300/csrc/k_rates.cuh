@@ -382,10 +382,10 @@ __device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, co
         return rate_of_progress<BLK, KIND>(m, x, sC, sG, P, dlnA, mt);
 }
 
-// Reactions [r0, r1) of one kind, scattered in reaction order.  (Unrolling by two or four
-// reactions per iteration measured slower once several warps share a point.)  direct: the
-// block's products in double (a negative concentration); else the logarithmic form (kDF and
-// kMixed; the native form always takes its own).
+// Reactions [r0, r1) of one kind, scattered in reaction order (one part per point).
+// (Unrolling by two or four reactions per iteration measured slower once several warps share a
+// point.)  direct: the block's products in double (a negative concentration); else the
+// logarithmic form (kDF and kMixed; the native form always takes its own).
 template <int BLK, int PREC, int KIND>
 __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1, const double* sC, const double* sG,
                                                double* sW, const Conc& cs, bool direct, const Pt& P,
@@ -403,21 +403,40 @@ __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1,
     }
 }
 
-// Per-point species arrays: C_k, then g_k/RT (native form only), then NP rows of omega_k
-// partials.
+// The reactions of one kind for NP > 1 parts per point, round by round (for_rounds): the parts'
+// reactions of a round share no species, so all scatter into the point's one omega_k row.
+template <int BLK, int NP, int PREC, int KIND>
+__device__ __forceinline__ void reaction_rounds(const DevMech& m, int part, const double* sC, const double* sG,
+                                                double* sW, const Conc& cs, bool direct, const Pt& P,
+                                                const double* dlnA, const MathTab& mt, const DfTab& dt) {
+    if (PREC == kNative || direct) {
+        for_rounds<NP>(m, KIND, part, [&](int r) {
+            const Rxn a = load_rxn(m.rxn + r);
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, false>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
+        });
+    } else {
+        for_rounds<NP>(m, KIND, part, [&](int r) {
+            const Rxn a = load_rxn(m.rxn + r);
+            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, true>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
+        });
+    }
+}
+
+// Per-point species arrays: C_k, then g_k/RT (native form only), then the omega_k row.
 template <int PREC>
 __host__ __device__ constexpr int shared_rows() {
     return PREC == kNative ? 2 : 1;
 }
 
 // BLK points per block, NP parts (warps) per point: thread (part, slot) works on point
-// blockIdx.x * BLK + slot.  The parts of a point share its C_k (and g_k/RT), each walks its
-// own slice of every kind and accumulates into its own omega_k partials; the partials are
-// added in part order, so results do not depend on scheduling.
+// blockIdx.x * BLK + slot.  The parts of a point share its C_k (and g_k/RT) and its omega_k row;
+// they take the reactions in rounds whose reactions share no species (for_rounds), so every
+// omega_k is summed in an order fixed by the mechanism's schedule, whatever the scheduling of
+// the warps.
 //
 // RHS: write the implicit-stage sources instead: omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p).
 template <int BLK, int NP, int PREC, bool RHS>
-__global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
+__global__ void __launch_bounds__(BLK * NP, 640 / (BLK * NP)) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                          const double* __restrict__ T, const double* __restrict__ p,
                                                          const double* __restrict__ Y,
                                                          const double* __restrict__ dlnA,
@@ -439,7 +458,7 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     double* sC = smem + kMathTabDoubles + slot;                       // C_k       at sC[k * BLK]
     double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (native form)
     double* sW0 = smem + kMathTabDoubles + (size_t)shared_rows<PREC>() * K * BLK + slot;
-    double* sW = sW0 + (size_t)part * K * BLK;                        // this part's omega_k partials
+    double* sW = sW0;                                                  // omega_k
 
     Pt P;
     P.T = T[i];
@@ -473,7 +492,7 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
             reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
         }
     }
-    for (int k = 0; k < K; ++k) sW[k * BLK] = 0.0;
+    for (int k = part; k < K; k += NP) sW[k * BLK] = 0.0;
     bool direct = false;
     if constexpr (NP > 1) {
         if constexpr (PREC == kNative)
@@ -484,15 +503,17 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
         direct = __any_sync(__activemask(), neg);
     }
 
-    int a, b;
-    const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    slice<NP>(0, e1, part, a, b);
-    reaction_group<BLK, PREC, 0>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-    slice<NP>(e1, t1, part, a, b);
-    reaction_group<BLK, PREC, 1>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-    slice<NP>(t1, m.R, part, a, b);
-    reaction_group<BLK, PREC, 2>(m, a, b, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-    if (NP > 1) __syncthreads();
+    if constexpr (NP == 1) {
+        const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
+        reaction_group<BLK, PREC, 0>(m, 0, e1, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+        reaction_group<BLK, PREC, 1>(m, e1, t1, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+        reaction_group<BLK, PREC, 2>(m, t1, m.R, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+    } else {
+        // (each round ends with a barrier: the omega_k row is complete after the last one)
+        reaction_rounds<BLK, NP, PREC, 0>(m, part, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+        reaction_rounds<BLK, NP, PREC, 1>(m, part, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+        reaction_rounds<BLK, NP, PREC, 2>(m, part, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+    }
 
     // omega_k (or the source W_k omega_k / rho), sum_k h_k/RT omega_k and, for the sources,
     // c_p/R = sum_k Y_k/W_k c_p,k/R of this part's species
@@ -500,8 +521,6 @@ __global__ void __launch_bounds__(BLK * NP) rates_kernel(const DevMech m, const 
     if constexpr (RHS) inv_rho = 1.0 / rho_w;
     for (int k = part; k < K; k += NP) {
         double w = sW0[k * BLK];
-#pragma unroll
-        for (int q = 1; q < NP; ++q) w += sW0[((size_t)q * K + k) * BLK];
         const double* c = nasa_range(m, k, P.T);
         h = fma(nasa_hRT(c, P.T, P.invT), w, h);
         if constexpr (RHS) {
@@ -575,7 +594,7 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech&
 template <int PREC>
 size_t rates_smem(int K, const Shape& sh) {
     return (size_t)kMathTabDoubles * sizeof(double) +
-           (size_t)(shared_rows<PREC>() + sh.np) * K * sh.blk * sizeof(double);
+           (size_t)(shared_rows<PREC>() + 1) * K * sh.blk * sizeof(double);
 }
 
 // The shape with the most resident warps per SM (CUDA's occupancy calculator: shared memory,

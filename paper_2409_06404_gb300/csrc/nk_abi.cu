@@ -340,6 +340,50 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
         lin_boff[q] = lin_nb;
         lin_nb += rxn[q].nr + rxn[q].np;
     }
+    // Reaction rounds of the rates and JVP kernels for NP = 2 and 4 parts per point: per kind, rows
+    // of NP reactions (device order; -1 idle) whose species (reactants and products) are pairwise
+    // disjoint, so the parts of a point add into one omega_k row without a conflict between the
+    // barriers that separate the rounds.  Greedy in device order.
+    std::vector<int32_t> rsched[2];
+    int32_t rrnd[2][4];
+    {
+        const int words = (K + 63) / 64;
+        std::vector<uint64_t> spb((size_t)R * words, 0);
+        for (int q = 0; q < R; ++q)
+            for (int a = 0; a < rxn[q].nr + rxn[q].np; ++a) {
+                const int k = rxn[q].sp[a < rxn[q].nr ? a : nk::kMaxSide + (a - rxn[q].nr)];
+                spb[(size_t)q * words + k / 64] |= 1ULL << (k % 64);
+            }
+        const int bounds[4] = {0, R_el, R_el + R_tb, R};
+        for (int v = 0; v < 2; ++v) {
+            const int NP = v == 0 ? 2 : 4;
+            std::vector<int32_t>& S = rsched[v];
+            std::vector<uint64_t> used(words);
+            for (int g = 0; g < 3; ++g) {
+                rrnd[v][g] = (int32_t)(S.size() / NP);
+                std::vector<int> pool, rest, row;
+                for (int q = bounds[g]; q < bounds[g + 1]; ++q) pool.push_back(q);
+                while (!pool.empty()) {
+                    std::fill(used.begin(), used.end(), 0ULL);
+                    row.clear();
+                    rest.clear();
+                    for (int q : pool) {
+                        bool take = (int)row.size() < NP;
+                        for (int w = 0; take && w < words; ++w) take = (used[w] & spb[(size_t)q * words + w]) == 0;
+                        if (take) {
+                            row.push_back(q);
+                            for (int w = 0; w < words; ++w) used[w] |= spb[(size_t)q * words + w];
+                        } else {
+                            rest.push_back(q);
+                        }
+                    }
+                    for (int j = 0; j < NP; ++j) S.push_back(j < (int)row.size() ? row[j] : -1);
+                    pool.swap(rest);
+                }
+            }
+            rrnd[v][3] = (int32_t)(S.size() / NP);
+        }
+    }
     // Jacobian assembly terms (nk_internal.cuh): for every entry a of reaction q (species k,
     // signed coefficient nu), V_k gets nu A_q; G_k,j gets nu B_q,b for every entry b (species j)
     // and, for third-body and Troe reactions, Lam_k gets nu L_q and G_k,j nu (eps_j - 1) L_q for
@@ -452,7 +496,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_jr = L.add(jac_row.size() * 4 + 16), o_jt = L.add(jac_term.size() * sizeof(nk::JacTerm) + 16),
                  o_fnud = L.add(f_nud.size() * 4), o_feff = L.add(f_effm1.size() * 4 + 16),
                  o_fcp = L.add(f_cp.size() * 4 + 16), o_lcw = L.add(lc_w.size() * 8),
-                 o_dfe = L.add(df_effm1.size() * 8 + 16);
+                 o_dfe = L.add(df_effm1.size() * 8 + 16), o_rs2 = L.add(rsched[0].size() * 4 + 16),
+                 o_rs4 = L.add(rsched[1].size() * 4 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -498,6 +543,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_lb, lin_boff.data(), (size_t)R * 4);
     put(o_jr, jac_row.data(), jac_row.size() * 4);
     put(o_jt, jac_term.data(), jac_term.size() * sizeof(nk::JacTerm));
+    put(o_rs2, rsched[0].data(), rsched[0].size() * 4);
+    put(o_rs4, rsched[1].data(), rsched[1].size() * 4);
     put(o_fnud, f_nud.data(), f_nud.size() * 4);
     put(o_feff, f_effm1.data(), f_effm1.size() * 4);
     put(o_fcp, f_cp.data(), f_cp.size() * 4);
@@ -580,6 +627,12 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.f_cp = reinterpret_cast<const float*>(b + o_fcp);
     dm.lc_w = reinterpret_cast<const double*>(b + o_lcw);
     dm.df_eff_m1 = reinterpret_cast<const float2*>(b + o_dfe);
+    dm.rsched2 = reinterpret_cast<const int32_t*>(b + o_rs2);
+    dm.rsched4 = reinterpret_cast<const int32_t*>(b + o_rs4);
+    for (int g = 0; g < 4; ++g) {
+        dm.rrnd2[g] = rrnd[0][g];
+        dm.rrnd4[g] = rrnd[1][g];
+    }
     *out = m;
     return ok();
 }

@@ -146,6 +146,13 @@ struct DevMech {
     const double* grp_Tmid;       // [groups] the group's T_mid
     const int32_t* lin_boff;      // [R] first entry slot of each reaction in a stored linearization
     int32_t lin_nb;               // entry slots of all reactions (sum of nr + np)
+    // reaction rounds for 2 and 4 parts per point (rates and JVP kernels): rsched[round * NP + q]
+    // is part q's reaction (device order) in that round or -1; within a round the parts'
+    // reactions share no species; kind g (elementary, third-body, Troe) has rounds
+    // [rrnd[g], rrnd[g + 1])
+    const int32_t* rsched2;
+    const int32_t* rsched4;
+    int32_t rrnd2[4], rrnd4[4];
     // single-precision products from an FP32 linearization: signed coefficients of each
     // reaction's entries (RxnRec::nud order, device order), efficiencies - 1 (eff_m1 order),
     // c_p/R coefficients a1..a5 per species and range ([K][2][8], low then high)
