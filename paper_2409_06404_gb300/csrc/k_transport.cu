@@ -17,6 +17,10 @@
 //  * each binary coefficient exp(-ln D_jk) is evaluated once per pair and used for both
 //    species of the pair; the factor p/p_ref of D_jk(p) multiplies the finished sums.
 //  * double exp/log are the table-driven versions of nk_math.cuh.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "nk_internal.cuh"
 
 namespace nk {
@@ -51,22 +55,82 @@ __device__ __forceinline__ F poly3(const F* c, F L) {
 __device__ __forceinline__ double texp(double x, const MathTab& mt) { return fexp(x, mt); }
 __device__ __forceinline__ float texp(float x, const MathTab&) { return expf(x); }
 
+// The species-pair triangle of the diffusion sums in G = 2 NP contiguous species groups, taken
+// by the NP parts of a point in rounds of group pairs that share no species (the circle method
+// of a round-robin schedule; the last round pairs each part's two groups with themselves), so
+// every part adds straight into the one row of sums, in an order fixed by the schedule.
+template <int NP>
+__device__ __forceinline__ void round_groups(int r, int part, int& ga, int& gb) {
+    constexpr int G = 2 * NP;
+    if (part == 0) {
+        ga = r;
+        gb = G - 1;
+    } else {
+        ga = (r + part) % (G - 1);
+        gb = (r - part + G - 1) % (G - 1);
+    }
+    if (ga > gb) {
+        const int t = ga;
+        ga = gb;
+        gb = t;
+    }
+}
+
+// The pairs (j, k), j in [j0, j1), k in [k0, k1), k > j (k0 = j0, k1 = j1 for a group with itself):
+// S_j += X_k / D_jk in registers and S_k += X_j / D_jk in the row, one exponential per pair, two
+// pairs per iteration.
 template <int BLK, class F>
-__global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const int64_t n, const int64_t ld,
-                                                        const double* __restrict__ T, const double* __restrict__ p,
-                                                        const double* __restrict__ Y, double* __restrict__ mu_out,
-                                                        double* __restrict__ lam_out, double* __restrict__ Dmix) {
+__device__ __forceinline__ void diffusion_pairs(int K, int j0, int j1, int k0, int k1, bool same, const F* Dc, F L,
+                                                const MathTab& mt, const F* sX, F* sS) {
+    for (int j = j0; j < j1; ++j) {
+        const int kb = same ? j + 1 : k0;
+        int pi = j * (2 * K - j - 1) / 2 + (kb - j - 1);       // index of the pair (j, kb)
+        const F xj = sX[j * BLK];
+        F acc0 = F(0), acc1 = F(0);
+        int k = kb;
+        for (; k + 1 < k1; k += 2, pi += 2) {
+            const F i0 = texp(-poly3(Dc + 4 * pi, L), mt);
+            const F i1 = texp(-poly3(Dc + 4 * pi + 4, L), mt);
+            sS[k * BLK] = fma(xj, i0, sS[k * BLK]);
+            sS[(k + 1) * BLK] = fma(xj, i1, sS[(k + 1) * BLK]);
+            acc0 = fma(sX[k * BLK], i0, acc0);
+            acc1 = fma(sX[(k + 1) * BLK], i1, acc1);
+        }
+        if (k < k1) {
+            const F i0 = texp(-poly3(Dc + 4 * pi, L), mt);
+            sS[k * BLK] = fma(xj, i0, sS[k * BLK]);
+            acc0 = fma(sX[k * BLK], i0, acc0);
+        }
+        sS[j * BLK] += acc0 + acc1;
+    }
+}
+
+// BLK points per block, NP parts (warps) per point: the parts split the species-pair triangle
+// of the diffusion sums by the rounds above, then the species of the conductivity, the diffusion
+// outputs and the Wilke sums; the parts' scalar sums are added in part order.  Shared rows per
+// point: X_k, the diffusion sums (then X_k tau_k), the mass-fraction prefix sums (then
+// X_k tau_k^2).
+template <int BLK, int NP, class F>
+__global__ void __launch_bounds__(BLK * NP) transport_kernel(const DevMech m, const int64_t n, const int64_t ld,
+                                                             const double* __restrict__ T,
+                                                             const double* __restrict__ p,
+                                                             const double* __restrict__ Y,
+                                                             double* __restrict__ mu_out,
+                                                             double* __restrict__ lam_out,
+                                                             double* __restrict__ Dmix) {
     extern __shared__ double smem_d[];
     const MathTab mt = stage_math_tables(smem_d, m.mtab);
     __syncthreads();
     F* smem = reinterpret_cast<F*>(smem_d + kMathTabDoubles);
     const int K = m.K;
-    const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
-    if (i >= n) return;
-    F* sX = smem + tid;                        // X_k
-    F* sA = smem + (size_t)K * BLK + tid;      // D denominators, then X_k tau_k
-    F* sB = smem + (size_t)2 * K * BLK + tid;  // prefix sums of Y, then X_k tau_k^2
+    const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
+    const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    const bool live = i0 < n;
+    const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
+    F* sX = smem + slot;                         // X_k
+    F* sA = smem + (size_t)K * BLK + slot;       // D denominators, then X_k tau_k
+    F* sB = smem + (size_t)2 * K * BLK + slot;   // prefix sums of Y, then X_k tau_k^2
     using Tb = Tab<F>;
 
     const double Ti = T[i];
@@ -75,56 +139,50 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double Wbar = 1.0 / s;
-    for (int k = 0; k < K; ++k) sX[k * BLK] = (F)(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar);
+    for (int k = part; k < K; k += NP) sX[k * BLK] = (F)(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar);
 
     // ---- diffusion: sum_{j != k} X_j / D_jk(p_ref), one exponential per pair; the pressure
     // factor p/p_ref multiplies the finished sums
     if (Dmix) {
-        for (int k = 0; k < K; ++k) sA[k * BLK] = F(0);
+        for (int k = part; k < K; k += NP) sA[k * BLK] = F(0);
+        if (NP > 1) __syncthreads();
         const F* Dc = Tb::D(m);
-        int pi = 0;
-        for (int j = 0; j < K; ++j) {
-            const F xj = sX[j * BLK];
-            F acc0 = F(0), acc1 = F(0);
-            int k = j + 1;
-            for (; k + 1 < K; k += 2, pi += 2) {
-                const F i0 = texp(-poly3(Dc + 4 * pi, L), mt);
-                const F i1 = texp(-poly3(Dc + 4 * pi + 4, L), mt);
-                sA[k * BLK] = fma(xj, i0, sA[k * BLK]);
-                sA[(k + 1) * BLK] = fma(xj, i1, sA[(k + 1) * BLK]);
-                acc0 = fma(sX[k * BLK], i0, acc0);
-                acc1 = fma(sX[(k + 1) * BLK], i1, acc1);
-            }
-            if (k < K) {
-                const F i0 = texp(-poly3(Dc + 4 * pi, L), mt);
-                sA[k * BLK] = fma(xj, i0, sA[k * BLK]);
-                acc0 = fma(sX[k * BLK], i0, acc0);
-                ++pi;
-            }
-            sA[j * BLK] += acc0 + acc1;
+        constexpr int G = 2 * NP;
+        for (int r = 0; r < G - 1; ++r) {
+            int ga, gb;
+            round_groups<NP>(r, part, ga, gb);
+            diffusion_pairs<BLK, F>(K, K * ga / G, K * (ga + 1) / G, K * gb / G, K * (gb + 1) / G, false, Dc, L, mt,
+                                    sX, sA);
+            if (NP > 1) __syncthreads();
         }
+        for (int g = 2 * part; g < 2 * part + 2; ++g)
+            diffusion_pairs<BLK, F>(K, K * g / G, K * (g + 1) / G, K * g / G, K * (g + 1) / G, true, Dc, L, mt, sX,
+                                    sA);
+        if (NP > 1) __syncthreads();
         // numerators sum_{j != k} Y_j from prefix and suffix sums (no 1 - Y_k cancellation)
         const double pscale = p[i] / m.p_ref;
         double pre = 0.0;
         for (int k = 0; k < K; ++k) {
-            sB[k * BLK] = (F)pre;
+            if (NP == 1 || k % NP == part) sB[k * BLK] = (F)pre;
             pre += Y[(int64_t)k * ld + i];
         }
         double suf = 0.0;
         for (int k = K - 1; k >= 0; --k) {
-            const double num = (double)sB[k * BLK] + suf;
-            double den = (double)sA[k * BLK] * pscale;
-            if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
-            Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
+            if (NP == 1 || k % NP == part) {
+                const double num = (double)sB[k * BLK] + suf;
+                double den = (double)sA[k * BLK] * pscale;
+                if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
+                if (live) Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
+            }
             suf += Y[(int64_t)k * ld + i];
         }
     }
 
-    // ---- conductivity (Mathur-Saxena) and the Wilke weights
+    // ---- conductivity (Mathur-Saxena) and the Wilke weights of this part's species
     F s1 = F(0), s2 = F(0);
     const F* lamc = Tb::lam(m);
     const F* muc = Tb::mu(m);
-    for (int k = 0; k < K; ++k) {
+    for (int k = part; k < K; k += NP) {
         const F x = sX[k * BLK];
         const F lnlam = poly3(lamc + 4 * k, L);
         s1 = fma(x, texp(lnlam, mt), s1);
@@ -134,13 +192,13 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
         sA[k * BLK] = xt;
         sB[k * BLK] = xt * tau;
     }
-    if (lam_out) lam_out[i] = (double)(F(0.5) * (s1 + F(1) / s2));
 
-    // ---- Wilke viscosity
+    // ---- Wilke viscosity over this part's species
+    F mu = F(0);
     if (mu_out) {
+        if (NP > 1) __syncthreads();
         const F* A = Tb::A(m);
-        F mu = F(0);
-        for (int k = 0; k < K; ++k) {
+        for (int k = part; k < K; k += NP) {
             const F hs = texp(F(0.5) * poly3(muc + 4 * k, L), mt);     // mu_k^1/2
             const F sig = hs / __ldg(Tb::qrtW(m) + k);                  // sigma_k
             const F* Ak = A + (size_t)k * K;
@@ -154,19 +212,123 @@ __global__ void __launch_bounds__(BLK) transport_kernel(const DevMech m, const i
             const F den = fma(sig, fma(sig, S2, F(2) * S1), S0);
             mu = fma(sX[k * BLK], hs * hs / den, mu);
         }
-        mu_out[i] = (double)mu;
+    }
+    if constexpr (NP > 1) {
+        // the parts' sums in part order, through the (dead) X row: rows 3q .. 3q+2 (3 NP <= K)
+        __syncthreads();
+        sX[(3 * part) * BLK] = s1;
+        sX[(3 * part + 1) * BLK] = s2;
+        sX[(3 * part + 2) * BLK] = mu;
+        __syncthreads();
+        if (part != 0) return;
+        s1 = sX[0];
+        s2 = sX[BLK];
+        mu = sX[2 * BLK];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            s1 += sX[(3 * q) * BLK];
+            s2 += sX[(3 * q + 1) * BLK];
+            mu += sX[(3 * q + 2) * BLK];
+        }
+    }
+    if (live) {
+        if (lam_out) lam_out[i] = (double)(F(0.5) * (s1 + F(1) / s2));
+        if (mu_out) mu_out[i] = (double)mu;
     }
 }
 
-template <int BLK, class F>
-cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
-                     double* mu, double* lam, double* D, size_t smem, cudaStream_t s) {
-    auto kern = transport_kernel<BLK, F>;
-    cudaError_t e = ensure_smem((const void*)kern, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = (n + BLK - 1) / BLK;
-    kern<<<(unsigned)grid, BLK, smem, s>>>(m, n, ld, T, p, Y, mu, lam, D);
-    return cudaGetLastError();
+// ---------------------------------------------------------------- launch shapes
+struct Shape {
+    int blk, np;
+};
+constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <class F, int S>
+constexpr auto kernel_of() {
+    return transport_kernel<kShapes[S].blk, kShapes[S].np, F>;
+}
+
+template <class F, int... S>
+const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
+    const void* ptrs[] = {(const void*)kernel_of<F, S>()...};
+    return ptrs[idx];
+}
+
+template <class F>
+size_t transport_smem(int K, const Shape& sh) {
+    return (size_t)kMathTabDoubles * sizeof(double) + (size_t)3 * K * sh.blk * sizeof(F);
+}
+
+struct Plan {
+    int dev, K, mixed, idx;
+};
+std::mutex g_plan_mu;
+std::vector<Plan> g_plans;
+
+// The shape with the most resident warps per SM, fewer parts on ties (cached per device, K and
+// arithmetic type).
+template <class F>
+int plan_shape(int K) {
+    constexpr int mixed = sizeof(F) == sizeof(float);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const Plan& q : g_plans)
+            if (q.dev == dev && q.K == K && q.mixed == mixed) return q.idx;
+    }
+    int per_block = 0;
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < kNumShapes; ++c) {
+        const Shape& sh = kShapes[c];
+        if (sh.np > 1 && 3 * sh.np > K) continue;
+        const size_t bytes = transport_smem<F>(K, sh);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<F>(c, std::make_integer_sequence<int, kNumShapes>{});
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, sh.blk * sh.np, bytes) != cudaSuccess)
+            continue;
+        const int warps = blocks * sh.blk * sh.np / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best = c;
+        }
+    }
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back({dev, K, mixed, best});
+    }
+    return best;
+}
+
+template <class F, int... S>
+cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
+                       const double* T, const double* p, const double* Y, double* mu, double* lam, double* D,
+                       cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    ((S == idx ? (void)(e = [&] {
+        constexpr Shape sh = kShapes[S];
+        auto kern = kernel_of<F, S>();
+        const size_t smem = transport_smem<F>(m.K, sh);
+        cudaError_t r = ensure_smem((const void*)kern, smem);
+        if (r != cudaSuccess) return r;
+        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, mu, lam, D);
+        return cudaGetLastError();
+    }())
+               : (void)0),
+     ...);
+    return e;
+}
+
+template <class F>
+cudaError_t launch_f(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                     double* mu, double* lam, double* Dmix, cudaStream_t s) {
+    const int idx = plan_shape<F>(m.K);
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    return launch_idx<F>(idx, std::make_integer_sequence<int, kNumShapes>{}, m, n, ld, T, p, Y, mu, lam, Dmix, s);
 }
 
 }  // namespace
@@ -174,23 +336,8 @@ cudaError_t launch_t(const DevMech& m, int64_t n, int64_t ld, const double* T, c
 cudaError_t launch_transport(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                              const double* Y, double* mu, double* lam, double* Dmix, int precision,
                              cudaStream_t s) {
-    const bool mixed = precision == NK_MIXED;
-    const size_t per_thread = (size_t)3 * m.K * (mixed ? sizeof(float) : sizeof(double));
-    const size_t tab = kMathTabDoubles * sizeof(double);
-    const int blk = pick_block_occupancy(per_thread, tab);
-    if (!blk) return cudaErrorInvalidConfiguration;
-    const size_t smem = per_thread * blk + tab;
-#define NK_TR_CASE(B)                                                                 \
-    case B:                                                                           \
-        return mixed ? launch_t<B, float>(m, n, ld, T, p, Y, mu, lam, Dmix, smem, s)  \
-                     : launch_t<B, double>(m, n, ld, T, p, Y, mu, lam, Dmix, smem, s);
-    switch (blk) {
-        NK_TR_CASE(128)
-        NK_TR_CASE(64)
-        NK_TR_CASE(32)
-    }
-#undef NK_TR_CASE
-    return cudaErrorInvalidConfiguration;
+    return precision == NK_MIXED ? launch_f<float>(m, n, ld, T, p, Y, mu, lam, Dmix, s)
+                                 : launch_f<double>(m, n, ld, T, p, Y, mu, lam, Dmix, s);
 }
 
 }  // namespace nk

@@ -12,10 +12,11 @@
 // the points of a warp by shuffles, over the point tiles of a block in shared memory and over
 // blocks by a second kernel in a fixed order: deterministic, no atomics.
 //
-// FP64 form as the rates kernel (exponent chains in double-float pairs, everything else in
-// double; the falloff chain in double with pair-based exp/log).  Layout: blocks of 32 points,
-// NP warps per point sharing C_k and bar_omega_k in shared memory, each warp accumulating its
-// own Cbar_k partials, added in part order; a persistent grid walks the point tiles.
+// FP64 form as the rates kernel (exponent chains and, in the logarithmic form, the falloff
+// chain in double-float pairs, everything else in double).  Layout: blocks of 32 points, NP
+// warps per point sharing C_k, bar_omega_k and the Cbar_k row in shared memory, into which they
+// add in rounds of reactions that share no species (third-body efficiencies included): every
+// sum in an order fixed by the schedule.  A persistent grid walks the point tiles.
 #include <algorithm>
 #include <mutex>
 #include <utility>
@@ -315,12 +316,13 @@ __device__ __forceinline__ double vjp_reaction_log(const DevMech& m, int r, cons
     return gl;
 }
 
-// gw[j] += the warp sum of a_j for the first nv of four consecutive reactions: one transposed
+// gw[r_j] += the warp sum of a_j for the first nv of four reactions r_0..r_3: one transposed
 // butterfly (the lanes trade halves of the four values, then of the two left, then reduce
 // within groups of eight), so lane 8 j ends with the sum of a_j.  Every sum is the same
 // pairwise tree as a butterfly all-reduce of a_j alone (bit-identical), at 7 FP64 additions for
 // the four instead of 24.
-__device__ __forceinline__ void warp_sum4_add(double* gw, double a0, double a1, double a2, double a3, int nv) {
+__device__ __forceinline__ void warp_sum4_add(double* gw, double a0, double a1, double a2, double a3, int r0, int r1,
+                                              int r2, int r3, int nv) {
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool hi = (lane & 16) != 0, b3 = (lane & 8) != 0;
@@ -334,34 +336,73 @@ __device__ __forceinline__ void warp_sum4_add(double* gw, double a0, double a1, 
     k += __shfl_xor_sync(kAll, k, 2);
     k += __shfl_xor_sync(kAll, k, 1);
     const int j = lane >> 3;
-    if ((lane & 7) == 0 && j < nv) gw[j] += k;
+    const int rj = j == 0 ? r0 : (j == 1 ? r1 : (j == 2 ? r2 : r3));
+    if ((lane & 7) == 0 && j < nv) gw[rj] += k;
 }
 
-// The ln A gradient terms of consecutive reactions are held in threes and summed over the warp
-// four at a time (warp_sum4_add); the slice's last one to three go out with the remaining slots
-// zero.
+// The ln A gradient terms of a warp's reactions, held three at a time and summed over the warp
+// with the fourth (warp_sum4_add); flush() sends the last one to three with the other slots zero.
+struct GradBatch {
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    int r0 = 0, r1 = 0, r2 = 0, nb = 0;          // the held terms' reactions and count (warp-uniform)
+    __device__ __forceinline__ void add(double* gw, int r, double g) {
+        if (nb == 3) {
+            warp_sum4_add(gw, g0, g1, g2, g, r0, r1, r2, r, 4);
+            nb = 0;
+        } else {
+            if (nb == 0) {
+                g0 = g;
+                r0 = r;
+            } else if (nb == 1) {
+                g1 = g;
+                r1 = r;
+            } else {
+                g2 = g;
+                r2 = r;
+            }
+            ++nb;
+        }
+    }
+    __device__ __forceinline__ void flush(double* gw) {
+        if (nb > 0) warp_sum4_add(gw, g0, nb > 1 ? g1 : 0.0, nb > 2 ? g2 : 0.0, 0.0, r0, r1, r2, 0, nb);
+        nb = 0;
+    }
+};
+
+// Reactions [r0, r1) of one kind in order (one part per point).
 template <int KIND, bool WANT_G, bool HB>
 __device__ __forceinline__ void vjp_group_log(const DevMech& m, int r0, int r1, const double* sC, const double* sWb,
                                               double* sB, double* gw, const VjpPoint& Q, const double* dlnA,
                                               const DfTab& dt, double& Tbar) {
     const float2* sL = reinterpret_cast<const float2*>(sC);
-    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    int nb = 0;                                                   // terms held (warp-uniform)
+    GradBatch gb;
     for (int r = r0; r < r1; ++r) {
         const double g = vjp_reaction_log<KIND, WANT_G, HB>(m, r, sL, sWb, sB, Q, dlnA, dt, Tbar);
-        if (WANT_G) {
-            if (nb == 3) {
-                warp_sum4_add(gw + r - 3, g0, g1, g2, g, 4);
-                nb = 0;
-            } else {
-                if (nb == 0) g0 = g;
-                else if (nb == 1) g1 = g;
-                else g2 = g;
-                ++nb;
-            }
-        }
+        if (WANT_G) gb.add(gw, r, g);
     }
-    if (WANT_G && nb > 0) warp_sum4_add(gw + r1 - nb, g0, nb > 1 ? g1 : 0.0, nb > 2 ? g2 : 0.0, 0.0, nb);
+    if (WANT_G) gb.flush(gw);
+}
+
+// The reactions of one kind for NP > 1 parts per point, round by round (for_rounds with the
+// VJP's schedule: the parts' reactions of a round share no species, efficiencies included), all
+// parts adding into the point's one row of S_k (or Cbar_k).
+template <int NP, int KIND, bool WANT_G, bool HB>
+__device__ __forceinline__ void vjp_rounds(const DevMech& m, int part, bool direct, const double* sC,
+                                           const double* sWb, double* sB, double* gw, const VjpPoint& Q,
+                                           const double* dlnA, const DfTab& dt, double& Tbar) {
+    if (direct) {
+        for_rounds<NP, true>(m, KIND, part, [&](int r) {
+            vjp_reaction<KIND, WANT_G, HB>(m, r, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        });
+    } else {
+        const float2* sL = reinterpret_cast<const float2*>(sC);
+        GradBatch gb;
+        for_rounds<NP, true>(m, KIND, part, [&](int r) {
+            const double g = vjp_reaction_log<KIND, WANT_G, HB>(m, r, sL, sWb, sB, Q, dlnA, dt, Tbar);
+            if (WANT_G) gb.add(gw, r, g);
+        });
+        if (WANT_G) gb.flush(gw);
+    }
 }
 
 template <int KIND, bool WANT_G, bool HB>
@@ -372,14 +413,15 @@ __device__ __forceinline__ void vjp_group(const DevMech& m, int r0, int r1, cons
 }
 
 // Shared memory of a block: the pair tables, the ln A sums [R] (WANT_G), then per point C_k,
-// bar_omega_k and NP rows of Cbar_k partials.
+// bar_omega_k and the Cbar_k row.
 size_t vjp_smem(int K, int R, int np, bool want_g) {
+    (void)np;
     return (size_t)kMathTabDoubles * sizeof(double) + (want_g ? (size_t)((R + 1) & ~1) * sizeof(double) : 0) +
-           (size_t)(2 + np) * K * kVjpBlk * sizeof(double);
+           (size_t)3 * K * kVjpBlk * sizeof(double);
 }
 
 template <int NP, bool WANT_G, bool HB>
-__global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, const int64_t n, const int64_t ld,
+__global__ void __launch_bounds__(kVjpBlk * NP, 384 / (kVjpBlk * NP)) vjp_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                            const double* __restrict__ T, const double* __restrict__ p,
                                                            const double* __restrict__ Y,
                                                            const double* __restrict__ dlnA,
@@ -398,8 +440,8 @@ __global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, cons
     double* base = smem + kMathTabDoubles + (WANT_G ? ((R + 1) & ~1) : 0) + slot;
     double* sC = base;                                            // C_k
     double* sWb = base + (size_t)K * BLK;                         // bar_omega_k
-    double* sB0 = base + (size_t)2 * K * BLK;                     // Cbar_k partials, part q at row q
-    double* sB = sB0 + (size_t)part * K * BLK;
+    double* sB0 = base + (size_t)2 * K * BLK;                     // Cbar_k (S_k in the logarithmic form)
+    double* sB = sB0;
     int ra[3], rb[3];
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
     slice<NP>(0, e1, part, ra[0], rb[0]);
@@ -438,30 +480,34 @@ __global__ void __launch_bounds__(kVjpBlk * NP) vjp_kernel(const DevMech m, cons
             }
             sWb[k * BLK] = bar_omega[(int64_t)k * ld + i];
         }
-        for (int k = 0; k < K; ++k) sB[k * BLK] = 0.0;
+        for (int k = part; k < K; k += NP) sB[k * BLK] = 0.0;
         __syncthreads();
 
         double Tbar = 0.0;
-        if (direct) {
-            vjp_group<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            vjp_group<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            vjp_group<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+        if constexpr (NP == 1) {
+            if (direct) {
+                vjp_group<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+                vjp_group<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+                vjp_group<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            } else {
+                vjp_group_log<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+                vjp_group_log<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+                vjp_group_log<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            }
         } else {
-            vjp_group_log<0, WANT_G, HB>(m, ra[0], rb[0], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            vjp_group_log<1, WANT_G, HB>(m, ra[1], rb[1], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            vjp_group_log<2, WANT_G, HB>(m, ra[2], rb[2], sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            Tbar *= Q.invT;                                       // the logarithmic form sums T Tbar
+            // (each round ends with a barrier: the row is complete after the last one)
+            vjp_rounds<NP, 0, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_rounds<NP, 1, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_rounds<NP, 2, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
         }
+        if (!direct) Tbar *= Q.invT;                              // the logarithmic form sums T Tbar
         __syncthreads();
 
-        // Cbar_k totals (part order) into row 0 (in the logarithmic form S_k = Cbar_k C_k), and
-        // this part's share of sum_k Cbar_k C_k
+        // this part's share of sum_k Cbar_k C_k (in the logarithmic form the row holds
+        // S_k = Cbar_k C_k)
         double cc = 0.0;
         for (int k = part; k < K; k += NP) {
-            double cb = sB0[k * BLK];
-#pragma unroll
-            for (int q = 1; q < NP; ++q) cb += sB0[((size_t)q * K + k) * BLK];
-            sB0[k * BLK] = cb;
+            const double cb = sB0[k * BLK];
             cc = direct ? fma(cb, sC[k * BLK], cc) : cc + cb;
         }
         if (NP > 1) {

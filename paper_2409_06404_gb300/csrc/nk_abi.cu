@@ -344,19 +344,28 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     // of NP reactions (device order; -1 idle) whose species (reactants and products) are pairwise
     // disjoint, so the parts of a point add into one omega_k row without a conflict between the
     // barriers that separate the rounds.  Greedy in device order.
-    std::vector<int32_t> rsched[2];
-    int32_t rrnd[2][4];
+    // Schedules 2 and 3 are the VJP's: its reverse pass also adds into the rows of the species with
+    // a third-body efficiency, which therefore count as the reaction's species there.
+    std::vector<int32_t> rsched[4];
+    int32_t rrnd[4][4];
     {
         const int words = (K + 63) / 64;
-        std::vector<uint64_t> spb((size_t)R * words, 0);
+        std::vector<uint64_t> spb((size_t)R * words, 0), spe;
         for (int q = 0; q < R; ++q)
             for (int a = 0; a < rxn[q].nr + rxn[q].np; ++a) {
                 const int k = rxn[q].sp[a < rxn[q].nr ? a : nk::kMaxSide + (a - rxn[q].nr)];
                 spb[(size_t)q * words + k / 64] |= 1ULL << (k % 64);
             }
+        spe = spb;
+        for (int q = 0; q < R; ++q)
+            for (int j = rxn[q].eff0; j < rxn[q].eff1; ++j) {
+                const int k = eff_sp[j];
+                spe[(size_t)q * words + k / 64] |= 1ULL << (k % 64);
+            }
         const int bounds[4] = {0, R_el, R_el + R_tb, R};
-        for (int v = 0; v < 2; ++v) {
-            const int NP = v == 0 ? 2 : 4;
+        for (int v = 0; v < 4; ++v) {
+            const int NP = v % 2 == 0 ? 2 : 4;
+            const std::vector<uint64_t>& spv = v < 2 ? spb : spe;
             std::vector<int32_t>& S = rsched[v];
             std::vector<uint64_t> used(words);
             for (int g = 0; g < 3; ++g) {
@@ -369,10 +378,10 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                     rest.clear();
                     for (int q : pool) {
                         bool take = (int)row.size() < NP;
-                        for (int w = 0; take && w < words; ++w) take = (used[w] & spb[(size_t)q * words + w]) == 0;
+                        for (int w = 0; take && w < words; ++w) take = (used[w] & spv[(size_t)q * words + w]) == 0;
                         if (take) {
                             row.push_back(q);
-                            for (int w = 0; w < words; ++w) used[w] |= spb[(size_t)q * words + w];
+                            for (int w = 0; w < words; ++w) used[w] |= spv[(size_t)q * words + w];
                         } else {
                             rest.push_back(q);
                         }
@@ -497,7 +506,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_fnud = L.add(f_nud.size() * 4), o_feff = L.add(f_effm1.size() * 4 + 16),
                  o_fcp = L.add(f_cp.size() * 4 + 16), o_lcw = L.add(lc_w.size() * 8),
                  o_dfe = L.add(df_effm1.size() * 8 + 16), o_rs2 = L.add(rsched[0].size() * 4 + 16),
-                 o_rs4 = L.add(rsched[1].size() * 4 + 16);
+                 o_rs4 = L.add(rsched[1].size() * 4 + 16), o_rv2 = L.add(rsched[2].size() * 4 + 16),
+                 o_rv4 = L.add(rsched[3].size() * 4 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -545,6 +555,8 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_jt, jac_term.data(), jac_term.size() * sizeof(nk::JacTerm));
     put(o_rs2, rsched[0].data(), rsched[0].size() * 4);
     put(o_rs4, rsched[1].data(), rsched[1].size() * 4);
+    put(o_rv2, rsched[2].data(), rsched[2].size() * 4);
+    put(o_rv4, rsched[3].data(), rsched[3].size() * 4);
     put(o_fnud, f_nud.data(), f_nud.size() * 4);
     put(o_feff, f_effm1.data(), f_effm1.size() * 4);
     put(o_fcp, f_cp.data(), f_cp.size() * 4);
@@ -629,9 +641,13 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.df_eff_m1 = reinterpret_cast<const float2*>(b + o_dfe);
     dm.rsched2 = reinterpret_cast<const int32_t*>(b + o_rs2);
     dm.rsched4 = reinterpret_cast<const int32_t*>(b + o_rs4);
+    dm.rschedv2 = reinterpret_cast<const int32_t*>(b + o_rv2);
+    dm.rschedv4 = reinterpret_cast<const int32_t*>(b + o_rv4);
     for (int g = 0; g < 4; ++g) {
         dm.rrnd2[g] = rrnd[0][g];
         dm.rrnd4[g] = rrnd[1][g];
+        dm.rrndv2[g] = rrnd[2][g];
+        dm.rrndv4[g] = rrnd[3][g];
     }
     *out = m;
     return ok();

@@ -153,6 +153,10 @@ struct DevMech {
     const int32_t* rsched2;
     const int32_t* rsched4;
     int32_t rrnd2[4], rrnd4[4];
+    // the same for the VJP, whose rounds also keep the species with a third-body efficiency apart
+    const int32_t* rschedv2;
+    const int32_t* rschedv4;
+    int32_t rrndv2[4], rrndv4[4];
     // single-precision products from an FP32 linearization: signed coefficients of each
     // reaction's entries (RxnRec::nud order, device order), efficiencies - 1 (eff_m1 order),
     // c_p/R coefficients a1..a5 per species and range ([K][2][8], low then high)

@@ -361,11 +361,14 @@ __device__ __forceinline__ void slice(int a, int b, int part, int& r0, int& r1) 
 // NP = 2 or 4 parts per point: f(r) for the part's reaction r of each round (none when the round
 // leaves it idle), the block synchronised after every round.  Within a round the parts'
 // reactions share no species (DevMech::rsched2/4), so they may add into one row per point.
-template <int NP, class Fn>
+// EFF: the VJP's schedule (the parts' reactions of a round also share no species with a
+// third-body efficiency).
+template <int NP, bool EFF = false, class Fn>
 __device__ __forceinline__ void for_rounds(const DevMech& m, int g, int part, Fn&& f) {
     static_assert(NP == 2 || NP == 4, "reaction rounds exist for 2 and 4 parts");
-    const int32_t* S = NP == 2 ? m.rsched2 : m.rsched4;
-    const int rd0 = NP == 2 ? m.rrnd2[g] : m.rrnd4[g], rd1 = NP == 2 ? m.rrnd2[g + 1] : m.rrnd4[g + 1];
+    const int32_t* S = EFF ? (NP == 2 ? m.rschedv2 : m.rschedv4) : (NP == 2 ? m.rsched2 : m.rsched4);
+    const int rd0 = EFF ? (NP == 2 ? m.rrndv2[g] : m.rrndv4[g]) : (NP == 2 ? m.rrnd2[g] : m.rrnd4[g]);
+    const int rd1 = EFF ? (NP == 2 ? m.rrndv2[g + 1] : m.rrndv4[g + 1]) : (NP == 2 ? m.rrnd2[g + 1] : m.rrnd4[g + 1]);
     for (int rd = rd0; rd < rd1; ++rd) {
         const int r = __ldg(S + rd * NP + part);
         if (r >= 0) f(r);
