@@ -27,6 +27,7 @@ collective in the data path); the time is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -73,6 +74,15 @@ def pipe_peaks():
             raise RuntimeError(f"pipe probe {name} failed ({st})")
         out[name] = v.value
     return out
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth in MEASURED_PEAKS.json (GB/s), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
 
 
 def _json_profile(name):
@@ -663,6 +673,17 @@ def run_ours(args):
     Vc = torch.empty((3, n), **f64)
     hflux = torch.empty((3, n), **f64)
     wsb = torch.empty(max(nk.rates_vjp_workspace(m, n), 8), dtype=torch.uint8, device=dev)
+    # block-Jacobi preconditioner of the implicit stage: the sources at the state, the solver's
+    # weights 1/(rtol |y| + atol), the LU factors (~23 KB per point) and one vector to solve for
+    N1 = K + 1
+    fTb, fYb = torch.empty(n, **f64), torch.empty((K, n), **f64)
+    wts = torch.empty((N1, n), **f64)
+    wts[0] = 1.0 / (1e-6 * T + 1e-6)
+    wts[1:] = 1.0 / (1e-6 * Y + 1e-12)
+    Fb = torch.empty((N1, N1, n), **f64)
+    pivb = torch.empty((N1, n), dtype=torch.int32, device=dev)
+    vb = torch.randn((N1, n), generator=gen, **f64)
+    zb = torch.empty((N1, n), **f64)
     L = nk.lib()
     s = torch.cuda.current_stream()
     sp = nk._vp(s.cuda_stream)
@@ -711,7 +732,13 @@ def run_ours(args):
         "jvp_linearized_compact": lambda: chk(L.nk_rates_jvp_linearized_compact(h, n, n, P(T), P(p), P(Y), P(linc),
                                                                                 n, P(vT), P(vY), P(out["dw"]),
                                                                                 P(out["dh"]), sp)),
+        # (after "linearize": the factors are formed from the stored linearization)
+        "block_factor": lambda: chk(L.nk_block_jacobi_factor(h, n, n, P(T), P(p), P(Y), P(lin), n, P(fTb), P(fYb),
+                                                             P(wts), n, ctypes.c_double(1e-9), P(Fb), P(pivb), n,
+                                                             sp)),
+        "block_apply": lambda: chk(L.nk_block_jacobi_apply(h, n, P(Fb), P(pivb), n, P(vb), n, P(zb), n, sp)),
     }
+    chk(L.nk_rhs_eval(h, n, n, P(T), P(p), P(Y), None, P(fTb), P(fYb), 0, sp))
     # the mechanism-specialised kernel is compiled (NVRTC) before any timing
     t_jit = time.perf_counter()
     nk.mechanism_jit(m)
@@ -847,6 +874,13 @@ def run_ours(args):
         base = k.split("_")[0]
         if base in ("rates", "transport") and base in alg and k != "rates_jit":
             r["alg_tflops"] = alg[base]["flops"] * n / (both[k] * 1e-3) / 1e12
+        if k == "block_apply":
+            # algorithmic bytes: the factors (N^2 doubles), the pivot words, v read and z written
+            N1 = K + 1
+            bpp = N1 * N1 * 8 + N1 * 4 + 2 * N1 * 8
+            r["bytes_per_point"] = bpp
+            r["hbm_gbs"] = bpp * n / (both[k] * 1e-3) / 1e9
+            r["hbm_frac_of_measured"] = r["hbm_gbs"] / hbm_peak_gbs() if hbm_peak_gbs() else None
         rows_out[k] = r
     dom = max(names, key=lambda k: avg[k])
     peak_src = ("measured in this run: libnkprobe.so, independent multiply-add streams on every SM "

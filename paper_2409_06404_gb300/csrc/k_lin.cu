@@ -208,7 +208,7 @@ __device__ __forceinline__ void lin_group(const DevMech& m, int r0, int r1, cons
 
 // TS: the stored type (double, or float for the single-precision products)
 template <int BLK, int NP, class TS>
-__global__ void __launch_bounds__(BLK * NP) linearize_kernel(const DevMech m, const int64_t n, const int64_t ld,
+__global__ void __launch_bounds__(BLK * NP, 512 / (BLK * NP)) linearize_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                              const double* __restrict__ T,
                                                              const double* __restrict__ p,
                                                              const double* __restrict__ Y,
@@ -296,6 +296,43 @@ __device__ __forceinline__ LinCoef load_coef(const DevMech& m, int r, const doub
     return c;
 }
 
+// One reaction of the double product pass: dq from its stored coefficients and dC, then its
+// scatter into d omega_k.
+template <int BLK, int KIND>
+__device__ __forceinline__ void apply_one(const DevMech& m, const Rxn& x, const LinCoef& c, const double* sdC,
+                                          double* sD, double tT, double dpRT) {
+    double dq = c.A * tT;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.nr) dq = fma(c.Br[e], sdC[x.sp[e] * BLK], dq);
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.np) dq = fma(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
+    if (KIND != 0) {
+        double dM = dpRT;
+        for (int j = x.eff0; j < x.eff1; ++j) dM = fma(__ldg(m.eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
+        dq = fma(c.L, dM, dq);
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            double* w = sD + x.sp[e] * BLK;
+            *w = fma(x.nud[e], dq, *w);
+        }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.np) {
+            double* w = sD + x.sp[kMaxSide + e] * BLK;
+            *w = fma(x.nud[kMaxSide + e], dq, *w);
+        }
+}
+
+struct RxnLin {
+    Rxn x;
+    LinCoef c;
+};
+
+// Reactions [r0, r1) of one kind in order (one part per point).
 template <int BLK, int KIND>
 __device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, const double* sdC, double* sD,
                                             const double* __restrict__ lin, int64_t ldl, int64_t i, double tT,
@@ -310,30 +347,7 @@ __device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, co
             xn = load_rxn(m.rxn + r + 1);
             cn = load_coef<KIND>(m, r + 1, lin, ldl, i, xn.nr, xn.np);
         }
-        double dq = c.A * tT;
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.nr) dq = fma(c.Br[e], sdC[x.sp[e] * BLK], dq);
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.np) dq = fma(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
-        if (KIND != 0) {
-            double dM = dpRT;
-            for (int j = x.eff0; j < x.eff1; ++j) dM = fma(__ldg(m.eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
-            dq = fma(c.L, dM, dq);
-        }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.nr) {
-                double* w = sD + x.sp[e] * BLK;
-                *w = fma(x.nud[e], dq, *w);
-            }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.np) {
-                double* w = sD + x.sp[kMaxSide + e] * BLK;
-                *w = fma(x.nud[kMaxSide + e], dq, *w);
-            }
+        apply_one<BLK, KIND>(m, x, c, sdC, sD, tT, dpRT);
         if (r + 1 < r1) {
             x = xn;
             c = cn;
@@ -341,11 +355,28 @@ __device__ __forceinline__ void apply_group(const DevMech& m, int r0, int r1, co
     }
 }
 
+// The reactions of one kind for NP > 1 parts per point in the rates kernel's rounds, all parts
+// adding into the point's one d omega_k row.
+template <int BLK, int NP, int KIND>
+__device__ __forceinline__ void apply_rounds(const DevMech& m, int part, const double* sdC, double* sD,
+                                             const double* __restrict__ lin, int64_t ldl, int64_t i, double tT,
+                                             double dpRT) {
+    for_rounds_prefetch<NP>(
+        m, KIND, part,
+        [&](int r) {
+            RxnLin v;
+            v.x = load_rxn(m.rxn + r);
+            v.c = load_coef<KIND>(m, r, lin, ldl, i, v.x.nr, v.x.np);
+            return v;
+        },
+        [&](int, const RxnLin& v) { apply_one<BLK, KIND>(m, v.x, v.c, sdC, sD, tT, dpRT); });
+}
+
 // RHS: the tangent of the implicit-stage sources instead, given the sources fT, fY at the same
 // state: dfY_k = (W_k/rho) d omega_k - fY_k d rho/rho, dfT = d hrr/(rho c_p) - fT (d rho/rho +
 // d c_p/c_p) (d_omega, d_hrr then receive dfY, dfT).
 template <int BLK, int NP, bool RHS>
-__global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, const int64_t n, const int64_t ld,
+__global__ void __launch_bounds__(BLK * NP, 512 / (BLK * NP)) jvp_lin_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                            const double* __restrict__ T,
                                                            const double* __restrict__ p,
                                                            const double* __restrict__ Y,
@@ -363,8 +394,8 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;
     double* sdC = smem + slot;                                   // dC_k
-    double* sD0 = smem + (size_t)K * BLK + slot;                 // d omega_k partials, part q at row q
-    double* sD = sD0 + (size_t)part * K * BLK;
+    double* sD0 = smem + (size_t)K * BLK + slot;                 // d omega_k
+    double* sD = sD0;
 
     const double Ti = T[i], dT = vT[i];
     const double invT = 1.0 / Ti, tT = dT * invT;
@@ -381,22 +412,24 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin_kernel(const DevMech m, cons
         const double iw = __ldg(m.invW + k);
         sdC[k * BLK] = fma(Y[(int64_t)k * ld + i] * iw * rho, arho, rho * vY[(int64_t)k * ld + i] * iw);
     }
-    for (int k = 0; k < K; ++k) sD[k * BLK] = 0.0;
+    for (int k = part; k < K; k += NP) sD[k * BLK] = 0.0;
     if (NP > 1) __syncthreads();
 
     const double dpRT = -pRT * tT;
-    int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    slice<NP>(0, e1, part, a, b);
-    apply_group<BLK, 0>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
-    slice<NP>(e1, t1, part, a, b);
-    apply_group<BLK, 1>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
-    slice<NP>(t1, m.R, part, a, b);
-    apply_group<BLK, 2>(m, a, b, sdC, sD, lin, ldl, i, tT, dpRT);
-    if (NP > 1) __syncthreads();
+    if constexpr (NP == 1) {
+        apply_group<BLK, 0>(m, 0, e1, sdC, sD, lin, ldl, i, tT, dpRT);
+        apply_group<BLK, 1>(m, e1, t1, sdC, sD, lin, ldl, i, tT, dpRT);
+        apply_group<BLK, 2>(m, t1, m.R, sdC, sD, lin, ldl, i, tT, dpRT);
+    } else {
+        // (each round ends with a barrier: the row is complete after the last one)
+        apply_rounds<BLK, NP, 0>(m, part, sdC, sD, lin, ldl, i, tT, dpRT);
+        apply_rounds<BLK, NP, 1>(m, part, sdC, sD, lin, ldl, i, tT, dpRT);
+        apply_rounds<BLK, NP, 2>(m, part, sdC, sD, lin, ldl, i, tT, dpRT);
+    }
 
-    lin_epilogue<BLK, NP, RHS>(m, part, live, i, Ti, dT, rho, arho, sD0, sdC, lin + slot_H(m) * ldl + i,
-                               lin + slot_S(m) * ldl + i, ldl, Y, vY, ld, fT, fY, ldf, d_omega, d_hrr);
+    lin_epilogue<BLK, NP, RHS, 1>(m, part, live, i, Ti, dT, rho, arho, sD0, sdC, lin + slot_H(m) * ldl + i,
+                                  lin + slot_S(m) * ldl + i, ldl, Y, vY, ld, fT, fY, ldf, d_omega, d_hrr);
 }
 
 // ---------------------------------------------------------------- FP32 apply pass
@@ -472,6 +505,43 @@ __device__ __forceinline__ double scale2(double v, int e) {
 // 2^d as a float for an integer d <= 0 (zero below -126)
 __device__ __forceinline__ float pow2f(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.0f; }
 
+// One reaction of the single-precision product pass: dq' from its scaled coefficients and dC,
+// scattered into the species sums at the species' scales.
+template <int BLK, int KIND>
+__device__ __forceinline__ void apply_one32(const DevMech& m, const Rxn32& x, const LinCoef32& c, const float* sdC,
+                                            float* sD, const int* sE, float tT, float dpRT) {
+    float dq = c.A * tT;
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.nr) dq = fmaf(c.Br[e], sdC[x.sp[e] * BLK], dq);
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.np) dq = fmaf(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
+    if (KIND != 0) {
+        float dM = dpRT;
+        for (int j = x.eff0; j < x.eff1; ++j) dM = fmaf(__ldg(m.f_eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
+        dq = fmaf(c.L, dM, dq);
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.nr) {
+            const int k = x.sp[e] * BLK;
+            sD[k] = fmaf(x.nud[e] * pow2f(c.e - sE[k]), dq, sD[k]);
+        }
+#pragma unroll
+    for (int e = 0; e < kMaxSide; ++e)
+        if (e < x.np) {
+            const int k = x.sp[kMaxSide + e] * BLK;
+            sD[k] = fmaf(x.nud[kMaxSide + e] * pow2f(c.e - sE[k]), dq, sD[k]);
+        }
+}
+
+struct RxnLin32 {
+    Rxn32 x;
+    LinCoef32 c;
+};
+
+// Reactions [r0, r1) of one kind in order (one part per point).
 template <int BLK, int KIND>
 __device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, const float* sdC, float* sD,
                                               const int* sE, const float* __restrict__ lin, int64_t ldl, int64_t i,
@@ -486,31 +556,7 @@ __device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, 
             xn = load_rxn32(m, r + 1);
             cn = load_coef32<KIND>(m, r + 1, lin, ldl, i, xn.nr, xn.np);
         }
-        float dq = c.A * tT;
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.nr) dq = fmaf(c.Br[e], sdC[x.sp[e] * BLK], dq);
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.np) dq = fmaf(c.Bp[e], sdC[x.sp[kMaxSide + e] * BLK], dq);
-        if (KIND != 0) {
-            float dM = dpRT;
-            for (int j = x.eff0; j < x.eff1; ++j)
-                dM = fmaf(__ldg(m.f_eff_m1 + j), sdC[__ldg(m.eff_sp + j) * BLK], dM);
-            dq = fmaf(c.L, dM, dq);
-        }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.nr) {
-                const int k = x.sp[e] * BLK;
-                sD[k] = fmaf(x.nud[e] * pow2f(c.e - sE[k]), dq, sD[k]);
-            }
-#pragma unroll
-        for (int e = 0; e < kMaxSide; ++e)
-            if (e < x.np) {
-                const int k = x.sp[kMaxSide + e] * BLK;
-                sD[k] = fmaf(x.nud[kMaxSide + e] * pow2f(c.e - sE[k]), dq, sD[k]);
-            }
+        apply_one32<BLK, KIND>(m, x, c, sdC, sD, sE, tT, dpRT);
         if (r + 1 < r1) {
             x = xn;
             c = cn;
@@ -518,14 +564,31 @@ __device__ __forceinline__ void apply_group32(const DevMech& m, int r0, int r1, 
     }
 }
 
-// Shared memory: 3 NP sums per point (double), NP rows of scaled d omega_k partials, dC_k, E_k
+// The reactions of one kind for NP > 1 parts per point in the rates kernel's rounds, all parts
+// adding into the point's one row of scaled sums.
+template <int BLK, int NP, int KIND>
+__device__ __forceinline__ void apply_rounds32(const DevMech& m, int part, const float* sdC, float* sD,
+                                               const int* sE, const float* __restrict__ lin, int64_t ldl, int64_t i,
+                                               float tT, float dpRT) {
+    for_rounds_prefetch<NP>(
+        m, KIND, part,
+        [&](int r) {
+            RxnLin32 v;
+            v.x = load_rxn32(m, r);
+            v.c = load_coef32<KIND>(m, r, lin, ldl, i, v.x.nr, v.x.np);
+            return v;
+        },
+        [&](int, const RxnLin32& v) { apply_one32<BLK, KIND>(m, v.x, v.c, sdC, sD, sE, tT, dpRT); });
+}
+
+// Shared memory: 3 NP sums per point (double), the row of scaled d omega_k sums, dC_k, E_k
 // (4-byte words).
 __host__ __device__ constexpr size_t lin32_smem(int K, int blk, int np) {
-    return (size_t)3 * np * blk * sizeof(double) + (size_t)(np + 2) * K * blk * sizeof(float);
+    return (size_t)3 * np * blk * sizeof(double) + (size_t)3 * K * blk * sizeof(float);
 }
 
 template <int BLK, int NP, bool RHS>
-__global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, const int64_t n, const int64_t ld,
+__global__ void __launch_bounds__(BLK * NP, 768 / (BLK * NP)) jvp_lin32_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                              const double* __restrict__ T,
                                                              const double* __restrict__ p,
                                                              const double* __restrict__ Y,
@@ -544,9 +607,9 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, co
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;
     double* sR = smd + slot;                                     // part sums
-    float* sD0 = reinterpret_cast<float*>(smd + (size_t)3 * NP * BLK) + slot;   // scaled partials, part q at row q
-    float* sD = sD0 + (size_t)part * K * BLK;
-    float* sdC = sD0 + (size_t)NP * K * BLK;                     // dC_k
+    float* sD0 = reinterpret_cast<float*>(smd + (size_t)3 * NP * BLK) + slot;   // scaled d omega_k sums
+    float* sD = sD0;
+    float* sdC = sD0 + (size_t)K * BLK;                          // dC_k
     int* sE = reinterpret_cast<int*>(sdC + (size_t)K * BLK);     // E_k
     const int32_t* linE = reinterpret_cast<const int32_t*>(lin) + slot_EK32(m) * ldl + i;
 
@@ -567,28 +630,28 @@ __global__ void __launch_bounds__(BLK * NP) jvp_lin32_kernel(const DevMech m, co
         sdC[k * BLK] = fmaf(narrow(Y[(int64_t)k * ld + i]) * iw * rho, arho, rho * narrow(vY[(int64_t)k * ld + i]) * iw);
         sE[k * BLK] = linE[(int64_t)k * ldl];
     }
-    for (int k = 0; k < K; ++k) sD[k * BLK] = 0.0f;
+    for (int k = part; k < K; k += NP) sD[k * BLK] = 0.0f;
     if (NP > 1) __syncthreads();
 
     const float dpRT = -pRT * tT;
-    int a, b;
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-    slice<NP>(0, e1, part, a, b);
-    apply_group32<BLK, 0>(m, a, b, sdC, sD, sE, lin, ldl, i, tT, dpRT);
-    slice<NP>(e1, t1, part, a, b);
-    apply_group32<BLK, 1>(m, a, b, sdC, sD, sE, lin, ldl, i, tT, dpRT);
-    slice<NP>(t1, m.R, part, a, b);
-    apply_group32<BLK, 2>(m, a, b, sdC, sD, sE, lin, ldl, i, tT, dpRT);
-    if (NP > 1) __syncthreads();
+    if constexpr (NP == 1) {
+        apply_group32<BLK, 0>(m, 0, e1, sdC, sD, sE, lin, ldl, i, tT, dpRT);
+        apply_group32<BLK, 1>(m, e1, t1, sdC, sD, sE, lin, ldl, i, tT, dpRT);
+        apply_group32<BLK, 2>(m, t1, m.R, sdC, sD, sE, lin, ldl, i, tT, dpRT);
+    } else {
+        // (each round ends with a barrier: the row is complete after the last one)
+        apply_rounds32<BLK, NP, 0>(m, part, sdC, sD, sE, lin, ldl, i, tT, dpRT);
+        apply_rounds32<BLK, NP, 1>(m, part, sdC, sD, sE, lin, ldl, i, tT, dpRT);
+        apply_rounds32<BLK, NP, 2>(m, part, sdC, sD, sE, lin, ldl, i, tT, dpRT);
+    }
 
     double hsum = 0.0;
     float cpm = 0.0f, dcpm = 0.0f;
     const float inv_rho = RHS ? 1.0f / rho : 0.0f;
     const double arho_d = widen(arho);
     for (int k = part; k < K; k += NP) {
-        float dws = sD0[k * BLK];
-#pragma unroll
-        for (int q = 1; q < NP; ++q) dws += sD0[((size_t)q * K + k) * BLK];
+        const float dws = sD0[k * BLK];
         double dw = scale2(widen(dws), sE[k * BLK]);
         hsum = fma(widen(lin[(slot_H32(m) + k) * ldl + i]), dw, hsum);
         if constexpr (RHS) {
@@ -671,13 +734,13 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
     return ptrs[idx];
 }
 
-// linearization: the pair tables and C_k; apply: dC_k and NP rows of d omega_k partials (and
-// the part sums of the single-precision apply)
+// linearization: the pair tables and C_k; apply: dC_k and the d omega_k row (and the part sums
+// of the single-precision apply)
 size_t lin_smem(int K, const Shape& sh, int mode) {
     if (mode == 0 || mode == 5)
         return (size_t)kMathTabDoubles * sizeof(double) + (size_t)K * sh.blk * (mode == 5 ? 12 : 8);
     if (mode == 3 || mode == 4) return lin32_smem(K, sh.blk, sh.np);
-    return (size_t)(1 + sh.np) * K * sh.blk * sizeof(double);
+    return (size_t)2 * K * sh.blk * sizeof(double);
 }
 
 struct Plan {

@@ -91,8 +91,9 @@ __device__ __forceinline__ LinPoint make_lin_point(double Ti, double pi, const D
 // implicit-stage sources instead, given the sources fT, fY at the same state:
 //   dfY_k = (W_k/rho) d omega_k - fY_k d rho/rho,  dfT = d hrr/(rho c_p) - fT (d rho/rho + d c_p/c_p)
 // (written to d_omega and d_hrr).  sX: per-point shared rows no longer in use, at least
-// (1 + 2 RHS) NP of them, for the parts' scalar sums.  Part 0 writes the point terms.
-template <int BLK, int NP, bool RHS>
+// (1 + 2 RHS) NP of them, for the parts' scalar sums.  Part 0 writes the point terms.  NR: the
+// rows of d omega_k partials in sD0 (NP, or 1 when the parts share one row).
+template <int BLK, int NP, bool RHS, int NR = NP>
 __device__ __forceinline__ void lin_epilogue(const DevMech& m, int part, bool live, int64_t i, double Ti, double dT,
                                              double rho, double arho, const double* sD0, double* sX,
                                              const double* __restrict__ hRT, const double* __restrict__ S1p,
@@ -107,7 +108,7 @@ __device__ __forceinline__ void lin_epilogue(const DevMech& m, int part, bool li
     for (int k = part; k < K; k += NP) {
         double dw = sD0[k * BLK];
 #pragma unroll
-        for (int q = 1; q < NP; ++q) dw += sD0[((size_t)q * K + k) * BLK];
+        for (int q = 1; q < NR; ++q) dw += sD0[((size_t)q * K + k) * BLK];
         hsum = fma(hRT[(int64_t)k * ldl], dw, hsum);
         if constexpr (RHS) {
             const double* c = nasa_range(m, k, Ti);

@@ -376,4 +376,29 @@ __device__ __forceinline__ void for_rounds(const DevMech& m, int g, int part, Fn
     }
 }
 
+// As for_rounds (NP = 2 or 4, the rates kernel's schedule) for passes that read stored data per
+// reaction: ld(r) issues the loads the reaction needs, ap(r, v) uses them; the part's next
+// reaction's loads are issued before the current one is applied, so they stay in flight across
+// the round's barrier.
+template <int NP, class Ld, class Ap>
+__device__ __forceinline__ void for_rounds_prefetch(const DevMech& m, int g, int part, Ld&& ld, Ap&& ap) {
+    static_assert(NP == 2 || NP == 4, "reaction rounds exist for 2 and 4 parts");
+    const int32_t* S = NP == 2 ? m.rsched2 : m.rsched4;
+    const int rd0 = NP == 2 ? m.rrnd2[g] : m.rrnd4[g], rd1 = NP == 2 ? m.rrnd2[g + 1] : m.rrnd4[g + 1];
+    if (rd0 >= rd1) return;
+    using V = decltype(ld(0));
+    int r = __ldg(S + rd0 * NP + part);
+    V cur{};
+    if (r >= 0) cur = ld(r);
+    for (int rd = rd0; rd < rd1; ++rd) {
+        const int rn = rd + 1 < rd1 ? __ldg(S + (rd + 1) * NP + part) : -1;
+        V nxt{};
+        if (rn >= 0) nxt = ld(rn);
+        if (r >= 0) ap(r, cur);
+        __syncthreads();
+        r = rn;
+        cur = nxt;
+    }
+}
+
 }  // namespace nk
