@@ -8,9 +8,9 @@
 // contiguous), rows in pivot order: row k holds L_k,0..k-1 (unit lower part) and U_k,k..N-1 of
 // the row-scaled block D P, with 1/U_kk in place of U_kk; piv[k ldq + i] holds that row's
 // original index (low 16 bits) and its exponent e (high 16 bits, signed), D = diag(2^-e).  P z = v
-// is then L U z = (D v) in pivot order.  Four threads per point, forward then backward
-// substitution with the vector in shared memory and the factors read once, in order (each warp
-// reads eight points' consecutive entries: whole 32-byte sectors).
+// is then L U z = (D v) in pivot order.  One thread per point, forward then backward
+// substitution with the vector in shared memory and the factors read once, in order, streamed
+// into shared memory ahead of use (coalesced across the warp's points).
 #include <algorithm>
 #include <cstdint>
 
@@ -19,77 +19,105 @@
 namespace nk {
 namespace {
 
-constexpr int kApplyBlk = 128;
+constexpr int kApplyPts = 32;   // points (threads) per block
 
-// TPP threads per point (adjacent lanes): thread t sums the terms j = j0 + t, j0 + t + TPP, ...
-// of sum_{j0 <= j < j1} f[j ldF] y[j] in two independent partial sums, and the point's threads
-// combine theirs by shuffles, so each gets the whole dot product.  Splitting a point over
-// threads divides its vector's shared memory among them (more resident warps) and multiplies
-// the factor loads in flight per point.  y: the point's vector at y[j * PPB].
-template <int TPP, int PPB>
-__device__ __forceinline__ double dot_run(const double* __restrict__ f, int64_t ldF, const double* y, int j0, int j1,
-                                          int t) {
-    double s0 = 0.0, s1 = 0.0;
-    int j = j0 + t;
-    for (; j + TPP < j1; j += 2 * TPP) {
-        const double f0 = f[(int64_t)j * ldF], f1 = f[(int64_t)(j + TPP) * ldF];
-        s0 = fma(f0, y[j * PPB], s0);
-        s1 = fma(f1, y[(j + TPP) * PPB], s1);
+// Asynchronous 8-byte copy global -> shared (cp.async, completion tracked per thread in commit
+// groups), its group commit and the wait for all but the newest N groups.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Step s of the two substitutions: the forward row k = s (entries 0..k-1 of L) for s < N, then
+// the backward row k = 2N - 1 - s (entries k..N-1 of U, the first being 1/U_kk).
+__device__ __forceinline__ void step_row(int s, int N, int& k, int& j0, int& j1) {
+    if (s < N) {
+        k = s;
+        j0 = 0;
+        j1 = s;
+    } else {
+        k = 2 * N - 1 - s;
+        j0 = k;
+        j1 = N;
     }
-    if (j < j1) s0 = fma(f[(int64_t)j * ldF], y[j * PPB], s0);
-    double sum = s0 + s1;
-#pragma unroll
-    for (int o = 1; o < TPP; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    return sum;
 }
 
 // z = P^-1 v per point: v and z rows of ldv / ldz (row r of point i at r ld + i), of type TI and
-// TO, arithmetic in double.  z may alias v: every point's threads read its entries of v before
-// they write z (the row of y each thread reads at step k was written by the point's thread 0
-// before the shuffles of step k, which order it).  Threads past the last point shadow point
-// n - 1 without writing (the shuffles need the whole warp).
-template <class TI, class TO, int TPP>
-__global__ void __launch_bounds__(kApplyBlk) lu_apply_kernel(const int N, const int64_t n, const double* __restrict__ F,
+// TO, arithmetic in double.  One thread per point; the factor entries each step needs are copied
+// into shared memory asynchronously two steps ahead (cp.async into two row buffers), so each
+// thread keeps up to two factor rows of loads in flight instead of stalling on every row's first
+// load.  Every thread works on its own columns of the shared arrays only (no block barrier).  z
+// may alias v: each thread reads its point's entries of v before it writes z.
+template <class TI, class TO>
+__global__ void __launch_bounds__(kApplyPts) lu_apply_kernel(const int N, const int64_t n, const double* __restrict__ F,
                                                              const int64_t ldF, const int32_t* __restrict__ piv,
                                                              const int64_t ldq, const TI* v, const int64_t ldv, TO* z,
                                                              const int64_t ldz) {
-    constexpr int PPB = kApplyBlk / TPP;                       // points per block
-    extern __shared__ double sy[];
-    const int pt = threadIdx.x / TPP, t = threadIdx.x % TPP;
-    const int64_t i0 = (int64_t)blockIdx.x * PPB + pt;
-    const bool live = i0 < n;
-    const int64_t i = live ? i0 : n - 1;
-    double* y = sy + pt;
+    extern __shared__ double sm[];
+    const int64_t i = (int64_t)blockIdx.x * kApplyPts + threadIdx.x;
+    if (i >= n) return;
+    double* y = sm + threadIdx.x;                                  // y[j * kApplyPts]
+    double* const buf0 = sm + (size_t)N * kApplyPts + threadIdx.x;   // the two row buffers
+    double* const buf1 = buf0 + (size_t)N * kApplyPts;
     const double* f = F + i;
-    for (int k = 0; k < N; ++k) {                              // L y = (D v)(perm), unit diagonal
+    const int S = 2 * N;
+    auto issue = [&](int s, double* b) {
+        int k, j0, j1;
+        step_row(s, N, k, j0, j1);
         const double* fk = f + (int64_t)k * N * ldF;
-        const double d = dot_run<TPP, PPB>(fk, ldF, y, 0, k, t);
-        if (t == 0) {
+        for (int j = j0; j < j1; ++j) cp_async8(b + j * kApplyPts, fk + (int64_t)j * ldF);
+        cp_async_commit();
+    };
+    issue(0, buf0);
+    if (S > 1) issue(1, buf1);
+    for (int s = 0; s < S; ++s) {
+        double* b = (s & 1) ? buf1 : buf0;
+        cp_async_wait<1>();                                        // step s's copies have landed
+        int k, j0, j1;
+        step_row(s, N, k, j0, j1);
+        if (s < N) {                                               // L y = (D v)(perm), unit diagonal
+            double d0 = 0.0, d1 = 0.0;
+            int j = 0;
+            for (; j + 1 < k; j += 2) {
+                d0 = fma(b[j * kApplyPts], y[j * kApplyPts], d0);
+                d1 = fma(b[(j + 1) * kApplyPts], y[(j + 1) * kApplyPts], d1);
+            }
+            if (j < k) d0 = fma(b[j * kApplyPts], y[j * kApplyPts], d0);
             const int32_t pk = piv[(int64_t)k * ldq + i];
-            y[k * PPB] = ldexp((double)v[(int64_t)(pk & 0xffff) * ldv + i], -(pk >> 16)) - d;
+            y[k * kApplyPts] = ldexp((double)v[(int64_t)(pk & 0xffff) * ldv + i], -(pk >> 16)) - (d0 + d1);
+        } else {                                                   // U x = y, 1/U_kk stored
+            double d0 = 0.0, d1 = 0.0;
+            int j = k + 1;
+            for (; j + 1 < N; j += 2) {
+                d0 = fma(b[j * kApplyPts], y[j * kApplyPts], d0);
+                d1 = fma(b[(j + 1) * kApplyPts], y[(j + 1) * kApplyPts], d1);
+            }
+            if (j < N) d0 = fma(b[j * kApplyPts], y[j * kApplyPts], d0);
+            y[k * kApplyPts] = (y[k * kApplyPts] - (d0 + d1)) * b[k * kApplyPts];
         }
-        __syncwarp();
+        if (s + 2 < S)
+            issue(s + 2, b);                                       // (b's entries of step s are used)
+        else
+            cp_async_commit();                                     // an empty group keeps the count
     }
-    for (int k = N - 1; k >= 0; --k) {                         // U x = y, 1/U_kk stored
-        const double* fk = f + (int64_t)k * N * ldF;
-        const double d = dot_run<TPP, PPB>(fk, ldF, y, k + 1, N, t);
-        if (t == 0) y[k * PPB] = (y[k * PPB] - d) * fk[(int64_t)k * ldF];
-        __syncwarp();
-    }
-    if (live)
-        for (int k = t; k < N; k += TPP) z[(int64_t)k * ldz + i] = (TO)y[k * PPB];
+    for (int k = 0; k < N; ++k) z[(int64_t)k * ldz + i] = (TO)y[k * kApplyPts];
 }
 
 template <class TI, class TO>
 cudaError_t apply(int N, int64_t n, const double* F, int64_t ldF, const int32_t* piv, int64_t ldq, const TI* v,
                   int64_t ldv, TO* z, int64_t ldz, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    constexpr int TPP = 4, PPB = kApplyBlk / TPP;
-    const size_t bytes = (size_t)N * PPB * sizeof(double);
-    auto kern = lu_apply_kernel<TI, TO, TPP>;
+    const size_t bytes = (size_t)3 * N * kApplyPts * sizeof(double);
+    auto kern = lu_apply_kernel<TI, TO>;
     cudaError_t e = ensure_smem((const void*)kern, bytes);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)((n + PPB - 1) / PPB), kApplyBlk, bytes, s>>>(N, n, F, ldF, piv, ldq, v, ldv, z, ldz);
+    kern<<<(unsigned)((n + kApplyPts - 1) / kApplyPts), kApplyPts, bytes, s>>>(N, n, F, ldF, piv, ldq, v, ldv, z,
+                                                                              ldz);
     return cudaGetLastError();
 }
 
