@@ -458,7 +458,10 @@ def config_rows(nk, dev, stream):
     launching stream around `reps` back-to-back launches (after 3 untimed ones):
       h2_9sp_21rx on 64 elements x 512 = 32,768 points (uniform states), FP64: inputs 2.9 MB, L2-resident,
         so the per-launch times include launch latency;
-      big_120sp_700rx on the 4,096-element flame field (2,097,152 points), FP64 and mixed."""
+      h2_9sp_21rx on the 4,096-element flame field (2,097,152 points), FP64 and mixed: the paper's
+        mechanism size at a production point count (its own figures are for this size);
+      big_120sp_700rx on the 4,096-element flame field (2,097,152 points), FP64 and mixed.
+    Results are keyed by mechanism, the 9-species production row as h2_9sp_21rx@flame_4096el."""
     import torch
     from paper_2409_06404_gb300 import synth
     L = nk.lib()
@@ -466,6 +469,7 @@ def config_rows(nk, dev, stream):
     P = lambda t: nk._vp(t.data_ptr())
     res = {}
     for name, wl, reps, forms in (("h2_9sp_21rx", "uniform_64el", 50, ("fp64",)),
+                                  ("h2_9sp_21rx", "flame_4096el", 20, ("fp64", "mixed")),
                                   ("big_120sp_700rx", "flame_4096el", 5, ("fp64", "mixed"))):
         mech = synth.mechanism(name)
         st = synth.workload_states(wl, mech.K)
@@ -506,7 +510,7 @@ def config_rows(nk, dev, stream):
         m.close()
         del T, p, Y, w, D, h, mu, lam
         torch.cuda.empty_cache()
-        res[name] = rec
+        res[name if name not in res else f"{name}@{wl}"] = rec
     return res
 
 

@@ -32,6 +32,27 @@ __device__ __forceinline__ float2 as_f2(dfl a) { return make_float2(a.h, a.l); }
 __device__ __forceinline__ dfl dneg(dfl a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ dfl dscale(dfl a, float s) { return {a.h * s, a.l * s}; }   // s a power of 2
 
+// A sum of products a_j x_j of positive pairs kept as an unevaluated float sum hi + lo that is
+// not renormalised per term: hi collects the high products by two-sum, lo the two-sums' rounding
+// errors, the products' own errors and the cross terms (each about 2^-24 of its term, so a float
+// carries them), and dot_value renormalises once.  12 FP32 operations per term instead of the 15
+// of df_fma; for positive terms the result keeps the pair's ~2^-46 relative error.
+struct DotAcc {
+    float hi = 0.0f, lo = 0.0f;
+};
+__device__ __forceinline__ void dot_add(DotAcc& s, dfl a, dfl x) {
+    const float p = __fmul_rn(a.h, x.h);
+    float e = __fmaf_rn(a.h, x.h, -p);
+    e = __fmaf_rn(a.h, x.l, e);
+    e = __fmaf_rn(a.l, x.h, e);
+    const float t = __fadd_rn(s.hi, p);
+    const float bb = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ dfl dot_value(const DotAcc& s) { return fast_two_sum(s.hi, s.lo); }
+
 // c0 + u (c1 + u (c2 + u c3)) in pairs
 __device__ __forceinline__ dfl poly3_df(const float2* c, dfl u) {
     dfl acc = ld2(c + 3);
@@ -44,21 +65,23 @@ __device__ __forceinline__ dfl poly3_df(const float2* c, dfl u) {
 // one row for the mass-fraction prefix sums (later X_k tau_k^2).
 constexpr int kTransportRows = 3;
 
-// The species-pair triangle of the diffusion sums in G = 2 NP contiguous species groups.  In
-// each of the first G - 1 rounds the NP parts take NP group pairs that share no species (the
-// circle method of a round-robin schedule: group G - 1 meets group r, groups (r + q) and
-// (r - q) mod (G - 1) meet for q = 1 .. NP - 1); in the last round part q takes the pairs within
-// groups 2q and 2q + 1.  So within a round no two parts touch one species, every part adds
+// The species-pair triangle of the diffusion sums in G = kGroupsPerPart NP contiguous species
+// groups.  In each of the first G - 1 rounds the G/2 group pairs of a round-robin schedule (the
+// circle method: group G - 1 meets group r, groups (r + q) and (r - q) mod (G - 1) meet for
+// q = 1 .. G/2 - 1) share no species; part q takes pairs q kGroupsPerPart/2 .. (q + 1)
+// kGroupsPerPart/2 - 1 of the round.  In the last round part q takes the pairs within its own
+// kGroupsPerPart groups.  So within a round no two parts touch one species, every part adds
 // straight into the one row of sums, and the order of each sum is fixed by the schedule.
-template <int NP>
-__device__ __forceinline__ void round_groups(int r, int part, int& ga, int& gb) {
-    constexpr int G = 2 * NP;
-    if (part == 0) {
+constexpr int kGroupsPerPart = 2;
+
+template <int G>
+__device__ __forceinline__ void round_pair(int r, int q, int& ga, int& gb) {
+    if (q == 0) {
         ga = r;
         gb = G - 1;
     } else {
-        ga = (r + part) % (G - 1);
-        gb = (r - part + G - 1) % (G - 1);
+        ga = (r + q) % (G - 1);
+        gb = (r - q + G - 1) % (G - 1);
     }
     if (ga > gb) {
         const int t = ga;
@@ -143,15 +166,18 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
         for (int k = part; k < K; k += NP) sA0[k * BLK] = make_float2(0.0f, 0.0f);
         if (NP > 1) __syncthreads();
         const float2* Dc = m.df_D_fit;
-        constexpr int G = 2 * NP;
+        constexpr int G = kGroupsPerPart * NP, H = kGroupsPerPart / 2;
         for (int r = 0; r < G - 1; ++r) {
-            int ga, gb;
-            round_groups<NP>(r, part, ga, gb);
-            diffusion_pairs<BLK>(K, K * ga / G, K * (ga + 1) / G, K * gb / G, K * (gb + 1) / G, false, Dc, u, etab,
-                                 sX, sA0);
+#pragma unroll 1
+            for (int h = 0; h < H; ++h) {
+                int ga, gb;
+                round_pair<G>(r, part * H + h, ga, gb);
+                diffusion_pairs<BLK>(K, K * ga / G, K * (ga + 1) / G, K * gb / G, K * (gb + 1) / G, false, Dc, u,
+                                     etab, sX, sA0);
+            }
             if (NP > 1) __syncthreads();
         }
-        for (int g = 2 * part; g < 2 * part + 2; ++g)
+        for (int g = kGroupsPerPart * part; g < kGroupsPerPart * (part + 1); ++g)
             diffusion_pairs<BLK>(K, K * g / G, K * (g + 1) / G, K * g / G, K * (g + 1) / G, true, Dc, u, etab, sX,
                                  sA0);
         if (NP > 1) __syncthreads();
@@ -196,35 +222,28 @@ __global__ void __launch_bounds__(BLK * NP) transport_df_kernel(const DevMech m,
             const dfl lnmu = poly3_df(m.df_mu_fit + 4 * k, u);
             const dfl sig = df_exp(df_add(dscale(lnmu, 0.5f), dneg(ld2(m.df_qlnW + k))), etab);   // mu^1/2 W^-1/4
             const float2* Ak = m.df_wilkeA + (size_t)k * K;
-            // j in four interleaved sums: twelve independent chains per thread
-            dfl S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, T1{0.0f, 0.0f}, T2{0.0f, 0.0f};
-            dfl U0{0.0f, 0.0f}, U1{0.0f, 0.0f}, U2{0.0f, 0.0f}, V0{0.0f, 0.0f}, V1{0.0f, 0.0f}, V2{0.0f, 0.0f};
+            // j in two interleaved sums of each of the three: six independent chains per thread
+            DotAcc S0, S1, S2, T0, T1, T2;
             int j = 0;
-            for (; j + 3 < K; j += 4) {
-                const dfl a = ld2(Ak + j), b = ld2(Ak + j + 1), c = ld2(Ak + j + 2), d = ld2(Ak + j + 3);
-                S0 = df_fma(a, as_df(sX[j * BLK]), S0);
-                T0 = df_fma(b, as_df(sX[(j + 1) * BLK]), T0);
-                U0 = df_fma(c, as_df(sX[(j + 2) * BLK]), U0);
-                V0 = df_fma(d, as_df(sX[(j + 3) * BLK]), V0);
-                S1 = df_fma(a, as_df(sA0[j * BLK]), S1);
-                T1 = df_fma(b, as_df(sA0[(j + 1) * BLK]), T1);
-                U1 = df_fma(c, as_df(sA0[(j + 2) * BLK]), U1);
-                V1 = df_fma(d, as_df(sA0[(j + 3) * BLK]), V1);
-                S2 = df_fma(a, as_df(sB[j * BLK]), S2);
-                T2 = df_fma(b, as_df(sB[(j + 1) * BLK]), T2);
-                U2 = df_fma(c, as_df(sB[(j + 2) * BLK]), U2);
-                V2 = df_fma(d, as_df(sB[(j + 3) * BLK]), V2);
+            for (; j + 1 < K; j += 2) {
+                const dfl a = ld2(Ak + j), b = ld2(Ak + j + 1);
+                dot_add(S0, a, as_df(sX[j * BLK]));
+                dot_add(T0, b, as_df(sX[(j + 1) * BLK]));
+                dot_add(S1, a, as_df(sA0[j * BLK]));
+                dot_add(T1, b, as_df(sA0[(j + 1) * BLK]));
+                dot_add(S2, a, as_df(sB[j * BLK]));
+                dot_add(T2, b, as_df(sB[(j + 1) * BLK]));
             }
-            for (; j < K; ++j) {
+            if (j < K) {
                 const dfl a = ld2(Ak + j);
-                S0 = df_fma(a, as_df(sX[j * BLK]), S0);
-                S1 = df_fma(a, as_df(sA0[j * BLK]), S1);
-                S2 = df_fma(a, as_df(sB[j * BLK]), S2);
+                dot_add(S0, a, as_df(sX[j * BLK]));
+                dot_add(S1, a, as_df(sA0[j * BLK]));
+                dot_add(S2, a, as_df(sB[j * BLK]));
             }
-            S0 = df_add(df_add(S0, T0), df_add(U0, V0));
-            S1 = df_add(df_add(S1, T1), df_add(U1, V1));
-            S2 = df_add(df_add(S2, T2), df_add(U2, V2));
-            const dfl den = df_fma(sig, df_fma(sig, S2, dscale(S1, 2.0f)), S0);
+            const dfl W0 = df_add(dot_value(S0), dot_value(T0));
+            const dfl W1 = df_add(dot_value(S1), dot_value(T1));
+            const dfl W2 = df_add(dot_value(S2), dot_value(T2));
+            const dfl den = df_fma(sig, df_fma(sig, W2, dscale(W1, 2.0f)), W0);
             const dfl muk = df_exp(lnmu, etab);
             mu = df_add(mu, df_div(df_mul(as_df(sX[k * BLK]), muk), den));
         }
