@@ -14,7 +14,9 @@ cudaError_t launch_jvp(const DevMech& m, int64_t n, int64_t ld, const double* T,
                        double* hrr, double* d_omega, double* d_hrr, cudaStream_t s, int rhs) {
     static_assert(kDfTabBytes <= kMathTabDoubles * sizeof(double), "table space");
     if (rhs) return launch_jvp_rhs(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
-    if (omega) return launch_o<true, false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
+    // the primal outputs (either one) take the variant that sums them; without them the kernel
+    // skips the heat-release sum
+    if (omega || hrr) return launch_o<true, false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
     return launch_o<false, false>(m, n, ld, T, p, Y, dlnA, vT, vY, omega, hrr, d_omega, d_hrr, s);
 }
 

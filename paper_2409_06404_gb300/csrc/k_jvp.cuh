@@ -176,7 +176,7 @@ __device__ __forceinline__ void jvp_reaction(const DevMech& m, int r, const doub
             sD[k * BLK] = fma(x.nud[kMaxSide + e], dqs, sD[k * BLK]);
             if (OMEGA) sW[k * BLK] = fma(x.nud[kMaxSide + e], q, sW[k * BLK]);
         }
-    acc.h = fma(q, sumh, acc.h);
+    if constexpr (OMEGA || RHS) acc.h = fma(q, sumh, acc.h);     // the primal heat release
     acc.cp = fma(q, sumcp, acc.cp);
     acc.dh = fma(dq, sumh, acc.dh);
 }
@@ -262,7 +262,7 @@ __device__ __forceinline__ void jvp_reaction_log(const DevMech& m, int r, const 
         scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sW, q);
     }
     const double sumh = df_to_d(dH);
-    acc.h = fma(q, sumh, acc.h);
+    if constexpr (OMEGA || RHS) acc.h = fma(q, sumh, acc.h);     // the primal heat release
     acc.cp = fma(q, df_to_d(dCp), acc.cp);
     acc.dh = fma(dq, sumh, acc.dh);
 }
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(BLK * NP, 512 / (BLK * NP)) jvp_kernel(const D
         }
         if (live) {
             d_omega[(int64_t)k * ld + i] = dw;
-            if (OMEGA) omega[(int64_t)k * ld + i] = w;
+            if (OMEGA && omega) omega[(int64_t)k * ld + i] = w;
         }
     }
     if constexpr (NP > 1) {

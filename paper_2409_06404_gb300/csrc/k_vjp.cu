@@ -228,6 +228,7 @@ __device__ __forceinline__ void vjp_reaction(const DevMech& m, int r, const doub
 // row holds ln C_k as pairs; with F the falloff factor (1 but for Troe reactions)
 //   q_f = exp(ln k_f + ln F + sum_reac nu ln C),  q_r = exp(ln k_f + ln F - ln K_c + sum_prod nu ln C),
 // so d q_c / d ln C_k = nu (q_f or -q_r), d q_c / d (ln k_f + ln F) = q_c and d q_c / d ln K_c = q_r.
+// The bar_omega_k row holds the cotangents as pairs (the reaction's sum nu bar_omega in pairs).
 // The species rows accumulate S_k = Cbar_k C_k (the cotangent of ln C_k), turned into
 // Cbar_k = S_k/C_k once per point at the end; the third-body terms Mbar (eps - 1) enter as
 // Mbar (eps - 1) C_k.  The temperature cotangent is accumulated times T (TbarT), term by term:
@@ -243,8 +244,10 @@ __device__ __forceinline__ double vjp_reaction_log(const DevMech& m, int r, cons
                                                    const DfTab& dt, double& TbarT) {
     constexpr int BLK = kVjpBlk;
     const Rxn x = load_rxn(m.rxn + r);
-    const double wsum = gather_side<BLK>(x.sp, x.nud, x.nr, sWb) +
-                        gather_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sWb);
+    // sum_k nu_k bar_omega_k (products minus reactants) from the pair row, one conversion
+    const float2* sW2 = reinterpret_cast<const float2*>(sWb);
+    const double wsum = df_to_d(df_add(side_sum_df<BLK>(sW2, x.sp + kMaxSide, x.nu + kMaxSide, x.np),
+                                       df_neg(side_sum_df<BLK>(sW2, x.sp, x.nu, x.nr))));
     const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
     const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
     dfl dG, dH, dCp;
@@ -466,19 +469,24 @@ __global__ void __launch_bounds__(kVjpBlk * NP, 384 / (kVjpBlk * NP)) vjp_kernel
         const double rho = Q.pRT / s;
         // logarithmic form unless a point of the tile has a mass fraction outside 2^+-100 (zero,
         // negative, tiny or non-finite): then the products in double (C_k in the row)
+        // (and the logarithmic form sums the cotangents bar_omega_k in pairs: each within 2^+-100
+        // or zero)
         bool bad = false;
-        for (int k = part; k < K; k += NP) bad |= !log_form_ok(Y[(int64_t)k * ld + i]);
+        for (int k = part; k < K; k += NP)
+            bad |= !log_form_ok(Y[(int64_t)k * ld + i]) || !pair_range_ok(bar_omega[(int64_t)k * ld + i]);
         const bool direct = __syncthreads_or(bad) != 0;
         Q.pRTd = df_split(Q.pRT);
         for (int k = part; k < K; k += NP) {
             const double c = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
+            const double wb = bar_omega[(int64_t)k * ld + i];
             if (direct) {
                 sC[k * BLK] = c;
+                sWb[k * BLK] = wb;
             } else {
-                const dfl l = log_df(c, dt.rc, dt.lc);
+                const dfl l = log_df(c, dt.rc, dt.lc), w = df_split(wb);
                 reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
+                reinterpret_cast<float2*>(sWb)[k * BLK] = make_float2(w.h, w.l);
             }
-            sWb[k * BLK] = bar_omega[(int64_t)k * ld + i];
         }
         for (int k = part; k < K; k += NP) sB[k * BLK] = 0.0;
         __syncthreads();
