@@ -133,13 +133,28 @@ __global__ void __launch_bounds__(BLK * NP) transport_kernel(const DevMech m, co
     F* sB = smem + (size_t)2 * K * BLK + slot;   // prefix sums of Y, then X_k tau_k^2
     using Tb = Tab<F>;
 
+    // The mixed form (F = float) keeps every step in single precision: inputs rounded to float and
+    // outputs widened by integer operations, the mole fractions, numerators and quotients in
+    // float, so it issues no FP64-pipe instruction (the double form keeps its sums in double).
+    constexpr bool kF32 = sizeof(F) == sizeof(float);
     const double Ti = T[i];
-    const F L = (F)flog(Ti, mt);
+    F L;
+    if constexpr (kF32)
+        L = logf(narrow(Ti));
+    else
+        L = flog(Ti, mt);
     // mole fractions
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
-    const double Wbar = 1.0 / s;
-    for (int k = part; k < K; k += NP) sX[k * BLK] = (F)(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar);
+    if constexpr (kF32) {
+        float s = 0.0f;
+        for (int k = 0; k < K; ++k) s = fmaf(narrow(Y[(int64_t)k * ld + i]), __ldg(m.f_invW + k), s);
+        const float Wbar = 1.0f / s;
+        for (int k = part; k < K; k += NP) sX[k * BLK] = narrow(Y[(int64_t)k * ld + i]) * __ldg(m.f_invW + k) * Wbar;
+    } else {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
+        const double Wbar = 1.0 / s;
+        for (int k = part; k < K; k += NP) sX[k * BLK] = (F)(Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * Wbar);
+    }
 
     // ---- diffusion: sum_{j != k} X_j / D_jk(p_ref), one exponential per pair; the pressure
     // factor p/p_ref multiplies the finished sums
@@ -160,21 +175,40 @@ __global__ void __launch_bounds__(BLK * NP) transport_kernel(const DevMech m, co
                                     sA);
         if (NP > 1) __syncthreads();
         // numerators sum_{j != k} Y_j from prefix and suffix sums (no 1 - Y_k cancellation)
-        const double pscale = p[i] / m.p_ref;
-        double pre = 0.0;
-        for (int k = 0; k < K; ++k) {
-            if (NP == 1 || k % NP == part) sB[k * BLK] = (F)pre;
-            pre += Y[(int64_t)k * ld + i];
-        }
-        double suf = 0.0;
-        for (int k = K - 1; k >= 0; --k) {
-            if (NP == 1 || k % NP == part) {
-                const double num = (double)sB[k * BLK] + suf;
-                double den = (double)sA[k * BLK] * pscale;
-                if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
-                if (live) Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
+        if constexpr (kF32) {
+            const float pscale = narrow(p[i]) / narrow(m.p_ref);
+            float pre = 0.0f;
+            for (int k = 0; k < K; ++k) {
+                if (NP == 1 || k % NP == part) sB[k * BLK] = pre;
+                pre += narrow(Y[(int64_t)k * ld + i]);
             }
-            suf += Y[(int64_t)k * ld + i];
+            float suf = 0.0f;
+            for (int k = K - 1; k >= 0; --k) {
+                if (NP == 1 || k % NP == part) {
+                    const float num = sB[k * BLK] + suf;
+                    float den = sA[k * BLK] * pscale;
+                    if (den < 1.17549435e-38f) den = 1.17549435e-38f;
+                    if (live) Dmix[(int64_t)k * ld + i] = num == 0.0f ? 0.0 : widen(num / den);
+                }
+                suf += narrow(Y[(int64_t)k * ld + i]);
+            }
+        } else {
+            const double pscale = p[i] / m.p_ref;
+            double pre = 0.0;
+            for (int k = 0; k < K; ++k) {
+                if (NP == 1 || k % NP == part) sB[k * BLK] = (F)pre;
+                pre += Y[(int64_t)k * ld + i];
+            }
+            double suf = 0.0;
+            for (int k = K - 1; k >= 0; --k) {
+                if (NP == 1 || k % NP == part) {
+                    const double num = (double)sB[k * BLK] + suf;
+                    double den = (double)sA[k * BLK] * pscale;
+                    if (den < 2.2250738585072014e-308) den = 2.2250738585072014e-308;
+                    if (live) Dmix[(int64_t)k * ld + i] = num == 0.0 ? 0.0 : num / den;
+                }
+                suf += Y[(int64_t)k * ld + i];
+            }
         }
     }
 
@@ -232,8 +266,13 @@ __global__ void __launch_bounds__(BLK * NP) transport_kernel(const DevMech m, co
         }
     }
     if (live) {
-        if (lam_out) lam_out[i] = (double)(F(0.5) * (s1 + F(1) / s2));
-        if (mu_out) mu_out[i] = (double)mu;
+        if constexpr (kF32) {
+            if (lam_out) lam_out[i] = widen(0.5f * (s1 + 1.0f / s2));
+            if (mu_out) mu_out[i] = widen(mu);
+        } else {
+            if (lam_out) lam_out[i] = (double)(F(0.5) * (s1 + F(1) / s2));
+            if (mu_out) mu_out[i] = (double)mu;
+        }
     }
 }
 
