@@ -926,7 +926,8 @@ def run_ours(args):
                    "step": names, "forms_after_steps": list(forms),
                    "l2": "inputs (0.92 GB) larger than L2; no flush",
                    "arithmetic": "FP64 form (NK_FP64): exponent chains (ln k_f, the Gibbs and enthalpy sums, ln K_c, "
-                                 "the logarithms of the concentration products) and all of transport in double-float "
+                                 "the Troe falloff chain, the third-body sums, the logarithms of the concentration "
+                                 "products) and all of transport in double-float "
                                  "pairs (48-bit) on the FP32 pipe; the rate terms' values, the forward-minus-reverse "
                                  "differences and every accumulation in double; results within 1e-10 of the FP64 "
                                  "definitions.  The all-double form is fp64_native_value"},

@@ -369,10 +369,12 @@ __device__ __forceinline__ void for_rounds(const DevMech& m, int g, int part, Fn
     const int32_t* S = EFF ? (NP == 2 ? m.rschedv2 : m.rschedv4) : (NP == 2 ? m.rsched2 : m.rsched4);
     const int rd0 = EFF ? (NP == 2 ? m.rrndv2[g] : m.rrndv4[g]) : (NP == 2 ? m.rrnd2[g] : m.rrnd4[g]);
     const int rd1 = EFF ? (NP == 2 ? m.rrndv2[g + 1] : m.rrndv4[g + 1]) : (NP == 2 ? m.rrnd2[g + 1] : m.rrnd4[g + 1]);
+    int r = rd0 < rd1 ? __ldg(S + rd0 * NP + part) : -1;
     for (int rd = rd0; rd < rd1; ++rd) {
-        const int r = __ldg(S + rd * NP + part);
+        const int rn = rd + 1 < rd1 ? __ldg(S + (rd + 1) * NP + part) : -1;   // the next round's, early
         if (r >= 0) f(r);
         __syncthreads();
+        r = rn;
     }
 }
 
