@@ -758,7 +758,7 @@ def run_ours(args):
     nk.mechanism_jit(m)
     jit_compile_s = time.perf_counter() - t_jit
     launches_per_step = {"thermo": 1, "rates_fp64": 1, "transport_fp64": 1, "rates_mixed": 1,
-                         "transport_mixed": 1, "jvp": 1, "vjp": 2}
+                         "transport_mixed": 1, "jvp": 1, "vjp": 3}
     names = list(rows)
 
     for _ in range(args.warmup):

@@ -489,9 +489,9 @@ nk_status nk_rates_vjp(const nk_mech* mech, int64_t n, int64_t ld, const double*
  * Same arguments, results and errors as nk_rates_vjp, except that the per-block ln A partial
  * sums go to a fixed scratch array compiled into the library (2^20 doubles = 8 MiB, held on
  * every GPU that loads the library until the process exits).  g_lnA needs one R-vector per
- * block of the VJP's persistent grid (SMs x resident VJP blocks, at most the blocks n needs):
- * on a 152-SM GB300 that allows about 2,300 reactions when 3 VJP blocks are resident per SM
- * (53 species), about 1,700 with 4.  nk_rates_vjp_workspace gives the exact bytes a call
+ * block of the VJP's two persistent passes (SMs x resident blocks of each, at most the blocks n
+ * needs): on a 152-SM GB300 that allows about 980 reactions with 4 + 3 resident blocks per SM
+ * (53 species).  nk_rates_vjp_workspace gives the exact bytes a call
  * needs; above 8 MiB the call returns NK_EUNSUPPORTED and enqueues nothing.  The first call on
  * a device looks up the scratch address on that device (make that first call before any
  * stream capture); later calls read the cached pointer.  The cache lives as long as the

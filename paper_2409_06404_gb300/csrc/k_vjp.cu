@@ -423,8 +423,11 @@ size_t vjp_smem(int K, int R, int np, bool want_g) {
            (size_t)3 * K * kVjpBlk * sizeof(double);
 }
 
-template <int NP, bool WANT_G, bool HB>
-__global__ void __launch_bounds__(kVjpBlk * NP, 384 / (kVjpBlk * NP)) vjp_kernel(const DevMech m, const int64_t n, const int64_t ld,
+// PASS 0 takes the tiles of the logarithmic form and skips the others; PASS 1 takes only those
+// (products in double).  Each pass alone compiles to fewer registers than both paths together:
+// the logarithmic pass runs four blocks of 4 warps per SM, the fallback pass three.
+template <int NP, bool WANT_G, bool HB, int PASS>
+__global__ void __launch_bounds__(kVjpBlk * NP, (PASS == 0 ? 512 : 384) / (kVjpBlk * NP)) vjp_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                            const double* __restrict__ T, const double* __restrict__ p,
                                                            const double* __restrict__ Y,
                                                            const double* __restrict__ dlnA,
@@ -457,6 +460,16 @@ __global__ void __launch_bounds__(kVjpBlk * NP, 384 / (kVjpBlk * NP)) vjp_kernel
         VjpPoint Q;
         Q.valid = i0 < n;
         const int64_t i = Q.valid ? i0 : n - 1;                   // idle lanes shadow the last point
+        // logarithmic form unless a point of the tile has a mass fraction outside 2^+-100 (zero,
+        // negative, tiny or non-finite): then the products in double (C_k in the row)
+        // (and the logarithmic form sums the cotangents bar_omega_k in pairs: each within 2^+-100
+        // or zero).  Decided first, so a pass skips a tile after these loads alone.
+        bool bad = false;
+        for (int k = part; k < K; k += NP)
+            bad |= !log_form_ok(Y[(int64_t)k * ld + i]) || !pair_range_ok(bar_omega[(int64_t)k * ld + i]);
+        const bool dvote = __syncthreads_or(bad) != 0;
+        if (PASS == 0 ? dvote : !dvote) continue;                 // the other pass takes this tile
+        constexpr bool direct = PASS == 1;
         const double Ti = T[i];
         Q.invT = 1.0 / Ti;
         Q.pRT = p[i] * Q.invT * kInvR;
@@ -467,14 +480,6 @@ __global__ void __launch_bounds__(kVjpBlk * NP, 384 / (kVjpBlk * NP)) vjp_kernel
         double s = 0.0;
         for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
         const double rho = Q.pRT / s;
-        // logarithmic form unless a point of the tile has a mass fraction outside 2^+-100 (zero,
-        // negative, tiny or non-finite): then the products in double (C_k in the row)
-        // (and the logarithmic form sums the cotangents bar_omega_k in pairs: each within 2^+-100
-        // or zero)
-        bool bad = false;
-        for (int k = part; k < K; k += NP)
-            bad |= !log_form_ok(Y[(int64_t)k * ld + i]) || !pair_range_ok(bar_omega[(int64_t)k * ld + i]);
-        const bool direct = __syncthreads_or(bad) != 0;
         Q.pRTd = df_split(Q.pRT);
         for (int k = part; k < K; k += NP) {
             const double c = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho;
@@ -563,22 +568,50 @@ __global__ void reduce_blocks_kernel(const double* __restrict__ ws, int nblocks,
 // ---------------------------------------------------------------- launch plan
 constexpr int kParts[] = {1, 2, 4};
 
-template <bool WANT_G, bool HB>
+template <bool WANT_G, bool HB, int PASS>
 const void* kernel_ptr(int c) {
     switch (c) {
-        case 0: return (const void*)vjp_kernel<1, WANT_G, HB>;
-        case 1: return (const void*)vjp_kernel<2, WANT_G, HB>;
-        default: return (const void*)vjp_kernel<4, WANT_G, HB>;
+        case 0: return (const void*)vjp_kernel<1, WANT_G, HB, PASS>;
+        case 1: return (const void*)vjp_kernel<2, WANT_G, HB, PASS>;
+        default: return (const void*)vjp_kernel<4, WANT_G, HB, PASS>;
     }
 }
 
+// Per pass: the parts per point with the most resident warps and a grid of resident blocks (the
+// fallback pass finds work only in tiles with mass fractions or cotangents outside the pairs'
+// range; it reads the rest's Y and bar_omega once to see that).  The ln A partial sums of the two
+// passes' blocks lie one after the other in the workspace.
 struct VjpPlan {
     int dev, K, R, variant;
-    int parts_idx;   // index into kParts
-    int grid_cap;    // resident blocks on the device (SMs x blocks per SM)
+    int parts_idx[2];   // index into kParts, per pass
+    int grid_cap[2];    // blocks of each pass
 };
 std::mutex g_plan_mu;
 std::vector<VjpPlan> g_plans;
+
+template <bool WANT_G, bool HB, int PASS>
+bool plan_pass(int K, int R, int sms, int per_block, int& parts_idx, int& blocks_per_sm) {
+    int best = -1, best_warps = 0;
+    for (int c = 0; c < 3; ++c) {
+        const int np = kParts[c];
+        if (np > 1 && 2 * np > K) continue;
+        const size_t bytes = vjp_smem(K, R, np, WANT_G);
+        if (bytes > (size_t)per_block) continue;
+        const void* kern = kernel_ptr<WANT_G, HB, PASS>(c);
+        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kVjpBlk * np, bytes) != cudaSuccess)
+            continue;
+        if (blocks * np > best_warps) {
+            best_warps = blocks * np;
+            blocks_per_sm = blocks;
+            best = c;
+        }
+    }
+    parts_idx = best;
+    (void)sms;
+    return best >= 0;
+}
 
 template <bool WANT_G, bool HB>
 bool plan_variant(int K, int R, VjpPlan& out) {
@@ -596,25 +629,10 @@ bool plan_variant(int K, int R, VjpPlan& out) {
     int per_block = 0, sms = 0;
     cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int best = -1, best_warps = 0, best_blocks = 0;
-    for (int c = 0; c < 3; ++c) {
-        const int np = kParts[c];
-        if (np > 1 && 2 * np > K) continue;
-        const size_t bytes = vjp_smem(K, R, np, WANT_G);
-        if (bytes > (size_t)per_block) continue;
-        const void* kern = kernel_ptr<WANT_G, HB>(c);
-        if (ensure_smem(kern, bytes) != cudaSuccess) continue;
-        int blocks = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kVjpBlk * np, bytes) != cudaSuccess)
-            continue;
-        if (blocks * np > best_warps) {
-            best_warps = blocks * np;
-            best_blocks = blocks;
-            best = c;
-        }
-    }
-    if (best < 0) return false;
-    out = VjpPlan{dev, K, R, variant, best, sms * best_blocks};
+    int p0 = -1, p1 = -1, b0 = 0, b1 = 0;
+    if (!plan_pass<WANT_G, HB, 0>(K, R, sms, per_block, p0, b0)) return false;
+    if (!plan_pass<WANT_G, HB, 1>(K, R, sms, per_block, p1, b1)) return false;
+    out = VjpPlan{dev, K, R, variant, {p0, p1}, {sms * b0, sms * b1}};
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans.push_back(out);
     return true;
@@ -625,35 +643,48 @@ bool plan_for(const DevMech& m, bool want_g, bool hb, VjpPlan& out) {
     return hb ? plan_variant<false, true>(m.K, m.R, out) : plan_variant<false, false>(m.K, m.R, out);
 }
 
-int64_t vjp_grid(const VjpPlan& pl, int64_t n) {
+int64_t vjp_grid(const VjpPlan& pl, int pass, int64_t n) {
     const int64_t tiles = (n + kVjpBlk - 1) / kVjpBlk;
-    return tiles < pl.grid_cap ? tiles : pl.grid_cap;
+    return tiles < pl.grid_cap[pass] ? tiles : pl.grid_cap[pass];
+}
+
+// blocks of both passes, the ln A partial sums' rows in the workspace
+int64_t vjp_blocks(const VjpPlan& pl, int64_t n) { return vjp_grid(pl, 0, n) + vjp_grid(pl, 1, n); }
+
+template <bool WANT_G, bool HB, int PASS>
+cudaError_t launch_pass(const VjpPlan& pl, const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                        const double* Y, const double* dlnA, const double* bar_omega, const double* bar_hrr,
+                        double* gT, double* gY, double* ws, cudaStream_t s) {
+    const int np = kParts[pl.parts_idx[PASS]];
+    const size_t smem = vjp_smem(m.K, m.R, np, WANT_G);
+    const void* kp = kernel_ptr<WANT_G, HB, PASS>(pl.parts_idx[PASS]);
+    cudaError_t e = ensure_smem(kp, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)vjp_grid(pl, PASS, n);
+    switch (np) {
+        case 1:
+            vjp_kernel<1, WANT_G, HB, PASS><<<grid, kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr,
+                                                                        gT, gY, ws);
+            break;
+        case 2:
+            vjp_kernel<2, WANT_G, HB, PASS><<<grid, 2 * kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega,
+                                                                            bar_hrr, gT, gY, ws);
+            break;
+        default:
+            vjp_kernel<4, WANT_G, HB, PASS><<<grid, 4 * kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega,
+                                                                            bar_hrr, gT, gY, ws);
+    }
+    return cudaGetLastError();
 }
 
 template <bool WANT_G, bool HB>
 cudaError_t launch_v(const VjpPlan& pl, const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                      const double* Y, const double* dlnA, const double* bar_omega, const double* bar_hrr, double* gT,
                      double* gY, double* ws, cudaStream_t s) {
-    const int np = kParts[pl.parts_idx];
-    const size_t smem = vjp_smem(m.K, m.R, np, WANT_G);
-    const void* kp = kernel_ptr<WANT_G, HB>(pl.parts_idx);
-    cudaError_t e = ensure_smem(kp, smem);
+    cudaError_t e = launch_pass<WANT_G, HB, 0>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, ws, s);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)vjp_grid(pl, n);
-    switch (np) {
-        case 1:
-            vjp_kernel<1, WANT_G, HB><<<grid, kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT,
-                                                                  gY, ws);
-            break;
-        case 2:
-            vjp_kernel<2, WANT_G, HB><<<grid, 2 * kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr,
-                                                                      gT, gY, ws);
-            break;
-        default:
-            vjp_kernel<4, WANT_G, HB><<<grid, 4 * kVjpBlk, smem, s>>>(m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr,
-                                                                      gT, gY, ws);
-    }
-    return cudaGetLastError();
+    double* ws1 = ws ? ws + (size_t)vjp_grid(pl, 0, n) * m.R : nullptr;
+    return launch_pass<WANT_G, HB, 1>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, ws1, s);
 }
 
 }  // namespace
@@ -694,8 +725,8 @@ size_t vjp_workspace_bytes(const DevMech& m, int64_t n) {
     if (!plan_for(m, true, false, pl)) return 0;
     VjpPlan pl2;
     if (!plan_for(m, true, true, pl2)) return 0;
-    const int64_t grid = std::max(vjp_grid(pl, n), vjp_grid(pl2, n));   // either cotangent set
-    return (size_t)grid * m.R * sizeof(double);
+    const int64_t blocks = std::max(vjp_blocks(pl, n), vjp_blocks(pl2, n));   // either cotangent set
+    return (size_t)blocks * m.R * sizeof(double);
 }
 
 cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
@@ -714,7 +745,7 @@ cudaError_t launch_vjp(const DevMech& m, int64_t n, int64_t ld, const double* T,
         e = hb ? launch_v<false, true>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, nullptr, s)
                : launch_v<false, false>(pl, m, n, ld, T, p, Y, dlnA, bar_omega, bar_hrr, gT, gY, nullptr, s);
     if (e != cudaSuccess || !want_g) return e;
-    reduce_blocks_kernel<<<(m.R + 127) / 128, 128, 0, s>>>(wsd, (int)vjp_grid(pl, n), m.rxn, m.R, g_lnA);
+    reduce_blocks_kernel<<<(m.R + 127) / 128, 128, 0, s>>>(wsd, (int)vjp_blocks(pl, n), m.rxn, m.R, g_lnA);
     return cudaGetLastError();
 }
 
