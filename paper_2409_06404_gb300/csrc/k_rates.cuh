@@ -435,8 +435,15 @@ __host__ __device__ constexpr int shared_rows() {
 // the warps.
 //
 // RHS: write the implicit-stage sources instead: omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p).
-template <int BLK, int NP, int PREC, bool RHS>
-__global__ void __launch_bounds__(BLK * NP, 640 / (BLK * NP)) rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
+//
+// PASS (kDF and kMixed): 0 takes the blocks of the logarithmic form and skips the others, 1 takes
+// only those (a negative concentration: products in double), so the logarithmic pass compiles
+// without the double path's registers and runs six blocks of 4 warps per SM instead of five.  The
+// fallback pass leaves at once where no mass fraction of the block is negative.  The native form
+// has one pass (0) over every block.
+template <int BLK, int NP, int PREC, bool RHS, int PASS>
+__global__ void __launch_bounds__(BLK * NP, (PREC != kNative && PASS == 0 ? 768 : 640) / (BLK * NP))
+    rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                          const double* __restrict__ T, const double* __restrict__ p,
                                                          const double* __restrict__ Y,
                                                          const double* __restrict__ dlnA,
@@ -452,9 +459,18 @@ __global__ void __launch_bounds__(BLK * NP, 640 / (BLK * NP)) rates_kernel(const
     const int K = m.K;
     const int slot = threadIdx.x % BLK, part = threadIdx.x / BLK;
     const int64_t i0 = (int64_t)blockIdx.x * BLK + slot;
-    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no barrier below)
+    if (NP == 1 && i0 >= n) return;              // (NP = 1 has no block barrier below)
     const bool live = i0 < n;
     const int64_t i = live ? i0 : n - 1;         // idle slots of the last block recompute point n-1
+    if constexpr (PREC != kNative && PASS == 1) {
+        // no negative mass fraction and positive T and p in the block (its warp for NP = 1): no
+        // concentration is negative (rho > 0), the logarithmic pass took it; anything else goes
+        // on to the exact vote below
+        bool anyneg = !(T[i] > 0.0 && p[i] > 0.0);
+        for (int k = part; k < K; k += NP) anyneg |= Y[(int64_t)k * ld + i] < 0.0;
+        const bool some = NP > 1 ? __syncthreads_or(anyneg) != 0 : __any_sync(__activemask(), anyneg);
+        if (!some) return;
+    }
     double* sC = smem + kMathTabDoubles + slot;                       // C_k       at sC[k * BLK]
     double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (native form)
     double* sW0 = smem + kMathTabDoubles + (size_t)shared_rows<PREC>() * K * BLK + slot;
@@ -493,15 +509,19 @@ __global__ void __launch_bounds__(BLK * NP, 640 / (BLK * NP)) rates_kernel(const
         }
     }
     for (int k = part; k < K; k += NP) sW[k * BLK] = 0.0;
-    bool direct = false;
+    bool vote = false;
     if constexpr (NP > 1) {
         if constexpr (PREC == kNative)
             __syncthreads();
         else
-            direct = __syncthreads_or(neg) != 0;
+            vote = __syncthreads_or(neg) != 0;
     } else if constexpr (PREC != kNative) {
-        direct = __any_sync(__activemask(), neg);
+        vote = __any_sync(__activemask(), neg);
     }
+    if constexpr (PREC != kNative) {
+        if (PASS == 0 ? vote : !vote) return;     // the other pass takes this block
+    }
+    constexpr bool direct = PREC != kNative && PASS == 1;
 
     if constexpr (NP == 1) {
         const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
@@ -560,9 +580,9 @@ struct Shape {
 constexpr Shape kShapes[] = {{32, 1}, {64, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <int PREC, bool RHS, int S>
+template <int PREC, bool RHS, int S, int PASS = 0>
 constexpr auto kernel_of() {
-    return rates_kernel<kShapes[S].blk, kShapes[S].np, PREC, RHS>;
+    return rates_kernel<kShapes[S].blk, kShapes[S].np, PREC, RHS, PASS>;
 }
 
 template <int PREC, bool RHS, int... S>
@@ -571,6 +591,7 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
     return ptrs[idx];
 }
 
+// The shape's logarithmic pass, then (kDF, kMixed) its fallback pass on the same stream.
 template <int PREC, bool RHS, int... S>
 cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
                        const double* T, const double* p, const double* Y, const double* dlnA, double* omega,
@@ -578,11 +599,17 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech&
     cudaError_t e = cudaErrorInvalidConfiguration;
     ((S == idx ? (void)(e = [&] {
         constexpr Shape sh = kShapes[S];
-        auto kern = kernel_of<PREC, RHS, S>();
+        const unsigned grid = (unsigned)((n + sh.blk - 1) / sh.blk);
+        auto kern = kernel_of<PREC, RHS, S, 0>();
         cudaError_t r = ensure_smem((const void*)kern, smem);
         if (r != cudaSuccess) return r;
-        kern<<<(unsigned)((n + sh.blk - 1) / sh.blk), sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega,
-                                                                                  hrr);
+        kern<<<grid, sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega, hrr);
+        r = cudaGetLastError();
+        if (r != cudaSuccess || PREC == kNative) return r;
+        auto kern1 = kernel_of<PREC, RHS, S, 1>();
+        r = ensure_smem((const void*)kern1, smem);
+        if (r != cudaSuccess) return r;
+        kern1<<<grid, sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega, hrr);
         return cudaGetLastError();
     }())
                : (void)0),
