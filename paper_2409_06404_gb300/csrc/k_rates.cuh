@@ -37,21 +37,6 @@ namespace {
 
 enum { kNative = 0, kMixed = 1, kDF = 2 };
 
-// exp of a single-precision argument, returned in double: x = n ln2 + r (Cody-Waite two-term
-// split of ln 2), expf(r) with |r| <= ln2/2, and 2^n added to the exponent field of the
-// double, so results beyond the single-precision range stay representable.
-__device__ __forceinline__ double exp_f32_to_f64(float x) {
-    if (x < -700.0f) return 0.0;
-    if (x > 700.0f) return __longlong_as_double(0x7ff0000000000000LL);
-    const float kd = __fmaf_rn(x, 1.44269504089f, 12582912.0f);   // 1.5 * 2^23 shifter: n in the low bits
-    const int ni = __float_as_int(kd) - 0x4B400000;
-    const float nf = __fsub_rn(kd, 12582912.0f);
-    float r = fmaf(nf, -0.693359375f, x);
-    r = fmaf(nf, 2.12194440054690583e-4f, r);
-    const double e = (double)expf(r);
-    return __longlong_as_double(__double_as_longlong(e) + ((long long)ni << 52));
-}
-
 // Per-point quantities shared by all reactions.
 struct Pt {
     double T, lnT, invT, pRT, lnP0RT;
@@ -180,79 +165,49 @@ __device__ __forceinline__ void products(const Rxn& x, const double* sC, double&
 }
 
 // Logarithmic form of the concentration products (kDF and kMixed forms).  The C_k row holds
-// ln C_k as pairs (a zero concentration as -2^100, whose exponential is 0), and each side's
+// ln |C_k| as pairs (a zero concentration as -2^100, whose exponential is 0), and each side's
 // product enters its rate term through the exponent:
 //   q_f = exp(ln k_f + sum_reactants nu ln C),  q_r = exp(ln k_f - ln K_c + sum_products nu ln C),
 // one pair exponential each (as k_f and k_r alone took), so no concentration product is formed
 // in double: the FP64 pipe keeps the exponentials' final additions, the forward-minus-reverse
-// difference, [M] and the scatter.  A block with a negative concentration (a negative mass
-// fraction) takes the products in double instead, from the state (Conc).
-// The point's concentrations C_k = rho Y_k / W_k from the state (the products in double).
-struct Conc {
-    const double* Y;
-    const double* invW;
-    int64_t ld, i;
-    double rho;
-    __device__ __forceinline__ double operator()(int k) const {
-        return Y[(int64_t)k * ld + i] * __ldg(invW + k) * rho;
-    }
-};
+// difference, [M] and the scatter.  A negative concentration (a negative mass fraction) enters
+// by its magnitude, with its sign in a byte row beside the logarithms (SG, the kernel's second
+// pass): a side's product changes sign with every factor of odd exponent that is negative, and
+// [M] takes the signed C_j.
 
-// Both sides' products in double from the state (Conc).
-__device__ __forceinline__ void products_direct(const Rxn& x, const Conc& cs, double& fw, double& rv) {
-    {
-        const double c = cs(x.sp[0]);
-        fw = c;
-        for (int j = 1; j < x.nu[0]; ++j) fw *= c;
-    }
+// the sign of one side's concentration product: 1 if an odd number of its factors (counted with
+// their integer exponents) are negative
+template <int BLK>
+__device__ __forceinline__ int side_sign(const uint8_t* sg, const int* sp, const int* nu, int ne) {
+    int s = sg[sp[0] * BLK] & nu[0];
 #pragma unroll
     for (int e = 1; e < kMaxSide; ++e)
-        if (e < x.nr) {
-            const double c = cs(x.sp[e]);
-            for (int j = 0; j < x.nu[e]; ++j) fw *= c;
-        }
-    {
-        const double c = cs(x.sp[kMaxSide]);
-        rv = c;
-        for (int j = 1; j < x.nu[kMaxSide]; ++j) rv *= c;
-    }
-#pragma unroll
-    for (int e = 1; e < kMaxSide; ++e)
-        if (e < x.np) {
-            const double c = cs(x.sp[kMaxSide + e]);
-            for (int j = 0; j < x.nu[kMaxSide + e]; ++j) rv *= c;
-        }
+        if (e < ne) s ^= sg[sp[e] * BLK] & nu[e];
+    return s & 1;
 }
 
-// [M] = p/(RT) + sum (eps - 1) C_j: C_j from the logarithms (LOG) or the state
-template <int BLK, bool LOG>
-__device__ __forceinline__ double third_body(const DevMech& m, const Rxn& x, const float2* sL, const Conc& cs,
-                                             const Pt& P, const DfTab& dt) {
-    double M = P.pRT;
+// [M] = p/(RT) + sum (eps - 1) C_j as a pair from the logarithms ln |C_j| (and, SG, the signs;
+// terms below the float range drop out: they are under 1e-37 against p/(RT))
+template <int BLK, bool SG>
+__device__ __forceinline__ dfl third_body_pair(const DevMech& m, const Rxn& x, const float2* sL, const uint8_t* sg,
+                                               const Pt& P, const DfTab& dt) {
+    dfl M = P.pRTd;
     for (int j = x.eff0; j < x.eff1; ++j) {
         const int k = __ldg(m.eff_sp + j);
-        M = fma(__ldg(m.eff_m1 + j), LOG ? exp_df_d(dfl_of(sL[k * BLK]), dt.e2) : cs(k), M);
+        dfl c = exp_df_pair(dfl_of(sL[k * BLK]), dt.e2);
+        if (SG && sg[k * BLK]) c = df_neg(c);
+        M = df_fma(dfl_of(__ldg(m.df_eff_m1 + j)), c, M);
     }
-    return M;
-}
-
-// [M] = p/(RT) + sum (eps - 1) C_j as a pair from the logarithms ln C_j (terms below the float
-// range drop out: they are under 1e-37 against p/(RT))
-template <int BLK>
-__device__ __forceinline__ dfl third_body_pair(const DevMech& m, const Rxn& x, const float2* sL, const Pt& P,
-                                               const DfTab& dt) {
-    dfl M = P.pRTd;
-    for (int j = x.eff0; j < x.eff1; ++j)
-        M = df_fma(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[__ldg(m.eff_sp + j) * BLK]), dt.e2), M);
     return M;
 }
 
 // FP64 form.  The exponent of each rate term, ln k_f (+ ln F, the Troe falloff factor, whose
-// whole chain runs in pairs: troe_log) + the concentration logarithms (LOG) - ln K_c, in pairs;
-// the terms, their difference and the [M] factor of third-body reactions in double.
-template <int BLK, int KIND, bool LOG>
+// whole chain runs in pairs: troe_log) + the concentration logarithms - ln K_c, in pairs; the
+// terms (signed by the sides' concentration signs, SG), their difference and the [M] factor of
+// third-body reactions in double.
+template <int BLK, int KIND, bool SG>
 __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rxn& x, int r, const float2* sL,
-                                                      const Conc& cs, const Pt& P, const double* dlnA,
+                                                      const uint8_t* sg, const Pt& P, const double* dlnA,
                                                       const DfTab& dt) {
     dfl sumg, unused_h, unused_cp;
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
@@ -263,13 +218,8 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
     double M = 0.0;
     dfl Mp{0.0f, 0.0f};
     if constexpr (KIND != 0) {
-        if constexpr (LOG) {
-            Mp = third_body_pair<BLK>(m, x, sL, P, dt);
-            if (KIND == 1) M = df_to_d(Mp);
-        } else {
-            M = third_body<BLK, false>(m, x, sL, cs, P, dt);
-            if (KIND == 2) Mp = df_split(M);
-        }
+        Mp = third_body_pair<BLK, SG>(m, x, sL, sg, P, dt);
+        if (KIND == 1) M = df_to_d(Mp);
     }
     dfl lnkF = lnkf;                                             // ln k_f + ln F
     bool noF = false;                                            // Troe with [M] = 0: no rate
@@ -281,19 +231,15 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
             lnkF = df_add(lnkf, troe_log(lnPr, troe_cent(m, x.aux, P.tp, dt).L, dt).lnF);
         }
     }
-    double q;
-    if constexpr (LOG) {
-        const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
-        const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
-        q = exp_df_d(df_add(lnkF, sf), dt.e2) - exp_df_d(df_add(df_add(lnkF, df_neg(lnKc)), sb), dt.e2);
-        if (KIND == 2 && noF) q = 0.0;
-    } else {
-        double fw, rv;
-        products_direct(x, cs, fw, rv);
-        double kf = exp_df_d(lnkF, dt.e2), kr = exp_df_d(df_add(lnkF, df_neg(lnKc)), dt.e2);
-        if (KIND == 2 && noF) kf = kr = 0.0;
-        q = fma(kf, fw, -kr * rv);
+    const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+    const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+    double qf = exp_df_d(df_add(lnkF, sf), dt.e2), qr = exp_df_d(df_add(df_add(lnkF, df_neg(lnKc)), sb), dt.e2);
+    if constexpr (SG) {
+        if (side_sign<BLK>(sg, x.sp, x.nu, x.nr)) qf = -qf;
+        if (side_sign<BLK>(sg, x.sp + kMaxSide, x.nu + kMaxSide, x.np)) qr = -qr;
     }
+    double q = qf - qr;
+    if (KIND == 2 && noF) q = 0.0;
     if (KIND == 1) q *= M;
     return q;
 }
@@ -302,9 +248,9 @@ __device__ __forceinline__ double rate_of_progress_df(const DevMech& m, const Rx
 // the reaction's thermo groups in pairs, the exponent sums of the rate terms in pairs (the
 // single-precision ln k_f enters both terms alike, so q keeps the FP64 difference of
 // K_c-consistent terms), the difference in double.
-template <int BLK, int KIND, bool LOG>
+template <int BLK, int KIND, bool SG>
 __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const Rxn& x, int r, const float2* sL,
-                                                         const Conc& cs, const Pt& P, const double* dlnA,
+                                                         const uint8_t* sg, const Pt& P, const double* dlnA,
                                                          const DfTab& dt) {
     dfl sumg, unused_h, unused_cp;
     rxn_thermo<false, false>(m, x.thermo, P.tp, sumg, unused_h, unused_cp);
@@ -313,14 +259,9 @@ __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const
     double M = 0.0;                                              // [M] in double (third-body rows)
     float Mf = 0.0f;                                             // and in float (the falloff)
     if constexpr (KIND != 0) {
-        if constexpr (LOG) {
-            const dfl Mp = third_body_pair<BLK>(m, x, sL, P, dt);
-            Mf = Mp.h;
-            if (KIND == 1) M = df_to_d(Mp);
-        } else {
-            M = third_body<BLK, false>(m, x, sL, cs, P, dt);
-            Mf = narrow(M);
-        }
+        const dfl Mp = third_body_pair<BLK, SG>(m, x, sL, sg, P, dt);
+        Mf = Mp.h;
+        if (KIND == 1) M = df_to_d(Mp);
     }
     const float4 xf = __ldg(reinterpret_cast<const float4*>(m.rxnf + r));   // lnA, beta, EaR
     const float lnkf = fmaf(-xf.z, P.invTf, fmaf(xf.y, P.lnTf, xf.x + shf));
@@ -344,21 +285,16 @@ __device__ __forceinline__ double rate_of_progress_mixed(const DevMech& m, const
             Ff = exp10f(lF) / (1.0f + expf(-lnPr));
         }
     }
-    double q;
-    if constexpr (LOG) {
-        const dfl lkf{lnkf, 0.0f};
-        const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
-        const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
-        q = exp_df_d(df_add(lkf, sf), dt.e2) - exp_df_d(df_add(df_add(lkf, df_neg(lnKc)), sb), dt.e2);
-        if (KIND == 2) q *= widen(Ff);
-    } else {
-        double fw, rv;
-        products_direct(x, cs, fw, rv);
-        double kf = exp_f32_to_f64(lnkf);
-        if (KIND == 2) kf = Mf == 0.0f ? 0.0 : kf * widen(Ff);
-        const double kr = kf * exp_df_d(df_neg(lnKc), dt.e2);
-        q = fma(kf, fw, -kr * rv);
+    const dfl lkf{lnkf, 0.0f};
+    const dfl sf = side_sum_df<BLK>(sL, x.sp, x.nu, x.nr);
+    const dfl sb = side_sum_df<BLK>(sL, x.sp + kMaxSide, x.nu + kMaxSide, x.np);
+    double qf = exp_df_d(df_add(lkf, sf), dt.e2), qr = exp_df_d(df_add(df_add(lkf, df_neg(lnKc)), sb), dt.e2);
+    if constexpr (SG) {
+        if (side_sign<BLK>(sg, x.sp, x.nu, x.nr)) qf = -qf;
+        if (side_sign<BLK>(sg, x.sp + kMaxSide, x.nu + kMaxSide, x.np)) qr = -qr;
     }
+    double q = qf - qr;
+    if (KIND == 2) q *= widen(Ff);
     if (KIND == 1) q *= M;
     return q;
 }
@@ -369,57 +305,42 @@ __device__ __forceinline__ void scatter(const Rxn& x, double* sW, double q) {
     scatter_side<BLK>(x.sp + kMaxSide, x.nud + kMaxSide, x.np, sW, q);
 }
 
-template <int BLK, int PREC, int KIND, bool LOG>
+template <int BLK, int PREC, int KIND, bool SG>
 __device__ __forceinline__ double q_of(const DevMech& m, const Rxn& x, int r, const double* sC, const double* sG,
-                                       const Conc& cs, const Pt& P, const double* dlnA, const MathTab& mt,
+                                       const uint8_t* sg, const Pt& P, const double* dlnA, const MathTab& mt,
                                        const DfTab& dt) {
     const float2* sL = reinterpret_cast<const float2*>(sC);
     if constexpr (PREC == kDF)
-        return rate_of_progress_df<BLK, KIND, LOG>(m, x, r, sL, cs, P, dlnA, dt);
+        return rate_of_progress_df<BLK, KIND, SG>(m, x, r, sL, sg, P, dlnA, dt);
     else if constexpr (PREC == kMixed)
-        return rate_of_progress_mixed<BLK, KIND, LOG>(m, x, r, sL, cs, P, dlnA, dt);
+        return rate_of_progress_mixed<BLK, KIND, SG>(m, x, r, sL, sg, P, dlnA, dt);
     else
         return rate_of_progress<BLK, KIND>(m, x, sC, sG, P, dlnA, mt);
 }
 
 // Reactions [r0, r1) of one kind, scattered in reaction order (one part per point).
 // (Unrolling by two or four reactions per iteration measured slower once several warps share a
-// point.)  direct: the block's products in double (a negative concentration); else the
-// logarithmic form (kDF and kMixed; the native form always takes its own).
-template <int BLK, int PREC, int KIND>
+// point.)  SG: the concentrations' signs enter (kDF and kMixed, second pass).
+template <int BLK, int PREC, int KIND, bool SG>
 __device__ __forceinline__ void reaction_group(const DevMech& m, int r0, int r1, const double* sC, const double* sG,
-                                               double* sW, const Conc& cs, bool direct, const Pt& P,
-                                               const double* dlnA, const MathTab& mt, const DfTab& dt) {
-    if (PREC == kNative || direct) {
-        for (int r = r0; r < r1; ++r) {
-            const Rxn a = load_rxn(m.rxn + r);
-            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, false>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
-        }
-    } else {
-        for (int r = r0; r < r1; ++r) {
-            const Rxn a = load_rxn(m.rxn + r);
-            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, true>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
-        }
+                                               double* sW, const uint8_t* sg, const Pt& P, const double* dlnA,
+                                               const MathTab& mt, const DfTab& dt) {
+    for (int r = r0; r < r1; ++r) {
+        const Rxn a = load_rxn(m.rxn + r);
+        scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, SG>(m, a, r, sC, sG, sg, P, dlnA, mt, dt));
     }
 }
 
 // The reactions of one kind for NP > 1 parts per point, round by round (for_rounds): the parts'
 // reactions of a round share no species, so all scatter into the point's one omega_k row.
-template <int BLK, int NP, int PREC, int KIND>
+template <int BLK, int NP, int PREC, int KIND, bool SG>
 __device__ __forceinline__ void reaction_rounds(const DevMech& m, int part, const double* sC, const double* sG,
-                                                double* sW, const Conc& cs, bool direct, const Pt& P,
-                                                const double* dlnA, const MathTab& mt, const DfTab& dt) {
-    if (PREC == kNative || direct) {
-        for_rounds<NP>(m, KIND, part, [&](int r) {
-            const Rxn a = load_rxn(m.rxn + r);
-            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, false>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
-        });
-    } else {
-        for_rounds<NP>(m, KIND, part, [&](int r) {
-            const Rxn a = load_rxn(m.rxn + r);
-            scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, true>(m, a, r, sC, sG, cs, P, dlnA, mt, dt));
-        });
-    }
+                                                double* sW, const uint8_t* sg, const Pt& P, const double* dlnA,
+                                                const MathTab& mt, const DfTab& dt) {
+    for_rounds<NP>(m, KIND, part, [&](int r) {
+        const Rxn a = load_rxn(m.rxn + r);
+        scatter<BLK>(a, sW, q_of<BLK, PREC, KIND, SG>(m, a, r, sC, sG, sg, P, dlnA, mt, dt));
+    });
 }
 
 // Per-point species arrays: C_k, then g_k/RT (native form only), then the omega_k row.
@@ -436,13 +357,13 @@ __host__ __device__ constexpr int shared_rows() {
 //
 // RHS: write the implicit-stage sources instead: omega -> W_k omega_k / rho, hrr -> hrr/(rho c_p).
 //
-// PASS (kDF and kMixed): 0 takes the blocks of the logarithmic form and skips the others, 1 takes
-// only those (a negative concentration: products in double), so the logarithmic pass compiles
-// without the double path's registers and runs six blocks of 4 warps per SM instead of five.  The
-// fallback pass leaves at once where no mass fraction of the block is negative.  The native form
-// has one pass (0) over every block.
+// PASS (kDF and kMixed): 0 takes the blocks without a negative concentration and skips the
+// others, 1 takes only those, with the concentrations' signs in a byte row after the omega_k row
+// (rates_smem_signs); so the common pass carries no sign work.  The second pass leaves at once
+// where no mass fraction of the block is negative.  The native form has one pass (0) over every
+// block.
 template <int BLK, int NP, int PREC, bool RHS, int PASS>
-__global__ void __launch_bounds__(BLK * NP, (PREC != kNative && PASS == 0 ? 768 : 640) / (BLK * NP))
+__global__ void __launch_bounds__(BLK * NP, (PREC != kNative ? 768 : 640) / (BLK * NP))
     rates_kernel(const DevMech m, const int64_t n, const int64_t ld,
                                                          const double* __restrict__ T, const double* __restrict__ p,
                                                          const double* __restrict__ Y,
@@ -475,6 +396,8 @@ __global__ void __launch_bounds__(BLK * NP, (PREC != kNative && PASS == 0 ? 768 
     double* sG = smem + kMathTabDoubles + (size_t)K * BLK + slot;     // g_k / RT (native form)
     double* sW0 = smem + kMathTabDoubles + (size_t)shared_rows<PREC>() * K * BLK + slot;
     double* sW = sW0;                                                  // omega_k
+    constexpr bool SG = PREC != kNative && PASS == 1;
+    uint8_t* sg = reinterpret_cast<uint8_t*>(sW0 - slot + (size_t)K * BLK) + slot;   // (SG) sign of C_k
 
     Pt P;
     P.T = T[i];
@@ -493,7 +416,6 @@ __global__ void __launch_bounds__(BLK * NP, (PREC != kNative && PASS == 0 ? 768 
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += Y[(int64_t)k * ld + i] * __ldg(m.invW + k);
     const double rho_w = P.pRT / s;                    // rho = p Wbar/(RT) with Wbar = 1/s
-    const Conc cs{Y, m.invW, ld, i, rho_w};
     bool neg = false;
     for (int k = part; k < K; k += NP) {
         const double c = Y[(int64_t)k * ld + i] * __ldg(m.invW + k) * rho_w;   // C_k = rho Y_k / W_k
@@ -501,11 +423,11 @@ __global__ void __launch_bounds__(BLK * NP, (PREC != kNative && PASS == 0 ? 768 
             sC[k * BLK] = c;
             sG[k * BLK] = nasa_gRT(nasa_range(m, k, P.T), P.T, P.lnT, P.invT);
         } else {
-            // ln C_k as a pair in the C_k row (zero: -2^100; negative: the block takes the products
-            // in double)
+            // ln |C_k| as a pair in the C_k row (zero: -2^100), and in the second pass its sign
             neg |= c < 0.0;
-            const dfl l = c == 0.0 ? dfl{-0x1p100f, 0.0f} : log_df(c, dt.rc, dt.lc);
+            const dfl l = c == 0.0 ? dfl{-0x1p100f, 0.0f} : log_df(SG ? fabs(c) : c, dt.rc, dt.lc);
             reinterpret_cast<float2*>(sC)[k * BLK] = make_float2(l.h, l.l);
+            if constexpr (SG) sg[k * BLK] = c < 0.0;
         }
     }
     for (int k = part; k < K; k += NP) sW[k * BLK] = 0.0;
@@ -521,18 +443,17 @@ __global__ void __launch_bounds__(BLK * NP, (PREC != kNative && PASS == 0 ? 768 
     if constexpr (PREC != kNative) {
         if (PASS == 0 ? vote : !vote) return;     // the other pass takes this block
     }
-    constexpr bool direct = PREC != kNative && PASS == 1;
 
     if constexpr (NP == 1) {
         const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
-        reaction_group<BLK, PREC, 0>(m, 0, e1, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-        reaction_group<BLK, PREC, 1>(m, e1, t1, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-        reaction_group<BLK, PREC, 2>(m, t1, m.R, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+        reaction_group<BLK, PREC, 0, SG>(m, 0, e1, sC, sG, sW, sg, P, dlnA, mt, dt);
+        reaction_group<BLK, PREC, 1, SG>(m, e1, t1, sC, sG, sW, sg, P, dlnA, mt, dt);
+        reaction_group<BLK, PREC, 2, SG>(m, t1, m.R, sC, sG, sW, sg, P, dlnA, mt, dt);
     } else {
         // (each round ends with a barrier: the omega_k row is complete after the last one)
-        reaction_rounds<BLK, NP, PREC, 0>(m, part, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-        reaction_rounds<BLK, NP, PREC, 1>(m, part, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
-        reaction_rounds<BLK, NP, PREC, 2>(m, part, sC, sG, sW, cs, direct, P, dlnA, mt, dt);
+        reaction_rounds<BLK, NP, PREC, 0, SG>(m, part, sC, sG, sW, sg, P, dlnA, mt, dt);
+        reaction_rounds<BLK, NP, PREC, 1, SG>(m, part, sC, sG, sW, sg, P, dlnA, mt, dt);
+        reaction_rounds<BLK, NP, PREC, 2, SG>(m, part, sC, sG, sW, sg, P, dlnA, mt, dt);
     }
 
     // omega_k (or the source W_k omega_k / rho), sum_k h_k/RT omega_k and, for the sources,
@@ -591,7 +512,16 @@ const void* kernel_ptr(int idx, std::integer_sequence<int, S...>) {
     return ptrs[idx];
 }
 
-// The shape's logarithmic pass, then (kDF, kMixed) its fallback pass on the same stream.
+// Shared bytes of a block: the staged tables, then the per-point species arrays; the second pass
+// adds the byte row of the concentrations' signs.
+template <int PREC>
+size_t rates_smem(int K, const Shape& sh) {
+    return (size_t)kMathTabDoubles * sizeof(double) +
+           (size_t)(shared_rows<PREC>() + 1) * K * sh.blk * sizeof(double);
+}
+inline size_t rates_smem_signs(int K, const Shape& sh) { return ((size_t)K * sh.blk + 7) / 8 * 8; }
+
+// The shape's first pass, then (kDF, kMixed) its second pass on the same stream.
 template <int PREC, bool RHS, int... S>
 cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech& m, int64_t n, int64_t ld,
                        const double* T, const double* p, const double* Y, const double* dlnA, double* omega,
@@ -607,9 +537,10 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech&
         r = cudaGetLastError();
         if (r != cudaSuccess || PREC == kNative) return r;
         auto kern1 = kernel_of<PREC, RHS, S, 1>();
-        r = ensure_smem((const void*)kern1, smem);
+        const size_t smem1 = smem + rates_smem_signs(m.K, sh);
+        r = ensure_smem((const void*)kern1, smem1);
         if (r != cudaSuccess) return r;
-        kern1<<<grid, sh.blk * sh.np, smem, st>>>(m, n, ld, T, p, Y, dlnA, omega, hrr);
+        kern1<<<grid, sh.blk * sh.np, smem1, st>>>(m, n, ld, T, p, Y, dlnA, omega, hrr);
         return cudaGetLastError();
     }())
                : (void)0),
@@ -617,12 +548,6 @@ cudaError_t launch_idx(int idx, std::integer_sequence<int, S...>, const DevMech&
     return e;
 }
 
-// Shared bytes of a block: the staged tables, then the per-point species arrays.
-template <int PREC>
-size_t rates_smem(int K, const Shape& sh) {
-    return (size_t)kMathTabDoubles * sizeof(double) +
-           (size_t)(shared_rows<PREC>() + 1) * K * sh.blk * sizeof(double);
-}
 
 // The shape with the most resident warps per SM (CUDA's occupancy calculator: shared memory,
 // registers, threads), fewer parts on ties.  Cached per
