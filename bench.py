@@ -310,6 +310,9 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
                  rates at the state (FP64), then nk_rates_jvp_linearized_compact per direction;
       per-entry  the same forward as recompute plus nk_rates_linearize, then
                  nk_rates_jvp_linearized per direction (only where its data fit: not at 16.8M points).
+    Beside them, not one of them (its products are single precision): the same forward plus
+    nk_rates_linearize_f32, then nk_rates_jvp_linearized_f32 per direction, with its error against
+    the exact FP64 JVP.
     Every call goes through the C ABI into buffers allocated before timing, and the difference
     quotients use in-place operations, so no arm waits on the allocator inside its spans.  Each
     direction is drawn (seeded, on the device) before its product, outside the timed spans; a
@@ -426,6 +429,39 @@ def implicit_stage(nk, m, T, p, Y, n_dir, steps, stream):
         sc = exact.abs().amax(0).clamp_min(1e-300)
         res["fd_jvp_median_rel_err"] = ((dw - exact).abs().amax(0) / sc).median().item()
         del exact, sc, linc
+        torch.cuda.empty_cache()
+    # the single-precision per-entry linearization (the products the reactor's FP32 Krylov basis
+    # takes), where it fits; reported beside the FP64-exact arms, not as one of them
+    slots_f = nk.linearization_slots_f32(m)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if slots_f * n * 4 < free - (4 << 30):
+        linf = torch.empty((slots_f, n), dtype=torch.float32, device=T.device)
+
+        def fwd_f32():
+            fwd_mixed()
+            chk(L.nk_rates_linearize_f32(h, n, n, P(T), P(p), P(Y), None, P(linf), n, sp))
+
+        def prod_f32(_):
+            chk(L.nk_rates_jvp_linearized_f32(h, n, n, P(T), P(p), P(Y), P(linf), n, P(vT), P(vY), P(dw), P(dh),
+                                              sp))
+
+        res["sweep_f32_ms"] = t_f = timed(fwd_f32, prod_f32)
+        res["speedup_f32_vs_fd"] = t_fd / t_f
+        res["f32_bytes"] = slots_f * n * 4
+        # its products against the exact FP64 JVP (recomputed), last direction; the exact one is
+        # kept in the difference quotient's buffer w1, the comparison runs in column chunks
+        direction(n_dir - 1)
+        recompute(None)
+        w1.copy_(dw)
+        prod_f32(None)
+        rel = torch.empty(n, **f64)
+        for a in range(0, n, 1 << 20):
+            e, x = w1[:, a:a + (1 << 20)], dw[:, a:a + (1 << 20)]
+            rel[a:a + (1 << 20)] = (x - e).abs().amax(0) / e.abs().amax(0).clamp_min(1e-300)
+        res["f32_jvp_median_rel_err"] = rel.median().item()
+        res["f32_jvp_max_rel_err"] = rel.max().item()
+        del rel, linf
         torch.cuda.empty_cache()
     lin = None
     try:

@@ -17,10 +17,10 @@
 //    per-species g_k/RT in shared memory.
 //  kDF (NK_FP64): the exponent chains -- the reaction's Gibbs sum (from its thermo groups),
 //    ln k_f, ln K_c, the Troe falloff -- in double-float pairs on the FP32 pipe (nk_df.cuh),
-//    each exponential returned as a double with one FP64 add; concentrations and their
-//    products, the forward-minus-reverse difference and the omega accumulation stay in
-//    double.  Results match the double-precision definition to ~1e-12 (the pairs carry 48
-//    bits).
+//    each exponential returned as a double with one FP64 add; the concentrations enter the
+//    rate terms' exponents as pair logarithms (their signs beside them), and the rate terms,
+//    the forward-minus-reverse difference and the omega accumulation stay in double.  Results
+//    match the double-precision definition to ~1e-12 (the pairs carry 48 bits).
 //  kMixed (NK_MIXED): the Arrhenius argument ln A + beta ln T - Ea/(RT), k_f and the whole
 //    Troe falloff in single precision; the Gibbs sum and K_c as in the kDF form (pairs), the
 //    forward-minus-reverse difference and the omega accumulation in double.
