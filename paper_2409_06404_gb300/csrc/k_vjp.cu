@@ -15,8 +15,10 @@
 // FP64 form as the rates kernel (exponent chains and, in the logarithmic form, the falloff
 // chain in double-float pairs, everything else in double).  Layout: blocks of 32 points, NP
 // warps per point sharing C_k, bar_omega_k and the Cbar_k row in shared memory, into which they
-// add in rounds of reactions that share no species (third-body efficiencies included): every
-// sum in an order fixed by the schedule.  A persistent grid walks the point tiles.
+// add in rounds of reactions that share no species (the logarithmic form on the rates kernel's
+// rounds, its efficiency terms deferred to per-species sums after each kind; the double-product
+// form on rounds that also keep efficiency species apart): every sum in an order fixed by the
+// schedule.  A persistent grid walks the point tiles.
 #include <algorithm>
 #include <mutex>
 #include <utility>
@@ -236,12 +238,14 @@ __device__ __forceinline__ void vjp_reaction(const DevMech& m, int r, const doub
 // is c1 = beta + Ea/(RT) but for Troe reactions), qcbar q_r (sum nu h/RT - sum nu) through ln K_c,
 // -Mbar p/(RT) through sum_k C_k and -bar_hrr R T q sum nu c_p/R through h_k.  The falloff chain
 // runs in pairs (troe_log).
+// DEFER: the efficiency terms wait: Mbar goes to this reaction's slot *sMb (deferred_eff adds
+// them after the kind's rounds).
 // Returns this point's term qbar_r q_r of the ln A gradient (0 without WANT_G); the caller sums
 // it over the warp.
-template <int KIND, bool WANT_G, bool HB>
+template <int KIND, bool WANT_G, bool HB, bool DEFER = false>
 __device__ __forceinline__ double vjp_reaction_log(const DevMech& m, int r, const float2* sL, const double* sWb,
                                                    double* sS, const VjpPoint& Q, const double* dlnA,
-                                                   const DfTab& dt, double& TbarT) {
+                                                   const DfTab& dt, double& TbarT, double* sMb = nullptr) {
     constexpr int BLK = kVjpBlk;
     const Rxn x = load_rxn(m.rxn + r);
     // sum_k nu_k bar_omega_k (products minus reactants) from the pair row, one conversion
@@ -307,9 +311,10 @@ __device__ __forceinline__ double vjp_reaction_log(const DevMech& m, int r, cons
     TbarT = fma(qcbar * qr, df_to_d(df_add(dH, dfl{-dnu, 0.0f})), TbarT);
     TbarT = fma(Lbar, df_to_d(kT), TbarT);
     if constexpr (KIND == 2) Mbar = Lbar * df_to_d(kM);
+    if constexpr (KIND != 0 && DEFER) *sMb = Mbar;
     if (KIND != 0 && Mbar != 0.0) {
         TbarT = fma(-Mbar, Q.pRT, TbarT);                       // sum_k C_k = p/(RT)
-        for (int j = x.eff0; j < x.eff1; ++j) {
+        for (int j = x.eff0; !DEFER && j < x.eff1; ++j) {
             const int k = __ldg(m.eff_sp + j);
             double* b = sS + k * BLK;
             const dfl ec = df_mul(dfl_of(__ldg(m.df_eff_m1 + j)), exp_df_pair(dfl_of(sL[k * BLK]), dt.e2));
@@ -386,25 +391,63 @@ __device__ __forceinline__ void vjp_group_log(const DevMech& m, int r0, int r1, 
     if (WANT_G) gb.flush(gw);
 }
 
-// The reactions of one kind for NP > 1 parts per point, round by round (for_rounds with the
-// VJP's schedule: the parts' reactions of a round share no species, efficiencies included), all
-// parts adding into the point's one row of S_k (or Cbar_k).
+// The deferred efficiency terms of kind KIND (1, 2) after its rounds: species k of this part
+// (k = part, part + NP, ...) takes C_k sum Mbar_slot (eps - 1) over its entries, in round order.
+template <int NP, int KIND>
+__device__ __forceinline__ void deferred_eff(const DevMech& m, int part, const float2* sL, double* sS,
+                                             const double* sMb, const DfTab& dt) {
+    constexpr int BLK = kVjpBlk;
+    const int K = m.K;
+    const int32_t* ptr = (NP == 2 ? m.mt_ptr2 : m.mt_ptr4) + (size_t)(KIND - 1) * (K + 1);
+    const int32_t* sl = NP == 2 ? m.mt_slot2 : m.mt_slot4;
+    const double* ev = NP == 2 ? m.mt_eps2 : m.mt_eps4;
+    for (int k = part; k < K; k += NP) {
+        const int e0 = __ldg(ptr + k), e1 = __ldg(ptr + k + 1);
+        if (e0 == e1) continue;
+        double acc = 0.0;
+        for (int e = e0; e < e1; ++e) acc = fma(sMb[__ldg(sl + e) * BLK], __ldg(ev + e), acc);
+        sS[k * BLK] = fma(acc, exp_df_d(dfl_of(sL[k * BLK]), dt.e2), sS[k * BLK]);
+    }
+}
+
+// The reactions of one kind for NP > 1 parts per point, round by round, all parts adding into
+// the point's one row of S_k (or Cbar_k).  The double-product form (direct) takes the VJP's
+// schedule (for_rounds with EFF: the parts' reactions of a round share no species, efficiencies
+// included).  The logarithmic form takes the plain schedule of the rates kernel and defers the
+// efficiency terms of third-body and Troe reactions: each leaves its Mbar in the slot of its
+// round and part (sMb), and deferred_eff adds them per species after the kind's rounds.
 template <int NP, int KIND, bool WANT_G, bool HB>
 __device__ __forceinline__ void vjp_rounds(const DevMech& m, int part, bool direct, const double* sC,
                                            const double* sWb, double* sB, double* gw, const VjpPoint& Q,
-                                           const double* dlnA, const DfTab& dt, double& Tbar) {
+                                           const double* dlnA, const DfTab& dt, double& Tbar, double* sMb) {
     if (direct) {
         for_rounds<NP, true>(m, KIND, part, [&](int r) {
             vjp_reaction<KIND, WANT_G, HB>(m, r, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
         });
     } else {
+        constexpr int BLK = kVjpBlk;
         const float2* sL = reinterpret_cast<const float2*>(sC);
+        const int32_t* S = NP == 2 ? m.rsched2 : m.rsched4;
+        const int rd0 = NP == 2 ? m.rrnd2[KIND] : m.rrnd4[KIND], rd1 = NP == 2 ? m.rrnd2[KIND + 1] : m.rrnd4[KIND + 1];
         GradBatch gb;
-        for_rounds<NP, true>(m, KIND, part, [&](int r) {
-            const double g = vjp_reaction_log<KIND, WANT_G, HB>(m, r, sL, sWb, sB, Q, dlnA, dt, Tbar);
-            if (WANT_G) gb.add(gw, r, g);
-        });
+        int r = rd0 < rd1 ? __ldg(S + rd0 * NP + part) : -1;
+        for (int rd = rd0; rd < rd1; ++rd) {
+            const int rn = rd + 1 < rd1 ? __ldg(S + (rd + 1) * NP + part) : -1;   // the next round's, early
+            if (r >= 0) {
+                const double g = vjp_reaction_log<KIND, WANT_G, HB, true>(m, r, sL, sWb, sB, Q, dlnA, dt, Tbar,
+                                                                          sMb + ((rd - rd0) * NP + part) * BLK);
+                if (WANT_G) gb.add(gw, r, g);
+            }
+            __syncthreads();
+            r = rn;
+        }
         if (WANT_G) gb.flush(gw);
+        if constexpr (KIND != 0) {
+            if (rd0 < rd1) {
+                deferred_eff<NP, KIND>(m, part, sL, sB, sMb, dt);
+                __syncthreads();                                  // before the next kind's rounds
+            }
+        }
     }
 }
 
@@ -416,11 +459,11 @@ __device__ __forceinline__ void vjp_group(const DevMech& m, int r0, int r1, cons
 }
 
 // Shared memory of a block: the pair tables, the ln A sums [R] (WANT_G), then per point C_k,
-// bar_omega_k and the Cbar_k row.
-size_t vjp_smem(int K, int R, int np, bool want_g) {
-    (void)np;
+// bar_omega_k, the Cbar_k row and (NP > 1) the deferred [M] cotangents' slots.
+int vjp_mslots(const DevMech& m, int np) { return np == 2 ? m.mslots2 : (np == 4 ? m.mslots4 : 0); }
+size_t vjp_smem(int K, int R, int mslots, bool want_g) {
     return (size_t)kMathTabDoubles * sizeof(double) + (want_g ? (size_t)((R + 1) & ~1) * sizeof(double) : 0) +
-           (size_t)3 * K * kVjpBlk * sizeof(double);
+           ((size_t)3 * K + mslots) * kVjpBlk * sizeof(double);
 }
 
 // PASS 0 takes the tiles of the logarithmic form and skips the others; PASS 1 takes only those
@@ -448,6 +491,7 @@ __global__ void __launch_bounds__(kVjpBlk * NP, (PASS == 0 ? 512 : 384) / (kVjpB
     double* sWb = base + (size_t)K * BLK;                         // bar_omega_k
     double* sB0 = base + (size_t)2 * K * BLK;                     // Cbar_k (S_k in the logarithmic form)
     double* sB = sB0;
+    double* sMb = base + (size_t)3 * K * BLK;                     // (NP > 1) deferred Mbar slots
     int ra[3], rb[3];
     const int e1 = m.R_el, t1 = m.R_el + m.R_tb;
     slice<NP>(0, e1, part, ra[0], rb[0]);
@@ -509,9 +553,9 @@ __global__ void __launch_bounds__(kVjpBlk * NP, (PASS == 0 ? 512 : 384) / (kVjpB
             }
         } else {
             // (each round ends with a barrier: the row is complete after the last one)
-            vjp_rounds<NP, 0, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            vjp_rounds<NP, 1, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
-            vjp_rounds<NP, 2, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar);
+            vjp_rounds<NP, 0, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar, sMb);
+            vjp_rounds<NP, 1, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar, sMb);
+            vjp_rounds<NP, 2, WANT_G, HB>(m, part, direct, sC, sWb, sB, gw, Q, dlnA, dt, Tbar, sMb);
         }
         if (!direct) Tbar *= Q.invT;                              // the logarithmic form sums T Tbar
         __syncthreads();
@@ -582,7 +626,7 @@ const void* kernel_ptr(int c) {
 // range; it reads the rest's Y and bar_omega once to see that).  The ln A partial sums of the two
 // passes' blocks lie one after the other in the workspace.
 struct VjpPlan {
-    int dev, K, R, variant;
+    int dev, K, R, ms2, ms4, variant;
     int parts_idx[2];   // index into kParts, per pass
     int grid_cap[2];    // blocks of each pass
 };
@@ -590,12 +634,12 @@ std::mutex g_plan_mu;
 std::vector<VjpPlan> g_plans;
 
 template <bool WANT_G, bool HB, int PASS>
-bool plan_pass(int K, int R, int sms, int per_block, int& parts_idx, int& blocks_per_sm) {
+bool plan_pass(const DevMech& m, int sms, int per_block, int& parts_idx, int& blocks_per_sm) {
     int best = -1, best_warps = 0;
     for (int c = 0; c < 3; ++c) {
         const int np = kParts[c];
-        if (np > 1 && 2 * np > K) continue;
-        const size_t bytes = vjp_smem(K, R, np, WANT_G);
+        if (np > 1 && 2 * np > m.K) continue;
+        const size_t bytes = vjp_smem(m.K, m.R, vjp_mslots(m, np), WANT_G);
         if (bytes > (size_t)per_block) continue;
         const void* kern = kernel_ptr<WANT_G, HB, PASS>(c);
         if (ensure_smem(kern, bytes) != cudaSuccess) continue;
@@ -614,14 +658,15 @@ bool plan_pass(int K, int R, int sms, int per_block, int& parts_idx, int& blocks
 }
 
 template <bool WANT_G, bool HB>
-bool plan_variant(int K, int R, VjpPlan& out) {
+bool plan_variant(const DevMech& m, VjpPlan& out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     const int variant = (WANT_G ? 1 : 0) | (HB ? 2 : 0);
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         for (const VjpPlan& q : g_plans)
-            if (q.dev == dev && q.K == K && q.R == R && q.variant == variant) {
+            if (q.dev == dev && q.K == m.K && q.R == m.R && q.ms2 == m.mslots2 && q.ms4 == m.mslots4 &&
+                q.variant == variant) {
                 out = q;
                 return true;
             }
@@ -630,17 +675,17 @@ bool plan_variant(int K, int R, VjpPlan& out) {
     cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int p0 = -1, p1 = -1, b0 = 0, b1 = 0;
-    if (!plan_pass<WANT_G, HB, 0>(K, R, sms, per_block, p0, b0)) return false;
-    if (!plan_pass<WANT_G, HB, 1>(K, R, sms, per_block, p1, b1)) return false;
-    out = VjpPlan{dev, K, R, variant, {p0, p1}, {sms * b0, sms * b1}};
+    if (!plan_pass<WANT_G, HB, 0>(m, sms, per_block, p0, b0)) return false;
+    if (!plan_pass<WANT_G, HB, 1>(m, sms, per_block, p1, b1)) return false;
+    out = VjpPlan{dev, m.K, m.R, m.mslots2, m.mslots4, variant, {p0, p1}, {sms * b0, sms * b1}};
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans.push_back(out);
     return true;
 }
 
 bool plan_for(const DevMech& m, bool want_g, bool hb, VjpPlan& out) {
-    if (want_g) return hb ? plan_variant<true, true>(m.K, m.R, out) : plan_variant<true, false>(m.K, m.R, out);
-    return hb ? plan_variant<false, true>(m.K, m.R, out) : plan_variant<false, false>(m.K, m.R, out);
+    if (want_g) return hb ? plan_variant<true, true>(m, out) : plan_variant<true, false>(m, out);
+    return hb ? plan_variant<false, true>(m, out) : plan_variant<false, false>(m, out);
 }
 
 int64_t vjp_grid(const VjpPlan& pl, int pass, int64_t n) {
@@ -656,7 +701,7 @@ cudaError_t launch_pass(const VjpPlan& pl, const DevMech& m, int64_t n, int64_t 
                         const double* Y, const double* dlnA, const double* bar_omega, const double* bar_hrr,
                         double* gT, double* gY, double* ws, cudaStream_t s) {
     const int np = kParts[pl.parts_idx[PASS]];
-    const size_t smem = vjp_smem(m.K, m.R, np, WANT_G);
+    const size_t smem = vjp_smem(m.K, m.R, vjp_mslots(m, np), WANT_G);
     const void* kp = kernel_ptr<WANT_G, HB, PASS>(pl.parts_idx[PASS]);
     cudaError_t e = ensure_smem(kp, smem);
     if (e != cudaSuccess) return e;

@@ -393,6 +393,36 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
             rrnd[v][3] = (int32_t)(S.size() / NP);
         }
     }
+    // The VJP's deferred efficiency terms on the plain rounds (nk_internal.cuh: mt_*), NP = 2, 4.
+    std::vector<int32_t> mt_ptr[2], mt_slot[2];
+    std::vector<double> mt_eps[2];
+    int32_t mslots[2] = {0, 0};
+    for (int v = 0; v < 2; ++v) {
+        const int NP = v == 0 ? 2 : 4;
+        const std::vector<int32_t>& S = rsched[v];
+        mt_ptr[v].assign((size_t)2 * (K + 1), 0);
+        for (int g = 1; g <= 2; ++g) {
+            const int rd0 = rrnd[v][g], rd1 = rrnd[v][g + 1];
+            mslots[v] = std::max(mslots[v], (rd1 - rd0) * NP);
+            std::vector<std::vector<std::pair<int32_t, double>>> by_k(K);
+            for (int rd = rd0; rd < rd1; ++rd)
+                for (int pt = 0; pt < NP; ++pt) {
+                    const int q = S[(size_t)rd * NP + pt];
+                    if (q < 0) continue;
+                    for (int j = rxn[q].eff0; j < rxn[q].eff1; ++j)
+                        by_k[eff_sp[j]].push_back({(rd - rd0) * NP + pt, eff_m1[j]});
+                }
+            int32_t* ptr = mt_ptr[v].data() + (size_t)(g - 1) * (K + 1);
+            for (int k = 0; k < K; ++k) {
+                ptr[k] = (int32_t)mt_slot[v].size();
+                for (const auto& e : by_k[k]) {
+                    mt_slot[v].push_back(e.first);
+                    mt_eps[v].push_back(e.second);
+                }
+            }
+            ptr[K] = (int32_t)mt_slot[v].size();
+        }
+    }
     // Jacobian assembly terms (nk_internal.cuh): for every entry a of reaction q (species k,
     // signed coefficient nu), V_k gets nu A_q; G_k,j gets nu B_q,b for every entry b (species j)
     // and, for third-body and Troe reactions, Lam_k gets nu L_q and G_k,j nu (eps_j - 1) L_q for
@@ -507,7 +537,10 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
                  o_fcp = L.add(f_cp.size() * 4 + 16), o_lcw = L.add(lc_w.size() * 8),
                  o_dfe = L.add(df_effm1.size() * 8 + 16), o_rs2 = L.add(rsched[0].size() * 4 + 16),
                  o_rs4 = L.add(rsched[1].size() * 4 + 16), o_rv2 = L.add(rsched[2].size() * 4 + 16),
-                 o_rv4 = L.add(rsched[3].size() * 4 + 16);
+                 o_rv4 = L.add(rsched[3].size() * 4 + 16), o_mp2 = L.add(mt_ptr[0].size() * 4 + 16),
+                 o_mp4 = L.add(mt_ptr[1].size() * 4 + 16), o_ms2 = L.add(mt_slot[0].size() * 4 + 16),
+                 o_ms4 = L.add(mt_slot[1].size() * 4 + 16), o_me2 = L.add(mt_eps[0].size() * 8 + 16),
+                 o_me4 = L.add(mt_eps[1].size() * 8 + 16);
     std::vector<unsigned char> host(L.bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) {
         if (n) std::memcpy(host.data() + off, src, n);
@@ -557,6 +590,12 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     put(o_rs4, rsched[1].data(), rsched[1].size() * 4);
     put(o_rv2, rsched[2].data(), rsched[2].size() * 4);
     put(o_rv4, rsched[3].data(), rsched[3].size() * 4);
+    put(o_mp2, mt_ptr[0].data(), mt_ptr[0].size() * 4);
+    put(o_mp4, mt_ptr[1].data(), mt_ptr[1].size() * 4);
+    put(o_ms2, mt_slot[0].data(), mt_slot[0].size() * 4);
+    put(o_ms4, mt_slot[1].data(), mt_slot[1].size() * 4);
+    put(o_me2, mt_eps[0].data(), mt_eps[0].size() * 8);
+    put(o_me4, mt_eps[1].data(), mt_eps[1].size() * 8);
     put(o_fnud, f_nud.data(), f_nud.size() * 4);
     put(o_feff, f_effm1.data(), f_effm1.size() * 4);
     put(o_fcp, f_cp.data(), f_cp.size() * 4);
@@ -643,6 +682,14 @@ nk_status nk_mechanism_load(const nk_mech_desc* d, nk_mech** out) {
     dm.rsched4 = reinterpret_cast<const int32_t*>(b + o_rs4);
     dm.rschedv2 = reinterpret_cast<const int32_t*>(b + o_rv2);
     dm.rschedv4 = reinterpret_cast<const int32_t*>(b + o_rv4);
+    dm.mt_ptr2 = reinterpret_cast<const int32_t*>(b + o_mp2);
+    dm.mt_ptr4 = reinterpret_cast<const int32_t*>(b + o_mp4);
+    dm.mt_slot2 = reinterpret_cast<const int32_t*>(b + o_ms2);
+    dm.mt_slot4 = reinterpret_cast<const int32_t*>(b + o_ms4);
+    dm.mt_eps2 = reinterpret_cast<const double*>(b + o_me2);
+    dm.mt_eps4 = reinterpret_cast<const double*>(b + o_me4);
+    dm.mslots2 = mslots[0];
+    dm.mslots4 = mslots[1];
     for (int g = 0; g < 4; ++g) {
         dm.rrnd2[g] = rrnd[0][g];
         dm.rrnd4[g] = rrnd[1][g];

@@ -157,6 +157,19 @@ struct DevMech {
     const int32_t* rschedv2;
     const int32_t* rschedv4;
     int32_t rrndv2[4], rrndv4[4];
+    // the VJP's logarithmic pass takes the plain rounds above for every kind and defers the
+    // [M] cotangents' efficiency terms: each third-body or Troe reaction leaves its Mbar in a
+    // per-point slot (round - first round of its kind) * NP + part, and after the kind's rounds
+    // species k takes sum Mbar_slot (eps - 1) over the entries [mt_ptr[(g - 1)(K + 1) + k],
+    // mt_ptr[(g - 1)(K + 1) + k + 1]) of kind g (1, 2): slots mt_slot, values mt_eps, in round
+    // order.  mslots: the slots per point (the larger kind's rounds x NP).
+    const int32_t* mt_ptr2;
+    const int32_t* mt_ptr4;
+    const int32_t* mt_slot2;
+    const int32_t* mt_slot4;
+    const double* mt_eps2;
+    const double* mt_eps4;
+    int32_t mslots2, mslots4;
     // single-precision products from an FP32 linearization: signed coefficients of each
     // reaction's entries (RxnRec::nud order, device order), efficiencies - 1 (eff_m1 order),
     // c_p/R coefficients a1..a5 per species and range ([K][2][8], low then high)
