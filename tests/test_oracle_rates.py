@@ -4,7 +4,8 @@ The paper names the species production rates and the heat release sum_k h_k omeg
 (Eq. 1a-b, Sec. 3.3) but prints no kinetics; the oracle follows the Chemkin/Cantera
 mass-action convention.  These tests pin it to what the definitions force, without
 retyping them:
-  * conservation of mass and of every element (sum_k W_k omega_k = 0, sum_k a_ek omega_k = 0);
+  * conservation of mass and of every element (sum_k W_k omega_k = 0, sum_k a_ek omega_k = 0),
+    also with negative mass fractions, whose concentrations enter as plain integer powers;
   * zero net rates at equilibrium states built from element potentials and the
     (separately pinned) Gibbs energies, at p = 1 atm and away from it;
   * the de Donder relation rev_r/fwd_r = exp(sum_k nu_kr mu_k/RT) at arbitrary states;
@@ -165,6 +166,43 @@ def test_third_body_concentration():
     m5 = _one_reaction([(0, 1), (1, 1)], [(2, 1)], W, rtype=1, eff=[5.0, 1.0, 1.0])
     fwd5, _ = oracle.rates_of_progress(m5, T, p, Y)
     assert np.allclose(fwd5[0], 1e10 * C[0] * C[1] * (p / (R_GAS * T) + 4.0 * C[0]), rtol=1e-13)
+
+
+def test_negative_concentrations_enter_as_plain_powers():
+    """Mass action with a negative concentration (a negative mass fraction): the products are
+    plain integer powers, so a squared negative concentration gives a positive term and a single
+    one a negative term, and [M] takes the signed C_k."""
+    W = [0.002, 0.032, 0.034]
+    T = np.array([900.0, 1700.0])
+    p = np.array([P_ATM, 2 * P_ATM])
+    Y = np.array([[-0.01, -1e-4], [0.6, 0.7], [0.41, 0.3001]])
+    sq = _one_reaction([(0, 2)], [(2, 1)], W)                       # 2 A -> C
+    fwd, rev = oracle.rates_of_progress(sq, T, p, Y)
+    C = _conc(sq, T, p, Y)
+    assert np.all(C[0] < 0) and np.all(fwd[0] > 0) and np.all(rev[0] > 0)
+    assert np.allclose(fwd[0], 1e10 * C[0] * C[0], rtol=1e-13)
+    ab = _one_reaction([(0, 1), (1, 1)], [(2, 1)], W)               # A + B -> C
+    fwd, _ = oracle.rates_of_progress(ab, T, p, Y)
+    assert np.all(fwd[0] < 0) and np.allclose(fwd[0], 1e10 * C[0] * C[1], rtol=1e-13)
+    tb = _one_reaction([(0, 1), (1, 1)], [(2, 1)], W, rtype=1, eff=[5.0, 1.0, 1.0])
+    fwd, _ = oracle.rates_of_progress(tb, T, p, Y)
+    assert np.allclose(fwd[0], 1e10 * C[0] * C[1] * (p / (R_GAS * T) + 4.0 * C[0]), rtol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["h2_9sp_21rx", "ch4_53sp_325rx"])
+def test_conservation_with_negative_fractions(name):
+    """Mass and elements are conserved whatever the signs of the concentrations."""
+    m = synth.mechanism(name)
+    T, p, Y = _states(m, 200, seed=23)
+    rng = np.random.default_rng(24)
+    Y = Y - 1e-3 * rng.random(Y.shape) * (rng.random(Y.shape) < 0.2)   # some fractions negative
+    assert np.any(Y < 0)
+    w, h, ws, hs = oracle.rates(m, T, p, Y, scales=True)
+    assert np.all(np.isfinite(w))
+    assert np.all(np.abs(m.W @ w) <= 1e-13 * (m.W @ ws))
+    for e in range(m.atoms.shape[1]):
+        a = m.atoms[:, e].astype(float)
+        assert np.all(np.abs(a @ w) <= 1e-13 * (a @ ws + 1e-300)), e
 
 
 def _troe_k(troe, p, T=1500.0, A0=1e12, Ainf=1e8):
