@@ -65,6 +65,8 @@ MUTATIONS = {
     "mole_fraction_inverted": ("mx.X[k] = Y[k] * mx.Wbar / S(m.W[k]);", "mx.X[k] = Y[k] * S(m.W[k]) / mx.Wbar;"),
     "rhs_jacobian_T_row_column_shift": ("            Ji[j] = ft.imag() / hstep;",
                                         "            Ji[j > 0 ? j - 1 : 0] = ft.imag() / hstep;"),
+    "powers_of_magnitudes": ("    for (int i = 0; i < m; ++i) r = r * x;",
+                             "    for (int i = 0; i < m; ++i) r = r * (re(x) < 0.0 ? -x : x);"),
 }
 
 
@@ -83,6 +85,7 @@ def _pins():
         lambda: rt.test_de_donder_relation("h2_9sp_21rx"),
         rt.test_arrhenius_special_values,
         rt.test_third_body_concentration,
+        rt.test_negative_concentrations_enter_as_plain_powers,
         rt.test_troe_lindemann_limit,
         rt.test_troe_centre_and_limits,
         lambda: rt.test_enthalpy_shift_invariance("h2_9sp_21rx"),
